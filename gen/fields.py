@@ -1,0 +1,286 @@
+"""Seeded synthetic fields with the structure of the paper's workload.
+
+The paper ran ASUCA on real JMA data (Sec. 4, "Productivity- and Performance
+Results"): a rectangular grid with 2 km spacing and 58 levels (Sec. 1.1,
+"ASUCA on GPU").  That data is not available, so these generators build
+stand-ins of the same shape:
+
+* dz stretched geometrically from 40 m to 1 km, dx = dy = 2 km;
+* rho0(z) = 1.2 exp(-z / 8000) kg/m^3, horizontally uniform;
+* theta = 300 + 0.004 z K plus four Gaussian bubbles of +-2 K;
+* tracer mixing ratios from four Gaussian blobs each, in [0, 0.02];
+* horizontally non-divergent C-grid mass fluxes MU, MV from an 8-mode sine
+  streamfunction scaled to max |u|, |v| = 20 m/s, plus one x-z overturning
+  mode (max 2 m/s) whose vertical mass flux MW follows from discrete
+  continuity, so the 3D mass divergence is zero up to rounding;
+* dt from a Courant number of 0.8.
+
+Array layout (all C order, i fastest):
+  rho, rhotheta : [nz][ny][nx]
+  rhoq          : [ntracers][nz][ny][nx]
+  mu            : [nz][ny][nx], mu[k, j, i] is the flux through face i+1/2
+  mv            : [nz][ny][nx], mv[k, j, i] is the flux through face j+1/2
+  mw            : [nz+1][ny][nx], mw[k, j, i] is the flux through the face
+                  below cell k (mw[0] and mw[nz] are the rigid lids, zero).
+
+Nothing here is arithmetic of the time step; the same arrays feed the FP64
+oracle and the CUDA library.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+import math
+
+import numpy as np
+
+SEED_BASE = 171008616
+DX = 2000.0
+DY = 2000.0
+COURANT = 0.8
+UMAX = 20.0          # max |u|, |v| of the streamfunction winds (m/s)
+OVERTURN_DU = 2.0    # max |du| of the x-z overturning mode (m/s)
+
+# Workloads by what they are; "index" offsets the seed.
+CONFIGS = {
+    "fp64_32x32x16": dict(index=0, nx=32, ny=32, nz=16, ntracers=3, nsteps=20),
+    "precision_256x256x58": dict(index=1, nx=256, ny=256, nz=58, ntracers=6, nsteps=100),
+    "adjoint_128x128x58": dict(index=2, nx=128, ny=128, nz=58, ntracers=4, nsteps=50),
+    "ensemble_32x_64to320x58": dict(index=3, members=32, nmin=64, nmax=320, nz=58,
+                                    ntracers=4, nsteps=100),
+    "large_1024x1024x58": dict(index=4, nx=1024, ny=1024, nz=58, ntracers=8, nsteps=200),
+}
+
+
+@dataclass
+class Case:
+    nx: int
+    ny: int
+    nz: int
+    ntracers: int
+    dx: float
+    dy: float
+    dz: np.ndarray
+    rho: np.ndarray
+    rhotheta: np.ndarray
+    rhoq: np.ndarray
+    mu: np.ndarray
+    mv: np.ndarray
+    mw: np.ndarray
+    dt: float
+    seed: int
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def nfields(self) -> int:
+        return 2 + self.ntracers
+
+    @property
+    def cells(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    def state(self) -> np.ndarray:
+        """All prognostic fields stacked as [F][nz][ny][nx]: rho, rho*theta, rho*q_1..N."""
+        return np.concatenate([self.rho[None], self.rhotheta[None], self.rhoq], axis=0)
+
+
+def make_dz(nz: int) -> np.ndarray:
+    """Geometric stretching, 40 m at the ground to 1 km at the top level."""
+    if nz < 2:
+        return np.full(nz, 40.0)
+    k = np.arange(nz, dtype=np.float64)
+    return 40.0 * 25.0 ** (k / (nz - 1))
+
+
+def _levels(dz: np.ndarray):
+    zf = np.concatenate([[0.0], np.cumsum(dz)])     # faces, zf[k] below cell k
+    zc = zf[:-1] + 0.5 * dz                          # cell centres
+    return zf, zc
+
+
+def _rho0(z):
+    return 1.2 * np.exp(-np.asarray(z) / 8000.0)
+
+
+def _draw_pattern(rng: np.random.Generator, ntracers: int) -> dict:
+    """Shape parameters in domain-relative coordinates; the draw order is fixed."""
+    p = {}
+    p["bub_c"] = np.stack([rng.uniform(0, 1, 4), rng.uniform(0, 1, 4), rng.uniform(0, 0.5, 4)], 1)
+    p["bub_a"] = rng.uniform(-2.0, 2.0, 4)
+    blobs = []
+    for _ in range(ntracers):
+        c = np.stack([rng.uniform(0, 1, 4), rng.uniform(0, 1, 4), rng.uniform(0, 0.5, 4)], 1)
+        a = rng.uniform(0.0, 1.0, 4)
+        blobs.append((c, a))
+    p["blobs"] = blobs
+    modes = []
+    while len(modes) < 8:
+        kx, ky = int(rng.integers(-3, 4)), int(rng.integers(-3, 4))
+        if kx == 0 and ky == 0:
+            continue
+        modes.append((kx, ky, rng.uniform(0.5, 1.0), rng.uniform(0, 2 * math.pi)))
+    p["modes"] = modes
+    p["ot_phase"] = rng.uniform(0, 2 * math.pi)
+    return p
+
+
+def _periodic_offset(x, c, L):
+    d = x - c
+    return d - L * np.round(d / L)
+
+
+def _gauss_sep(nx, ny, nz, dx, dy, zc, H, centre):
+    """exp(-r^2) on cell centres as a separable product; minimum-image in x, y."""
+    Lx, Ly = nx * dx, ny * dy
+    x = (np.arange(nx) + 0.5) * dx
+    y = (np.arange(ny) + 0.5) * dy
+    ex = np.exp(-(_periodic_offset(x, centre[0] * Lx, Lx) / (Lx / 8)) ** 2)
+    ey = np.exp(-(_periodic_offset(y, centre[1] * Ly, Ly) / (Ly / 8)) ** 2)
+    ez = np.exp(-((zc - centre[2] * H) / (H / 8)) ** 2)
+    return ez[:, None, None] * ey[None, :, None] * ex[None, None, :]
+
+
+def _streamfunction(nx, ny, dx, dy, modes):
+    """psi at cell corners (i+1/2, j+1/2) -> array [ny][nx]."""
+    Lx, Ly = nx * dx, ny * dy
+    xc = (np.arange(nx) + 1.0) * dx
+    yc = (np.arange(ny) + 1.0) * dy
+    psi = np.zeros((ny, nx))
+    for kx, ky, a, ph in modes:
+        psi += a * np.sin(2 * math.pi * (kx * xc[None, :] / Lx + ky * yc[:, None] / Ly) + ph)
+    return psi
+
+
+def _winds_from_psi(psi, dx, dy):
+    """u at faces i+1/2 and v at faces j+1/2 (per unit density) from corner psi."""
+    u = -(psi - np.roll(psi, 1, axis=0)) / dy
+    v = (psi - np.roll(psi, 1, axis=1)) / dx
+    return u, v
+
+
+def make_case(nx: int, ny: int, nz: int, ntracers: int, seed: int, *,
+              overturning: bool = True, pattern_seed: int | None = None,
+              perturb_seed: int | None = None, dtype=np.float64) -> Case:
+    """Build one seeded case.
+
+    pattern_seed draws the bubble/blob/mode parameters (domain-relative, so
+    domains of different sizes share a pattern); perturb_seed, when given, adds
+    an ensemble member's perturbation: one more bubble set of +-0.5 K and one
+    more streamfunction mode scaled to max 1 m/s.
+    """
+    if nx < 1 or ny < 1 or nz < 1 or ntracers < 0:
+        raise ValueError("bad grid size")
+    rng = np.random.default_rng(seed if pattern_seed is None else pattern_seed)
+    pat = _draw_pattern(rng, ntracers)
+    dx, dy = DX, DY
+    dz = make_dz(nz)
+    zf, zc = _levels(dz)
+    H = zf[-1]
+    rho0c = _rho0(zc)
+
+    theta = np.broadcast_to((300.0 + 0.004 * zc)[:, None, None], (nz, ny, nx)).copy()
+    for b in range(4):
+        theta += pat["bub_a"][b] * _gauss_sep(nx, ny, nz, dx, dy, zc, H, pat["bub_c"][b])
+    q = np.zeros((ntracers, nz, ny, nx))
+    for n, (c, a) in enumerate(pat["blobs"]):
+        acc = np.zeros((nz, ny, nx))
+        for b in range(4):
+            np.maximum(acc, a[b] * _gauss_sep(nx, ny, nz, dx, dy, zc, H, c[b]), out=acc)
+        q[n] = 0.02 * acc
+
+    psi = _streamfunction(nx, ny, dx, dy, pat["modes"])
+    u, v = _winds_from_psi(psi, dx, dy)
+    s = UMAX / max(np.abs(u).max(), np.abs(v).max())
+    u *= s
+    v *= s
+
+    if perturb_seed is not None:
+        prng = np.random.default_rng(perturb_seed)
+        pc = np.stack([prng.uniform(0, 1, 4), prng.uniform(0, 1, 4), prng.uniform(0, 0.5, 4)], 1)
+        pa = prng.uniform(-0.5, 0.5, 4)
+        for b in range(4):
+            theta += pa[b] * _gauss_sep(nx, ny, nz, dx, dy, zc, H, pc[b])
+        while True:
+            kx, ky = int(prng.integers(-3, 4)), int(prng.integers(-3, 4))
+            if kx or ky:
+                break
+        ppsi = _streamfunction(nx, ny, dx, dy, [(kx, ky, 1.0, prng.uniform(0, 2 * math.pi))])
+        pu, pv = _winds_from_psi(ppsi, dx, dy)
+        ps = 1.0 / max(np.abs(pu).max(), np.abs(pv).max(), 1e-300)
+        u += ps * pu
+        v += ps * pv
+
+    mu = rho0c[:, None, None] * u[None, :, :]
+    mv = rho0c[:, None, None] * v[None, :, :]
+    mu = np.ascontiguousarray(np.broadcast_to(mu, (nz, ny, nx)))
+    mv = np.ascontiguousarray(np.broadcast_to(mv, (nz, ny, nx)))
+
+    mw = np.zeros((nz + 1, ny, nx))
+    if overturning and nz >= 2:
+        # mass streamfunction Phi at (i+1/2, k+1/2) edges, zero on both lids;
+        # a whole number of wavelengths near 32 dx keeps it periodic.
+        waves = max(1, int(round(nx / 32.0)))
+        lam = nx * dx / waves
+        xe = (np.arange(nx) + 1.0) * dx
+        phi = np.sin(2 * math.pi * xe / lam + pat["ot_phase"])[None, :] * \
+            np.sin(math.pi * zf / H)[:, None]
+        phi[0] = 0.0
+        phi[-1] = 0.0
+        dmu = -(phi[1:] - phi[:-1]) / dz[:, None]              # [nz][nx]
+        amp = OVERTURN_DU / np.abs(dmu / rho0c[:, None]).max()
+        mu = mu + amp * dmu[:, None, :]
+        # discrete continuity, bottom-up from the lower lid
+        div_h = (mu - np.roll(mu, 1, axis=2)) / dx + (mv - np.roll(mv, 1, axis=1)) / dy
+        for k in range(nz):
+            mw[k + 1] = mw[k] - dz[k] * div_h[k]
+        mw[nz] = 0.0
+    rho = np.ascontiguousarray(np.broadcast_to(rho0c[:, None, None], (nz, ny, nx)))
+
+    umax = np.abs(mu / rho0c[:, None, None]).max()
+    vmax = np.abs(mv / rho0c[:, None, None]).max()
+    wmax = 0.0
+    for kf in range(1, nz):
+        w = np.abs(mw[kf]).max() / _rho0(zf[kf]) / min(dz[kf - 1], dz[kf])
+        wmax = max(wmax, w)
+    dt = COURANT / (umax / dx + vmax / dy + wmax)
+
+    cast = (lambda a: np.ascontiguousarray(a, dtype=dtype))
+    return Case(nx=nx, ny=ny, nz=nz, ntracers=ntracers, dx=dx, dy=dy, dz=dz,
+                rho=cast(rho), rhotheta=cast(rho * theta), rhoq=cast(rho[None] * q),
+                mu=cast(mu), mv=cast(mv), mw=cast(mw), dt=float(dt), seed=seed,
+                meta=dict(umax=float(umax), vmax=float(vmax), wmax_over_dz=float(wmax),
+                          top=float(H)))
+
+
+def make_config_case(name: str, *, dtype=np.float64, nx=None, ny=None, nz=None,
+                     ntracers=None, overturning=True) -> Case:
+    """The named workload's fields; sizes may be overridden for scaled-down tests."""
+    c = CONFIGS[name]
+    if "members" in c:
+        raise ValueError("use make_ensemble_cases for the ensemble workload")
+    return make_case(nx or c["nx"], ny or c["ny"], nz or c["nz"],
+                     c["ntracers"] if ntracers is None else ntracers,
+                     SEED_BASE + c["index"], overturning=overturning, dtype=dtype)
+
+
+def ensemble_sizes(members: int | None = None, nmin: int | None = None,
+                   nmax: int | None = None) -> list[int]:
+    c = CONFIGS["ensemble_32x_64to320x58"]
+    rng = np.random.default_rng(SEED_BASE + c["index"])
+    return [int(v) for v in rng.integers(nmin or c["nmin"], (nmax or c["nmax"]) + 1,
+                                         members or c["members"])]
+
+
+def make_ensemble_cases(members: int | None = None, *, sizes=None, nz=None, ntracers=None,
+                        dtype=np.float64) -> list[Case]:
+    """Uneven ensemble: member m has nx = ny drawn from U{64..320} and its own
+    perturbation seeded with SEED_BASE + index + 1000 (m + 1)."""
+    c = CONFIGS["ensemble_32x_64to320x58"]
+    seed = SEED_BASE + c["index"]
+    if sizes is None:
+        sizes = ensemble_sizes(members)
+    out = []
+    for m, n in enumerate(sizes):
+        out.append(make_case(n, n, nz or c["nz"], c["ntracers"] if ntracers is None else ntracers,
+                             seed + 1000 * (m + 1), pattern_seed=seed,
+                             perturb_seed=seed + 1000 * (m + 1), dtype=dtype))
+    return out

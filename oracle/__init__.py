@@ -1,0 +1,209 @@
+"""FP64 CPU oracle of the ASUCA-style step -- TEST INFRASTRUCTURE ONLY.
+
+Only tests/, the smoke check and the benchmark's CPU-baseline leg may import
+this package.  It compiles asuca_oracle.c (plain C, FP64, no fast-math, no FP
+contraction) into liborc.so next to the source and calls it through ctypes.
+It shares no code with the CUDA library.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "asuca_oracle.c")
+_HDR = os.path.join(_HERE, "asuca_oracle.h")
+_SO = os.path.join(_HERE, "liborc.so")
+_lock = threading.Lock()
+_lib = None
+
+LIM_KOREN, LIM_LINEAR, LIM_UPWIND1 = 0, 1, 2
+# default physics constants (relaxation time, diffusivity scale, decay height, fall speed)
+TAU, K0, KH, VSED = 3600.0, 50.0, 1000.0, 2.0
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle if the library is missing or older than its source."""
+    with _lock:
+        newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
+        if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= newest:
+            return _SO
+        cc = os.environ.get("CC", "cc")
+        tmp = _SO + f".tmp{os.getpid()}"
+        cmd = [cc, "-O2", "-fno-fast-math", "-ffp-contract=off", "-fopenmp", "-std=c11",
+               "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _SO)
+        return _SO
+
+
+class OrcGrid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("ntr", ctypes.c_int), ("dx", ctypes.c_double), ("dy", ctypes.c_double),
+                ("dz", ctypes.POINTER(ctypes.c_double)), ("tau", ctypes.c_double),
+                ("k0", ctypes.c_double), ("kh", ctypes.c_double), ("vsed", ctypes.c_double),
+                ("sed", ctypes.c_int), ("lim", ctypes.c_int)]
+
+
+_D = ctypes.POINTER(ctypes.c_double)
+_U8 = ctypes.POINTER(ctypes.c_ubyte)
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_SO)
+        G = ctypes.POINTER(OrcGrid)
+        L.orc_limiter.restype = ctypes.c_double
+        L.orc_limiter.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                  ctypes.POINTER(ctypes.c_int)]
+        L.orc_face.restype = ctypes.c_double
+        L.orc_face.argtypes = [ctypes.c_double] * 5 + [ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+        L.orc_rhs.argtypes = [G, _D, _D, _D, _D, _D, _D, _U8]
+        L.orc_euler.argtypes = [G, _D, _D, _D, _D, _D, ctypes.c_double, _D]
+        L.orc_rk3.argtypes = [G, _D, _D, _D, _D, _D, ctypes.c_double]
+        L.orc_column.argtypes = [G, _D, ctypes.c_double, _D]
+        L.orc_thomas.argtypes = [ctypes.c_int, _D, _D, _D, _D, _D]
+        L.orc_budgets.argtypes = [G, _D, ctypes.c_double, _D]
+        L.orc_step.argtypes = [G, _D, _D, _D, _D, _D, ctypes.c_double, ctypes.c_int, _D]
+        L.orc_step_window.restype = ctypes.c_int
+        L.orc_step_window.argtypes = [G, _D, _D, _D, _D, _D, ctypes.c_double, ctypes.c_int,
+                                      ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D]
+        L.orc_set_threads.argtypes = [ctypes.c_int]
+        L.orc_get_threads.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _p(a):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_D)
+
+
+class Grid:
+    """Grid + physics constants.  Defaults follow the scheme's readings."""
+
+    def __init__(self, nx, ny, nz, ntr, dz, dx=2000.0, dy=2000.0, *, tau=TAU, k0=K0, kh=KH,
+                 vsed=VSED, sed=None, lim=LIM_KOREN):
+        self.dz = np.ascontiguousarray(dz, dtype=np.float64)
+        assert self.dz.shape == (nz,)
+        if sed is None:
+            sed = ntr - 1
+        self.s = OrcGrid(nx, ny, nz, ntr, dx, dy, _p(self.dz), tau, k0, kh, vsed, sed, lim)
+        self.nx, self.ny, self.nz, self.ntr = nx, ny, nz, ntr
+
+    @classmethod
+    def from_case(cls, case, **kw):
+        return cls(case.nx, case.ny, case.nz, case.ntracers, case.dz, case.dx, case.dy, **kw)
+
+    @property
+    def F(self):
+        return 2 + self.ntr
+
+    @property
+    def shape(self):
+        return (self.F, self.nz, self.ny, self.nx)
+
+    @property
+    def ref(self):
+        return ctypes.byref(self.s)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def limiter(d0, d1, lim=LIM_KOREN):
+    b = ctypes.c_int(-1)
+    v = lib().orc_limiter(float(d0), float(d1), lim, ctypes.byref(b))
+    return v, b.value
+
+
+def face(pm1, p0, p1, p2, m, lim=LIM_KOREN):
+    b = ctypes.c_int(-1)
+    v = lib().orc_face(float(pm1), float(p0), float(p1), float(p2), float(m), lim, ctypes.byref(b))
+    return v, b.value
+
+
+def rhs(g: Grid, Y, mu, mv, mw, tend=None, branches=False):
+    Y, mu, mv, mw = _f64(Y), _f64(mu), _f64(mv), _f64(mw)
+    tend = None if tend is None else _f64(tend)
+    R = np.empty(g.shape)
+    br = np.zeros(g.shape, dtype=np.uint8) if branches else None
+    lib().orc_rhs(g.ref, _p(Y), _p(mu), _p(mv), _p(mw), _p(tend), _p(R),
+                  None if br is None else br.ctypes.data_as(_U8))
+    return (R, br) if branches else R
+
+
+def euler(g: Grid, Y, mu, mv, mw, dt, tend=None):
+    Y, mu, mv, mw = _f64(Y), _f64(mu), _f64(mv), _f64(mw)
+    tend = None if tend is None else _f64(tend)
+    out = np.empty(g.shape)
+    lib().orc_euler(g.ref, _p(Y), _p(mu), _p(mv), _p(mw), _p(tend), dt, _p(out))
+    return out
+
+
+def rk3(g: Grid, Y, mu, mv, mw, dt, tend=None):
+    Y = _f64(Y).copy()
+    mu, mv, mw = _f64(mu), _f64(mv), _f64(mw)
+    tend = None if tend is None else _f64(tend)
+    lib().orc_rk3(g.ref, _p(Y), _p(mu), _p(mv), _p(mw), _p(tend), dt)
+    return Y
+
+
+def column(g: Grid, Y, dt):
+    """Column physics (relaxation, sedimentation, diffusion); returns (Y, precip per column)."""
+    Y = _f64(Y).copy()
+    pc = np.zeros((g.ny, g.nx))
+    lib().orc_column(g.ref, _p(Y), dt, _p(pc))
+    return Y, pc
+
+
+def thomas(a, b, c, d):
+    a, b, c, d = _f64(a), _f64(b), _f64(c), _f64(d)
+    x = np.empty_like(d)
+    lib().orc_thomas(len(d), _p(a), _p(b), _p(c), _p(d), _p(x))
+    return x
+
+
+def budgets(g: Grid, Y, precip=0.0):
+    out = np.empty(g.F + 1)
+    lib().orc_budgets(g.ref, _p(_f64(Y)), float(precip), _p(out))
+    return out
+
+
+def step(g: Grid, Y, mu, mv, mw, dt, nsteps, tend=None):
+    """nsteps full steps; returns (Y, budgets[F+1]: mass, rho*theta, tracers, precip)."""
+    Y = _f64(Y).copy()
+    mu, mv, mw = _f64(mu), _f64(mv), _f64(mw)
+    tend = None if tend is None else _f64(tend)
+    bud = np.empty(g.F + 1)
+    lib().orc_step(g.ref, _p(Y), _p(mu), _p(mv), _p(mw), _p(tend), dt, nsteps, _p(bud))
+    return Y, bud
+
+
+def step_window(g: Grid, Y, mu, mv, mw, dt, nsteps, i0, j0, w, h, tend=None):
+    """nsteps steps evaluated only on the cone of the window; returns [F][nz][h][w]."""
+    Y, mu, mv, mw = _f64(Y), _f64(mu), _f64(mv), _f64(mw)
+    tend = None if tend is None else _f64(tend)
+    out = np.empty((g.F, g.nz, h, w))
+    rc = lib().orc_step_window(g.ref, _p(Y), _p(mu), _p(mv), _p(mw), _p(tend), dt, nsteps,
+                               i0, j0, w, h, _p(out))
+    if rc:
+        raise RuntimeError(f"orc_step_window failed ({rc})")
+    return out
+
+
+def set_threads(n: int):
+    lib().orc_set_threads(int(n))
+
+
+def get_threads() -> int:
+    return lib().orc_get_threads()

@@ -1,0 +1,441 @@
+/* FP64 CPU oracle of the ASUCA-style step -- TEST INFRASTRUCTURE ONLY.
+ *
+ * Plain, slow and written to be checked by eye against the scheme:
+ *   - finite-volume flux form on a rectangular 2 km grid, time-stepped by the
+ *     third-order Runge-Kutta scheme of Wicker and Skamarock (Sec. 1.1,
+ *     "ASUCA on GPU"); the stage weights are 1/3, 1/2, 1;
+ *   - horizontal (i, j) work is parallel, the K column is marched
+ *     sequentially (Sec. 1.1 and Sec. 1.3, "Memory Layout");
+ *   - physics is a per-column process applied once per long step
+ *     (Sec. 1.2, "Parallelization Granularity"; Fig. 1 and 2).
+ * The paper prints none of the operators below.  Each one is the textbook
+ * scheme the specification names, in the reading stated beside it:
+ *   - Koren limiter psi(r) = max(0, min(2r, (1 + 2r)/3, 2)) in
+ *     division-free form with sign tests;
+ *   - upwind side chosen by the sign of the face mass flux (M = 0 counts as
+ *     M >= 0); vertical ghosts copy the boundary cell; both lids carry zero
+ *     flux; the lateral boundaries are periodic;
+ *   - implicit theta relaxation, top-down implicit sedimentation, implicit
+ *     vertical diffusion by the Thomas algorithm (Lie splitting, in that
+ *     order, after the three RK stages).
+ * Parity of the full nonlinear Koren step is pinned only through the
+ * invariants the test suite checks (conservation, constant preservation,
+ * the Courant-1 shift, the linear Fourier-mode closed form, Thomas vs dense
+ * LU, sedimentation closure, relaxation fixed point).
+ *
+ * Build: cc -O2 -fno-fast-math -ffp-contract=off [-fopenmp] -shared -fPIC.
+ * OpenMP only splits independent cells or columns; every sum runs serially
+ * in a fixed order, so results do not depend on the thread count.
+ */
+#include "asuca_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* reference theta profile of the relaxation term: 300 K + 4 K/km */
+#define THETA_REF0 300.0
+#define THETA_REF_LAPSE 0.004
+
+void orc_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
+int orc_get_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+static int wrap(int i, int n) {
+    int r = i % n;
+    return r < 0 ? r + n : r;
+}
+
+/* ---------------------------------------------------------------- limiter */
+
+double orc_limiter(double d0, double d1, int lim, int *branch) {
+    int br;
+    double L;
+    if (lim == 2) {                       /* first-order upwind */
+        br = 0;
+        L = 0.0;
+    } else if (lim == 1) {                /* unlimited kappa = 1/3 */
+        br = 2;
+        L = (d0 + 2.0 * d1) / 3.0;
+    } else {
+        /* Koren: zero unless d0 and d1 are both > 0 or both < 0 (sign
+         * tests, not the product, so nothing underflows) */
+        int same = (d0 > 0.0 && d1 > 0.0) || (d0 < 0.0 && d1 < 0.0);
+        if (!same) {
+            br = 0;
+            L = 0.0;
+        } else {
+            double a0 = fabs(d0), a1 = fabs(d1);
+            double t1 = 2.0 * a1;                 /* "2r" */
+            double t2 = (a0 + 2.0 * a1) / 3.0;    /* kappa = 1/3 */
+            double t3 = 2.0 * a0;                 /* cap at 2 */
+            double m = t1;
+            br = 1;
+            if (t2 < m) { m = t2; br = 2; }       /* ties keep the earlier branch */
+            if (t3 < m) { m = t3; br = 3; }
+            L = d0 > 0.0 ? m : -m;
+        }
+    }
+    if (branch) *branch = br;
+    return L;
+}
+
+double orc_face(double pm1, double p0, double p1, double p2, double m, int lim, int *branch) {
+    if (m >= 0.0) {
+        double d0 = p0 - pm1, d1 = p1 - p0;
+        return p0 + 0.5 * orc_limiter(d0, d1, lim, branch);
+    } else {
+        double d0 = p1 - p2, d1 = p0 - p1;
+        return p1 + 0.5 * orc_limiter(d0, d1, lim, branch);
+    }
+}
+
+/* ------------------------------------------------------------ patches
+ * A patch is a rectangle of columns held in its own [F][nz][ph][pw] array.
+ * The whole domain is the periodic patch; a window patch is not periodic and
+ * is only evaluated where the stencil stays inside it. */
+typedef struct {
+    int pw, ph;     /* patch width (i) and height (j) */
+    int gi0, gj0;   /* global index of local (0, 0) */
+    int per;        /* 1: local indices wrap (whole periodic domain) */
+} patch;
+
+static double pval(const orc_grid *g, const patch *p, const double *Y, int f, int k, int lj, int li) {
+    if (p->per) {
+        li = wrap(li, p->pw);
+        lj = wrap(lj, p->ph);
+    }
+    (void)g;
+    return Y[(((size_t)f * g->nz + k) * p->ph + lj) * p->pw + li];
+}
+
+/* phi = (rho phi) / rho; the density field itself has phi = 1 */
+static double phi_at(const orc_grid *g, const patch *p, const double *Y, int f, int k, int lj, int li) {
+    return pval(g, p, Y, f, k, lj, li) / pval(g, p, Y, 0, k, lj, li);
+}
+
+static size_t gidx(const orc_grid *g, int k, int gj, int gi) {
+    return ((size_t)k * g->ny + wrap(gj, g->ny)) * g->nx + wrap(gi, g->nx);
+}
+
+/* flux through face i+1/2 (dir 0), j+1/2 (dir 1) or k+1/2 (dir 2) of local cell (li, lj, k) */
+static double face_flux(const orc_grid *g, const patch *p, const double *Y, int f, int dir,
+                        int k, int lj, int li, const double *mu, const double *mv,
+                        const double *mw, int *branch) {
+    int gi = p->gi0 + li, gj = p->gj0 + lj;
+    double m;
+    if (branch) *branch = 0;
+    if (dir == 0) {
+        m = mu[gidx(g, k, gj, gi)];
+        if (f == 0) return m;
+        return m * orc_face(phi_at(g, p, Y, f, k, lj, li - 1), phi_at(g, p, Y, f, k, lj, li),
+                            phi_at(g, p, Y, f, k, lj, li + 1), phi_at(g, p, Y, f, k, lj, li + 2),
+                            m, g->lim, branch);
+    } else if (dir == 1) {
+        m = mv[gidx(g, k, gj, gi)];
+        if (f == 0) return m;
+        return m * orc_face(phi_at(g, p, Y, f, k, lj - 1, li), phi_at(g, p, Y, f, k, lj, li),
+                            phi_at(g, p, Y, f, k, lj + 1, li), phi_at(g, p, Y, f, k, lj + 2, li),
+                            m, g->lim, branch);
+    } else {
+        int nz = g->nz;
+        if (k < 0 || k >= nz - 1) return 0.0;    /* rigid lids: no flux */
+        m = mw[gidx(g, k + 1, gj, gi)];
+        if (f == 0) return m;
+        /* ghost levels copy the boundary cell */
+        int km1 = k - 1 < 0 ? 0 : k - 1;
+        int kp2 = k + 2 > nz - 1 ? nz - 1 : k + 2;
+        return m * orc_face(phi_at(g, p, Y, f, km1, lj, li), phi_at(g, p, Y, f, k, lj, li),
+                            phi_at(g, p, Y, f, k + 1, lj, li), phi_at(g, p, Y, f, kp2, lj, li),
+                            m, g->lim, branch);
+    }
+}
+
+/* R = -[dX/dx + dY/dy + dZ/dz] + tendency on local cells [li0,li1) x [lj0,lj1) */
+static void rhs_patch(const orc_grid *g, const patch *p, const double *Y, const double *mu,
+                      const double *mv, const double *mw, const double *tend, int li0,
+                      int li1, int lj0, int lj1, double *R, unsigned char *branch) {
+    const int F = 2 + g->ntr, nz = g->nz;
+    const size_t pc = (size_t)nz * p->ph * p->pw;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
+    for (int lj = lj0; lj < lj1; lj++) {
+        for (int f = 0; f < F; f++) {
+            for (int k = 0; k < nz; k++) {
+                for (int li = li0; li < li1; li++) {
+                    int bx, by, bz;
+                    double xp = face_flux(g, p, Y, f, 0, k, lj, li, mu, mv, mw, &bx);
+                    double xm = face_flux(g, p, Y, f, 0, k, lj, li - 1, mu, mv, mw, NULL);
+                    double yp = face_flux(g, p, Y, f, 1, k, lj, li, mu, mv, mw, &by);
+                    double ym = face_flux(g, p, Y, f, 1, k, lj - 1, li, mu, mv, mw, NULL);
+                    double zp = face_flux(g, p, Y, f, 2, k, lj, li, mu, mv, mw, &bz);
+                    double zm = face_flux(g, p, Y, f, 2, k - 1, lj, li, mu, mv, mw, NULL);
+                    double r = -((xp - xm) / g->dx + (yp - ym) / g->dy + (zp - zm) / g->dz[k]);
+                    if (tend && f > 0) {
+                        int gi = p->gi0 + li, gj = p->gj0 + lj;
+                        r += tend[(size_t)(f - 1) * nz * g->ny * g->nx + gidx(g, k, gj, gi)];
+                    }
+                    size_t o = (((size_t)f * nz + k) * p->ph + lj) * p->pw + li;
+                    R[o] = r;
+                    if (branch) {
+                        /* one byte per face: 2 bits per direction (i, j, k) */
+                        branch[o] = (unsigned char)(bx | (by << 2) | (bz << 4));
+                    }
+                }
+            }
+        }
+    }
+    (void)pc;
+}
+
+void orc_rhs(const orc_grid *g, const double *Y, const double *mu, const double *mv,
+             const double *mw, const double *tend, double *R, unsigned char *branch) {
+    patch p = {g->nx, g->ny, 0, 0, 1};
+    rhs_patch(g, &p, Y, mu, mv, mw, tend, 0, g->nx, 0, g->ny, R, branch);
+}
+
+void orc_euler(const orc_grid *g, const double *Y, const double *mu, const double *mv,
+               const double *mw, const double *tend, double dt, double *out) {
+    size_t n = (size_t)(2 + g->ntr) * g->nz * g->ny * g->nx;
+    double *R = (double *)malloc(n * sizeof(double));
+    orc_rhs(g, Y, mu, mv, mw, tend, R, NULL);
+    for (size_t q = 0; q < n; q++) out[q] = Y[q] + dt * R[q];
+    free(R);
+}
+
+/* Wicker-Skamarock RK3 on a patch region: Y* = Yn + dt/3 R(Yn),
+ * Y** = Yn + dt/2 R(Y*), Yn+1 = Yn + dt R(Y**).  Each stage is evaluated on
+ * the region shrunk by `shrink` columns on every side (0 for the periodic
+ * domain, 2 per stage for a window patch). */
+static void rk3_patch(const orc_grid *g, const patch *p, double *Y, const double *mu,
+                      const double *mv, const double *mw, const double *tend, double dt,
+                      int margin, int shrink) {
+    size_t n = (size_t)(2 + g->ntr) * g->nz * p->ph * p->pw;
+    double *Yn = (double *)malloc(n * sizeof(double));
+    double *Ys = (double *)malloc(n * sizeof(double));
+    double *R = (double *)malloc(n * sizeof(double));
+    memcpy(Yn, Y, n * sizeof(double));
+    memcpy(Ys, Y, n * sizeof(double));
+    const double c[3] = {dt / 3.0, dt / 2.0, dt};
+    const int F = 2 + g->ntr, nz = g->nz;
+    for (int s = 0; s < 3; s++) {
+        int m = margin + shrink * (s + 1);
+        int li0 = m, li1 = p->pw - m, lj0 = m, lj1 = p->ph - m;
+        rhs_patch(g, p, Ys, mu, mv, mw, tend, li0, li1, lj0, lj1, R, NULL);
+        double *dst = (s == 2) ? Y : Ys;
+        for (int f = 0; f < F; f++)
+            for (int k = 0; k < nz; k++)
+                for (int lj = lj0; lj < lj1; lj++)
+                    for (int li = li0; li < li1; li++) {
+                        size_t o = (((size_t)f * nz + k) * p->ph + lj) * p->pw + li;
+                        dst[o] = Yn[o] + c[s] * R[o];
+                    }
+    }
+    free(Yn);
+    free(Ys);
+    free(R);
+}
+
+void orc_rk3(const orc_grid *g, double *Y, const double *mu, const double *mv,
+             const double *mw, const double *tend, double dt) {
+    patch p = {g->nx, g->ny, 0, 0, 1};
+    rk3_patch(g, &p, Y, mu, mv, mw, tend, dt, 0, 0);
+}
+
+/* ------------------------------------------------------------ column physics */
+
+void orc_thomas(int n, const double *a, const double *b, const double *c, const double *d,
+                double *x) {
+    /* textbook Thomas algorithm: forward elimination upward, back substitution downward */
+    double *cp = (double *)malloc((size_t)n * sizeof(double));
+    double *dp = (double *)malloc((size_t)n * sizeof(double));
+    cp[0] = c[0] / b[0];
+    dp[0] = d[0] / b[0];
+    for (int k = 1; k < n; k++) {
+        double den = b[k] - a[k] * cp[k - 1];
+        cp[k] = c[k] / den;
+        dp[k] = (d[k] - a[k] * dp[k - 1]) / den;
+    }
+    x[n - 1] = dp[n - 1];
+    for (int k = n - 2; k >= 0; k--) x[k] = dp[k] - cp[k] * x[k + 1];
+    free(cp);
+    free(dp);
+}
+
+static void level_heights(const orc_grid *g, double *zf, double *zc) {
+    zf[0] = 0.0;
+    for (int k = 0; k < g->nz; k++) zf[k + 1] = zf[k] + g->dz[k];
+    for (int k = 0; k < g->nz; k++) zc[k] = zf[k] + 0.5 * g->dz[k];
+}
+
+/* physics of one column whose values sit at stride `cs` apart in k and
+ * `fs` apart between fields; precip receives dt * P_bottom * dx * dy */
+static void column_one(const orc_grid *g, double *Y, size_t fs, size_t cs, double dt,
+                       const double *zf, const double *zc, double *precip) {
+    const int nz = g->nz, F = 2 + g->ntr;
+    /* (i) implicit relaxation of theta towards theta_ref(z) */
+    if (g->tau > 0.0) {
+        double r = dt / g->tau;
+        for (int k = 0; k < nz; k++) {
+            double rho = Y[k * cs];
+            double th = Y[fs + k * cs] / rho;
+            th = (th + r * (THETA_REF0 + THETA_REF_LAPSE * zc[k])) / (1.0 + r);
+            Y[fs + k * cs] = rho * th;
+        }
+    }
+    /* (ii) top-down implicit sedimentation of one tracer:
+     * (rho q)_k <- ((rho q)_k dz_k + dt P_{k+1/2}) / (dz_k + dt v), P_{k-1/2} = v (rho q)_k */
+    if (g->vsed > 0.0 && g->sed >= 0 && g->sed < g->ntr) {
+        double *q = Y + (size_t)(2 + g->sed) * fs;
+        double P = 0.0;
+        for (int k = nz - 1; k >= 0; k--) {
+            double dz = g->dz[k];
+            q[k * cs] = (q[k * cs] * dz + dt * P) / (dz + dt * g->vsed);
+            P = g->vsed * q[k * cs];
+        }
+        *precip += dt * P * g->dx * g->dy;
+    }
+    /* (iii) implicit vertical diffusion of every phi = (rho phi) / rho, phi != rho:
+     * a_k = -g_{k-1/2}, c_k = -g_{k+1/2}, b_k = rho_k dz_k + g_{k-1/2} + g_{k+1/2},
+     * d_k = dz_k (rho phi)_k, with g_{k+1/2} = dt rho_{k+1/2} K_{k+1/2} / dzc_{k+1/2}
+     * and g = 0 at both lids. */
+    if (g->k0 > 0.0 && nz >= 2) {
+        double *a = (double *)malloc((size_t)nz * sizeof(double));
+        double *b = (double *)malloc((size_t)nz * sizeof(double));
+        double *c = (double *)malloc((size_t)nz * sizeof(double));
+        double *d = (double *)malloc((size_t)nz * sizeof(double));
+        double *x = (double *)malloc((size_t)nz * sizeof(double));
+        double *gf = (double *)malloc((size_t)(nz + 1) * sizeof(double));
+        gf[0] = 0.0;
+        gf[nz] = 0.0;
+        for (int k = 0; k < nz - 1; k++) {
+            double rhof = 0.5 * (Y[k * cs] + Y[(k + 1) * cs]);
+            double K = g->k0 * exp(-zf[k + 1] / g->kh);
+            double dzc = zc[k + 1] - zc[k];
+            gf[k + 1] = dt * rhof * K / dzc;
+        }
+        for (int k = 0; k < nz; k++) {
+            a[k] = -gf[k];
+            c[k] = -gf[k + 1];
+            b[k] = Y[k * cs] * g->dz[k] + gf[k] + gf[k + 1];
+        }
+        for (int f = 1; f < F; f++) {
+            for (int k = 0; k < nz; k++) d[k] = g->dz[k] * Y[f * fs + k * cs];
+            orc_thomas(nz, a, b, c, d, x);
+            for (int k = 0; k < nz; k++) Y[f * fs + k * cs] = Y[k * cs] * x[k];
+        }
+        free(a); free(b); free(c); free(d); free(x); free(gf);
+    }
+}
+
+static void column_patch(const orc_grid *g, const patch *p, double *Y, double dt, int li0,
+                         int li1, int lj0, int lj1, double *precip_col) {
+    const int nz = g->nz;
+    double *zf = (double *)malloc((size_t)(nz + 1) * sizeof(double));
+    double *zc = (double *)malloc((size_t)nz * sizeof(double));
+    level_heights(g, zf, zc);
+    size_t cs = (size_t)p->ph * p->pw, fs = (size_t)nz * cs;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
+    for (int lj = lj0; lj < lj1; lj++)
+        for (int li = li0; li < li1; li++) {
+            double pr = 0.0;
+            column_one(g, Y + (size_t)lj * p->pw + li, fs, cs, dt, zf, zc, &pr);
+            if (precip_col) precip_col[(size_t)lj * p->pw + li] += pr;
+        }
+    free(zf);
+    free(zc);
+}
+
+void orc_column(const orc_grid *g, double *Y, double dt, double *precip_col) {
+    patch p = {g->nx, g->ny, 0, 0, 1};
+    column_patch(g, &p, Y, dt, 0, g->nx, 0, g->ny, precip_col);
+}
+
+/* ------------------------------------------------------------ budgets */
+
+void orc_budgets(const orc_grid *g, const double *Y, double precip, double *out) {
+    const int F = 2 + g->ntr, nz = g->nz;
+    const size_t cs = (size_t)g->ny * g->nx, fs = (size_t)nz * cs;
+    for (int f = 0; f < F; f++) {
+        double s = 0.0;
+        /* fixed order: k innermost, then i, then j */
+        for (int j = 0; j < g->ny; j++)
+            for (int i = 0; i < g->nx; i++)
+                for (int k = 0; k < nz; k++)
+                    s += Y[f * fs + k * cs + (size_t)j * g->nx + i] * g->dz[k] * g->dx * g->dy;
+        out[f] = s;
+    }
+    out[F] = precip;
+}
+
+/* ------------------------------------------------------------ the step */
+
+void orc_step(const orc_grid *g, double *Y, const double *mu, const double *mv,
+              const double *mw, const double *tend, double dt, int nsteps, double *budgets) {
+    size_t ncol = (size_t)g->ny * g->nx;
+    double *pc = (double *)calloc(ncol, sizeof(double));
+    for (int s = 0; s < nsteps; s++) {
+        orc_rk3(g, Y, mu, mv, mw, tend, dt);
+        orc_column(g, Y, dt, pc);
+    }
+    if (budgets) {
+        double tot = 0.0;
+        for (int j = 0; j < g->ny; j++)
+            for (int i = 0; i < g->nx; i++) tot += pc[(size_t)j * g->nx + i];
+        orc_budgets(g, Y, tot, budgets);
+    }
+    free(pc);
+}
+
+/* nsteps full steps evaluated only on the dependency cone of the window
+ * [i0, i0+w) x [j0, j0+h) (periodic global indices).  Each step reaches 6
+ * columns out (three stages of a 2-wide stencil), so the working patch is
+ * 6*nsteps wider on each side.  out is [F][nz][h][w].  Returns 0 on success. */
+int orc_step_window(const orc_grid *g, const double *Y, const double *mu, const double *mv,
+                    const double *mw, const double *tend, double dt, int nsteps,
+                    int i0, int j0, int w, int h, double *out) {
+    if (w <= 0 || h <= 0 || nsteps < 0) return 1;
+    const int F = 2 + g->ntr, nz = g->nz, r = 6 * nsteps;
+    patch p = {w + 2 * r, h + 2 * r, i0 - r, j0 - r, 0};
+    size_t n = (size_t)F * nz * p.ph * p.pw;
+    double *P = (double *)malloc(n * sizeof(double));
+    if (!P) return 2;
+    for (int f = 0; f < F; f++)
+        for (int k = 0; k < nz; k++)
+            for (int lj = 0; lj < p.ph; lj++)
+                for (int li = 0; li < p.pw; li++)
+                    P[(((size_t)f * nz + k) * p.ph + lj) * p.pw + li] =
+                        Y[(size_t)f * nz * g->ny * g->nx + gidx(g, k, p.gj0 + lj, p.gi0 + li)];
+    for (int s = 0; s < nsteps; s++) {
+        int margin = 6 * s;
+        rk3_patch(g, &p, P, mu, mv, mw, tend, dt, margin, 2);
+        int m = margin + 6;
+        column_patch(g, &p, P, dt, m, p.pw - m, m, p.ph - m, NULL);
+    }
+    for (int f = 0; f < F; f++)
+        for (int k = 0; k < nz; k++)
+            for (int lj = 0; lj < h; lj++)
+                for (int li = 0; li < w; li++)
+                    out[(((size_t)f * nz + k) * h + lj) * w + li] =
+                        P[(((size_t)f * nz + k) * p.ph + lj + r) * p.pw + li + r];
+    free(P);
+    return 0;
+}

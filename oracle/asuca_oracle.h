@@ -1,0 +1,58 @@
+/* FP64 CPU oracle of the ASUCA-style step -- TEST INFRASTRUCTURE ONLY.
+ *
+ * Only the test suite, the smoke check and the benchmark's CPU-baseline leg
+ * may load this library.  It shares no code, header or constant table with
+ * the CUDA library; the two meet only through the seeded inputs of the
+ * generator package.
+ *
+ * Field layout: the prognostic state Y is one array [F][nz][ny][nx] with
+ * F = 2 + ntr fields in the order rho, rho*theta, rho*q_1 .. rho*q_ntr;
+ * i is fastest.  mu[k][j][i] is the mass flux through face i+1/2,
+ * mv[k][j][i] through face j+1/2, mw[k][j][i] (k = 0..nz) through the face
+ * below cell k.  Tendencies, when given, are [F-1][nz][ny][nx] for
+ * rho*theta and the tracers.
+ */
+#ifndef ASUCA_ORACLE_H
+#define ASUCA_ORACLE_H
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+    int nx, ny, nz, ntr;
+    double dx, dy;
+    const double *dz;          /* nz layer depths */
+    double tau;                /* theta relaxation time scale (s); 0 = off */
+    double k0, kh;             /* K(z) = k0 exp(-z / kh); k0 = 0 = off */
+    double vsed;               /* sedimentation speed (m/s); 0 = off */
+    int sed;                   /* index of the sedimenting tracer; -1 = none */
+    int lim;                   /* 0 Koren, 1 linear (kappa = 1/3), 2 first-order upwind */
+} orc_grid;
+
+/* limiter increment L(d0, d1); branch receives 0 zero, 1 "2r", 2 "kappa=1/3", 3 "cap 2" */
+double orc_limiter(double d0, double d1, int lim, int *branch);
+/* face value from the four cells around face i+1/2 (values at i-1, i, i+1, i+2) */
+double orc_face(double pm1, double p0, double p1, double p2, double m, int lim, int *branch);
+
+void orc_rhs(const orc_grid *g, const double *Y, const double *mu, const double *mv,
+             const double *mw, const double *tend, double *R, unsigned char *branch);
+void orc_euler(const orc_grid *g, const double *Y, const double *mu, const double *mv,
+               const double *mw, const double *tend, double dt, double *out);
+void orc_rk3(const orc_grid *g, double *Y, const double *mu, const double *mv,
+             const double *mw, const double *tend, double dt);
+void orc_column(const orc_grid *g, double *Y, double dt, double *precip_col);
+void orc_thomas(int n, const double *a, const double *b, const double *c, const double *d,
+                double *x);
+void orc_budgets(const orc_grid *g, const double *Y, double precip, double *out);
+void orc_step(const orc_grid *g, double *Y, const double *mu, const double *mv,
+              const double *mw, const double *tend, double dt, int nsteps, double *budgets);
+int orc_step_window(const orc_grid *g, const double *Y, const double *mu, const double *mv,
+                    const double *mw, const double *tend, double dt, int nsteps,
+                    int i0, int j0, int w, int h, double *out);
+void orc_set_threads(int n);
+int orc_get_threads(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

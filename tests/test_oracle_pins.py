@@ -1,0 +1,399 @@
+"""Pins of the FP64 oracle against what the scheme and the mathematics fix.
+
+Each test is chosen so that a plausible slip in the oracle (a dropped flux
+term, a wrong sign or index, swapped MU/MV, a wrong RK weight, a wrong lid or
+ghost rule, a transposed Thomas coefficient) fails at least one of them.
+"""
+import cmath
+import math
+import os
+
+import numpy as np
+import pytest
+
+import gen
+import oracle
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _physics_off(case, **kw):
+    return oracle.Grid.from_case(case, tau=0.0, k0=0.0, vsed=0.0, **kw)
+
+
+# ------------------------------------------------------------------ limiter
+
+def _hand_table():
+    rows = []
+    with open(os.path.join(GOLDEN, "koren_hand_table.txt")) as fh:
+        for line in fh:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            d0, d1, L, br = line.split()
+            rows.append((float(d0), float(d1), float(L), int(br)))
+    return rows
+
+
+@pytest.mark.parametrize("row", _hand_table())
+def test_koren_hand_table(row):
+    d0, d1, L, br = row
+    v, b = oracle.limiter(d0, d1)
+    assert v == L and b == br
+
+
+def test_koren_matches_psi_of_r_with_division():
+    rng = np.random.default_rng(1)
+    for _ in range(2000):
+        d0 = rng.normal() * 10 ** rng.uniform(-3, 3)
+        d1 = rng.normal() * 10 ** rng.uniform(-3, 3)
+        r = d1 / d0
+        psi = max(0.0, min(2 * r, (1 + 2 * r) / 3, 2.0))
+        v, _ = oracle.limiter(d0, d1)
+        assert abs(v - psi * d0) <= 4e-16 * max(abs(d0), abs(d1)) * 4
+
+
+def test_limiter_modes_linear_and_upwind():
+    for d0, d1 in [(1.0, 2.0), (-1.0, 3.0), (0.5, -0.25)]:
+        v, b = oracle.limiter(d0, d1, oracle.LIM_LINEAR)
+        assert v == (d0 + 2 * d1) / 3 and b == 2
+        v, b = oracle.limiter(d0, d1, oracle.LIM_UPWIND1)
+        assert v == 0.0 and b == 0
+
+
+def test_face_upwind_side_follows_flux_sign():
+    # M >= 0: upwind cell i with neighbours (i-1, i+1); M < 0: mirror around i+1
+    v, _ = oracle.face(0.0, 1.0, 2.0, 10.0, 1.0, oracle.LIM_LINEAR)
+    assert v == 1.0 + 0.5 * (1.0 + 2.0 * 1.0) / 3.0
+    v, _ = oracle.face(10.0, 2.0, 1.0, 0.0, -1.0, oracle.LIM_LINEAR)
+    assert v == 1.0 + 0.5 * ((1.0 - 0.0) + 2.0 * (2.0 - 1.0)) / 3.0
+    # M = 0 counts as M >= 0
+    a, _ = oracle.face(0.0, 1.0, 2.0, 10.0, 0.0, oracle.LIM_LINEAR)
+    b, _ = oracle.face(0.0, 1.0, 2.0, 10.0, 1e-300, oracle.LIM_LINEAR)
+    assert a == b
+
+
+# ------------------------------------------------------------------ flux form
+
+def _uniform_case(nx, ny, nz, ntr, u=0.0, v=0.0, w=0.0, dz=None, rng=None, integer=False):
+    """rho = 1 and uniform M on a grid; tracers random (integers if asked)."""
+    rng = rng or np.random.default_rng(7)
+    dz = np.full(nz, 100.0) if dz is None else dz
+    F = 2 + ntr
+    Y = np.empty((F, nz, ny, nx))
+    Y[0] = 1.0
+    if integer:
+        Y[1:] = rng.integers(-50, 50, (F - 1, nz, ny, nx)).astype(np.float64)
+    else:
+        Y[1:] = rng.uniform(0.5, 1.5, (F - 1, nz, ny, nx))
+    mu = np.full((nz, ny, nx), float(u))
+    mv = np.full((nz, ny, nx), float(v))
+    mw = np.full((nz + 1, ny, nx), float(w))
+    mw[0] = 0.0
+    mw[nz] = 0.0
+    return Y, mu, mv, mw, dz
+
+
+@pytest.mark.parametrize("axis,sign", [(0, 1), (0, -1), (1, 1), (1, -1)])
+def test_courant_one_upwind_shift_is_bit_exact(axis, sign):
+    """One forward-Euler stage of first-order upwind at Courant 1 moves every
+    value exactly one cell downstream (powers of two keep all steps exact)."""
+    nx, ny, nz = 12, 10, 3
+    u = 16.0 * sign if axis == 0 else 0.0
+    v = 16.0 * sign if axis == 1 else 0.0
+    Y, mu, mv, mw, dz = _uniform_case(nx, ny, nz, 2, u=u, v=v, integer=True)
+    g = oracle.Grid(nx, ny, nz, 2, dz, 2048.0, 2048.0, tau=0, k0=0, vsed=0, lim=oracle.LIM_UPWIND1)
+    out = oracle.euler(g, Y, mu, mv, mw, 128.0)
+    expect = np.roll(Y, sign, axis=3 if axis == 0 else 2)
+    assert np.array_equal(out, expect)
+
+
+def test_courant_one_vertical_shift_with_lids():
+    """Upward Courant-1 upwind stage: interior cells take the value from below,
+    the bottom cell empties through its lid-closed lower face, the top cell
+    keeps its own value plus the inflow (rigid lids carry no flux)."""
+    nx, ny, nz = 4, 4, 6
+    Y, mu, mv, mw, dz = _uniform_case(nx, ny, nz, 1, w=16.0, dz=np.full(6, 2048.0),
+                                      integer=True)
+    g = oracle.Grid(nx, ny, nz, 1, dz, 2000.0, 2000.0, tau=0, k0=0, vsed=0,
+                    lim=oracle.LIM_UPWIND1)
+    out = oracle.euler(g, Y, mu, mv, mw, 128.0)
+    exp = np.empty_like(Y)
+    exp[:, 1:nz - 1] = Y[:, 0:nz - 2]
+    exp[:, 0] = 0.0
+    exp[:, nz - 1] = Y[:, nz - 1] + Y[:, nz - 2]
+    assert np.array_equal(out, exp)
+
+
+@pytest.mark.parametrize("axis", [0, 1])
+@pytest.mark.parametrize("mode,u", [(1, 20.0), (3, -13.0), (5, 7.5)])
+def test_linear_fourier_mode_rk3_closed_form(axis, mode, u):
+    """kappa=1/3 upwind-biased fluxes with WS-RK3 on a single Fourier mode:
+    the amplitude evolves exactly as P(lambda dt)^n, P(z) = 1 + z + z^2/2 + z^3/6,
+    lambda = -(u/dx)(1 - e^{-i th})(5 - e^{-i th} + 2 e^{i th})/6 for u >= 0."""
+    n, nz, nsteps = 32, 3, 7
+    dx = 2000.0
+    dt = 0.6 * dx / abs(u)
+    th = 2 * math.pi * mode / n
+    ph = 0.3
+    idx = np.arange(n)
+    prof = 1.0 + 0.1 * np.cos(th * idx + ph)
+    nx, ny = (n, 4) if axis == 0 else (4, n)
+    Y = np.empty((3, nz, ny, nx))
+    Y[0] = 1.0
+    Y[1] = prof[None, None, :] if axis == 0 else prof[None, :, None]
+    Y[2] = 2.0
+    mu = np.full((nz, ny, nx), u if axis == 0 else 0.0)
+    mv = np.full((nz, ny, nx), u if axis == 1 else 0.0)
+    mw = np.zeros((nz + 1, ny, nx))
+    g = oracle.Grid(nx, ny, nz, 1, np.full(nz, 50.0), dx, dx, tau=0, k0=0, vsed=0,
+                    lim=oracle.LIM_LINEAR)
+    for _ in range(nsteps):
+        Y = oracle.rk3(g, Y, mu, mv, mw, dt)
+    s = 1.0 if u >= 0 else -1.0
+    e = cmath.exp(-1j * s * th)
+    ep = cmath.exp(1j * s * th)
+    lam = -(abs(u) / dx) * (1 - e) * (5 - e + 2 * ep) / 6
+    z = lam * dt
+    amp = (1 + z + z * z / 2 + z ** 3 / 6) ** nsteps
+    exact = 1.0 + 0.1 * np.real(amp * np.exp(1j * (th * idx + ph)))
+    got = Y[1, 1, 0, :] if axis == 0 else Y[1, 1, :, 0]
+    assert np.abs(got - exact).max() < 1e-13
+    assert np.abs(Y[2] - 2.0).max() < 1e-14
+    assert np.array_equal(Y[0], np.ones_like(Y[0]))
+
+
+def test_constant_forcing_rk3_is_exact():
+    """With M = 0 the RHS is the tendency alone and RK3 adds dt * tendency."""
+    nx, ny, nz = 6, 5, 4
+    Y, mu, mv, mw, dz = _uniform_case(nx, ny, nz, 2)
+    rng = np.random.default_rng(3)
+    tend = rng.uniform(-1e-3, 1e-3, (3, nz, ny, nx))
+    g = oracle.Grid(nx, ny, nz, 2, dz, tau=0, k0=0, vsed=0)
+    out = oracle.rk3(g, Y, mu, mv, mw, 40.0, tend=tend)
+    assert np.array_equal(out[0], Y[0])
+    assert np.abs(out[1:] - (Y[1:] + 40.0 * tend)).max() < 1e-15
+
+
+# ------------------------------------------------------------------ invariants
+
+def test_mass_and_tracer_conservation_20_steps():
+    c = gen.make_config_case("fp64_32x32x16")
+    g = oracle.Grid.from_case(c)                    # all physics on
+    Y0 = c.state()
+    Y, bud = oracle.step(g, Y0, c.mu, c.mv, c.mw, c.dt, 20)
+    b0 = oracle.budgets(g, Y0)
+    F = g.F
+    assert abs(bud[0] - b0[0]) <= 1e-13 * abs(b0[0])
+    for n in range(g.ntr):
+        extra = bud[F] if n == g.ntr - 1 else 0.0   # the sedimenting tracer rains out
+        assert abs(bud[2 + n] + extra - b0[2 + n]) <= 1e-13 * abs(b0[2 + n])
+    assert bud[F] > 0.0
+
+
+@pytest.mark.parametrize("lim", [oracle.LIM_KOREN, oracle.LIM_LINEAR])
+def test_constant_tracer_is_preserved(lim):
+    c = gen.make_config_case("fp64_32x32x16")
+    g = oracle.Grid.from_case(c, vsed=0.0, lim=lim)  # relaxation + diffusion on
+    Y0 = c.state()
+    Y0[2] = 0.01 * Y0[0]
+    Y, _ = oracle.step(g, Y0, c.mu, c.mv, c.mw, c.dt, 20)
+    q = Y[2] / Y[0]
+    assert np.abs(q - 0.01).max() <= 1e-13 * 0.01
+
+
+def test_density_constant_under_nondivergent_flux():
+    c = gen.make_config_case("fp64_32x32x16")
+    g = _physics_off(c)
+    Y = oracle.rk3(g, c.state(), c.mu, c.mv, c.mw, c.dt)
+    assert np.abs(Y[0] - c.rho).max() <= 1e-13 * c.rho.max()
+
+
+def test_overturning_exercises_vertical_flux():
+    c = gen.make_config_case("fp64_32x32x16")
+    assert np.abs(c.mw[1:-1]).max() > 0.01
+    assert np.all(c.mw[0] == 0) and np.all(c.mw[-1] == 0)
+    c0 = gen.make_config_case("fp64_32x32x16", overturning=False)
+    assert np.all(c0.mw == 0)
+
+
+# ------------------------------------------------------------------ time order
+
+def test_third_order_temporal_convergence():
+    c = gen.make_config_case("fp64_32x32x16")
+    g = oracle.Grid.from_case(c, tau=0, k0=0, vsed=0, lim=oracle.LIM_LINEAR)
+    T = 8 * c.dt
+    Y0 = c.state()
+
+    def run(n):
+        Y = Y0
+        for _ in range(n):
+            Y = oracle.rk3(g, Y, c.mu, c.mv, c.mw, T / n)
+        return Y
+
+    ref = run(8 * 16)
+    errs = [np.sqrt(np.mean((run(8 * m)[2:] - ref[2:]) ** 2)) for m in (1, 2, 4)]
+    ratios = [math.log2(errs[0] / errs[1]), math.log2(errs[1] / errs[2])]
+    assert all(2.8 <= r <= 3.2 for r in ratios), (errs, ratios)
+
+
+# ------------------------------------------------------------------ column physics
+
+@pytest.mark.parametrize("n", [3, 16, 58])
+def test_thomas_matches_dense_solve(n):
+    scipy_linalg = pytest.importorskip("scipy.linalg")
+    rng = np.random.default_rng(n)
+    for _ in range(20):
+        a = rng.uniform(-1, 1, n)
+        c = rng.uniform(-1, 1, n)
+        a[0] = 0.0
+        c[-1] = 0.0
+        b = np.abs(a) + np.abs(c) + rng.uniform(0.1, 2.0, n)
+        d = rng.normal(size=n)
+        A = np.diag(b) + np.diag(a[1:], -1) + np.diag(c[:-1], 1)
+        x = oracle.thomas(a, b, c, d)
+        ref = scipy_linalg.solve(A, d)
+        assert np.abs(x - ref).max() <= 1e-13 * max(1.0, np.abs(ref).max())
+
+
+def _one_column_grid(nz, **kw):
+    dz = gen.make_dz(nz)
+    return oracle.Grid(1, 1, nz, 2, dz, **kw), dz
+
+
+def test_diffusion_conserves_and_matches_dense_system():
+    nz = 58
+    g, dz = _one_column_grid(nz, tau=0, vsed=0)
+    rng = np.random.default_rng(11)
+    Y = np.empty((4, nz, 1, 1))
+    zf = np.concatenate([[0.0], np.cumsum(dz)])
+    zc = zf[:-1] + dz / 2
+    Y[0, :, 0, 0] = 1.2 * np.exp(-zc / 8000) * (1 + 0.01 * rng.normal(size=nz))
+    Y[1:, :, 0, 0] = Y[0, :, 0, 0] * rng.uniform(0.5, 1.5, (3, nz))
+    dt = 80.0
+    out, _ = oracle.column(g, Y, dt)
+    rho = Y[0, :, 0, 0]
+    # dense system built independently from the definition of the implicit diffusion
+    A = np.zeros((nz, nz))
+    for k in range(nz - 1):
+        gk = dt * 0.5 * (rho[k] + rho[k + 1]) * 50.0 * np.exp(-zf[k + 1] / 1000.0) / (zc[k + 1] - zc[k])
+        A[k, k] += gk
+        A[k + 1, k + 1] += gk
+        A[k, k + 1] -= gk
+        A[k + 1, k] -= gk
+    A += np.diag(rho * dz)
+    for f in range(1, 4):
+        phi = np.linalg.solve(A, dz * Y[f, :, 0, 0])
+        assert np.abs(out[f, :, 0, 0] - rho * phi).max() <= 1e-13 * np.abs(rho * phi).max()
+        s0 = np.sum(Y[f, :, 0, 0] * dz)
+        assert abs(np.sum(out[f, :, 0, 0] * dz) - s0) <= 1e-14 * abs(s0)
+    assert np.array_equal(out[0], Y[0])
+    # a constant mixing ratio does not diffuse
+    Yc = Y.copy()
+    Yc[1:] = 0.37 * Y[0]
+    outc, _ = oracle.column(g, Yc, dt)
+    assert np.abs(outc[1:] / outc[0] - 0.37).max() < 1e-14
+
+
+def test_sedimentation_single_cell_and_column_closure():
+    g1 = oracle.Grid(1, 1, 1, 1, np.array([100.0]), tau=0, k0=0, vsed=2.0)
+    Y = np.array([1.0, 300.0, 0.015]).reshape(3, 1, 1, 1)
+    out, pc = oracle.column(g1, Y, 40.0)
+    assert out[2, 0, 0, 0] == 0.015 * 100.0 / (100.0 + 40.0 * 2.0)
+    assert abs(pc[0, 0] - 40.0 * 2.0 * out[2, 0, 0, 0] * 2000.0 * 2000.0) < 1e-12
+    # two levels by hand: the top level feeds the bottom one
+    g2 = oracle.Grid(1, 1, 2, 1, np.array([100.0, 200.0]), tau=0, k0=0, vsed=2.0)
+    Y2 = np.array([[1.0, 1.0], [300.0, 300.0], [0.01, 0.02]]).reshape(3, 2, 1, 1)
+    out2, pc2 = oracle.column(g2, Y2, 40.0)
+    top = 0.02 * 200.0 / (200.0 + 80.0)
+    bot = (0.01 * 100.0 + 40.0 * 2.0 * top) / (100.0 + 80.0)
+    assert out2[2, 1, 0, 0] == top and out2[2, 0, 0, 0] == bot
+    # column budget closure on a real column: sum(rho q dz) + precip / (dx dy) is unchanged
+    c = gen.make_config_case("fp64_32x32x16")
+    g = oracle.Grid.from_case(c, tau=0, k0=0)
+    Y0 = c.state()
+    out, pc = oracle.column(g, Y0, c.dt)
+    s0 = (Y0[-1] * c.dz[:, None, None]).sum(axis=0)
+    s1 = (out[-1] * c.dz[:, None, None]).sum(axis=0) + pc / (c.dx * c.dy)
+    assert np.abs(s1 - s0).max() <= 1e-14 * np.abs(s0).max()
+    assert np.array_equal(out[:-1], Y0[:-1])
+
+
+def test_relaxation_closed_form_and_fixed_point():
+    nz = 16
+    g, dz = _one_column_grid(nz, k0=0, vsed=0, tau=3600.0)
+    zf = np.concatenate([[0.0], np.cumsum(dz)])
+    zc = zf[:-1] + dz / 2
+    thref = 300.0 + 0.004 * zc
+    Y = np.empty((4, nz, 1, 1))
+    Y[0, :, 0, 0] = 1.1
+    Y[1, :, 0, 0] = 1.1 * thref
+    Y[2:] = 0.0
+    out, _ = oracle.column(g, Y, 90.0)
+    assert np.abs(out[1, :, 0, 0] / 1.1 - thref).max() < 1e-12
+    Y[1, :, 0, 0] = 1.1 * (thref + 2.0)
+    out, _ = oracle.column(g, Y, 90.0)
+    r = 90.0 / 3600.0
+    assert np.abs(out[1, :, 0, 0] / 1.1 - (thref + 2.0 / (1 + r))).max() < 1e-12
+
+
+# ------------------------------------------------------------------ windows
+
+def test_window_step_equals_full_domain_step():
+    c = gen.make_config_case("fp64_32x32x16")
+    g = oracle.Grid.from_case(c)
+    Y0 = c.state()
+    Yf, _ = oracle.step(g, Y0, c.mu, c.mv, c.mw, c.dt, 2)
+    for (i0, j0, w, h) in [(30, 5, 4, 3), (0, 0, 1, 1), (31, 31, 2, 2)]:
+        win = oracle.step_window(g, Y0, c.mu, c.mv, c.mw, c.dt, 2, i0, j0, w, h)
+        ii = [(i0 + q) % c.nx for q in range(w)]
+        jj = [(j0 + q) % c.ny for q in range(h)]
+        ref = Yf[:, :, jj][:, :, :, ii]
+        assert np.array_equal(win, ref)
+
+
+def test_thread_count_does_not_change_results():
+    c = gen.make_config_case("fp64_32x32x16")
+    g = oracle.Grid.from_case(c)
+    n0 = oracle.get_threads()
+    try:
+        oracle.set_threads(1)
+        a, ba = oracle.step(g, c.state(), c.mu, c.mv, c.mw, c.dt, 2)
+        oracle.set_threads(max(2, n0))
+        b, bb = oracle.step(g, c.state(), c.mu, c.mv, c.mw, c.dt, 2)
+    finally:
+        oracle.set_threads(n0)
+    assert np.array_equal(a, b) and np.array_equal(ba, bb)
+
+
+@pytest.mark.parametrize("w", [1.0, -1.0])
+def test_vertical_kappa_third_exact_for_quadratics_and_ghosts(w):
+    """The kappa=1/3 face value is exact for cell averages of z^2: with
+    phi_k = k^2 + 1/12 (average of z^2 over [k-1/2, k+1/2]) every face whose
+    stencil is interior gets (k+1/2)^2.  Next to a lid the ghost copies the
+    boundary cell, so d0 = 0 there and the face is phi_up + (phi_down - phi_up)/3."""
+    from fractions import Fraction as Fr
+    nz = 9
+    phi = [Fr(k * k) + Fr(1, 12) for k in range(nz)]
+    face = {}
+    for k in range(nz - 1):                       # face k+1/2
+        if w > 0 and k == 0:
+            face[k] = phi[0] + (phi[1] - phi[0]) / 3
+        elif w < 0 and k == nz - 2:
+            face[k] = phi[nz - 1] + (phi[nz - 2] - phi[nz - 1]) / 3
+        else:
+            face[k] = (Fr(2 * k + 1, 2)) ** 2
+    Zp = lambda k: Fr(0) if k < 0 or k >= nz - 1 else Fr(int(w)) * face[k]
+    expect = [-(Zp(k) - Zp(k - 1)) for k in range(nz)]
+    Y = np.empty((3, nz, 4, 4))
+    Y[0] = 1.0
+    Y[1] = np.array([float(p) for p in phi])[:, None, None]
+    Y[2] = 1.0
+    mu = np.zeros((nz, 4, 4))
+    mv = np.zeros((nz, 4, 4))
+    mw = np.full((nz + 1, 4, 4), w)
+    mw[0] = mw[nz] = 0.0
+    g = oracle.Grid(4, 4, nz, 1, np.ones(nz), tau=0, k0=0, vsed=0, lim=oracle.LIM_LINEAR)
+    R = oracle.rhs(g, Y, mu, mv, mw)
+    got = R[1, :, 2, 1]
+    assert np.abs(got - np.array([float(e) for e in expect])).max() < 1e-12
