@@ -1,0 +1,371 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300-native ASUCA-style RK3 step.
+
+Metric: grid-cell updates per second per RK3 step (one step = three RK stage
+sweeps + the column pass + FP64 budgets), on the 1024x1024x58, 8-tracer
+workload with FP32 fields and stencils and an FP64 Thomas solve and sums; the
+all-FP64 path is timed on the same workload beside it.  Inputs are seeded
+synthetic fields (gen/), resident in HBM when the timed region starts; the
+2.4 GB state is larger than L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (test infrastructure) on the host
+cores, each step a bounded sample of the same workload.  Under torchrun
+(N > 1) every rank advances its own replica (no data-path collective; weak
+scaling) and rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "cell-updates/s per RK3 step (FP32 vs FP64), % HBM roofline; adjoint/fwd cost"
+UNIT = "cell-updates/s"
+WORKLOAD = "large_1024x1024x58"
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------- helpers
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _max_over_ranks(ws, v):
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_oracle_rate(min_seconds=10.0, nx=256, ny=256, steps_cap=50):
+    """The FP64 oracle as it stands on the host cores: 256x256x58, 8 tracers."""
+    import gen
+    import oracle
+    case = gen.make_case(nx, ny, 58, 8, seed=gen.SEED_BASE + 4)
+    g = oracle.Grid.from_case(case)
+    Y = case.state()
+    oracle.step(g, Y, case.mu, case.mv, case.mw, case.dt, 1)       # warm, builds the library
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        Y, _ = oracle.step(g, Y, case.mu, case.mv, case.mw, case.dt, 1)
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= min_seconds or n >= steps_cap:
+            break
+    return {"value": case.cells * n / el, "unit": UNIT, "cores": oracle.get_threads(),
+            "kind": "oracle",
+            "sample": f"{n} step(s) of a {nx}x{ny}x58 periodic domain with 8 tracers (same per-cell "
+                      f"work as the 1024x1024x58 workload), {el:.1f} s, FP64, OpenMP over j"}
+
+
+# ---------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import gen
+    import oracle
+    nx = ny = args.ref_n
+    case = gen.make_case(nx, ny, 58, 8, seed=gen.SEED_BASE + 4)
+    g = oracle.Grid.from_case(case)
+    Y = case.state()
+    for _ in range(args.warmup):
+        Y, _b = oracle.step(g, Y, case.mu, case.mv, case.mw, case.dt, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        Y, _b = oracle.step(g, Y, case.mu, case.mv, case.mw, case.dt, 1)
+    el = time.perf_counter() - t0
+    value = case.cells * args.steps / el
+    cores = oracle.get_threads()
+    sample = (f"each step: one oracle RK3 step of a {nx}x{ny}x58 periodic domain with 8 tracers "
+              f"(the 1024x1024x58 workload's per-cell work on a bounded sample), FP64")
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "impl": "reference",
+           "config": {"workload": WORKLOAD, "sample": f"{nx}x{ny}x58", "ntracers": 8,
+                      "precision": "fp64 (CPU oracle)"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- our arm
+
+def _time_steps(asuca, g, st, dt, ws_t, bud, steps, warmup, world, profile=False):
+    import torch
+    for _ in range(warmup):
+        asuca.step(g, st, dt, 1, workspace=ws_t, budgets=bud)
+    torch.cuda.synchronize()
+    if profile:
+        asuca.profile_enable(g, True)
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    _barrier(world)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        asuca.step(g, st, dt, 1, workspace=ws_t, budgets=bud)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    _barrier(world)
+    ms = e0.elapsed_time(e1)
+    prof = asuca.profile_read(g) if profile else None
+    if profile:
+        asuca.profile_enable(g, False)
+    assert asuca.get_status(g) == asuca.OK
+    return ms, prof
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    world, rank, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    from paper_1710_08616_gb300 import build as _b
+    _b.build()
+    import paper_1710_08616_gb300 as asuca
+    import gen
+
+    case = gen.make_config_case(WORKLOAD)
+    F = case.nfields
+    C = case.cells
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    # ---- FP32-mixed, device-resident (headline)
+    g = asuca.Grid.from_case(case, prec=asuca.FP32_MIXED)
+    st = asuca.State.from_case(case, prec=asuca.FP32_MIXED, device=dev)
+    ws_t = g.workspace(device=dev)
+    bud = torch.empty(F + 1, dtype=torch.float64, device=dev)
+    props = torch.cuda.get_device_properties(dev)
+    gpu_id = str(getattr(props, "uuid", "")) or str(local)
+    if gpu_id and not gpu_id.startswith("GPU-") and len(gpu_id) > 8:
+        gpu_id = "GPU-" + gpu_id
+    sampler = ClockSampler(gpu_id if rank == 0 else str(local))
+    if rank == 0:
+        sampler.start()
+    ms, prof = _time_steps(asuca, g, st, case.dt, ws_t, bud, args.steps, args.warmup, world, profile=True)
+    clocks = sampler.stop() if rank == 0 else None
+    ms = _max_over_ranks(world, ms)
+    value = world * C * args.steps / (ms * 1e-3)
+
+    # ---- roofline of the dominant kernel, from the live per-kernel events
+    hbm_peak, peak_kind = _peaks()
+    s = 4
+    kinds = {asuca.KERNEL_STAGE: "stage", asuca.KERNEL_COLUMN: "column", asuca.KERNEL_REDUCE: "budget_reduce"}
+    # algorithmic bytes per launch (values per cell): stage 1 reads Yn and M, writes Y*;
+    # stages 2 and 3 read Y^(s-1), Yn and M and write; the column pass reads F and writes F-1.
+    algo = {asuca.KERNEL_STAGE: ((2 * F + 3) + 2 * (3 * F + 3)) / 3.0 * C * s,
+            asuca.KERNEL_COLUMN: (2 * F - 1) * C * s,
+            asuca.KERNEL_REDUCE: 0.0}
+    kern = {}
+    for k, (tot, n) in (prof or {}).items():
+        avg = tot / n
+        kern[kinds.get(k, str(k))] = {"launches": n, "total_ms": tot, "avg_ms": avg,
+                                      "share": tot / max(sum(v[0] for v in prof.values()), 1e-30),
+                                      "algo_bytes_per_launch": algo.get(k, 0.0),
+                                      "achieved_gbs": algo.get(k, 0.0) / (avg * 1e-3) / 1e9 if avg else None}
+    dom = max(prof.items(), key=lambda kv: kv[1][0])[0] if prof else asuca.KERNEL_STAGE
+    dname = kinds.get(dom, str(dom))
+    ach = kern[dname]["achieved_gbs"] if dname in kern else None
+    roofline = {"kernel": dname, "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                "frac": (ach / hbm_peak) if ach else None, "peak_source": peak_kind,
+                "traffic": None,
+                "step_frac": (10 * F + 8) * s * C / (ms / args.steps * 1e-3) / 1e9 / hbm_peak,
+                "step_model_bytes_per_cell": (10 * F + 8) * s, "kernels": kern}
+
+    # ---- e2e through the C ABI with pinned host buffers, copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        host = {k: getattr(st, k).cpu().pin_memory() for k in ("rho", "rhotheta", "rhoq", "mu", "mv", "mw")}
+        hbud = torch.empty(F + 1, dtype=torch.float64).pin_memory()
+        h2d = sum(t.numel() * t.element_size() for t in host.values())
+        d2h = sum(host[k].numel() * host[k].element_size() for k in ("rho", "rhotheta", "rhoq")) + hbud.numel() * 8
+        ne = max(1, min(args.steps, args.e2e_steps))
+
+        def e2e_step():
+            for k, t in host.items():
+                getattr(st, k).copy_(t, non_blocking=True)
+            asuca.step(g, st, case.dt, 1, workspace=ws_t, budgets=bud)
+            for k in ("rho", "rhotheta", "rhoq"):
+                host[k].copy_(getattr(st, k), non_blocking=True)
+            hbud.copy_(bud, non_blocking=True)
+
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        _barrier(world)
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record()
+        for _ in range(ne):
+            e2e_step()
+        a1.record()
+        torch.cuda.synchronize()
+        _barrier(world)
+        ems = _max_over_ranks(world, a0.elapsed_time(a1))
+        e2e = {"value": world * C * ne / (ems * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "steps": ne, "ms_per_step": ems / ne}
+        del host
+    del st, ws_t
+    torch.cuda.empty_cache()
+
+    # ---- all-FP64 path on the same workload
+    fp64 = None
+    if not args.no_fp64:
+        g64 = asuca.Grid.from_case(case, prec=asuca.FP64)
+        st64 = asuca.State.from_case(case, prec=asuca.FP64, device=dev)
+        ws64 = g64.workspace(device=dev)
+        bud64 = torch.empty(F + 1, dtype=torch.float64, device=dev)
+        n64 = max(1, min(args.steps, args.fp64_steps))
+        ms64, prof64 = _time_steps(asuca, g64, st64, case.dt, ws64, bud64, n64, 1, world, profile=True)
+        ms64 = _max_over_ranks(world, ms64)
+        fp64 = {"value": world * C * n64 / (ms64 * 1e-3), "ms_per_step": ms64 / n64, "steps": n64,
+                "kernels": {kinds.get(k, str(k)): {"launches": n, "avg_ms": t / n} for k, (t, n) in prof64.items()}}
+        del st64, ws64
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_oracle_rate()
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+               "config": {"workload": WORKLOAD, "nx": case.nx, "ny": case.ny, "nz": case.nz,
+                          "ntracers": case.ntracers, "cells": C, "dt_s": case.dt,
+                          "precision": "fp32 fields/stencils/physics, fp64 Thomas solve and budget sums",
+                          "limiter": "koren", "l2": "inputs larger than L2 (2.4 GB state), no flush",
+                          "parallelism": f"{world} independent replica(s), one per GPU"},
+               "clocks": clocks, "gpu_launches": 5 * args.steps, "roofline": roofline,
+               "e2e": e2e, "fp64": fp64,
+               "fp32_over_fp64_speedup": (value / fp64["value"]) if fp64 else None,
+               "cpu_baseline": cpu}
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--fp64-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--ref-n", type=int, default=128, help="reference arm sample size (n x n x 58)")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,167 @@
+/* libasuca -- C ABI of the GB300-native ASUCA-style time step.
+ *
+ * The computation is the structured-grid weather step the Hybrid Fortran
+ * paper ports to GPUs (arXiv 1710.08616): a finite-volume scheme on a
+ * rectangular grid advanced by Wicker-Skamarock RK3 (Sec. 1.1 "ASUCA on
+ * GPU"), parallel over the horizontal I/J columns with the K column marched
+ * in one thread (Sec. 1.1, Sec. 1.3 "Memory Layout"), followed by per-column
+ * physics applied at column granularity (Sec. 1.2 "Parallelization
+ * Granularity"; Fig. 1 and 2).  The paper prints no operator, so the
+ * operators are the textbook ones named here:
+ *   - prognostic fields rho, rho*theta, rho*q_1..N in flux form on an
+ *     Arakawa-C grid, periodic in i and j, rigid lids (zero flux) in k;
+ *   - face values from the Koren limiter (or the unlimited kappa = 1/3
+ *     scheme, or first-order upwind) on the side the face mass flux comes
+ *     from (M = 0 counts as M >= 0), vertical ghost levels copying the
+ *     boundary cell;
+ *   - RK3 stages Y* = Yn + dt/3 R(Yn), Y** = Yn + dt/2 R(Y*),
+ *     Yn+1 = Yn + dt R(Y**), R = -div(M phi_face) + tendency;
+ *   - then, per column: implicit theta relaxation to 300 + 0.004 z K,
+ *     top-down implicit sedimentation of one tracer, and implicit vertical
+ *     diffusion of theta and every q by a Thomas solve whose factorisation
+ *     is shared by all fields (FP64 in both precisions);
+ *   - FP64 budgets: total mass, rho*theta, each tracer, precipitation.
+ *
+ * Memory and streams belong to the caller.  Every device pointer is
+ * caller-owned device memory; the library never allocates device memory
+ * (it allocates a few bytes of pinned host memory per grid for its status
+ * word).  Every call is asynchronous on the given CUDA stream (NULL = the
+ * legacy default stream).  Argument errors are returned synchronously;
+ * errors found on the device (non-finite budgets, a barrier that timed out)
+ * are written to the grid's status word and returned by the next call on
+ * that grid or by asuca_get_status().
+ *
+ * Field layout: every 3D field is [nz][ny][nx] with i fastest and no
+ * padding ("IJK" order of Sec. 1.3).  rhoq holds the N tracer fields back
+ * to back ([N][nz][ny][nx]).  mu[k][j][i] is the mass flux through face
+ * i+1/2, mv[k][j][i] through face j+1/2, and mw ([nz+1][ny][nx]) through the
+ * face below cell k; mw[0] and mw[nz] are the lids and are never read.
+ * The element type of every field is double for ASUCA_FP64 and float for
+ * ASUCA_FP32_MIXED.
+ */
+#ifndef ASUCA_H
+#define ASUCA_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ASUCA_MAX_TRACERS 8
+#define ASUCA_MAX_NZ 128
+
+typedef enum {
+    ASUCA_OK = 0,
+    ASUCA_ERR_ARG = 1,          /* invalid argument (returned synchronously) */
+    ASUCA_ERR_CUDA = 2,         /* a CUDA runtime call failed */
+    ASUCA_ERR_WORKSPACE = 3,    /* workspace missing, misaligned or too small */
+    ASUCA_ERR_NONFINITE = 4,    /* a budget sum was NaN or infinite */
+    ASUCA_ERR_TIMEOUT = 5,      /* a device-wide barrier gave up waiting */
+    ASUCA_ERR_UNSUPPORTED = 6   /* sizes beyond the compiled limits */
+} asuca_status;
+
+typedef enum {
+    ASUCA_FP64 = 0,             /* every operation in double */
+    ASUCA_FP32_MIXED = 1        /* float fields and stencils; double Thomas solve and sums */
+} asuca_precision;
+
+typedef enum {
+    ASUCA_LIM_KOREN = 0,        /* psi(r) = max(0, min(2r, (1 + 2r)/3, 2)) */
+    ASUCA_LIM_LINEAR = 1,       /* unlimited kappa = 1/3 upwind-biased face value */
+    ASUCA_LIM_UPWIND1 = 2       /* first-order upwind */
+} asuca_limiter;
+
+typedef enum {
+    ASUCA_OP_STEP = 0,
+    ASUCA_OP_ADJOINT = 1,
+    ASUCA_OP_ENSEMBLE = 2
+} asuca_op;
+
+typedef struct {
+    int nx, ny, nz;             /* nx, ny >= 4; 3 <= nz <= ASUCA_MAX_NZ */
+    int ntracers;               /* 0 .. ASUCA_MAX_TRACERS */
+    double dx, dy;              /* horizontal spacing (m), > 0 */
+    const double *dz;           /* host array of nz layer depths (m), > 0; copied */
+    double tau_theta;           /* theta relaxation time (s); 0 disables it */
+    double k0, k_h;             /* K(z) = k0 exp(-z / k_h) (m^2/s); k0 = 0 disables diffusion */
+    double v_sed;               /* fall speed (m/s); 0 disables sedimentation */
+    int sed_tracer;             /* index of the sedimenting tracer; -1 = none */
+    asuca_limiter lim;
+    asuca_precision prec;
+} asuca_grid_desc;
+
+typedef struct asuca_grid asuca_grid;   /* opaque, host side */
+
+typedef struct {
+    void *rho, *rhotheta, *rhoq;        /* updated in place */
+    const void *mu, *mv, *mw;           /* steady mass fluxes */
+} asuca_state;
+
+/* Create a grid: validates the description, copies dz, precomputes level
+ * tables.  *out receives the grid; free it with asuca_free_grid. */
+asuca_status asuca_init_grid(const asuca_grid_desc *desc, asuca_grid **out);
+asuca_status asuca_free_grid(asuca_grid *grid);
+
+/* Bytes of device workspace op needs (256-byte aligned pointer required).
+ * ASUCA_OP_STEP: two stage states plus the column-solve scratch, per-column
+ * precipitation and budget partials.  ASUCA_OP_ADJOINT: param = checkpoint
+ * interval K (states kept every K steps, one segment recomputed).  Returns 0
+ * for an invalid grid or op. */
+size_t asuca_workspace_bytes(const asuca_grid *grid, int op, int param);
+
+/* Advance the state by nsteps RK3 steps, each followed by the column physics
+ * (Sec. 1.1 RK3 long step; Sec. 1.2 column processes).  tendencies, if not
+ * NULL, are 1+N fields ([1+N][nz][ny][nx], rho*theta then the tracers) of
+ * constant forcing added in every stage.  budgets_dev, if not NULL, receives
+ * N+3 doubles on the device: total mass, total rho*theta, each tracer's
+ * total (all sum(field * dz * dx * dy)) after the last step, and the
+ * precipitation accumulated over these nsteps.  nsteps = 0 only computes
+ * the budgets. */
+asuca_status asuca_step(asuca_grid *grid, asuca_state *state, const void *tendencies, double dt,
+                        int nsteps, void *workspace, size_t workspace_bytes, double *budgets_dev,
+                        void *cuda_stream);
+
+/* Synchronise the stream of the last call on this grid, return and clear
+ * the device status word (ASUCA_OK when no device error was recorded). */
+asuca_status asuca_get_status(asuca_grid *grid);
+const char *asuca_status_string(asuca_status s);
+
+/* ---- sub-steps, exported for per-kernel parity tests ------------------ */
+
+/* One RK stage: out = base + cdt * R(in), with M taken from in.  in, base
+ * and out may alias only as in == base (a forward-Euler stage). */
+asuca_status asuca_debug_stage(asuca_grid *grid, const asuca_state *in, const asuca_state *base,
+                               asuca_state *out, const void *tendencies, double cdt,
+                               void *cuda_stream);
+
+/* The column pass alone (relaxation, sedimentation, diffusion) at step dt.
+ * precip_col_dev ([ny][nx] doubles) is incremented by each column's
+ * precipitation (dt * P_bottom * dx * dy). */
+asuca_status asuca_debug_column(asuca_grid *grid, asuca_state *state, double dt,
+                                double *precip_col_dev, void *workspace, size_t workspace_bytes,
+                                void *cuda_stream);
+
+/* ---- per-kernel timing ------------------------------------------------- */
+
+typedef enum {
+    ASUCA_KERNEL_STAGE = 0,     /* one RK stage sweep */
+    ASUCA_KERNEL_COLUMN = 1,    /* column physics + Thomas solve (+ budget partials) */
+    ASUCA_KERNEL_REDUCE = 2,    /* final budget reduction */
+    ASUCA_KERNEL_KINDS = 8
+} asuca_kernel_kind;
+
+/* When on, every kernel launch of later calls on this grid is bracketed by
+ * two CUDA events on the call's stream (host-side event objects, created on
+ * demand; no device memory).  Turning it on or off discards pending marks. */
+asuca_status asuca_profile_enable(asuca_grid *grid, int on);
+
+/* Wait for the last recorded event, then report per kernel kind the summed
+ * event-measured duration (ms[kind]) and launch count since the last read;
+ * clears the marks.  nkinds entries are written. */
+asuca_status asuca_profile_read(asuca_grid *grid, double *ms, int *launches, int nkinds);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,262 @@
+"""Python binding of libasuca (the C ABI in include/asuca.h).
+
+Argument marshalling only: every step of the time step runs in the CUDA
+kernels of libasuca.so.  PyTorch supplies device memory (tensors) and
+streams.  There is no CPU fallback: if the compiled library is missing,
+every entry point raises.
+
+The computation is the ASUCA-style step that the Hybrid Fortran paper
+(arXiv 1710.08616) ports to GPUs: Wicker-Skamarock RK3 of flux-form rho,
+rho*theta and rho*q_n with Koren-limited i/j/k fluxes on a periodic
+Arakawa-C grid (Sec. 1.1 "ASUCA on GPU"), then per-column physics and an
+FP64 implicit vertical-diffusion solve (Sec. 1.2 "Parallelization
+Granularity"), with i-fastest fields (Sec. 1.3 "Memory Layout").
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .build import LIB as _LIB_PATH
+
+OK, ERR_ARG, ERR_CUDA, ERR_WORKSPACE, ERR_NONFINITE, ERR_TIMEOUT, ERR_UNSUPPORTED = range(7)
+FP64, FP32_MIXED = 0, 1
+LIM_KOREN, LIM_LINEAR, LIM_UPWIND1 = 0, 1, 2
+OP_STEP, OP_ADJOINT, OP_ENSEMBLE = 0, 1, 2
+MAX_TRACERS = 8
+MAX_NZ = 128
+
+_STATUS = {OK: "ok", ERR_ARG: "invalid argument", ERR_CUDA: "CUDA runtime error",
+           ERR_WORKSPACE: "workspace missing, misaligned or too small",
+           ERR_NONFINITE: "non-finite budget", ERR_TIMEOUT: "device barrier timed out",
+           ERR_UNSUPPORTED: "unsupported size"}
+
+
+class AsucaError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {_STATUS.get(status, 'unknown')} ({status})")
+
+
+class GridDesc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("ntracers", ctypes.c_int), ("dx", ctypes.c_double), ("dy", ctypes.c_double),
+                ("dz", ctypes.POINTER(ctypes.c_double)), ("tau_theta", ctypes.c_double),
+                ("k0", ctypes.c_double), ("k_h", ctypes.c_double), ("v_sed", ctypes.c_double),
+                ("sed_tracer", ctypes.c_int), ("lim", ctypes.c_int), ("prec", ctypes.c_int)]
+
+
+class StateStruct(ctypes.Structure):
+    _fields_ = [("rho", ctypes.c_void_p), ("rhotheta", ctypes.c_void_p), ("rhoq", ctypes.c_void_p),
+                ("mu", ctypes.c_void_p), ("mv", ctypes.c_void_p), ("mw", ctypes.c_void_p)]
+
+
+_lib = None
+_VP = ctypes.c_void_p
+
+# every symbol the C ABI exports, with its ctypes signature
+SIGNATURES = {
+    "asuca_init_grid": (ctypes.c_int, [ctypes.POINTER(GridDesc), ctypes.POINTER(_VP)]),
+    "asuca_free_grid": (ctypes.c_int, [_VP]),
+    "asuca_workspace_bytes": (ctypes.c_size_t, [_VP, ctypes.c_int, ctypes.c_int]),
+    "asuca_step": (ctypes.c_int, [_VP, ctypes.POINTER(StateStruct), _VP, ctypes.c_double,
+                                  ctypes.c_int, _VP, ctypes.c_size_t, _VP, _VP]),
+    "asuca_get_status": (ctypes.c_int, [_VP]),
+    "asuca_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "asuca_debug_stage": (ctypes.c_int, [_VP, ctypes.POINTER(StateStruct), ctypes.POINTER(StateStruct),
+                                         ctypes.POINTER(StateStruct), _VP, ctypes.c_double, _VP]),
+    "asuca_debug_column": (ctypes.c_int, [_VP, ctypes.POINTER(StateStruct), ctypes.c_double, _VP,
+                                          _VP, ctypes.c_size_t, _VP]),
+    "asuca_profile_enable": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "asuca_profile_read": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
+}
+KERNEL_STAGE, KERNEL_COLUMN, KERNEL_REDUCE = 0, 1, 2
+KERNEL_KINDS = 8
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def lib():
+    """Load libasuca.so; raises if it has not been built (no fallback exists)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB_PATH):
+            raise RuntimeError(f"libasuca.so is not built ({_LIB_PATH}); run "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(_LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status: int, where: str):
+    if status != OK:
+        raise AsucaError(status, where)
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+class Grid:
+    """Grid, physics constants and precision (asuca_init_grid)."""
+
+    def __init__(self, nx, ny, nz, ntracers, dz, dx=2000.0, dy=2000.0, *, tau_theta=3600.0,
+                 k0=50.0, k_h=1000.0, v_sed=2.0, sed_tracer=None, lim=LIM_KOREN,
+                 prec=FP32_MIXED):
+        self.dz = np.ascontiguousarray(dz, dtype=np.float64)
+        if sed_tracer is None:
+            sed_tracer = ntracers - 1
+        self.desc = GridDesc(nx, ny, nz, ntracers, dx, dy,
+                             self.dz.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                             tau_theta, k0, k_h, v_sed, sed_tracer, lim, prec)
+        self.nx, self.ny, self.nz, self.ntracers = nx, ny, nz, ntracers
+        self.dx, self.dy, self.prec = dx, dy, prec
+        h = ctypes.c_void_p()
+        _check(lib().asuca_init_grid(ctypes.byref(self.desc), ctypes.byref(h)), "asuca_init_grid")
+        self.handle = h
+
+    @classmethod
+    def from_case(cls, case, **kw):
+        return cls(case.nx, case.ny, case.nz, case.ntracers, case.dz, case.dx, case.dy, **kw)
+
+    @property
+    def nfields(self):
+        return 2 + self.ntracers
+
+    @property
+    def torch_dtype(self):
+        import torch
+        return torch.float64 if self.prec == FP64 else torch.float32
+
+    def workspace_bytes(self, op=OP_STEP, param=0) -> int:
+        return int(lib().asuca_workspace_bytes(self.handle, op, param))
+
+    def workspace(self, op=OP_STEP, param=0, device="cuda"):
+        import torch
+        n = self.workspace_bytes(op, param)
+        return torch.empty(max(n, 256), dtype=torch.uint8, device=device)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().asuca_free_grid(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class State:
+    """Caller-owned device fields: rho, rhotheta [nz][ny][nx], rhoq [N][nz][ny][nx],
+    mu, mv [nz][ny][nx], mw [nz+1][ny][nx] (i fastest)."""
+
+    def __init__(self, rho, rhotheta, rhoq, mu, mv, mw):
+        self.rho, self.rhotheta, self.rhoq = rho, rhotheta, rhoq
+        self.mu, self.mv, self.mw = mu, mv, mw
+
+    @classmethod
+    def from_case(cls, case, prec=FP32_MIXED, device="cuda"):
+        import torch
+        dt = torch.float64 if prec == FP64 else torch.float32
+        t = lambda a: torch.as_tensor(np.ascontiguousarray(a)).to(device=device, dtype=dt).contiguous()
+        rhoq = case.rhoq if case.ntracers > 0 else np.zeros((0,) + case.rho.shape)
+        return cls(t(case.rho), t(case.rhotheta), t(rhoq), t(case.mu), t(case.mv), t(case.mw))
+
+    def clone(self):
+        return State(self.rho.clone(), self.rhotheta.clone(), self.rhoq.clone(), self.mu, self.mv, self.mw)
+
+    def fields(self):
+        """[F][nz][ny][nx] stacked copy (rho, rho*theta, tracers)."""
+        import torch
+        return torch.cat([self.rho[None], self.rhotheta[None], self.rhoq], 0)
+
+    def struct(self) -> StateStruct:
+        return StateStruct(self.rho.data_ptr(), self.rhotheta.data_ptr(),
+                           self.rhoq.data_ptr() if self.rhoq.numel() else None,
+                           self.mu.data_ptr(), self.mv.data_ptr(), self.mw.data_ptr())
+
+
+def _check_state(grid: Grid, st: State):
+    dt = grid.torch_dtype
+    nz, ny, nx, N = grid.nz, grid.ny, grid.nx, grid.ntracers
+    for name, shape in (("rho", (nz, ny, nx)), ("rhotheta", (nz, ny, nx)), ("rhoq", (N, nz, ny, nx)),
+                        ("mu", (nz, ny, nx)), ("mv", (nz, ny, nx)), ("mw", (nz + 1, ny, nx))):
+        t = getattr(st, name)
+        if tuple(t.shape) != shape or t.dtype != dt or not t.is_contiguous() or not t.is_cuda:
+            raise ValueError(f"state.{name}: need contiguous CUDA {dt} of shape {shape}, "
+                             f"got {t.dtype} {tuple(t.shape)}")
+
+
+def step(grid: Grid, state: State, dt: float, nsteps: int, *, tendencies=None, workspace=None,
+         budgets=None, stream=None):
+    """Advance `state` in place by nsteps (asuca_step).  Returns the budgets tensor
+    (N+3 doubles on the device) if `budgets` is given or True."""
+    import torch
+    _check_state(grid, state)
+    if tendencies is not None:
+        shape = (grid.ntracers + 1, grid.nz, grid.ny, grid.nx)
+        if tuple(tendencies.shape) != shape or tendencies.dtype != grid.torch_dtype or \
+                not tendencies.is_contiguous():
+            raise ValueError(f"tendencies: need contiguous {grid.torch_dtype} of shape {shape}")
+    if workspace is None:
+        workspace = grid.workspace(device=state.rho.device)
+    if budgets is True:
+        budgets = torch.empty(grid.nfields + 1, dtype=torch.float64, device=state.rho.device)
+    s = state.struct()
+    _check(lib().asuca_step(grid.handle, ctypes.byref(s), _ptr(tendencies), float(dt), int(nsteps),
+                            _ptr(workspace), workspace.numel() * workspace.element_size(),
+                            _ptr(budgets), _stream_ptr(stream)), "asuca_step")
+    return budgets
+
+
+def get_status(grid: Grid) -> int:
+    return int(lib().asuca_get_status(grid.handle))
+
+
+def debug_stage(grid: Grid, yin: State, ybase: State, yout: State, cdt: float, *, tendencies=None,
+                stream=None):
+    """One RK stage: yout = ybase + cdt * R(yin) (asuca_debug_stage)."""
+    a, b, c = yin.struct(), ybase.struct(), yout.struct()
+    _check(lib().asuca_debug_stage(grid.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
+                                   _ptr(tendencies), float(cdt), _stream_ptr(stream)),
+           "asuca_debug_stage")
+
+
+def debug_column(grid: Grid, state: State, dt: float, precip_col, *, workspace=None, stream=None):
+    """The column pass alone (asuca_debug_column); precip_col [ny][nx] float64 is incremented."""
+    if workspace is None:
+        workspace = grid.workspace(device=state.rho.device)
+    s = state.struct()
+    _check(lib().asuca_debug_column(grid.handle, ctypes.byref(s), float(dt), _ptr(precip_col),
+                                    _ptr(workspace), workspace.numel(), _stream_ptr(stream)),
+           "asuca_debug_column")
+
+
+def profile_enable(grid: Grid, on: bool = True):
+    _check(lib().asuca_profile_enable(grid.handle, int(bool(on))), "asuca_profile_enable")
+
+
+def profile_read(grid: Grid):
+    """{kind: (total_ms, launches)} of the kernels launched since the last read."""
+    ms = (ctypes.c_double * KERNEL_KINDS)()
+    n = (ctypes.c_int * KERNEL_KINDS)()
+    _check(lib().asuca_profile_read(grid.handle, ms, n, KERNEL_KINDS), "asuca_profile_read")
+    return {k: (ms[k], n[k]) for k in range(KERNEL_KINDS) if n[k]}

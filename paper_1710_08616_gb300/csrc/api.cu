@@ -1,0 +1,428 @@
+// Host side of the C ABI declared in include/asuca.h: argument checks,
+// level tables, workspace layout and the launch sequence of one call.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <cstdlib>
+
+#include "common.cuh"
+
+using namespace asuca;
+
+struct asuca_grid {
+    asuca_grid_desc d;
+    double dz[MAXNZ], zf[MAXNZ + 1], zc[MAXNZ];
+    int F;
+    long long plane, cells;
+    int device, nsm;
+    int col_grid;                 // persistent column-kernel grid
+    volatile int *status_host;    // pinned, mapped; the device writes error codes here
+    int *status_dev;
+    cudaStream_t last_stream;
+    // opt-in per-kernel timing: events recorded around every launch
+    bool prof_on;
+    cudaEvent_t *prof_ev;
+    int prof_cap, prof_used;
+    int *prof_kind;               // kind of the launch bracketed by events 2q, 2q+1
+};
+
+namespace {
+
+constexpr size_t ALIGN = 256;
+constexpr int COL_BLOCKS_PER_SM = 1;
+
+size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
+
+size_t elem_size(const asuca_grid *g) { return g->d.prec == ASUCA_FP64 ? 8 : 4; }
+
+long long col_slots(const asuca_grid *g) { return (long long)g->col_grid * COL_TPB; }
+
+struct StepLayout {
+    size_t ystar, ystar2, precip, partials, scratch, total;
+};
+
+StepLayout step_layout(const asuca_grid *g) {
+    StepLayout L;
+    const size_t state = (size_t)g->F * g->cells * elem_size(g);
+    size_t off = 0;
+    L.ystar = off;
+    off = align_up(off + state);
+    L.ystar2 = off;
+    off = align_up(off + state);
+    L.precip = off;
+    off = align_up(off + (size_t)g->plane * sizeof(double));
+    L.partials = off;
+    off = align_up(off + (size_t)g->col_grid * (g->F + 1) * sizeof(double));
+    L.scratch = off;
+    off = align_up(off + (size_t)g->d.nz * (g->F + 1) * col_slots(g) * sizeof(double));
+    L.total = off;
+    return L;
+}
+
+asuca_status take_status(asuca_grid *g) {
+    int s = g->status_host[0];
+    if (s != 0) {
+        g->status_host[0] = 0;
+        return (asuca_status)s;
+    }
+    return ASUCA_OK;
+}
+
+bool state_ok(const asuca_grid *g, const asuca_state *s) {
+    return s && s->rho && s->rhotheta && (g->d.ntracers == 0 || s->rhoq) && s->mu && s->mv && s->mw;
+}
+
+template <typename T>
+void field_ptrs(const asuca_grid *g, void *rho, void *rhotheta, void *rhoq, T **out) {
+    out[0] = (T *)rho;
+    out[1] = (T *)rhotheta;
+    for (int n = 0; n < g->d.ntracers; n++) out[2 + n] = (T *)rhoq + (size_t)n * g->cells;
+    for (int f = g->F; f < MAXF; f++) out[f] = nullptr;
+}
+
+template <typename T>
+void workspace_fields(const asuca_grid *g, char *ws, size_t off, T **out) {
+    for (int f = 0; f < g->F; f++) out[f] = (T *)(ws + off) + (size_t)f * g->cells;
+    for (int f = g->F; f < MAXF; f++) out[f] = nullptr;
+}
+
+template <typename T>
+StageParams<T> stage_params(const asuca_grid *g, const asuca_state *fl, const void *tend) {
+    StageParams<T> p;
+    std::memset(&p, 0, sizeof(p));
+    p.mu = (const T *)fl->mu;
+    p.mv = (const T *)fl->mv;
+    p.mw = (const T *)fl->mw;
+    p.tend = (const T *)tend;
+    p.nx = g->d.nx;
+    p.ny = g->d.ny;
+    p.nz = g->d.nz;
+    p.lim = (int)g->d.lim;
+    p.plane = g->plane;
+    p.rdx = (T)(1.0 / g->d.dx);
+    p.rdy = (T)(1.0 / g->d.dy);
+    for (int k = 0; k < g->d.nz; k++) p.rdz[k] = (T)(1.0 / g->dz[k]);
+    return p;
+}
+
+template <typename T>
+ColumnParams<T> column_params(const asuca_grid *g, double dt) {
+    ColumnParams<T> p;
+    std::memset(&p, 0, sizeof(p));
+    const asuca_grid_desc &d = g->d;
+    const int nz = d.nz;
+    p.nx = d.nx;
+    p.ny = d.ny;
+    p.nz = nz;
+    p.plane = g->plane;
+    p.do_relax = d.tau_theta > 0.0;
+    p.do_sed = d.v_sed > 0.0 && d.sed_tracer >= 0 && d.sed_tracer < d.ntracers;
+    p.sed = p.do_sed ? 2 + d.sed_tracer : -1;
+    p.do_diff = d.k0 > 0.0;
+    p.do_phys = 1;
+    p.relax_r = p.do_relax ? (T)(dt / d.tau_theta) : T(0);
+    p.relax_inv = p.do_relax ? (T)(1.0 / (1.0 + dt / d.tau_theta)) : T(1);
+    p.sed_dt = (T)dt;
+    p.sed_v = (T)d.v_sed;
+    p.dt = dt;
+    p.dxdy = d.dx * d.dy;
+    p.nslots = col_slots(g);
+    for (int k = 0; k < nz; k++) {
+        p.dz[k] = g->dz[k];
+        p.dzT[k] = (T)g->dz[k];
+        p.sedr[k] = (T)(1.0 / (g->dz[k] + dt * d.v_sed));
+        p.thref[k] = (T)(300.0 + 0.004 * g->zc[k]);
+        p.dzr_up[k] = (k + 1 < nz) ? g->dz[k + 1] / g->dz[k] : 0.0;
+        p.dzr_dn[k] = (k > 0) ? g->dz[k - 1] / g->dz[k] : 0.0;
+        if (k + 1 < nz && p.do_diff) {
+            const double K = d.k0 * std::exp(-g->zf[k + 1] / d.k_h);
+            p.kc[k] = 0.5 * dt * K / (g->zc[k + 1] - g->zc[k]);
+        } else {
+            p.kc[k] = 0.0;
+        }
+    }
+    return p;
+}
+
+asuca_status cuda_status(cudaError_t e) { return e == cudaSuccess ? ASUCA_OK : ASUCA_ERR_CUDA; }
+
+// Launch through f(), bracketed by two events when profiling is on.
+template <typename Fn>
+cudaError_t timed(asuca_grid *g, int kind, cudaStream_t s, Fn f) {
+    if (!g->prof_on) return f();
+    if (2 * (g->prof_used + 1) > g->prof_cap) {
+        int cap = g->prof_cap ? 2 * g->prof_cap : 256;
+        cudaEvent_t *ev = (cudaEvent_t *)std::realloc(g->prof_ev, sizeof(cudaEvent_t) * cap);
+        int *kd = (int *)std::realloc(g->prof_kind, sizeof(int) * cap / 2);
+        if (!ev || !kd) return cudaErrorMemoryAllocation;
+        g->prof_ev = ev;
+        g->prof_kind = kd;
+        for (int q = g->prof_cap; q < cap; q++) {
+            cudaError_t e = cudaEventCreate(&g->prof_ev[q]);
+            if (e != cudaSuccess) return e;
+        }
+        g->prof_cap = cap;
+    }
+    const int q = g->prof_used;
+    cudaError_t e = cudaEventRecord(g->prof_ev[2 * q], s);
+    if (e != cudaSuccess) return e;
+    if ((e = f()) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(g->prof_ev[2 * q + 1], s)) != cudaSuccess) return e;
+    g->prof_kind[q] = kind;
+    g->prof_used = q + 1;
+    return cudaSuccess;
+}
+
+template <typename T>
+asuca_status run_step(asuca_grid *g, asuca_state *st, const void *tend, double dt, int nsteps,
+                      char *ws, double *budgets, cudaStream_t s) {
+    const StepLayout L = step_layout(g);
+    const int F = g->F;
+    T *yn[MAXF], *y1[MAXF], *y2[MAXF];
+    field_ptrs<T>(g, st->rho, st->rhotheta, st->rhoq, yn);
+    workspace_fields<T>(g, ws, L.ystar, y1);
+    workspace_fields<T>(g, ws, L.ystar2, y2);
+    StageParams<T> sp = stage_params<T>(g, st, tend);
+    ColumnParams<T> cp = column_params<T>(g, dt);
+    for (int f = 0; f < MAXF; f++) cp.y[f] = yn[f];
+    cp.precip_col = (double *)(ws + L.precip);
+    cp.partials = (double *)(ws + L.partials);
+    cp.scratch = (double *)(ws + L.scratch);
+
+    cudaError_t e = cudaMemsetAsync(ws + L.precip, 0, (size_t)g->plane * sizeof(double), s);
+    if (e != cudaSuccess) return ASUCA_ERR_CUDA;
+    const T cdt[3] = {(T)(dt / 3.0), (T)(dt / 2.0), (T)dt};
+    for (int n = 0; n < nsteps; n++) {
+        for (int stg = 0; stg < 3; stg++) {
+            T **in = stg == 0 ? yn : (stg == 1 ? y1 : y2);
+            T **out = stg == 0 ? y1 : (stg == 1 ? y2 : yn);
+            for (int f = 0; f < MAXF; f++) {
+                sp.yin[f] = in[f];
+                sp.ybase[f] = yn[f];
+                sp.yout[f] = out[f];
+            }
+            sp.cdt = cdt[stg];
+            if ((e = timed(g, ASUCA_KERNEL_STAGE, s, [&] { return launch_stage<T>(sp, F, s); })) != cudaSuccess)
+                return ASUCA_ERR_CUDA;
+        }
+        cp.budgets = (budgets != nullptr) && (n == nsteps - 1);
+        if ((e = timed(g, ASUCA_KERNEL_COLUMN, s, [&] { return launch_column<T>(cp, F, g->col_grid, COL_TPB, s); })) != cudaSuccess)
+            return ASUCA_ERR_CUDA;
+    }
+    if (budgets) {
+        if (nsteps == 0) {
+            cp.do_phys = 0;
+            cp.budgets = 1;
+            if ((e = timed(g, ASUCA_KERNEL_COLUMN, s, [&] { return launch_column<T>(cp, F, g->col_grid, COL_TPB, s); })) != cudaSuccess)
+                return ASUCA_ERR_CUDA;
+        }
+        e = timed(g, ASUCA_KERNEL_REDUCE, s, [&] {
+            return launch_budget_reduce(cp.partials, g->col_grid, F + 1, F, g->d.dx * g->d.dy, budgets,
+                                        g->status_dev, s);
+        });
+        if (e != cudaSuccess) return ASUCA_ERR_CUDA;
+    }
+    return ASUCA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *asuca_status_string(asuca_status s) {
+    switch (s) {
+        case ASUCA_OK: return "ok";
+        case ASUCA_ERR_ARG: return "invalid argument";
+        case ASUCA_ERR_CUDA: return "CUDA runtime error";
+        case ASUCA_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
+        case ASUCA_ERR_NONFINITE: return "non-finite budget";
+        case ASUCA_ERR_TIMEOUT: return "device barrier timed out";
+        case ASUCA_ERR_UNSUPPORTED: return "unsupported size";
+    }
+    return "unknown status";
+}
+
+asuca_status asuca_init_grid(const asuca_grid_desc *desc, asuca_grid **out) {
+    if (!desc || !out) return ASUCA_ERR_ARG;
+    *out = nullptr;
+    const asuca_grid_desc &d = *desc;
+    if (d.nx < 4 || d.ny < 4 || d.nz < 3 || d.ntracers < 0 || !d.dz) return ASUCA_ERR_ARG;
+    if (d.nz > ASUCA_MAX_NZ || d.ntracers > ASUCA_MAX_TRACERS) return ASUCA_ERR_UNSUPPORTED;
+    if (!(d.dx > 0.0) || !(d.dy > 0.0) || !std::isfinite(d.dx) || !std::isfinite(d.dy)) return ASUCA_ERR_ARG;
+    if (!(d.tau_theta >= 0.0) || !(d.k0 >= 0.0) || !(d.v_sed >= 0.0)) return ASUCA_ERR_ARG;
+    if (d.k0 > 0.0 && !(d.k_h > 0.0)) return ASUCA_ERR_ARG;
+    if (d.sed_tracer < -1 || d.sed_tracer >= d.ntracers) return ASUCA_ERR_ARG;
+    if (d.lim != ASUCA_LIM_KOREN && d.lim != ASUCA_LIM_LINEAR && d.lim != ASUCA_LIM_UPWIND1) return ASUCA_ERR_ARG;
+    if (d.prec != ASUCA_FP64 && d.prec != ASUCA_FP32_MIXED) return ASUCA_ERR_ARG;
+    for (int k = 0; k < d.nz; k++)
+        if (!(d.dz[k] > 0.0) || !std::isfinite(d.dz[k])) return ASUCA_ERR_ARG;
+    if ((long long)d.nx * d.ny > (1LL << 31)) return ASUCA_ERR_UNSUPPORTED;
+
+    asuca_grid *g = new (std::nothrow) asuca_grid;
+    if (!g) return ASUCA_ERR_ARG;
+    std::memset((void *)g, 0, sizeof(*g));
+    g->d = d;
+    g->d.dz = nullptr;
+    g->zf[0] = 0.0;
+    for (int k = 0; k < d.nz; k++) {
+        g->dz[k] = d.dz[k];
+        g->zf[k + 1] = g->zf[k] + d.dz[k];
+        g->zc[k] = g->zf[k] + 0.5 * d.dz[k];
+    }
+    g->F = 2 + d.ntracers;
+    g->plane = (long long)d.nx * d.ny;
+    g->cells = g->plane * d.nz;
+    if (cudaGetDevice(&g->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&g->nsm, cudaDevAttrMultiProcessorCount, g->device) != cudaSuccess) {
+        delete g;
+        return ASUCA_ERR_CUDA;
+    }
+    long long need = (g->plane + COL_TPB - 1) / COL_TPB;
+    long long cap = (long long)g->nsm * COL_BLOCKS_PER_SM;
+    g->col_grid = (int)(need < cap ? need : cap);
+    void *h = nullptr;
+    if (cudaHostAlloc(&h, 64, cudaHostAllocMapped) != cudaSuccess) {
+        delete g;
+        return ASUCA_ERR_CUDA;
+    }
+    std::memset(h, 0, 64);
+    g->status_host = (volatile int *)h;
+    if (cudaHostGetDevicePointer((void **)&g->status_dev, h, 0) != cudaSuccess) {
+        cudaFreeHost(h);
+        delete g;
+        return ASUCA_ERR_CUDA;
+    }
+    g->last_stream = nullptr;
+    *out = g;
+    return ASUCA_OK;
+}
+
+asuca_status asuca_free_grid(asuca_grid *g) {
+    if (!g) return ASUCA_ERR_ARG;
+    if (g->status_host) cudaFreeHost((void *)g->status_host);
+    for (int q = 0; q < g->prof_cap; q++) cudaEventDestroy(g->prof_ev[q]);
+    std::free(g->prof_ev);
+    std::free(g->prof_kind);
+    delete g;
+    return ASUCA_OK;
+}
+
+size_t asuca_workspace_bytes(const asuca_grid *g, int op, int param) {
+    (void)param;
+    if (!g) return 0;
+    if (op == ASUCA_OP_STEP) return step_layout(g).total;
+    return 0;
+}
+
+asuca_status asuca_get_status(asuca_grid *g) {
+    if (!g) return ASUCA_ERR_ARG;
+    if (cudaStreamSynchronize(g->last_stream) != cudaSuccess) return ASUCA_ERR_CUDA;
+    return take_status(g);
+}
+
+asuca_status asuca_step(asuca_grid *g, asuca_state *st, const void *tend, double dt, int nsteps,
+                        void *workspace, size_t workspace_bytes, double *budgets_dev,
+                        void *cuda_stream) {
+    if (!g || !state_ok(g, st) || nsteps < 0 || !std::isfinite(dt) || dt < 0.0) return ASUCA_ERR_ARG;
+    asuca_status prev = take_status(g);
+    if (prev != ASUCA_OK) return prev;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    g->last_stream = s;
+    if (nsteps == 0 && !budgets_dev) return ASUCA_OK;
+    if (!workspace || ((uintptr_t)workspace % ALIGN) != 0 ||
+        workspace_bytes < step_layout(g).total)
+        return ASUCA_ERR_WORKSPACE;
+    if (g->d.prec == ASUCA_FP64)
+        return run_step<double>(g, st, tend, dt, nsteps, (char *)workspace, budgets_dev, s);
+    return run_step<float>(g, st, tend, dt, nsteps, (char *)workspace, budgets_dev, s);
+}
+
+asuca_status asuca_debug_stage(asuca_grid *g, const asuca_state *in, const asuca_state *base,
+                               asuca_state *out, const void *tend, double cdt, void *cuda_stream) {
+    if (!g || !state_ok(g, in) || !base || !out || !base->rho || !out->rho || !std::isfinite(cdt))
+        return ASUCA_ERR_ARG;
+    asuca_status prev = take_status(g);
+    if (prev != ASUCA_OK) return prev;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    g->last_stream = s;
+    cudaError_t e;
+    if (g->d.prec == ASUCA_FP64) {
+        StageParams<double> p = stage_params<double>(g, in, tend);
+        field_ptrs<double>(g, in->rho, in->rhotheta, in->rhoq, (double **)p.yin);
+        field_ptrs<double>(g, base->rho, base->rhotheta, base->rhoq, (double **)p.ybase);
+        field_ptrs<double>(g, out->rho, out->rhotheta, out->rhoq, p.yout);
+        p.cdt = cdt;
+        e = launch_stage<double>(p, g->F, s);
+    } else {
+        StageParams<float> p = stage_params<float>(g, in, tend);
+        field_ptrs<float>(g, in->rho, in->rhotheta, in->rhoq, (float **)p.yin);
+        field_ptrs<float>(g, base->rho, base->rhotheta, base->rhoq, (float **)p.ybase);
+        field_ptrs<float>(g, out->rho, out->rhotheta, out->rhoq, p.yout);
+        p.cdt = (float)cdt;
+        e = launch_stage<float>(p, g->F, s);
+    }
+    return cuda_status(e);
+}
+
+asuca_status asuca_debug_column(asuca_grid *g, asuca_state *st, double dt, double *precip_col,
+                                void *workspace, size_t workspace_bytes, void *cuda_stream) {
+    if (!g || !st || !st->rho || !st->rhotheta || (g->d.ntracers && !st->rhoq) || !precip_col ||
+        !std::isfinite(dt) || dt < 0.0)
+        return ASUCA_ERR_ARG;
+    asuca_status prev = take_status(g);
+    if (prev != ASUCA_OK) return prev;
+    const StepLayout L = step_layout(g);
+    if (!workspace || ((uintptr_t)workspace % ALIGN) != 0 || workspace_bytes < L.total)
+        return ASUCA_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    g->last_stream = s;
+    char *ws = (char *)workspace;
+    cudaError_t e;
+    if (g->d.prec == ASUCA_FP64) {
+        ColumnParams<double> p = column_params<double>(g, dt);
+        field_ptrs<double>(g, st->rho, st->rhotheta, st->rhoq, p.y);
+        p.precip_col = precip_col;
+        p.partials = (double *)(ws + L.partials);
+        p.scratch = (double *)(ws + L.scratch);
+        e = launch_column<double>(p, g->F, g->col_grid, COL_TPB, s);
+    } else {
+        ColumnParams<float> p = column_params<float>(g, dt);
+        field_ptrs<float>(g, st->rho, st->rhotheta, st->rhoq, p.y);
+        p.precip_col = precip_col;
+        p.partials = (double *)(ws + L.partials);
+        p.scratch = (double *)(ws + L.scratch);
+        e = launch_column<float>(p, g->F, g->col_grid, COL_TPB, s);
+    }
+    return cuda_status(e);
+}
+
+asuca_status asuca_profile_enable(asuca_grid *g, int on) {
+    if (!g) return ASUCA_ERR_ARG;
+    g->prof_on = on != 0;
+    g->prof_used = 0;
+    return ASUCA_OK;
+}
+
+asuca_status asuca_profile_read(asuca_grid *g, double *ms, int *launches, int nkinds) {
+    if (!g || !ms || !launches || nkinds <= 0) return ASUCA_ERR_ARG;
+    for (int k = 0; k < nkinds; k++) {
+        ms[k] = 0.0;
+        launches[k] = 0;
+    }
+    if (g->prof_used > 0 && cudaEventSynchronize(g->prof_ev[2 * g->prof_used - 1]) != cudaSuccess)
+        return ASUCA_ERR_CUDA;
+    for (int q = 0; q < g->prof_used; q++) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, g->prof_ev[2 * q], g->prof_ev[2 * q + 1]) != cudaSuccess)
+            return ASUCA_ERR_CUDA;
+        const int k = g->prof_kind[q];
+        if (k >= 0 && k < nkinds) {
+            ms[k] += t;
+            launches[k] += 1;
+        }
+    }
+    g->prof_used = 0;
+    return ASUCA_OK;
+}
+
+}  // extern "C"

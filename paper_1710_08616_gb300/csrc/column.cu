@@ -1,0 +1,204 @@
+// Column physics, one thread per (i, j) column (the coarse per-column
+// granularity of Sec. 1.2 "Parallelization Granularity", Fig. 1 and 2), and
+// the FP64 budget sums.
+//
+// Per column, after the three RK stages (Lie splitting, once per long step):
+//   top-down pass, k = nz-1 .. 0:
+//     (i)   implicit theta relaxation   theta <- (theta + r theta_ref) / (1 + r)
+//     (ii)  implicit sedimentation      (rho q)_k <- ((rho q)_k dz_k + dt P_{k+1/2}) / (dz_k + dt v),
+//                                       P_{k-1/2} = v (rho q)_k; P_{-1/2} rains out
+//     (iii) forward elimination of the implicit vertical diffusion
+//           A phi = d, a_k = -g_{k-1/2}, c_k = -g_{k+1/2},
+//           b_k = rho_k dz_k + g_{k-1/2} + g_{k+1/2}, d_k = dz_k (rho phi)_k,
+//           run from the top down (the mirror of the textbook Thomas order),
+//           one factorisation shared by rho*theta and every tracer
+//   bottom-up pass: back substitution, (rho phi)_k = rho_k phi_k.
+// The elimination works on scaled unknowns so that each field costs one
+// FMA per level on the way down and one FMA plus one multiply on the way up:
+//   e_k = x_k + alpha_k e_{k+1},  alpha_k = g_{k+1/2} m_{k+1} dz_{k+1} / dz_k
+//   z_k = e_k + gamma_k z_{k-1},  gamma_k = g_{k-1/2} m_{k-1} dz_{k-1} / dz_k
+//   (rho phi)_k = sigma_k z_k,    sigma_k = rho_k dz_k m_k,   m_k = 1 / pivot_k
+// (x_k is the incoming rho*phi; d''_k = dz_k m_k e_k and phi_k = dz_k m_k z_k
+// are the usual eliminated right-hand side and solution).  The whole solve
+// runs in double in both precisions; a float result is rounded once.
+//
+// The per-level e_k, sigma_k, gamma_k live in a scratch area indexed by the
+// thread's slot.  The grid is persistent (one resident wave, a grid-stride
+// loop over columns), so the scratch is as large as the columns in flight
+// and stays resident in L2 while each slot reuses it column after column.
+#include "common.cuh"
+
+namespace asuca {
+
+template <typename T, int NF>
+__global__ void __launch_bounds__(COL_TPB) column_kernel(const __grid_constant__ ColumnParams<T> p) {
+    constexpr int NT = NF - 1;
+    constexpr int NQ = NF + 1;                    // sigma, gamma, e[NT]
+    const long long ncol = p.plane;
+    const long long nslots = p.nslots;
+    const long long slot = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int nz = p.nz;
+    const long long plane = p.plane;
+
+    double bsum[NF + 1];
+#pragma unroll
+    for (int q = 0; q <= NF; q++) bsum[q] = 0.0;
+
+    for (long long col = slot; col < ncol; col += nslots) {
+        double *sc = p.scratch + slot;
+        if (p.do_phys) {
+            double g_hi = 0.0, m_up = 0.0;
+            double e_up[NT];
+#pragma unroll
+            for (int f = 0; f < NT; f++) e_up[f] = 0.0;
+            T P = T(0);
+            T rho = p.y[0][(long long)(nz - 1) * plane + col];
+            for (int k = nz - 1; k >= 0; k--) {
+                const long long o = (long long)k * plane + col;
+                const T rho_dn = (k > 0) ? p.y[0][o - plane] : T(0);
+                T x[NT];
+#pragma unroll
+                for (int f = 0; f < NT; f++) x[f] = p.y[f + 1][o];
+                // (i) relaxation of theta
+                if (p.do_relax) {
+                    T th = x[0] / rho;
+                    th = (th + p.relax_r * p.thref[k]) * p.relax_inv;
+                    x[0] = rho * th;
+                }
+                // (ii) sedimentation of one tracer, top-down
+                if (p.do_sed) {
+#pragma unroll
+                    for (int f = 1; f < NT; f++) {
+                        if (f + 1 == p.sed) {
+                            x[f] = (x[f] * p.dzT[k] + p.sed_dt * P) * p.sedr[k];
+                            P = p.sed_v * x[f];
+                        }
+                    }
+                    if (k == 0) p.precip_col[col] += p.dt * (double)P * p.dxdy;
+                }
+                const double rd = (double)rho;
+                if (p.budgets) bsum[0] += rd * p.dz[k];
+                if (p.do_diff) {
+                    // (iii) forward elimination, top-down, on scaled unknowns
+                    const double g_lo = (k > 0) ? p.kc[k - 1] * ((double)rho_dn + rd) : 0.0;
+                    const double rdz = rd * p.dz[k];
+                    const double b = rdz + (g_lo + g_hi);
+                    const double t = g_hi * m_up;
+                    const double m = rcp_newton(fma(-g_hi, t, b));
+                    const double alpha = t * p.dzr_up[k];
+                    sc[(long long)(k * NQ + 0) * nslots] = rdz * m;                     // sigma_k
+                    if (k < nz - 1) sc[(long long)((k + 1) * NQ + 1) * nslots] = g_hi * m * p.dzr_dn[k + 1];
+#pragma unroll
+                    for (int f = 0; f < NT; f++) {
+                        const double e = fma(alpha, e_up[f], (double)x[f]);
+                        sc[(long long)(k * NQ + 2 + f) * nslots] = e;
+                        e_up[f] = e;
+                    }
+                    g_hi = g_lo;
+                    m_up = m;
+                } else {
+                    if (p.do_relax) p.y[1][o] = x[0];
+                    if (p.do_sed) {
+#pragma unroll
+                        for (int f = 1; f < NT; f++)
+                            if (f + 1 == p.sed) p.y[f + 1][o] = x[f];
+                    }
+                    if (p.budgets) {
+#pragma unroll
+                        for (int f = 0; f < NT; f++) bsum[f + 1] += (double)x[f] * p.dz[k];
+                    }
+                }
+                rho = rho_dn;
+            }
+            if (p.do_diff) {
+                // back substitution, bottom-up
+                double z[NT];
+#pragma unroll
+                for (int f = 0; f < NT; f++) z[f] = 0.0;
+                for (int k = 0; k < nz; k++) {
+                    const long long o = (long long)k * plane + col;
+                    const double sigma = sc[(long long)(k * NQ + 0) * nslots];
+                    const double gamma = (k > 0) ? sc[(long long)(k * NQ + 1) * nslots] : 0.0;
+#pragma unroll
+                    for (int f = 0; f < NT; f++) {
+                        z[f] = fma(gamma, z[f], sc[(long long)(k * NQ + 2 + f) * nslots]);
+                        const T u = (T)(sigma * z[f]);
+                        p.y[f + 1][o] = u;
+                        if (p.budgets) bsum[f + 1] += (double)u * p.dz[k];
+                    }
+                }
+            }
+        } else if (p.budgets) {
+            for (int k = 0; k < nz; k++) {
+                const long long o = (long long)k * plane + col;
+#pragma unroll
+                for (int f = 0; f < NF; f++) bsum[f] += (double)p.y[f][o] * p.dz[k];
+            }
+        }
+        if (p.budgets && p.precip_col) bsum[NF] += p.precip_col[col];
+    }
+
+    if (!p.budgets) return;
+    // deterministic block reduction of the per-thread partial sums
+    __shared__ double red[COL_TPB];
+#pragma unroll
+    for (int q = 0; q <= NF; q++) {
+        red[threadIdx.x] = bsum[q];
+        __syncthreads();
+        for (int s = COL_TPB / 2; s > 0; s >>= 1) {
+            if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) p.partials[(long long)blockIdx.x * (NF + 1) + q] = red[0];
+        __syncthreads();
+    }
+}
+
+// Sum the block partials in a fixed order, scale the field sums by dx*dy,
+// and flag a non-finite result in the status word.
+__global__ void budget_reduce_kernel(const double *partials, int nblocks, int nq, int nf,
+                                     double dxdy, double *out, int *status) {
+    __shared__ double red[256];
+    for (int q = 0; q < nq; q++) {
+        double s = 0.0;
+        for (int b = threadIdx.x; b < nblocks; b += blockDim.x) s += partials[(long long)b * nq + q];
+        red[threadIdx.x] = s;
+        __syncthreads();
+        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+            if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            const double v = q < nf ? red[0] * dxdy : red[0];
+            out[q] = v;
+            if (!isfinite(v) && status) atomicCAS(status, 0, (int)ASUCA_ERR_NONFINITE);
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T>
+cudaError_t launch_column(const ColumnParams<T> &p, int nf, int grid, int block, cudaStream_t s) {
+    if (block != COL_TPB) return cudaErrorInvalidValue;
+    switch (nf) {
+#define ASUCA_COL_CASE(N) \
+        case N: column_kernel<T, N><<<grid, COL_TPB, 0, s>>>(p); break;
+        ASUCA_COL_CASE(2) ASUCA_COL_CASE(3) ASUCA_COL_CASE(4) ASUCA_COL_CASE(5)
+        ASUCA_COL_CASE(6) ASUCA_COL_CASE(7) ASUCA_COL_CASE(8) ASUCA_COL_CASE(9)
+        ASUCA_COL_CASE(10)
+#undef ASUCA_COL_CASE
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_column<float>(const ColumnParams<float> &, int, int, int, cudaStream_t);
+template cudaError_t launch_column<double>(const ColumnParams<double> &, int, int, int, cudaStream_t);
+
+cudaError_t launch_budget_reduce(const double *partials, int nblocks, int nq, int nf, double dxdy,
+                                 double *out, int *status, cudaStream_t s) {
+    budget_reduce_kernel<<<1, 256, 0, s>>>(partials, nblocks, nq, nf, dxdy, out, status);
+    return cudaGetLastError();
+}
+
+}  // namespace asuca

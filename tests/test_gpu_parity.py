@@ -1,0 +1,210 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Bars (written here, from the specification): FP64 path within 1e-12
+relative, both as per-field ||d||_2/||ref||_2 and max|d|/max|ref|; FP32-mixed
+path within 2e-5 relative L2 per field.  Bit-exact where the arithmetic is
+exact (Courant-1 upwind shift).
+"""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOL32 = 2e-5
+
+
+@pytest.fixture(scope="module")
+def asuca():
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1710_08616_gb300 as a
+    torch.cuda.set_device(0)
+    return a
+
+
+def _rel(got, ref):
+    l2 = np.linalg.norm(got - ref) / max(np.linalg.norm(ref), 1e-300)
+    mx = np.abs(got - ref).max() / max(np.abs(ref).max(), 1e-300)
+    return l2, mx
+
+
+def _assert_fields(got, ref, tol, what, both=True):
+    for f in range(ref.shape[0]):
+        l2, mx = _rel(got[f], ref[f])
+        assert l2 <= tol, f"{what}: field {f} rel L2 {l2:.3e} > {tol}"
+        if both:
+            assert mx <= tol, f"{what}: field {f} rel max {mx:.3e} > {tol}"
+
+
+def _grid_pair(asuca, case, prec, **phys):
+    kw = dict(tau=oracle.TAU, k0=oracle.K0, kh=oracle.KH, vsed=oracle.VSED, lim=oracle.LIM_KOREN)
+    kw.update(phys)
+    og = oracle.Grid.from_case(case, tau=kw["tau"], k0=kw["k0"], kh=kw["kh"], vsed=kw["vsed"],
+                               lim=kw["lim"])
+    g = asuca.Grid.from_case(case, tau_theta=kw["tau"], k0=kw["k0"], k_h=kw["kh"], v_sed=kw["vsed"],
+                             lim=kw["lim"], prec=prec)
+    return og, g
+
+
+def _np(st):
+    return st.fields().double().cpu().numpy()
+
+
+# ------------------------------------------------------------------ single stage
+
+@pytest.mark.parametrize("lim", [0, 1, 2])
+@pytest.mark.parametrize("shape", [(32, 32, 16), (37, 13, 7), (4, 4, 3), (70, 9, 5)])
+def test_stage_fp64(asuca, lim, shape):
+    import torch
+    nx, ny, nz = shape
+    c = gen.make_case(nx, ny, nz, 3, seed=11 + nx)
+    og, g = _grid_pair(asuca, c, asuca.FP64, lim=lim)
+    rng = np.random.default_rng(5)
+    Yin = c.state() * (1 + 0.01 * rng.standard_normal(c.state().shape))
+    Ybase = c.state()
+    tend = rng.uniform(-1e-4, 1e-4, (4, nz, ny, nx))
+    R = oracle.rhs(og, Yin, c.mu, c.mv, c.mw, tend=tend)
+    ref = Ybase + (c.dt / 2) * R
+    dev = lambda a: torch.tensor(a, dtype=torch.float64, device="cuda")
+    sin = asuca.State(dev(Yin[0]), dev(Yin[1]), dev(Yin[2:]), dev(c.mu), dev(c.mv), dev(c.mw))
+    sbase = asuca.State(dev(Ybase[0]), dev(Ybase[1]), dev(Ybase[2:]), sin.mu, sin.mv, sin.mw)
+    sout = sbase.clone()
+    asuca.debug_stage(g, sin, sbase, sout, c.dt / 2, tendencies=dev(tend))
+    torch.cuda.synchronize()
+    _assert_fields(_np(sout), ref, TOL64, f"stage lim={lim} {shape}")
+
+
+@pytest.mark.parametrize("axis,sign", [(0, 1), (0, -1), (1, 1), (1, -1)])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_courant_one_shift_bit_exact(asuca, axis, sign, prec):
+    import torch
+    nx, ny, nz = 40, 20, 3
+    rng = np.random.default_rng(3)
+    Y = np.empty((4, nz, ny, nx))
+    Y[0] = 1.0
+    Y[1:] = rng.integers(-50, 50, (3, nz, ny, nx))
+    mu = np.full((nz, ny, nx), 16.0 * sign if axis == 0 else 0.0)
+    mv = np.full((nz, ny, nx), 16.0 * sign if axis == 1 else 0.0)
+    mw = np.zeros((nz + 1, ny, nx))
+    g = asuca.Grid(nx, ny, nz, 2, np.full(nz, 100.0), 2048.0, 2048.0, tau_theta=0, k0=0, v_sed=0,
+                   lim=asuca.LIM_UPWIND1, prec=prec)
+    dt_ = torch.float64 if prec == 0 else torch.float32
+    dev = lambda a: torch.tensor(a, dtype=dt_, device="cuda")
+    s = asuca.State(dev(Y[0]), dev(Y[1]), dev(Y[2:]), dev(mu), dev(mv), dev(mw))
+    out = s.clone()
+    asuca.debug_stage(g, s, s, out, 128.0)
+    torch.cuda.synchronize()
+    assert np.array_equal(_np(out), np.roll(Y, sign, axis=3 if axis == 0 else 2))
+
+
+# ------------------------------------------------------------------ column pass
+
+@pytest.mark.parametrize("prec,tol", [(0, TOL64), (1, TOL32)])
+@pytest.mark.parametrize("phys", [dict(), dict(k0=0.0), dict(vsed=0.0, tau=0.0), dict(tau=0.0, k0=0.0)])
+def test_column_pass(asuca, prec, tol, phys):
+    import torch
+    c = gen.make_case(45, 19, 16, 3, seed=99)
+    og, g = _grid_pair(asuca, c, prec, **phys)
+    ref, pc_ref = oracle.column(og, c.state(), c.dt)
+    st = asuca.State.from_case(c, prec=prec)
+    pc = torch.zeros((c.ny, c.nx), dtype=torch.float64, device="cuda")
+    asuca.debug_column(g, st, c.dt, pc)
+    torch.cuda.synchronize()
+    _assert_fields(_np(st), ref, tol, f"column {phys}", both=(prec == 0))
+    if phys.get("vsed", 1.0) > 0:
+        l2, mx = _rel(pc.cpu().numpy(), pc_ref)
+        assert l2 <= tol and (prec == 1 or mx <= tol)
+
+
+# ------------------------------------------------------------------ full steps
+
+def _full_step(asuca, case, prec, nsteps, tend=None, **phys):
+    import torch
+    og, g = _grid_pair(asuca, case, prec, **phys)
+    ref, rbud = oracle.step(og, case.state(), case.mu, case.mv, case.mw, case.dt, nsteps, tend=tend)
+    st = asuca.State.from_case(case, prec=prec)
+    td = None
+    if tend is not None:
+        td = torch.tensor(tend, dtype=g.torch_dtype, device="cuda")
+    bud = asuca.step(g, st, case.dt, nsteps, tendencies=td, budgets=True)
+    torch.cuda.synchronize()
+    assert asuca.get_status(g) == asuca.OK
+    return _np(st), ref, bud.cpu().numpy(), rbud
+
+
+def test_full_step_fp64_32x32x16_20_steps(asuca):
+    c = gen.make_config_case("fp64_32x32x16")
+    got, ref, bud, rbud = _full_step(asuca, c, asuca.FP64, 20)
+    _assert_fields(got, ref, TOL64, "fp64 32x32x16 x20")
+    assert np.all(np.abs(bud - rbud) <= TOL64 * np.abs(rbud))
+
+
+@pytest.mark.parametrize("shape,ntr,nsteps", [((37, 13, 7), 2, 5), ((4, 4, 3), 1, 4), ((70, 9, 5), 0, 3),
+                                              ((33, 65, 11), 8, 2)])
+def test_full_step_fp64_ragged_with_tendencies(asuca, shape, ntr, nsteps):
+    nx, ny, nz = shape
+    c = gen.make_case(nx, ny, nz, ntr, seed=1234 + nx)
+    rng = np.random.default_rng(nx)
+    tend = rng.uniform(-1e-5, 1e-5, (1 + ntr, nz, ny, nx))
+    got, ref, bud, rbud = _full_step(asuca, c, asuca.FP64, nsteps, tend=tend)
+    _assert_fields(got, ref, TOL64, f"fp64 {shape}")
+    nz_b = np.abs(rbud) > 0
+    assert np.all(np.abs(bud - rbud)[nz_b] <= TOL64 * np.abs(rbud)[nz_b])
+
+
+@pytest.mark.parametrize("lim", [0, 1, 2])
+def test_full_step_fp32_mixed_32x32x16_20_steps(asuca, lim):
+    c = gen.make_config_case("fp64_32x32x16")
+    got, ref, bud, rbud = _full_step(asuca, c, asuca.FP32_MIXED, 20, lim=lim)
+    _assert_fields(got, ref, TOL32, f"fp32 lim={lim}", both=False)
+    assert np.all(np.abs(bud - rbud) <= TOL32 * np.abs(rbud))
+
+
+def test_budgets_only_call(asuca):
+    import torch
+    c = gen.make_config_case("fp64_32x32x16")
+    og, g = _grid_pair(asuca, c, asuca.FP64)
+    st = asuca.State.from_case(c, prec=asuca.FP64)
+    bud = asuca.step(g, st, c.dt, 0, budgets=True)
+    torch.cuda.synchronize()
+    rb = oracle.budgets(og, c.state())
+    assert np.all(np.abs(bud.cpu().numpy() - rb) <= TOL64 * np.abs(rb) + 1e-300)
+
+
+# ------------------------------------------------------------------ full size, sampled
+
+SAMPLES = [(0, 0), (1023, 1023), (511, 0), (0, 700), (1023, 5)]
+
+
+@pytest.fixture(scope="module")
+def large_case():
+    return gen.make_config_case("large_1024x1024x58")
+
+
+@pytest.mark.parametrize("prec,tol", [(1, TOL32), (0, TOL64)])
+def test_large_1024x1024x58_one_step_sampled_columns(asuca, large_case, prec, tol):
+    """One step at the full 1024x1024x58, 8-tracer size in the launch
+    configuration the benchmark times; sampled 4x4 windows checked against the
+    oracle evaluated on their dependency cone."""
+    import torch
+    c = large_case
+    og, g = _grid_pair(asuca, c, prec)
+    st = asuca.State.from_case(c, prec=prec)
+    asuca.step(g, st, c.dt, 1, budgets=True)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(17)
+    picks = SAMPLES + [tuple(int(v) for v in rng.integers(0, 1024, 2)) for _ in range(6)]
+    Y0 = c.state()
+    for (i0, j0) in picks:
+        w = h = 4
+        ref = oracle.step_window(og, Y0, c.mu, c.mv, c.mw, c.dt, 1, i0, j0, w, h)
+        ii = torch.tensor([(i0 + q) % c.nx for q in range(w)], device="cuda")
+        jj = torch.tensor([(j0 + q) % c.ny for q in range(h)], device="cuda")
+        got = st.fields()[:, :, jj][:, :, :, ii].double().cpu().numpy()
+        _assert_fields(got, ref, tol, f"large prec={prec} window {(i0, j0)}", both=(prec == 0))
+    del st
