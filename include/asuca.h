@@ -142,6 +142,32 @@ asuca_status asuca_debug_column(asuca_grid *grid, asuca_state *state, double dt,
                                 double *precip_col_dev, void *workspace, size_t workspace_bytes,
                                 void *cuda_stream);
 
+/* ---- column pass without a workspace ------------------------------------
+ * The paper has no counterpart to this entry point; it serves callers that
+ * cannot allocate device memory, e.g. a host model whose memory pool is fixed
+ * at start-up, or a caller in the middle of capturing a stream, where
+ * cudaMalloc is not allowed.  It runs the same column pass as
+ * asuca_debug_column (relaxation, sedimentation, implicit vertical
+ * diffusion with the FP64 Thomas solve) on the caller's state and adds each
+ * column's precipitation to precip_col_dev ([ny][nx] doubles), but it takes
+ * no workspace: the solve's scratch is a 16 MiB array compiled into the
+ * library, which every GPU that loads the library keeps until the process
+ * exits.  It allocates nothing: no cudaMalloc, cudaFree or allocating
+ * library call.
+ *   - The scratch is looked up (cudaGetSymbolAddress) on the first call on
+ *     each device, with that device current; make that first call before
+ *     any stream capture.  The grid's device must be the current device.
+ *   - The launch uses as many 128-column blocks as fit in the array
+ *     (nz * (F + 1) * 128 * 8 bytes each; at least eleven within the compiled
+ *     limits of nz and tracers); a size whose single block would not fit is
+ *     rejected with ASUCA_ERR_UNSUPPORTED.
+ *   - All calls on a device share the array and it keeps the last call's
+ *     contents (every value is written before it is read, nothing needs to
+ *     start at zero).  Calls that overlap on the GPU (on different streams
+ *     without ordering) race on it and give wrong results. */
+asuca_status asuca_column_noalloc(asuca_grid *grid, asuca_state *state, double dt,
+                                  double *precip_col_dev, void *cuda_stream);
+
 /* ---- per-kernel timing ------------------------------------------------- */
 
 typedef enum {

@@ -69,6 +69,7 @@ SIGNATURES = {
                                          ctypes.POINTER(StateStruct), _VP, ctypes.c_double, _VP]),
     "asuca_debug_column": (ctypes.c_int, [_VP, ctypes.POINTER(StateStruct), ctypes.c_double, _VP,
                                           _VP, ctypes.c_size_t, _VP]),
+    "asuca_column_noalloc": (ctypes.c_int, [_VP, ctypes.POINTER(StateStruct), ctypes.c_double, _VP, _VP]),
     "asuca_profile_enable": (ctypes.c_int, [_VP, ctypes.c_int]),
     "asuca_profile_read": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
@@ -248,6 +249,14 @@ def debug_column(grid: Grid, state: State, dt: float, precip_col, *, workspace=N
     _check(lib().asuca_debug_column(grid.handle, ctypes.byref(s), float(dt), _ptr(precip_col),
                                     _ptr(workspace), workspace.numel(), _stream_ptr(stream)),
            "asuca_debug_column")
+
+
+def column_noalloc(grid: Grid, state: State, dt: float, precip_col, *, stream=None):
+    """The column pass without a workspace (asuca_column_noalloc): for callers that
+    cannot allocate device memory; its scratch is an array compiled into the library."""
+    s = state.struct()
+    _check(lib().asuca_column_noalloc(grid.handle, ctypes.byref(s), float(dt), _ptr(precip_col),
+                                      _stream_ptr(stream)), "asuca_column_noalloc")
 
 
 def profile_enable(grid: Grid, on: bool = True):

@@ -4,6 +4,7 @@
 #include <cstring>
 #include <new>
 #include <cstdlib>
+#include <mutex>
 
 #include "common.cuh"
 
@@ -227,6 +228,46 @@ asuca_status run_step(asuca_grid *g, asuca_state *st, const void *tend, double d
 
 }  // namespace
 
+// ---- column pass without a caller workspace ------------------------------
+// Scratch for the Thomas intermediates of asuca_column_noalloc().  It lives in
+// a file-scope device array, so every GPU that loads this library holds these
+// bytes until the process exits; all calls on one device share it.
+#define ASUCA_NOALLOC_BYTES (16u << 20)
+static __device__ __align__(256) double g_noalloc_scratch[ASUCA_NOALLOC_BYTES / sizeof(double)];
+
+namespace {
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mu;
+double *g_noalloc_ptr[NOALLOC_MAX_DEVICES];
+
+// Device address of the scratch array on the current device, looked up once
+// per device (host code cannot use the array's name as a device address).
+asuca_status noalloc_scratch(int dev, double **out) {
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return ASUCA_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return ASUCA_ERR_CUDA;
+        g_noalloc_ptr[dev] = (double *)p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return ASUCA_OK;
+}
+
+template <typename T>
+cudaError_t launch_column_noalloc(asuca_grid *g, asuca_state *st, double dt, double *precip_col,
+                                  double *scratch, int blocks, cudaStream_t s) {
+    ColumnParams<T> p = column_params<T>(g, dt);
+    field_ptrs<T>(g, st->rho, st->rhotheta, st->rhoq, p.y);
+    p.precip_col = precip_col;
+    p.partials = nullptr;          // budgets stay off: the kernel never touches partials
+    p.budgets = 0;
+    p.scratch = scratch;
+    p.nslots = (long long)blocks * COL_TPB;
+    return launch_column<T>(p, g->F, blocks, COL_TPB, s);
+}
+}  // namespace
+
 extern "C" {
 
 const char *asuca_status_string(asuca_status s) {
@@ -393,6 +434,32 @@ asuca_status asuca_debug_column(asuca_grid *g, asuca_state *st, double dt, doubl
         p.scratch = (double *)(ws + L.scratch);
         e = launch_column<float>(p, g->F, g->col_grid, COL_TPB, s);
     }
+    return cuda_status(e);
+}
+
+asuca_status asuca_column_noalloc(asuca_grid *g, asuca_state *st, double dt, double *precip_col,
+                                  void *cuda_stream) {
+    if (!g || !st || !st->rho || !st->rhotheta || (g->d.ntracers && !st->rhoq) || !precip_col ||
+        !std::isfinite(dt) || dt < 0.0)
+        return ASUCA_ERR_ARG;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return ASUCA_ERR_CUDA;
+    if (dev != g->device) return ASUCA_ERR_ARG;
+    // one 128-column block needs nz * (F + 1) doubles per column of scratch
+    const size_t per_block = (size_t)g->d.nz * (g->F + 1) * COL_TPB * sizeof(double);
+    const size_t fit = ASUCA_NOALLOC_BYTES / per_block;
+    if (fit < 1) return ASUCA_ERR_UNSUPPORTED;
+    asuca_status prev = take_status(g);
+    if (prev != ASUCA_OK) return prev;
+    double *scratch = nullptr;
+    asuca_status rs = noalloc_scratch(dev, &scratch);
+    if (rs != ASUCA_OK) return rs;
+    const int blocks = (int)((size_t)g->col_grid < fit ? (size_t)g->col_grid : fit);
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    g->last_stream = s;
+    cudaError_t e = g->d.prec == ASUCA_FP64
+                        ? launch_column_noalloc<double>(g, st, dt, precip_col, scratch, blocks, s)
+                        : launch_column_noalloc<float>(g, st, dt, precip_col, scratch, blocks, s);
     return cuda_status(e);
 }
 
