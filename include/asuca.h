@@ -142,6 +142,14 @@ asuca_status asuca_debug_column(asuca_grid *grid, asuca_state *state, double dt,
                                 double *precip_col_dev, void *workspace, size_t workspace_bytes,
                                 void *cuda_stream);
 
+/* Test hook for the arithmetic helpers of the column solve (device arrays of
+ * n values; any output may be NULL): widen[i] = in_f[i] as double, narrow[i]
+ * = in_d[i] rounded to float (nearest-even), both computed on the integer
+ * pipe from the IEEE-754 bit fields; rcp[i] = 1 / in_d[i] by two
+ * Newton-Raphson steps from the hardware approximation. */
+asuca_status asuca_debug_numerics(const float *in_f, const double *in_d, int n, double *widen,
+                                  float *narrow, double *rcp, void *cuda_stream);
+
 /* ---- column pass without a workspace ------------------------------------
  * The paper has no counterpart to this entry point; it serves callers that
  * cannot allocate device memory, e.g. a host model whose memory pool is fixed

@@ -69,6 +69,7 @@ SIGNATURES = {
                                          ctypes.POINTER(StateStruct), _VP, ctypes.c_double, _VP]),
     "asuca_debug_column": (ctypes.c_int, [_VP, ctypes.POINTER(StateStruct), ctypes.c_double, _VP,
                                           _VP, ctypes.c_size_t, _VP]),
+    "asuca_debug_numerics": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP, _VP, _VP, _VP]),
     "asuca_column_noalloc": (ctypes.c_int, [_VP, ctypes.POINTER(StateStruct), ctypes.c_double, _VP, _VP]),
     "asuca_profile_enable": (ctypes.c_int, [_VP, ctypes.c_int]),
     "asuca_profile_read": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double),
@@ -249,6 +250,19 @@ def debug_column(grid: Grid, state: State, dt: float, precip_col, *, workspace=N
     _check(lib().asuca_debug_column(grid.handle, ctypes.byref(s), float(dt), _ptr(precip_col),
                                     _ptr(workspace), workspace.numel(), _stream_ptr(stream)),
            "asuca_debug_column")
+
+
+def debug_numerics(in_f, in_d, *, stream=None):
+    """(widen(in_f), narrow(in_d), rcp(in_d)) computed by the library's column-solve helpers."""
+    import torch
+    n = in_f.numel()
+    assert in_d.numel() == n and in_f.dtype == torch.float32 and in_d.dtype == torch.float64
+    w = torch.empty(n, dtype=torch.float64, device=in_f.device)
+    nr = torch.empty(n, dtype=torch.float32, device=in_f.device)
+    r = torch.empty(n, dtype=torch.float64, device=in_f.device)
+    _check(lib().asuca_debug_numerics(_ptr(in_f), _ptr(in_d), n, _ptr(w), _ptr(nr), _ptr(r),
+                                      _stream_ptr(stream)), "asuca_debug_numerics")
+    return w, nr, r
 
 
 def column_noalloc(grid: Grid, state: State, dt: float, precip_col, *, stream=None):

@@ -20,6 +20,9 @@ struct asuca_grid {
     volatile int *status_host;    // pinned, mapped; the device writes error codes here
     int *status_dev;
     cudaStream_t last_stream;
+    // TMA descriptors of the two padded stage buffers, for the workspace they were made for
+    void *map_ws;
+    CUtensorMap map_ystar, map_ystar2;
     // opt-in per-kernel timing: events recorded around every launch
     bool prof_on;
     cudaEvent_t *prof_ev;
@@ -30,7 +33,12 @@ struct asuca_grid {
 namespace {
 
 constexpr size_t ALIGN = 256;
-constexpr int COL_BLOCKS_PER_SM = 1;
+// column-kernel blocks resident per SM; the Thomas scratch is sized to match
+int col_blocks_per_sm() {
+    const char *e = std::getenv("ASUCA_COL_BLOCKS_PER_SM");
+    const int v = e ? std::atoi(e) : 0;
+    return v > 0 ? v : 3;
+}
 
 size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
 
@@ -42,9 +50,13 @@ struct StepLayout {
     size_t ystar, ystar2, precip, partials, scratch, total;
 };
 
+size_t padded_field_elems(const asuca_grid *g) {
+    return (size_t)g->d.nz * (g->d.ny + 4) * padded_pitch(g->d.nx);
+}
+
 StepLayout step_layout(const asuca_grid *g) {
     StepLayout L;
-    const size_t state = (size_t)g->F * g->cells * elem_size(g);
+    const size_t state = (size_t)g->F * padded_field_elems(g) * elem_size(g);
     size_t off = 0;
     L.ystar = off;
     off = align_up(off + state);
@@ -81,9 +93,10 @@ void field_ptrs(const asuca_grid *g, void *rho, void *rhotheta, void *rhoq, T **
     for (int f = g->F; f < MAXF; f++) out[f] = nullptr;
 }
 
+// field bases (padded origin) of a padded stage buffer in the workspace
 template <typename T>
 void workspace_fields(const asuca_grid *g, char *ws, size_t off, T **out) {
-    for (int f = 0; f < g->F; f++) out[f] = (T *)(ws + off) + (size_t)f * g->cells;
+    for (int f = 0; f < g->F; f++) out[f] = (T *)(ws + off) + (size_t)f * padded_field_elems(g);
     for (int f = g->F; f < MAXF; f++) out[f] = nullptr;
 }
 
@@ -100,6 +113,9 @@ StageParams<T> stage_params(const asuca_grid *g, const asuca_state *fl, const vo
     p.nz = g->d.nz;
     p.lim = (int)g->d.lim;
     p.plane = g->plane;
+    p.status = g->status_dev;
+    p.opitch = padded_pitch(g->d.nx);
+    p.oplane = (long long)(g->d.ny + 4) * p.opitch;
     p.rdx = (T)(1.0 / g->d.dx);
     p.rdy = (T)(1.0 / g->d.dy);
     for (int k = 0; k < g->d.nz; k++) p.rdz[k] = (T)(1.0 / g->dz[k]);
@@ -131,6 +147,7 @@ ColumnParams<T> column_params(const asuca_grid *g, double dt) {
     for (int k = 0; k < nz; k++) {
         p.dz[k] = g->dz[k];
         p.dzT[k] = (T)g->dz[k];
+        p.dzlo[k] = (float)(g->dz[k] - (double)(float)g->dz[k]);
         p.sedr[k] = (T)(1.0 / (g->dz[k] + dt * d.v_sed));
         p.thref[k] = (T)(300.0 + 0.004 * g->zc[k]);
         p.dzr_up[k] = (k + 1 < nz) ? g->dz[k + 1] / g->dz[k] : 0.0;
@@ -192,14 +209,27 @@ asuca_status run_step(asuca_grid *g, asuca_state *st, const void *tend, double d
 
     cudaError_t e = cudaMemsetAsync(ws + L.precip, 0, (size_t)g->plane * sizeof(double), s);
     if (e != cudaSuccess) return ASUCA_ERR_CUDA;
+    if (g->map_ws != (void *)ws) {
+        if (encode_stage_map<T>(&g->map_ystar, ws + L.ystar, F, g->d.nx, g->d.ny, g->d.nz) != cudaSuccess ||
+            encode_stage_map<T>(&g->map_ystar2, ws + L.ystar2, F, g->d.nx, g->d.ny, g->d.nz) != cudaSuccess) {
+            g->map_ws = nullptr;
+            return ASUCA_ERR_CUDA;
+        }
+        g->map_ws = (void *)ws;
+    }
     const T cdt[3] = {(T)(dt / 3.0), (T)(dt / 2.0), (T)dt};
+    for (int f = 0; f < MAXF; f++) sp.ybase[f] = yn[f];
     for (int n = 0; n < nsteps; n++) {
         for (int stg = 0; stg < 3; stg++) {
-            T **in = stg == 0 ? yn : (stg == 1 ? y1 : y2);
+            // stage 1 reads the caller's fields (cp.async), stages 2 and 3 the padded
+            // buffers the previous stage wrote (TMA); stage 3 writes the caller's fields
+            sp.tma_in = stg > 0;
+            if (stg == 1) sp.tmap = g->map_ystar;
+            if (stg == 2) sp.tmap = g->map_ystar2;
+            sp.out_padded = stg < 2;
             T **out = stg == 0 ? y1 : (stg == 1 ? y2 : yn);
             for (int f = 0; f < MAXF; f++) {
-                sp.yin[f] = in[f];
-                sp.ybase[f] = yn[f];
+                sp.yin[f] = yn[f];
                 sp.yout[f] = out[f];
             }
             sp.cdt = cdt[stg];
@@ -319,7 +349,7 @@ asuca_status asuca_init_grid(const asuca_grid_desc *desc, asuca_grid **out) {
         return ASUCA_ERR_CUDA;
     }
     long long need = (g->plane + COL_TPB - 1) / COL_TPB;
-    long long cap = (long long)g->nsm * COL_BLOCKS_PER_SM;
+    long long cap = (long long)g->nsm * col_blocks_per_sm();
     g->col_grid = (int)(need < cap ? need : cap);
     void *h = nullptr;
     if (cudaHostAlloc(&h, 64, cudaHostAllocMapped) != cudaSuccess) {
@@ -461,6 +491,12 @@ asuca_status asuca_column_noalloc(asuca_grid *g, asuca_state *st, double dt, dou
                         ? launch_column_noalloc<double>(g, st, dt, precip_col, scratch, blocks, s)
                         : launch_column_noalloc<float>(g, st, dt, precip_col, scratch, blocks, s);
     return cuda_status(e);
+}
+
+asuca_status asuca_debug_numerics(const float *in_f, const double *in_d, int n, double *widen,
+                                  float *narrow, double *rcp, void *cuda_stream) {
+    if (n < 0 || (n > 0 && ((widen && !in_f) || ((narrow || rcp) && !in_d)))) return ASUCA_ERR_ARG;
+    return cuda_status(launch_numerics(in_f, in_d, n, widen, narrow, rcp, (cudaStream_t)cuda_stream));
 }
 
 asuca_status asuca_profile_enable(asuca_grid *g, int on) {

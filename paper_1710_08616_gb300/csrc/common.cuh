@@ -6,6 +6,7 @@
 // column and marches k (Sec. 1.1: parallel in I/J, sequential in K).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -18,15 +19,46 @@ constexpr int MAXNZ = ASUCA_MAX_NZ;
 
 // ------------------------------------------------------------------ params
 
+// Tile, ring depth and shared-memory layout of the stage kernel.  A CTA is
+// 32 x TY columns (one warp per row); a ring slot holds every field of one
+// level plane of the tile with a 4-column halo in i (2 used; the TMA box must
+// start on a 16-byte boundary) and a 2-row halo in j.
+template <typename T, int NF>
+struct StageShape {
+    static constexpr int TX = 32;
+    static constexpr int TY = 8;
+    static constexpr int D = 5;                          // ring depth (levels in flight + window)
+    static constexpr int MIN_BLOCKS = sizeof(T) == 4 ? 2 : 1;   // CTAs resident per SM
+    static constexpr int SX = TX + 8;
+    static constexpr int SY = TY + 4;
+    static constexpr int NT = NF - 1;
+    static constexpr int SLOT_RAW = NF * SY * SX;
+    static constexpr int SLOT_ELEMS = (SLOT_RAW * (int)sizeof(T) + 127) / 128 * 128 / (int)sizeof(T);
+    static constexpr unsigned TX_BYTES = (unsigned)(SLOT_RAW * sizeof(T));
+    static constexpr size_t RING_BYTES = (size_t)D * SLOT_ELEMS * sizeof(T);
+    static constexpr size_t YS_BYTES = ((size_t)NT * (TY + 1) * TX * sizeof(T) + 15) / 16 * 16;
+    static constexpr size_t XB_BYTES = ((size_t)NT * TY * sizeof(T) + 15) / 16 * 16;
+    static constexpr size_t SMEM_BYTES = RING_BYTES + YS_BYTES + XB_BYTES + (size_t)D * 8;
+};
+
+// Padded layout of the library's own stage buffers: [F][nz][ny + 4][pitch],
+// logical (i, j) at (i + 4, j + 2), pitch = nx + 8 rounded up to 8 elements;
+// the 2-wide periodic ghosts are written by the producing stage.
+__host__ __device__ __forceinline__ long long padded_pitch(int nx) { return ((long long)nx + 8 + 7) / 8 * 8; }
+
 template <typename T>
 struct StageParams {
-    const T *yin[MAXF];     // stage input Y^(s-1): phi and fluxes come from here
-    const T *ybase[MAXF];   // Y^n
-    T *yout[MAXF];          // Y^(s) = Y^n + cdt * R(Y^(s-1))
+    CUtensorMap tmap;       // padded stage input, when tma_in
+    const T *yin[MAXF];     // unpadded stage input, when !tma_in
+    const T *ybase[MAXF];   // Y^n (unpadded)
+    T *yout[MAXF];          // Y^(s) = Y^n + cdt * R(Y^(s-1)); padded origin when out_padded
     const T *mu, *mv, *mw;
     const T *tend;          // [F-1][nz][ny][nx] or nullptr
+    int *status;            // device status word (mapped host memory)
     int nx, ny, nz, lim;
+    int tma_in, out_padded;
     long long plane;        // nx * ny
+    long long opitch, oplane;   // padded output: row pitch and level stride (elements)
     T cdt, rdx, rdy;
     T rdz[MAXNZ];           // 1 / dz_k
 };
@@ -46,7 +78,8 @@ struct ColumnParams {
     double *partials;       // [gridDim.x][F + 1] budget partials (sum over columns of sum_k f dz)
     double *scratch;        // [nz][F + 1][nslots]
     long long nslots;
-    T dzT[MAXNZ];           // dz_k
+    T dzT[MAXNZ];           // dz_k (rounded to T)
+    float dzlo[MAXNZ];      // dz_k - (float)dz_k, the low part for float budget sums
     T sedr[MAXNZ];          // 1 / (dz_k + dt v)
     T thref[MAXNZ];         // theta_ref(z_k)
     double dz[MAXNZ];
@@ -62,16 +95,48 @@ __host__ __device__ __forceinline__ int wrap_index(int i, int n) {
     return r < 0 ? r + n : r;
 }
 
+// ---- float <-> double on the integer pipe -------------------------------
+// On this GPU the hardware conversions between float and double issue on the
+// FP64 pipe (1/64 of the FP32 rate), so the column solve converts through the
+// IEEE-754 bit fields instead (binary32: 1+8+23 bits, bias 127; binary64:
+// 1+11+52 bits, bias 1023).  Zero, subnormal, infinite and NaN inputs take
+// the hardware path, so every result equals the hardware conversion.
+
+// Exact widening: exponent rebiased by 1023 - 127 = 896, mantissa shifted by 29.
+__device__ __forceinline__ double f2d_bits(float x) {
+    const uint32_t u = __float_as_uint(x);
+    const uint32_t e = u & 0x7f800000u;
+    if (e == 0u || e == 0x7f800000u) return (double)x;
+    const uint32_t hi = (u & 0x80000000u) | (((u & 0x7fffffffu) >> 3) + (896u << 20));
+    return __hiloint2double((int)hi, (int)(u << 29));
+}
+
+// Narrowing with round-to-nearest-even on the 29 dropped mantissa bits; the
+// rounding carry may ripple into the exponent (and to infinity above FLT_MAX),
+// as IEEE rounding does.  Doubles outside the float normal range take the
+// hardware path.
+__device__ __forceinline__ float d2f_bits(double x) {
+    const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+    const uint32_t ea = (hi >> 20) & 0x7ffu;
+    if (ea < 897u || ea > 1150u) return __double2float_rn(x);
+    uint32_t mag = (((hi & 0x7fffffffu) - (896u << 20)) << 3) | (lo >> 29);
+    const uint32_t rem = lo & 0x1fffffffu;
+    mag += (rem > 0x10000000u || (rem == 0x10000000u && (mag & 1u))) ? 1u : 0u;
+    return __uint_as_float((hi & 0x80000000u) | mag);
+}
+
+template <typename T> __device__ __forceinline__ double to_f64(T x);
+template <> __device__ __forceinline__ double to_f64<double>(double x) { return x; }
+template <> __device__ __forceinline__ double to_f64<float>(float x) { return f2d_bits(x); }
+
 // Reciprocal in double by Newton-Raphson iteration on f(y) = 1/y - x,
-// y <- y (2 - x y), started from the hardware single-precision approximation.
-// Each iteration squares the relative error: ~2^-22 -> ~2^-44 -> below 2^-53
-// (the result is within a few ulp of 1/x).  Valid for |x| in the normal
-// float range, which holds for densities and the diagonally dominant pivots
-// of the vertical-diffusion solve.
+// y <- y (2 - x y), started from the hardware reciprocal approximation of the
+// high word.  Each iteration squares the relative error, so two iterations
+// reach double precision (within a few ulp).  Valid for normal, finite,
+// non-zero x (densities and the diagonally dominant pivots of the solve).
 __device__ __forceinline__ double rcp_newton(double x) {
-    float xf = (float)x, yf;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(xf));
-    double y = (double)yf;
+    double y;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
     double e = fma(-x, y, 1.0);
     y = fma(y, e, y);
     e = fma(-x, y, 1.0);
@@ -106,16 +171,58 @@ __device__ __forceinline__ T face_value(T pm1, T p0, T p1, T p2, T m, int lim) {
     return c + T(0.5) * limiter(d0, d1, lim);
 }
 
+// v with its sign flipped when s has its sign bit set (v * sgn(s) as a bit operation)
+__device__ __forceinline__ float sign_transfer(float v, float s) {
+    return __uint_as_float(__float_as_uint(v) ^ (__float_as_uint(s) & 0x80000000u));
+}
+__device__ __forceinline__ double sign_transfer(double v, double s) {
+    return __longlong_as_double(__double_as_longlong(v) ^
+                                (__double_as_longlong(s) & (long long)0x8000000000000000ull));
+}
+
+// Face value with the limiter fixed at compile time, from the four cells
+// around face i+1/2 (values at i-1, i, i+1, i+2), for the upwind predicate
+// u = (m >= 0) and h = u ? 1/2 : -1/2.  The limiter increment is odd,
+// L(-a, -b) = -L(a, b), so the m < 0 mirror of the stencil is the same
+// formula on the differences oriented with the flow:
+//   face = c + h L(dfar, dmid),  c the upwind cell,  dmid = p1 - p0,
+//   dfar = p0 - pm1 (u) or p2 - p1 (!u).
+// Koren: with x = dmid carrying the sign it has relative to dfar (x >= 0 iff
+// they share a sign) and a = |dfar|,
+//   L = sgn(dfar) max(0, min(2x, (a + 2x)/3, 2a)),
+// which is zero unless dfar and dmid share a sign, and equals
+// sgn(d0) min(2|d1|, (|d0| + 2|d1|)/3, 2|d0|) when they do.
+template <int LIM, typename T>
+__device__ __forceinline__ T face_fast(T pm1, T p0, T p1, T p2, bool u, T h) {
+    const T c = u ? p0 : p1;
+    if (LIM == ASUCA_LIM_UPWIND1) return c;
+    const T dmid = p1 - p0;
+    const T dfar = (u ? p0 : p2) - (u ? pm1 : p1);
+    if (LIM == ASUCA_LIM_LINEAR) return c + h * ((dfar + T(2) * dmid) * T(1.0 / 3.0));
+    const T x = sign_transfer(dmid, dfar);
+    const T a = fabs(dfar);
+    T m = fmin(x + x, fmin((a + T(2) * x) * T(1.0 / 3.0), a + a));
+    m = fmax(m, T(0));
+    return c + h * copysign(m, dfar);
+}
+
 // ------------------------------------------------------------------ launchers
 
 template <typename T>
 cudaError_t launch_stage(const StageParams<T> &p, int nf, cudaStream_t s);
+
+// Encode the TMA descriptor of a padded stage buffer (F fields at base).
+template <typename T>
+cudaError_t encode_stage_map(CUtensorMap *map, void *base, int nf, int nx, int ny, int nz);
 
 template <typename T>
 cudaError_t launch_column(const ColumnParams<T> &p, int nf, int grid, int block, cudaStream_t s);
 
 cudaError_t launch_budget_reduce(const double *partials, int nblocks, int nq, int nf,
                                  double dxdy, double *out, int *status, cudaStream_t s);
+
+cudaError_t launch_numerics(const float *in_f, const double *in_d, int n, double *widen, float *narrow,
+                            double *rcp, cudaStream_t s);
 
 constexpr int COL_TPB = 128;
 

@@ -1,0 +1,424 @@
+// One Wicker-Skamarock RK3 stage, fused (Sec. 1.1 "ASUCA on GPU"):
+//   phi = (rho phi) / rho                     (one reciprocal of rho per cell)
+//   face values by the Koren limiter in i, j, k, upwind by sign(M)
+//   R = -[dX/dx + dY/dy + dZ/dz] + tendency,  Y_out = Y_base + cdt R
+//
+// Mapping: a CTA owns a 32 x TY tile of (i, j) columns, one warp per row, and
+// marches k upward (parallel in I/J, sequential in K; Sec. 1.1, Sec. 1.3).
+// Level planes of the stage input stream through a ring of D shared-memory
+// slots, each holding every field of the tile plus a halo of 4 columns in i
+// (the TMA box must start on a 16-byte boundary; 2 are used) and 2 rows in j:
+//   * from the library's padded stage buffers, one 4D TMA box per level
+//     (cp.async.bulk.tensor, completion on an mbarrier); periodic halos are
+//     ghost copies written by the stage that produced the buffer;
+//   * from the caller's unpadded fields, per-thread cp.async copies with the
+//     periodic wrap done in the index arithmetic.
+// Levels are requested D-2 levels ahead.  Each arriving level is converted in
+// place from rho*phi to phi, once per cell.  Every face is reconstructed
+// once: i+1/2 by each thread (the i-1/2 flux comes from the neighbouring lane
+// by shuffle), j+1/2 by each thread into shared memory, k+1/2 by each thread
+// with the k-1/2 flux carried in registers; the faces on the tile's left and
+// bottom edges are computed by warps 1 and 0.
+#pragma once
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "common.cuh"
+
+namespace asuca {
+
+// ------------------------------------------------------------------ PTX helpers
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for the mbarrier phase with the given parity; gives up after about one
+// second of wall time and returns false.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    const uint32_t addr = smem_u32(bar);
+    uint64_t t0 = 0;
+    for (uint32_t it = 0;; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(addr), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (it == 0) t0 = global_ns();
+        else if ((it & 63u) == 0 && global_ns() - t0 > 1000000000ull) return false;
+    }
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, int x, int y, int z, int w,
+                                            uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(z), "r"(w), "r"(smem_u32(bar))
+        : "memory");
+}
+
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_u32(dst)), "l"(src), "n"(BYTES)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// ------------------------------------------------------------------ the kernel
+
+template <typename T, int NF, int LIM>
+__global__ void __launch_bounds__(32 * StageShape<T, NF>::TY, StageShape<T, NF>::MIN_BLOCKS)
+    stage_kernel(const __grid_constant__ StageParams<T> p) {
+    using S = StageShape<T, NF>;
+    constexpr int TX = S::TX, TY = S::TY, D = S::D, SX = S::SX, SY = S::SY, NT = S::NT;
+    constexpr int NTHR = TX * TY;
+    constexpr int FE = SY * SX;                   // elements of one field in a slot
+    constexpr int NCELL = TY * (TX + 4) + 4 * TX; // the slot cells the stencil reads (no corners)
+    constexpr int MAXC = (NCELL + NTHR - 1) / NTHR;
+
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    T *ring = reinterpret_cast<T *>(smem_raw);
+    T *ysm = reinterpret_cast<T *>(smem_raw + S::RING_BYTES);            // [NT][TY+1][TX]
+    T *xbs = reinterpret_cast<T *>(smem_raw + S::RING_BYTES + S::YS_BYTES); // [NT][TY]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw + S::RING_BYTES + S::YS_BYTES + S::XB_BYTES);
+
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+    const int nx = p.nx, ny = p.ny, nz = p.nz;
+    const long long plane = p.plane;
+    const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+    const int i = i0 + tx, j = j0 + ty;
+    const bool valid = (i < nx) && (j < ny);
+    const int ic = wrap_index(i, nx), jc = wrap_index(j, ny);
+    const long long own = (long long)jc * nx + ic;
+    const long long left = (long long)jc * nx + wrap_index(ic - 1, nx);
+    const long long down = (long long)wrap_index(jc - 1, ny) * nx + ic;
+    const bool tma = p.tma_in != 0;
+
+    if (tma && tid == 0) {
+        for (int s = 0; s < D; s++) mbar_init(&bars[s], 1);
+        fence_proxy_async();
+    }
+
+    // slot cells this thread copies (cp.async path) and converts (both paths)
+    int soff[MAXC];
+    long long goff[MAXC];
+    int nc = 0;
+#pragma unroll
+    for (int q = 0; q < MAXC; q++) {
+        const int c = tid + q * NTHR;
+        soff[q] = 0;
+        goff[q] = 0;
+        if (c < NCELL) {
+            int sy, sx;
+            if (c < TY * (TX + 4)) {
+                sy = 2 + c / (TX + 4);
+                sx = 2 + c % (TX + 4);
+            } else {
+                const int c2 = c - TY * (TX + 4);
+                const int r = c2 / TX;
+                sx = 4 + c2 % TX;
+                sy = r < 2 ? r : TY + r;
+            }
+            soff[q] = sy * SX + sx;
+            goff[q] = (long long)wrap_index(j0 + sy - 2, ny) * nx + wrap_index(i0 + sx - 4, nx);
+            nc = q + 1;
+        }
+    }
+    __syncthreads();
+
+    auto slot = [&](int lev) -> T * { return ring + (size_t)(lev % D) * S::SLOT_ELEMS; };
+
+    auto issue = [&](int lev) {
+        if (tma) {
+            if (tid == 0 && lev < nz) {
+                uint64_t *bar = &bars[lev % D];
+                mbar_expect_tx(bar, S::TX_BYTES);
+                tma_load_4d(slot(lev), &p.tmap, i0, j0, lev, 0, bar);
+            }
+        } else {
+            if (lev < nz) {
+                T *sl = slot(lev);
+                const long long lb = (long long)lev * plane;
+#pragma unroll
+                for (int q = 0; q < MAXC; q++) {
+                    if (q < nc) {
+#pragma unroll
+                        for (int f = 0; f < NF; f++) cp_async<sizeof(T)>(sl + f * FE + soff[q], p.yin[f] + lb + goff[q]);
+                    }
+                }
+            }
+            cp_async_commit();
+        }
+    };
+
+    // convert the cells this thread owns in the slot of level lev from rho*phi to phi
+    auto convert = [&](int lev) {
+        T *sl = slot(lev);
+#pragma unroll
+        for (int q = 0; q < MAXC; q++) {
+            if (q < nc) {
+                const T r = recip(sl[soff[q]]);
+#pragma unroll
+                for (int f = 1; f < NF; f++) sl[f * FE + soff[q]] *= r;
+            }
+        }
+    };
+
+    bool timed_out = false;
+    // ---- prologue: request levels 0 .. D-3, convert levels 0 and 1
+#pragma unroll 1
+    for (int lev = 0; lev <= D - 3; lev++) issue(lev);
+    if (tma) {
+        if (!mbar_wait(&bars[0], 0)) timed_out = true;
+        else convert(0);
+        if (nz > 1) {
+            if (!mbar_wait(&bars[1], 0)) timed_out = true;
+            else convert(1);
+        }
+    } else {
+        cp_async_wait<D - 3>();
+        convert(0);
+        cp_async_wait<D - 4>();
+        if (nz > 1) convert(1);
+    }
+
+    const T cdt = p.cdt;
+    const T ax = -cdt * p.rdx, ay = -cdt * p.rdy;   // out = base + ax dX + ay dY + az dZ + cdt t
+    const int warp = ty, lane = tx;
+    // Edge faces (j0-1/2 for the tile's 32 columns, i0-1/2 for its TY rows),
+    // one task per (field, edge), dealt round-robin to the warps.
+    const long long edge_b = (long long)wrap_index(j0 - 1, ny) * nx + ic;                 // MV below the tile
+    const int er = lane < TY ? lane : 0;
+    const long long edge_l = (long long)wrap_index(j0 + er, ny) * nx + wrap_index(i0 - 1, nx);  // MU left of row er
+
+    T zlo[NF];
+#pragma unroll
+    for (int f = 0; f < NF; f++) zlo[f] = T(0);
+
+    // per-level operands, requested one level ahead at the start of the previous level
+    T mup, mum, mvp, mvm, mwp, meb, mel, yb[NF];
+    T nmup, nmum, nmvp, nmvm, nmwp, nmeb, nmel, nyb[NF];
+    auto prefetch = [&](int k) {
+        const long long kb = (long long)k * plane;
+        nmup = p.mu[kb + own];
+        nmum = p.mu[kb + left];
+        nmvp = p.mv[kb + own];
+        nmvm = p.mv[kb + down];
+        nmwp = (k < nz - 1) ? p.mw[kb + plane + own] : T(0);
+        nmeb = p.mv[kb + edge_b];
+        nmel = p.mu[kb + edge_l];
+#pragma unroll
+        for (int f = 0; f < NF; f++) nyb[f] = p.ybase[f][kb + own];
+    };
+    auto advance = [&]() {
+        mup = nmup; mum = nmum; mvp = nmvp; mvm = nmvm; mwp = nmwp; meb = nmeb; mel = nmel;
+#pragma unroll
+        for (int f = 0; f < NF; f++) yb[f] = nyb[f];
+    };
+    prefetch(0);
+    advance();
+
+    const int cy = ty + 2, cx = tx + 4, cc = cy * SX + cx;
+
+#pragma unroll 1
+    for (int k = 0; k < nz; k++) {
+        // ---- level k+2 must be resident and converted before anyone computes level k
+        if (k + 2 < nz) {
+            if (tma) {
+                if (!mbar_wait(&bars[(k + 2) % D], ((k + 2) / D) & 1)) timed_out = true;
+                else convert(k + 2);
+            } else {
+                cp_async_wait<(D >= 5 ? D - 5 : 0)>();
+                convert(k + 2);
+            }
+        }
+        if (tma) fence_proxy_async();
+        if (__syncthreads_or(timed_out)) break;
+        issue(k + D - 2);   // into the slot of level k-2, which nobody reads any more
+        if (k + 1 < nz) prefetch(k + 1);
+
+        // ---- faces
+        const T *Sk = slot(k);
+        const T *Skm = slot(k > 0 ? k - 1 : 0);
+        const T *Skp = slot(k + 1 < nz ? k + 1 : nz - 1);
+        const T *Skp2 = slot(k + 2 < nz ? k + 2 : nz - 1);
+        const bool top = (k == nz - 1);
+        const bool ux = mup >= T(0), uy = mvp >= T(0), uz = mwp >= T(0);
+        const T hx = ux ? T(0.5) : T(-0.5), hy = uy ? T(0.5) : T(-0.5), hz = uz ? T(0.5) : T(-0.5);
+        T xp[NT], yp[NT], zp[NT];
+#pragma unroll
+        for (int f = 0; f < NT; f++) {
+            const int fo = (f + 1) * FE;
+            const T c = Sk[fo + cc];
+            xp[f] = mup * face_fast<LIM>(Sk[fo + cc - 1], c, Sk[fo + cc + 1], Sk[fo + cc + 2], ux, hx);
+            yp[f] = mvp * face_fast<LIM>(Sk[fo + cc - SX], c, Sk[fo + cc + SX], Sk[fo + cc + 2 * SX], uy, hy);
+            ysm[(f * (TY + 1) + ty + 1) * TX + tx] = yp[f];
+            zp[f] = top ? T(0) : mwp * face_fast<LIM>(Skm[fo + cc], c, Skp[fo + cc], Skp2[fo + cc], uz, hz);
+        }
+        {
+            const bool ub = meb >= T(0), ul = mel >= T(0);
+            const T hb = ub ? T(0.5) : T(-0.5), hl = ul ? T(0.5) : T(-0.5);
+#pragma unroll 1
+            for (int t = warp; t < 2 * NT; t += TY) {
+                const int f = t >> 1;
+                if ((t & 1) == 0) {
+                    // Y at j0-1/2 for column lane: phi rows 0..3 of the slot
+                    const int fo = (f + 1) * FE + cx;
+                    ysm[(f * (TY + 1)) * TX + tx] =
+                        meb * face_fast<LIM>(Sk[fo], Sk[fo + SX], Sk[fo + 2 * SX], Sk[fo + 3 * SX], ub, hb);
+                } else if (lane < TY) {
+                    // X at i0-1/2 for row lane: phi columns 2..5 of the slot
+                    const int fo = (f + 1) * FE + (lane + 2) * SX;
+                    xbs[f * TY + lane] = mel * face_fast<LIM>(Sk[fo + 2], Sk[fo + 3], Sk[fo + 4], Sk[fo + 5], ul, hl);
+                }
+            }
+        }
+        __syncthreads();
+
+        // ---- divergence, RK combine, store
+        const T az = -cdt * p.rdz[k];
+        T out[NF];
+        out[0] = yb[0] + ax * (mup - mum) + ay * (mvp - mvm) + az * (mwp - zlo[0]);
+        zlo[0] = mwp;
+#pragma unroll
+        for (int f = 0; f < NT; f++) {
+            T xm = __shfl_up_sync(0xffffffffu, xp[f], 1);
+            if (lane == 0) xm = xbs[f * TY + ty];
+            const T ym = ysm[(f * (TY + 1) + ty) * TX + tx];
+            T o = yb[f + 1] + ax * (xp[f] - xm);
+            o += ay * (yp[f] - ym);
+            o += az * (zp[f] - zlo[f + 1]);
+            if (p.tend) o += cdt * p.tend[(long long)f * nz * plane + (long long)k * plane + own];
+            zlo[f + 1] = zp[f];
+            out[f + 1] = o;
+        }
+        if (valid) {
+            if (p.out_padded) {
+                const long long ob = (long long)k * p.oplane + (long long)(j + 2) * p.opitch + (i + 4);
+                const long long gx = (i < 2) ? nx : ((i >= nx - 2) ? -nx : 0);
+                const long long gy = (j < 2) ? (long long)ny * p.opitch : ((j >= ny - 2) ? -(long long)ny * p.opitch : 0);
+#pragma unroll
+                for (int f = 0; f < NF; f++) {
+                    T *o = p.yout[f] + ob;
+                    o[0] = out[f];
+                    if (gx) o[gx] = out[f];
+                    if (gy) o[gy] = out[f];
+                }
+            } else {
+                const long long o = (long long)k * plane + own;
+#pragma unroll
+                for (int f = 0; f < NF; f++) p.yout[f][o] = out[f];
+            }
+        }
+        if (k + 1 < nz) advance();
+    }
+
+    if (timed_out) {
+        if (tid == 0 && p.status) atomicCAS(p.status, 0, (int)ASUCA_ERR_TIMEOUT);
+    }
+    if (!tma) cp_async_wait<0>();
+}
+
+template <typename T, int NF, int LIM>
+static cudaError_t launch_lim(const StageParams<T> &p, cudaStream_t s) {
+    using S = StageShape<T, NF>;
+    static bool attr_set = false;   // one attribute call per instantiation
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(stage_kernel<T, NF, LIM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)S::SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    dim3 block(S::TX, S::TY);
+    dim3 grid((p.nx + S::TX - 1) / S::TX, (p.ny + S::TY - 1) / S::TY);
+    stage_kernel<T, NF, LIM><<<grid, block, S::SMEM_BYTES, s>>>(p);
+    return cudaGetLastError();
+}
+
+template <typename T, int NF>
+static cudaError_t launch_nf(const StageParams<T> &p, cudaStream_t s) {
+    switch (p.lim) {
+        case ASUCA_LIM_KOREN: return launch_lim<T, NF, ASUCA_LIM_KOREN>(p, s);
+        case ASUCA_LIM_LINEAR: return launch_lim<T, NF, ASUCA_LIM_LINEAR>(p, s);
+        case ASUCA_LIM_UPWIND1: return launch_lim<T, NF, ASUCA_LIM_UPWIND1>(p, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename T>
+cudaError_t launch_stage(const StageParams<T> &p, int nf, cudaStream_t s) {
+    switch (nf) {
+        case 2: return launch_nf<T, 2>(p, s);
+        case 3: return launch_nf<T, 3>(p, s);
+        case 4: return launch_nf<T, 4>(p, s);
+        case 5: return launch_nf<T, 5>(p, s);
+        case 6: return launch_nf<T, 6>(p, s);
+        case 7: return launch_nf<T, 7>(p, s);
+        case 8: return launch_nf<T, 8>(p, s);
+        case 9: return launch_nf<T, 9>(p, s);
+        case 10: return launch_nf<T, 10>(p, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+
+static inline PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)f;
+    }
+    return fn;
+}
+
+template <typename T>
+cudaError_t encode_stage_map(CUtensorMap *map, void *base, int nf, int nx, int ny, int nz) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return cudaErrorNotSupported;
+    using S = StageShape<T, 2>;   // TY, SX, SY do not depend on the field count
+    const long long P = padded_pitch(nx);
+    const cuuint64_t dims[4] = {(cuuint64_t)P, (cuuint64_t)(ny + 4), (cuuint64_t)nz, (cuuint64_t)nf};
+    const cuuint64_t strides[3] = {(cuuint64_t)(P * sizeof(T)), (cuuint64_t)(P * (ny + 4) * sizeof(T)),
+                                   (cuuint64_t)(P * (ny + 4) * (long long)nz * sizeof(T))};
+    const cuuint32_t box[4] = {(cuuint32_t)S::SX, (cuuint32_t)S::SY, 1u, (cuuint32_t)nf};
+    const cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
+    CUresult r = enc(map, sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4,
+                     base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+
+}  // namespace asuca

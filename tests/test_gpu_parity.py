@@ -208,3 +208,42 @@ def test_large_1024x1024x58_one_step_sampled_columns(asuca, large_case, prec, to
         got = st.fields()[:, :, jj][:, :, :, ii].double().cpu().numpy()
         _assert_fields(got, ref, tol, f"large prec={prec} window {(i0, j0)}", both=(prec == 0))
     del st
+
+
+# ------------------------------------------------------------------ arithmetic helpers
+
+def test_integer_pipe_conversions_match_hardware(asuca):
+    """The column solve widens floats and narrows doubles through the IEEE-754
+    bit fields; the results must equal CUDA's own conversions bit for bit,
+    including ties, the float range limits, zeros, subnormals, inf and NaN."""
+    import torch
+    rng = np.random.default_rng(8)
+    f = rng.standard_normal(200000).astype(np.float32) * (10.0 ** rng.uniform(-30, 30, 200000)).astype(np.float32)
+    specials_f = np.array([0.0, -0.0, 1e-45, -1e-40, 1.17549435e-38, 3.4028235e38, np.inf, -np.inf, np.nan],
+                          dtype=np.float32)
+    f = np.concatenate([f, specials_f])
+    d = rng.standard_normal(200000) * 10.0 ** rng.uniform(-50, 50, 200000)
+    base = rng.standard_normal(20000).astype(np.float32).astype(np.float64)
+    ulp = np.abs(np.spacing(base.astype(np.float32)).astype(np.float64))
+    ties = np.concatenate([base + ulp / 2, base - ulp / 2, base + ulp / 2 * (1 + 2 ** -30)])
+    specials_d = np.array([0.0, -0.0, 1e-320, 1.1754942e-38, 1.17549435e-38, 3.4028234663852886e38,
+                           3.4028235677973366e38, 3.5e38, -3.5e38, 1e300, np.inf, -np.inf, np.nan])
+    d = np.concatenate([d, ties, specials_d])
+    n = max(len(f), len(d))
+    f = np.resize(f, n)
+    d = np.resize(d, n)
+    tf = torch.tensor(f, device="cuda")
+    td = torch.tensor(d, device="cuda")
+    w, nr, r = asuca.debug_numerics(tf, td)
+    torch.cuda.synchronize()
+    hw_w = tf.double()
+    hw_n = td.float()
+    same_w = (w.view(torch.int64) == hw_w.view(torch.int64)) | (torch.isnan(w) & torch.isnan(hw_w))
+    same_n = (nr.view(torch.int32) == hw_n.view(torch.int32)) | (torch.isnan(nr) & torch.isnan(hw_n))
+    assert bool(same_w.all()) and bool(same_n.all())
+    # Newton reciprocal within 2 ulp of the correctly rounded 1/x on the normal range
+    x = torch.tensor(rng.uniform(1e-3, 1e6, 100000) * rng.choice([-1, 1], 100000), device="cuda")
+    _, _, r = asuca.debug_numerics(torch.zeros(len(x), dtype=torch.float32, device="cuda"), x)
+    exact = 1.0 / x
+    ulps = ((r - exact).abs() / torch.abs(exact) / 2.0 ** -52).max().item()
+    assert ulps <= 2.0, ulps
