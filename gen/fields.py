@@ -159,7 +159,8 @@ def _winds_from_psi(psi, dx, dy):
 
 def make_case(nx: int, ny: int, nz: int, ntracers: int, seed: int, *,
               overturning: bool = True, pattern_seed: int | None = None,
-              perturb_seed: int | None = None, dtype=np.float64) -> Case:
+              perturb_seed: int | None = None, smooth_tracers: bool = False,
+              dtype=np.float64) -> Case:
     """Build one seeded case.
 
     pattern_seed draws the bubble/blob/mode parameters (domain-relative, so
@@ -186,6 +187,22 @@ def make_case(nx: int, ny: int, nz: int, ntracers: int, seed: int, *,
         for b in range(4):
             np.maximum(acc, a[b] * _gauss_sep(nx, ny, nz, dx, dy, zc, H, c[b]), out=acc)
         q[n] = 0.02 * acc
+
+    if smooth_tracers and ntracers > 0:
+        srng = np.random.default_rng(seed + 77)
+        x = (np.arange(nx) + 0.5) / nx
+        y = (np.arange(ny) + 0.5) / ny
+        zz = zc / H
+        for n in range(ntracers):
+            acc = np.zeros((nz, ny, nx))
+            for _ in range(3):
+                kx, ky = int(srng.integers(1, 3)), int(srng.integers(1, 3))
+                kz = srng.uniform(0.5, 1.5)
+                ph = srng.uniform(0, 2 * math.pi, 3)
+                acc += (np.sin(2 * math.pi * kx * x + ph[0])[None, None, :] *
+                        np.sin(2 * math.pi * ky * y + ph[1])[None, :, None] *
+                        np.sin(math.pi * kz * zz + ph[2])[:, None, None])
+            q[n] = 0.0125 + 0.0075 * acc / 3.0
 
     psi = _streamfunction(nx, ny, dx, dy, pat["modes"])
     u, v = _winds_from_psi(psi, dx, dy)

@@ -207,3 +207,100 @@ def set_threads(n: int):
 
 def get_threads() -> int:
     return lib().orc_get_threads()
+
+
+# ---------------------------------------------------------------- tangent-linear / adjoint
+
+def _sig_tl():
+    L = lib()
+    if not getattr(L, "_tl_ready", False):
+        G = ctypes.POINTER(OrcGrid)
+        L.orc_rhs_tl.argtypes = [G, _D, _D, _D, _D, _D, _D, _D, _D, _D]
+        L.orc_rhs_adj.argtypes = [G, _D, _D, _D, _D, _D, _D, _D, _D, _D]
+        L.orc_column_tl.argtypes = [G, _D, _D, ctypes.c_double, _D]
+        L.orc_column_adj.argtypes = [G, _D, _D, ctypes.c_double]
+        L.orc_step_tl.argtypes = [G, _D, _D, _D, _D, _D, ctypes.c_double, ctypes.c_int, _D, _D, _D, _D, _D]
+        L.orc_step_adj.argtypes = [G, _D, _D, _D, _D, _D, ctypes.c_double, ctypes.c_int, _D, _D, _D, _D, _D]
+        L.orc_trajectory_branches.argtypes = [G, _D, _D, _D, _D, _D, ctypes.c_double, ctypes.c_int, _U8]
+        L._tl_ready = True
+    return L
+
+
+def rhs_tl(g: Grid, Y, mu, mv, mw, dY, dmu=None, dmv=None, dmw=None):
+    L = _sig_tl()
+    Y, mu, mv, mw, dY = map(_f64, (Y, mu, mv, mw, dY))
+    dm = [None if a is None else _f64(a) for a in (dmu, dmv, dmw)]
+    out = np.empty(g.shape)
+    L.orc_rhs_tl(g.ref, _p(Y), _p(mu), _p(mv), _p(mw), _p(dY), _p(dm[0]), _p(dm[1]), _p(dm[2]), _p(out))
+    return out
+
+
+def rhs_adj(g: Grid, Y, mu, mv, mw, lamR):
+    """((dR/dY)^T lamR, (dR/dMU)^T lamR, (dR/dMV)^T lamR, (dR/dMW)^T lamR)"""
+    L = _sig_tl()
+    Y, mu, mv, mw, lamR = map(_f64, (Y, mu, mv, mw, lamR))
+    lY = np.zeros(g.shape)
+    gmu, gmv, gmw = np.zeros_like(mu), np.zeros_like(mv), np.zeros_like(mw)
+    L.orc_rhs_adj(g.ref, _p(Y), _p(mu), _p(mv), _p(mw), _p(lamR), _p(lY), _p(gmu), _p(gmv), _p(gmw))
+    return lY, gmu, gmv, gmw
+
+
+def column_tl(g: Grid, Y3, dY3, dt):
+    L = _sig_tl()
+    out = np.empty(g.shape)
+    L.orc_column_tl(g.ref, _p(_f64(Y3)), _p(_f64(dY3)), dt, _p(out))
+    return out
+
+
+def column_adj(g: Grid, Y3, lam, dt):
+    L = _sig_tl()
+    lam = _f64(lam).copy()
+    L.orc_column_adj(g.ref, _p(_f64(Y3)), _p(lam), dt)
+    return lam
+
+
+def step_tl(g: Grid, Y0, mu, mv, mw, dt, nsteps, dY0, dmu=None, dmv=None, dmw=None, tend=None):
+    L = _sig_tl()
+    Y0, mu, mv, mw, dY0 = map(_f64, (Y0, mu, mv, mw, dY0))
+    dm = [None if a is None else _f64(a) for a in (dmu, dmv, dmw)]
+    tend = None if tend is None else _f64(tend)
+    out = np.empty(g.shape)
+    L.orc_step_tl(g.ref, _p(Y0), _p(mu), _p(mv), _p(mw), _p(tend), dt, nsteps, _p(dY0),
+                  _p(dm[0]), _p(dm[1]), _p(dm[2]), _p(out))
+    return out
+
+
+def step_adj(g: Grid, Y0, mu, mv, mw, dt, nsteps, lam_final, tend=None):
+    """adjoint of nsteps steps: (lam0 [F][nz][ny][nx], g_mu, g_mv, g_mw)"""
+    L = _sig_tl()
+    Y0, mu, mv, mw, lam_final = map(_f64, (Y0, mu, mv, mw, lam_final))
+    tend = None if tend is None else _f64(tend)
+    lam0 = np.empty(g.shape)
+    gmu, gmv, gmw = np.empty_like(mu), np.empty_like(mv), np.empty_like(mw)
+    L.orc_step_adj(g.ref, _p(Y0), _p(mu), _p(mv), _p(mw), _p(tend), dt, nsteps, _p(lam_final),
+                   _p(lam0), _p(gmu), _p(gmv), _p(gmw))
+    return lam0, gmu, gmv, gmw
+
+
+def trajectory_branches(g: Grid, Y0, mu, mv, mw, dt, nsteps, tend=None):
+    """limiter branch bytes of every face of every stage of nsteps steps"""
+    L = _sig_tl()
+    Y0, mu, mv, mw = map(_f64, (Y0, mu, mv, mw))
+    tend = None if tend is None else _f64(tend)
+    out = np.zeros((max(nsteps, 1), 3) + g.shape, dtype=np.uint8)
+    L.orc_trajectory_branches(g.ref, _p(Y0), _p(mu), _p(mv), _p(mw), _p(tend), dt, nsteps,
+                              out.ctypes.data_as(_U8))
+    return out
+
+
+def tracer_cost(g: Grid, Y, q_target):
+    """J = 1/2 sum over cells and tracers of (q_n - q_target_n)^2, q = rho q / rho,
+    and its gradient with respect to Y (all F fields)."""
+    Y = _f64(Y)
+    q = Y[2:] / Y[0]
+    r = q - q_target
+    J = 0.5 * float(np.sum(r * r))
+    lam = np.zeros(g.shape)
+    lam[2:] = r / Y[0]
+    lam[0] = -np.sum(r * q, axis=0) / Y[0]
+    return J, lam

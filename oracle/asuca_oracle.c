@@ -439,3 +439,503 @@ int orc_step_window(const orc_grid *g, const double *Y, const double *mu, const 
     free(P);
     return 0;
 }
+
+/* ====================================================================
+ * Tangent-linear and adjoint of the discrete step (FP64, plain).
+ *
+ * Differentiated map: Y^{n+1} = Col(Y3), Y3 from the three RK stages of
+ * Y^n with mass fluxes M = (mu, mv, mw) treated as independent inputs (the
+ * vertical flux is not re-derived from continuity); tendencies are constant.
+ * Limiter branches are frozen at the values the forward pass takes: with a
+ * fixed branch the limiter increment is linear, L = a d0 + b d1 with
+ * (a, b) = (0,0) zero, (0,2) "2r", (1/3,2/3) "kappa=1/3", (2,0) "cap 2".
+ * ==================================================================== */
+
+static void branch_ab(int br, double *a, double *b) {
+    switch (br) {
+        case 1: *a = 0.0; *b = 2.0; break;
+        case 2: *a = 1.0 / 3.0; *b = 2.0 / 3.0; break;
+        case 3: *a = 2.0; *b = 0.0; break;
+        default: *a = 0.0; *b = 0.0; break;
+    }
+}
+
+/* d face / d (pm1, p0, p1, p2) for the branch taken at this face */
+static void face_coefs(double pm1, double p0, double p1, double p2, double m, int lim, double c[4]) {
+    int br;
+    (void)orc_face(pm1, p0, p1, p2, m, lim, &br);
+    double a, b;
+    branch_ab(br, &a, &b);
+    if (m >= 0.0) {   /* face = p0 + (a (p0 - pm1) + b (p1 - p0)) / 2 */
+        c[0] = -0.5 * a; c[1] = 1.0 + 0.5 * a - 0.5 * b; c[2] = 0.5 * b; c[3] = 0.0;
+    } else {          /* face = p1 + (a (p1 - p2) + b (p0 - p1)) / 2 */
+        c[0] = 0.0; c[1] = 0.5 * b; c[2] = 1.0 + 0.5 * a - 0.5 * b; c[3] = -0.5 * a;
+    }
+}
+
+/* cell indices (global, periodic in i/j, clamped in k) of the 4-cell stencil of
+ * face "a+1/2" of cell a = (i, j, k) in direction dir */
+static void face_stencil(const orc_grid *g, int dir, int k, int j, int i, size_t idx[4], int kk[4]) {
+    for (int q = 0; q < 4; q++) {
+        int o = q - 1;
+        int ii = i, jj = j, kq = k;
+        if (dir == 0) ii = i + o;
+        else if (dir == 1) jj = j + o;
+        else {
+            kq = k + o;
+            if (kq < 0) kq = 0;
+            if (kq > g->nz - 1) kq = g->nz - 1;
+        }
+        kk[q] = kq;
+        idx[q] = gidx(g, kq, jj, ii);
+    }
+}
+
+static size_t mface_index(const orc_grid *g, int dir, int k, int j, int i) {
+    return dir == 2 ? gidx(g, k + 1, j, i) : gidx(g, k, j, i);
+}
+
+static const double *mface_array(int dir, const double *mu, const double *mv, const double *mw) {
+    return dir == 0 ? mu : (dir == 1 ? mv : mw);
+}
+
+static double rdelta(const orc_grid *g, int dir, int k) {
+    return dir == 0 ? 1.0 / g->dx : (dir == 1 ? 1.0 / g->dy : 1.0 / g->dz[k]);
+}
+
+/* dR = d/dY R(Y; M)[dY] + d/dM R(Y; M)[dM]  (dM may be NULL) */
+void orc_rhs_tl(const orc_grid *g, const double *Y, const double *mu, const double *mv,
+                const double *mw, const double *dY, const double *dmu, const double *dmv,
+                const double *dmw, double *dR) {
+    const int F = 2 + g->ntr, nz = g->nz;
+    const size_t C = (size_t)nz * g->ny * g->nx;
+    memset(dR, 0, (size_t)F * C * sizeof(double));
+    for (int dir = 0; dir < 3; dir++) {
+        const double *M = mface_array(dir, mu, mv, mw);
+        const double *dM = dmu ? mface_array(dir, dmu, dmv, dmw) : NULL;
+        for (int k = 0; k < nz; k++) {
+            if (dir == 2 && k >= nz - 1) continue;          /* lids carry no flux */
+            for (int j = 0; j < g->ny; j++)
+                for (int i = 0; i < g->nx; i++) {
+                    const size_t fm = mface_index(g, dir, k, j, i);
+                    const double m = M[fm], dm = dM ? dM[fm] : 0.0;
+                    size_t a = gidx(g, k, j, i);
+                    size_t b = dir == 0 ? gidx(g, k, j, i + 1) : (dir == 1 ? gidx(g, k, j + 1, i) : gidx(g, k + 1, j, i));
+                    const int kb = dir == 2 ? k + 1 : k;
+                    size_t st[4];
+                    int kk[4];
+                    face_stencil(g, dir, k, j, i, st, kk);
+                    for (int f = 0; f < F; f++) {
+                        double dF;
+                        if (f == 0) {
+                            dF = dm;
+                        } else {
+                            double ph[4], dph[4], c[4];
+                            for (int q = 0; q < 4; q++) {
+                                double rho = Y[st[q]], rp = Y[(size_t)f * C + st[q]];
+                                ph[q] = rp / rho;
+                                dph[q] = (dY[(size_t)f * C + st[q]] - ph[q] * dY[st[q]]) / rho;
+                            }
+                            face_coefs(ph[0], ph[1], ph[2], ph[3], m, g->lim, c);
+                            double face = orc_face(ph[0], ph[1], ph[2], ph[3], m, g->lim, NULL);
+                            double dface = c[0] * dph[0] + c[1] * dph[1] + c[2] * dph[2] + c[3] * dph[3];
+                            dF = dm * face + m * dface;
+                        }
+                        dR[(size_t)f * C + a] -= dF * rdelta(g, dir, k);
+                        dR[(size_t)f * C + b] += dF * rdelta(g, dir, kb);
+                    }
+                }
+        }
+    }
+}
+
+/* lamY += (dR/dY)^T mu,  gM += (dR/dM)^T mu   (gM arrays may be NULL) */
+void orc_rhs_adj(const orc_grid *g, const double *Y, const double *mu, const double *mv,
+                 const double *mw, const double *lamR, double *lamY, double *gmu, double *gmv,
+                 double *gmw) {
+    const int F = 2 + g->ntr, nz = g->nz;
+    const size_t C = (size_t)nz * g->ny * g->nx;
+    for (int dir = 0; dir < 3; dir++) {
+        const double *M = mface_array(dir, mu, mv, mw);
+        double *gM = gmu ? (dir == 0 ? gmu : (dir == 1 ? gmv : gmw)) : NULL;
+        for (int k = 0; k < nz; k++) {
+            if (dir == 2 && k >= nz - 1) continue;
+            for (int j = 0; j < g->ny; j++)
+                for (int i = 0; i < g->nx; i++) {
+                    const size_t fm = mface_index(g, dir, k, j, i);
+                    const double m = M[fm];
+                    size_t a = gidx(g, k, j, i);
+                    size_t b = dir == 0 ? gidx(g, k, j, i + 1) : (dir == 1 ? gidx(g, k, j + 1, i) : gidx(g, k + 1, j, i));
+                    const int kb = dir == 2 ? k + 1 : k;
+                    size_t st[4];
+                    int kk[4];
+                    face_stencil(g, dir, k, j, i, st, kk);
+                    for (int f = 0; f < F; f++) {
+                        /* adjoint of the flux through this face */
+                        const double lF = lamR[(size_t)f * C + b] * rdelta(g, dir, kb) -
+                                          lamR[(size_t)f * C + a] * rdelta(g, dir, k);
+                        if (f == 0) {
+                            if (gM) gM[fm] += lF;
+                            continue;
+                        }
+                        double ph[4], c[4];
+                        for (int q = 0; q < 4; q++) ph[q] = Y[(size_t)f * C + st[q]] / Y[st[q]];
+                        face_coefs(ph[0], ph[1], ph[2], ph[3], m, g->lim, c);
+                        double face = orc_face(ph[0], ph[1], ph[2], ph[3], m, g->lim, NULL);
+                        if (gM) gM[fm] += lF * face;
+                        for (int q = 0; q < 4; q++) {
+                            const double lph = lF * m * c[q];         /* adjoint of phi at stencil cell q */
+                            const double rho = Y[st[q]];
+                            lamY[(size_t)f * C + st[q]] += lph / rho;
+                            lamY[st[q]] -= lph * ph[q] / rho;
+                        }
+                    }
+                }
+        }
+    }
+}
+
+/* forward column pass of one column, keeping the intermediates the
+ * derivatives need: Ya (after relaxation), Yb (after sedimentation),
+ * phi[f][k] (diffusion solution, f >= 1) and the face weights gf[k] */
+typedef struct {
+    double *Ya, *Yb, *phi, *gf, *kcf;
+} colwork;
+
+static void col_forward(const orc_grid *g, const double *Y3, double dt, const double *zf,
+                        const double *zc, colwork *w) {
+    const int nz = g->nz, F = 2 + g->ntr;
+    /* Y3, Ya, Yb are [F][nz] for one column */
+    memcpy(w->Ya, Y3, (size_t)F * nz * sizeof(double));
+    if (g->tau > 0.0) {
+        double r = dt / g->tau;
+        for (int k = 0; k < nz; k++) {
+            double rho = w->Ya[k];
+            double th = w->Ya[nz + k] / rho;
+            th = (th + r * (THETA_REF0 + THETA_REF_LAPSE * zc[k])) / (1.0 + r);
+            w->Ya[nz + k] = rho * th;
+        }
+    }
+    memcpy(w->Yb, w->Ya, (size_t)F * nz * sizeof(double));
+    if (g->vsed > 0.0 && g->sed >= 0 && g->sed < g->ntr) {
+        double *q = w->Yb + (size_t)(2 + g->sed) * nz;
+        double P = 0.0;
+        for (int k = nz - 1; k >= 0; k--) {
+            q[k] = (q[k] * g->dz[k] + dt * P) / (g->dz[k] + dt * g->vsed);
+            P = g->vsed * q[k];
+        }
+    }
+    for (int k = 0; k <= nz; k++) { w->gf[k] = 0.0; w->kcf[k] = 0.0; }
+    if (g->k0 > 0.0 && nz >= 2) {
+        for (int k = 0; k < nz - 1; k++) {
+            double K = g->k0 * exp(-zf[k + 1] / g->kh);
+            w->kcf[k + 1] = 0.5 * dt * K / (zc[k + 1] - zc[k]);    /* d g_{k+1/2} / d rho_k */
+            w->gf[k + 1] = dt * 0.5 * (w->Yb[k] + w->Yb[k + 1]) * K / (zc[k + 1] - zc[k]);
+        }
+        double *a = (double *)malloc((size_t)nz * sizeof(double));
+        double *b = (double *)malloc((size_t)nz * sizeof(double));
+        double *c = (double *)malloc((size_t)nz * sizeof(double));
+        double *d = (double *)malloc((size_t)nz * sizeof(double));
+        for (int k = 0; k < nz; k++) {
+            a[k] = -w->gf[k];
+            c[k] = -w->gf[k + 1];
+            b[k] = w->Yb[k] * g->dz[k] + w->gf[k] + w->gf[k + 1];
+        }
+        for (int f = 1; f < F; f++) {
+            for (int k = 0; k < nz; k++) d[k] = g->dz[k] * w->Yb[(size_t)f * nz + k];
+            orc_thomas(nz, a, b, c, d, w->phi + (size_t)f * nz);
+        }
+        free(a); free(b); free(c); free(d);
+    }
+}
+
+static void col_matrix(const orc_grid *g, const colwork *w, double *a, double *b, double *c) {
+    for (int k = 0; k < g->nz; k++) {
+        a[k] = -w->gf[k];
+        c[k] = -w->gf[k + 1];
+        b[k] = w->Yb[k] * g->dz[k] + w->gf[k] + w->gf[k + 1];
+    }
+}
+
+/* tangent of the column pass of one column: dY3 -> dOut ([F][nz]) */
+static void col_tl(const orc_grid *g, const double *Y3, const double *dY3, double dt,
+                   const double *zf, const double *zc, colwork *w, double *dOut) {
+    const int nz = g->nz, F = 2 + g->ntr;
+    col_forward(g, Y3, dt, zf, zc, w);
+    double *dA = (double *)malloc((size_t)F * nz * sizeof(double));
+    memcpy(dA, dY3, (size_t)F * nz * sizeof(double));
+    if (g->tau > 0.0) {   /* rho theta_a = (rho theta + r rho theta_ref) / (1 + r) */
+        double r = dt / g->tau;
+        for (int k = 0; k < nz; k++)
+            dA[nz + k] = (dY3[nz + k] + r * (THETA_REF0 + THETA_REF_LAPSE * zc[k]) * dY3[k]) / (1.0 + r);
+    }
+    if (g->vsed > 0.0 && g->sed >= 0 && g->sed < g->ntr) {
+        double *dq = dA + (size_t)(2 + g->sed) * nz;
+        double dP = 0.0;
+        for (int k = nz - 1; k >= 0; k--) {
+            dq[k] = (dq[k] * g->dz[k] + dt * dP) / (g->dz[k] + dt * g->vsed);
+            dP = g->vsed * dq[k];
+        }
+    }
+    memcpy(dOut, dA, (size_t)F * nz * sizeof(double));
+    if (g->k0 > 0.0 && nz >= 2) {
+        /* u = rho phi, A(rho) phi = dz x  =>  A dphi = dz dx - dA phi,  du = drho phi + rho dphi */
+        double *a = (double *)malloc((size_t)nz * sizeof(double));
+        double *b = (double *)malloc((size_t)nz * sizeof(double));
+        double *c = (double *)malloc((size_t)nz * sizeof(double));
+        double *d = (double *)malloc((size_t)nz * sizeof(double));
+        double *x = (double *)malloc((size_t)nz * sizeof(double));
+        col_matrix(g, w, a, b, c);
+        const double *drho = dA;
+        for (int f = 1; f < F; f++) {
+            const double *ph = w->phi + (size_t)f * nz;
+            for (int k = 0; k < nz; k++) {
+                /* (dA phi)_k = drho_k dz_k phi_k + sum over faces of dg (phi_k - phi_other) */
+                double dAp = drho[k] * g->dz[k] * ph[k];
+                if (k > 0) dAp += w->kcf[k] * (drho[k - 1] + drho[k]) * (ph[k] - ph[k - 1]);
+                if (k < nz - 1) dAp += w->kcf[k + 1] * (drho[k] + drho[k + 1]) * (ph[k] - ph[k + 1]);
+                d[k] = g->dz[k] * dA[(size_t)f * nz + k] - dAp;
+            }
+            orc_thomas(nz, a, b, c, d, x);
+            for (int k = 0; k < nz; k++) dOut[(size_t)f * nz + k] = drho[k] * ph[k] + w->Yb[k] * x[k];
+        }
+        free(a); free(b); free(c); free(d); free(x);
+    }
+    free(dA);
+}
+
+/* adjoint of the column pass of one column: lam ([F][nz]) in: adjoint of
+ * the output; out: adjoint of Y3 */
+static void col_adj(const orc_grid *g, const double *Y3, double *lam, double dt, const double *zf,
+                    const double *zc, colwork *w) {
+    const int nz = g->nz, F = 2 + g->ntr;
+    col_forward(g, Y3, dt, zf, zc, w);
+    if (g->k0 > 0.0 && nz >= 2) {
+        double *a = (double *)malloc((size_t)nz * sizeof(double));
+        double *b = (double *)malloc((size_t)nz * sizeof(double));
+        double *c = (double *)malloc((size_t)nz * sizeof(double));
+        double *d = (double *)malloc((size_t)nz * sizeof(double));
+        double *psi = (double *)malloc((size_t)nz * sizeof(double));
+        col_matrix(g, w, a, b, c);   /* A is symmetric: A^T = A */
+        for (int f = 1; f < F; f++) {
+            const double *ph = w->phi + (size_t)f * nz;
+            double *lu = lam + (size_t)f * nz;
+            for (int k = 0; k < nz; k++) d[k] = w->Yb[k] * lu[k];
+            orc_thomas(nz, a, b, c, d, psi);
+            for (int k = 0; k < nz; k++) {
+                double lr = lu[k] * ph[k] - g->dz[k] * psi[k] * ph[k];
+                if (k > 0) lr -= w->kcf[k] * (psi[k] - psi[k - 1]) * (ph[k] - ph[k - 1]);
+                if (k < nz - 1) lr -= w->kcf[k + 1] * (psi[k] - psi[k + 1]) * (ph[k] - ph[k + 1]);
+                lam[k] += lr;
+            }
+            for (int k = 0; k < nz; k++) lu[k] = g->dz[k] * psi[k];
+        }
+        free(a); free(b); free(c); free(d); free(psi);
+    }
+    if (g->vsed > 0.0 && g->sed >= 0 && g->sed < g->ntr) {
+        /* q'_k = (q_k dz_k + dt v q'_{k+1}) w_k, w_k = 1/(dz_k + dt v): the adjoint runs bottom-up */
+        double *lq = lam + (size_t)(2 + g->sed) * nz;
+        double nu_prev = 0.0;
+        for (int k = 0; k < nz; k++) {
+            double nu = lq[k];
+            if (k > 0) nu += dt * g->vsed / (g->dz[k - 1] + dt * g->vsed) * nu_prev;
+            nu_prev = nu;
+            lq[k] = nu * g->dz[k] / (g->dz[k] + dt * g->vsed);
+        }
+    }
+    if (g->tau > 0.0) {
+        double r = dt / g->tau;
+        for (int k = 0; k < nz; k++) {
+            double lt = lam[nz + k];
+            lam[k] += lt * r * (THETA_REF0 + THETA_REF_LAPSE * zc[k]) / (1.0 + r);
+            lam[nz + k] = lt / (1.0 + r);
+        }
+    }
+}
+
+static void col_alloc(const orc_grid *g, colwork *w) {
+    size_t n = (size_t)(2 + g->ntr) * g->nz;
+    w->Ya = (double *)calloc(n, sizeof(double));
+    w->Yb = (double *)calloc(n, sizeof(double));
+    w->phi = (double *)calloc(n, sizeof(double));
+    w->gf = (double *)calloc((size_t)g->nz + 1, sizeof(double));
+    w->kcf = (double *)calloc((size_t)g->nz + 1, sizeof(double));
+}
+
+static void col_free(colwork *w) {
+    free(w->Ya); free(w->Yb); free(w->phi); free(w->gf); free(w->kcf);
+}
+
+static void gather_col(const orc_grid *g, const double *Y, int j, int i, double *out) {
+    const size_t C = (size_t)g->nz * g->ny * g->nx;
+    for (int f = 0; f < 2 + g->ntr; f++)
+        for (int k = 0; k < g->nz; k++) out[(size_t)f * g->nz + k] = Y[(size_t)f * C + gidx(g, k, j, i)];
+}
+
+static void scatter_col(const orc_grid *g, double *Y, int j, int i, const double *in) {
+    const size_t C = (size_t)g->nz * g->ny * g->nx;
+    for (int f = 0; f < 2 + g->ntr; f++)
+        for (int k = 0; k < g->nz; k++) Y[(size_t)f * C + gidx(g, k, j, i)] = in[(size_t)f * g->nz + k];
+}
+
+void orc_column_tl(const orc_grid *g, const double *Y3, const double *dY3, double dt, double *dOut) {
+    const int nz = g->nz, F = 2 + g->ntr;
+    double *zf = (double *)malloc((size_t)(nz + 1) * sizeof(double));
+    double *zc = (double *)malloc((size_t)nz * sizeof(double));
+    level_heights(g, zf, zc);
+    colwork w;
+    col_alloc(g, &w);
+    double *y = (double *)malloc((size_t)F * nz * sizeof(double));
+    double *dy = (double *)malloc((size_t)F * nz * sizeof(double));
+    double *o = (double *)malloc((size_t)F * nz * sizeof(double));
+    for (int j = 0; j < g->ny; j++)
+        for (int i = 0; i < g->nx; i++) {
+            gather_col(g, Y3, j, i, y);
+            gather_col(g, dY3, j, i, dy);
+            col_tl(g, y, dy, dt, zf, zc, &w, o);
+            scatter_col(g, dOut, j, i, o);
+        }
+    free(y); free(dy); free(o); col_free(&w); free(zf); free(zc);
+}
+
+void orc_column_adj(const orc_grid *g, const double *Y3, double *lam, double dt) {
+    const int nz = g->nz, F = 2 + g->ntr;
+    double *zf = (double *)malloc((size_t)(nz + 1) * sizeof(double));
+    double *zc = (double *)malloc((size_t)nz * sizeof(double));
+    level_heights(g, zf, zc);
+    colwork w;
+    col_alloc(g, &w);
+    double *y = (double *)malloc((size_t)F * nz * sizeof(double));
+    double *l = (double *)malloc((size_t)F * nz * sizeof(double));
+    for (int j = 0; j < g->ny; j++)
+        for (int i = 0; i < g->nx; i++) {
+            gather_col(g, Y3, j, i, y);
+            gather_col(g, lam, j, i, l);
+            col_adj(g, y, l, dt, zf, zc, &w);
+            scatter_col(g, lam, j, i, l);
+        }
+    free(y); free(l); col_free(&w); free(zf); free(zc);
+}
+
+/* states of one forward step: Yn (input), Y1, Y2 (stage states), Y3 (before the column pass) */
+static void step_states(const orc_grid *g, const double *Yn, const double *mu, const double *mv,
+                        const double *mw, const double *tend, double dt, double *Y1, double *Y2,
+                        double *Y3, double *Ynext) {
+    const size_t n = (size_t)(2 + g->ntr) * g->nz * g->ny * g->nx;
+    double *R = (double *)malloc(n * sizeof(double));
+    const double c[3] = {dt / 3.0, dt / 2.0, dt};
+    double *outs[3] = {Y1, Y2, Y3};
+    const double *in = Yn;
+    for (int s = 0; s < 3; s++) {
+        orc_rhs(g, in, mu, mv, mw, tend, R, NULL);
+        for (size_t q = 0; q < n; q++) outs[s][q] = Yn[q] + c[s] * R[q];
+        in = outs[s];
+    }
+    memcpy(Ynext, Y3, n * sizeof(double));
+    orc_column(g, Ynext, dt, NULL);
+    free(R);
+}
+
+/* tangent of nsteps steps: (dY0, dM) -> dYn */
+void orc_step_tl(const orc_grid *g, const double *Y0, const double *mu, const double *mv,
+                 const double *mw, const double *tend, double dt, int nsteps, const double *dY0,
+                 const double *dmu, const double *dmv, const double *dmw, double *dYn) {
+    const size_t n = (size_t)(2 + g->ntr) * g->nz * g->ny * g->nx;
+    double *Y = (double *)malloc(n * sizeof(double));
+    double *Y1 = (double *)malloc(n * sizeof(double));
+    double *Y2 = (double *)malloc(n * sizeof(double));
+    double *Y3 = (double *)malloc(n * sizeof(double));
+    double *Yx = (double *)malloc(n * sizeof(double));
+    double *dY = (double *)malloc(n * sizeof(double));
+    double *dS = (double *)malloc(n * sizeof(double));
+    double *dR = (double *)malloc(n * sizeof(double));
+    const double c[3] = {dt / 3.0, dt / 2.0, dt};
+    memcpy(Y, Y0, n * sizeof(double));
+    memcpy(dY, dY0, n * sizeof(double));
+    for (int s = 0; s < nsteps; s++) {
+        step_states(g, Y, mu, mv, mw, tend, dt, Y1, Y2, Y3, Yx);
+        const double *st[3] = {Y, Y1, Y2};
+        memcpy(dS, dY, n * sizeof(double));              /* tangent of the stage input */
+        for (int q = 0; q < 3; q++) {
+            orc_rhs_tl(g, st[q], mu, mv, mw, dS, dmu, dmv, dmw, dR);
+            for (size_t e = 0; e < n; e++) dS[e] = dY[e] + c[q] * dR[e];
+        }
+        orc_column_tl(g, Y3, dS, dt, dY);
+        memcpy(Y, Yx, n * sizeof(double));
+    }
+    memcpy(dYn, dY, n * sizeof(double));
+    free(Y); free(Y1); free(Y2); free(Y3); free(Yx); free(dY); free(dS); free(dR);
+}
+
+/* adjoint of nsteps steps: lam_final -> lam0 (adjoint of Y0), g_mu/g_mv/g_mw
+ * (adjoint of the mass fluxes; overwritten).  The whole trajectory is kept. */
+void orc_step_adj(const orc_grid *g, const double *Y0, const double *mu, const double *mv,
+                  const double *mw, const double *tend, double dt, int nsteps,
+                  const double *lam_final, double *lam0, double *gmu, double *gmv, double *gmw) {
+    const size_t C = (size_t)g->nz * g->ny * g->nx;
+    const size_t n = (size_t)(2 + g->ntr) * C;
+    const size_t nw = (size_t)(g->nz + 1) * g->ny * g->nx;
+    double *traj = (double *)malloc((size_t)(nsteps + 1) * 3 * n * sizeof(double) + 1);
+    /* per step s: [Y^s, Y1, Y2] at traj + 3 n s, Y3 kept at the next slot's ... */
+    double *Y3s = (double *)malloc((size_t)(nsteps > 0 ? nsteps : 1) * n * sizeof(double));
+    memcpy(traj, Y0, n * sizeof(double));
+    for (int s = 0; s < nsteps; s++) {
+        double *Ys = traj + (size_t)3 * n * s;
+        step_states(g, Ys, mu, mv, mw, tend, dt, Ys + n, Ys + 2 * n, Y3s + (size_t)s * n,
+                    traj + (size_t)3 * n * (s + 1));
+    }
+    memset(gmu, 0, C * sizeof(double));
+    memset(gmv, 0, C * sizeof(double));
+    memset(gmw, 0, nw * sizeof(double));
+    double *lam = (double *)malloc(n * sizeof(double));
+    double *l2 = (double *)malloc(n * sizeof(double));
+    double *l1 = (double *)malloc(n * sizeof(double));
+    double *mu_r = (double *)malloc(n * sizeof(double));
+    const double c[3] = {dt / 3.0, dt / 2.0, dt};
+    memcpy(lam, lam_final, n * sizeof(double));
+    for (int s = nsteps - 1; s >= 0; s--) {
+        const double *Ys = traj + (size_t)3 * n * s;
+        orc_column_adj(g, Y3s + (size_t)s * n, lam, dt);          /* lam: adjoint of Y3 */
+        /* Y3 = Yn + c3 R(Y2) */
+        for (size_t e = 0; e < n; e++) { mu_r[e] = c[2] * lam[e]; l2[e] = 0.0; }
+        orc_rhs_adj(g, Ys + 2 * n, mu, mv, mw, mu_r, l2, gmu, gmv, gmw);
+        /* Y2 = Yn + c2 R(Y1) */
+        for (size_t e = 0; e < n; e++) { mu_r[e] = c[1] * l2[e]; l1[e] = 0.0; }
+        orc_rhs_adj(g, Ys + n, mu, mv, mw, mu_r, l1, gmu, gmv, gmw);
+        /* Y1 = Yn + c1 R(Yn) */
+        for (size_t e = 0; e < n; e++) { lam[e] += l2[e] + l1[e]; mu_r[e] = c[0] * l1[e]; }
+        orc_rhs_adj(g, Ys, mu, mv, mw, mu_r, lam, gmu, gmv, gmw);
+    }
+    memcpy(lam0, lam, n * sizeof(double));
+    free(traj); free(Y3s); free(lam); free(l2); free(l1); free(mu_r);
+}
+
+/* limiter branches of every face of every stage of nsteps steps:
+ * out[(step * 3 + stage) * F * C + f * C + cell] (2 bits per direction) */
+void orc_trajectory_branches(const orc_grid *g, const double *Y0, const double *mu,
+                             const double *mv, const double *mw, const double *tend, double dt,
+                             int nsteps, unsigned char *out) {
+    const size_t n = (size_t)(2 + g->ntr) * g->nz * g->ny * g->nx;
+    double *Y = (double *)malloc(n * sizeof(double));
+    double *S = (double *)malloc(n * sizeof(double));
+    double *R = (double *)malloc(n * sizeof(double));
+    const double c[3] = {dt / 3.0, dt / 2.0, dt};
+    memcpy(Y, Y0, n * sizeof(double));
+    for (int s = 0; s < nsteps; s++) {
+        const double *in = Y;
+        for (int q = 0; q < 3; q++) {
+            orc_rhs(g, in, mu, mv, mw, tend, R, out + ((size_t)s * 3 + q) * n);
+            for (size_t e = 0; e < n; e++) S[e] = Y[e] + c[q] * R[e];
+            if (q < 2) {
+                double *t = (double *)malloc(n * sizeof(double));
+                memcpy(t, S, n * sizeof(double));
+                if (in != Y) free((void *)in);
+                in = t;
+            }
+        }
+        if (in != Y) free((void *)in);
+        orc_column(g, S, dt, NULL);
+        memcpy(Y, S, n * sizeof(double));
+    }
+    free(Y); free(S); free(R);
+}

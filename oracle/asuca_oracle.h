@@ -49,6 +49,24 @@ void orc_step(const orc_grid *g, double *Y, const double *mu, const double *mv,
 int orc_step_window(const orc_grid *g, const double *Y, const double *mu, const double *mv,
                     const double *mw, const double *tend, double dt, int nsteps,
                     int i0, int j0, int w, int h, double *out);
+/* tangent-linear and adjoint (limiter branches frozen at the forward values) */
+void orc_rhs_tl(const orc_grid *g, const double *Y, const double *mu, const double *mv,
+                const double *mw, const double *dY, const double *dmu, const double *dmv,
+                const double *dmw, double *dR);
+void orc_rhs_adj(const orc_grid *g, const double *Y, const double *mu, const double *mv,
+                 const double *mw, const double *lamR, double *lamY, double *gmu, double *gmv,
+                 double *gmw);
+void orc_column_tl(const orc_grid *g, const double *Y3, const double *dY3, double dt, double *dOut);
+void orc_column_adj(const orc_grid *g, const double *Y3, double *lam, double dt);
+void orc_step_tl(const orc_grid *g, const double *Y0, const double *mu, const double *mv,
+                 const double *mw, const double *tend, double dt, int nsteps, const double *dY0,
+                 const double *dmu, const double *dmv, const double *dmw, double *dYn);
+void orc_step_adj(const orc_grid *g, const double *Y0, const double *mu, const double *mv,
+                  const double *mw, const double *tend, double dt, int nsteps,
+                  const double *lam_final, double *lam0, double *gmu, double *gmv, double *gmw);
+void orc_trajectory_branches(const orc_grid *g, const double *Y0, const double *mu,
+                             const double *mv, const double *mw, const double *tend, double dt,
+                             int nsteps, unsigned char *out);
 void orc_set_threads(int n);
 int orc_get_threads(void);
 
