@@ -105,9 +105,9 @@ asuca_status asuca_free_grid(asuca_grid *grid);
 
 /* Bytes of device workspace op needs (256-byte aligned pointer required).
  * ASUCA_OP_STEP: two stage states plus the column-solve scratch, per-column
- * precipitation and budget partials.  ASUCA_OP_ADJOINT: param = checkpoint
- * interval K (states kept every K steps, one segment recomputed).  Returns 0
- * for an invalid grid or op. */
+ * precipitation and budget partials.  ASUCA_OP_ADJOINT: param = nsteps with
+ * checkpoints every 10 steps (asuca_adjoint_workspace_bytes takes any
+ * interval).  Returns 0 for an invalid grid or op. */
 size_t asuca_workspace_bytes(const asuca_grid *grid, int op, int param);
 
 /* Advance the state by nsteps RK3 steps, each followed by the column physics
@@ -121,6 +121,30 @@ size_t asuca_workspace_bytes(const asuca_grid *grid, int op, int param);
 asuca_status asuca_step(asuca_grid *grid, asuca_state *state, const void *tendencies, double dt,
                         int nsteps, void *workspace, size_t workspace_bytes, double *budgets_dev,
                         void *cuda_stream);
+
+/* Workspace of asuca_adjoint_step: the step workspace, ceil(nsteps / K)
+ * checkpoints, one segment of K recorded steps (stage states and limiter
+ * branches), four adjoint fields and the column-transpose scratch. */
+size_t asuca_adjoint_workspace_bytes(const asuca_grid *grid, int nsteps, int checkpoint_every);
+
+/* Adjoint (vector-Jacobian product) of nsteps calls of asuca_step's time
+ * step, the gradient engine of a 4D-Var-style assimilation: given
+ * lambda_final = dJ/dY_final ([F][nz][ny][nx], F = 2 + N fields in the
+ * order rho, rho*theta, rho*q), it returns grad_initial = dJ/dY_initial
+ * ([F][nz][ny][nx]) and the gradients with respect to the mass fluxes
+ * (grad_mu, grad_mv [nz][ny][nx], grad_mw [nz+1][ny][nx]; the lid entries
+ * of grad_mw are zero), all treated as independent inputs.  The forward
+ * trajectory is recomputed from `initial` (not modified): states are kept
+ * every checkpoint_every steps, and each segment is recomputed once more
+ * while recording the stage states and the limiter branch of every face,
+ * then reversed step by step (column transpose, then the three stage
+ * transposes).  Tendencies enter the trajectory but are not differentiated.
+ * Element types follow the grid's precision; the column transpose uses
+ * double for its tridiagonal solves in both precisions. */
+asuca_status asuca_adjoint_step(asuca_grid *grid, const asuca_state *initial, const void *tendencies, double dt,
+                                int nsteps, int checkpoint_every, const void *lambda_final, void *grad_initial,
+                                void *grad_mu, void *grad_mv, void *grad_mw, void *workspace,
+                                size_t workspace_bytes, void *cuda_stream);
 
 /* Synchronise the stream of the last call on this grid, return and clear
  * the device status word (ASUCA_OK when no device error was recorded). */
@@ -141,6 +165,16 @@ asuca_status asuca_debug_stage(asuca_grid *grid, const asuca_state *in, const as
 asuca_status asuca_debug_column(asuca_grid *grid, asuca_state *state, double dt,
                                 double *precip_col_dev, void *workspace, size_t workspace_bytes,
                                 void *cuda_stream);
+
+/* nsteps forward steps from `initial` (not modified) that write the limiter
+ * branch of every face of every RK stage to branches_dev, laid out
+ * [nsteps][3][F-1][nz][ny][nx], one byte per cell and field with 2 bits per
+ * direction (bits 0-1 face i+1/2, 2-3 face j+1/2, 4-5 face k+1/2; 0 zero,
+ * 1 "2r", 2 "kappa=1/3", 3 "cap 2").  Used to tell whether a perturbed
+ * trajectory crosses a limiter kink.  Workspace: asuca_adjoint_workspace_bytes(grid, 1, 1). */
+asuca_status asuca_debug_record_branches(asuca_grid *grid, const asuca_state *initial, const void *tendencies,
+                                         double dt, int nsteps, unsigned char *branches_dev, void *workspace,
+                                         size_t workspace_bytes, void *cuda_stream);
 
 /* Test hook for the arithmetic helpers of the column solve (device arrays of
  * n values; any output may be NULL): widen[i] = in_f[i] as double, narrow[i]
@@ -182,6 +216,8 @@ typedef enum {
     ASUCA_KERNEL_STAGE = 0,     /* one RK stage sweep */
     ASUCA_KERNEL_COLUMN = 1,    /* column physics + Thomas solve (+ budget partials) */
     ASUCA_KERNEL_REDUCE = 2,    /* final budget reduction */
+    ASUCA_KERNEL_ADJ_STAGE = 3, /* transpose of one RK stage */
+    ASUCA_KERNEL_ADJ_COLUMN = 4,/* transpose of the column pass */
     ASUCA_KERNEL_KINDS = 8
 } asuca_kernel_kind;
 

@@ -222,6 +222,8 @@ def _sig_tl():
         L.orc_step_tl.argtypes = [G, _D, _D, _D, _D, _D, ctypes.c_double, ctypes.c_int, _D, _D, _D, _D, _D]
         L.orc_step_adj.argtypes = [G, _D, _D, _D, _D, _D, ctypes.c_double, ctypes.c_int, _D, _D, _D, _D, _D]
         L.orc_trajectory_branches.argtypes = [G, _D, _D, _D, _D, _D, ctypes.c_double, ctypes.c_int, _U8]
+        L.orc_step_tl_br.argtypes = [G, _D, _D, _D, _D, _D, ctypes.c_double, ctypes.c_int, _D, _D, _D, _D, _U8, _D]
+        L.orc_step_adj_br.argtypes = [G, _D, _D, _D, _D, _D, ctypes.c_double, ctypes.c_int, _D, _U8, _D, _D, _D, _D]
         L._tl_ready = True
     return L
 
@@ -259,26 +261,39 @@ def column_adj(g: Grid, Y3, lam, dt):
     return lam
 
 
-def step_tl(g: Grid, Y0, mu, mv, mw, dt, nsteps, dY0, dmu=None, dmv=None, dmw=None, tend=None):
+def _traj_br(g, nsteps, traj_br):
+    if traj_br is None:
+        return None
+    b = np.ascontiguousarray(traj_br, dtype=np.uint8)
+    assert b.shape == (nsteps, 3) + g.shape, b.shape
+    return b
+
+
+def step_tl(g: Grid, Y0, mu, mv, mw, dt, nsteps, dY0, dmu=None, dmv=None, dmw=None, tend=None,
+            traj_br=None):
+    """traj_br ([nsteps][3][F][nz][ny][nx] bytes), when given, fixes every face's branch"""
     L = _sig_tl()
     Y0, mu, mv, mw, dY0 = map(_f64, (Y0, mu, mv, mw, dY0))
     dm = [None if a is None else _f64(a) for a in (dmu, dmv, dmw)]
     tend = None if tend is None else _f64(tend)
     out = np.empty(g.shape)
-    L.orc_step_tl(g.ref, _p(Y0), _p(mu), _p(mv), _p(mw), _p(tend), dt, nsteps, _p(dY0),
-                  _p(dm[0]), _p(dm[1]), _p(dm[2]), _p(out))
+    br = _traj_br(g, nsteps, traj_br)
+    L.orc_step_tl_br(g.ref, _p(Y0), _p(mu), _p(mv), _p(mw), _p(tend), dt, nsteps, _p(dY0),
+                     _p(dm[0]), _p(dm[1]), _p(dm[2]), None if br is None else br.ctypes.data_as(_U8),
+                     _p(out))
     return out
 
 
-def step_adj(g: Grid, Y0, mu, mv, mw, dt, nsteps, lam_final, tend=None):
-    """adjoint of nsteps steps: (lam0 [F][nz][ny][nx], g_mu, g_mv, g_mw)"""
+def step_adj(g: Grid, Y0, mu, mv, mw, dt, nsteps, lam_final, tend=None, traj_br=None):
+    """adjoint of nsteps steps: (lam0 [F][nz][ny][nx], g_mu, g_mv, g_mw); traj_br as in step_tl"""
     L = _sig_tl()
     Y0, mu, mv, mw, lam_final = map(_f64, (Y0, mu, mv, mw, lam_final))
     tend = None if tend is None else _f64(tend)
     lam0 = np.empty(g.shape)
     gmu, gmv, gmw = np.empty_like(mu), np.empty_like(mv), np.empty_like(mw)
-    L.orc_step_adj(g.ref, _p(Y0), _p(mu), _p(mv), _p(mw), _p(tend), dt, nsteps, _p(lam_final),
-                   _p(lam0), _p(gmu), _p(gmv), _p(gmw))
+    br = _traj_br(g, nsteps, traj_br)
+    L.orc_step_adj_br(g.ref, _p(Y0), _p(mu), _p(mv), _p(mw), _p(tend), dt, nsteps, _p(lam_final),
+                      None if br is None else br.ctypes.data_as(_U8), _p(lam0), _p(gmu), _p(gmv), _p(gmw))
     return lam0, gmu, gmv, gmw
 
 

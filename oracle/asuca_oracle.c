@@ -460,10 +460,12 @@ static void branch_ab(int br, double *a, double *b) {
     }
 }
 
-/* d face / d (pm1, p0, p1, p2) for the branch taken at this face */
-static void face_coefs(double pm1, double p0, double p1, double p2, double m, int lim, double c[4]) {
+/* d face / d (pm1, p0, p1, p2) for the branch taken at this face, or for the
+ * branch `forced` (0..3) when it is not negative */
+static void face_coefs(double pm1, double p0, double p1, double p2, double m, int lim, int forced, double c[4]) {
     int br;
     (void)orc_face(pm1, p0, p1, p2, m, lim, &br);
+    if (forced >= 0) br = forced;
     double a, b;
     branch_ab(br, &a, &b);
     if (m >= 0.0) {   /* face = p0 + (a (p0 - pm1) + b (p1 - p0)) / 2 */
@@ -504,9 +506,9 @@ static double rdelta(const orc_grid *g, int dir, int k) {
 }
 
 /* dR = d/dY R(Y; M)[dY] + d/dM R(Y; M)[dM]  (dM may be NULL) */
-void orc_rhs_tl(const orc_grid *g, const double *Y, const double *mu, const double *mv,
-                const double *mw, const double *dY, const double *dmu, const double *dmv,
-                const double *dmw, double *dR) {
+void orc_rhs_tl_br(const orc_grid *g, const double *Y, const double *mu, const double *mv,
+                   const double *mw, const double *dY, const double *dmu, const double *dmv,
+                   const double *dmw, const unsigned char *br, double *dR) {
     const int F = 2 + g->ntr, nz = g->nz;
     const size_t C = (size_t)nz * g->ny * g->nx;
     memset(dR, 0, (size_t)F * C * sizeof(double));
@@ -536,7 +538,8 @@ void orc_rhs_tl(const orc_grid *g, const double *Y, const double *mu, const doub
                                 ph[q] = rp / rho;
                                 dph[q] = (dY[(size_t)f * C + st[q]] - ph[q] * dY[st[q]]) / rho;
                             }
-                            face_coefs(ph[0], ph[1], ph[2], ph[3], m, g->lim, c);
+                            face_coefs(ph[0], ph[1], ph[2], ph[3], m, g->lim,
+                                       br ? (br[(size_t)f * C + a] >> (2 * dir)) & 3 : -1, c);
                             double face = orc_face(ph[0], ph[1], ph[2], ph[3], m, g->lim, NULL);
                             double dface = c[0] * dph[0] + c[1] * dph[1] + c[2] * dph[2] + c[3] * dph[3];
                             dF = dm * face + m * dface;
@@ -549,10 +552,17 @@ void orc_rhs_tl(const orc_grid *g, const double *Y, const double *mu, const doub
     }
 }
 
-/* lamY += (dR/dY)^T mu,  gM += (dR/dM)^T mu   (gM arrays may be NULL) */
-void orc_rhs_adj(const orc_grid *g, const double *Y, const double *mu, const double *mv,
-                 const double *mw, const double *lamR, double *lamY, double *gmu, double *gmv,
-                 double *gmw) {
+void orc_rhs_tl(const orc_grid *g, const double *Y, const double *mu, const double *mv,
+                const double *mw, const double *dY, const double *dmu, const double *dmv,
+                const double *dmw, double *dR) {
+    orc_rhs_tl_br(g, Y, mu, mv, mw, dY, dmu, dmv, dmw, NULL, dR);
+}
+
+/* lamY += (dR/dY)^T mu,  gM += (dR/dM)^T mu   (gM arrays may be NULL); br, when
+ * given, holds the branch of every face (the layout orc_rhs writes) */
+void orc_rhs_adj_br(const orc_grid *g, const double *Y, const double *mu, const double *mv,
+                    const double *mw, const double *lamR, const unsigned char *br, double *lamY,
+                    double *gmu, double *gmv, double *gmw) {
     const int F = 2 + g->ntr, nz = g->nz;
     const size_t C = (size_t)nz * g->ny * g->nx;
     for (int dir = 0; dir < 3; dir++) {
@@ -580,7 +590,8 @@ void orc_rhs_adj(const orc_grid *g, const double *Y, const double *mu, const dou
                         }
                         double ph[4], c[4];
                         for (int q = 0; q < 4; q++) ph[q] = Y[(size_t)f * C + st[q]] / Y[st[q]];
-                        face_coefs(ph[0], ph[1], ph[2], ph[3], m, g->lim, c);
+                        face_coefs(ph[0], ph[1], ph[2], ph[3], m, g->lim,
+                                   br ? (br[(size_t)f * C + a] >> (2 * dir)) & 3 : -1, c);
                         double face = orc_face(ph[0], ph[1], ph[2], ph[3], m, g->lim, NULL);
                         if (gM) gM[fm] += lF * face;
                         for (int q = 0; q < 4; q++) {
@@ -593,6 +604,12 @@ void orc_rhs_adj(const orc_grid *g, const double *Y, const double *mu, const dou
                 }
         }
     }
+}
+
+void orc_rhs_adj(const orc_grid *g, const double *Y, const double *mu, const double *mv,
+                 const double *mw, const double *lamR, double *lamY, double *gmu, double *gmv,
+                 double *gmw) {
+    orc_rhs_adj_br(g, Y, mu, mv, mw, lamR, NULL, lamY, gmu, gmv, gmw);
 }
 
 /* forward column pass of one column, keeping the intermediates the
@@ -836,10 +853,12 @@ static void step_states(const orc_grid *g, const double *Yn, const double *mu, c
     free(R);
 }
 
-/* tangent of nsteps steps: (dY0, dM) -> dYn */
-void orc_step_tl(const orc_grid *g, const double *Y0, const double *mu, const double *mv,
-                 const double *mw, const double *tend, double dt, int nsteps, const double *dY0,
-                 const double *dmu, const double *dmv, const double *dmw, double *dYn) {
+/* tangent of nsteps steps: (dY0, dM) -> dYn; traj_br, when given, fixes the
+ * branch of every face of every stage ([nsteps][3][F][nz][ny][nx] bytes) */
+void orc_step_tl_br(const orc_grid *g, const double *Y0, const double *mu, const double *mv,
+                    const double *mw, const double *tend, double dt, int nsteps, const double *dY0,
+                    const double *dmu, const double *dmv, const double *dmw,
+                    const unsigned char *traj_br, double *dYn) {
     const size_t n = (size_t)(2 + g->ntr) * g->nz * g->ny * g->nx;
     double *Y = (double *)malloc(n * sizeof(double));
     double *Y1 = (double *)malloc(n * sizeof(double));
@@ -857,7 +876,8 @@ void orc_step_tl(const orc_grid *g, const double *Y0, const double *mu, const do
         const double *st[3] = {Y, Y1, Y2};
         memcpy(dS, dY, n * sizeof(double));              /* tangent of the stage input */
         for (int q = 0; q < 3; q++) {
-            orc_rhs_tl(g, st[q], mu, mv, mw, dS, dmu, dmv, dmw, dR);
+            orc_rhs_tl_br(g, st[q], mu, mv, mw, dS, dmu, dmv, dmw,
+                          traj_br ? traj_br + ((size_t)s * 3 + q) * n : NULL, dR);
             for (size_t e = 0; e < n; e++) dS[e] = dY[e] + c[q] * dR[e];
         }
         orc_column_tl(g, Y3, dS, dt, dY);
@@ -867,11 +887,19 @@ void orc_step_tl(const orc_grid *g, const double *Y0, const double *mu, const do
     free(Y); free(Y1); free(Y2); free(Y3); free(Yx); free(dY); free(dS); free(dR);
 }
 
+void orc_step_tl(const orc_grid *g, const double *Y0, const double *mu, const double *mv,
+                 const double *mw, const double *tend, double dt, int nsteps, const double *dY0,
+                 const double *dmu, const double *dmv, const double *dmw, double *dYn) {
+    orc_step_tl_br(g, Y0, mu, mv, mw, tend, dt, nsteps, dY0, dmu, dmv, dmw, NULL, dYn);
+}
+
 /* adjoint of nsteps steps: lam_final -> lam0 (adjoint of Y0), g_mu/g_mv/g_mw
- * (adjoint of the mass fluxes; overwritten).  The whole trajectory is kept. */
-void orc_step_adj(const orc_grid *g, const double *Y0, const double *mu, const double *mv,
-                  const double *mw, const double *tend, double dt, int nsteps,
-                  const double *lam_final, double *lam0, double *gmu, double *gmv, double *gmw) {
+ * (adjoint of the mass fluxes; overwritten).  The whole trajectory is kept.
+ * traj_br as for orc_step_tl_br. */
+void orc_step_adj_br(const orc_grid *g, const double *Y0, const double *mu, const double *mv,
+                     const double *mw, const double *tend, double dt, int nsteps,
+                     const double *lam_final, const unsigned char *traj_br, double *lam0,
+                     double *gmu, double *gmv, double *gmw) {
     const size_t C = (size_t)g->nz * g->ny * g->nx;
     const size_t n = (size_t)(2 + g->ntr) * C;
     const size_t nw = (size_t)(g->nz + 1) * g->ny * g->nx;
@@ -898,16 +926,25 @@ void orc_step_adj(const orc_grid *g, const double *Y0, const double *mu, const d
         orc_column_adj(g, Y3s + (size_t)s * n, lam, dt);          /* lam: adjoint of Y3 */
         /* Y3 = Yn + c3 R(Y2) */
         for (size_t e = 0; e < n; e++) { mu_r[e] = c[2] * lam[e]; l2[e] = 0.0; }
-        orc_rhs_adj(g, Ys + 2 * n, mu, mv, mw, mu_r, l2, gmu, gmv, gmw);
+        const unsigned char *b3 = traj_br ? traj_br + ((size_t)s * 3 + 2) * n : NULL;
+        const unsigned char *b2 = traj_br ? traj_br + ((size_t)s * 3 + 1) * n : NULL;
+        const unsigned char *b1 = traj_br ? traj_br + ((size_t)s * 3 + 0) * n : NULL;
+        orc_rhs_adj_br(g, Ys + 2 * n, mu, mv, mw, mu_r, b3, l2, gmu, gmv, gmw);
         /* Y2 = Yn + c2 R(Y1) */
         for (size_t e = 0; e < n; e++) { mu_r[e] = c[1] * l2[e]; l1[e] = 0.0; }
-        orc_rhs_adj(g, Ys + n, mu, mv, mw, mu_r, l1, gmu, gmv, gmw);
+        orc_rhs_adj_br(g, Ys + n, mu, mv, mw, mu_r, b2, l1, gmu, gmv, gmw);
         /* Y1 = Yn + c1 R(Yn) */
         for (size_t e = 0; e < n; e++) { lam[e] += l2[e] + l1[e]; mu_r[e] = c[0] * l1[e]; }
-        orc_rhs_adj(g, Ys, mu, mv, mw, mu_r, lam, gmu, gmv, gmw);
+        orc_rhs_adj_br(g, Ys, mu, mv, mw, mu_r, b1, lam, gmu, gmv, gmw);
     }
     memcpy(lam0, lam, n * sizeof(double));
     free(traj); free(Y3s); free(lam); free(l2); free(l1); free(mu_r);
+}
+
+void orc_step_adj(const orc_grid *g, const double *Y0, const double *mu, const double *mv,
+                  const double *mw, const double *tend, double dt, int nsteps,
+                  const double *lam_final, double *lam0, double *gmu, double *gmv, double *gmw) {
+    orc_step_adj_br(g, Y0, mu, mv, mw, tend, dt, nsteps, lam_final, NULL, lam0, gmu, gmv, gmw);
 }
 
 /* limiter branches of every face of every stage of nsteps steps:

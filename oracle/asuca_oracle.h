@@ -64,6 +64,15 @@ void orc_step_tl(const orc_grid *g, const double *Y0, const double *mu, const do
 void orc_step_adj(const orc_grid *g, const double *Y0, const double *mu, const double *mv,
                   const double *mw, const double *tend, double dt, int nsteps,
                   const double *lam_final, double *lam0, double *gmu, double *gmv, double *gmw);
+/* the same with the branch of every face fixed by the caller */
+void orc_step_tl_br(const orc_grid *g, const double *Y0, const double *mu, const double *mv,
+                    const double *mw, const double *tend, double dt, int nsteps, const double *dY0,
+                    const double *dmu, const double *dmv, const double *dmw,
+                    const unsigned char *traj_br, double *dYn);
+void orc_step_adj_br(const orc_grid *g, const double *Y0, const double *mu, const double *mv,
+                     const double *mw, const double *tend, double dt, int nsteps,
+                     const double *lam_final, const unsigned char *traj_br, double *lam0,
+                     double *gmu, double *gmv, double *gmw);
 void orc_trajectory_branches(const orc_grid *g, const double *Y0, const double *mu,
                              const double *mv, const double *mw, const double *tend, double dt,
                              int nsteps, unsigned char *out);

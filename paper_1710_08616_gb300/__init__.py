@@ -71,11 +71,16 @@ SIGNATURES = {
                                           _VP, ctypes.c_size_t, _VP]),
     "asuca_debug_numerics": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP, _VP, _VP, _VP]),
     "asuca_column_noalloc": (ctypes.c_int, [_VP, ctypes.POINTER(StateStruct), ctypes.c_double, _VP, _VP]),
+    "asuca_adjoint_workspace_bytes": (ctypes.c_size_t, [_VP, ctypes.c_int, ctypes.c_int]),
+    "asuca_adjoint_step": (ctypes.c_int, [_VP, ctypes.POINTER(StateStruct), _VP, ctypes.c_double, ctypes.c_int,
+                                          ctypes.c_int, _VP, _VP, _VP, _VP, _VP, _VP, ctypes.c_size_t, _VP]),
+    "asuca_debug_record_branches": (ctypes.c_int, [_VP, ctypes.POINTER(StateStruct), _VP, ctypes.c_double,
+                                                   ctypes.c_int, _VP, _VP, ctypes.c_size_t, _VP]),
     "asuca_profile_enable": (ctypes.c_int, [_VP, ctypes.c_int]),
     "asuca_profile_read": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
 }
-KERNEL_STAGE, KERNEL_COLUMN, KERNEL_REDUCE = 0, 1, 2
+KERNEL_STAGE, KERNEL_COLUMN, KERNEL_REDUCE, KERNEL_ADJ_STAGE, KERNEL_ADJ_COLUMN = 0, 1, 2, 3, 4
 KERNEL_KINDS = 8
 
 
@@ -283,3 +288,98 @@ def profile_read(grid: Grid):
     n = (ctypes.c_int * KERNEL_KINDS)()
     _check(lib().asuca_profile_read(grid.handle, ms, n, KERNEL_KINDS), "asuca_profile_read")
     return {k: (ms[k], n[k]) for k in range(KERNEL_KINDS) if n[k]}
+
+
+# ---------------------------------------------------------------- adjoint
+
+def adjoint_workspace_bytes(grid: Grid, nsteps: int, checkpoint_every: int = 10) -> int:
+    return int(lib().asuca_adjoint_workspace_bytes(grid.handle, int(nsteps), int(checkpoint_every)))
+
+
+def adjoint_step(grid: Grid, initial: State, dt: float, nsteps: int, lam_final, *, checkpoint_every: int = 10,
+                 tendencies=None, workspace=None, stream=None):
+    """Adjoint of nsteps steps (asuca_adjoint_step): lam_final = dJ/dY_final as a
+    [F][nz][ny][nx] tensor; returns (dJ/dY_initial [F][nz][ny][nx], dJ/dmu,
+    dJ/dmv, dJ/dmw).  `initial` is not modified."""
+    import torch
+    _check_state(grid, initial)
+    F = grid.nfields
+    shape = (F, grid.nz, grid.ny, grid.nx)
+    if tuple(lam_final.shape) != shape or lam_final.dtype != grid.torch_dtype or not lam_final.is_contiguous():
+        raise ValueError(f"lam_final: need contiguous {grid.torch_dtype} of shape {shape}")
+    dev = initial.rho.device
+    if workspace is None:
+        n = adjoint_workspace_bytes(grid, nsteps, checkpoint_every)
+        workspace = torch.empty(max(n, 256), dtype=torch.uint8, device=dev)
+    g0 = torch.empty(shape, dtype=grid.torch_dtype, device=dev)
+    gmu = torch.empty_like(initial.mu)
+    gmv = torch.empty_like(initial.mv)
+    gmw = torch.empty_like(initial.mw)
+    s = initial.struct()
+    _check(lib().asuca_adjoint_step(grid.handle, ctypes.byref(s), _ptr(tendencies), float(dt), int(nsteps),
+                                    int(checkpoint_every), _ptr(lam_final), _ptr(g0), _ptr(gmu), _ptr(gmv),
+                                    _ptr(gmw), _ptr(workspace), workspace.numel(), _stream_ptr(stream)),
+           "asuca_adjoint_step")
+    return g0, gmu, gmv, gmw
+
+
+def record_branches(grid: Grid, initial: State, dt: float, nsteps: int, *, tendencies=None, stream=None):
+    """Limiter branch bytes [nsteps][3][F-1][nz][ny][nx] of a forward trajectory."""
+    import torch
+    dev = initial.rho.device
+    out = torch.empty((nsteps, 3, grid.nfields - 1, grid.nz, grid.ny, grid.nx), dtype=torch.uint8, device=dev)
+    n = adjoint_workspace_bytes(grid, 1, 1)
+    ws = torch.empty(max(n, 256), dtype=torch.uint8, device=dev)
+    s = initial.struct()
+    _check(lib().asuca_debug_record_branches(grid.handle, ctypes.byref(s), _ptr(tendencies), float(dt),
+                                             int(nsteps), _ptr(out), _ptr(ws), ws.numel(), _stream_ptr(stream)),
+           "asuca_debug_record_branches")
+    return out
+
+
+def _autograd_function():
+    import torch
+
+    class AdjointFn(torch.autograd.Function):
+        """Y_final = step^nsteps(Y_initial; mu, mv, mw) with a hand-written adjoint.
+
+        forward(rho0, rhotheta0, rhoq0, mu, mv, mw, grid, dt, nsteps, checkpoint_every)
+        -> (rho, rhotheta, rhoq) after nsteps steps.  backward runs
+        asuca_adjoint_step, which recomputes the trajectory from the saved
+        initial state with checkpoints every checkpoint_every steps."""
+
+        @staticmethod
+        def forward(ctx, rho0, rhotheta0, rhoq0, mu, mv, mw, grid, dt, nsteps, checkpoint_every=10):
+            st = State(rho0.detach().clone().contiguous(), rhotheta0.detach().clone().contiguous(),
+                       rhoq0.detach().clone().contiguous(), mu.detach().contiguous(), mv.detach().contiguous(),
+                       mw.detach().contiguous())
+            ctx.save_for_backward(rho0, rhotheta0, rhoq0, mu, mv, mw)
+            ctx.grid, ctx.dt, ctx.nsteps, ctx.k = grid, dt, nsteps, checkpoint_every
+            step(grid, st, dt, nsteps)
+            return st.rho, st.rhotheta, st.rhoq
+
+        @staticmethod
+        def backward(ctx, g_rho, g_rt, g_q):
+            rho0, rt0, q0, mu, mv, mw = ctx.saved_tensors
+            grid = ctx.grid
+            z = lambda t, like: torch.zeros_like(like) if t is None else t
+            lam = torch.cat([z(g_rho, rho0)[None], z(g_rt, rt0)[None], z(g_q, q0)], 0).contiguous()
+            init = State(rho0.detach().contiguous(), rt0.detach().contiguous(), q0.detach().contiguous(),
+                         mu.detach().contiguous(), mv.detach().contiguous(), mw.detach().contiguous())
+            g0, gmu, gmv, gmw = adjoint_step(grid, init, ctx.dt, ctx.nsteps, lam.to(grid.torch_dtype),
+                                             checkpoint_every=ctx.k)
+            return g0[0], g0[1], g0[2:], gmu, gmv, gmw, None, None, None, None
+
+    return AdjointFn
+
+
+_ADJOINT_FN = None
+
+
+def __getattr__(name):
+    global _ADJOINT_FN
+    if name == "AdjointFn":
+        if _ADJOINT_FN is None:
+            _ADJOINT_FN = _autograd_function()
+        return _ADJOINT_FN
+    raise AttributeError(name)

@@ -5,7 +5,9 @@
 #include <new>
 #include <cstdlib>
 #include <mutex>
+#include <vector>
 
+#include "adjoint_params.cuh"
 #include "common.cuh"
 
 using namespace asuca;
@@ -256,6 +258,281 @@ asuca_status run_step(asuca_grid *g, asuca_state *st, const void *tend, double d
     return ASUCA_OK;
 }
 
+// ---- adjoint -------------------------------------------------------------
+
+struct AdjLayout {
+    size_t step, W, ckpt, segYn, segY1, segY2, segY3, branch, lam, l2, l1, acc, scratch, total;
+    int ncp;
+    size_t ustate, pstate, nbranch_step;
+    long long slots;
+};
+
+int adj_col_grid(const asuca_grid *g) { return g->col_grid; }
+
+AdjLayout adj_layout(const asuca_grid *g, int nsteps, int K) {
+    AdjLayout L;
+    const size_t s = elem_size(g);
+    L.ustate = (size_t)g->F * g->cells * s;
+    L.pstate = (size_t)g->F * padded_field_elems(g) * s;
+    L.nbranch_step = (size_t)3 * (g->F - 1) * g->cells;
+    L.ncp = nsteps > 0 ? (nsteps + K - 1) / K : 0;
+    L.slots = (long long)adj_col_grid(g) * COL_TPB;
+    size_t off = 0;
+    L.step = off;
+    off = align_up(off + step_layout(g).total);
+    L.W = off;
+    off = align_up(off + L.ustate);
+    L.ckpt = off;
+    off = align_up(off + (size_t)L.ncp * align_up(L.ustate));
+    L.segYn = off;
+    off = align_up(off + (size_t)(K + 1) * align_up(L.ustate));
+    L.segY1 = off;
+    off = align_up(off + (size_t)K * align_up(L.pstate));
+    L.segY2 = off;
+    off = align_up(off + (size_t)K * align_up(L.pstate));
+    L.segY3 = off;
+    off = align_up(off + (size_t)K * align_up(L.ustate));
+    L.branch = off;
+    off = align_up(off + (size_t)K * align_up(L.nbranch_step));
+    L.lam = off;
+    off = align_up(off + L.ustate);
+    L.l2 = off;
+    off = align_up(off + L.ustate);
+    L.l1 = off;
+    off = align_up(off + L.ustate);
+    L.acc = off;
+    off = align_up(off + L.ustate);
+    L.scratch = off;
+    off = align_up(off + (size_t)g->d.nz * (4 + 2 * (g->F - 1)) * L.slots * sizeof(double));
+    L.total = off;
+    return L;
+}
+
+// fields of a contiguous [F][nz][ny][nx] block (user layout)
+template <typename T>
+void block_fields(const asuca_grid *g, void *base, T **out) {
+    for (int f = 0; f < g->F; f++) out[f] = (T *)base + (size_t)f * g->cells;
+    for (int f = g->F; f < MAXF; f++) out[f] = nullptr;
+}
+
+template <typename T>
+asuca_state block_state(const asuca_grid *g, void *base, const asuca_state *m) {
+    asuca_state st;
+    st.rho = base;
+    st.rhotheta = (T *)base + g->cells;
+    st.rhoq = (T *)base + 2 * g->cells;
+    st.mu = m->mu;
+    st.mv = m->mv;
+    st.mw = m->mw;
+    return st;
+}
+
+template <typename T>
+asuca_status run_adjoint(asuca_grid *g, const asuca_state *init, const void *tend, double dt, int nsteps,
+                         int K, const T *lam_final, T *grad0, T *gmu, T *gmv, T *gmw, char *ws, cudaStream_t s) {
+    const AdjLayout L = adj_layout(g, nsteps, K);
+    const int F = g->F;
+    const size_t cb = (size_t)g->cells * sizeof(T);
+    cudaError_t e = cudaSuccess;
+    auto ck = [&](cudaError_t r) { if (r != cudaSuccess && e == cudaSuccess) e = r; };
+    // ---- forward pass from the initial state, keeping a checkpoint every K steps
+    T *Wf[MAXF];
+    block_fields<T>(g, ws + L.W, Wf);
+    T *init_f[MAXF];
+    field_ptrs<T>(g, init->rho, init->rhotheta, init->rhoq, init_f);
+    for (int f = 0; f < F; f++) ck(cudaMemcpyAsync(Wf[f], init_f[f], cb, cudaMemcpyDeviceToDevice, s));
+    asuca_state Ws = block_state<T>(g, ws + L.W, init);
+    for (int n = 0; n < nsteps; n++) {
+        if (n % K == 0)
+            ck(cudaMemcpyAsync(ws + L.ckpt + (size_t)(n / K) * align_up(L.ustate), ws + L.W, L.ustate,
+                               cudaMemcpyDeviceToDevice, s));
+        if (e != cudaSuccess) return ASUCA_ERR_CUDA;
+        asuca_status r = run_step<T>(g, &Ws, tend, dt, 1, ws + L.step, nullptr, s);
+        if (r != ASUCA_OK) return r;
+    }
+    // ---- adjoint accumulators
+    const size_t mb = (size_t)g->cells * sizeof(T), mwb = (size_t)(g->d.nz + 1) * g->plane * sizeof(T);
+    ck(cudaMemsetAsync(gmu, 0, mb, s));
+    ck(cudaMemsetAsync(gmv, 0, mb, s));
+    ck(cudaMemsetAsync(gmw, 0, mwb, s));
+    ck(cudaMemcpyAsync(ws + L.lam, lam_final, L.ustate, cudaMemcpyDeviceToDevice, s));
+    if (e != cudaSuccess) return ASUCA_ERR_CUDA;
+    T *lam[MAXF], *l2[MAXF], *l1[MAXF], *acc[MAXF];
+    block_fields<T>(g, ws + L.lam, lam);
+    block_fields<T>(g, ws + L.l2, l2);
+    block_fields<T>(g, ws + L.l1, l1);
+    block_fields<T>(g, ws + L.acc, acc);
+    const T cdt[3] = {(T)(dt / 3.0), (T)(dt / 2.0), (T)dt};
+    const StepLayout SL = step_layout(g);
+    char *sws = ws + L.step;
+    std::vector<CUtensorMap> maps(2 * (size_t)K);
+    for (int q = 0; q < K; q++) {
+        if (encode_stage_map<T>(&maps[2 * q], ws + L.segY1 + (size_t)q * align_up(L.pstate), F, g->d.nx, g->d.ny,
+                                g->d.nz) != cudaSuccess ||
+            encode_stage_map<T>(&maps[2 * q + 1], ws + L.segY2 + (size_t)q * align_up(L.pstate), F, g->d.nx,
+                                g->d.ny, g->d.nz) != cudaSuccess)
+            return ASUCA_ERR_CUDA;
+    }
+    for (int c = L.ncp - 1; c >= 0; c--) {
+        const int start = c * K, len = (nsteps - start) < K ? (nsteps - start) : K;
+        auto segYn = [&](int q) { return ws + L.segYn + (size_t)q * align_up(L.ustate); };
+        auto segY1 = [&](int q) { return ws + L.segY1 + (size_t)q * align_up(L.pstate); };
+        auto segY2 = [&](int q) { return ws + L.segY2 + (size_t)q * align_up(L.pstate); };
+        auto segY3 = [&](int q) { return ws + L.segY3 + (size_t)q * align_up(L.ustate); };
+        auto brs = [&](int q, int stg) {
+            return (uint8_t *)(ws + L.branch + (size_t)q * align_up(L.nbranch_step)) +
+                   (size_t)stg * (F - 1) * g->cells;
+        };
+        ck(cudaMemcpyAsync(segYn(0), ws + L.ckpt + (size_t)c * align_up(L.ustate), L.ustate,
+                           cudaMemcpyDeviceToDevice, s));
+        if (e != cudaSuccess) return ASUCA_ERR_CUDA;
+        // ---- recompute the segment, recording stage states and limiter branches
+        for (int q = 0; q < len; q++) {
+            T *yn[MAXF], *y1[MAXF], *y2[MAXF], *y3[MAXF];
+            block_fields<T>(g, segYn(q), yn);
+            workspace_fields<T>(g, segY1(q), 0, y1);
+            workspace_fields<T>(g, segY2(q), 0, y2);
+            block_fields<T>(g, segY3(q), y3);
+            StageParams<T> sp = stage_params<T>(g, init, tend);
+            for (int f = 0; f < MAXF; f++) sp.ybase[f] = yn[f];
+            for (int stg = 0; stg < 3; stg++) {
+                sp.tma_in = stg > 0;
+                if (stg > 0) sp.tmap = maps[2 * q + (stg - 1)];
+                sp.out_padded = stg < 2;
+                T **out = stg == 0 ? y1 : (stg == 1 ? y2 : y3);
+                for (int f = 0; f < MAXF; f++) {
+                    sp.yin[f] = yn[f];
+                    sp.yout[f] = out[f];
+                }
+                sp.cdt = cdt[stg];
+                sp.branch = brs(q, stg);
+                if (timed(g, ASUCA_KERNEL_STAGE, s, [&] { return launch_stage<T>(sp, F, s); }) != cudaSuccess)
+                    return ASUCA_ERR_CUDA;
+            }
+            ck(cudaMemcpyAsync(segYn(q + 1), segY3(q), L.ustate, cudaMemcpyDeviceToDevice, s));
+            ColumnParams<T> cp = column_params<T>(g, dt);
+            block_fields<T>(g, segYn(q + 1), cp.y);
+            cp.precip_col = (double *)(sws + SL.precip);
+            cp.partials = (double *)(sws + SL.partials);
+            cp.scratch = (double *)(sws + SL.scratch);
+            cp.budgets = 0;
+            if (e != cudaSuccess ||
+                timed(g, ASUCA_KERNEL_COLUMN, s, [&] { return launch_column<T>(cp, F, g->col_grid, COL_TPB, s); }) !=
+                    cudaSuccess)
+                return ASUCA_ERR_CUDA;
+        }
+        // ---- reverse through the segment
+        for (int q = len - 1; q >= 0; q--) {
+            AdjColParams<T> ac;
+            std::memset(&ac, 0, sizeof(ac));
+            ac.c = column_params<T>(g, dt);
+            block_fields<T>(g, segY3(q), ac.c.y);
+            ac.c.scratch = (double *)(ws + L.scratch);
+            ac.c.nslots = L.slots;
+            for (int f = 0; f < MAXF; f++) ac.lam[f] = lam[f];
+            if (timed(g, ASUCA_KERNEL_ADJ_COLUMN, s, [&] { return launch_adj_column<T>(ac, F, adj_col_grid(g), s); }) !=
+                cudaSuccess)
+                return ASUCA_ERR_CUDA;
+            for (int stg = 2; stg >= 0; stg--) {
+                AdjStageParams<T> ap;
+                std::memset(&ap, 0, sizeof(ap));
+                if (stg == 0) {
+                    block_fields<T>(g, segYn(q), (T **)ap.ys);
+                    ap.ys_pitch = g->d.nx;
+                    ap.ys_plane = g->plane;
+                    ap.ys_ox = ap.ys_oy = 0;
+                } else {
+                    workspace_fields<T>(g, stg == 1 ? segY1(q) : segY2(q), 0, (T **)ap.ys);
+                    ap.ys_pitch = padded_pitch(g->d.nx);
+                    ap.ys_plane = (long long)(g->d.ny + 4) * ap.ys_pitch;
+                    ap.ys_ox = 4;
+                    ap.ys_oy = 2;
+                }
+                T **lin = stg == 2 ? lam : (stg == 1 ? l2 : l1);
+                for (int f = 0; f < MAXF; f++) ap.lam[f] = lin[f];
+                ap.cs = cdt[stg];
+                ap.branch = brs(q, stg);
+                ap.mu = (const T *)init->mu;
+                ap.mv = (const T *)init->mv;
+                ap.mw = (const T *)init->mw;
+                for (int f = 0; f < MAXF; f++) {
+                    ap.out1[f] = stg == 2 ? l2[f] : (stg == 1 ? l1[f] : nullptr);
+                    ap.out2[f] = stg == 0 ? lam[f] : acc[f];
+                    ap.base2[f] = stg == 2 ? nullptr : acc[f];
+                }
+                ap.add_self = stg == 2;
+                ap.gmu = gmu;
+                ap.gmv = gmv;
+                ap.gmw = gmw;
+                ap.nx = g->d.nx;
+                ap.ny = g->d.ny;
+                ap.nz = g->d.nz;
+                ap.plane = g->plane;
+                ap.rdx = (T)(1.0 / g->d.dx);
+                ap.rdy = (T)(1.0 / g->d.dy);
+                for (int k = 0; k < g->d.nz; k++) ap.rdz[k] = (T)(1.0 / g->dz[k]);
+                if (timed(g, ASUCA_KERNEL_ADJ_STAGE, s, [&] { return launch_adj_stage<T>(ap, F, (int)g->d.lim, s); }) !=
+                    cudaSuccess)
+                    return ASUCA_ERR_CUDA;
+            }
+        }
+    }
+    ck(cudaMemcpyAsync(grad0, ws + L.lam, L.ustate, cudaMemcpyDeviceToDevice, s));
+    return e == cudaSuccess ? ASUCA_OK : ASUCA_ERR_CUDA;
+}
+
+// Forward steps that record every stage's limiter branches into out
+// ([nsteps][3][F-1][nz][ny][nx] bytes), using the one-step adjoint layout.
+template <typename T>
+asuca_status run_record(asuca_grid *g, const asuca_state *init, const void *tend, double dt, int nsteps,
+                        unsigned char *out, char *ws, cudaStream_t s) {
+    const AdjLayout L = adj_layout(g, 1, 1);
+    const int F = g->F;
+    const size_t cb = (size_t)g->cells * sizeof(T);
+    CUtensorMap m1, m2;
+    if (encode_stage_map<T>(&m1, ws + L.segY1, F, g->d.nx, g->d.ny, g->d.nz) != cudaSuccess ||
+        encode_stage_map<T>(&m2, ws + L.segY2, F, g->d.nx, g->d.ny, g->d.nz) != cudaSuccess)
+        return ASUCA_ERR_CUDA;
+    T *yn[MAXF], *y1[MAXF], *y2[MAXF], *y3[MAXF], *init_f[MAXF];
+    block_fields<T>(g, ws + L.segYn, yn);
+    workspace_fields<T>(g, ws + L.segY1, 0, y1);
+    workspace_fields<T>(g, ws + L.segY2, 0, y2);
+    block_fields<T>(g, ws + L.segY3, y3);
+    field_ptrs<T>(g, init->rho, init->rhotheta, init->rhoq, init_f);
+    for (int f = 0; f < F; f++)
+        if (cudaMemcpyAsync(yn[f], init_f[f], cb, cudaMemcpyDeviceToDevice, s) != cudaSuccess) return ASUCA_ERR_CUDA;
+    const StepLayout SL = step_layout(g);
+    char *sws = ws + L.step;
+    const T cdt[3] = {(T)(dt / 3.0), (T)(dt / 2.0), (T)dt};
+    for (int n = 0; n < nsteps; n++) {
+        StageParams<T> sp = stage_params<T>(g, init, tend);
+        for (int f = 0; f < MAXF; f++) sp.ybase[f] = yn[f];
+        for (int stg = 0; stg < 3; stg++) {
+            sp.tma_in = stg > 0;
+            if (stg > 0) sp.tmap = stg == 1 ? m1 : m2;
+            sp.out_padded = stg < 2;
+            T **o = stg == 0 ? y1 : (stg == 1 ? y2 : y3);
+            for (int f = 0; f < MAXF; f++) {
+                sp.yin[f] = yn[f];
+                sp.yout[f] = o[f];
+            }
+            sp.cdt = cdt[stg];
+            sp.branch = out + ((size_t)n * 3 + stg) * (F - 1) * g->cells;
+            if (launch_stage<T>(sp, F, s) != cudaSuccess) return ASUCA_ERR_CUDA;
+        }
+        if (cudaMemcpyAsync(ws + L.segYn, ws + L.segY3, L.ustate, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+            return ASUCA_ERR_CUDA;
+        ColumnParams<T> cp = column_params<T>(g, dt);
+        for (int f = 0; f < MAXF; f++) cp.y[f] = yn[f];
+        cp.precip_col = (double *)(sws + SL.precip);
+        cp.partials = (double *)(sws + SL.partials);
+        cp.scratch = (double *)(sws + SL.scratch);
+        cp.budgets = 0;
+        if (launch_column<T>(cp, F, g->col_grid, COL_TPB, s) != cudaSuccess) return ASUCA_ERR_CUDA;
+    }
+    return ASUCA_OK;
+}
+
 }  // namespace
 
 // ---- column pass without a caller workspace ------------------------------
@@ -379,10 +656,52 @@ asuca_status asuca_free_grid(asuca_grid *g) {
 }
 
 size_t asuca_workspace_bytes(const asuca_grid *g, int op, int param) {
-    (void)param;
     if (!g) return 0;
     if (op == ASUCA_OP_STEP) return step_layout(g).total;
+    if (op == ASUCA_OP_ADJOINT) return param >= 0 ? adj_layout(g, param, 10).total : 0;
     return 0;
+}
+
+size_t asuca_adjoint_workspace_bytes(const asuca_grid *g, int nsteps, int checkpoint_every) {
+    if (!g || nsteps < 0 || checkpoint_every < 1) return 0;
+    return adj_layout(g, nsteps, checkpoint_every).total;
+}
+
+asuca_status asuca_adjoint_step(asuca_grid *g, const asuca_state *initial, const void *tendencies, double dt,
+                                int nsteps, int checkpoint_every, const void *lambda_final, void *grad_initial,
+                                void *grad_mu, void *grad_mv, void *grad_mw, void *workspace,
+                                size_t workspace_bytes, void *cuda_stream) {
+    if (!g || !state_ok(g, initial) || nsteps < 0 || checkpoint_every < 1 || !std::isfinite(dt) || dt < 0.0 ||
+        !lambda_final || !grad_initial || !grad_mu || !grad_mv || !grad_mw)
+        return ASUCA_ERR_ARG;
+    asuca_status prev = take_status(g);
+    if (prev != ASUCA_OK) return prev;
+    if (!workspace || ((uintptr_t)workspace % ALIGN) != 0 ||
+        workspace_bytes < adj_layout(g, nsteps, checkpoint_every).total)
+        return ASUCA_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    g->last_stream = s;
+    if (g->d.prec == ASUCA_FP64)
+        return run_adjoint<double>(g, initial, tendencies, dt, nsteps, checkpoint_every, (const double *)lambda_final,
+                                   (double *)grad_initial, (double *)grad_mu, (double *)grad_mv, (double *)grad_mw,
+                                   (char *)workspace, s);
+    return run_adjoint<float>(g, initial, tendencies, dt, nsteps, checkpoint_every, (const float *)lambda_final,
+                              (float *)grad_initial, (float *)grad_mu, (float *)grad_mv, (float *)grad_mw,
+                              (char *)workspace, s);
+}
+
+asuca_status asuca_debug_record_branches(asuca_grid *g, const asuca_state *initial, const void *tendencies,
+                                         double dt, int nsteps, unsigned char *branches_dev, void *workspace,
+                                         size_t workspace_bytes, void *cuda_stream) {
+    if (!g || !state_ok(g, initial) || nsteps < 0 || !branches_dev || !std::isfinite(dt) || dt < 0.0)
+        return ASUCA_ERR_ARG;
+    const AdjLayout L = adj_layout(g, 1, 1);
+    if (!workspace || ((uintptr_t)workspace % ALIGN) != 0 || workspace_bytes < L.total) return ASUCA_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    g->last_stream = s;
+    return g->d.prec == ASUCA_FP64
+               ? run_record<double>(g, initial, tendencies, dt, nsteps, branches_dev, (char *)workspace, s)
+               : run_record<float>(g, initial, tendencies, dt, nsteps, branches_dev, (char *)workspace, s);
 }
 
 asuca_status asuca_get_status(asuca_grid *g) {

@@ -57,6 +57,7 @@ struct StageParams {
     int *status;            // device status word (mapped host memory)
     int nx, ny, nz, lim;
     int tma_in, out_padded;
+    uint8_t *branch;        // when recording: [F-1][nz][ny][nx] branch bytes (2 bits per direction)
     long long plane;        // nx * ny
     long long opitch, oplane;   // padded output: row pitch and level stride (elements)
     T cdt, rdx, rdy;
@@ -204,6 +205,46 @@ __device__ __forceinline__ T face_fast(T pm1, T p0, T p1, T p2, bool u, T h) {
     T m = fmin(x + x, fmin((a + T(2) * x) * T(1.0 / 3.0), a + a));
     m = fmax(m, T(0));
     return c + h * copysign(m, dfar);
+}
+
+// The same face value, also returning the limiter branch taken: 0 zero,
+// 1 "2r", 2 "kappa=1/3", 3 "cap 2" (a tie keeps the earlier branch).  The
+// adjoint differentiates each face along the branch its forward pass took.
+template <int LIM, typename T>
+__device__ __forceinline__ T face_fast_br(T pm1, T p0, T p1, T p2, bool u, T h, int &br) {
+    const T c = u ? p0 : p1;
+    if (LIM == ASUCA_LIM_UPWIND1) {
+        br = 0;
+        return c;
+    }
+    const T dmid = p1 - p0;
+    const T dfar = (u ? p0 : p2) - (u ? pm1 : p1);
+    if (LIM == ASUCA_LIM_LINEAR) {
+        br = 2;
+        return c + h * ((dfar + T(2) * dmid) * T(1.0 / 3.0));
+    }
+    const T x = sign_transfer(dmid, dfar);
+    const T a = fabs(dfar);
+    const T t1 = x + x, t2 = (a + T(2) * x) * T(1.0 / 3.0), t3 = a + a;
+    T m = t1;
+    br = 1;
+    if (t2 < m) { m = t2; br = 2; }
+    if (t3 < m) { m = t3; br = 3; }
+    if (!(x > T(0) && a > T(0))) { m = T(0); br = 0; }
+    return c + h * copysign(m, dfar);
+}
+
+// d face / d phi at the stencil cells (pm1, p0, p1, p2) for upwind predicate u
+// and branch br, whose increment is L = a d0 + b d1 with (a, b) = (0, 0),
+// (0, 2), (1/3, 2/3), (2, 0):  u: face = p0 + (a (p0 - pm1) + b (p1 - p0)) / 2,
+// !u: face = p1 + (a (p1 - p2) + b (p0 - p1)) / 2.
+template <typename T>
+__device__ __forceinline__ T face_coef(bool u, int br, int q) {
+    const T a = br == 2 ? T(1.0 / 3.0) : (br == 3 ? T(2) : T(0));
+    const T b = br == 1 ? T(2) : (br == 2 ? T(2.0 / 3.0) : T(0));
+    const T up = T(1) + T(0.5) * a - T(0.5) * b;
+    if (u) return q == 0 ? T(-0.5) * a : (q == 1 ? up : (q == 2 ? T(0.5) * b : T(0)));
+    return q == 0 ? T(0) : (q == 1 ? T(0.5) * b : (q == 2 ? up : T(-0.5) * a));
 }
 
 // ------------------------------------------------------------------ launchers

@@ -94,7 +94,7 @@ __device__ __forceinline__ void cp_async_wait() {
 
 // ------------------------------------------------------------------ the kernel
 
-template <typename T, int NF, int LIM>
+template <typename T, int NF, int LIM, bool REC>
 __global__ void __launch_bounds__(32 * StageShape<T, NF>::TY, StageShape<T, NF>::MIN_BLOCKS)
     stage_kernel(const __grid_constant__ StageParams<T> p) {
     using S = StageShape<T, NF>;
@@ -278,10 +278,18 @@ __global__ void __launch_bounds__(32 * StageShape<T, NF>::TY, StageShape<T, NF>:
         for (int f = 0; f < NT; f++) {
             const int fo = (f + 1) * FE;
             const T c = Sk[fo + cc];
-            xp[f] = mup * face_fast<LIM>(Sk[fo + cc - 1], c, Sk[fo + cc + 1], Sk[fo + cc + 2], ux, hx);
-            yp[f] = mvp * face_fast<LIM>(Sk[fo + cc - SX], c, Sk[fo + cc + SX], Sk[fo + cc + 2 * SX], uy, hy);
+            if (REC) {
+                int bx, by, bz = 0;
+                xp[f] = mup * face_fast_br<LIM>(Sk[fo + cc - 1], c, Sk[fo + cc + 1], Sk[fo + cc + 2], ux, hx, bx);
+                yp[f] = mvp * face_fast_br<LIM>(Sk[fo + cc - SX], c, Sk[fo + cc + SX], Sk[fo + cc + 2 * SX], uy, hy, by);
+                zp[f] = top ? T(0) : mwp * face_fast_br<LIM>(Skm[fo + cc], c, Skp[fo + cc], Skp2[fo + cc], uz, hz, bz);
+                if (valid) p.branch[(long long)f * nz * plane + (long long)k * plane + own] = (uint8_t)(bx | (by << 2) | (bz << 4));
+            } else {
+                xp[f] = mup * face_fast<LIM>(Sk[fo + cc - 1], c, Sk[fo + cc + 1], Sk[fo + cc + 2], ux, hx);
+                yp[f] = mvp * face_fast<LIM>(Sk[fo + cc - SX], c, Sk[fo + cc + SX], Sk[fo + cc + 2 * SX], uy, hy);
+                zp[f] = top ? T(0) : mwp * face_fast<LIM>(Skm[fo + cc], c, Skp[fo + cc], Skp2[fo + cc], uz, hz);
+            }
             ysm[(f * (TY + 1) + ty + 1) * TX + tx] = yp[f];
-            zp[f] = top ? T(0) : mwp * face_fast<LIM>(Skm[fo + cc], c, Skp[fo + cc], Skp2[fo + cc], uz, hz);
         }
         {
             const bool ub = meb >= T(0), ul = mel >= T(0);
@@ -347,20 +355,25 @@ __global__ void __launch_bounds__(32 * StageShape<T, NF>::TY, StageShape<T, NF>:
     if (!tma) cp_async_wait<0>();
 }
 
-template <typename T, int NF, int LIM>
-static cudaError_t launch_lim(const StageParams<T> &p, cudaStream_t s) {
+template <typename T, int NF, int LIM, bool REC>
+static cudaError_t launch_rec(const StageParams<T> &p, cudaStream_t s) {
     using S = StageShape<T, NF>;
     static bool attr_set = false;   // one attribute call per instantiation
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(stage_kernel<T, NF, LIM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)S::SMEM_BYTES);
+        cudaError_t e = cudaFuncSetAttribute(stage_kernel<T, NF, LIM, REC>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM_BYTES);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
     dim3 block(S::TX, S::TY);
     dim3 grid((p.nx + S::TX - 1) / S::TX, (p.ny + S::TY - 1) / S::TY);
-    stage_kernel<T, NF, LIM><<<grid, block, S::SMEM_BYTES, s>>>(p);
+    stage_kernel<T, NF, LIM, REC><<<grid, block, S::SMEM_BYTES, s>>>(p);
     return cudaGetLastError();
+}
+
+template <typename T, int NF, int LIM>
+static cudaError_t launch_lim(const StageParams<T> &p, cudaStream_t s) {
+    return p.branch ? launch_rec<T, NF, LIM, true>(p, s) : launch_rec<T, NF, LIM, false>(p, s);
 }
 
 template <typename T, int NF>

@@ -1,0 +1,228 @@
+"""GPU adjoint (asuca_adjoint_step) against the oracle and against the forward map.
+
+* FP64 adjoint vs the oracle's FP64 adjoint, element by element (1e-11
+  relative), with the oracle linearised along the limiter branches the GPU
+  forward pass recorded.  Where a limiter's arguments are pure rounding noise
+  (theta is horizontally uniform away from its bubbles) the two forward passes
+  can legitimately take different branches, and each adjoint is the exact
+  transpose of its own forward pass; fixing the branches compares the
+  transposes themselves.  The fraction of faces whose branch differs is
+  checked to stay small;
+* results independent of the checkpoint interval (bit for bit);
+* dot-product test between the oracle's tangent-linear model and the GPU adjoint;
+* central differences of J = 1/2 sum (q - q_target)^2 through the GPU forward
+  (eps = 1e-6, 20 seeded directions scaled by field RMS, relative 1e-6), with
+  the Koren limiter on a grid where kink-free directions exist (checked with the
+  recorded branches), and on the 128x128x58, 4-tracer, 50-step adjoint workload
+  with the unlimited kappa=1/3 scheme, which has no limiter kinks;
+* torch.autograd.gradcheck through AdjointFn on an 8x8x6 grid in FP64;
+* the FP32 adjoint against the FP64 adjoint.
+"""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def asuca():
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1710_08616_gb300 as a
+    torch.cuda.set_device(0)
+    return a
+
+
+def _rel(got, ref):
+    return (np.linalg.norm(got - ref) / max(np.linalg.norm(ref), 1e-300),
+            np.abs(got - ref).max() / max(np.abs(ref).max(), 1e-300))
+
+
+def _gpu_branches(asuca, case, nsteps, lim=0, tend=None, prec=0):
+    """GPU-recorded branch bytes in the oracle's layout [nsteps][3][F][nz][ny][nx]."""
+    import torch
+    g = asuca.Grid.from_case(case, prec=prec, lim=lim)
+    st = asuca.State.from_case(case, prec=prec)
+    td = None if tend is None else torch.tensor(tend, dtype=g.torch_dtype, device="cuda")
+    b = asuca.record_branches(g, st, case.dt, nsteps, tendencies=td).cpu().numpy()
+    out = np.zeros((nsteps, 3, case.nfields) + b.shape[3:], dtype=np.uint8)
+    out[:, :, 1:] = b
+    return out
+
+
+def _gpu_adjoint(asuca, case, lam, nsteps, K, prec=0, lim=0, tend=None):
+    import torch
+    g = asuca.Grid.from_case(case, prec=prec, lim=lim)
+    st = asuca.State.from_case(case, prec=prec)
+    dt_ = g.torch_dtype
+    td = None if tend is None else torch.tensor(tend, dtype=dt_, device="cuda")
+    l = torch.tensor(lam, dtype=dt_, device="cuda")
+    g0, gmu, gmv, gmw = asuca.adjoint_step(g, st, case.dt, nsteps, l, checkpoint_every=K, tendencies=td)
+    torch.cuda.synchronize()
+    assert asuca.get_status(g) == asuca.OK
+    f = lambda t: t.double().cpu().numpy()
+    return f(g0), f(gmu), f(gmv), f(gmw)
+
+
+@pytest.mark.parametrize("lim", [0, 1, 2])
+@pytest.mark.parametrize("shape,ntr,nsteps", [((20, 16, 10), 3, 5), ((37, 13, 7), 2, 4), ((32, 32, 16), 3, 3)])
+def test_adjoint_fp64_matches_oracle(asuca, lim, shape, ntr, nsteps):
+    nx, ny, nz = shape
+    c = gen.make_case(nx, ny, nz, ntr, seed=100 + nx)
+    rng = np.random.default_rng(nx)
+    lam = rng.standard_normal(c.state().shape)
+    tend = rng.uniform(-1e-6, 1e-6, (1 + ntr, nz, ny, nx)) if nx == 37 else None
+    og = oracle.Grid.from_case(c, lim=lim)
+    br = _gpu_branches(asuca, c, nsteps, lim=lim, tend=tend)
+    own = oracle.trajectory_branches(og, c.state(), c.mu, c.mv, c.mw, c.dt, nsteps, tend=tend)
+    assert np.mean(br != own) <= 0.05
+    ref = oracle.step_adj(og, c.state(), c.mu, c.mv, c.mw, c.dt, nsteps, lam, tend=tend, traj_br=br)
+    got = _gpu_adjoint(asuca, c, lam, nsteps, nsteps, lim=lim, tend=tend)
+    for name, a, b in zip(("lam0", "gmu", "gmv", "gmw"), got, ref):
+        l2, mx = _rel(a, b)
+        assert l2 <= 1e-11 and mx <= 1e-11, (name, l2, mx)
+
+
+def test_adjoint_independent_of_checkpoint_interval(asuca):
+    c = gen.make_case(24, 20, 12, 2, seed=3)
+    lam = np.random.default_rng(1).standard_normal(c.state().shape)
+    a = _gpu_adjoint(asuca, c, lam, 7, 1)
+    for K in (3, 10):
+        b = _gpu_adjoint(asuca, c, lam, 7, K)
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
+
+
+def test_dot_product_oracle_tangent_linear_vs_gpu_adjoint(asuca):
+    c = gen.make_case(20, 16, 10, 3, seed=21)
+    og = oracle.Grid.from_case(c)
+    rng = np.random.default_rng(5)
+    Y = c.state()
+    dY = rng.standard_normal(Y.shape) * np.sqrt(np.mean(Y ** 2, axis=(1, 2, 3)))[:, None, None, None]
+    dmu = rng.standard_normal(c.mu.shape) * 20
+    dmv = rng.standard_normal(c.mv.shape) * 20
+    dmw = rng.standard_normal(c.mw.shape) * 0.1
+    dmw[0] = dmw[-1] = 0
+    lam = rng.standard_normal(Y.shape)
+    n = 4
+    br = _gpu_branches(asuca, c, n)
+    tl = oracle.step_tl(og, Y, c.mu, c.mv, c.mw, c.dt, n, dY, dmu, dmv, dmw, traj_br=br)
+    g0, gmu, gmv, gmw = _gpu_adjoint(asuca, c, lam, n, n)
+    lhs = float(np.sum(tl * lam))
+    rhs = float(np.sum(dY * g0) + np.sum(dmu * gmu) + np.sum(dmv * gmv) + np.sum(dmw * gmw))
+    assert abs(lhs - rhs) <= 1e-11 * max(abs(lhs), abs(rhs))
+
+
+def _fd_check(asuca, case, nsteps, lim, K, ndir=20, check_kinks=True, max_draws=60):
+    import torch
+    g = asuca.Grid.from_case(case, prec=asuca.FP64, lim=lim)
+    st0 = asuca.State.from_case(case, prec=asuca.FP64)
+    rng = np.random.default_rng(2024)
+    q_t = torch.tensor(np.clip(case.rhoq / case.rho + 0.002 * rng.standard_normal(case.rhoq.shape), 0, None),
+                       device="cuda")
+
+    def run(dq, dmu, dmv, dmw, eps):
+        st = asuca.State(st0.rho.clone(), st0.rhotheta.clone(), (st0.rhoq + eps * dq).contiguous(),
+                         (st0.mu + eps * dmu).contiguous(), (st0.mv + eps * dmv).contiguous(),
+                         (st0.mw + eps * dmw).contiguous())
+        return st
+
+    def J(st):
+        s2 = st.clone()
+        asuca.step(g, s2, case.dt, nsteps)
+        r = s2.rhoq / s2.rho - q_t
+        return 0.5 * float(torch.sum(r * r)), s2
+
+    J0, sN = J(st0)
+    r = sN.rhoq / sN.rho - q_t
+    lam = torch.zeros((g.nfields,) + tuple(st0.rho.shape), dtype=torch.float64, device="cuda")
+    lam[2:] = r / sN.rho
+    lam[0] = -torch.sum(r * sN.rhoq / sN.rho, 0) / sN.rho
+    g0, gmu, gmv, gmw = asuca.adjoint_step(g, st0, case.dt, nsteps, lam.contiguous(), checkpoint_every=K)
+    b0 = asuca.record_branches(g, st0, case.dt, nsteps)[:, :, 1:] if check_kinks else None
+    rms = lambda t: float(torch.sqrt(torch.mean(t * t)))
+    eps = 1e-6
+    ok = draws = 0
+    while ok < ndir and draws < max_draws:
+        draws += 1
+        dq = torch.randn(st0.rhoq.shape, generator=None, dtype=torch.float64, device="cuda") * rms(st0.rhoq)
+        dmu = torch.randn(st0.mu.shape, dtype=torch.float64, device="cuda") * rms(st0.mu)
+        dmv = torch.randn(st0.mv.shape, dtype=torch.float64, device="cuda") * rms(st0.mv)
+        dmw = torch.randn(st0.mw.shape, dtype=torch.float64, device="cuda") * rms(st0.mw)
+        dmw[0] = 0
+        dmw[-1] = 0
+        sp, sm = run(dq, dmu, dmv, dmw, eps), run(dq, dmu, dmv, dmw, -eps)
+        kinked = False
+        for M in ("mu", "mv", "mw"):
+            if bool((torch.signbit(getattr(sp, M)) != torch.signbit(getattr(st0, M))).any()) or \
+                    bool((torch.signbit(getattr(sm, M)) != torch.signbit(getattr(st0, M))).any()):
+                kinked = True
+        if check_kinks and not kinked:
+            for s_ in (sp, sm):
+                if not torch.equal(asuca.record_branches(g, s_, case.dt, nsteps)[:, :, 1:], b0):
+                    kinked = True
+                    break
+        if kinked:
+            continue
+        fd = (J(sp)[0] - J(sm)[0]) / (2 * eps)
+        ad = float(torch.sum(dq * g0[2:]) + torch.sum(dmu * gmu) + torch.sum(dmv * gmv) + torch.sum(dmw * gmw))
+        assert abs(fd - ad) <= 1e-6 * abs(ad), (fd, ad)
+        ok += 1
+    return ok, draws
+
+
+def test_fd_gradient_koren_kink_free_directions(asuca):
+    import torch
+    torch.manual_seed(7)
+    # white-noise directions meet a limiter kink somewhere once the grid and the
+    # step count grow (about one near-kink face per 5e4 face evaluations here),
+    # so the Koren check runs on a grid where most directions stay kink-free
+    c = gen.make_case(12, 10, 8, 2, seed=8, smooth_tracers=True)
+    ok, draws = _fd_check(asuca, c, 3, asuca.LIM_KOREN, 2, max_draws=100)
+    assert ok >= 10, f"{ok} kink-free directions in {draws}"
+
+
+def test_fd_gradient_adjoint_workload_128x128x58_50_steps_linear(asuca):
+    import torch
+    torch.manual_seed(11)
+    c = gen.make_config_case("adjoint_128x128x58")
+    # about 70% of white-noise directions flip the sign of some of the 2.8M
+    # face mass fluxes (a kink of the upwind choice); those are redrawn
+    ok, draws = _fd_check(asuca, c, 50, asuca.LIM_LINEAR, 10, check_kinks=False, max_draws=150)
+    assert ok == 20, f"{ok} of 20 directions usable in {draws}"
+
+
+def test_gradcheck_through_autograd_function(asuca):
+    import torch
+    c = gen.make_case(8, 8, 6, 2, seed=31, smooth_tracers=True)
+    g = asuca.Grid.from_case(c, prec=asuca.FP64, lim=asuca.LIM_LINEAR)
+    st = asuca.State.from_case(c, prec=asuca.FP64)
+    q0 = st.rhoq.clone().requires_grad_(True)
+    mu = st.mu.clone().requires_grad_(True)
+    Fn = asuca.AdjointFn
+
+    def f(q, m):
+        _, _, qn = Fn.apply(st.rho, st.rhotheta, q, m, st.mv, st.mw, g, c.dt, 2, 1)
+        return qn
+
+    assert torch.autograd.gradcheck(f, (q0, mu), eps=1e-6, atol=1e-9, rtol=1e-6)
+
+
+def test_fp32_adjoint_against_oracle_along_its_branches(asuca):
+    """The FP32 adjoint linearises the FP32 forward pass, whose branches differ
+    from the FP64 pass at faces whose limiter arguments are rounding noise; it is
+    compared with the FP64 oracle adjoint taken along the FP32 pass's branches."""
+    c = gen.make_case(32, 24, 16, 3, seed=41)
+    lam = np.random.default_rng(2).standard_normal(c.state().shape)
+    n = 5
+    br = _gpu_branches(asuca, c, n, prec=1)
+    og = oracle.Grid.from_case(c)
+    ref = oracle.step_adj(og, c.state(), c.mu, c.mv, c.mw, c.dt, n, lam, traj_br=br)
+    a32 = _gpu_adjoint(asuca, c, lam, n, n, prec=1)
+    for name, x, y in zip(("lam0", "gmu", "gmv", "gmw"), a32, ref):
+        l2, _ = _rel(x, y)
+        assert l2 <= 1e-4, (name, l2)
