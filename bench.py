@@ -210,6 +210,55 @@ def _time_steps(asuca, g, st, dt, ws_t, bud, steps, warmup, world, profile=False
     return ms, prof
 
 
+def adjoint_cost(asuca, dev, reps=3):
+    """Wall time of asuca_adjoint_step (checkpointed recompute + reverse) over the
+    wall time of asuca_step for the same 50 steps, on the 128x128x58, 4-tracer
+    workload with checkpoints every 10 steps; FP64 and FP32."""
+    import torch
+    import gen
+    case = gen.make_config_case("adjoint_128x128x58")
+    nsteps, K = gen.CONFIGS["adjoint_128x128x58"]["nsteps"], 10
+    out = {"workload": "adjoint_128x128x58", "nsteps": nsteps, "checkpoint_every": K}
+    for name, prec in (("fp64", asuca.FP64), ("fp32", asuca.FP32_MIXED)):
+        g = asuca.Grid.from_case(case, prec=prec)
+        st0 = asuca.State.from_case(case, prec=prec, device=dev)
+        ws = g.workspace(device=dev)
+        nadj = asuca.adjoint_workspace_bytes(g, nsteps, K)
+        wsa = torch.empty(nadj, dtype=torch.uint8, device=dev)
+        lam = torch.randn((case.nfields,) + tuple(st0.rho.shape), dtype=g.torch_dtype, device=dev).contiguous()
+
+        def fwd():
+            s_ = st0.clone()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            asuca.step(g, s_, case.dt, nsteps, workspace=ws)
+            e1.record()
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1)
+
+        def adj():
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            asuca.adjoint_step(g, st0, case.dt, nsteps, lam, checkpoint_every=K, workspace=wsa)
+            e1.record()
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1)
+
+        fwd(); adj()
+        tf = min(fwd() for _ in range(reps))
+        asuca.profile_enable(g, True)
+        ta = min(adj() for _ in range(reps))
+        prof = asuca.profile_read(g)
+        asuca.profile_enable(g, False)
+        names = {0: "stage", 1: "column", 2: "budget_reduce", 3: "adj_stage", 4: "adj_column"}
+        out[name] = {"forward_ms": tf, "adjoint_ms": ta, "adjoint_over_forward": ta / tf,
+                     "forward_plus_backward_over_forward": (tf + ta) / tf,
+                     "adjoint_kernels_ms_per_call": {names.get(k, str(k)): v[0] / reps for k, v in prof.items()}}
+        del st0, ws, wsa, lam
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -323,6 +372,10 @@ def run_ours(args):
                 "kernels": {kinds.get(k, str(k)): {"launches": n, "avg_ms": t / n} for k, (t, n) in prof64.items()}}
         del st64, ws64
 
+    adjoint = None
+    if not args.no_adjoint:
+        adjoint = adjoint_cost(asuca, dev)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_oracle_rate()
@@ -337,7 +390,7 @@ def run_ours(args):
                           "limiter": "koren", "l2": "inputs larger than L2 (2.4 GB state), no flush",
                           "parallelism": f"{world} independent replica(s), one per GPU"},
                "clocks": clocks, "gpu_launches": 5 * args.steps, "roofline": roofline,
-               "e2e": e2e, "fp64": fp64,
+               "e2e": e2e, "fp64": fp64, "adjoint": adjoint,
                "fp32_over_fp64_speedup": (value / fp64["value"]) if fp64 else None,
                "cpu_baseline": cpu}
         print(json.dumps(out), flush=True)
@@ -359,6 +412,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

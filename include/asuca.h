@@ -146,6 +146,35 @@ asuca_status asuca_adjoint_step(asuca_grid *grid, const asuca_state *initial, co
                                 void *grad_mu, void *grad_mv, void *grad_mw, void *workspace,
                                 size_t workspace_bytes, void *cuda_stream);
 
+/* ---- ensemble -------------------------------------------------------------
+ * Members are grids with the same nz, number of tracers, precision and
+ * limiter and any horizontal size; they are advanced together by one
+ * persistent cooperative kernel per call (three stage phases and one column
+ * phase per step, each phase a flattened list of (member, tile) or (member,
+ * column) work items, separated by device-wide barriers whose waits give up
+ * after about one second and report ASUCA_ERR_TIMEOUT).  Members never share
+ * a tile, so every member's result equals asuca_step on that member alone.
+ * On a non-default stream that is not already being captured, the launch
+ * sequence of a call (parameter upload, resets, the persistent kernel, the
+ * per-member budget kernels) is captured once into a CUDA graph, cached by
+ * its arguments (up to four), and replayed by later calls with the same
+ * arguments. */
+size_t asuca_ensemble_workspace_bytes(asuca_grid *const *grids, int nmembers);
+
+/* states[m] and dts[m] belong to grids[m]; budgets_dev, if not NULL, receives
+ * nmembers x (N + 3) doubles, member-major, as for asuca_step. */
+asuca_status asuca_ensemble_step(asuca_grid *const *grids, asuca_state *states, const double *dts, int nmembers,
+                                 int nsteps, void *workspace, size_t workspace_bytes, double *budgets_dev,
+                                 void *cuda_stream);
+
+/* ---- tuning knobs (set by the autotuner) --------------------------------- */
+typedef enum {
+    ASUCA_TUNE_COL_BLOCKS_PER_SM = 0,   /* resident column-kernel blocks per SM (1..16); sizes the column scratch */
+    ASUCA_TUNE_BARRIER_EXTRA = 1        /* test hook: the ensemble barrier waits for this many extra CTAs (0) */
+} asuca_tune_key;
+asuca_status asuca_set_tuning(asuca_grid *grid, int key, int value);
+int asuca_get_tuning(const asuca_grid *grid, int key);
+
 /* Synchronise the stream of the last call on this grid, return and clear
  * the device status word (ASUCA_OK when no device error was recorded). */
 asuca_status asuca_get_status(asuca_grid *grid);
@@ -218,6 +247,7 @@ typedef enum {
     ASUCA_KERNEL_REDUCE = 2,    /* final budget reduction */
     ASUCA_KERNEL_ADJ_STAGE = 3, /* transpose of one RK stage */
     ASUCA_KERNEL_ADJ_COLUMN = 4,/* transpose of the column pass */
+    ASUCA_KERNEL_ENSEMBLE = 5,  /* persistent ensemble kernel (all steps of a call) */
     ASUCA_KERNEL_KINDS = 8
 } asuca_kernel_kind;
 

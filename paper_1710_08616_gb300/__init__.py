@@ -76,11 +76,18 @@ SIGNATURES = {
                                           ctypes.c_int, _VP, _VP, _VP, _VP, _VP, _VP, ctypes.c_size_t, _VP]),
     "asuca_debug_record_branches": (ctypes.c_int, [_VP, ctypes.POINTER(StateStruct), _VP, ctypes.c_double,
                                                    ctypes.c_int, _VP, _VP, ctypes.c_size_t, _VP]),
+    "asuca_ensemble_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(_VP), ctypes.c_int]),
+    "asuca_ensemble_step": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.POINTER(StateStruct),
+                                           ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_int, _VP,
+                                           ctypes.c_size_t, _VP, _VP]),
+    "asuca_set_tuning": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int]),
+    "asuca_get_tuning": (ctypes.c_int, [_VP, ctypes.c_int]),
     "asuca_profile_enable": (ctypes.c_int, [_VP, ctypes.c_int]),
     "asuca_profile_read": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
 }
-KERNEL_STAGE, KERNEL_COLUMN, KERNEL_REDUCE, KERNEL_ADJ_STAGE, KERNEL_ADJ_COLUMN = 0, 1, 2, 3, 4
+KERNEL_STAGE, KERNEL_COLUMN, KERNEL_REDUCE, KERNEL_ADJ_STAGE, KERNEL_ADJ_COLUMN, KERNEL_ENSEMBLE = 0, 1, 2, 3, 4, 5
+TUNE_COL_BLOCKS_PER_SM, TUNE_BARRIER_EXTRA = 0, 1
 KERNEL_KINDS = 8
 
 
@@ -383,3 +390,63 @@ def __getattr__(name):
             _ADJOINT_FN = _autograd_function()
         return _ADJOINT_FN
     raise AttributeError(name)
+
+
+# ---------------------------------------------------------------- ensemble and tuning
+
+def set_tuning(grid: Grid, key: int, value: int):
+    _check(lib().asuca_set_tuning(grid.handle, int(key), int(value)), "asuca_set_tuning")
+
+
+def get_tuning(grid: Grid, key: int) -> int:
+    return int(lib().asuca_get_tuning(grid.handle, int(key)))
+
+
+def _grid_array(grids):
+    arr = (_VP * len(grids))()
+    for m, g in enumerate(grids):
+        arr[m] = g.handle.value if isinstance(g.handle, ctypes.c_void_p) else g.handle
+    return arr
+
+
+def ensemble_workspace_bytes(grids) -> int:
+    return int(lib().asuca_ensemble_workspace_bytes(_grid_array(grids), len(grids)))
+
+
+_side_streams = {}
+
+
+def ensemble_step(grids, states, dts, nsteps: int, *, workspace=None, budgets=None, stream=None):
+    """Advance every member by nsteps in one persistent launch (asuca_ensemble_step).
+    Without an explicit stream the call runs on a side stream ordered after the
+    current stream, so that its launch sequence can be captured into (and later
+    replayed from) a CUDA graph.  Returns the budgets tensor [M][N+3] if asked."""
+    import torch
+    M = len(grids)
+    assert len(states) == M and len(dts) == M and M > 0
+    for g, st in zip(grids, states):
+        _check_state(g, st)
+    dev = states[0].rho.device
+    if workspace is None:
+        n = ensemble_workspace_bytes(grids)
+        if n == 0:
+            raise AsucaError(ERR_CUDA, "asuca_ensemble_workspace_bytes")
+        workspace = torch.empty(n, dtype=torch.uint8, device=dev)
+    if budgets is True:
+        budgets = torch.empty((M, grids[0].nfields + 1), dtype=torch.float64, device=dev)
+    sts = (StateStruct * M)(*[st.struct() for st in states])
+    dd = (ctypes.c_double * M)(*[float(x) for x in dts])
+    cur = torch.cuda.current_stream(dev)
+    run = stream
+    if run is None:
+        run = _side_streams.get(dev.index)
+        if run is None:
+            run = _side_streams[dev.index] = torch.cuda.Stream(device=dev)
+        run.wait_stream(cur)
+    _check(lib().asuca_ensemble_step(_grid_array(grids), sts, dd, M, int(nsteps), _ptr(workspace),
+                                     workspace.numel(), _ptr(budgets), ctypes.c_void_p(run.cuda_stream)),
+           "asuca_ensemble_step")
+    if stream is None:
+        cur.wait_stream(run)
+        workspace.record_stream(run)
+    return budgets

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "adjoint_params.cuh"
+#include "ensemble_params.cuh"
 #include "common.cuh"
 
 using namespace asuca;
@@ -19,6 +20,9 @@ struct asuca_grid {
     long long plane, cells;
     int device, nsm;
     int col_grid;                 // persistent column-kernel grid
+    int col_blocks_per_sm;        // tuning knob behind col_grid
+    int barrier_extra;            // test hook: extra arrivals the ensemble barrier waits for
+    std::vector<void *> *kept_pinned;   // parameter buffers referenced by a caller's captured graphs
     volatile int *status_host;    // pinned, mapped; the device writes error codes here
     int *status_dev;
     cudaStream_t last_stream;
@@ -43,6 +47,12 @@ int col_blocks_per_sm() {
 }
 
 size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
+
+void set_col_grid(asuca_grid *g) {
+    long long need = (g->plane + COL_TPB - 1) / COL_TPB;
+    long long cap = (long long)g->nsm * g->col_blocks_per_sm;
+    g->col_grid = (int)(need < cap ? need : cap);
+}
 
 size_t elem_size(const asuca_grid *g) { return g->d.prec == ASUCA_FP64 ? 8 : 4; }
 
@@ -335,14 +345,16 @@ asuca_status run_adjoint(asuca_grid *g, const asuca_state *init, const void *ten
     const size_t cb = (size_t)g->cells * sizeof(T);
     cudaError_t e = cudaSuccess;
     auto ck = [&](cudaError_t r) { if (r != cudaSuccess && e == cudaSuccess) e = r; };
-    // ---- forward pass from the initial state, keeping a checkpoint every K steps
+    // ---- forward pass from the initial state, keeping a checkpoint every K steps;
+    // the last segment is not checkpointed: it is recorded below straight from W
     T *Wf[MAXF];
     block_fields<T>(g, ws + L.W, Wf);
     T *init_f[MAXF];
     field_ptrs<T>(g, init->rho, init->rhotheta, init->rhoq, init_f);
     for (int f = 0; f < F; f++) ck(cudaMemcpyAsync(Wf[f], init_f[f], cb, cudaMemcpyDeviceToDevice, s));
     asuca_state Ws = block_state<T>(g, ws + L.W, init);
-    for (int n = 0; n < nsteps; n++) {
+    const int last_start = L.ncp > 0 ? (L.ncp - 1) * K : 0;
+    for (int n = 0; n < last_start; n++) {
         if (n % K == 0)
             ck(cudaMemcpyAsync(ws + L.ckpt + (size_t)(n / K) * align_up(L.ustate), ws + L.W, L.ustate,
                                cudaMemcpyDeviceToDevice, s));
@@ -350,6 +362,9 @@ asuca_status run_adjoint(asuca_grid *g, const asuca_state *init, const void *ten
         asuca_status r = run_step<T>(g, &Ws, tend, dt, 1, ws + L.step, nullptr, s);
         if (r != ASUCA_OK) return r;
     }
+    if (L.ncp > 0)
+        ck(cudaMemcpyAsync(ws + L.ckpt + (size_t)(L.ncp - 1) * align_up(L.ustate), ws + L.W, L.ustate,
+                           cudaMemcpyDeviceToDevice, s));
     // ---- adjoint accumulators
     const size_t mb = (size_t)g->cells * sizeof(T), mwb = (size_t)(g->d.nz + 1) * g->plane * sizeof(T);
     ck(cudaMemsetAsync(gmu, 0, mb, s));
@@ -533,6 +548,155 @@ asuca_status run_record(asuca_grid *g, const asuca_state *init, const void *tend
     return ASUCA_OK;
 }
 
+// ---- ensemble ------------------------------------------------------------
+
+struct EnsLayout {
+    size_t members, bar, per_member, partials, scratch, total;
+    std::vector<size_t> ystar, ystar2, precip;
+    int grid, threads;
+};
+
+template <typename T>
+cudaError_t ens_grid(const asuca_grid *g0, int *grid) {
+    EnsParams<T> dummy;
+    std::memset(&dummy, 0, sizeof(dummy));
+    return launch_ensemble<T>(dummy, g0->F, (int)g0->d.lim, 0, nullptr, grid);
+}
+
+bool ens_layout(asuca_grid *const *grids, int M, EnsLayout *L) {
+    const asuca_grid *g0 = grids[0];
+    int grid = 0;
+    cudaError_t e = g0->d.prec == ASUCA_FP64 ? ens_grid<double>(g0, &grid) : ens_grid<float>(g0, &grid);
+    if (e != cudaSuccess || grid <= 0) return false;
+    L->grid = grid;
+    L->threads = 32 * (g0->d.prec == ASUCA_FP64 ? StageShape<double, 2>::TY : StageShape<float, 2>::TY);
+    const size_t msize = g0->d.prec == ASUCA_FP64 ? sizeof(EnsMember<double>) : sizeof(EnsMember<float>);
+    size_t off = 0;
+    L->members = off;
+    off = align_up(off + (size_t)M * msize);
+    L->bar = off;
+    off = align_up(off + 2 * sizeof(unsigned));
+    L->ystar.resize(M);
+    L->ystar2.resize(M);
+    L->precip.resize(M);
+    int maxcol = 0;
+    for (int m = 0; m < M; m++) {
+        const size_t ps = (size_t)grids[m]->F * padded_field_elems(grids[m]) * elem_size(grids[m]);
+        L->ystar[m] = off;
+        off = align_up(off + ps);
+        L->ystar2[m] = off;
+        off = align_up(off + ps);
+        L->precip[m] = off;
+        off = align_up(off + (size_t)grids[m]->plane * sizeof(double));
+        if (grids[m]->col_grid > maxcol) maxcol = grids[m]->col_grid;
+    }
+    L->partials = off;
+    off = align_up(off + (size_t)maxcol * (g0->F + 1) * sizeof(double));
+    L->scratch = off;
+    off = align_up(off + (size_t)g0->d.nz * (g0->F + 1) * (size_t)grid * L->threads * sizeof(double));
+    L->total = off;
+    return true;
+}
+
+struct EnsGraph {
+    std::vector<unsigned char> key;
+    cudaGraphExec_t exec = nullptr;
+    void *staging = nullptr;
+};
+std::mutex g_ens_mu;
+EnsGraph g_ens_cache[4];
+int g_ens_next = 0;
+
+template <typename T>
+asuca_status ens_enqueue(asuca_grid *const *grids, asuca_state *states, const double *dts, int M, int nsteps,
+                         char *ws, const EnsLayout &L, double *budgets, void *staging, cudaStream_t s) {
+    asuca_grid *g0 = grids[0];
+    const int F = g0->F;
+    EnsMember<T> *mb = (EnsMember<T> *)staging;
+    long long tile0 = 0, col0 = 0;
+    using S = StageShape<T, 2>;
+    for (int m = 0; m < M; m++) {
+        asuca_grid *g = grids[m];
+        const double dt = dts[m];
+        std::memset((void *)&mb[m], 0, sizeof(EnsMember<T>));
+        T *yn[MAXF], *y1[MAXF], *y2[MAXF];
+        field_ptrs<T>(g, states[m].rho, states[m].rhotheta, states[m].rhoq, yn);
+        workspace_fields<T>(g, ws, L.ystar[m], y1);
+        workspace_fields<T>(g, ws, L.ystar2[m], y2);
+        CUtensorMap m1, m2;
+        if (encode_stage_map<T>(&m1, ws + L.ystar[m], F, g->d.nx, g->d.ny, g->d.nz) != cudaSuccess ||
+            encode_stage_map<T>(&m2, ws + L.ystar2[m], F, g->d.nx, g->d.ny, g->d.nz) != cudaSuccess)
+            return ASUCA_ERR_CUDA;
+        const T cdt[3] = {(T)(dt / 3.0), (T)(dt / 2.0), (T)dt};
+        for (int stg = 0; stg < 3; stg++) {
+            StageParams<T> sp = stage_params<T>(g, &states[m], nullptr);
+            sp.status = g0->status_dev;
+            sp.tma_in = stg > 0;
+            if (stg == 1) sp.tmap = m1;
+            if (stg == 2) sp.tmap = m2;
+            sp.out_padded = stg < 2;
+            T **out = stg == 0 ? y1 : (stg == 1 ? y2 : yn);
+            for (int f = 0; f < MAXF; f++) {
+                sp.yin[f] = yn[f];
+                sp.ybase[f] = yn[f];
+                sp.yout[f] = out[f];
+            }
+            sp.cdt = cdt[stg];
+            mb[m].stage[stg] = sp;
+        }
+        ColumnParams<T> cp = column_params<T>(g, dt);
+        for (int f = 0; f < MAXF; f++) cp.y[f] = yn[f];
+        cp.precip_col = (double *)(ws + L.precip[m]);
+        cp.budgets = 0;
+        mb[m].col = cp;
+        const int tx = (g->d.nx + S::TX - 1) / S::TX, ty = (g->d.ny + S::TY - 1) / S::TY;
+        mb[m].tiles_x = tx;
+        mb[m].tile0 = tile0;
+        mb[m].col0 = col0;
+        tile0 += (long long)tx * ty;
+        col0 += g->plane;
+    }
+    cudaError_t e = cudaMemcpyAsync(ws + L.members, staging, (size_t)M * sizeof(EnsMember<T>),
+                                    cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ws + L.bar, 0, 2 * sizeof(unsigned), s);
+    for (int m = 0; m < M && e == cudaSuccess; m++)
+        e = cudaMemsetAsync(ws + L.precip[m], 0, (size_t)grids[m]->plane * sizeof(double), s);
+    if (e != cudaSuccess) return ASUCA_ERR_CUDA;
+    EnsParams<T> ep;
+    std::memset(&ep, 0, sizeof(ep));
+    ep.members = (const EnsMember<T> *)(ws + L.members);
+    ep.nmembers = M;
+    ep.nsteps = nsteps;
+    ep.total_tiles = tile0;
+    ep.total_cols = col0;
+    ep.bar_count = (unsigned *)(ws + L.bar);
+    ep.bar_gen = ep.bar_count + 1;
+    ep.bar_extra = g0->barrier_extra;
+    ep.status = g0->status_dev;
+    ep.scratch = (double *)(ws + L.scratch);
+    if (nsteps > 0 &&
+        timed(g0, ASUCA_KERNEL_ENSEMBLE, s, [&] { return launch_ensemble<T>(ep, F, (int)g0->d.lim, L.grid, s, nullptr); }) !=
+            cudaSuccess)
+        return ASUCA_ERR_CUDA;
+    if (budgets) {
+        for (int m = 0; m < M; m++) {
+            asuca_grid *g = grids[m];
+            ColumnParams<T> cp = column_params<T>(g, dts[m]);
+            field_ptrs<T>(g, states[m].rho, states[m].rhotheta, states[m].rhoq, cp.y);
+            cp.do_phys = 0;
+            cp.budgets = 1;
+            cp.precip_col = (double *)(ws + L.precip[m]);
+            cp.partials = (double *)(ws + L.partials);
+            cp.nslots = col_slots(g);
+            if (launch_column<T>(cp, F, g->col_grid, COL_TPB, s) != cudaSuccess ||
+                launch_budget_reduce(cp.partials, g->col_grid, F + 1, F, g->d.dx * g->d.dy, budgets + (size_t)m * (F + 1),
+                                     g0->status_dev, s) != cudaSuccess)
+                return ASUCA_ERR_CUDA;
+        }
+    }
+    return ASUCA_OK;
+}
+
 }  // namespace
 
 // ---- column pass without a caller workspace ------------------------------
@@ -625,9 +789,8 @@ asuca_status asuca_init_grid(const asuca_grid_desc *desc, asuca_grid **out) {
         delete g;
         return ASUCA_ERR_CUDA;
     }
-    long long need = (g->plane + COL_TPB - 1) / COL_TPB;
-    long long cap = (long long)g->nsm * col_blocks_per_sm();
-    g->col_grid = (int)(need < cap ? need : cap);
+    g->col_blocks_per_sm = col_blocks_per_sm();
+    set_col_grid(g);
     void *h = nullptr;
     if (cudaHostAlloc(&h, 64, cudaHostAllocMapped) != cudaSuccess) {
         delete g;
@@ -649,6 +812,10 @@ asuca_status asuca_free_grid(asuca_grid *g) {
     if (!g) return ASUCA_ERR_ARG;
     if (g->status_host) cudaFreeHost((void *)g->status_host);
     for (int q = 0; q < g->prof_cap; q++) cudaEventDestroy(g->prof_ev[q]);
+    if (g->kept_pinned) {
+        for (void *p : *g->kept_pinned) cudaFreeHost(p);
+        delete g->kept_pinned;
+    }
     std::free(g->prof_ev);
     std::free(g->prof_kind);
     delete g;
@@ -702,6 +869,139 @@ asuca_status asuca_debug_record_branches(asuca_grid *g, const asuca_state *initi
     return g->d.prec == ASUCA_FP64
                ? run_record<double>(g, initial, tendencies, dt, nsteps, branches_dev, (char *)workspace, s)
                : run_record<float>(g, initial, tendencies, dt, nsteps, branches_dev, (char *)workspace, s);
+}
+
+size_t asuca_ensemble_workspace_bytes(asuca_grid *const *grids, int nmembers) {
+    if (!grids || nmembers <= 0 || !grids[0]) return 0;
+    EnsLayout L;
+    if (!ens_layout(grids, nmembers, &L)) return 0;
+    return L.total;
+}
+
+asuca_status asuca_ensemble_step(asuca_grid *const *grids, asuca_state *states, const double *dts, int nmembers,
+                                 int nsteps, void *workspace, size_t workspace_bytes, double *budgets_dev,
+                                 void *cuda_stream) {
+    if (!grids || !states || !dts || nmembers <= 0 || nsteps < 0) return ASUCA_ERR_ARG;
+    asuca_grid *g0 = grids[0];
+    if (!g0) return ASUCA_ERR_ARG;
+    for (int m = 0; m < nmembers; m++) {
+        const asuca_grid *g = grids[m];
+        if (!g || !state_ok(g, &states[m]) || !std::isfinite(dts[m]) || dts[m] < 0.0) return ASUCA_ERR_ARG;
+        if (g->F != g0->F || g->d.nz != g0->d.nz || g->d.prec != g0->d.prec || g->d.lim != g0->d.lim ||
+            g->device != g0->device)
+            return ASUCA_ERR_ARG;
+    }
+    asuca_status prev = take_status(g0);
+    if (prev != ASUCA_OK) return prev;
+    EnsLayout L;
+    if (!ens_layout(grids, nmembers, &L)) return ASUCA_ERR_CUDA;
+    if (!workspace || ((uintptr_t)workspace % ALIGN) != 0 || workspace_bytes < L.total) return ASUCA_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    g0->last_stream = s;
+    const size_t msize = g0->d.prec == ASUCA_FP64 ? sizeof(EnsMember<double>) : sizeof(EnsMember<float>);
+    // graph key: everything the captured launches depend on
+    std::vector<unsigned char> key;
+    auto put = [&](const void *p, size_t n) { key.insert(key.end(), (const unsigned char *)p, (const unsigned char *)p + n); };
+    put(&nmembers, sizeof(int));
+    put(&nsteps, sizeof(int));
+    put(&workspace, sizeof(void *));
+    put(&budgets_dev, sizeof(void *));
+    for (int m = 0; m < nmembers; m++) {
+        put(&grids[m], sizeof(void *));
+        put(&states[m], sizeof(asuca_state));
+        put(&dts[m], sizeof(double));
+        put(&grids[m]->col_grid, sizeof(int));
+        put(&grids[m]->d.nx, sizeof(int));
+        put(&grids[m]->d.ny, sizeof(int));
+        put(&grids[m]->barrier_extra, sizeof(int));
+    }
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (s != nullptr && cudaStreamIsCapturing(s, &cap) != cudaSuccess) return ASUCA_ERR_CUDA;
+    if (cap != cudaStreamCaptureStatusNone) {
+        // the caller is capturing: record the launches into the caller's graph; the
+        // parameter buffer its copy node reads is kept until the first grid is freed
+        void *pin = nullptr;
+        if (cudaHostAlloc(&pin, (size_t)nmembers * msize, cudaHostAllocDefault) != cudaSuccess) return ASUCA_ERR_CUDA;
+        if (!g0->kept_pinned) g0->kept_pinned = new (std::nothrow) std::vector<void *>();
+        if (!g0->kept_pinned) {
+            cudaFreeHost(pin);
+            return ASUCA_ERR_CUDA;
+        }
+        g0->kept_pinned->push_back(pin);
+        return g0->d.prec == ASUCA_FP64
+                   ? ens_enqueue<double>(grids, states, dts, nmembers, nsteps, (char *)workspace, L, budgets_dev, pin, s)
+                   : ens_enqueue<float>(grids, states, dts, nmembers, nsteps, (char *)workspace, L, budgets_dev, pin, s);
+    }
+    if (s == nullptr || g0->prof_on) {
+        // the legacy stream cannot be captured, and per-kernel profiling needs the
+        // event pairs: launch directly, then release the parameter buffer
+        void *pin = nullptr;
+        if (cudaHostAlloc(&pin, (size_t)nmembers * msize, cudaHostAllocDefault) != cudaSuccess) return ASUCA_ERR_CUDA;
+        asuca_status r = g0->d.prec == ASUCA_FP64
+                             ? ens_enqueue<double>(grids, states, dts, nmembers, nsteps, (char *)workspace, L, budgets_dev, pin, s)
+                             : ens_enqueue<float>(grids, states, dts, nmembers, nsteps, (char *)workspace, L, budgets_dev, pin, s);
+        if (cudaStreamSynchronize(s) != cudaSuccess && r == ASUCA_OK) r = ASUCA_ERR_CUDA;
+        cudaFreeHost(pin);
+        return r;
+    }
+    std::lock_guard<std::mutex> lock(g_ens_mu);
+    for (EnsGraph &c : g_ens_cache) {
+        if (c.exec && c.key == key) return cudaGraphLaunch(c.exec, s) == cudaSuccess ? ASUCA_OK : ASUCA_ERR_CUDA;
+    }
+    EnsGraph &c = g_ens_cache[g_ens_next];
+    g_ens_next = (g_ens_next + 1) % 4;
+    if (c.exec) {
+        cudaGraphExecDestroy(c.exec);
+        c.exec = nullptr;
+    }
+    if (c.staging) {
+        cudaFreeHost(c.staging);
+        c.staging = nullptr;
+    }
+    if (cudaHostAlloc(&c.staging, (size_t)nmembers * msize, cudaHostAllocDefault) != cudaSuccess) return ASUCA_ERR_CUDA;
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return ASUCA_ERR_CUDA;
+    asuca_status r = g0->d.prec == ASUCA_FP64
+                         ? ens_enqueue<double>(grids, states, dts, nmembers, nsteps, (char *)workspace, L, budgets_dev, c.staging, s)
+                         : ens_enqueue<float>(grids, states, dts, nmembers, nsteps, (char *)workspace, L, budgets_dev, c.staging, s);
+    cudaError_t ee = cudaStreamEndCapture(s, &graph);
+    if (r != ASUCA_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return r;
+    }
+    if (ee != cudaSuccess || cudaGraphInstantiate(&c.exec, graph, 0) != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        c.exec = nullptr;
+        return ASUCA_ERR_CUDA;
+    }
+    cudaGraphDestroy(graph);
+    c.key = key;
+    return cudaGraphLaunch(c.exec, s) == cudaSuccess ? ASUCA_OK : ASUCA_ERR_CUDA;
+}
+
+asuca_status asuca_set_tuning(asuca_grid *g, int key, int value) {
+    if (!g) return ASUCA_ERR_ARG;
+    switch (key) {
+        case ASUCA_TUNE_COL_BLOCKS_PER_SM:
+            if (value < 1 || value > 16) return ASUCA_ERR_ARG;
+            g->col_blocks_per_sm = value;
+            set_col_grid(g);
+            return ASUCA_OK;
+        case ASUCA_TUNE_BARRIER_EXTRA:
+            if (value < 0) return ASUCA_ERR_ARG;
+            g->barrier_extra = value;
+            return ASUCA_OK;
+        default: return ASUCA_ERR_ARG;
+    }
+}
+
+int asuca_get_tuning(const asuca_grid *g, int key) {
+    if (!g) return -1;
+    switch (key) {
+        case ASUCA_TUNE_COL_BLOCKS_PER_SM: return g->col_blocks_per_sm;
+        case ASUCA_TUNE_BARRIER_EXTRA: return g->barrier_extra;
+        default: return -1;
+    }
 }
 
 asuca_status asuca_get_status(asuca_grid *g) {

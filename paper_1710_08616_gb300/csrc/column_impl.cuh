@@ -1,0 +1,209 @@
+// Column physics (per-column device code), one thread per (i, j) column (the coarse per-column
+// granularity of Sec. 1.2 "Parallelization Granularity", Fig. 1 and 2), and
+// the FP64 budget sums.
+//
+// Per column, after the three RK stages (Lie splitting, once per long step):
+//   top-down pass, k = nz-1 .. 0:
+//     (i)   implicit theta relaxation   theta <- (theta + r theta_ref) / (1 + r)
+//     (ii)  implicit sedimentation      (rho q)_k <- ((rho q)_k dz_k + dt P_{k+1/2}) / (dz_k + dt v),
+//                                       P_{k-1/2} = v (rho q)_k; P_{-1/2} rains out
+//     (iii) forward elimination of the implicit vertical diffusion
+//           A phi = d, a_k = -g_{k-1/2}, c_k = -g_{k+1/2},
+//           b_k = rho_k dz_k + g_{k-1/2} + g_{k+1/2}, d_k = dz_k (rho phi)_k,
+//           run from the top down (the mirror of the textbook Thomas order),
+//           one factorisation shared by rho*theta and every tracer
+//   bottom-up pass: back substitution, (rho phi)_k = rho_k phi_k.
+// The elimination works on scaled unknowns so that each field costs one
+// FMA per level on the way down and one FMA plus one multiply on the way up:
+//   e_k = x_k + alpha_k e_{k+1},  alpha_k = g_{k+1/2} m_{k+1} dz_{k+1} / dz_k
+//   z_k = e_k + gamma_k z_{k-1},  gamma_k = g_{k-1/2} m_{k-1} dz_{k-1} / dz_k
+//   (rho phi)_k = sigma_k z_k,    sigma_k = rho_k dz_k m_k,   m_k = 1 / pivot_k
+// Per field and level that is two FP64 operations; the shared factorisation
+// costs about fifteen.  Float inputs are widened and the result narrowed on
+// the integer pipe (the hardware conversions issue on the slow FP64 pipe);
+// for float fields the final multiply by sigma_k is done in float.
+// (x_k is the incoming rho*phi; d''_k = dz_k m_k e_k and phi_k = dz_k m_k z_k
+// are the usual eliminated right-hand side and solution).  The whole solve
+// runs in double in both precisions; a float result is rounded once.
+//
+// The per-level e_k, m_k, gamma_k live in a scratch area indexed by the
+// thread's slot.  The grid is persistent (one resident wave, a grid-stride
+// loop over columns), so the scratch is as large as the columns in flight
+// and stays resident in L2 while each slot reuses it column after column.
+#pragma once
+
+#include "common.cuh"
+
+namespace asuca {
+
+// Budget partial of one column: sum_k f_k dz_k.  In double for the FP64 path;
+// for float fields the per-column sum is carried as a compensated float pair
+// (TwoProduct by FMA for f * dz_hi, Neumaier's compensated summation) and
+// widened once per column, which keeps double-precision accuracy without a
+// conversion and an FP64 operation per cell.
+template <typename T> struct ColSum;
+template <> struct ColSum<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double f, double dz, float, float) { s = fma(f, dz, s); }
+    __device__ __forceinline__ double value() const { return s; }
+};
+template <> struct ColSum<float> {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float f, double, float dz_hi, float dz_lo) {
+        const float p = f * dz_hi;
+        const float pe = fmaf(f, dz_hi, -p);          // exact error of the product
+        c = fmaf(f, dz_lo, c + pe);                   // small terms go to the compensation
+        const float t = s + p;
+        c += (fabsf(s) >= fabsf(p)) ? ((s - t) + p) : ((p - t) + s);
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return f2d_bits(s) + f2d_bits(c); }
+};
+
+template <typename T> __device__ __forceinline__ T scale_out(double z, double sigma, float sigma_f);
+// FP64 path: the rescaled unknown times sigma in double.
+template <> __device__ __forceinline__ double scale_out<double>(double z, double sigma, float) { return sigma * z; }
+// FP32 path: z rounded once to float (integer-pipe rounding), times sigma in float.
+template <> __device__ __forceinline__ float scale_out<float>(double z, double, float sigma_f) {
+    return d2f_bits(z) * sigma_f;
+}
+
+// The column pass of one column (col = j * nx + i); sc points at the
+// thread's scratch slot (stride nslots between entries).  cs receives the
+// column's budget partials when p.budgets is set.
+template <typename T, int NF>
+__device__ __forceinline__ void column_one(const ColumnParams<T> &p, long long col, double *sc, long long nslots,
+                                           ColSum<T> (&cs)[NF]) {
+    constexpr int NT = NF - 1;
+    constexpr int NQ = NF + 1;                    // m, gamma, e[NT]
+    const int nz = p.nz;
+    const long long plane = p.plane;
+    if (p.do_phys) {
+        double g_hi = 0.0, m_up = 0.0;
+        double e_up[NT];
+#pragma unroll
+        for (int f = 0; f < NT; f++) e_up[f] = 0.0;
+        T P = T(0);
+        long long o = (long long)(nz - 1) * plane + col;
+        T rho = p.y[0][o];
+        T rho_dn = (nz > 1) ? p.y[0][o - plane] : T(0);
+        double rd = to_f64(rho);
+        T x[NT];
+#pragma unroll
+        for (int f = 0; f < NT; f++) x[f] = p.y[f + 1][o];
+        for (int k = nz - 1; k >= 0; k--, o -= plane) {
+            // prefetch the level below (and rho two below) while this level computes
+            T xn[NT];
+            T rho_dn2 = T(0);
+            if (k > 0) {
+#pragma unroll
+                for (int f = 0; f < NT; f++) xn[f] = p.y[f + 1][o - plane];
+                if (k > 1) rho_dn2 = p.y[0][o - 2 * plane];
+            }
+            // (i) relaxation of theta
+            if (p.do_relax) {
+                T th = x[0] / rho;
+                th = (th + p.relax_r * p.thref[k]) * p.relax_inv;
+                x[0] = rho * th;
+            }
+            // (ii) sedimentation of one tracer, top-down
+            if (p.do_sed) {
+#pragma unroll
+                for (int f = 1; f < NT; f++) {
+                    if (f + 1 == p.sed) {
+                        x[f] = (x[f] * p.dzT[k] + p.sed_dt * P) * p.sedr[k];
+                        P = p.sed_v * x[f];
+                    }
+                }
+                if (k == 0) p.precip_col[col] += p.dt * to_f64(P) * p.dxdy;
+            }
+            if (p.budgets) cs[0].add(rho, p.dz[k], p.dzT[k], p.dzlo[k]);
+            const double rd_dn = (k > 0) ? to_f64(rho_dn) : 0.0;
+            if (p.do_diff) {
+                // (iii) forward elimination, top-down, on scaled unknowns
+                const double g_lo = (k > 0) ? p.kc[k - 1] * (rd_dn + rd) : 0.0;
+                const double rdz = rd * p.dz[k];
+                const double b = rdz + (g_lo + g_hi);
+                const double t = g_hi * m_up;
+                const double m = rcp_newton(fma(-g_hi, t, b));
+                const double alpha = t * p.dzr_up[k];
+                sc[(long long)(k * NQ + 0) * nslots] = m;
+                if (k < nz - 1) sc[(long long)((k + 1) * NQ + 1) * nslots] = g_hi * m * p.dzr_dn[k + 1];
+#pragma unroll
+                for (int f = 0; f < NT; f++) {
+                    const double e = fma(alpha, e_up[f], to_f64(x[f]));
+                    sc[(long long)(k * NQ + 2 + f) * nslots] = e;
+                    e_up[f] = e;
+                }
+                g_hi = g_lo;
+                m_up = m;
+            } else {
+                if (p.do_relax) p.y[1][o] = x[0];
+                if (p.do_sed) {
+#pragma unroll
+                    for (int f = 1; f < NT; f++)
+                        if (f + 1 == p.sed) p.y[f + 1][o] = x[f];
+                }
+                if (p.budgets) {
+#pragma unroll
+                    for (int f = 0; f < NT; f++) cs[f + 1].add(x[f], p.dz[k], p.dzT[k], p.dzlo[k]);
+                }
+            }
+            if (k > 0) {
+#pragma unroll
+                for (int f = 0; f < NT; f++) x[f] = xn[f];
+            }
+            rho = rho_dn;
+            rho_dn = rho_dn2;
+            rd = rd_dn;
+        }
+        if (p.do_diff) {
+            // back substitution, bottom-up; sigma_k = rho_k dz_k m_k
+            double z[NT];
+#pragma unroll
+            for (int f = 0; f < NT; f++) z[f] = 0.0;
+            long long ob = col;
+            double mk = sc[0], gk = 0.0;
+            double ek[NT];
+#pragma unroll
+            for (int f = 0; f < NT; f++) ek[f] = sc[(long long)(2 + f) * nslots];
+            T rk = p.y[0][ob];
+            for (int k = 0; k < nz; k++, ob += plane) {
+                double mn = 0.0, gn = 0.0, en[NT];
+                T rn = T(0);
+                if (k + 1 < nz) {   // prefetch level k+1
+                    mn = sc[(long long)((k + 1) * NQ + 0) * nslots];
+                    gn = sc[(long long)((k + 1) * NQ + 1) * nslots];
+#pragma unroll
+                    for (int f = 0; f < NT; f++) en[f] = sc[(long long)((k + 1) * NQ + 2 + f) * nslots];
+                    rn = p.y[0][ob + plane];
+                }
+                const double sigma = to_f64(rk) * p.dz[k] * mk;
+                // float path: sigma in float from rho (float), dz and m rounded once
+                const float sf = (sizeof(T) == 4) ? (float)rk * (float)p.dzT[k] * d2f_bits(mk) : 0.f;
+#pragma unroll
+                for (int f = 0; f < NT; f++) {
+                    z[f] = fma(gk, z[f], ek[f]);
+                    const T u = scale_out<T>(z[f], sigma, sf);
+                    p.y[f + 1][ob] = u;
+                    if (p.budgets) cs[f + 1].add(u, p.dz[k], p.dzT[k], p.dzlo[k]);
+                }
+                if (k + 1 < nz) {
+                    mk = mn;
+                    gk = gn;
+#pragma unroll
+                    for (int f = 0; f < NT; f++) ek[f] = en[f];
+                    rk = rn;
+                }
+            }
+        }
+    } else if (p.budgets) {
+        for (int k = 0; k < nz; k++) {
+            const long long o = (long long)k * plane + col;
+#pragma unroll
+            for (int f = 0; f < NF; f++) cs[f].add(p.y[f][o], p.dz[k], p.dzT[k], p.dzlo[k]);
+        }
+    }
+}
+
+}  // namespace asuca

@@ -1,0 +1,156 @@
+// Ensemble of members with uneven horizontal domains advanced in one
+// persistent, cooperative launch.  For each step the kernel runs three stage
+// phases and one column phase; a phase walks a flattened list of work items
+// (member, tile) or (member, column), dealt round-robin to the resident CTAs,
+// and ends at a device-wide barrier.  Members never share a tile, so each
+// member's result equals its own single-member step bit for bit.
+//
+// The barrier is a generation counter in the workspace.  Its wait is bounded
+// (about one second of wall time); a CTA that gives up writes
+// ASUCA_ERR_TIMEOUT to the status word and leaves the kernel, and so do the
+// others when their own waits run out.
+#pragma once
+
+#include "ensemble_params.cuh"
+#include "column_impl.cuh"
+#include "stage_impl.cuh"
+
+namespace asuca {
+
+__device__ __forceinline__ bool ens_barrier(unsigned *count, unsigned *gen, unsigned target, int *status) {
+    __shared__ int ok_s;
+    __syncthreads();
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        volatile unsigned *vgen = gen;
+        const unsigned g0 = *vgen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(count, 1u) + 1u;
+        int ok = 1;
+        if (arrived == target) {
+            atomicExch(count, 0u);
+            __threadfence();
+            atomicAdd(gen, 1u);
+        } else {
+            const uint64_t t0 = global_ns();
+            while (*vgen == g0) {
+                if (global_ns() - t0 > 1000000000ull) {
+                    ok = 0;
+                    if (status) atomicCAS(status, 0, (int)ASUCA_ERR_TIMEOUT);
+                    break;
+                }
+                __nanosleep(200);
+            }
+        }
+        __threadfence();
+        ok_s = ok;
+    }
+    __syncthreads();
+    return ok_s != 0;
+}
+
+template <typename T>
+__device__ __forceinline__ int member_of(const EnsMember<T> *m, int nm, long long idx, bool by_tile) {
+    int lo = 0, hi = nm - 1;
+    while (lo < hi) {   // last member whose first index <= idx
+        const int mid = (lo + hi + 1) >> 1;
+        const long long first = by_tile ? m[mid].tile0 : m[mid].col0;
+        if (first <= idx) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <typename T, int NF, int LIM>
+__global__ void __launch_bounds__(32 * StageShape<T, NF>::TY, StageShape<T, NF>::MIN_BLOCKS)
+    ensemble_kernel(const __grid_constant__ EnsParams<T> e) {
+    using S = StageShape<T, NF>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const unsigned target = gridDim.x + (unsigned)e.bar_extra;
+    const long long nth = (long long)gridDim.x * blockDim.x * blockDim.y;
+    const long long gtid = (long long)blockIdx.x * blockDim.x * blockDim.y + threadIdx.y * blockDim.x + threadIdx.x;
+    for (int n = 0; n < e.nsteps; n++) {
+        for (int stg = 0; stg < 3; stg++) {
+            bool bad = false;
+            for (long long t = blockIdx.x; t < e.total_tiles; t += gridDim.x) {
+                const int m = member_of(e.members, e.nmembers, t, true);
+                const EnsMember<T> &mb = e.members[m];
+                const long long lt = t - mb.tile0;
+                const int tx = (int)(lt % mb.tiles_x), ty = (int)(lt / mb.tiles_x);
+                const StageParams<T> &sp = mb.stage[stg];
+                if (stage_tile<T, NF, LIM, false>(sp, &sp.tmap, tx * S::TX, ty * S::TY, smem_raw)) {
+                    bad = true;
+                    break;
+                }
+            }
+            if (bad || !ens_barrier(e.bar_count, e.bar_gen, target, e.status)) return;
+        }
+        for (long long c = gtid; c < e.total_cols; c += nth) {
+            const int m = member_of(e.members, e.nmembers, c, false);
+            const EnsMember<T> &mb = e.members[m];
+            ColSum<T> cs[NF];
+            column_one<T, NF>(mb.col, c - mb.col0, e.scratch + gtid, nth, cs);
+        }
+        if (!ens_barrier(e.bar_count, e.bar_gen, target, e.status)) return;
+    }
+}
+
+template <typename T, int NF, int LIM>
+static cudaError_t ens_launch_lim(const EnsParams<T> &e, int grid, cudaStream_t s, int *grid_out) {
+    using S = StageShape<T, NF>;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t r = cudaFuncSetAttribute(ensemble_kernel<T, NF, LIM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)S::SMEM_BYTES);
+        if (r != cudaSuccess) return r;
+        attr_set = true;
+    }
+    if (grid_out) {   // size query: resident CTAs per SM times SMs
+        int per_sm = 0, dev = 0, nsm = 0;
+        cudaError_t r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ensemble_kernel<T, NF, LIM>,
+                                                                      32 * S::TY, S::SMEM_BYTES);
+        if (r != cudaSuccess) return r;
+        if ((r = cudaGetDevice(&dev)) != cudaSuccess) return r;
+        if ((r = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return r;
+        *grid_out = per_sm * nsm;
+        return cudaSuccess;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(32, S::TY);
+    cfg.dynamicSmemBytes = S::SMEM_BYTES;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, ensemble_kernel<T, NF, LIM>, e);
+}
+
+template <typename T, int NF>
+static cudaError_t ens_launch_nf(const EnsParams<T> &e, int lim, int grid, cudaStream_t s, int *grid_out) {
+    switch (lim) {
+        case ASUCA_LIM_KOREN: return ens_launch_lim<T, NF, ASUCA_LIM_KOREN>(e, grid, s, grid_out);
+        case ASUCA_LIM_LINEAR: return ens_launch_lim<T, NF, ASUCA_LIM_LINEAR>(e, grid, s, grid_out);
+        case ASUCA_LIM_UPWIND1: return ens_launch_lim<T, NF, ASUCA_LIM_UPWIND1>(e, grid, s, grid_out);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename T>
+cudaError_t launch_ensemble(const EnsParams<T> &e, int nf, int lim, int grid, cudaStream_t s, int *grid_out) {
+    switch (nf) {
+        case 2: return ens_launch_nf<T, 2>(e, lim, grid, s, grid_out);
+        case 3: return ens_launch_nf<T, 3>(e, lim, grid, s, grid_out);
+        case 4: return ens_launch_nf<T, 4>(e, lim, grid, s, grid_out);
+        case 5: return ens_launch_nf<T, 5>(e, lim, grid, s, grid_out);
+        case 6: return ens_launch_nf<T, 6>(e, lim, grid, s, grid_out);
+        case 7: return ens_launch_nf<T, 7>(e, lim, grid, s, grid_out);
+        case 8: return ens_launch_nf<T, 8>(e, lim, grid, s, grid_out);
+        case 9: return ens_launch_nf<T, 9>(e, lim, grid, s, grid_out);
+        case 10: return ens_launch_nf<T, 10>(e, lim, grid, s, grid_out);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace asuca

@@ -1,0 +1,6 @@
+// The double instantiation of the ensemble kernel (see ensemble.cuh).
+#include "ensemble.cuh"
+
+namespace asuca {
+template cudaError_t launch_ensemble<double>(const EnsParams<double> &, int, int, int, cudaStream_t, int *);
+}  // namespace asuca

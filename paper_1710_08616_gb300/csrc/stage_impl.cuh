@@ -94,9 +94,14 @@ __device__ __forceinline__ void cp_async_wait() {
 
 // ------------------------------------------------------------------ the kernel
 
+// One tile of one stage: the CTA computes columns [i0, i0+32) x [j0, j0+TY)
+// for every level.  Returns true when a level's data did not arrive within the
+// wait limit (the status word has been set).  The caller's CTA owns smem_raw;
+// the function begins and ends with a CTA-wide barrier, so consecutive tiles
+// may reuse the same shared memory and mbarriers.
 template <typename T, int NF, int LIM, bool REC>
-__global__ void __launch_bounds__(32 * StageShape<T, NF>::TY, StageShape<T, NF>::MIN_BLOCKS)
-    stage_kernel(const __grid_constant__ StageParams<T> p) {
+__device__ __forceinline__ bool stage_tile(const StageParams<T> &p, const CUtensorMap *tmap, int i0, int j0,
+                                           unsigned char *smem_raw) {
     using S = StageShape<T, NF>;
     constexpr int TX = S::TX, TY = S::TY, D = S::D, SX = S::SX, SY = S::SY, NT = S::NT;
     constexpr int NTHR = TX * TY;
@@ -104,7 +109,6 @@ __global__ void __launch_bounds__(32 * StageShape<T, NF>::TY, StageShape<T, NF>:
     constexpr int NCELL = TY * (TX + 4) + 4 * TX; // the slot cells the stencil reads (no corners)
     constexpr int MAXC = (NCELL + NTHR - 1) / NTHR;
 
-    extern __shared__ __align__(128) unsigned char smem_raw[];
     T *ring = reinterpret_cast<T *>(smem_raw);
     T *ysm = reinterpret_cast<T *>(smem_raw + S::RING_BYTES);            // [NT][TY+1][TX]
     T *xbs = reinterpret_cast<T *>(smem_raw + S::RING_BYTES + S::YS_BYTES); // [NT][TY]
@@ -113,7 +117,6 @@ __global__ void __launch_bounds__(32 * StageShape<T, NF>::TY, StageShape<T, NF>:
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
     const int nx = p.nx, ny = p.ny, nz = p.nz;
     const long long plane = p.plane;
-    const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
     const int i = i0 + tx, j = j0 + ty;
     const bool valid = (i < nx) && (j < ny);
     const int ic = wrap_index(i, nx), jc = wrap_index(j, ny);
@@ -122,6 +125,7 @@ __global__ void __launch_bounds__(32 * StageShape<T, NF>::TY, StageShape<T, NF>:
     const long long down = (long long)wrap_index(jc - 1, ny) * nx + ic;
     const bool tma = p.tma_in != 0;
 
+    __syncthreads();   // the previous tile (if any) is done with the shared memory
     if (tma && tid == 0) {
         for (int s = 0; s < D; s++) mbar_init(&bars[s], 1);
         fence_proxy_async();
@@ -161,7 +165,7 @@ __global__ void __launch_bounds__(32 * StageShape<T, NF>::TY, StageShape<T, NF>:
             if (tid == 0 && lev < nz) {
                 uint64_t *bar = &bars[lev % D];
                 mbar_expect_tx(bar, S::TX_BYTES);
-                tma_load_4d(slot(lev), &p.tmap, i0, j0, lev, 0, bar);
+                tma_load_4d(slot(lev), tmap, i0, j0, lev, 0, bar);
             }
         } else {
             if (lev < nz) {
@@ -353,6 +357,16 @@ __global__ void __launch_bounds__(32 * StageShape<T, NF>::TY, StageShape<T, NF>:
         if (tid == 0 && p.status) atomicCAS(p.status, 0, (int)ASUCA_ERR_TIMEOUT);
     }
     if (!tma) cp_async_wait<0>();
+    __syncthreads();
+    return timed_out;
+}
+
+template <typename T, int NF, int LIM, bool REC>
+__global__ void __launch_bounds__(32 * StageShape<T, NF>::TY, StageShape<T, NF>::MIN_BLOCKS)
+    stage_kernel(const __grid_constant__ StageParams<T> p) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    (void)stage_tile<T, NF, LIM, REC>(p, &p.tmap, blockIdx.x * StageShape<T, NF>::TX,
+                                      blockIdx.y * StageShape<T, NF>::TY, smem_raw);
 }
 
 template <typename T, int NF, int LIM, bool REC>

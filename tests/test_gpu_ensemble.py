@@ -1,0 +1,100 @@
+"""Ensemble path (asuca_ensemble_step): uneven members in one persistent launch.
+
+* every member equals asuca_step on that member alone, bit for bit (members
+  never share a tile; the same tile and column code runs in both);
+* a second call replays the cached CUDA graph and still matches;
+* an FP64 member against the oracle (1e-12);
+* the device-wide barrier gives up (test hook: it waits for one CTA more than
+  the grid has) and the call reports ASUCA_ERR_TIMEOUT without faulting; the
+  next call succeeds.
+"""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def asuca():
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1710_08616_gb300 as a
+    torch.cuda.set_device(0)
+    return a
+
+
+def _members(sizes, ntr=4, nz=14):
+    return gen.make_ensemble_cases(sizes=sizes, nz=nz, ntracers=ntr)
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+def test_members_equal_single_member_steps(asuca, prec):
+    import torch
+    cases = _members([64, 71, 40, 97, 33])
+    grids = [asuca.Grid.from_case(c, prec=prec) for c in cases]
+    ens = [asuca.State.from_case(c, prec=prec) for c in cases]
+    one = [s.clone() for s in ens]
+    n = 3
+    bud = asuca.ensemble_step(grids, ens, [c.dt for c in cases], n, budgets=True)
+    torch.cuda.synchronize()
+    assert asuca.get_status(grids[0]) == asuca.OK
+    for m, (g, c) in enumerate(zip(grids, cases)):
+        b1 = asuca.step(g, one[m], c.dt, n, budgets=True)
+        torch.cuda.synchronize()
+        assert torch.equal(ens[m].fields(), one[m].fields()), f"member {m}"
+        rel = (bud[m] - b1).abs() / b1.abs().clamp_min(1e-300)
+        assert float(rel.max()) <= 1e-13
+
+
+def test_graph_replay_matches(asuca):
+    import torch
+    cases = _members([50, 81, 64])
+    grids = [asuca.Grid.from_case(c) for c in cases]
+    ens = [asuca.State.from_case(c) for c in cases]
+    one = [s.clone() for s in ens]
+    ws = torch.empty(asuca.ensemble_workspace_bytes(grids), dtype=torch.uint8, device="cuda")
+    dts = [c.dt for c in cases]
+    for _ in range(3):      # the first call captures, the next ones replay
+        asuca.ensemble_step(grids, ens, dts, 2, workspace=ws)
+    for m, (g, c) in enumerate(zip(grids, cases)):
+        for _ in range(3):
+            asuca.step(g, one[m], c.dt, 2)
+    torch.cuda.synchronize()
+    for m in range(len(cases)):
+        assert torch.equal(ens[m].fields(), one[m].fields())
+
+
+def test_fp64_member_against_oracle(asuca):
+    import torch
+    cases = _members([40, 36], ntr=2, nz=10)
+    grids = [asuca.Grid.from_case(c, prec=0) for c in cases]
+    ens = [asuca.State.from_case(c, prec=0) for c in cases]
+    asuca.ensemble_step(grids, ens, [c.dt for c in cases], 4)
+    torch.cuda.synchronize()
+    for m, c in enumerate(cases):
+        ref, _ = oracle.step(oracle.Grid.from_case(c), c.state(), c.mu, c.mv, c.mw, c.dt, 4)
+        got = ens[m].fields().cpu().numpy()
+        for f in range(ref.shape[0]):
+            assert np.linalg.norm(got[f] - ref[f]) <= 1e-12 * np.linalg.norm(ref[f])
+
+
+def test_barrier_timeout_reports_status(asuca):
+    import time
+    import torch
+    cases = _members([48, 40], nz=8)
+    grids = [asuca.Grid.from_case(c) for c in cases]
+    ens = [asuca.State.from_case(c) for c in cases]
+    asuca.set_tuning(grids[0], asuca.TUNE_BARRIER_EXTRA, 1)
+    t0 = time.time()
+    asuca.ensemble_step(grids, ens, [c.dt for c in cases], 1)
+    assert asuca.get_status(grids[0]) == asuca.ERR_TIMEOUT
+    assert time.time() - t0 < 30
+    asuca.set_tuning(grids[0], asuca.TUNE_BARRIER_EXTRA, 0)
+    fresh = [asuca.State.from_case(c) for c in cases]
+    asuca.ensemble_step(grids, fresh, [c.dt for c in cases], 1)
+    torch.cuda.synchronize()
+    assert asuca.get_status(grids[0]) == asuca.OK
