@@ -259,6 +259,55 @@ def adjoint_cost(asuca, dev, reps=3):
     return out
 
 
+def ensemble_throughput(asuca, dev, nsteps=10, reps=3):
+    """32 members with nx = ny drawn from U{64..320}, 58 levels, 4 tracers, FP32:
+    cell-updates/s of one persistent launch per call (graph-replayed) against the
+    same members advanced one after another with asuca_step."""
+    import torch
+    import gen
+    from paper_1710_08616_gb300 import autotune
+    cases = gen.make_ensemble_cases()
+    grids = [asuca.Grid.from_case(c) for c in cases]
+    states = [asuca.State.from_case(c, device=dev) for c in cases]
+    dts = [c.dt for c in cases]
+    cells = sum(c.cells for c in cases)
+    tune = autotune.tune_ensemble(grids, states, dts, steps=2, reps=2, save=False)
+    ws = torch.empty(asuca.ensemble_workspace_bytes(grids), dtype=torch.uint8, device=dev)
+    asuca.ensemble_step(grids, states, dts, nsteps, workspace=ws)     # capture + warm
+    asuca.ensemble_step(grids, states, dts, nsteps, workspace=ws)
+    torch.cuda.synchronize()
+
+    def ens():
+        asuca.ensemble_step(grids, states, dts, nsteps, workspace=ws)
+
+    wss = [g.workspace(device=dev) for g in grids]
+
+    def seq():
+        for g, s, d, w in zip(grids, states, dts, wss):
+            asuca.step(g, s, d, nsteps, workspace=w)
+
+    def timed(fn):
+        best = None
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            best = e0.elapsed_time(e1) if best is None else min(best, e0.elapsed_time(e1))
+        return best
+
+    seq()
+    t_ens, t_seq = timed(ens), timed(seq)
+    assert asuca.get_status(grids[0]) == asuca.OK
+    return {"workload": "ensemble_32x_64to320x58", "members": len(cases), "cells": cells, "nsteps_per_call": nsteps,
+            "sizes": [c.nx for c in cases], "ensemble_tile_rows": tune["best"]["ensemble_tile_rows"],
+            "ensemble_cell_updates_per_s": cells * nsteps / (t_ens * 1e-3),
+            "sequential_members_cell_updates_per_s": cells * nsteps / (t_seq * 1e-3),
+            "ensemble_ms_per_step": t_ens / nsteps, "sequential_ms_per_step": t_seq / nsteps,
+            "speedup_over_sequential": t_seq / t_ens}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -375,6 +424,9 @@ def run_ours(args):
     adjoint = None
     if not args.no_adjoint:
         adjoint = adjoint_cost(asuca, dev)
+    ensemble = None
+    if not args.no_ensemble:
+        ensemble = ensemble_throughput(asuca, dev, args.ens_steps)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -390,7 +442,7 @@ def run_ours(args):
                           "limiter": "koren", "l2": "inputs larger than L2 (2.4 GB state), no flush",
                           "parallelism": f"{world} independent replica(s), one per GPU"},
                "clocks": clocks, "gpu_launches": 5 * args.steps, "roofline": roofline,
-               "e2e": e2e, "fp64": fp64, "adjoint": adjoint,
+               "e2e": e2e, "fp64": fp64, "adjoint": adjoint, "ensemble": ensemble,
                "fp32_over_fp64_speedup": (value / fp64["value"]) if fp64 else None,
                "cpu_baseline": cpu}
         print(json.dumps(out), flush=True)
@@ -413,6 +465,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--ens-steps", type=int, default=10)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

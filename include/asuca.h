@@ -170,7 +170,9 @@ asuca_status asuca_ensemble_step(asuca_grid *const *grids, asuca_state *states, 
 /* ---- tuning knobs (set by the autotuner) --------------------------------- */
 typedef enum {
     ASUCA_TUNE_COL_BLOCKS_PER_SM = 0,   /* resident column-kernel blocks per SM (1..16); sizes the column scratch */
-    ASUCA_TUNE_BARRIER_EXTRA = 1        /* test hook: the ensemble barrier waits for this many extra CTAs (0) */
+    ASUCA_TUNE_BARRIER_EXTRA = 1,       /* test hook: the ensemble barrier waits for this many extra CTAs (0) */
+    ASUCA_TUNE_STAGE_TILE_ROWS = 2,     /* stage tile 32 x rows: 4, 8 (default) or 16 for FP32; 8 for FP64 */
+    ASUCA_TUNE_ENSEMBLE_TILE_ROWS = 3   /* ensemble tile 32 x rows: 4 or 8 (default) for FP32; 8 for FP64 */
 } asuca_tune_key;
 asuca_status asuca_set_tuning(asuca_grid *grid, int key, int value);
 int asuca_get_tuning(const asuca_grid *grid, int key);

@@ -87,7 +87,7 @@ SIGNATURES = {
                                           ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
 }
 KERNEL_STAGE, KERNEL_COLUMN, KERNEL_REDUCE, KERNEL_ADJ_STAGE, KERNEL_ADJ_COLUMN, KERNEL_ENSEMBLE = 0, 1, 2, 3, 4, 5
-TUNE_COL_BLOCKS_PER_SM, TUNE_BARRIER_EXTRA = 0, 1
+TUNE_COL_BLOCKS_PER_SM, TUNE_BARRIER_EXTRA, TUNE_STAGE_TILE_ROWS, TUNE_ENSEMBLE_TILE_ROWS = 0, 1, 2, 3
 KERNEL_KINDS = 8
 
 

@@ -22,12 +22,15 @@ struct asuca_grid {
     int col_grid;                 // persistent column-kernel grid
     int col_blocks_per_sm;        // tuning knob behind col_grid
     int barrier_extra;            // test hook: extra arrivals the ensemble barrier waits for
+    int stage_ty;                 // tile rows of the stage kernel (tuned; 8 for FP64)
+    int ens_ty;                   // tile rows of the ensemble kernel (tuned; 8 for FP64)
     std::vector<void *> *kept_pinned;   // parameter buffers referenced by a caller's captured graphs
     volatile int *status_host;    // pinned, mapped; the device writes error codes here
     int *status_dev;
     cudaStream_t last_stream;
     // TMA descriptors of the two padded stage buffers, for the workspace they were made for
     void *map_ws;
+    int map_ty;
     CUtensorMap map_ystar, map_ystar2;
     // opt-in per-kernel timing: events recorded around every launch
     bool prof_on;
@@ -126,6 +129,7 @@ StageParams<T> stage_params(const asuca_grid *g, const asuca_state *fl, const vo
     p.lim = (int)g->d.lim;
     p.plane = g->plane;
     p.status = g->status_dev;
+    p.ty = g->stage_ty;
     p.opitch = padded_pitch(g->d.nx);
     p.oplane = (long long)(g->d.ny + 4) * p.opitch;
     p.rdx = (T)(1.0 / g->d.dx);
@@ -221,13 +225,14 @@ asuca_status run_step(asuca_grid *g, asuca_state *st, const void *tend, double d
 
     cudaError_t e = cudaMemsetAsync(ws + L.precip, 0, (size_t)g->plane * sizeof(double), s);
     if (e != cudaSuccess) return ASUCA_ERR_CUDA;
-    if (g->map_ws != (void *)ws) {
-        if (encode_stage_map<T>(&g->map_ystar, ws + L.ystar, F, g->d.nx, g->d.ny, g->d.nz) != cudaSuccess ||
-            encode_stage_map<T>(&g->map_ystar2, ws + L.ystar2, F, g->d.nx, g->d.ny, g->d.nz) != cudaSuccess) {
+    if (g->map_ws != (void *)ws || g->map_ty != g->stage_ty) {
+        if (encode_stage_map<T>(&g->map_ystar, ws + L.ystar, F, g->d.nx, g->d.ny, g->d.nz, g->stage_ty) != cudaSuccess ||
+            encode_stage_map<T>(&g->map_ystar2, ws + L.ystar2, F, g->d.nx, g->d.ny, g->d.nz, g->stage_ty) != cudaSuccess) {
             g->map_ws = nullptr;
             return ASUCA_ERR_CUDA;
         }
         g->map_ws = (void *)ws;
+        g->map_ty = g->stage_ty;
     }
     const T cdt[3] = {(T)(dt / 3.0), (T)(dt / 2.0), (T)dt};
     for (int f = 0; f < MAXF; f++) sp.ybase[f] = yn[f];
@@ -383,9 +388,9 @@ asuca_status run_adjoint(asuca_grid *g, const asuca_state *init, const void *ten
     std::vector<CUtensorMap> maps(2 * (size_t)K);
     for (int q = 0; q < K; q++) {
         if (encode_stage_map<T>(&maps[2 * q], ws + L.segY1 + (size_t)q * align_up(L.pstate), F, g->d.nx, g->d.ny,
-                                g->d.nz) != cudaSuccess ||
+                                g->d.nz, 8) != cudaSuccess ||
             encode_stage_map<T>(&maps[2 * q + 1], ws + L.segY2 + (size_t)q * align_up(L.pstate), F, g->d.nx,
-                                g->d.ny, g->d.nz) != cudaSuccess)
+                                g->d.ny, g->d.nz, 8) != cudaSuccess)
             return ASUCA_ERR_CUDA;
     }
     for (int c = L.ncp - 1; c >= 0; c--) {
@@ -409,6 +414,7 @@ asuca_status run_adjoint(asuca_grid *g, const asuca_state *init, const void *ten
             workspace_fields<T>(g, segY2(q), 0, y2);
             block_fields<T>(g, segY3(q), y3);
             StageParams<T> sp = stage_params<T>(g, init, tend);
+            sp.ty = 8;   // branch recording runs with 8-row tiles
             for (int f = 0; f < MAXF; f++) sp.ybase[f] = yn[f];
             for (int stg = 0; stg < 3; stg++) {
                 sp.tma_in = stg > 0;
@@ -505,8 +511,8 @@ asuca_status run_record(asuca_grid *g, const asuca_state *init, const void *tend
     const int F = g->F;
     const size_t cb = (size_t)g->cells * sizeof(T);
     CUtensorMap m1, m2;
-    if (encode_stage_map<T>(&m1, ws + L.segY1, F, g->d.nx, g->d.ny, g->d.nz) != cudaSuccess ||
-        encode_stage_map<T>(&m2, ws + L.segY2, F, g->d.nx, g->d.ny, g->d.nz) != cudaSuccess)
+    if (encode_stage_map<T>(&m1, ws + L.segY1, F, g->d.nx, g->d.ny, g->d.nz, 8) != cudaSuccess ||
+        encode_stage_map<T>(&m2, ws + L.segY2, F, g->d.nx, g->d.ny, g->d.nz, 8) != cudaSuccess)
         return ASUCA_ERR_CUDA;
     T *yn[MAXF], *y1[MAXF], *y2[MAXF], *y3[MAXF], *init_f[MAXF];
     block_fields<T>(g, ws + L.segYn, yn);
@@ -521,6 +527,7 @@ asuca_status run_record(asuca_grid *g, const asuca_state *init, const void *tend
     const T cdt[3] = {(T)(dt / 3.0), (T)(dt / 2.0), (T)dt};
     for (int n = 0; n < nsteps; n++) {
         StageParams<T> sp = stage_params<T>(g, init, tend);
+        sp.ty = 8;
         for (int f = 0; f < MAXF; f++) sp.ybase[f] = yn[f];
         for (int stg = 0; stg < 3; stg++) {
             sp.tma_in = stg > 0;
@@ -560,7 +567,7 @@ template <typename T>
 cudaError_t ens_grid(const asuca_grid *g0, int *grid) {
     EnsParams<T> dummy;
     std::memset(&dummy, 0, sizeof(dummy));
-    return launch_ensemble<T>(dummy, g0->F, (int)g0->d.lim, 0, nullptr, grid);
+    return launch_ensemble<T>(dummy, g0->F, (int)g0->d.lim, g0->ens_ty, 0, nullptr, grid);
 }
 
 bool ens_layout(asuca_grid *const *grids, int M, EnsLayout *L) {
@@ -569,7 +576,7 @@ bool ens_layout(asuca_grid *const *grids, int M, EnsLayout *L) {
     cudaError_t e = g0->d.prec == ASUCA_FP64 ? ens_grid<double>(g0, &grid) : ens_grid<float>(g0, &grid);
     if (e != cudaSuccess || grid <= 0) return false;
     L->grid = grid;
-    L->threads = 32 * (g0->d.prec == ASUCA_FP64 ? StageShape<double, 2>::TY : StageShape<float, 2>::TY);
+    L->threads = 32 * g0->ens_ty;
     const size_t msize = g0->d.prec == ASUCA_FP64 ? sizeof(EnsMember<double>) : sizeof(EnsMember<float>);
     size_t off = 0;
     L->members = off;
@@ -614,7 +621,7 @@ asuca_status ens_enqueue(asuca_grid *const *grids, asuca_state *states, const do
     const int F = g0->F;
     EnsMember<T> *mb = (EnsMember<T> *)staging;
     long long tile0 = 0, col0 = 0;
-    using S = StageShape<T, 2>;
+    const int TX = 32, TY = g0->ens_ty;
     for (int m = 0; m < M; m++) {
         asuca_grid *g = grids[m];
         const double dt = dts[m];
@@ -624,13 +631,14 @@ asuca_status ens_enqueue(asuca_grid *const *grids, asuca_state *states, const do
         workspace_fields<T>(g, ws, L.ystar[m], y1);
         workspace_fields<T>(g, ws, L.ystar2[m], y2);
         CUtensorMap m1, m2;
-        if (encode_stage_map<T>(&m1, ws + L.ystar[m], F, g->d.nx, g->d.ny, g->d.nz) != cudaSuccess ||
-            encode_stage_map<T>(&m2, ws + L.ystar2[m], F, g->d.nx, g->d.ny, g->d.nz) != cudaSuccess)
+        if (encode_stage_map<T>(&m1, ws + L.ystar[m], F, g->d.nx, g->d.ny, g->d.nz, TY) != cudaSuccess ||
+            encode_stage_map<T>(&m2, ws + L.ystar2[m], F, g->d.nx, g->d.ny, g->d.nz, TY) != cudaSuccess)
             return ASUCA_ERR_CUDA;
         const T cdt[3] = {(T)(dt / 3.0), (T)(dt / 2.0), (T)dt};
         for (int stg = 0; stg < 3; stg++) {
             StageParams<T> sp = stage_params<T>(g, &states[m], nullptr);
             sp.status = g0->status_dev;
+            sp.ty = TY;
             sp.tma_in = stg > 0;
             if (stg == 1) sp.tmap = m1;
             if (stg == 2) sp.tmap = m2;
@@ -649,7 +657,7 @@ asuca_status ens_enqueue(asuca_grid *const *grids, asuca_state *states, const do
         cp.precip_col = (double *)(ws + L.precip[m]);
         cp.budgets = 0;
         mb[m].col = cp;
-        const int tx = (g->d.nx + S::TX - 1) / S::TX, ty = (g->d.ny + S::TY - 1) / S::TY;
+        const int tx = (g->d.nx + TX - 1) / TX, ty = (g->d.ny + TY - 1) / TY;
         mb[m].tiles_x = tx;
         mb[m].tile0 = tile0;
         mb[m].col0 = col0;
@@ -675,7 +683,7 @@ asuca_status ens_enqueue(asuca_grid *const *grids, asuca_state *states, const do
     ep.status = g0->status_dev;
     ep.scratch = (double *)(ws + L.scratch);
     if (nsteps > 0 &&
-        timed(g0, ASUCA_KERNEL_ENSEMBLE, s, [&] { return launch_ensemble<T>(ep, F, (int)g0->d.lim, L.grid, s, nullptr); }) !=
+        timed(g0, ASUCA_KERNEL_ENSEMBLE, s, [&] { return launch_ensemble<T>(ep, F, (int)g0->d.lim, TY, L.grid, s, nullptr); }) !=
             cudaSuccess)
         return ASUCA_ERR_CUDA;
     if (budgets) {
@@ -790,6 +798,8 @@ asuca_status asuca_init_grid(const asuca_grid_desc *desc, asuca_grid **out) {
         return ASUCA_ERR_CUDA;
     }
     g->col_blocks_per_sm = col_blocks_per_sm();
+    g->stage_ty = 8;
+    g->ens_ty = 8;
     set_col_grid(g);
     void *h = nullptr;
     if (cudaHostAlloc(&h, 64, cudaHostAllocMapped) != cudaSuccess) {
@@ -888,7 +898,7 @@ asuca_status asuca_ensemble_step(asuca_grid *const *grids, asuca_state *states, 
         const asuca_grid *g = grids[m];
         if (!g || !state_ok(g, &states[m]) || !std::isfinite(dts[m]) || dts[m] < 0.0) return ASUCA_ERR_ARG;
         if (g->F != g0->F || g->d.nz != g0->d.nz || g->d.prec != g0->d.prec || g->d.lim != g0->d.lim ||
-            g->device != g0->device)
+            g->device != g0->device || g->ens_ty != g0->ens_ty)
             return ASUCA_ERR_ARG;
     }
     asuca_status prev = take_status(g0);
@@ -914,6 +924,7 @@ asuca_status asuca_ensemble_step(asuca_grid *const *grids, asuca_state *states, 
         put(&grids[m]->d.nx, sizeof(int));
         put(&grids[m]->d.ny, sizeof(int));
         put(&grids[m]->barrier_extra, sizeof(int));
+        put(&grids[m]->ens_ty, sizeof(int));
     }
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     if (s != nullptr && cudaStreamIsCapturing(s, &cap) != cudaSuccess) return ASUCA_ERR_CUDA;
@@ -991,6 +1002,14 @@ asuca_status asuca_set_tuning(asuca_grid *g, int key, int value) {
             if (value < 0) return ASUCA_ERR_ARG;
             g->barrier_extra = value;
             return ASUCA_OK;
+        case ASUCA_TUNE_STAGE_TILE_ROWS:
+            if (g->d.prec == ASUCA_FP64 ? value != 8 : (value != 4 && value != 8 && value != 16)) return ASUCA_ERR_ARG;
+            g->stage_ty = value;
+            return ASUCA_OK;
+        case ASUCA_TUNE_ENSEMBLE_TILE_ROWS:
+            if (g->d.prec == ASUCA_FP64 ? value != 8 : (value != 4 && value != 8)) return ASUCA_ERR_ARG;
+            g->ens_ty = value;
+            return ASUCA_OK;
         default: return ASUCA_ERR_ARG;
     }
 }
@@ -1000,6 +1019,8 @@ int asuca_get_tuning(const asuca_grid *g, int key) {
     switch (key) {
         case ASUCA_TUNE_COL_BLOCKS_PER_SM: return g->col_blocks_per_sm;
         case ASUCA_TUNE_BARRIER_EXTRA: return g->barrier_extra;
+        case ASUCA_TUNE_STAGE_TILE_ROWS: return g->stage_ty;
+        case ASUCA_TUNE_ENSEMBLE_TILE_ROWS: return g->ens_ty;
         default: return -1;
     }
 }

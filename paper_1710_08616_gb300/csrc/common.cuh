@@ -23,12 +23,13 @@ constexpr int MAXNZ = ASUCA_MAX_NZ;
 // 32 x TY columns (one warp per row); a ring slot holds every field of one
 // level plane of the tile with a 4-column halo in i (2 used; the TMA box must
 // start on a 16-byte boundary) and a 2-row halo in j.
-template <typename T, int NF>
+template <typename T, int NF, int TYV = 8>
 struct StageShape {
     static constexpr int TX = 32;
-    static constexpr int TY = 8;
+    static constexpr int TY = TYV;                       // tile rows: 4, 8 or 16 (an autotuned choice)
     static constexpr int D = 5;                          // ring depth (levels in flight + window)
-    static constexpr int MIN_BLOCKS = sizeof(T) == 4 ? 2 : 1;   // CTAs resident per SM
+    // CTAs resident per SM (shared memory and registers allow this many)
+    static constexpr int MIN_BLOCKS = sizeof(T) == 8 ? 1 : (TYV >= 16 ? 1 : (TYV >= 8 ? 2 : 3));
     static constexpr int SX = TX + 8;
     static constexpr int SY = TY + 4;
     static constexpr int NT = NF - 1;
@@ -57,6 +58,7 @@ struct StageParams {
     int *status;            // device status word (mapped host memory)
     int nx, ny, nz, lim;
     int tma_in, out_padded;
+    int ty;                 // tile rows of the instantiation to launch (the TMA box height follows it)
     uint8_t *branch;        // when recording: [F-1][nz][ny][nx] branch bytes (2 bits per direction)
     long long plane;        // nx * ny
     long long opitch, oplane;   // padded output: row pitch and level stride (elements)
@@ -252,9 +254,14 @@ __device__ __forceinline__ T face_coef(bool u, int br, int q) {
 template <typename T>
 cudaError_t launch_stage(const StageParams<T> &p, int nf, cudaStream_t s);
 
-// Encode the TMA descriptor of a padded stage buffer (F fields at base).
+// Encode the TMA descriptor of a padded stage buffer (F fields at base) for
+// tiles of ty rows.
 template <typename T>
-cudaError_t encode_stage_map(CUtensorMap *map, void *base, int nf, int nx, int ny, int nz);
+cudaError_t encode_stage_map(CUtensorMap *map, void *base, int nf, int nx, int ny, int nz, int ty);
+
+// the stage kernels of one tile height (one translation unit each)
+template <typename T, int TY>
+cudaError_t launch_stage_ty(const StageParams<T> &p, int nf, cudaStream_t s);
 
 template <typename T>
 cudaError_t launch_column(const ColumnParams<T> &p, int nf, int grid, int block, cudaStream_t s);

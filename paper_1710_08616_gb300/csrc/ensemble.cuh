@@ -60,10 +60,10 @@ __device__ __forceinline__ int member_of(const EnsMember<T> *m, int nm, long lon
     return lo;
 }
 
-template <typename T, int NF, int LIM>
-__global__ void __launch_bounds__(32 * StageShape<T, NF>::TY, StageShape<T, NF>::MIN_BLOCKS)
+template <typename T, int NF, int LIM, int TYV>
+__global__ void __launch_bounds__(32 * TYV, StageShape<T, NF, TYV>::MIN_BLOCKS)
     ensemble_kernel(const __grid_constant__ EnsParams<T> e) {
-    using S = StageShape<T, NF>;
+    using S = StageShape<T, NF, TYV>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const unsigned target = gridDim.x + (unsigned)e.bar_extra;
     const long long nth = (long long)gridDim.x * blockDim.x * blockDim.y;
@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(32 * StageShape<T, NF>::TY, StageShape<T, NF>:
                 const long long lt = t - mb.tile0;
                 const int tx = (int)(lt % mb.tiles_x), ty = (int)(lt / mb.tiles_x);
                 const StageParams<T> &sp = mb.stage[stg];
-                if (stage_tile<T, NF, LIM, false>(sp, &sp.tmap, tx * S::TX, ty * S::TY, smem_raw)) {
+                if (stage_tile<T, NF, LIM, false, TYV>(sp, &sp.tmap, tx * S::TX, ty * S::TY, smem_raw)) {
                     bad = true;
                     break;
                 }
@@ -94,19 +94,19 @@ __global__ void __launch_bounds__(32 * StageShape<T, NF>::TY, StageShape<T, NF>:
     }
 }
 
-template <typename T, int NF, int LIM>
+template <typename T, int NF, int LIM, int TYV>
 static cudaError_t ens_launch_lim(const EnsParams<T> &e, int grid, cudaStream_t s, int *grid_out) {
-    using S = StageShape<T, NF>;
+    using S = StageShape<T, NF, TYV>;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t r = cudaFuncSetAttribute(ensemble_kernel<T, NF, LIM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t r = cudaFuncSetAttribute(ensemble_kernel<T, NF, LIM, TYV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)S::SMEM_BYTES);
         if (r != cudaSuccess) return r;
         attr_set = true;
     }
     if (grid_out) {   // size query: resident CTAs per SM times SMs
         int per_sm = 0, dev = 0, nsm = 0;
-        cudaError_t r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ensemble_kernel<T, NF, LIM>,
+        cudaError_t r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ensemble_kernel<T, NF, LIM, TYV>,
                                                                       32 * S::TY, S::SMEM_BYTES);
         if (r != cudaSuccess) return r;
         if ((r = cudaGetDevice(&dev)) != cudaSuccess) return r;
@@ -124,31 +124,31 @@ static cudaError_t ens_launch_lim(const EnsParams<T> &e, int grid, cudaStream_t 
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, ensemble_kernel<T, NF, LIM>, e);
+    return cudaLaunchKernelEx(&cfg, ensemble_kernel<T, NF, LIM, TYV>, e);
 }
 
-template <typename T, int NF>
+template <typename T, int NF, int TYV>
 static cudaError_t ens_launch_nf(const EnsParams<T> &e, int lim, int grid, cudaStream_t s, int *grid_out) {
     switch (lim) {
-        case ASUCA_LIM_KOREN: return ens_launch_lim<T, NF, ASUCA_LIM_KOREN>(e, grid, s, grid_out);
-        case ASUCA_LIM_LINEAR: return ens_launch_lim<T, NF, ASUCA_LIM_LINEAR>(e, grid, s, grid_out);
-        case ASUCA_LIM_UPWIND1: return ens_launch_lim<T, NF, ASUCA_LIM_UPWIND1>(e, grid, s, grid_out);
+        case ASUCA_LIM_KOREN: return ens_launch_lim<T, NF, ASUCA_LIM_KOREN, TYV>(e, grid, s, grid_out);
+        case ASUCA_LIM_LINEAR: return ens_launch_lim<T, NF, ASUCA_LIM_LINEAR, TYV>(e, grid, s, grid_out);
+        case ASUCA_LIM_UPWIND1: return ens_launch_lim<T, NF, ASUCA_LIM_UPWIND1, TYV>(e, grid, s, grid_out);
         default: return cudaErrorInvalidValue;
     }
 }
 
-template <typename T>
-cudaError_t launch_ensemble(const EnsParams<T> &e, int nf, int lim, int grid, cudaStream_t s, int *grid_out) {
+template <typename T, int TYV>
+cudaError_t launch_ensemble_ty(const EnsParams<T> &e, int nf, int lim, int grid, cudaStream_t s, int *grid_out) {
     switch (nf) {
-        case 2: return ens_launch_nf<T, 2>(e, lim, grid, s, grid_out);
-        case 3: return ens_launch_nf<T, 3>(e, lim, grid, s, grid_out);
-        case 4: return ens_launch_nf<T, 4>(e, lim, grid, s, grid_out);
-        case 5: return ens_launch_nf<T, 5>(e, lim, grid, s, grid_out);
-        case 6: return ens_launch_nf<T, 6>(e, lim, grid, s, grid_out);
-        case 7: return ens_launch_nf<T, 7>(e, lim, grid, s, grid_out);
-        case 8: return ens_launch_nf<T, 8>(e, lim, grid, s, grid_out);
-        case 9: return ens_launch_nf<T, 9>(e, lim, grid, s, grid_out);
-        case 10: return ens_launch_nf<T, 10>(e, lim, grid, s, grid_out);
+        case 2: return ens_launch_nf<T, 2, TYV>(e, lim, grid, s, grid_out);
+        case 3: return ens_launch_nf<T, 3, TYV>(e, lim, grid, s, grid_out);
+        case 4: return ens_launch_nf<T, 4, TYV>(e, lim, grid, s, grid_out);
+        case 5: return ens_launch_nf<T, 5, TYV>(e, lim, grid, s, grid_out);
+        case 6: return ens_launch_nf<T, 6, TYV>(e, lim, grid, s, grid_out);
+        case 7: return ens_launch_nf<T, 7, TYV>(e, lim, grid, s, grid_out);
+        case 8: return ens_launch_nf<T, 8, TYV>(e, lim, grid, s, grid_out);
+        case 9: return ens_launch_nf<T, 9, TYV>(e, lim, grid, s, grid_out);
+        case 10: return ens_launch_nf<T, 10, TYV>(e, lim, grid, s, grid_out);
         default: return cudaErrorInvalidValue;
     }
 }

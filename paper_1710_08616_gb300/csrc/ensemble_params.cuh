@@ -27,7 +27,17 @@ struct EnsParams {
 };
 
 // grid_out != nullptr: only store the co-resident grid size in *grid_out
+template <typename T, int TYV>
+cudaError_t launch_ensemble_ty(const EnsParams<T> &e, int nf, int lim, int grid, cudaStream_t s, int *grid_out);
+
+// tile rows ty: 4 or 8 for float, 8 for double
 template <typename T>
-cudaError_t launch_ensemble(const EnsParams<T> &e, int nf, int lim, int grid, cudaStream_t s, int *grid_out);
+inline cudaError_t launch_ensemble(const EnsParams<T> &e, int nf, int lim, int ty, int grid, cudaStream_t s,
+                                   int *grid_out) {
+    if constexpr (sizeof(T) == 4) {
+        if (ty == 4) return launch_ensemble_ty<T, 4>(e, nf, lim, grid, s, grid_out);
+    }
+    return launch_ensemble_ty<T, 8>(e, nf, lim, grid, s, grid_out);
+}
 
 }  // namespace asuca

@@ -99,10 +99,10 @@ __device__ __forceinline__ void cp_async_wait() {
 // wait limit (the status word has been set).  The caller's CTA owns smem_raw;
 // the function begins and ends with a CTA-wide barrier, so consecutive tiles
 // may reuse the same shared memory and mbarriers.
-template <typename T, int NF, int LIM, bool REC>
+template <typename T, int NF, int LIM, bool REC, int TYV = 8>
 __device__ __forceinline__ bool stage_tile(const StageParams<T> &p, const CUtensorMap *tmap, int i0, int j0,
                                            unsigned char *smem_raw) {
-    using S = StageShape<T, NF>;
+    using S = StageShape<T, NF, TYV>;
     constexpr int TX = S::TX, TY = S::TY, D = S::D, SX = S::SX, SY = S::SY, NT = S::NT;
     constexpr int NTHR = TX * TY;
     constexpr int FE = SY * SX;                   // elements of one field in a slot
@@ -361,61 +361,65 @@ __device__ __forceinline__ bool stage_tile(const StageParams<T> &p, const CUtens
     return timed_out;
 }
 
-template <typename T, int NF, int LIM, bool REC>
-__global__ void __launch_bounds__(32 * StageShape<T, NF>::TY, StageShape<T, NF>::MIN_BLOCKS)
+template <typename T, int NF, int LIM, bool REC, int TYV>
+__global__ void __launch_bounds__(32 * TYV, StageShape<T, NF, TYV>::MIN_BLOCKS)
     stage_kernel(const __grid_constant__ StageParams<T> p) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    (void)stage_tile<T, NF, LIM, REC>(p, &p.tmap, blockIdx.x * StageShape<T, NF>::TX,
-                                      blockIdx.y * StageShape<T, NF>::TY, smem_raw);
+    (void)stage_tile<T, NF, LIM, REC, TYV>(p, &p.tmap, blockIdx.x * StageShape<T, NF, TYV>::TX,
+                                           blockIdx.y * TYV, smem_raw);
 }
 
-template <typename T, int NF, int LIM, bool REC>
+template <typename T, int NF, int LIM, bool REC, int TYV>
 static cudaError_t launch_rec(const StageParams<T> &p, cudaStream_t s) {
-    using S = StageShape<T, NF>;
+    using S = StageShape<T, NF, TYV>;
     static bool attr_set = false;   // one attribute call per instantiation
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(stage_kernel<T, NF, LIM, REC>,
+        cudaError_t e = cudaFuncSetAttribute(stage_kernel<T, NF, LIM, REC, TYV>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM_BYTES);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
     dim3 block(S::TX, S::TY);
     dim3 grid((p.nx + S::TX - 1) / S::TX, (p.ny + S::TY - 1) / S::TY);
-    stage_kernel<T, NF, LIM, REC><<<grid, block, S::SMEM_BYTES, s>>>(p);
+    stage_kernel<T, NF, LIM, REC, TYV><<<grid, block, S::SMEM_BYTES, s>>>(p);
     return cudaGetLastError();
 }
 
-template <typename T, int NF, int LIM>
+// branch recording is instantiated for 8-row tiles only (the adjoint's forward pass)
+template <typename T, int NF, int LIM, int TYV>
 static cudaError_t launch_lim(const StageParams<T> &p, cudaStream_t s) {
-    return p.branch ? launch_rec<T, NF, LIM, true>(p, s) : launch_rec<T, NF, LIM, false>(p, s);
+    if (p.branch) {
+        if (TYV != 8) return cudaErrorInvalidValue;
+        return launch_rec<T, NF, LIM, true, 8>(p, s);
+    }
+    return launch_rec<T, NF, LIM, false, TYV>(p, s);
 }
 
-template <typename T, int NF>
+template <typename T, int NF, int TYV>
 static cudaError_t launch_nf(const StageParams<T> &p, cudaStream_t s) {
     switch (p.lim) {
-        case ASUCA_LIM_KOREN: return launch_lim<T, NF, ASUCA_LIM_KOREN>(p, s);
-        case ASUCA_LIM_LINEAR: return launch_lim<T, NF, ASUCA_LIM_LINEAR>(p, s);
-        case ASUCA_LIM_UPWIND1: return launch_lim<T, NF, ASUCA_LIM_UPWIND1>(p, s);
+        case ASUCA_LIM_KOREN: return launch_lim<T, NF, ASUCA_LIM_KOREN, TYV>(p, s);
+        case ASUCA_LIM_LINEAR: return launch_lim<T, NF, ASUCA_LIM_LINEAR, TYV>(p, s);
+        case ASUCA_LIM_UPWIND1: return launch_lim<T, NF, ASUCA_LIM_UPWIND1, TYV>(p, s);
         default: return cudaErrorInvalidValue;
     }
 }
 
-template <typename T>
-cudaError_t launch_stage(const StageParams<T> &p, int nf, cudaStream_t s) {
+template <typename T, int TYV>
+cudaError_t launch_stage_ty(const StageParams<T> &p, int nf, cudaStream_t s) {
     switch (nf) {
-        case 2: return launch_nf<T, 2>(p, s);
-        case 3: return launch_nf<T, 3>(p, s);
-        case 4: return launch_nf<T, 4>(p, s);
-        case 5: return launch_nf<T, 5>(p, s);
-        case 6: return launch_nf<T, 6>(p, s);
-        case 7: return launch_nf<T, 7>(p, s);
-        case 8: return launch_nf<T, 8>(p, s);
-        case 9: return launch_nf<T, 9>(p, s);
-        case 10: return launch_nf<T, 10>(p, s);
+        case 2: return launch_nf<T, 2, TYV>(p, s);
+        case 3: return launch_nf<T, 3, TYV>(p, s);
+        case 4: return launch_nf<T, 4, TYV>(p, s);
+        case 5: return launch_nf<T, 5, TYV>(p, s);
+        case 6: return launch_nf<T, 6, TYV>(p, s);
+        case 7: return launch_nf<T, 7, TYV>(p, s);
+        case 8: return launch_nf<T, 8, TYV>(p, s);
+        case 9: return launch_nf<T, 9, TYV>(p, s);
+        case 10: return launch_nf<T, 10, TYV>(p, s);
         default: return cudaErrorInvalidValue;
     }
 }
-
 
 static inline PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -431,15 +435,15 @@ static inline PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 }
 
 template <typename T>
-cudaError_t encode_stage_map(CUtensorMap *map, void *base, int nf, int nx, int ny, int nz) {
+cudaError_t encode_stage_map(CUtensorMap *map, void *base, int nf, int nx, int ny, int nz, int ty) {
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (!enc) return cudaErrorNotSupported;
-    using S = StageShape<T, 2>;   // TY, SX, SY do not depend on the field count
+    using S = StageShape<T, 2>;   // SX does not depend on the field count or the tile height
     const long long P = padded_pitch(nx);
     const cuuint64_t dims[4] = {(cuuint64_t)P, (cuuint64_t)(ny + 4), (cuuint64_t)nz, (cuuint64_t)nf};
     const cuuint64_t strides[3] = {(cuuint64_t)(P * sizeof(T)), (cuuint64_t)(P * (ny + 4) * sizeof(T)),
                                    (cuuint64_t)(P * (ny + 4) * (long long)nz * sizeof(T))};
-    const cuuint32_t box[4] = {(cuuint32_t)S::SX, (cuuint32_t)S::SY, 1u, (cuuint32_t)nf};
+    const cuuint32_t box[4] = {(cuuint32_t)S::SX, (cuuint32_t)(ty + 4), 1u, (cuuint32_t)nf};
     const cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
     CUresult r = enc(map, sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4,
                      base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,

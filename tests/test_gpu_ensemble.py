@@ -98,3 +98,38 @@ def test_barrier_timeout_reports_status(asuca):
     asuca.ensemble_step(grids, fresh, [c.dt for c in cases], 1)
     torch.cuda.synchronize()
     assert asuca.get_status(grids[0]) == asuca.OK
+
+
+def test_tile_shapes_give_identical_results_and_autotuner_picks_one(asuca, tmp_path, monkeypatch):
+    import torch
+    from paper_1710_08616_gb300 import autotune
+    monkeypatch.setenv("ASUCA_TUNE_CACHE", str(tmp_path / "tuning.json"))
+    c = gen.make_case(70, 45, 12, 3, seed=5)
+    g = asuca.Grid.from_case(c)
+    ref = None
+    for rows in (4, 8, 16):
+        for blocks in (1, 3):
+            asuca.set_tuning(g, asuca.TUNE_STAGE_TILE_ROWS, rows)
+            asuca.set_tuning(g, asuca.TUNE_COL_BLOCKS_PER_SM, blocks)
+            st = asuca.State.from_case(c)
+            asuca.step(g, st, c.dt, 3)
+            torch.cuda.synchronize()
+            if ref is None:
+                ref = st.fields()
+            assert torch.equal(st.fields(), ref), (rows, blocks)
+    out = autotune.tune_step(g, asuca.State.from_case(c), c.dt, steps=1, reps=1)
+    assert out["best"]["stage_tile_rows"] in (4, 8, 16)
+    assert autotune.apply_cached_step(g)
+    cases = _members([64, 40, 71], nz=10)
+    grids = [asuca.Grid.from_case(m) for m in cases]
+    outs = []
+    for rows in (4, 8):
+        for gg in grids:
+            asuca.set_tuning(gg, asuca.TUNE_ENSEMBLE_TILE_ROWS, rows)
+        sts = [asuca.State.from_case(m) for m in cases]
+        asuca.ensemble_step(grids, sts, [m.dt for m in cases], 2)
+        torch.cuda.synchronize()
+        outs.append([s.fields() for s in sts])
+    assert all(torch.equal(a, b) for a, b in zip(*outs))
+    e = autotune.tune_ensemble(grids, [asuca.State.from_case(m) for m in cases], [m.dt for m in cases], steps=1, reps=1)
+    assert e["best"]["ensemble_tile_rows"] in (4, 8)
