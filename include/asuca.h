@@ -172,7 +172,10 @@ typedef enum {
     ASUCA_TUNE_COL_BLOCKS_PER_SM = 0,   /* resident column-kernel blocks per SM (1..16); sizes the column scratch */
     ASUCA_TUNE_BARRIER_EXTRA = 1,       /* test hook: the ensemble barrier waits for this many extra CTAs (0) */
     ASUCA_TUNE_STAGE_TILE_ROWS = 2,     /* stage tile 32 x rows: 4, 8 (default) or 16 for FP32; 8 for FP64 */
-    ASUCA_TUNE_ENSEMBLE_TILE_ROWS = 3   /* ensemble tile 32 x rows: 4 or 8 (default) for FP32; 8 for FP64 */
+    ASUCA_TUNE_ENSEMBLE_TILE_ROWS = 3,  /* ensemble tile 32 x rows: 4 or 8 (default) for FP32; 8 for FP64 */
+    ASUCA_TUNE_STEP_MODE = 4            /* asuca_step: 0 one launch per stage and column pass; 1 one persistent
+                                           dataflow launch per 16 steps (tasks wait on per-tile counters, so the
+                                           FP64 column work overlaps the stencil stages); sizes the workspace */
 } asuca_tune_key;
 asuca_status asuca_set_tuning(asuca_grid *grid, int key, int value);
 int asuca_get_tuning(const asuca_grid *grid, int key);
@@ -206,6 +209,11 @@ asuca_status asuca_debug_column(asuca_grid *grid, asuca_state *state, double dt,
 asuca_status asuca_debug_record_branches(asuca_grid *grid, const asuca_state *initial, const void *tendencies,
                                          double dt, int nsteps, unsigned char *branches_dev, void *workspace,
                                          size_t workspace_bytes, void *cuda_stream);
+
+/* Host-only test hook: the task order of the dataflow step kernel for
+ * nphases phases (4 per step, at most 64) on nrows tile rows; out receives
+ * nphases * nrows entries (phase << 12) | row. */
+asuca_status asuca_debug_dataflow_order(int nphases, int nrows, unsigned *out);
 
 /* Test hook for the arithmetic helpers of the column solve (device arrays of
  * n values; any output may be NULL): widen[i] = in_f[i] as double, narrow[i]
@@ -250,6 +258,7 @@ typedef enum {
     ASUCA_KERNEL_ADJ_STAGE = 3, /* transpose of one RK stage */
     ASUCA_KERNEL_ADJ_COLUMN = 4,/* transpose of the column pass */
     ASUCA_KERNEL_ENSEMBLE = 5,  /* persistent ensemble kernel (all steps of a call) */
+    ASUCA_KERNEL_DATAFLOW = 6,  /* persistent dataflow step kernel (up to 16 steps) */
     ASUCA_KERNEL_KINDS = 8
 } asuca_kernel_kind;
 

@@ -82,12 +82,14 @@ SIGNATURES = {
                                            ctypes.c_size_t, _VP, _VP]),
     "asuca_set_tuning": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int]),
     "asuca_get_tuning": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "asuca_debug_dataflow_order": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _VP]),
     "asuca_profile_enable": (ctypes.c_int, [_VP, ctypes.c_int]),
     "asuca_profile_read": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
 }
 KERNEL_STAGE, KERNEL_COLUMN, KERNEL_REDUCE, KERNEL_ADJ_STAGE, KERNEL_ADJ_COLUMN, KERNEL_ENSEMBLE = 0, 1, 2, 3, 4, 5
-TUNE_COL_BLOCKS_PER_SM, TUNE_BARRIER_EXTRA, TUNE_STAGE_TILE_ROWS, TUNE_ENSEMBLE_TILE_ROWS = 0, 1, 2, 3
+TUNE_COL_BLOCKS_PER_SM, TUNE_BARRIER_EXTRA, TUNE_STAGE_TILE_ROWS, TUNE_ENSEMBLE_TILE_ROWS, TUNE_STEP_MODE = 0, 1, 2, 3, 4
+KERNEL_DATAFLOW = 6
 KERNEL_KINDS = 8
 
 

@@ -3,8 +3,9 @@
 It times candidate shapes through the public C ABI on the caller's grid and
 state (CUDA events, best of a few repetitions) and keeps the fastest per
 (GPU name, operation, domain sizes, field count, precision) in a JSON cache:
-  step:      stage tile rows (32 x 4 / 8 / 16 for FP32, 8 for FP64) and the
-             column kernel's resident blocks per SM (1..4);
+  step:      one launch per stage and column pass, with the stage tile rows
+             (32 x 4 / 8 / 16 for FP32, 8 for FP64) and the column kernel's
+             resident blocks per SM (1..4); or the persistent dataflow kernel;
   ensemble:  ensemble tile rows (32 x 4 / 8 for FP32, 8 for FP64).
 Every shape computes the same arithmetic per cell, so results do not depend
 on the choice (a GPU test checks this bit for bit).  The cache file is
@@ -15,7 +16,7 @@ from __future__ import annotations
 import json
 import os
 
-from . import (FP64, TUNE_COL_BLOCKS_PER_SM, TUNE_ENSEMBLE_TILE_ROWS, TUNE_STAGE_TILE_ROWS,
+from . import (FP64, TUNE_COL_BLOCKS_PER_SM, TUNE_ENSEMBLE_TILE_ROWS, TUNE_STAGE_TILE_ROWS, TUNE_STEP_MODE,
                ensemble_step, ensemble_workspace_bytes, get_tuning, set_tuning, step)
 
 TUNE_STAGE_TILE_ROWS_FP32 = (4, 8, 16)
@@ -80,10 +81,13 @@ def _timed(fn, reps):
 
 def step_candidates(grid):
     rows = (8,) if grid.prec == FP64 else TUNE_STAGE_TILE_ROWS_FP32
-    return [{"stage_tile_rows": r, "col_blocks_per_sm": b} for r in rows for b in COL_BLOCKS]
+    out = [{"step_mode": 0, "stage_tile_rows": r, "col_blocks_per_sm": b} for r in rows for b in COL_BLOCKS]
+    out.append({"step_mode": 1, "stage_tile_rows": 8, "col_blocks_per_sm": 3})
+    return out
 
 
 def apply_step(grid, cfg: dict) -> None:
+    set_tuning(grid, TUNE_STEP_MODE, cfg.get("step_mode", 0))
     set_tuning(grid, TUNE_STAGE_TILE_ROWS, cfg["stage_tile_rows"])
     set_tuning(grid, TUNE_COL_BLOCKS_PER_SM, cfg["col_blocks_per_sm"])
 
@@ -154,6 +158,7 @@ def apply_cached_ensemble(grids) -> bool:
 
 
 def current(grid) -> dict:
-    return {"stage_tile_rows": get_tuning(grid, TUNE_STAGE_TILE_ROWS),
+    return {"step_mode": get_tuning(grid, TUNE_STEP_MODE),
+            "stage_tile_rows": get_tuning(grid, TUNE_STAGE_TILE_ROWS),
             "col_blocks_per_sm": get_tuning(grid, TUNE_COL_BLOCKS_PER_SM),
             "ensemble_tile_rows": get_tuning(grid, TUNE_ENSEMBLE_TILE_ROWS)}

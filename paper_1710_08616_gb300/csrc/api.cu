@@ -9,6 +9,7 @@
 
 #include "adjoint_params.cuh"
 #include "ensemble_params.cuh"
+#include "dataflow_params.cuh"
 #include "common.cuh"
 
 using namespace asuca;
@@ -23,6 +24,10 @@ struct asuca_grid {
     int col_blocks_per_sm;        // tuning knob behind col_grid
     int barrier_extra;            // test hook: extra arrivals the ensemble barrier waits for
     int stage_ty;                 // tile rows of the stage kernel (tuned; 8 for FP64)
+    int step_mode;                // 0: one launch per stage and column pass; 1: persistent dataflow kernel
+    int df_grid;                  // co-resident CTAs of the dataflow kernel (0 until queried)
+    unsigned *df_order_host[2];   // pinned wave-order tables: a full chunk and the remainder chunk
+    int df_order_q[2];
     int ens_ty;                   // tile rows of the ensemble kernel (tuned; 8 for FP64)
     std::vector<void *> *kept_pinned;   // parameter buffers referenced by a caller's captured graphs
     volatile int *status_host;    // pinned, mapped; the device writes error codes here
@@ -62,8 +67,14 @@ size_t elem_size(const asuca_grid *g) { return g->d.prec == ASUCA_FP64 ? 8 : 4; 
 long long col_slots(const asuca_grid *g) { return (long long)g->col_grid * COL_TPB; }
 
 struct StepLayout {
-    size_t ystar, ystar2, precip, partials, scratch, total;
+    size_t ystar, ystar2, precip, partials, scratch, df_order, df_counter, df_flags, df_partials, df_scratch, total;
 };
+
+constexpr int DF_CHUNK = 16;   // steps per dataflow launch
+
+int df_tiles_x(const asuca_grid *g) { return (g->d.nx + 31) / 32; }
+int df_tiles_y(const asuca_grid *g) { return (g->d.ny + 7) / 8; }
+int df_grid_size(asuca_grid *g);
 
 size_t padded_field_elems(const asuca_grid *g) {
     return (size_t)g->d.nz * (g->d.ny + 4) * padded_pitch(g->d.nx);
@@ -83,6 +94,22 @@ StepLayout step_layout(const asuca_grid *g) {
     off = align_up(off + (size_t)g->col_grid * (g->F + 1) * sizeof(double));
     L.scratch = off;
     off = align_up(off + (size_t)g->d.nz * (g->F + 1) * col_slots(g) * sizeof(double));
+    L.df_order = L.df_counter = L.df_flags = L.df_partials = L.df_scratch = off;
+    if (g->step_mode == 1) {
+        const size_t R = (size_t)df_tiles_y(g), tiles = R * df_tiles_x(g);
+        L.df_order = off;
+        off = align_up(off + 2 * (4 * DF_CHUNK * R) * sizeof(unsigned));
+        L.df_counter = off;
+        off = align_up(off + sizeof(unsigned));
+        L.df_flags = off;
+        off = align_up(off + tiles * sizeof(unsigned));
+        L.df_partials = off;
+        off = align_up(off + tiles * (g->F + 1) * sizeof(double));
+        L.df_scratch = off;
+        // the co-resident grid is a property of the device and the kernel; it is cached in the grid
+        const int dg = df_grid_size(const_cast<asuca_grid *>(g));
+        off = align_up(off + (size_t)g->d.nz * (g->F + 1) * (size_t)dg * 256 * sizeof(double));
+    }
     L.total = off;
     return L;
 }
@@ -207,9 +234,34 @@ cudaError_t timed(asuca_grid *g, int kind, cudaStream_t s, Fn f) {
     return cudaSuccess;
 }
 
+// Order of the dataflow tasks for Q phases on R tile rows, entries (q << 12) | r.
+// Phase q of row r reads phase q-1 of rows r-1, r, r+1, periodic in the row
+// index, so the rows form a ring.  Entries are sorted by the slot
+// 2 q + d(r) with d(r) = min(r, R - r): ring neighbours differ by at most 1
+// in d, hence every input comes at least one slot earlier, and rows far from
+// row 0 lag behind by up to R/2 slots, so phases of different steps
+// interleave across the ring.
+void df_fill_order(unsigned *out, int Q, int R) {
+    int n = 0;
+    const int dmax = R / 2;
+    for (int w = 0; w <= 2 * (Q - 1) + dmax; w++)
+        for (int r = 0; r < R; r++) {
+            const int d = r < R - r ? r : R - r;
+            const int t = w - d;
+            if (t < 0 || (t & 1)) continue;
+            const int q = t / 2;
+            if (q < Q) out[n++] = ((unsigned)q << 12) | (unsigned)r;
+        }
+}
+
+template <typename T>
+asuca_status run_step_dataflow(asuca_grid *g, asuca_state *st, const void *tend, double dt, int nsteps,
+                               char *ws, double *budgets, cudaStream_t s);
+
 template <typename T>
 asuca_status run_step(asuca_grid *g, asuca_state *st, const void *tend, double dt, int nsteps,
                       char *ws, double *budgets, cudaStream_t s) {
+    if (g->step_mode == 1) return run_step_dataflow<T>(g, st, tend, dt, nsteps, ws, budgets, s);
     const StepLayout L = step_layout(g);
     const int F = g->F;
     T *yn[MAXF], *y1[MAXF], *y2[MAXF];
@@ -269,6 +321,122 @@ asuca_status run_step(asuca_grid *g, asuca_state *st, const void *tend, double d
                                         g->status_dev, s);
         });
         if (e != cudaSuccess) return ASUCA_ERR_CUDA;
+    }
+    return ASUCA_OK;
+}
+
+int df_grid_size(asuca_grid *g) {
+    if (g->df_grid <= 0) {
+        DfParams<double> d64;
+        DfParams<float> d32;
+        int grid = 0;
+        cudaError_t e = g->d.prec == ASUCA_FP64 ? launch_dataflow<double>(d64, g->F, (int)g->d.lim, 0, nullptr, &grid)
+                                                : launch_dataflow<float>(d32, g->F, (int)g->d.lim, 0, nullptr, &grid);
+        g->df_grid = (e == cudaSuccess && grid > 0) ? grid : 0;
+    }
+    return g->df_grid;
+}
+
+template <typename T>
+asuca_status run_step_dataflow(asuca_grid *g, asuca_state *st, const void *tend, double dt, int nsteps,
+                               char *ws, double *budgets, cudaStream_t s) {
+    const StepLayout L = step_layout(g);
+    const int F = g->F, R = df_tiles_y(g), TXn = df_tiles_x(g);
+    const int grid = df_grid_size(g);
+    if (grid <= 0 || R > 4095) return ASUCA_ERR_UNSUPPORTED;
+    T *yn[MAXF], *y1[MAXF], *y2[MAXF];
+    field_ptrs<T>(g, st->rho, st->rhotheta, st->rhoq, yn);
+    workspace_fields<T>(g, ws, L.ystar, y1);
+    workspace_fields<T>(g, ws, L.ystar2, y2);
+    if (cudaMemsetAsync(ws + L.precip, 0, (size_t)g->plane * sizeof(double), s) != cudaSuccess) return ASUCA_ERR_CUDA;
+    if (g->map_ws != (void *)ws || g->map_ty != 8) {
+        if (encode_stage_map<T>(&g->map_ystar, ws + L.ystar, F, g->d.nx, g->d.ny, g->d.nz, 8) != cudaSuccess ||
+            encode_stage_map<T>(&g->map_ystar2, ws + L.ystar2, F, g->d.nx, g->d.ny, g->d.nz, 8) != cudaSuccess) {
+            g->map_ws = nullptr;
+            return ASUCA_ERR_CUDA;
+        }
+        g->map_ws = (void *)ws;
+        g->map_ty = 8;
+    }
+    DfParams<T> p;
+    std::memset(&p, 0, sizeof(p));
+    const T cdt[3] = {(T)(dt / 3.0), (T)(dt / 2.0), (T)dt};
+    for (int stg = 0; stg < 3; stg++) {
+        StageParams<T> sp = stage_params<T>(g, st, tend);
+        sp.ty = 8;
+        sp.tma_in = stg > 0;
+        if (stg == 1) sp.tmap = g->map_ystar;
+        if (stg == 2) sp.tmap = g->map_ystar2;
+        sp.out_padded = stg < 2;
+        T **out = stg == 0 ? y1 : (stg == 1 ? y2 : yn);
+        for (int f = 0; f < MAXF; f++) {
+            sp.yin[f] = yn[f];
+            sp.ybase[f] = yn[f];
+            sp.yout[f] = out[f];
+        }
+        sp.cdt = cdt[stg];
+        p.stage[stg] = sp;
+    }
+    p.col = column_params<T>(g, dt);
+    for (int f = 0; f < MAXF; f++) p.col.y[f] = yn[f];
+    p.col.precip_col = (double *)(ws + L.precip);
+    p.col.budgets = 0;
+    p.col_last = p.col;
+    p.col_last.budgets = budgets != nullptr;
+    p.txn = TXn;
+    p.tyn = R;
+    p.counter = (unsigned *)(ws + L.df_counter);
+    p.flags = (unsigned *)(ws + L.df_flags);
+    p.scratch = (double *)(ws + L.df_scratch);
+    p.partials = (double *)(ws + L.df_partials);
+    p.status = g->status_dev;
+    const size_t tiles = (size_t)R * TXn;
+    for (int c0 = 0; c0 < nsteps; c0 += DF_CHUNK) {
+        const int n = (nsteps - c0) < DF_CHUNK ? (nsteps - c0) : DF_CHUNK;
+        const int which = n == DF_CHUNK ? 0 : 1, Q = 4 * n;
+        if (!g->df_order_host[which]) {
+            void *h = nullptr;
+            if (cudaHostAlloc(&h, (size_t)4 * DF_CHUNK * R * sizeof(unsigned), cudaHostAllocDefault) != cudaSuccess)
+                return ASUCA_ERR_CUDA;
+            g->df_order_host[which] = (unsigned *)h;
+            g->df_order_q[which] = -1;
+        }
+        if (g->df_order_q[which] != Q) {   // contents only change with Q (the grid fixes R)
+            df_fill_order(g->df_order_host[which], Q, R);
+            g->df_order_q[which] = Q;
+        }
+        unsigned *dorder = (unsigned *)(ws + L.df_order) + (size_t)which * 4 * DF_CHUNK * R;
+        if (cudaMemcpyAsync(dorder, g->df_order_host[which], (size_t)Q * R * sizeof(unsigned), cudaMemcpyHostToDevice,
+                            s) != cudaSuccess ||
+            cudaMemsetAsync(ws + L.df_counter, 0, sizeof(unsigned), s) != cudaSuccess ||
+            cudaMemsetAsync(ws + L.df_flags, 0, tiles * sizeof(unsigned), s) != cudaSuccess)
+            return ASUCA_ERR_CUDA;
+        p.order = dorder;
+        p.nslot = Q * R;
+        const bool last_chunk = c0 + n >= nsteps;
+        p.last_q0 = (last_chunk && budgets) ? 4 * (n - 1) + 3 : Q + 1;
+        if (timed(g, ASUCA_KERNEL_DATAFLOW, s, [&] { return launch_dataflow<T>(p, F, (int)g->d.lim, grid, s, nullptr); }) !=
+            cudaSuccess)
+            return ASUCA_ERR_CUDA;
+    }
+    if (budgets) {
+        if (nsteps == 0) {
+            ColumnParams<T> cp = column_params<T>(g, dt);
+            for (int f = 0; f < MAXF; f++) cp.y[f] = yn[f];
+            cp.do_phys = 0;
+            cp.budgets = 1;
+            cp.precip_col = (double *)(ws + L.precip);
+            cp.partials = (double *)(ws + L.partials);
+            if (launch_column<T>(cp, F, g->col_grid, COL_TPB, s) != cudaSuccess ||
+                launch_budget_reduce(cp.partials, g->col_grid, F + 1, F, g->d.dx * g->d.dy, budgets, g->status_dev, s) !=
+                    cudaSuccess)
+                return ASUCA_ERR_CUDA;
+        } else if (timed(g, ASUCA_KERNEL_REDUCE, s, [&] {
+                       return launch_budget_reduce(p.partials, (int)tiles, F + 1, F, g->d.dx * g->d.dy, budgets,
+                                                   g->status_dev, s);
+                   }) != cudaSuccess) {
+            return ASUCA_ERR_CUDA;
+        }
     }
     return ASUCA_OK;
 }
@@ -800,6 +968,7 @@ asuca_status asuca_init_grid(const asuca_grid_desc *desc, asuca_grid **out) {
     g->col_blocks_per_sm = col_blocks_per_sm();
     g->stage_ty = 8;
     g->ens_ty = 8;
+    g->step_mode = 0;
     set_col_grid(g);
     void *h = nullptr;
     if (cudaHostAlloc(&h, 64, cudaHostAllocMapped) != cudaSuccess) {
@@ -822,6 +991,8 @@ asuca_status asuca_free_grid(asuca_grid *g) {
     if (!g) return ASUCA_ERR_ARG;
     if (g->status_host) cudaFreeHost((void *)g->status_host);
     for (int q = 0; q < g->prof_cap; q++) cudaEventDestroy(g->prof_ev[q]);
+    for (int w = 0; w < 2; w++)
+        if (g->df_order_host[w]) cudaFreeHost(g->df_order_host[w]);
     if (g->kept_pinned) {
         for (void *p : *g->kept_pinned) cudaFreeHost(p);
         delete g->kept_pinned;
@@ -1010,6 +1181,10 @@ asuca_status asuca_set_tuning(asuca_grid *g, int key, int value) {
             if (g->d.prec == ASUCA_FP64 ? value != 8 : (value != 4 && value != 8)) return ASUCA_ERR_ARG;
             g->ens_ty = value;
             return ASUCA_OK;
+        case ASUCA_TUNE_STEP_MODE:
+            if (value != 0 && value != 1) return ASUCA_ERR_ARG;
+            g->step_mode = value;
+            return ASUCA_OK;
         default: return ASUCA_ERR_ARG;
     }
 }
@@ -1021,6 +1196,7 @@ int asuca_get_tuning(const asuca_grid *g, int key) {
         case ASUCA_TUNE_BARRIER_EXTRA: return g->barrier_extra;
         case ASUCA_TUNE_STAGE_TILE_ROWS: return g->stage_ty;
         case ASUCA_TUNE_ENSEMBLE_TILE_ROWS: return g->ens_ty;
+        case ASUCA_TUNE_STEP_MODE: return g->step_mode;
         default: return -1;
     }
 }
@@ -1137,6 +1313,12 @@ asuca_status asuca_debug_numerics(const float *in_f, const double *in_d, int n, 
                                   float *narrow, double *rcp, void *cuda_stream) {
     if (n < 0 || (n > 0 && ((widen && !in_f) || ((narrow || rcp) && !in_d)))) return ASUCA_ERR_ARG;
     return cuda_status(launch_numerics(in_f, in_d, n, widen, narrow, rcp, (cudaStream_t)cuda_stream));
+}
+
+asuca_status asuca_debug_dataflow_order(int nphases, int nrows, unsigned *out) {
+    if (nphases < 1 || nrows < 1 || nrows > 4095 || nphases > 4 * DF_CHUNK || !out) return ASUCA_ERR_ARG;
+    df_fill_order(out, nphases, nrows);
+    return ASUCA_OK;
 }
 
 asuca_status asuca_profile_enable(asuca_grid *g, int on) {

@@ -88,3 +88,20 @@ def test_null_arguments(lib):
     assert lib.asuca_free_grid(None) == asuca.ERR_ARG
     assert lib.asuca_workspace_bytes(None, 0, 0) == 0
     assert lib.asuca_step(None, None, None, 1.0, 1, None, 0, None, None) == asuca.ERR_ARG
+
+
+@pytest.mark.parametrize("Q,R", [(4, 1), (4, 2), (8, 3), (64, 5), (64, 128), (12, 129)])
+def test_dataflow_task_order_is_topological(lib, Q, R):
+    """Host logic of the dataflow kernel: every (phase, row) task appears once
+    and after the tasks it reads (phase - 1 on rows r - 1, r, r + 1, periodic)."""
+    import numpy as np
+    out = np.zeros(Q * R, dtype=np.uint32)
+    assert lib.asuca_debug_dataflow_order(Q, R, out.ctypes.data_as(ctypes.c_void_p)) == asuca.OK
+    tasks = [(int(v) >> 12, int(v) & 0xFFF) for v in out]
+    assert len(set(tasks)) == Q * R
+    pos = {t: k for k, t in enumerate(tasks)}
+    for (q, r), k in pos.items():
+        for dr in (-1, 0, 1):
+            if q > 0:
+                assert pos[(q - 1, (r + dr) % R)] < k
+    assert lib.asuca_debug_dataflow_order(65, 4, out.ctypes.data_as(ctypes.c_void_p)) == asuca.ERR_ARG

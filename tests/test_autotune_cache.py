@@ -37,3 +37,4 @@ def test_candidates():
     assert {c["stage_tile_rows"] for c in c32} == {4, 8, 16}
     assert {c["stage_tile_rows"] for c in c64} == {8}
     assert {c["col_blocks_per_sm"] for c in c32} == {1, 2, 3, 4}
+    assert {c["step_mode"] for c in c32} == {0, 1}

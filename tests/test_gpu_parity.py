@@ -247,3 +247,29 @@ def test_integer_pipe_conversions_match_hardware(asuca):
     exact = 1.0 / x
     ulps = ((r - exact).abs() / torch.abs(exact) / 2.0 ** -52).max().item()
     assert ulps <= 2.0, ulps
+
+
+# ------------------------------------------------------------------ dataflow step mode
+
+@pytest.mark.parametrize("prec", [1, 0])
+@pytest.mark.parametrize("shape,ntr,nsteps", [((70, 45, 12), 3, 20), ((32, 32, 16), 3, 3), ((100, 9, 7), 1, 2),
+                                              ((4, 4, 3), 0, 17)])
+def test_dataflow_mode_equals_stage_launches(asuca, prec, shape, ntr, nsteps):
+    """The persistent dataflow kernel runs the same per-cell arithmetic as the
+    per-stage launches, only in another order, so results match bit for bit
+    (20 steps span two 16-step launches)."""
+    import torch
+    nx, ny, nz = shape
+    c = gen.make_case(nx, ny, nz, ntr, seed=77 + nx)
+    g0 = asuca.Grid.from_case(c, prec=prec)
+    g1 = asuca.Grid.from_case(c, prec=prec)
+    asuca.set_tuning(g1, asuca.TUNE_STEP_MODE, 1)
+    a = asuca.State.from_case(c, prec=prec)
+    b = a.clone()
+    ba = asuca.step(g0, a, c.dt, nsteps, budgets=True)
+    bb = asuca.step(g1, b, c.dt, nsteps, budgets=True)
+    torch.cuda.synchronize()
+    assert asuca.get_status(g1) == asuca.OK
+    assert torch.equal(a.fields(), b.fields())
+    rel = (ba - bb).abs() / ba.abs().clamp_min(1e-300)
+    assert float(rel.max()) <= 1e-13
