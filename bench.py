@@ -43,6 +43,25 @@ def _peaks():
     return 6800.0, "fallback"
 
 
+def _recorded_traffic(kernel, cells):
+    """DRAM bytes per launch of `kernel` from the recorded ncu capture, scaled to
+    `cells`; None when the record is missing or the kernel's sources changed since."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(p) as fh:
+            rec = json.load(fh)[kernel]
+        h = hashlib.sha256()
+        for f in rec["sources"]:
+            with open(os.path.join(ROOT, "paper_1710_08616_gb300", "csrc", f), "rb") as fh:
+                h.update(fh.read())
+        if h.hexdigest()[:16] != rec["source_sha256_16"]:
+            return None
+        return rec["bytes_per_cell"] * cells
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 # ---------------------------------------------------------------- clocks
 
 class ClockSampler:
@@ -324,7 +343,12 @@ def run_ours(args):
     import paper_1710_08616_gb300 as asuca
     import gen
 
-    case = gen.make_config_case(WORKLOAD)
+    if args.nx == 1024:
+        case = gen.make_config_case(WORKLOAD)
+        workload = WORKLOAD
+    else:   # a smaller case of the same workload, for profiler captures
+        case = gen.make_config_case(WORKLOAD, nx=args.nx, ny=args.nx)
+        workload = f"profile_{args.nx}x{args.nx}x58"
     F = case.nfields
     C = case.cells
     dev = torch.device("cuda", torch.cuda.current_device())
@@ -367,7 +391,7 @@ def run_ours(args):
     ach = kern[dname]["achieved_gbs"] if dname in kern else None
     roofline = {"kernel": dname, "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
                 "frac": (ach / hbm_peak) if ach else None, "peak_source": peak_kind,
-                "traffic": None,
+                "traffic": _recorded_traffic(dname, C) if dname == "stage" else None,
                 "step_frac": (10 * F + 8) * s * C / (ms / args.steps * 1e-3) / 1e9 / hbm_peak,
                 "step_model_bytes_per_cell": (10 * F + 8) * s, "kernels": kern}
 
@@ -436,7 +460,7 @@ def run_ours(args):
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-               "config": {"workload": WORKLOAD, "nx": case.nx, "ny": case.ny, "nz": case.nz,
+               "config": {"workload": workload, "nx": case.nx, "ny": case.ny, "nz": case.nz,
                           "ntracers": case.ntracers, "cells": C, "dt_s": case.dt,
                           "precision": "fp32 fields/stencils/physics, fp64 Thomas solve and budget sums",
                           "limiter": "koren", "l2": "inputs larger than L2 (2.4 GB state), no flush",
@@ -467,6 +491,9 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--ens-steps", type=int, default=10)
+    ap.add_argument("--nx", type=int, default=1024,
+                    help="nx = ny of the timed case; anything but 1024 is a smaller case of the same "
+                         "workload for profiler captures, not a bench line")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
