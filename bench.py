@@ -139,7 +139,8 @@ def _max_over_ranks(ws, v):
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -276,6 +277,48 @@ def adjoint_cost(asuca, dev, reps=3):
         del st0, ws, wsa, lam
         torch.cuda.empty_cache()
     return out
+
+
+def precision_report(asuca, dev):
+    """256x256x58, 6 tracers, 100 steps from the same initial state in FP32-mixed
+    and in FP64 on the GPU: per-field relative L2 and max error of FP32 against
+    FP64, and the drift of the FP64 budgets over the run (mass; each tracer plus
+    its precipitation for the sedimenting one) in both precisions."""
+    import numpy as np
+    import torch
+    import gen
+    name = "precision_256x256x58"
+    case = gen.make_config_case(name)
+    nsteps = gen.CONFIGS[name]["nsteps"]
+    res, buds, times = {}, {}, {}
+    for label, prec in (("fp64", asuca.FP64), ("fp32", asuca.FP32_MIXED)):
+        g = asuca.Grid.from_case(case, prec=prec)
+        st = asuca.State.from_case(case, prec=prec, device=dev)
+        b0 = asuca.step(g, st, case.dt, 0, budgets=True).cpu().numpy()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        b1 = asuca.step(g, st, case.dt, nsteps, budgets=True)
+        e1.record()
+        torch.cuda.synchronize()
+        assert asuca.get_status(g) == asuca.OK
+        times[label] = e0.elapsed_time(e1) / nsteps
+        res[label] = st.fields().double().cpu().numpy()
+        buds[label] = (b0, b1.cpu().numpy())
+    names = ["rho", "rhotheta"] + [f"rhoq{n + 1}" for n in range(case.ntracers)]
+    errs = {}
+    for f, nm in enumerate(names):
+        d = res["fp32"][f] - res["fp64"][f]
+        errs[nm] = {"rel_l2": float(np.linalg.norm(d) / np.linalg.norm(res["fp64"][f])),
+                    "rel_max": float(np.abs(d).max() / np.abs(res["fp64"][f]).max())}
+    drift = {}
+    F = case.nfields
+    for label, (b0, b1) in buds.items():
+        tr = b1[2:F].copy()
+        tr[-1] += b1[F]      # the sedimenting (last) tracer: mass aloft + precipitation
+        drift[label] = {"mass": float((b1[0] - b0[0]) / b0[0]),
+                        "tracers_plus_precip": [float(v) for v in (tr - b0[2:F]) / b0[2:F]]}
+    return {"workload": name, "nsteps": nsteps, "fp32_vs_fp64_gpu": errs, "budget_drift": drift,
+            "ms_per_step": times, "fp32_over_fp64_speedup": times["fp64"] / times["fp32"]}
 
 
 def ensemble_throughput(asuca, dev, nsteps=10, reps=3):
@@ -445,6 +488,9 @@ def run_ours(args):
                 "kernels": {kinds.get(k, str(k)): {"launches": n, "avg_ms": t / n} for k, (t, n) in prof64.items()}}
         del st64, ws64
 
+    precision = None
+    if not args.no_precision:
+        precision = precision_report(asuca, dev)
     adjoint = None
     if not args.no_adjoint:
         adjoint = adjoint_cost(asuca, dev)
@@ -466,7 +512,7 @@ def run_ours(args):
                           "limiter": "koren", "l2": "inputs larger than L2 (2.4 GB state), no flush",
                           "parallelism": f"{world} independent replica(s), one per GPU"},
                "clocks": clocks, "gpu_launches": 5 * args.steps, "roofline": roofline,
-               "e2e": e2e, "fp64": fp64, "adjoint": adjoint, "ensemble": ensemble,
+               "e2e": e2e, "fp64": fp64, "precision": precision, "adjoint": adjoint, "ensemble": ensemble,
                "fp32_over_fp64_speedup": (value / fp64["value"]) if fp64 else None,
                "cpu_baseline": cpu}
         print(json.dumps(out), flush=True)
@@ -489,6 +535,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-precision", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--ens-steps", type=int, default=10)
     ap.add_argument("--nx", type=int, default=1024,

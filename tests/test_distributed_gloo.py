@@ -1,0 +1,78 @@
+"""Multi-rank host logic on CPU (gloo, world size 2): sharding ensemble members
+over ranks, the exact FP64 budget gather, and the benchmark's max-over-ranks
+timing.  The GPU-side step of each rank is the single-GPU path tested elsewhere."""
+import os
+import socket
+
+import numpy as np
+import pytest
+
+from paper_1710_08616_gb300.distributed import shard_members
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def test_shard_members_covers_each_member_once_and_balances():
+    import gen
+    sizes = gen.ensemble_sizes()
+    cells = [n * n * 58 for n in sizes]
+    for world in (1, 2, 3, 4, 8, 40):
+        sh = shard_members(cells, world)
+        assert len(sh) == world
+        flat = sorted(m for r in sh for m in r)
+        assert flat == list(range(len(cells)))
+        loads = [sum(cells[m] for m in r) for r in sh]
+        # greedy largest-first: no rank exceeds the mean load by more than the largest member
+        assert max(loads) <= sum(cells) / world + max(cells)
+        assert sh == shard_members(cells, world)     # deterministic
+
+
+def test_shard_members_small_cases():
+    assert shard_members([5, 5, 5, 5], 2) == [[0, 2], [1, 3]]
+    assert shard_members([10, 1, 1, 1], 2) == [[0], [1, 2, 3]]
+    assert shard_members([], 3) == [[], [], []]
+    assert shard_members([3], 2) == [[0], []]
+    with pytest.raises(ValueError):
+        shard_members([1], 0)
+
+
+def _worker(rank, world, port, q):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    os.environ["RANK"] = str(rank)
+    os.environ["WORLD_SIZE"] = str(world)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        from paper_1710_08616_gb300.distributed import gather_budgets
+        import bench
+        M, nb = 7, 5
+        rng = np.random.default_rng(99)
+        full = rng.standard_normal((M, nb)) * 10.0 ** rng.integers(-20, 20, (M, nb))
+        sh = shard_members([(m * 37) % 11 + 1 for m in range(M)], world)
+        got = gather_budgets({m: full[m] for m in sh[rank]}, M, nb)
+        tmax = bench._max_over_ranks(world, 1.5 + rank)
+        q.put((rank, got.tobytes() == full.tobytes(), tmax))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_gloo_world2_budget_gather_and_max_over_ranks():
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = [q.get(timeout=120) for _ in procs]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, exact, tmax in res:
+        assert exact, f"rank {rank}: gathered budgets differ"
+        assert tmax == 2.5

@@ -176,6 +176,37 @@ def test_budgets_only_call(asuca):
     assert np.all(np.abs(bud.cpu().numpy() - rb) <= TOL64 * np.abs(rb) + 1e-300)
 
 
+# ------------------------------------------------------------------ precision workload, full size
+
+@pytest.fixture(scope="module")
+def precision_ref():
+    """The FP64 oracle after 100 steps of the 256x256x58, 6-tracer workload
+    (about two minutes on the host cores)."""
+    c = gen.make_config_case("precision_256x256x58")
+    og = oracle.Grid.from_case(c)
+    ref, rbud = oracle.step(og, c.state(), c.mu, c.mv, c.mw, c.dt, gen.CONFIGS["precision_256x256x58"]["nsteps"])
+    return c, ref, rbud
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("prec,tol", [(0, TOL64), (1, TOL32)])
+def test_precision_256x256x58_100_steps(asuca, precision_ref, prec, tol):
+    """The whole 100-step run of the precision workload, every cell of every
+    field against the oracle: FP64 within 1e-12 (L2 and max), FP32-mixed within
+    2e-5 relative L2 per field; the FP64 budgets (mass, rho theta, tracers,
+    precipitation) within the same bars."""
+    import torch
+    c, ref, rbud = precision_ref
+    g = asuca.Grid.from_case(c, prec=prec)
+    st = asuca.State.from_case(c, prec=prec)
+    bud = asuca.step(g, st, c.dt, gen.CONFIGS["precision_256x256x58"]["nsteps"], budgets=True)
+    torch.cuda.synchronize()
+    assert asuca.get_status(g) == asuca.OK
+    _assert_fields(_np(st), ref, tol, f"precision prec={prec}", both=(prec == 0))
+    bud = bud.cpu().numpy()
+    assert np.all(np.abs(bud - rbud) <= tol * np.abs(rbud))
+
+
 # ------------------------------------------------------------------ full size, sampled
 
 SAMPLES = [(0, 0), (1023, 1023), (511, 0), (0, 700), (1023, 5)]
