@@ -371,17 +371,31 @@ void orc_column(const orc_grid *g, double *Y, double dt, double *precip_col) {
 
 /* ------------------------------------------------------------ budgets */
 
+/* Compensated summation (Neumaier, 1974): the running sum s and the rounding
+ * errors c of its additions, recovered exactly by Fast2Sum ordered by
+ * magnitude.  The result is within about 2 ulp of the exact sum of the terms
+ * for any count, where a plain running sum drifts by up to n ulp (a budget
+ * sums tens of millions of cells). */
+typedef struct { double s, c; } csum;
+static void csum_add(csum *a, double x) {
+    const double t = a->s + x;
+    if (fabs(a->s) >= fabs(x)) a->c += (a->s - t) + x;
+    else a->c += (x - t) + a->s;
+    a->s = t;
+}
+static double csum_value(const csum *a) { return a->s + a->c; }
+
 void orc_budgets(const orc_grid *g, const double *Y, double precip, double *out) {
     const int F = 2 + g->ntr, nz = g->nz;
     const size_t cs = (size_t)g->ny * g->nx, fs = (size_t)nz * cs;
     for (int f = 0; f < F; f++) {
-        double s = 0.0;
-        /* fixed order: k innermost, then i, then j */
+        csum s = {0.0, 0.0};
+        /* sum over cells of f dV, dV = dz_k dx dy; fixed order: k innermost, then i, then j */
         for (int j = 0; j < g->ny; j++)
             for (int i = 0; i < g->nx; i++)
                 for (int k = 0; k < nz; k++)
-                    s += Y[f * fs + k * cs + (size_t)j * g->nx + i] * g->dz[k] * g->dx * g->dy;
-        out[f] = s;
+                    csum_add(&s, Y[f * fs + k * cs + (size_t)j * g->nx + i] * g->dz[k] * g->dx * g->dy);
+        out[f] = csum_value(&s);
     }
     out[F] = precip;
 }
@@ -397,10 +411,10 @@ void orc_step(const orc_grid *g, double *Y, const double *mu, const double *mv,
         orc_column(g, Y, dt, pc);
     }
     if (budgets) {
-        double tot = 0.0;
+        csum tot = {0.0, 0.0};
         for (int j = 0; j < g->ny; j++)
-            for (int i = 0; i < g->nx; i++) tot += pc[(size_t)j * g->nx + i];
-        orc_budgets(g, Y, tot, budgets);
+            for (int i = 0; i < g->nx; i++) csum_add(&tot, pc[(size_t)j * g->nx + i]);
+        orc_budgets(g, Y, csum_value(&tot), budgets);
     }
     free(pc);
 }

@@ -366,6 +366,32 @@ def test_thread_count_does_not_change_results():
     assert np.array_equal(a, b) and np.array_equal(ba, bb)
 
 
+def test_budgets_are_the_correctly_rounded_sum():
+    """Budgets are sums over every cell of f dV (dV = dz_k dx dy).  Against
+    Python's math.fsum of the same products (correctly rounded, Shewchuk's
+    algorithm), on a field with cancellation and a wide range of magnitudes,
+    the oracle's sum agrees to a few ulp of the sum of |terms|; a plain running
+    sum over this many terms is off by far more."""
+    rng = np.random.default_rng(5)
+    nx, ny, nz = 96, 80, 12
+    dz = np.geomspace(40.0, 1000.0, nz)
+    g = oracle.Grid(nx, ny, nz, 0, dz, 2000.0, 2000.0)
+    Y = rng.standard_normal((2, nz, ny, nx)) * 10.0 ** rng.uniform(-3, 6, (2, nz, ny, nx))
+    Y[0] += 1e7          # a large common offset, as a mass budget has
+    out = oracle.budgets(g, Y, precip=0.25)
+    for f in range(2):
+        terms = ((Y[f] * dz[:, None, None]) * 2000.0) * 2000.0
+        exact = math.fsum(terms.ravel().tolist())
+        scale = math.fsum(np.abs(terms).ravel().tolist())
+        assert abs(out[f] - exact) <= 4 * np.finfo(float).eps * scale, (f, out[f], exact)
+        if f == 1:   # the cancelling field: correct to a few ulp of the result itself
+            assert abs(out[f] - exact) <= 4 * np.finfo(float).eps * abs(exact) + 1e-300
+        # the bound is tight enough to tell: a plain running sum in the same order misses it
+        plain = np.cumsum(terms.transpose(1, 2, 0).ravel())[-1]
+        assert abs(plain - exact) > 4 * np.finfo(float).eps * scale
+    assert out[2] == 0.25
+
+
 @pytest.mark.parametrize("w", [1.0, -1.0])
 def test_vertical_kappa_third_exact_for_quadratics_and_ghosts(w):
     """The kappa=1/3 face value is exact for cell averages of z^2: with
