@@ -117,24 +117,24 @@ __global__ void __launch_bounds__(128) adj_stage_kernel(const __grid_constant__ 
             // gradient of M at the cell's own faces
             const T *Y = p.ys[f + 1];
             const T *R0 = p.ys[0];
-            auto phi = [&](long long off) { return Y[off] / R0[off]; };
-            const T ph = Y[skb + sx[2]] * rr;
+            // phi as the forward stage saw it: stored as phi in the padded
+            // stage buffers, as rho*phi (converted with the reciprocal of rho) otherwise
+            const bool sphi = p.ys_phi != 0;
+            auto phi = [&](long long off) { return sphi ? Y[off] : Y[off] * recip(R0[off]); };
+            const T ph = sphi ? Y[skb + sx[2]] : Y[skb + sx[2]] * rr;
             {
                 const T mx = mxf[2];
-                const T fx = face_fast<LIM>(phi(skb + sx[1]), ph, phi(skb + sx[3]), phi(skb + sx[4]), mx >= T(0),
-                                            mx >= T(0) ? T(0.5) : T(-0.5));
+                const T fx = face_val4<LIM>(phi(skb + sx[1]), ph, phi(skb + sx[3]), phi(skb + sx[4]), mx >= T(0));
                 gx += cs * (L[kb + ox[3]] - L[own]) * rdx * fx;
                 const T my = myf[2];
-                const T fy = face_fast<LIM>(phi(skb + sy[1]), ph, phi(skb + sy[3]), phi(skb + sy[4]), my >= T(0),
-                                            my >= T(0) ? T(0.5) : T(-0.5));
+                const T fy = face_val4<LIM>(phi(skb + sy[1]), ph, phi(skb + sy[3]), phi(skb + sy[4]), my >= T(0));
                 gy += cs * (L[kb + oy[3]] - L[own]) * rdy * fy;
                 if (k <= nz - 2) {
                     const T mz = mzf[2];
                     const long long km1 = (long long)(k > 0 ? k - 1 : 0) * p.ys_plane + sx[2];
                     const long long kp1 = (long long)(k + 1) * p.ys_plane + sx[2];
                     const long long kp2 = (long long)(k + 2 < nz ? k + 2 : nz - 1) * p.ys_plane + sx[2];
-                    const T fz = face_fast<LIM>(phi(km1), ph, phi(kp1), phi(kp2), mz >= T(0),
-                                                mz >= T(0) ? T(0.5) : T(-0.5));
+                    const T fz = face_val4<LIM>(phi(km1), ph, phi(kp1), phi(kp2), mz >= T(0));
                     gz += cs * (L[own + plane] * p.rdz[k + 1] - L[own] * p.rdz[k]) * fz;
                 }
             }

@@ -37,6 +37,9 @@ struct asuca_grid {
     void *map_ws;
     int map_ty;
     CUtensorMap map_ystar, map_ystar2;
+    const void *umap_key[3];      // caller fields the cached user maps describe (rho, rho theta, rho q)
+    int umap_ty, umap_ok;
+    CUtensorMap umap[3];
     // opt-in per-kernel timing: events recorded around every launch
     bool prof_on;
     cudaEvent_t *prof_ev;
@@ -254,6 +257,27 @@ void df_fill_order(unsigned *out, int Q, int R) {
         }
 }
 
+// Tensor maps over the caller's fields for stage 1, cached on the grid for the
+// last fields seen.  False when the fields do not meet TMA's alignment rules
+// (16-byte bases, rows a multiple of 16 bytes) or the domain has no interior tile.
+template <typename T>
+bool user_maps(asuca_grid *g, const asuca_state *st, int ty) {
+    const int nx = g->d.nx, ny = g->d.ny, ntr = g->d.ntracers;
+    const void *key[3] = {st->rho, st->rhotheta, ntr > 0 ? st->rhoq : nullptr};
+    if (g->umap_ok && g->umap_ty == ty && key[0] == g->umap_key[0] && key[1] == g->umap_key[1] &&
+        key[2] == g->umap_key[2])
+        return true;
+    g->umap_ok = 0;
+    if (((size_t)nx * sizeof(T)) % 16 != 0 || nx < 40 || ny < ty + 4) return false;
+    for (int q = 0; q < 3; q++)
+        if (key[q] && ((uintptr_t)key[q] % 16) != 0) return false;
+    if (encode_user_maps<T>(g->umap, key[0], key[1], key[2], ntr, nx, ny, g->d.nz, ty) != cudaSuccess) return false;
+    for (int q = 0; q < 3; q++) g->umap_key[q] = key[q];
+    g->umap_ty = ty;
+    g->umap_ok = 1;
+    return true;
+}
+
 template <typename T>
 asuca_status run_step_dataflow(asuca_grid *g, asuca_state *st, const void *tend, double dt, int nsteps,
                                char *ws, double *budgets, cudaStream_t s);
@@ -286,13 +310,17 @@ asuca_status run_step(asuca_grid *g, asuca_state *st, const void *tend, double d
         g->map_ws = (void *)ws;
         g->map_ty = g->stage_ty;
     }
+    const bool umaps = user_maps<T>(g, st, g->stage_ty);
     const T cdt[3] = {(T)(dt / 3.0), (T)(dt / 2.0), (T)dt};
     for (int f = 0; f < MAXF; f++) sp.ybase[f] = yn[f];
+    for (int q = 0; q < 3 && umaps; q++) sp.umap[q] = g->umap[q];
     for (int n = 0; n < nsteps; n++) {
         for (int stg = 0; stg < 3; stg++) {
-            // stage 1 reads the caller's fields (cp.async), stages 2 and 3 the padded
-            // buffers the previous stage wrote (TMA); stage 3 writes the caller's fields
+            // stage 1 reads the caller's fields (TMA for interior tiles, cp.async at the
+            // periodic edges), stages 2 and 3 the padded buffers of phi the previous
+            // stage wrote (TMA); stage 3 writes the caller's fields
             sp.tma_in = stg > 0;
+            sp.user_tma = (stg == 0) && umaps;
             if (stg == 1) sp.tmap = g->map_ystar;
             if (stg == 2) sp.tmap = g->map_ystar2;
             sp.out_padded = stg < 2;
@@ -636,6 +664,7 @@ asuca_status run_adjoint(asuca_grid *g, const asuca_state *init, const void *ten
                     ap.ys_plane = (long long)(g->d.ny + 4) * ap.ys_pitch;
                     ap.ys_ox = 4;
                     ap.ys_oy = 2;
+                    ap.ys_phi = 1;
                 }
                 T **lin = stg == 2 ? lam : (stg == 1 ? l2 : l1);
                 for (int f = 0; f < MAXF; f++) ap.lam[f] = lin[f];

@@ -49,15 +49,18 @@ __host__ __device__ __forceinline__ long long padded_pitch(int nx) { return ((lo
 
 template <typename T>
 struct StageParams {
-    CUtensorMap tmap;       // padded stage input, when tma_in
-    const T *yin[MAXF];     // unpadded stage input, when !tma_in
+    CUtensorMap tmap;       // padded stage input (phi; rho in field 0), when tma_in
+    CUtensorMap umap[3];    // caller's unpadded rho, rho*theta, rho*q (3D, 3D, 4D), when user_tma
+    const T *yin[MAXF];     // unpadded stage input (rho, rho*phi), when !tma_in
     const T *ybase[MAXF];   // Y^n (unpadded)
     T *yout[MAXF];          // Y^(s) = Y^n + cdt * R(Y^(s-1)); padded origin when out_padded
     const T *mu, *mv, *mw;
     const T *tend;          // [F-1][nz][ny][nx] or nullptr
     int *status;            // device status word (mapped host memory)
     int nx, ny, nz, lim;
-    int tma_in, out_padded;
+    int tma_in;             // input is a padded stage buffer holding phi (TMA)
+    int out_padded;         // output to a padded stage buffer: phi for f >= 1, with periodic ghosts
+    int user_tma;           // unpadded input through umap for tiles whose halo lies inside the domain
     int ty;                 // tile rows of the instantiation to launch (the TMA box height follows it)
     uint8_t *branch;        // when recording: [F-1][nz][ny][nx] branch bytes (2 bits per direction)
     long long plane;        // nx * ny
@@ -151,29 +154,6 @@ template <typename T> __device__ __forceinline__ T recip(T x);
 template <> __device__ __forceinline__ double recip<double>(double x) { return rcp_newton(x); }
 template <> __device__ __forceinline__ float recip<float>(float x) { return __frcp_rn(x); }
 
-// Koren limiter increment L(d0, d1) = psi(d1/d0) d0 in division-free form:
-// sgn(d0) min(2|d1|, (|d0| + 2|d1|)/3, 2|d0|) when d0 and d1 share a sign,
-// else 0.  If either is zero the min is zero, so only the sign test is needed.
-template <typename T>
-__device__ __forceinline__ T limiter(T d0, T d1, int lim) {
-    if (lim == ASUCA_LIM_LINEAR) return (d0 + T(2) * d1) * T(1.0 / 3.0);
-    if (lim == ASUCA_LIM_UPWIND1) return T(0);
-    const T a0 = fabs(d0), a1 = fabs(d1);
-    const T m = fmin(T(2) * a1, fmin((a0 + T(2) * a1) * T(1.0 / 3.0), T(2) * a0));
-    return (signbit(d0) == signbit(d1)) ? copysign(m, d0) : T(0);
-}
-
-// Face value at i+1/2 from phi at i-1, i, i+1, i+2, upwind by the sign of the
-// face mass flux m (m = 0 counts as m >= 0): the mirrored stencil for m < 0.
-template <typename T>
-__device__ __forceinline__ T face_value(T pm1, T p0, T p1, T p2, T m, int lim) {
-    const bool up = m >= T(0);
-    const T c = up ? p0 : p1;
-    const T d0 = up ? (p0 - pm1) : (p1 - p2);
-    const T d1 = up ? (p1 - p0) : (p0 - p1);
-    return c + T(0.5) * limiter(d0, d1, lim);
-}
-
 // v with its sign flipped when s has its sign bit set (v * sgn(s) as a bit operation)
 __device__ __forceinline__ float sign_transfer(float v, float s) {
     return __uint_as_float(__float_as_uint(v) ^ (__float_as_uint(s) & 0x80000000u));
@@ -183,57 +163,67 @@ __device__ __forceinline__ double sign_transfer(double v, double s) {
                                 (__double_as_longlong(s) & (long long)0x8000000000000000ull));
 }
 
-// Face value with the limiter fixed at compile time, from the four cells
-// around face i+1/2 (values at i-1, i, i+1, i+2), for the upwind predicate
-// u = (m >= 0) and h = u ? 1/2 : -1/2.  The limiter increment is odd,
-// L(-a, -b) = -L(a, b), so the m < 0 mirror of the stencil is the same
-// formula on the differences oriented with the flow:
-//   face = c + h L(dfar, dmid),  c the upwind cell,  dmid = p1 - p0,
-//   dfar = p0 - pm1 (u) or p2 - p1 (!u).
-// Koren: with x = dmid carrying the sign it has relative to dfar (x >= 0 iff
-// they share a sign) and a = |dfar|,
-//   L = sgn(dfar) max(0, min(2x, (a + 2x)/3, 2a)),
-// which is zero unless dfar and dmid share a sign, and equals
-// sgn(d0) min(2|d1|, (|d0| + 2|d1|)/3, 2|d0|) when they do.
+// Face value from the upwind cell c, the downwind cell o and the far upwind
+// cell far, with the limiter fixed at compile time (for M >= 0 at face
+// i+1/2: c = phi_i, o = phi_{i+1}, far = phi_{i-1}; for M < 0 the mirror:
+// phi_{i+1}, phi_i, phi_{i+2}; M = 0 counts as M >= 0).  With d0 = c - far
+// and d1 = o - c the face value is c + L(d0, d1) / 2 in either direction.
+// Koren's increment L = sgn(d0) min(2|d1|, (|d0| + 2|d1|)/3, 2|d0|) when d0
+// and d1 share a sign, else 0, is evaluated halved and division-free: with
+// x = d1 carrying the sign it has relative to d0 (x >= 0 iff they share a
+// sign) and a = |d0|,
+//   L / 2 = sgn(d0) max(0, min(x, a, x/3 + a/6)).
+// The caller picks the three cells by address, so nothing here depends on
+// the flow direction.
 template <int LIM, typename T>
-__device__ __forceinline__ T face_fast(T pm1, T p0, T p1, T p2, bool u, T h) {
-    const T c = u ? p0 : p1;
+__device__ __forceinline__ T face_val(T c, T o, T far) {
     if (LIM == ASUCA_LIM_UPWIND1) return c;
-    const T dmid = p1 - p0;
-    const T dfar = (u ? p0 : p2) - (u ? pm1 : p1);
-    if (LIM == ASUCA_LIM_LINEAR) return c + h * ((dfar + T(2) * dmid) * T(1.0 / 3.0));
-    const T x = sign_transfer(dmid, dfar);
-    const T a = fabs(dfar);
-    T m = fmin(x + x, fmin((a + T(2) * x) * T(1.0 / 3.0), a + a));
-    m = fmax(m, T(0));
-    return c + h * copysign(m, dfar);
+    const T d1 = o - c;
+    const T d0 = c - far;
+    if (LIM == ASUCA_LIM_LINEAR) return c + (d0 * T(1.0 / 6.0) + d1 * T(1.0 / 3.0));
+    const T x = sign_transfer(d1, d0);
+    const T a = fabs(d0);
+    T h = fmin(fmin(x, a), fma(x, T(1.0 / 3.0), a * T(1.0 / 6.0)));
+    h = fmax(h, T(0));
+    return c + copysign(h, d0);
 }
 
 // The same face value, also returning the limiter branch taken: 0 zero,
 // 1 "2r", 2 "kappa=1/3", 3 "cap 2" (a tie keeps the earlier branch).  The
 // adjoint differentiates each face along the branch its forward pass took.
 template <int LIM, typename T>
-__device__ __forceinline__ T face_fast_br(T pm1, T p0, T p1, T p2, bool u, T h, int &br) {
-    const T c = u ? p0 : p1;
+__device__ __forceinline__ T face_val_br(T c, T o, T far, int &br) {
     if (LIM == ASUCA_LIM_UPWIND1) {
         br = 0;
         return c;
     }
-    const T dmid = p1 - p0;
-    const T dfar = (u ? p0 : p2) - (u ? pm1 : p1);
+    const T d1 = o - c;
+    const T d0 = c - far;
     if (LIM == ASUCA_LIM_LINEAR) {
         br = 2;
-        return c + h * ((dfar + T(2) * dmid) * T(1.0 / 3.0));
+        return c + (d0 * T(1.0 / 6.0) + d1 * T(1.0 / 3.0));
     }
-    const T x = sign_transfer(dmid, dfar);
-    const T a = fabs(dfar);
-    const T t1 = x + x, t2 = (a + T(2) * x) * T(1.0 / 3.0), t3 = a + a;
-    T m = t1;
+    const T x = sign_transfer(d1, d0);
+    const T a = fabs(d0);
+    const T t2 = fma(x, T(1.0 / 3.0), a * T(1.0 / 6.0));
+    T h = x;
     br = 1;
-    if (t2 < m) { m = t2; br = 2; }
-    if (t3 < m) { m = t3; br = 3; }
-    if (!(x > T(0) && a > T(0))) { m = T(0); br = 0; }
-    return c + h * copysign(m, dfar);
+    if (t2 < h) { h = t2; br = 2; }
+    if (a < h) { h = a; br = 3; }
+    if (!(x > T(0) && a > T(0))) { h = T(0); br = 0; }
+    return c + copysign(h, d0);
+}
+
+// Flux M * face through a face (cells as for face_val).
+template <int LIM, typename T>
+__device__ __forceinline__ T face_flux(T c, T o, T far, T m) { return m * face_val<LIM>(c, o, far); }
+template <int LIM, typename T>
+__device__ __forceinline__ T face_flux_br(T c, T o, T far, T m, int &br) { return m * face_val_br<LIM>(c, o, far, br); }
+
+// Face value at i+1/2 from the four cells i-1 .. i+2 and the upwind predicate u = (M >= 0).
+template <int LIM, typename T>
+__device__ __forceinline__ T face_val4(T pm1, T p0, T p1, T p2, bool u) {
+    return u ? face_val<LIM>(p0, p1, pm1) : face_val<LIM>(p1, p0, p2);
 }
 
 // d face / d phi at the stencil cells (pm1, p0, p1, p2) for upwind predicate u
@@ -258,6 +248,12 @@ cudaError_t launch_stage(const StageParams<T> &p, int nf, cudaStream_t s);
 // tiles of ty rows.
 template <typename T>
 cudaError_t encode_stage_map(CUtensorMap *map, void *base, int nf, int nx, int ny, int nz, int ty);
+// Tensor maps over the caller's unpadded rho, rho*theta and rho*q (N fields)
+// with the stage box (40 x (ty + 4) x 1 [x N]); the caller checks that every
+// base is 16-byte aligned and that a row (nx elements) is a multiple of 16 bytes.
+template <typename T>
+cudaError_t encode_user_maps(CUtensorMap *maps, const void *rho, const void *rhotheta, const void *rhoq, int ntr,
+                             int nx, int ny, int nz, int ty);
 
 // the stage kernels of one tile height (one translation unit each)
 template <typename T, int TY>

@@ -4,8 +4,10 @@
 // a fixed order in which every task comes after the tasks it reads:
 //   a stage task of phase q on tile T reads phase q-1 on T's 3 x 3 tile
 //   neighbourhood (the 2-wide halo), a column task reads phase q-1 on T only;
-// the order runs along diagonals 2 q + (tile row), so tasks of different
-// steps and phases interleave across tile rows.  A CTA that takes a task
+// the order sorts tasks by 2 q + min(r, R - r) for tile row r of R, a
+// distance on the periodic ring of rows in which neighbouring rows differ by
+// at most one, so tasks of different steps and phases interleave across
+// tile rows.  A CTA that takes a task
 // waits (bounded, about one second) until its inputs are complete, runs it,
 // and publishes the tile's completed-phase count with release semantics.
 // The column pass (FP64 elimination, bound by the FP64 pipe) and the stencil

@@ -4,25 +4,32 @@
 //   R = -[dX/dx + dY/dy + dZ/dz] + tendency,  Y_out = Y_base + cdt R
 //
 // Mapping: a CTA owns a 32 x TY tile of (i, j) columns, one warp per row, and
-// marches k upward (parallel in I/J, sequential in K; Sec. 1.1, Sec. 1.3).
+// marches k upward (parallel in I/J, sequential in K; Sec. 1.1, Sec. 1.2).
 // Level planes of the stage input stream through a ring of D shared-memory
 // slots, each holding every field of the tile plus a halo of 4 columns in i
 // (the TMA box must start on a 16-byte boundary; 2 are used) and 2 rows in j:
 //   * from the library's padded stage buffers, one 4D TMA box per level
-//     (cp.async.bulk.tensor, completion on an mbarrier); periodic halos are
-//     ghost copies written by the stage that produced the buffer;
-//   * from the caller's unpadded fields, per-thread cp.async copies with the
-//     periodic wrap done in the index arithmetic.
-// Levels are requested D-2 levels ahead.  Each arriving level is converted in
-// place from rho*phi to phi, once per cell.  Every face is reconstructed
-// once: i+1/2 by each thread (the i-1/2 flux comes from the neighbouring lane
-// by shuffle), j+1/2 by each thread into shared memory, k+1/2 by each thread
-// with the k-1/2 flux carried in registers; the faces on the tile's left and
-// bottom edges are computed by warps 1 and 0.
+//     (cp.async.bulk.tensor, completion on an mbarrier).  The stage that
+//     produced the buffer wrote phi (not rho*phi) and the periodic halo
+//     ghosts, so the level is used as it lands;
+//   * from the caller's unpadded fields (rho*phi): for tiles whose halo lies
+//     inside the domain, three TMA boxes per level (rho, rho*theta, the N
+//     tracers); at the periodic edges, per-thread cp.async copies with the
+//     wrap done in the index arithmetic.  These levels are converted in place
+//     to phi, once per cell.
+// Levels are requested D-2 levels ahead.  Every face is reconstructed once:
+// i+1/2 by each thread (the i-1/2 flux comes from the neighbouring lane by
+// shuffle), j+1/2 by each thread into shared memory, k+1/2 by each thread with
+// the k-1/2 flux carried in registers; the faces on the tile's left and
+// bottom edges are computed by warps dealt round-robin.  A face's upwind,
+// downwind and far cells are picked by address from the sign of M, so the
+// limiter arithmetic has no per-field selects.
 #pragma once
 
 #include <cuda.h>
 #include <cudaTypedefs.h>
+
+#include <cstring>
 
 #include "common.cuh"
 
@@ -81,6 +88,14 @@ __device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, i
         : "memory");
 }
 
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
 template <int BYTES>
 __device__ __forceinline__ void cp_async(void *dst, const void *src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_u32(dst)), "l"(src), "n"(BYTES)
@@ -108,6 +123,7 @@ __device__ __forceinline__ bool stage_tile(const StageParams<T> &p, const CUtens
     constexpr int FE = SY * SX;                   // elements of one field in a slot
     constexpr int NCELL = TY * (TX + 4) + 4 * TX; // the slot cells the stencil reads (no corners)
     constexpr int MAXC = (NCELL + NTHR - 1) / NTHR;
+    static_assert((FE * sizeof(T)) % 128 == 0, "each field of a slot must start on a 128-byte boundary");
 
     T *ring = reinterpret_cast<T *>(smem_raw);
     T *ysm = reinterpret_cast<T *>(smem_raw + S::RING_BYTES);            // [NT][TY+1][TX]
@@ -123,7 +139,13 @@ __device__ __forceinline__ bool stage_tile(const StageParams<T> &p, const CUtens
     const long long own = (long long)jc * nx + ic;
     const long long left = (long long)jc * nx + wrap_index(ic - 1, nx);
     const long long down = (long long)wrap_index(jc - 1, ny) * nx + ic;
-    const bool tma = p.tma_in != 0;
+    // Input paths: a padded stage buffer (phi, one 4D TMA box per level); the
+    // caller's fields (rho*phi) by TMA when the tile's halo lies inside the
+    // domain, else by per-thread cp.async with the periodic wrap.
+    const bool pad_in = p.tma_in != 0;
+    const bool user_tma = !pad_in && p.user_tma && i0 >= 4 && i0 + TX + 4 <= nx && j0 >= 2 && j0 + TY + 2 <= ny;
+    const bool tma = pad_in || user_tma;
+    const bool conv = !pad_in;
 
     __syncthreads();   // the previous tile (if any) is done with the shared memory
     if (tma && tid == 0) {
@@ -131,7 +153,7 @@ __device__ __forceinline__ bool stage_tile(const StageParams<T> &p, const CUtens
         fence_proxy_async();
     }
 
-    // slot cells this thread copies (cp.async path) and converts (both paths)
+    // slot cells this thread copies (cp.async path) and converts
     int soff[MAXC];
     long long goff[MAXC];
     int nc = 0;
@@ -160,12 +182,23 @@ __device__ __forceinline__ bool stage_tile(const StageParams<T> &p, const CUtens
 
     auto slot = [&](int lev) -> T * { return ring + (size_t)(lev % D) * S::SLOT_ELEMS; };
 
+    int issued = 0, seen = 0;   // TMA levels [0, issued) requested, [0, seen) seen complete
     auto issue = [&](int lev) {
         if (tma) {
-            if (tid == 0 && lev < nz) {
-                uint64_t *bar = &bars[lev % D];
-                mbar_expect_tx(bar, S::TX_BYTES);
-                tma_load_4d(slot(lev), tmap, i0, j0, lev, 0, bar);
+            if (lev < nz) {
+                issued = lev + 1;
+                if (tid == 0) {
+                    uint64_t *bar = &bars[lev % D];
+                    T *dst = slot(lev);
+                    mbar_expect_tx(bar, S::TX_BYTES);
+                    if (pad_in) {
+                        tma_load_4d(dst, tmap, i0, j0, lev, 0, bar);
+                    } else {
+                        tma_load_3d(dst, &p.umap[0], i0 - 4, j0 - 2, lev, bar);
+                        tma_load_3d(dst + FE, &p.umap[1], i0 - 4, j0 - 2, lev, bar);
+                        if (NF > 2) tma_load_4d(dst + 2 * FE, &p.umap[2], i0 - 4, j0 - 2, lev, 0, bar);
+                    }
+                }
             }
         } else {
             if (lev < nz) {
@@ -195,18 +228,21 @@ __device__ __forceinline__ bool stage_tile(const StageParams<T> &p, const CUtens
             }
         }
     };
+    // wait for level lev to land (TMA) and convert it if it holds rho*phi
+    auto arrive = [&](int lev) -> bool {
+        if (!mbar_wait(&bars[lev % D], (lev / D) & 1)) return false;
+        seen = lev + 1;
+        if (conv) convert(lev);
+        return true;
+    };
 
     bool timed_out = false;
-    // ---- prologue: request levels 0 .. D-3, convert levels 0 and 1
+    // ---- prologue: request levels 0 .. D-3, make levels 0 and 1 ready
 #pragma unroll 1
     for (int lev = 0; lev <= D - 3; lev++) issue(lev);
     if (tma) {
-        if (!mbar_wait(&bars[0], 0)) timed_out = true;
-        else convert(0);
-        if (nz > 1) {
-            if (!mbar_wait(&bars[1], 0)) timed_out = true;
-            else convert(1);
-        }
+        if (!arrive(0)) timed_out = true;
+        else if (nz > 1 && !arrive(1)) timed_out = true;
     } else {
         cp_async_wait<D - 3>();
         convert(0);
@@ -222,6 +258,9 @@ __device__ __forceinline__ bool stage_tile(const StageParams<T> &p, const CUtens
     const long long edge_b = (long long)wrap_index(j0 - 1, ny) * nx + ic;                 // MV below the tile
     const int er = lane < TY ? lane : 0;
     const long long edge_l = (long long)wrap_index(j0 + er, ny) * nx + wrap_index(i0 - 1, nx);  // MU left of row er
+    // tiles that hold cells whose values are also periodic ghosts of the padded output
+    const bool ghost_x = (i0 < 2) || (i0 + TX > nx - 2);
+    const bool ghost_y = (j0 < 2) || (j0 + TY > ny - 2);
 
     T zlo[NF];
 #pragma unroll
@@ -254,11 +293,10 @@ __device__ __forceinline__ bool stage_tile(const StageParams<T> &p, const CUtens
 
 #pragma unroll 1
     for (int k = 0; k < nz; k++) {
-        // ---- level k+2 must be resident and converted before anyone computes level k
+        // ---- level k+2 must be resident (and hold phi) before anyone computes level k
         if (k + 2 < nz) {
             if (tma) {
-                if (!mbar_wait(&bars[(k + 2) % D], ((k + 2) / D) & 1)) timed_out = true;
-                else convert(k + 2);
+                if (!arrive(k + 2)) timed_out = true;
             } else {
                 cp_async_wait<(D >= 5 ? D - 5 : 0)>();
                 convert(k + 2);
@@ -269,47 +307,48 @@ __device__ __forceinline__ bool stage_tile(const StageParams<T> &p, const CUtens
         issue(k + D - 2);   // into the slot of level k-2, which nobody reads any more
         if (k + 1 < nz) prefetch(k + 1);
 
-        // ---- faces
+        // ---- faces: upwind cell c, downwind cell o and far upwind cell by address
         const T *Sk = slot(k);
         const T *Skm = slot(k > 0 ? k - 1 : 0);
         const T *Skp = slot(k + 1 < nz ? k + 1 : nz - 1);
         const T *Skp2 = slot(k + 2 < nz ? k + 2 : nz - 1);
         const bool top = (k == nz - 1);
         const bool ux = mup >= T(0), uy = mvp >= T(0), uz = mwp >= T(0);
-        const T hx = ux ? T(0.5) : T(-0.5), hy = uy ? T(0.5) : T(-0.5), hz = uz ? T(0.5) : T(-0.5);
+        const int xc = cc + (ux ? 0 : 1), xo = cc + (ux ? 1 : 0), xf = cc + (ux ? -1 : 2);
+        const int yc = cc + (uy ? 0 : SX), yo = cc + (uy ? SX : 0), yf = cc + (uy ? -SX : 2 * SX);
+        const T *zc = (uz ? Sk : Skp) + cc, *zo = (uz ? Skp : Sk) + cc, *zf = (uz ? Skm : Skp2) + cc;
         T xp[NT], yp[NT], zp[NT];
 #pragma unroll
         for (int f = 0; f < NT; f++) {
             const int fo = (f + 1) * FE;
-            const T c = Sk[fo + cc];
             if (REC) {
                 int bx, by, bz = 0;
-                xp[f] = mup * face_fast_br<LIM>(Sk[fo + cc - 1], c, Sk[fo + cc + 1], Sk[fo + cc + 2], ux, hx, bx);
-                yp[f] = mvp * face_fast_br<LIM>(Sk[fo + cc - SX], c, Sk[fo + cc + SX], Sk[fo + cc + 2 * SX], uy, hy, by);
-                zp[f] = top ? T(0) : mwp * face_fast_br<LIM>(Skm[fo + cc], c, Skp[fo + cc], Skp2[fo + cc], uz, hz, bz);
+                xp[f] = face_flux_br<LIM>(Sk[fo + xc], Sk[fo + xo], Sk[fo + xf], mup, bx);
+                yp[f] = face_flux_br<LIM>(Sk[fo + yc], Sk[fo + yo], Sk[fo + yf], mvp, by);
+                zp[f] = top ? T(0) : face_flux_br<LIM>(zc[fo], zo[fo], zf[fo], mwp, bz);
                 if (valid) p.branch[(long long)f * nz * plane + (long long)k * plane + own] = (uint8_t)(bx | (by << 2) | (bz << 4));
             } else {
-                xp[f] = mup * face_fast<LIM>(Sk[fo + cc - 1], c, Sk[fo + cc + 1], Sk[fo + cc + 2], ux, hx);
-                yp[f] = mvp * face_fast<LIM>(Sk[fo + cc - SX], c, Sk[fo + cc + SX], Sk[fo + cc + 2 * SX], uy, hy);
-                zp[f] = top ? T(0) : mwp * face_fast<LIM>(Skm[fo + cc], c, Skp[fo + cc], Skp2[fo + cc], uz, hz);
+                xp[f] = face_flux<LIM>(Sk[fo + xc], Sk[fo + xo], Sk[fo + xf], mup);
+                yp[f] = face_flux<LIM>(Sk[fo + yc], Sk[fo + yo], Sk[fo + yf], mvp);
+                zp[f] = top ? T(0) : face_flux<LIM>(zc[fo], zo[fo], zf[fo], mwp);
             }
             ysm[(f * (TY + 1) + ty + 1) * TX + tx] = yp[f];
         }
         {
             const bool ub = meb >= T(0), ul = mel >= T(0);
-            const T hb = ub ? T(0.5) : T(-0.5), hl = ul ? T(0.5) : T(-0.5);
+            const int bc = (ub ? 1 : 2) * SX, bo = (ub ? 2 : 1) * SX, bf = (ub ? 0 : 3) * SX;
+            const int lc = ul ? 3 : 4, lo = ul ? 4 : 3, lf = ul ? 2 : 5;
 #pragma unroll 1
             for (int t = warp; t < 2 * NT; t += TY) {
                 const int f = t >> 1;
                 if ((t & 1) == 0) {
-                    // Y at j0-1/2 for column lane: phi rows 0..3 of the slot
+                    // flux at j0-1/2 for column lane: slot rows 0..3 (j0-2 .. j0+1)
                     const int fo = (f + 1) * FE + cx;
-                    ysm[(f * (TY + 1)) * TX + tx] =
-                        meb * face_fast<LIM>(Sk[fo], Sk[fo + SX], Sk[fo + 2 * SX], Sk[fo + 3 * SX], ub, hb);
+                    ysm[(f * (TY + 1)) * TX + tx] = face_flux<LIM>(Sk[fo + bc], Sk[fo + bo], Sk[fo + bf], meb);
                 } else if (lane < TY) {
-                    // X at i0-1/2 for row lane: phi columns 2..5 of the slot
+                    // flux at i0-1/2 for row lane: slot columns 2..5 (i0-2 .. i0+1)
                     const int fo = (f + 1) * FE + (lane + 2) * SX;
-                    xbs[f * TY + lane] = mel * face_fast<LIM>(Sk[fo + 2], Sk[fo + 3], Sk[fo + 4], Sk[fo + 5], ul, hl);
+                    xbs[f * TY + lane] = face_flux<LIM>(Sk[fo + lc], Sk[fo + lo], Sk[fo + lf], mel);
                 }
             }
         }
@@ -334,15 +373,22 @@ __device__ __forceinline__ bool stage_tile(const StageParams<T> &p, const CUtens
         }
         if (valid) {
             if (p.out_padded) {
-                const long long ob = (long long)k * p.oplane + (long long)(j + 2) * p.opitch + (i + 4);
-                const long long gx = (i < 2) ? nx : ((i >= nx - 2) ? -nx : 0);
-                const long long gy = (j < 2) ? (long long)ny * p.opitch : ((j >= ny - 2) ? -(long long)ny * p.opitch : 0);
+                // the next stage reads phi = (rho phi) / rho
+                const T r = recip(out[0]);
 #pragma unroll
-                for (int f = 0; f < NF; f++) {
-                    T *o = p.yout[f] + ob;
-                    o[0] = out[f];
-                    if (gx) o[gx] = out[f];
-                    if (gy) o[gy] = out[f];
+                for (int f = 1; f < NF; f++) out[f] *= r;
+                const long long ob = (long long)k * p.oplane + (long long)(j + 2) * p.opitch + (i + 4);
+#pragma unroll
+                for (int f = 0; f < NF; f++) p.yout[f][ob] = out[f];
+                if (ghost_x || ghost_y) {
+                    const long long gx = (i < 2) ? nx : ((i >= nx - 2) ? -nx : 0);
+                    const long long gy = (j < 2) ? (long long)ny * p.opitch : ((j >= ny - 2) ? -(long long)ny * p.opitch : 0);
+#pragma unroll
+                    for (int f = 0; f < NF; f++) {
+                        T *o = p.yout[f] + ob;
+                        if (gx) o[gx] = out[f];
+                        if (gy) o[gy] = out[f];
+                    }
                 }
             } else {
                 const long long o = (long long)k * plane + own;
@@ -355,6 +401,11 @@ __device__ __forceinline__ bool stage_tile(const StageParams<T> &p, const CUtens
 
     if (timed_out) {
         if (tid == 0 && p.status) atomicCAS(p.status, 0, (int)ASUCA_ERR_TIMEOUT);
+        // let the copies still in flight land (each wait bounded) before the
+        // shared memory is released
+        if (tma)
+            for (int lev = seen; lev < issued; lev++)
+                if (!mbar_wait(&bars[lev % D], (lev / D) & 1)) break;
     }
     if (!tma) cp_async_wait<0>();
     __syncthreads();
@@ -449,6 +500,33 @@ cudaError_t encode_stage_map(CUtensorMap *map, void *base, int nf, int nx, int n
                      base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+template <typename T>
+cudaError_t encode_user_maps(CUtensorMap *maps, const void *rho, const void *rhotheta, const void *rhoq, int ntr,
+                             int nx, int ny, int nz, int ty) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return cudaErrorNotSupported;
+    using S = StageShape<T, 2>;
+    const CUtensorMapDataType dt = sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+    const cuuint64_t dims[4] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz, (cuuint64_t)(ntr > 0 ? ntr : 1)};
+    const cuuint64_t strides[3] = {(cuuint64_t)nx * sizeof(T), (cuuint64_t)nx * ny * sizeof(T),
+                                   (cuuint64_t)nx * ny * (cuuint64_t)nz * sizeof(T)};
+    const cuuint32_t box[4] = {(cuuint32_t)S::SX, (cuuint32_t)(ty + 4), 1u, (cuuint32_t)(ntr > 0 ? ntr : 1)};
+    const cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
+    const void *base[3] = {rho, rhotheta, rhoq};
+    for (int q = 0; q < 3; q++) {
+        if (q == 2 && ntr == 0) {
+            std::memset(&maps[q], 0, sizeof(CUtensorMap));
+            continue;
+        }
+        const cuuint32_t rank = q == 2 ? 4u : 3u;
+        CUresult r = enc(&maps[q], dt, rank, const_cast<void *>(base[q]), dims, strides, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    }
+    return cudaSuccess;
 }
 
 
