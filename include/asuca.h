@@ -99,7 +99,13 @@ typedef struct {
 } asuca_state;
 
 /* Create a grid: validates the description, copies dz, precomputes level
- * tables.  *out receives the grid; free it with asuca_free_grid. */
+ * tables.  *out receives the grid; free it with asuca_free_grid.
+ * ASUCA_ERR_ARG for nx, ny < 4, nz < 3, non-positive or non-finite spacings
+ * or constants, an out-of-range tracer, limiter or precision;
+ * ASUCA_ERR_UNSUPPORTED beyond the compiled limits: N > ASUCA_MAX_TRACERS,
+ * nz > ASUCA_MAX_NZ, or a field (nx * ny * (nz + 1) elements, or its padded
+ * stage copy (nx + 8 rounded up to 8) * (ny + 4) * nz) of 2^32 elements or
+ * more, since the kernels index within a field with 32-bit offsets. */
 asuca_status asuca_init_grid(const asuca_grid_desc *desc, asuca_grid **out);
 asuca_status asuca_free_grid(asuca_grid *grid);
 

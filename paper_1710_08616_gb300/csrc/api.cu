@@ -974,6 +974,11 @@ asuca_status asuca_init_grid(const asuca_grid_desc *desc, asuca_grid **out) {
     for (int k = 0; k < d.nz; k++)
         if (!(d.dz[k] > 0.0) || !std::isfinite(d.dz[k])) return ASUCA_ERR_ARG;
     if ((long long)d.nx * d.ny > (1LL << 31)) return ASUCA_ERR_UNSUPPORTED;
+    // element offsets within one field (caller layout with nz + 1 levels of MW,
+    // and the padded stage buffers) are 32-bit in the kernels
+    if ((long long)d.nx * d.ny * (d.nz + 1) >= (1LL << 32) ||
+        padded_pitch(d.nx) * (d.ny + 4) * (long long)d.nz >= (1LL << 32))
+        return ASUCA_ERR_UNSUPPORTED;
 
     asuca_grid *g = new (std::nothrow) asuca_grid;
     if (!g) return ASUCA_ERR_ARG;

@@ -108,11 +108,17 @@ __host__ __device__ __forceinline__ int wrap_index(int i, int n) {
 // 1+11+52 bits, bias 1023).  Zero, subnormal, infinite and NaN inputs take
 // the hardware path, so every result equals the hardware conversion.
 
+// The rare inputs go to the hardware conversions in functions of their own,
+// so that they are reached by a branch: a conversion the compiler predicated
+// off would still take an issue slot of the FP64 pipe for every call.
+static __device__ __noinline__ double f2d_hw(float x) { return (double)x; }
+static __device__ __noinline__ float d2f_hw(double x) { return __double2float_rn(x); }
+
 // Exact widening: exponent rebiased by 1023 - 127 = 896, mantissa shifted by 29.
 __device__ __forceinline__ double f2d_bits(float x) {
     const uint32_t u = __float_as_uint(x);
     const uint32_t e = u & 0x7f800000u;
-    if (e == 0u || e == 0x7f800000u) return (double)x;
+    if (e == 0u || e == 0x7f800000u) return f2d_hw(x);
     const uint32_t hi = (u & 0x80000000u) | (((u & 0x7fffffffu) >> 3) + (896u << 20));
     return __hiloint2double((int)hi, (int)(u << 29));
 }
@@ -124,7 +130,7 @@ __device__ __forceinline__ double f2d_bits(float x) {
 __device__ __forceinline__ float d2f_bits(double x) {
     const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
     const uint32_t ea = (hi >> 20) & 0x7ffu;
-    if (ea < 897u || ea > 1150u) return __double2float_rn(x);
+    if (ea < 897u || ea > 1150u) return d2f_hw(x);
     uint32_t mag = (((hi & 0x7fffffffu) - (896u << 20)) << 3) | (lo >> 29);
     const uint32_t rem = lo & 0x1fffffffu;
     mag += (rem > 0x10000000u || (rem == 0x10000000u && (mag & 1u))) ? 1u : 0u;
@@ -180,7 +186,7 @@ __device__ __forceinline__ T face_val(T c, T o, T far) {
     if (LIM == ASUCA_LIM_UPWIND1) return c;
     const T d1 = o - c;
     const T d0 = c - far;
-    if (LIM == ASUCA_LIM_LINEAR) return c + (d0 * T(1.0 / 6.0) + d1 * T(1.0 / 3.0));
+    if (LIM == ASUCA_LIM_LINEAR) return c + fma(d1, T(1.0 / 3.0), d0 * T(1.0 / 6.0));
     const T x = sign_transfer(d1, d0);
     const T a = fabs(d0);
     T h = fmin(fmin(x, a), fma(x, T(1.0 / 3.0), a * T(1.0 / 6.0)));
@@ -201,7 +207,7 @@ __device__ __forceinline__ T face_val_br(T c, T o, T far, int &br) {
     const T d0 = c - far;
     if (LIM == ASUCA_LIM_LINEAR) {
         br = 2;
-        return c + (d0 * T(1.0 / 6.0) + d1 * T(1.0 / 3.0));
+        return c + fma(d1, T(1.0 / 3.0), d0 * T(1.0 / 6.0));
     }
     const T x = sign_transfer(d1, d0);
     const T a = fabs(d0);
@@ -219,6 +225,30 @@ template <int LIM, typename T>
 __device__ __forceinline__ T face_flux(T c, T o, T far, T m) { return m * face_val<LIM>(c, o, far); }
 template <int LIM, typename T>
 __device__ __forceinline__ T face_flux_br(T c, T o, T far, T m, int &br) { return m * face_val_br<LIM>(c, o, far, br); }
+
+// Two fields' fluxes through the same face at once (fields f and f+1 in the
+// two lanes of a float2), with the packed FP32x2 FMA/ADD/MUL of this GPU;
+// every packed operation rounds as its scalar twin in face_val, so the result
+// is bit-identical to two calls of face_flux.  Differences are taken as
+// fma(b, -1, a) = a - b exactly.
+template <int LIM>
+__device__ __forceinline__ float2 face_flux2(float2 c, float2 o, float2 far, float m) {
+    const float2 m2 = make_float2(m, m);
+    if (LIM == ASUCA_LIM_UPWIND1) return __fmul2_rn(m2, c);
+    const float2 neg1 = make_float2(-1.f, -1.f);
+    const float2 d1 = __ffma2_rn(c, neg1, o);
+    const float2 d0 = __ffma2_rn(far, neg1, c);
+    if (LIM == ASUCA_LIM_LINEAR) {
+        const float2 t = __ffma2_rn(d1, make_float2(1.f / 3.f, 1.f / 3.f), __fmul2_rn(d0, make_float2(1.f / 6.f, 1.f / 6.f)));
+        return __fmul2_rn(m2, __fadd2_rn(c, t));
+    }
+    const float2 x = make_float2(sign_transfer(d1.x, d0.x), sign_transfer(d1.y, d0.y));
+    const float2 a = make_float2(fabsf(d0.x), fabsf(d0.y));
+    const float2 t = __ffma2_rn(x, make_float2(1.f / 3.f, 1.f / 3.f), __fmul2_rn(a, make_float2(1.f / 6.f, 1.f / 6.f)));
+    const float hx = fmaxf(fminf(fminf(x.x, a.x), t.x), 0.f);
+    const float hy = fmaxf(fminf(fminf(x.y, a.y), t.y), 0.f);
+    return __fmul2_rn(m2, __fadd2_rn(c, make_float2(copysignf(hx, d0.x), copysignf(hy, d0.y))));
+}
 
 // Face value at i+1/2 from the four cells i-1 .. i+2 and the upwind predicate u = (M >= 0).
 template <int LIM, typename T>

@@ -30,6 +30,7 @@
 #include <cudaTypedefs.h>
 
 #include <cstring>
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -132,13 +133,15 @@ __device__ __forceinline__ bool stage_tile(const StageParams<T> &p, const CUtens
 
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
     const int nx = p.nx, ny = p.ny, nz = p.nz;
-    const long long plane = p.plane;
+    // element offsets within a field fit in 32 bits (the host checks), which
+    // keeps the per-field address arithmetic to one 32-bit index
+    const unsigned plane = (unsigned)p.plane;
     const int i = i0 + tx, j = j0 + ty;
     const bool valid = (i < nx) && (j < ny);
     const int ic = wrap_index(i, nx), jc = wrap_index(j, ny);
-    const long long own = (long long)jc * nx + ic;
-    const long long left = (long long)jc * nx + wrap_index(ic - 1, nx);
-    const long long down = (long long)wrap_index(jc - 1, ny) * nx + ic;
+    const unsigned own = (unsigned)(jc * nx + ic);
+    const unsigned left = (unsigned)(jc * nx + wrap_index(ic - 1, nx));
+    const unsigned down = (unsigned)(wrap_index(jc - 1, ny) * nx + ic);
     // Input paths: a padded stage buffer (phi, one 4D TMA box per level); the
     // caller's fields (rho*phi) by TMA when the tile's halo lies inside the
     // domain, else by per-thread cp.async with the periodic wrap.
@@ -155,7 +158,7 @@ __device__ __forceinline__ bool stage_tile(const StageParams<T> &p, const CUtens
 
     // slot cells this thread copies (cp.async path) and converts
     int soff[MAXC];
-    long long goff[MAXC];
+    unsigned goff[MAXC];
     int nc = 0;
 #pragma unroll
     for (int q = 0; q < MAXC; q++) {
@@ -174,7 +177,7 @@ __device__ __forceinline__ bool stage_tile(const StageParams<T> &p, const CUtens
                 sy = r < 2 ? r : TY + r;
             }
             soff[q] = sy * SX + sx;
-            goff[q] = (long long)wrap_index(j0 + sy - 2, ny) * nx + wrap_index(i0 + sx - 4, nx);
+            goff[q] = (unsigned)(wrap_index(j0 + sy - 2, ny) * nx + wrap_index(i0 + sx - 4, nx));
             nc = q + 1;
         }
     }
@@ -203,7 +206,7 @@ __device__ __forceinline__ bool stage_tile(const StageParams<T> &p, const CUtens
         } else {
             if (lev < nz) {
                 T *sl = slot(lev);
-                const long long lb = (long long)lev * plane;
+                const unsigned lb = (unsigned)lev * plane;
 #pragma unroll
                 for (int q = 0; q < MAXC; q++) {
                     if (q < nc) {
@@ -255,9 +258,9 @@ __device__ __forceinline__ bool stage_tile(const StageParams<T> &p, const CUtens
     const int warp = ty, lane = tx;
     // Edge faces (j0-1/2 for the tile's 32 columns, i0-1/2 for its TY rows),
     // one task per (field, edge), dealt round-robin to the warps.
-    const long long edge_b = (long long)wrap_index(j0 - 1, ny) * nx + ic;                 // MV below the tile
-    const int er = lane < TY ? lane : 0;
-    const long long edge_l = (long long)wrap_index(j0 + er, ny) * nx + wrap_index(i0 - 1, nx);  // MU left of row er
+    const unsigned edge_b = (unsigned)(wrap_index(j0 - 1, ny) * nx + ic);                 // MV below the tile
+    const int er = lane % TY;   // the tile row whose i0-1/2 faces this lane computes
+    const unsigned edge_l = (unsigned)(wrap_index(j0 + er, ny) * nx + wrap_index(i0 - 1, nx));  // MU left of row er
     // tiles that hold cells whose values are also periodic ghosts of the padded output
     const bool ghost_x = (i0 < 2) || (i0 + TX > nx - 2);
     const bool ghost_y = (j0 < 2) || (j0 + TY > ny - 2);
@@ -266,11 +269,11 @@ __device__ __forceinline__ bool stage_tile(const StageParams<T> &p, const CUtens
 #pragma unroll
     for (int f = 0; f < NF; f++) zlo[f] = T(0);
 
-    // per-level operands, requested one level ahead at the start of the previous level
-    T mup, mum, mvp, mvm, mwp, meb, mel, yb[NF];
-    T nmup, nmum, nmvp, nmvm, nmwp, nmeb, nmel, nyb[NF];
+    // per-level mass fluxes, requested one level ahead (the faces need them first)
+    T mup, mum, mvp, mvm, mwp, meb, mel;
+    T nmup, nmum, nmvp, nmvm, nmwp, nmeb, nmel;
     auto prefetch = [&](int k) {
-        const long long kb = (long long)k * plane;
+        const unsigned kb = (unsigned)k * plane;
         nmup = p.mu[kb + own];
         nmum = p.mu[kb + left];
         nmvp = p.mv[kb + own];
@@ -278,18 +281,16 @@ __device__ __forceinline__ bool stage_tile(const StageParams<T> &p, const CUtens
         nmwp = (k < nz - 1) ? p.mw[kb + plane + own] : T(0);
         nmeb = p.mv[kb + edge_b];
         nmel = p.mu[kb + edge_l];
-#pragma unroll
-        for (int f = 0; f < NF; f++) nyb[f] = p.ybase[f][kb + own];
     };
     auto advance = [&]() {
         mup = nmup; mum = nmum; mvp = nmvp; mvm = nmvm; mwp = nmwp; meb = nmeb; mel = nmel;
-#pragma unroll
-        for (int f = 0; f < NF; f++) yb[f] = nyb[f];
     };
     prefetch(0);
     advance();
 
     const int cy = ty + 2, cx = tx + 4, cc = cy * SX + cx;
+    // float stages evaluate faces and the divergence two fields at a time (FP32x2)
+    constexpr bool PACK = std::is_same<T, float>::value && !REC;
 
 #pragma unroll 1
     for (int k = 0; k < nz; k++) {
@@ -305,6 +306,13 @@ __device__ __forceinline__ bool stage_tile(const StageParams<T> &p, const CUtens
         if (tma) fence_proxy_async();
         if (__syncthreads_or(timed_out)) break;
         issue(k + D - 2);   // into the slot of level k-2, which nobody reads any more
+        // Y^n of this level: used after the faces, which cover the load latency
+        T yb[NF];
+        {
+            const unsigned kb = (unsigned)k * plane + own;
+#pragma unroll
+            for (int f = 0; f < NF; f++) yb[f] = p.ybase[f][kb];
+        }
         if (k + 1 < nz) prefetch(k + 1);
 
         // ---- faces: upwind cell c, downwind cell o and far upwind cell by address
@@ -318,58 +326,115 @@ __device__ __forceinline__ bool stage_tile(const StageParams<T> &p, const CUtens
         const int yc = cc + (uy ? 0 : SX), yo = cc + (uy ? SX : 0), yf = cc + (uy ? -SX : 2 * SX);
         const T *zc = (uz ? Sk : Skp) + cc, *zo = (uz ? Skp : Sk) + cc, *zf = (uz ? Skm : Skp2) + cc;
         T xp[NT], yp[NT], zp[NT];
+        if constexpr (PACK) {
 #pragma unroll
-        for (int f = 0; f < NT; f++) {
-            const int fo = (f + 1) * FE;
-            if (REC) {
-                int bx, by, bz = 0;
-                xp[f] = face_flux_br<LIM>(Sk[fo + xc], Sk[fo + xo], Sk[fo + xf], mup, bx);
-                yp[f] = face_flux_br<LIM>(Sk[fo + yc], Sk[fo + yo], Sk[fo + yf], mvp, by);
-                zp[f] = top ? T(0) : face_flux_br<LIM>(zc[fo], zo[fo], zf[fo], mwp, bz);
-                if (valid) p.branch[(long long)f * nz * plane + (long long)k * plane + own] = (uint8_t)(bx | (by << 2) | (bz << 4));
-            } else {
+            for (int f = 0; f + 1 < NT; f += 2) {
+                const int f0 = (f + 1) * FE, f1 = (f + 2) * FE;
+                const float2 rx = face_flux2<LIM>(make_float2(Sk[f0 + xc], Sk[f1 + xc]),
+                                                  make_float2(Sk[f0 + xo], Sk[f1 + xo]),
+                                                  make_float2(Sk[f0 + xf], Sk[f1 + xf]), mup);
+                const float2 ry = face_flux2<LIM>(make_float2(Sk[f0 + yc], Sk[f1 + yc]),
+                                                  make_float2(Sk[f0 + yo], Sk[f1 + yo]),
+                                                  make_float2(Sk[f0 + yf], Sk[f1 + yf]), mvp);
+                const float2 rz = top ? make_float2(0.f, 0.f)
+                                      : face_flux2<LIM>(make_float2(zc[f0], zc[f1]), make_float2(zo[f0], zo[f1]),
+                                                        make_float2(zf[f0], zf[f1]), mwp);
+                xp[f] = rx.x; xp[f + 1] = rx.y;
+                yp[f] = ry.x; yp[f + 1] = ry.y;
+                zp[f] = rz.x; zp[f + 1] = rz.y;
+                ysm[(f * (TY + 1) + ty + 1) * TX + tx] = ry.x;
+                ysm[((f + 1) * (TY + 1) + ty + 1) * TX + tx] = ry.y;
+            }
+            if (NT & 1) {
+                constexpr int f = NT - 1;
+                const int fo = (f + 1) * FE;
                 xp[f] = face_flux<LIM>(Sk[fo + xc], Sk[fo + xo], Sk[fo + xf], mup);
                 yp[f] = face_flux<LIM>(Sk[fo + yc], Sk[fo + yo], Sk[fo + yf], mvp);
                 zp[f] = top ? T(0) : face_flux<LIM>(zc[fo], zo[fo], zf[fo], mwp);
+                ysm[(f * (TY + 1) + ty + 1) * TX + tx] = yp[f];
             }
-            ysm[(f * (TY + 1) + ty + 1) * TX + tx] = yp[f];
+        } else {
+#pragma unroll
+            for (int f = 0; f < NT; f++) {
+                const int fo = (f + 1) * FE;
+                if (REC) {
+                    int bx, by, bz = 0;
+                    xp[f] = face_flux_br<LIM>(Sk[fo + xc], Sk[fo + xo], Sk[fo + xf], mup, bx);
+                    yp[f] = face_flux_br<LIM>(Sk[fo + yc], Sk[fo + yo], Sk[fo + yf], mvp, by);
+                    zp[f] = top ? T(0) : face_flux_br<LIM>(zc[fo], zo[fo], zf[fo], mwp, bz);
+                    if (valid) p.branch[(long long)f * nz * plane + (long long)k * plane + own] = (uint8_t)(bx | (by << 2) | (bz << 4));
+                } else {
+                    xp[f] = face_flux<LIM>(Sk[fo + xc], Sk[fo + xo], Sk[fo + xf], mup);
+                    yp[f] = face_flux<LIM>(Sk[fo + yc], Sk[fo + yo], Sk[fo + yf], mvp);
+                    zp[f] = top ? T(0) : face_flux<LIM>(zc[fo], zo[fo], zf[fo], mwp);
+                }
+                ysm[(f * (TY + 1) + ty + 1) * TX + tx] = yp[f];
+            }
         }
         {
+            // Edge faces as warp tasks: one per field for the j0-1/2 faces of the
+            // 32 columns, and the NT x TY faces at i0-1/2 packed 32 to a task
+            // (lane l takes row l % TY, as 32 is a multiple of TY).
+            constexpr int NYT = NT, NXT = (NT * TY + 31) / 32;
             const bool ub = meb >= T(0), ul = mel >= T(0);
             const int bc = (ub ? 1 : 2) * SX, bo = (ub ? 2 : 1) * SX, bf = (ub ? 0 : 3) * SX;
             const int lc = ul ? 3 : 4, lo = ul ? 4 : 3, lf = ul ? 2 : 5;
 #pragma unroll 1
-            for (int t = warp; t < 2 * NT; t += TY) {
-                const int f = t >> 1;
-                if ((t & 1) == 0) {
+            for (int t = warp; t < NYT + NXT; t += TY) {
+                if (t < NYT) {
                     // flux at j0-1/2 for column lane: slot rows 0..3 (j0-2 .. j0+1)
-                    const int fo = (f + 1) * FE + cx;
-                    ysm[(f * (TY + 1)) * TX + tx] = face_flux<LIM>(Sk[fo + bc], Sk[fo + bo], Sk[fo + bf], meb);
-                } else if (lane < TY) {
-                    // flux at i0-1/2 for row lane: slot columns 2..5 (i0-2 .. i0+1)
-                    const int fo = (f + 1) * FE + (lane + 2) * SX;
-                    xbs[f * TY + lane] = face_flux<LIM>(Sk[fo + lc], Sk[fo + lo], Sk[fo + lf], mel);
+                    const int fo = (t + 1) * FE + cx;
+                    ysm[(t * (TY + 1)) * TX + tx] = face_flux<LIM>(Sk[fo + bc], Sk[fo + bo], Sk[fo + bf], meb);
+                } else {
+                    // flux at i0-1/2 for row er of field f: slot columns 2..5 (i0-2 .. i0+1)
+                    const int f = ((t - NYT) * 32 + lane) / TY;
+                    if (f < NT) {
+                        const int fo = (f + 1) * FE + (er + 2) * SX;
+                        xbs[f * TY + er] = face_flux<LIM>(Sk[fo + lc], Sk[fo + lo], Sk[fo + lf], mel);
+                    }
                 }
             }
         }
         __syncthreads();
 
-        // ---- divergence, RK combine, store
+        // ---- divergence and RK combine: out = Y^n + ax dX + ay dY + az dZ (+ cdt tendency),
+        // each step one FMA on an exact difference
         const T az = -cdt * p.rdz[k];
         T out[NF];
-        out[0] = yb[0] + ax * (mup - mum) + ay * (mvp - mvm) + az * (mwp - zlo[0]);
+        out[0] = fma(az, mwp - zlo[0], fma(ay, mvp - mvm, fma(ax, mup - mum, yb[0])));
         zlo[0] = mwp;
+        T xm[NT], ym[NT];
 #pragma unroll
         for (int f = 0; f < NT; f++) {
-            T xm = __shfl_up_sync(0xffffffffu, xp[f], 1);
-            if (lane == 0) xm = xbs[f * TY + ty];
-            const T ym = ysm[(f * (TY + 1) + ty) * TX + tx];
-            T o = yb[f + 1] + ax * (xp[f] - xm);
-            o += ay * (yp[f] - ym);
-            o += az * (zp[f] - zlo[f + 1]);
-            if (p.tend) o += cdt * p.tend[(long long)f * nz * plane + (long long)k * plane + own];
+            xm[f] = __shfl_up_sync(0xffffffffu, xp[f], 1);
+            if (lane == 0) xm[f] = xbs[f * TY + ty];
+            ym[f] = ysm[(f * (TY + 1) + ty) * TX + tx];
+        }
+        if constexpr (PACK) {
+            const float2 neg1 = make_float2(-1.f, -1.f), ax2 = make_float2(ax, ax), ay2 = make_float2(ay, ay),
+                         az2 = make_float2(az, az);
+#pragma unroll
+            for (int f = 0; f + 1 < NT; f += 2) {
+                float2 o = __ffma2_rn(ax2, __ffma2_rn(make_float2(xm[f], xm[f + 1]), neg1, make_float2(xp[f], xp[f + 1])),
+                                      make_float2(yb[f + 1], yb[f + 2]));
+                o = __ffma2_rn(ay2, __ffma2_rn(make_float2(ym[f], ym[f + 1]), neg1, make_float2(yp[f], yp[f + 1])), o);
+                o = __ffma2_rn(az2, __ffma2_rn(make_float2(zlo[f + 1], zlo[f + 2]), neg1, make_float2(zp[f], zp[f + 1])), o);
+                out[f + 1] = o.x;
+                out[f + 2] = o.y;
+            }
+            if (NT & 1) {
+                constexpr int f = NT - 1;
+                out[f + 1] = fma(az, zp[f] - zlo[f + 1], fma(ay, yp[f] - ym[f], fma(ax, xp[f] - xm[f], yb[f + 1])));
+            }
+        } else {
+#pragma unroll
+            for (int f = 0; f < NT; f++)
+                out[f + 1] = fma(az, zp[f] - zlo[f + 1], fma(ay, yp[f] - ym[f], fma(ax, xp[f] - xm[f], yb[f + 1])));
+        }
+#pragma unroll
+        for (int f = 0; f < NT; f++) {
+            if (p.tend) out[f + 1] = fma(cdt, p.tend[(long long)f * nz * plane + (unsigned)k * plane + own], out[f + 1]);
             zlo[f + 1] = zp[f];
-            out[f + 1] = o;
         }
         if (valid) {
             if (p.out_padded) {
@@ -377,12 +442,12 @@ __device__ __forceinline__ bool stage_tile(const StageParams<T> &p, const CUtens
                 const T r = recip(out[0]);
 #pragma unroll
                 for (int f = 1; f < NF; f++) out[f] *= r;
-                const long long ob = (long long)k * p.oplane + (long long)(j + 2) * p.opitch + (i + 4);
+                const unsigned ob = (unsigned)k * (unsigned)p.oplane + (unsigned)(j + 2) * (unsigned)p.opitch + (unsigned)(i + 4);
 #pragma unroll
                 for (int f = 0; f < NF; f++) p.yout[f][ob] = out[f];
                 if (ghost_x || ghost_y) {
-                    const long long gx = (i < 2) ? nx : ((i >= nx - 2) ? -nx : 0);
-                    const long long gy = (j < 2) ? (long long)ny * p.opitch : ((j >= ny - 2) ? -(long long)ny * p.opitch : 0);
+                    const int gx = (i < 2) ? nx : ((i >= nx - 2) ? -nx : 0);
+                    const int gy = (j < 2) ? ny * (int)p.opitch : ((j >= ny - 2) ? -ny * (int)p.opitch : 0);
 #pragma unroll
                     for (int f = 0; f < NF; f++) {
                         T *o = p.yout[f] + ob;
@@ -391,7 +456,7 @@ __device__ __forceinline__ bool stage_tile(const StageParams<T> &p, const CUtens
                     }
                 }
             } else {
-                const long long o = (long long)k * plane + own;
+                const unsigned o = (unsigned)k * plane + own;
 #pragma unroll
                 for (int f = 0; f < NF; f++) p.yout[f][o] = out[f];
             }
