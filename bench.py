@@ -231,9 +231,14 @@ def _time_steps(asuca, g, st, dt, ws_t, bud, steps, warmup, world, profile=False
 
 
 def adjoint_cost(asuca, dev, reps=3):
-    """Wall time of asuca_adjoint_step (checkpointed recompute + reverse) over the
-    wall time of asuca_step for the same 50 steps, on the 128x128x58, 4-tracer
-    workload with checkpoints every 10 steps; FP64 and FP32."""
+    """Adjoint cost on the 128x128x58, 4-tracer workload, 50 steps, checkpoints
+    every 10 steps, FP64 and FP32, against the wall time of asuca_step for the
+    same 50 steps:
+      * backward: asuca_adjoint_from_checkpoints (what AdjointFn.backward runs:
+        each segment recomputed from the checkpoints AdjointFn.forward kept,
+        then reversed); adjoint_over_forward = backward / forward;
+      * the forward with checkpoints (asuca_forward_checkpointed, AdjointFn.forward);
+      * standalone asuca_adjoint_step, which also runs the checkpointing forward pass."""
     import torch
     import gen
     case = gen.make_config_case("adjoint_128x128x58")
@@ -245,36 +250,59 @@ def adjoint_cost(asuca, dev, reps=3):
         ws = g.workspace(device=dev)
         nadj = asuca.adjoint_workspace_bytes(g, nsteps, K)
         wsa = torch.empty(nadj, dtype=torch.uint8, device=dev)
+        ckb = torch.empty(max(asuca.checkpoint_bytes(g, nsteps, K), 256), dtype=torch.uint8, device=dev)
         lam = torch.randn((case.nfields,) + tuple(st0.rho.shape), dtype=g.torch_dtype, device=dev).contiguous()
 
-        def fwd():
-            s_ = st0.clone()
+        def timed(fn):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
-            asuca.step(g, s_, case.dt, nsteps, workspace=ws)
+            fn()
             e1.record()
             torch.cuda.synchronize()
             return e0.elapsed_time(e1)
 
-        def adj():
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            asuca.adjoint_step(g, st0, case.dt, nsteps, lam, checkpoint_every=K, workspace=wsa)
-            e1.record()
-            torch.cuda.synchronize()
-            return e0.elapsed_time(e1)
+        s_ = st0.clone()
 
-        fwd(); adj()
-        tf = min(fwd() for _ in range(reps))
+        def reset():
+            for a_, b_ in zip((s_.rho, s_.rhotheta, s_.rhoq), (st0.rho, st0.rhotheta, st0.rhoq)):
+                a_.copy_(b_)
+
+        fwd = lambda: asuca.step(g, s_, case.dt, nsteps, workspace=ws)
+        fwd_ck = lambda: asuca.forward_checkpointed(g, s_, case.dt, nsteps, checkpoint_every=K, workspace=ws,
+                                                     checkpoints=ckb)
+        bwd = lambda: asuca.adjoint_from_checkpoints(g, ckb, st0, case.dt, nsteps, lam, checkpoint_every=K,
+                                                     workspace=wsa)
+        alone = lambda: asuca.adjoint_step(g, st0, case.dt, nsteps, lam, checkpoint_every=K, workspace=wsa)
+
+        def best(fn):
+            r = []
+            for _ in range(reps):
+                reset()
+                torch.cuda.synchronize()
+                r.append(timed(fn))
+            return min(r)
+
+        for fn in (fwd, fwd_ck, bwd, alone):
+            reset()
+            fn()
+        torch.cuda.synchronize()
+        tf, tfc = best(fwd), best(fwd_ck)
+        reset()
+        fwd_ck()
+        torch.cuda.synchronize()
         asuca.profile_enable(g, True)
-        ta = min(adj() for _ in range(reps))
+        tb = min(timed(bwd) for _ in range(reps))
         prof = asuca.profile_read(g)
         asuca.profile_enable(g, False)
+        ta = min(timed(alone) for _ in range(reps))
+        assert asuca.get_status(g) == asuca.OK
         names = {0: "stage", 1: "column", 2: "budget_reduce", 3: "adj_stage", 4: "adj_column"}
-        out[name] = {"forward_ms": tf, "adjoint_ms": ta, "adjoint_over_forward": ta / tf,
-                     "forward_plus_backward_over_forward": (tf + ta) / tf,
-                     "adjoint_kernels_ms_per_call": {names.get(k, str(k)): v[0] / reps for k, v in prof.items()}}
-        del st0, ws, wsa, lam
+        out[name] = {"forward_ms": tf, "forward_checkpointed_ms": tfc, "backward_ms": tb,
+                     "adjoint_over_forward": tb / tf,
+                     "forward_plus_backward_over_forward": (tfc + tb) / tf,
+                     "standalone_adjoint_step_ms": ta, "standalone_over_forward": ta / tf,
+                     "backward_kernels_ms_per_call": {names.get(k, str(k)): v[0] / reps for k, v in prof.items()}}
+        del st0, ws, wsa, lam, ckb, s_
         torch.cuda.empty_cache()
     return out
 

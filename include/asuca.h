@@ -152,6 +152,38 @@ asuca_status asuca_adjoint_step(asuca_grid *grid, const asuca_state *initial, co
                                 void *grad_mu, void *grad_mv, void *grad_mw, void *workspace,
                                 size_t workspace_bytes, void *cuda_stream);
 
+/* Bytes of the checkpoint buffer of asuca_forward_checkpointed:
+ * ceil(nsteps / checkpoint_every) states of F fields, each rounded up to
+ * 256 bytes.  0 for nsteps = 0 or an invalid argument. */
+size_t asuca_checkpoint_bytes(const asuca_grid *grid, int nsteps, int checkpoint_every);
+
+/* The forward half of checkpointed differentiation: advances `state` by
+ * nsteps exactly as asuca_step does (same kernels, bit-identical result and
+ * budgets) and keeps the state before steps 0, K, 2K, ... (K =
+ * checkpoint_every) in `checkpoints` (device, 256-byte aligned, at least
+ * asuca_checkpoint_bytes; block c holds the F fields [F][nz][ny][nx] of
+ * step c K).  A later asuca_adjoint_from_checkpoints then recomputes only
+ * within segments, so the reverse pass does not repeat the forward run.
+ * The workspace is asuca_step's.  ASUCA_ERR_ARG for a missing or short
+ * checkpoint buffer. */
+asuca_status asuca_forward_checkpointed(asuca_grid *grid, asuca_state *state, const void *tendencies, double dt,
+                                        int nsteps, int checkpoint_every, void *checkpoints,
+                                        size_t checkpoint_bytes, void *workspace, size_t workspace_bytes,
+                                        double *budgets_dev, void *cuda_stream);
+
+/* The reverse half: the same result as asuca_adjoint_step (bit for bit),
+ * starting from the checkpoints an asuca_forward_checkpointed call with the
+ * same grid, fluxes, tendencies, dt, nsteps and checkpoint_every kept.
+ * Only fluxes->mu, mv, mw are read.  Each segment is recomputed once while
+ * recording stage states and limiter branches, then reversed.  The
+ * workspace is asuca_adjoint_workspace_bytes(grid, nsteps, K) bytes
+ * (its checkpoint area is left unused). */
+asuca_status asuca_adjoint_from_checkpoints(asuca_grid *grid, const void *checkpoints, const asuca_state *fluxes,
+                                            const void *tendencies, double dt, int nsteps, int checkpoint_every,
+                                            const void *lambda_final, void *grad_initial, void *grad_mu,
+                                            void *grad_mv, void *grad_mw, void *workspace, size_t workspace_bytes,
+                                            void *cuda_stream);
+
 /* ---- ensemble -------------------------------------------------------------
  * Members are grids with the same nz, number of tracers, precision and
  * limiter and any horizontal size; they are advanced together by one

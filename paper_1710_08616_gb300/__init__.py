@@ -74,6 +74,13 @@ SIGNATURES = {
     "asuca_adjoint_workspace_bytes": (ctypes.c_size_t, [_VP, ctypes.c_int, ctypes.c_int]),
     "asuca_adjoint_step": (ctypes.c_int, [_VP, ctypes.POINTER(StateStruct), _VP, ctypes.c_double, ctypes.c_int,
                                           ctypes.c_int, _VP, _VP, _VP, _VP, _VP, _VP, ctypes.c_size_t, _VP]),
+    "asuca_checkpoint_bytes": (ctypes.c_size_t, [_VP, ctypes.c_int, ctypes.c_int]),
+    "asuca_forward_checkpointed": (ctypes.c_int, [_VP, ctypes.POINTER(StateStruct), _VP, ctypes.c_double,
+                                                  ctypes.c_int, ctypes.c_int, _VP, ctypes.c_size_t, _VP,
+                                                  ctypes.c_size_t, _VP, _VP]),
+    "asuca_adjoint_from_checkpoints": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(StateStruct), _VP, ctypes.c_double,
+                                                      ctypes.c_int, ctypes.c_int, _VP, _VP, _VP, _VP, _VP, _VP,
+                                                      ctypes.c_size_t, _VP]),
     "asuca_debug_record_branches": (ctypes.c_int, [_VP, ctypes.POINTER(StateStruct), _VP, ctypes.c_double,
                                                    ctypes.c_int, _VP, _VP, ctypes.c_size_t, _VP]),
     "asuca_ensemble_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(_VP), ctypes.c_int]),
@@ -205,9 +212,9 @@ class State:
         return torch.cat([self.rho[None], self.rhotheta[None], self.rhoq], 0)
 
     def struct(self) -> StateStruct:
-        return StateStruct(self.rho.data_ptr(), self.rhotheta.data_ptr(),
-                           self.rhoq.data_ptr() if self.rhoq.numel() else None,
-                           self.mu.data_ptr(), self.mv.data_ptr(), self.mw.data_ptr())
+        ptr = lambda t: t.data_ptr() if t is not None and t.numel() else None
+        return StateStruct(ptr(self.rho), ptr(self.rhotheta), ptr(self.rhoq), ptr(self.mu), ptr(self.mv),
+                           ptr(self.mw))
 
 
 def _check_state(grid: Grid, st: State):
@@ -332,6 +339,59 @@ def adjoint_step(grid: Grid, initial: State, dt: float, nsteps: int, lam_final, 
     return g0, gmu, gmv, gmw
 
 
+def checkpoint_bytes(grid: Grid, nsteps: int, checkpoint_every: int = 10) -> int:
+    return int(lib().asuca_checkpoint_bytes(grid.handle, int(nsteps), int(checkpoint_every)))
+
+
+def forward_checkpointed(grid: Grid, state: State, dt: float, nsteps: int, *, checkpoint_every: int = 10,
+                         tendencies=None, workspace=None, checkpoints=None, budgets=None, stream=None):
+    """asuca_forward_checkpointed: advance `state` in place by nsteps (as step())
+    and return the uint8 checkpoint tensor (the state every checkpoint_every
+    steps) that adjoint_from_checkpoints reverses from."""
+    import torch
+    _check_state(grid, state)
+    dev = state.rho.device
+    if workspace is None:
+        workspace = grid.workspace(device=dev)
+    n = checkpoint_bytes(grid, nsteps, checkpoint_every)
+    if checkpoints is None:
+        checkpoints = torch.empty(max(n, 256), dtype=torch.uint8, device=dev)
+    if budgets is True:
+        budgets = torch.empty(grid.nfields + 1, dtype=torch.float64, device=dev)
+    s = state.struct()
+    _check(lib().asuca_forward_checkpointed(grid.handle, ctypes.byref(s), _ptr(tendencies), float(dt), int(nsteps),
+                                            int(checkpoint_every), _ptr(checkpoints), checkpoints.numel(),
+                                            _ptr(workspace), workspace.numel(), _ptr(budgets), _stream_ptr(stream)),
+           "asuca_forward_checkpointed")
+    return checkpoints
+
+
+def adjoint_from_checkpoints(grid: Grid, checkpoints, fluxes: State, dt: float, nsteps: int, lam_final, *,
+                             checkpoint_every: int = 10, tendencies=None, workspace=None, stream=None):
+    """asuca_adjoint_from_checkpoints: the adjoint_step result, reversing from
+    the checkpoints forward_checkpointed kept (fluxes supplies mu, mv, mw)."""
+    import torch
+    F = grid.nfields
+    shape = (F, grid.nz, grid.ny, grid.nx)
+    if tuple(lam_final.shape) != shape or lam_final.dtype != grid.torch_dtype or not lam_final.is_contiguous():
+        raise ValueError(f"lam_final: need contiguous {grid.torch_dtype} of shape {shape}")
+    dev = fluxes.mu.device
+    if workspace is None:
+        n = adjoint_workspace_bytes(grid, nsteps, checkpoint_every)
+        workspace = torch.empty(max(n, 256), dtype=torch.uint8, device=dev)
+    g0 = torch.empty(shape, dtype=grid.torch_dtype, device=dev)
+    gmu = torch.empty_like(fluxes.mu)
+    gmv = torch.empty_like(fluxes.mv)
+    gmw = torch.empty_like(fluxes.mw)
+    s = fluxes.struct()
+    _check(lib().asuca_adjoint_from_checkpoints(grid.handle, _ptr(checkpoints), ctypes.byref(s), _ptr(tendencies),
+                                                float(dt), int(nsteps), int(checkpoint_every), _ptr(lam_final),
+                                                _ptr(g0), _ptr(gmu), _ptr(gmv), _ptr(gmw), _ptr(workspace),
+                                                workspace.numel(), _stream_ptr(stream)),
+           "asuca_adjoint_from_checkpoints")
+    return g0, gmu, gmv, gmw
+
+
 def record_branches(grid: Grid, initial: State, dt: float, nsteps: int, *, tendencies=None, stream=None):
     """Limiter branch bytes [nsteps][3][F-1][nz][ny][nx] of a forward trajectory."""
     import torch
@@ -353,30 +413,32 @@ def _autograd_function():
         """Y_final = step^nsteps(Y_initial; mu, mv, mw) with a hand-written adjoint.
 
         forward(rho0, rhotheta0, rhoq0, mu, mv, mw, grid, dt, nsteps, checkpoint_every)
-        -> (rho, rhotheta, rhoq) after nsteps steps.  backward runs
-        asuca_adjoint_step, which recomputes the trajectory from the saved
-        initial state with checkpoints every checkpoint_every steps."""
+        -> (rho, rhotheta, rhoq) after nsteps steps.  The forward pass keeps the
+        state every checkpoint_every steps (asuca_forward_checkpointed); backward
+        runs asuca_adjoint_from_checkpoints, which recomputes each segment from
+        its checkpoint and reverses it."""
 
         @staticmethod
         def forward(ctx, rho0, rhotheta0, rhoq0, mu, mv, mw, grid, dt, nsteps, checkpoint_every=10):
             st = State(rho0.detach().clone().contiguous(), rhotheta0.detach().clone().contiguous(),
                        rhoq0.detach().clone().contiguous(), mu.detach().contiguous(), mv.detach().contiguous(),
                        mw.detach().contiguous())
-            ctx.save_for_backward(rho0, rhotheta0, rhoq0, mu, mv, mw)
+            ckpt = forward_checkpointed(grid, st, dt, nsteps, checkpoint_every=checkpoint_every)
+            ctx.save_for_backward(mu, mv, mw, ckpt)
             ctx.grid, ctx.dt, ctx.nsteps, ctx.k = grid, dt, nsteps, checkpoint_every
-            step(grid, st, dt, nsteps)
+            ctx.like = [(t.shape, t.dtype, t.device) for t in (rho0, rhotheta0, rhoq0)]
             return st.rho, st.rhotheta, st.rhoq
 
         @staticmethod
         def backward(ctx, g_rho, g_rt, g_q):
-            rho0, rt0, q0, mu, mv, mw = ctx.saved_tensors
+            mu, mv, mw, ckpt = ctx.saved_tensors
             grid = ctx.grid
-            z = lambda t, like: torch.zeros_like(like) if t is None else t
-            lam = torch.cat([z(g_rho, rho0)[None], z(g_rt, rt0)[None], z(g_q, q0)], 0).contiguous()
-            init = State(rho0.detach().contiguous(), rt0.detach().contiguous(), q0.detach().contiguous(),
-                         mu.detach().contiguous(), mv.detach().contiguous(), mw.detach().contiguous())
-            g0, gmu, gmv, gmw = adjoint_step(grid, init, ctx.dt, ctx.nsteps, lam.to(grid.torch_dtype),
-                                             checkpoint_every=ctx.k)
+            z = lambda t, like: torch.zeros(like[0], dtype=like[1], device=like[2]) if t is None else t
+            lam = torch.cat([z(g_rho, ctx.like[0])[None], z(g_rt, ctx.like[1])[None], z(g_q, ctx.like[2])],
+                            0).contiguous()
+            fl = State(None, None, None, mu.detach().contiguous(), mv.detach().contiguous(), mw.detach().contiguous())
+            g0, gmu, gmv, gmw = adjoint_from_checkpoints(grid, ckpt, fl, ctx.dt, ctx.nsteps,
+                                                         lam.to(grid.torch_dtype), checkpoint_every=ctx.k)
             return g0[0], g0[1], g0[2:], gmu, gmv, gmw, None, None, None, None
 
     return AdjointFn

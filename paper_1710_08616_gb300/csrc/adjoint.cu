@@ -246,54 +246,66 @@ __global__ void __launch_bounds__(COL_TPB) adj_column_kernel(const __grid_consta
                 }
                 S(k, 3) = 0.0;                        // lambda_rho increment
             }
-            // ---- transpose of the diffusion, field by field
-            for (int f = 0; f < NT; f++) {
-                double eu = 0.0;
-                for (int k = nz - 1; k >= 0; k--) {
-                    const long long o = (long long)k * plane + col;
-                    const double xr = to_f64(p.y[0][o]) * to_f64(a.lam[f + 1][o]) / p.dz[k];
-                    eu = fma(S(k, 1), eu, xr);
-                    S(k, 4 + NT + f) = eu;
-                }
-                double zp = 0.0, psi_prev = 0.0, phi_prev = 0.0;
-                for (int k = 0; k < nz; k++) {
-                    const long long o = (long long)k * plane + col;
-                    const double gk = k > 0 ? S(k, 2) : 0.0;
-                    zp = fma(gk, zp, S(k, 4 + NT + f));
-                    const double psi = p.dz[k] * S(k, 0) * zp;
-                    const double ph = S(k, 4 + f);
-                    const double lu = to_f64(a.lam[f + 1][o]);
-                    double lr = lu * ph - p.dz[k] * psi * ph;
-                    if (k > 0) {
-                        const double t = p.kc[k - 1] * (psi - psi_prev) * (ph - phi_prev);
-                        lr -= t;
-                        S(k - 1, 3) -= t;
-                    }
-                    S(k, 3) += lr;
-                    a.lam[f + 1][o] = (T)(p.dz[k] * psi);
-                    psi_prev = psi;
-                    phi_prev = ph;
+            // ---- transpose of the diffusion, every field in the same sweep over k
+            // (the fields' recurrences are independent, so their latencies overlap)
+            double eu[NT];
+#pragma unroll
+            for (int f = 0; f < NT; f++) eu[f] = 0.0;
+            for (int k = nz - 1; k >= 0; k--) {
+                const long long o = (long long)k * plane + col;
+                const double rk = to_f64(p.y[0][o]) * p.rdz64[k];   // rho_k / dz_k
+                const double al = S(k, 1);
+#pragma unroll
+                for (int f = 0; f < NT; f++) {
+                    eu[f] = fma(al, eu[f], rk * to_f64(a.lam[f + 1][o]));
+                    S(k, 4 + NT + f) = eu[f];
                 }
             }
+            double zp[NT], psi_prev[NT], phi_prev[NT];
+#pragma unroll
+            for (int f = 0; f < NT; f++) zp[f] = psi_prev[f] = phi_prev[f] = 0.0;
+            double carry = 0.0;   // lambda_rho increment of level k-1 still to be stored
+            for (int k = 0; k < nz; k++) {
+                const long long o = (long long)k * plane + col;
+                const double gk = k > 0 ? S(k, 2) : 0.0, dmk = p.dz[k] * S(k, 0), kcl = k > 0 ? p.kc[k - 1] : 0.0;
+                double lr = 0.0, tsum = 0.0;
+#pragma unroll
+                for (int f = 0; f < NT; f++) {
+                    zp[f] = fma(gk, zp[f], S(k, 4 + NT + f));
+                    const double psi = dmk * zp[f];
+                    const double ph = S(k, 4 + f);
+                    const double lu = to_f64(a.lam[f + 1][o]);
+                    lr += (lu - p.dz[k] * psi) * ph;
+                    tsum += kcl * (psi - psi_prev[f]) * (ph - phi_prev[f]);
+                    a.lam[f + 1][o] = from_f64<T>(p.dz[k] * psi);
+                    psi_prev[f] = psi;
+                    phi_prev[f] = ph;
+                }
+                // the face k-1/2 term enters level k with a minus sign and level k-1 with a minus sign
+                if (k > 0) S(k - 1, 3) = carry - tsum;
+                carry = lr - tsum;
+            }
+            S(nz - 1, 3) = carry;
         }
         // ---- transpose of the sedimentation (bottom-up) and of the relaxation
         double nu_prev = 0.0;
+        const double sv = to_f64(p.sed_v), rr = to_f64(p.relax_r), ri = to_f64(p.relax_inv);
         for (int k = 0; k < nz; k++) {
             const long long o = (long long)k * plane + col;
             if (p.do_sed) {
                 double nu = to_f64(a.lam[p.sed][o]);
-                if (k > 0) nu += p.dt * to_f64(p.sed_v) * (double)p.sedr[k - 1] * nu_prev;
+                if (k > 0) nu += p.dt * sv * to_f64(p.sedr[k - 1]) * nu_prev;
                 nu_prev = nu;
-                a.lam[p.sed][o] = (T)(nu * p.dz[k] * (double)p.sedr[k]);
+                a.lam[p.sed][o] = from_f64<T>(nu * p.dz[k] * to_f64(p.sedr[k]));
             }
             double lrho = to_f64(a.lam[0][o]);
             if (p.do_diff) lrho += S(k, 3);
             if (p.do_relax) {
                 const double lt = to_f64(a.lam[1][o]);
-                lrho += lt * (double)p.relax_r * (double)p.thref[k] * (double)p.relax_inv;
-                a.lam[1][o] = (T)(lt * (double)p.relax_inv);
+                lrho += lt * rr * to_f64(p.thref[k]) * ri;
+                a.lam[1][o] = from_f64<T>(lt * ri);
             }
-            a.lam[0][o] = (T)lrho;
+            a.lam[0][o] = from_f64<T>(lrho);
         }
     }
 }

@@ -198,6 +198,7 @@ ColumnParams<T> column_params(const asuca_grid *g, double dt) {
         p.thref[k] = (T)(300.0 + 0.004 * g->zc[k]);
         p.dzr_up[k] = (k + 1 < nz) ? g->dz[k + 1] / g->dz[k] : 0.0;
         p.dzr_dn[k] = (k > 0) ? g->dz[k - 1] / g->dz[k] : 0.0;
+        p.rdz64[k] = 1.0 / g->dz[k];
         if (k + 1 < nz && p.do_diff) {
             const double K = d.k0 * std::exp(-g->zf[k + 1] / d.k_h);
             p.kc[k] = 0.5 * dt * K / (g->zc[k + 1] - g->zc[k]);
@@ -282,10 +283,12 @@ template <typename T>
 asuca_status run_step_dataflow(asuca_grid *g, asuca_state *st, const void *tend, double dt, int nsteps,
                                char *ws, double *budgets, cudaStream_t s);
 
+// zero_precip = false continues the precipitation total of a previous call
+// on the same workspace (the checkpointed forward runs one call per segment).
 template <typename T>
 asuca_status run_step(asuca_grid *g, asuca_state *st, const void *tend, double dt, int nsteps,
-                      char *ws, double *budgets, cudaStream_t s) {
-    if (g->step_mode == 1) return run_step_dataflow<T>(g, st, tend, dt, nsteps, ws, budgets, s);
+                      char *ws, double *budgets, cudaStream_t s, bool zero_precip = true) {
+    if (g->step_mode == 1 && zero_precip) return run_step_dataflow<T>(g, st, tend, dt, nsteps, ws, budgets, s);
     const StepLayout L = step_layout(g);
     const int F = g->F;
     T *yn[MAXF], *y1[MAXF], *y2[MAXF];
@@ -299,7 +302,7 @@ asuca_status run_step(asuca_grid *g, asuca_state *st, const void *tend, double d
     cp.partials = (double *)(ws + L.partials);
     cp.scratch = (double *)(ws + L.scratch);
 
-    cudaError_t e = cudaMemsetAsync(ws + L.precip, 0, (size_t)g->plane * sizeof(double), s);
+    cudaError_t e = zero_precip ? cudaMemsetAsync(ws + L.precip, 0, (size_t)g->plane * sizeof(double), s) : cudaSuccess;
     if (e != cudaSuccess) return ASUCA_ERR_CUDA;
     if (g->map_ws != (void *)ws || g->map_ty != g->stage_ty) {
         if (encode_stage_map<T>(&g->map_ystar, ws + L.ystar, F, g->d.nx, g->d.ny, g->d.nz, g->stage_ty) != cudaSuccess ||
@@ -540,32 +543,37 @@ asuca_state block_state(const asuca_grid *g, void *base, const asuca_state *m) {
 
 template <typename T>
 asuca_status run_adjoint(asuca_grid *g, const asuca_state *init, const void *tend, double dt, int nsteps,
-                         int K, const T *lam_final, T *grad0, T *gmu, T *gmv, T *gmw, char *ws, cudaStream_t s) {
+                         int K, const T *lam_final, T *grad0, T *gmu, T *gmv, T *gmw, char *ws,
+                         const char *ckpt_ext, cudaStream_t s) {
     const AdjLayout L = adj_layout(g, nsteps, K);
     const int F = g->F;
     const size_t cb = (size_t)g->cells * sizeof(T);
     cudaError_t e = cudaSuccess;
     auto ck = [&](cudaError_t r) { if (r != cudaSuccess && e == cudaSuccess) e = r; };
-    // ---- forward pass from the initial state, keeping a checkpoint every K steps;
-    // the last segment is not checkpointed: it is recorded below straight from W
-    T *Wf[MAXF];
-    block_fields<T>(g, ws + L.W, Wf);
-    T *init_f[MAXF];
-    field_ptrs<T>(g, init->rho, init->rhotheta, init->rhoq, init_f);
-    for (int f = 0; f < F; f++) ck(cudaMemcpyAsync(Wf[f], init_f[f], cb, cudaMemcpyDeviceToDevice, s));
-    asuca_state Ws = block_state<T>(g, ws + L.W, init);
-    const int last_start = L.ncp > 0 ? (L.ncp - 1) * K : 0;
-    for (int n = 0; n < last_start; n++) {
-        if (n % K == 0)
-            ck(cudaMemcpyAsync(ws + L.ckpt + (size_t)(n / K) * align_up(L.ustate), ws + L.W, L.ustate,
+    // checkpoints: the caller's (kept by its forward pass), or made here
+    const char *ckbase = ckpt_ext ? ckpt_ext : ws + L.ckpt;
+    if (!ckpt_ext) {
+        // ---- forward pass from the initial state, keeping a checkpoint every K steps;
+        // the last segment's checkpoint is all that is needed of it
+        T *Wf[MAXF];
+        block_fields<T>(g, ws + L.W, Wf);
+        T *init_f[MAXF];
+        field_ptrs<T>(g, init->rho, init->rhotheta, init->rhoq, init_f);
+        for (int f = 0; f < F; f++) ck(cudaMemcpyAsync(Wf[f], init_f[f], cb, cudaMemcpyDeviceToDevice, s));
+        asuca_state Ws = block_state<T>(g, ws + L.W, init);
+        const int last_start = L.ncp > 0 ? (L.ncp - 1) * K : 0;
+        for (int n = 0; n < last_start; n++) {
+            if (n % K == 0)
+                ck(cudaMemcpyAsync(ws + L.ckpt + (size_t)(n / K) * align_up(L.ustate), ws + L.W, L.ustate,
+                                   cudaMemcpyDeviceToDevice, s));
+            if (e != cudaSuccess) return ASUCA_ERR_CUDA;
+            asuca_status r = run_step<T>(g, &Ws, tend, dt, 1, ws + L.step, nullptr, s);
+            if (r != ASUCA_OK) return r;
+        }
+        if (L.ncp > 0)
+            ck(cudaMemcpyAsync(ws + L.ckpt + (size_t)(L.ncp - 1) * align_up(L.ustate), ws + L.W, L.ustate,
                                cudaMemcpyDeviceToDevice, s));
-        if (e != cudaSuccess) return ASUCA_ERR_CUDA;
-        asuca_status r = run_step<T>(g, &Ws, tend, dt, 1, ws + L.step, nullptr, s);
-        if (r != ASUCA_OK) return r;
     }
-    if (L.ncp > 0)
-        ck(cudaMemcpyAsync(ws + L.ckpt + (size_t)(L.ncp - 1) * align_up(L.ustate), ws + L.W, L.ustate,
-                           cudaMemcpyDeviceToDevice, s));
     // ---- adjoint accumulators
     const size_t mb = (size_t)g->cells * sizeof(T), mwb = (size_t)(g->d.nz + 1) * g->plane * sizeof(T);
     ck(cudaMemsetAsync(gmu, 0, mb, s));
@@ -599,7 +607,7 @@ asuca_status run_adjoint(asuca_grid *g, const asuca_state *init, const void *ten
             return (uint8_t *)(ws + L.branch + (size_t)q * align_up(L.nbranch_step)) +
                    (size_t)stg * (F - 1) * g->cells;
         };
-        ck(cudaMemcpyAsync(segYn(0), ws + L.ckpt + (size_t)c * align_up(L.ustate), L.ustate,
+        ck(cudaMemcpyAsync(segYn(0), ckbase + (size_t)c * align_up(L.ustate), L.ustate,
                            cudaMemcpyDeviceToDevice, s));
         if (e != cudaSuccess) return ASUCA_ERR_CUDA;
         // ---- recompute the segment, recording stage states and limiter branches
@@ -697,6 +705,30 @@ asuca_status run_adjoint(asuca_grid *g, const asuca_state *init, const void *ten
     }
     ck(cudaMemcpyAsync(grad0, ws + L.lam, L.ustate, cudaMemcpyDeviceToDevice, s));
     return e == cudaSuccess ? ASUCA_OK : ASUCA_ERR_CUDA;
+}
+
+// Forward steps (asuca_step's) that also keep the state before steps 0, K,
+// 2K, ... in ckpt ([ceil(nsteps / K)] blocks of F fields, each block padded
+// to 256 bytes), the checkpoints run_adjoint reverses from.
+template <typename T>
+asuca_status run_forward_ckpt(asuca_grid *g, asuca_state *st, const void *tend, double dt, int nsteps, int K,
+                              char *ckpt, char *ws, double *budgets, cudaStream_t s) {
+    const int F = g->F;
+    const size_t cb = (size_t)g->cells * sizeof(T), us = align_up((size_t)F * cb);
+    T *yf[MAXF];
+    field_ptrs<T>(g, st->rho, st->rhotheta, st->rhoq, yf);
+    if (nsteps == 0) return run_step<T>(g, st, tend, dt, 0, ws, budgets, s);
+    for (int c = 0; c * K < nsteps; c++) {
+        for (int f = 0; f < F; f++)
+            if (cudaMemcpyAsync(ckpt + (size_t)c * us + (size_t)f * cb, yf[f], cb, cudaMemcpyDeviceToDevice, s) !=
+                cudaSuccess)
+                return ASUCA_ERR_CUDA;
+        const int n = (nsteps - c * K) < K ? (nsteps - c * K) : K;
+        const bool last = (c + 1) * K >= nsteps;
+        asuca_status r = run_step<T>(g, st, tend, dt, n, ws, last ? budgets : nullptr, s, c == 0);
+        if (r != ASUCA_OK) return r;
+    }
+    return ASUCA_OK;
 }
 
 // Forward steps that record every stage's limiter branches into out
@@ -1066,10 +1098,63 @@ asuca_status asuca_adjoint_step(asuca_grid *g, const asuca_state *initial, const
     if (g->d.prec == ASUCA_FP64)
         return run_adjoint<double>(g, initial, tendencies, dt, nsteps, checkpoint_every, (const double *)lambda_final,
                                    (double *)grad_initial, (double *)grad_mu, (double *)grad_mv, (double *)grad_mw,
-                                   (char *)workspace, s);
+                                   (char *)workspace, nullptr, s);
     return run_adjoint<float>(g, initial, tendencies, dt, nsteps, checkpoint_every, (const float *)lambda_final,
                               (float *)grad_initial, (float *)grad_mu, (float *)grad_mv, (float *)grad_mw,
-                              (char *)workspace, s);
+                              (char *)workspace, nullptr, s);
+}
+
+size_t asuca_checkpoint_bytes(const asuca_grid *g, int nsteps, int checkpoint_every) {
+    if (!g || nsteps < 0 || checkpoint_every < 1) return 0;
+    const size_t n = nsteps > 0 ? (size_t)((nsteps + checkpoint_every - 1) / checkpoint_every) : 0;
+    return n * align_up((size_t)g->F * g->cells * elem_size(g));
+}
+
+asuca_status asuca_forward_checkpointed(asuca_grid *g, asuca_state *state, const void *tendencies, double dt,
+                                        int nsteps, int checkpoint_every, void *checkpoints,
+                                        size_t checkpoint_bytes, void *workspace, size_t workspace_bytes,
+                                        double *budgets_dev, void *cuda_stream) {
+    if (!g || !state_ok(g, state) || nsteps < 0 || checkpoint_every < 1 || !std::isfinite(dt) || dt < 0.0)
+        return ASUCA_ERR_ARG;
+    if (nsteps > 0 && (!checkpoints || checkpoint_bytes < asuca_checkpoint_bytes(g, nsteps, checkpoint_every) ||
+                       ((uintptr_t)checkpoints % ALIGN) != 0))
+        return ASUCA_ERR_ARG;
+    asuca_status prev = take_status(g);
+    if (prev != ASUCA_OK) return prev;
+    if (!workspace || ((uintptr_t)workspace % ALIGN) != 0 || workspace_bytes < step_layout(g).total)
+        return ASUCA_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    g->last_stream = s;
+    return g->d.prec == ASUCA_FP64
+               ? run_forward_ckpt<double>(g, state, tendencies, dt, nsteps, checkpoint_every, (char *)checkpoints,
+                                          (char *)workspace, budgets_dev, s)
+               : run_forward_ckpt<float>(g, state, tendencies, dt, nsteps, checkpoint_every, (char *)checkpoints,
+                                         (char *)workspace, budgets_dev, s);
+}
+
+asuca_status asuca_adjoint_from_checkpoints(asuca_grid *g, const void *checkpoints, const asuca_state *fluxes,
+                                            const void *tendencies, double dt, int nsteps, int checkpoint_every,
+                                            const void *lambda_final, void *grad_initial, void *grad_mu,
+                                            void *grad_mv, void *grad_mw, void *workspace, size_t workspace_bytes,
+                                            void *cuda_stream) {
+    if (!g || !fluxes || !fluxes->mu || !fluxes->mv || !fluxes->mw || nsteps < 0 || checkpoint_every < 1 ||
+        !std::isfinite(dt) || dt < 0.0 || !lambda_final || !grad_initial || !grad_mu || !grad_mv || !grad_mw ||
+        (nsteps > 0 && (!checkpoints || ((uintptr_t)checkpoints % ALIGN) != 0)))
+        return ASUCA_ERR_ARG;
+    asuca_status prev = take_status(g);
+    if (prev != ASUCA_OK) return prev;
+    if (!workspace || ((uintptr_t)workspace % ALIGN) != 0 ||
+        workspace_bytes < adj_layout(g, nsteps, checkpoint_every).total)
+        return ASUCA_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    g->last_stream = s;
+    if (g->d.prec == ASUCA_FP64)
+        return run_adjoint<double>(g, fluxes, tendencies, dt, nsteps, checkpoint_every, (const double *)lambda_final,
+                                   (double *)grad_initial, (double *)grad_mu, (double *)grad_mv, (double *)grad_mw,
+                                   (char *)workspace, (const char *)checkpoints, s);
+    return run_adjoint<float>(g, fluxes, tendencies, dt, nsteps, checkpoint_every, (const float *)lambda_final,
+                              (float *)grad_initial, (float *)grad_mu, (float *)grad_mv, (float *)grad_mw,
+                              (char *)workspace, (const char *)checkpoints, s);
 }
 
 asuca_status asuca_debug_record_branches(asuca_grid *g, const asuca_state *initial, const void *tendencies,

@@ -92,6 +92,7 @@ struct ColumnParams {
     double kc[MAXNZ];       // dt K(z_{k+1/2}) / dzc_{k+1/2} / 2 for face k+1/2 (0 at the top lid)
     double dzr_up[MAXNZ];   // dz_{k+1} / dz_k
     double dzr_dn[MAXNZ];   // dz_{k-1} / dz_k
+    double rdz64[MAXNZ];    // 1 / dz_k
 };
 
 // ------------------------------------------------------------------ helpers
@@ -140,6 +141,9 @@ __device__ __forceinline__ float d2f_bits(double x) {
 template <typename T> __device__ __forceinline__ double to_f64(T x);
 template <> __device__ __forceinline__ double to_f64<double>(double x) { return x; }
 template <> __device__ __forceinline__ double to_f64<float>(float x) { return f2d_bits(x); }
+template <typename T> __device__ __forceinline__ T from_f64(double x);
+template <> __device__ __forceinline__ double from_f64<double>(double x) { return x; }
+template <> __device__ __forceinline__ float from_f64<float>(double x) { return d2f_bits(x); }
 
 // Reciprocal in double by Newton-Raphson iteration on f(y) = 1/y - x,
 // y <- y (2 - x y), started from the hardware reciprocal approximation of the

@@ -97,6 +97,36 @@ def test_adjoint_independent_of_checkpoint_interval(asuca):
             assert np.array_equal(x, y)
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("nsteps,K", [(7, 3), (6, 3), (1, 10), (0, 4)])
+def test_checkpointed_forward_and_adjoint_from_checkpoints(asuca, prec, nsteps, K):
+    """asuca_forward_checkpointed advances the state bit for bit as asuca_step
+    (budgets included), and asuca_adjoint_from_checkpoints on its checkpoints
+    returns asuca_adjoint_step's gradients bit for bit."""
+    import torch
+    c = gen.make_case(40, 24, 10, 3, seed=11)
+    g = asuca.Grid.from_case(c, prec=prec)
+    st_a = asuca.State.from_case(c, prec=prec)
+    st_b = st_a.clone()
+    st_0 = st_a.clone()
+    ba = asuca.step(g, st_a, c.dt, nsteps, budgets=True)
+    bb = torch.empty_like(ba)
+    ck = asuca.forward_checkpointed(g, st_b, c.dt, nsteps, checkpoint_every=K, budgets=bb)
+    torch.cuda.synchronize()
+    assert asuca.get_status(g) == asuca.OK
+    for x, y in zip(st_a.fields(), st_b.fields()):
+        assert torch.equal(x, y)
+    assert torch.equal(ba, bb)
+    lam = torch.tensor(np.random.default_rng(2).standard_normal(c.state().shape), dtype=g.torch_dtype,
+                       device="cuda")
+    ref = asuca.adjoint_step(g, st_0, c.dt, nsteps, lam, checkpoint_every=K)
+    got = asuca.adjoint_from_checkpoints(g, ck, st_0, c.dt, nsteps, lam, checkpoint_every=K)
+    torch.cuda.synchronize()
+    assert asuca.get_status(g) == asuca.OK
+    for x, y in zip(ref, got):
+        assert torch.equal(x, y)
+
+
 def test_dot_product_oracle_tangent_linear_vs_gpu_adjoint(asuca):
     c = gen.make_case(20, 16, 10, 3, seed=21)
     og = oracle.Grid.from_case(c)
