@@ -18,38 +18,44 @@
 namespace asuca {
 
 template <typename T, int NF, int LIM>
-__global__ void __launch_bounds__(128) adj_stage_kernel(const __grid_constant__ AdjStageParams<T> p) {
+__global__ void __launch_bounds__(128, 4) adj_stage_kernel(const __grid_constant__ AdjStageParams<T> p) {
     constexpr int NT = NF - 1;
+    // d face / d phi of the four stencil cells of a face for each upwind side
+    // and limiter branch, ctab[u * 16 + br * 4 + q] (u = 1 for M >= 0)
+    __shared__ T ctab[32];
+    {
+        const int t = threadIdx.y * blockDim.x + threadIdx.x;
+        if (t < 32) ctab[t] = face_coef<T>((t >> 4) != 0, (t >> 2) & 3, t & 3);
+        __syncthreads();
+    }
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int nx = p.nx, ny = p.ny, nz = p.nz;
     if (i >= nx || j >= ny) return;
-    const long long plane = p.plane;
-    int ix[5], jy[5];
+    // offsets within a field fit in 32 bits (the host checks)
+    const unsigned plane = (unsigned)p.plane, ysp = (unsigned)p.ys_plane;
+    // planar offsets (caller layout) of the cells i-2..i+2 (row j) and j-2..j+2
+    // (column i), and the same cells in the layout of the stage input
+    unsigned ox[5], oy[5], sx[5], sy[5];
 #pragma unroll
     for (int q = 0; q < 5; q++) {
-        ix[q] = wrap_index(i + q - 2, nx);
-        jy[q] = wrap_index(j + q - 2, ny);
-    }
-    // planar offsets (caller layout) of the cells i-2..i+2 (row j) and j-2..j+2 (column i)
-    long long ox[5], oy[5];
-#pragma unroll
-    for (int q = 0; q < 5; q++) {
-        ox[q] = (long long)j * nx + ix[q];
-        oy[q] = (long long)jy[q] * nx + i;
-    }
-    // the same cells in the layout of the stage input
-    long long sx[5], sy[5];
-#pragma unroll
-    for (int q = 0; q < 5; q++) {
-        sx[q] = (long long)(j + p.ys_oy) * p.ys_pitch + ix[q] + p.ys_ox;
-        sy[q] = (long long)(jy[q] + p.ys_oy) * p.ys_pitch + i + p.ys_ox;
+        const int ix = wrap_index(i + q - 2, nx), jy = wrap_index(j + q - 2, ny);
+        ox[q] = (unsigned)(j * nx + ix);
+        oy[q] = (unsigned)(jy * nx + i);
+        sx[q] = (unsigned)((j + p.ys_oy) * p.ys_pitch + ix + p.ys_ox);
+        sy[q] = (unsigned)((jy + p.ys_oy) * p.ys_pitch + i + p.ys_ox);
     }
     const T cs = p.cs, rdx = p.rdx, rdy = p.rdy;
+    const bool sphi = p.ys_phi != 0;
+    const T *R0 = p.ys[0];
+    // every cell is independent in this gather form, so the levels are split
+    // into chunks of kchunk, one chunk per blockIdx.z (parallel over i, j and k)
+    const int kbeg = blockIdx.z * p.kchunk;
+    const int kend = min(nz, kbeg + p.kchunk);
 
-    for (int k = 0; k < nz; k++) {
-        const long long kb = (long long)k * plane, skb = (long long)k * p.ys_plane;
-        const long long own = kb + ox[2];
+    for (int k = kbeg; k < kend; k++) {
+        const unsigned kb = (unsigned)k * plane, skb = (unsigned)k * ysp;
+        const unsigned own = kb + ox[2];
         // mass fluxes of the four faces per direction that touch cell c; face a+1/2 is stored at cell a
         T mxf[4], myf[4], mzf[4];
 #pragma unroll
@@ -57,85 +63,100 @@ __global__ void __launch_bounds__(128) adj_stage_kernel(const __grid_constant__ 
             mxf[q] = p.mu[kb + ox[q]];
             myf[q] = p.mv[kb + oy[q]];
             const int a = k + q - 2;
-            mzf[q] = (a >= 0 && a <= nz - 2) ? p.mw[(long long)(a + 1) * plane + ox[2]] : T(0);
+            mzf[q] = (a >= 0 && a <= nz - 2) ? p.mw[(unsigned)(a + 1) * plane + ox[2]] : T(0);
         }
-        const T rho = p.ys[0][skb + sx[2]];
+        // stencil cells of the cell's own +1/2 faces in the stage input
+        const unsigned zm1 = (unsigned)(k > 0 ? k - 1 : 0) * ysp + sx[2];
+        const unsigned zp1 = (unsigned)(k + 1 < nz ? k + 1 : nz - 1) * ysp + sx[2];
+        const unsigned zp2 = (unsigned)(k + 2 < nz ? k + 2 : nz - 1) * ysp + sx[2];
+        const T rho = R0[skb + sx[2]];
         const T rr = recip(rho);
+        // phi as the forward stage saw it: stored as phi in the padded stage
+        // buffers; as rho*phi in the caller layout, converted with 1/rho of each
+        // stencil cell (taken once per cell, shared by the fields)
+        T rx[4], ry[3], rz[3];
+        if (!sphi) {
+            rx[0] = recip(R0[skb + sx[1]]); rx[1] = rr; rx[2] = recip(R0[skb + sx[3]]); rx[3] = recip(R0[skb + sx[4]]);
+            ry[0] = recip(R0[skb + sy[1]]); ry[1] = recip(R0[skb + sy[3]]); ry[2] = recip(R0[skb + sy[4]]);
+            rz[0] = recip(R0[zm1]); rz[1] = recip(R0[zp1]); rz[2] = recip(R0[zp2]);
+        }
         T vrho = T(0);
         // --- density: no phi, only the gradient of M
-        T lf0x, lf0y, lf0z;
+        T gx, gy, gz;
         {
             const T m0 = p.lam[0][own], mxp = p.lam[0][kb + ox[3]], myp = p.lam[0][kb + oy[3]];
-            lf0x = cs * (mxp - m0) * rdx;
-            lf0y = cs * (myp - m0) * rdy;
-            lf0z = (k <= nz - 2) ? cs * (p.lam[0][own + plane] * p.rdz[k + 1] - m0 * p.rdz[k]) : T(0);
+            gx = cs * (mxp - m0) * rdx;
+            gy = cs * (myp - m0) * rdy;
+            gz = (k <= nz - 2) ? cs * (p.lam[0][own + plane] * p.rdz[k + 1] - m0 * p.rdz[k]) : T(0);
         }
-        T gx = lf0x, gy = lf0y, gz = lf0z;
         T vf[NT];
 #pragma unroll
         for (int f = 0; f < NT; f++) {
             const T *L = p.lam[f + 1];
-            const uint8_t *B = p.branch + (long long)f * nz * plane;
+            const uint8_t *B = p.branch + (size_t)f * nz * plane;
+            T lx[5], ly[5], lz[5];
+#pragma unroll
+            for (int q = 0; q < 5; q++) {
+                lx[q] = L[kb + ox[q]];
+                ly[q] = L[kb + oy[q]];
+                const int lev = k + q - 2;
+                lz[q] = (lev >= 0 && lev < nz) ? L[(unsigned)lev * plane + ox[2]] : T(0);
+            }
             T lphi = T(0);
             // i direction: faces a = i-2 .. i+1; cell c is stencil member 3, 2, 1, 0 of them
-            T lm[5];
-#pragma unroll
-            for (int q = 0; q < 5; q++) lm[q] = L[kb + ox[q]];
 #pragma unroll
             for (int q = 0; q < 4; q++) {
-                const T lF = cs * (lm[q + 1] - lm[q]) * rdx;
+                const T lF = cs * (lx[q + 1] - lx[q]) * rdx;
                 const int br = B[kb + ox[q]] & 3;
-                lphi += lF * mxf[q] * face_coef<T>(mxf[q] >= T(0), br, 3 - q);
+                lphi += lF * mxf[q] * ctab[(mxf[q] >= T(0) ? 16 : 0) + br * 4 + (3 - q)];
             }
             // j direction
 #pragma unroll
-            for (int q = 0; q < 5; q++) lm[q] = L[kb + oy[q]];
-#pragma unroll
             for (int q = 0; q < 4; q++) {
-                const T lF = cs * (lm[q + 1] - lm[q]) * rdy;
+                const T lF = cs * (ly[q + 1] - ly[q]) * rdy;
                 const int br = (B[kb + oy[q]] >> 2) & 3;
-                lphi += lF * myf[q] * face_coef<T>(myf[q] >= T(0), br, 3 - q);
+                lphi += lF * myf[q] * ctab[(myf[q] >= T(0) ? 16 : 0) + br * 4 + (3 - q)];
             }
-            // k direction: faces a = k-2 .. k+1 that exist; ghost levels fold into the boundary cell
+            // k direction: faces a = k-2 .. k+1 that exist; next to a lid the ghost
+            // levels fold several stencil members into the boundary cell
 #pragma unroll
             for (int q = 0; q < 4; q++) {
                 const int a = k + q - 2;
                 if (a < 0 || a > nz - 2) continue;
-                const T lF = cs * (L[(long long)(a + 1) * plane + ox[2]] * p.rdz[a + 1] -
-                                   L[(long long)a * plane + ox[2]] * p.rdz[a]);
-                const int br = (B[(long long)a * plane + ox[2]] >> 4) & 3;
-                const bool u = mzf[q] >= T(0);
-                T cf = T(0);
+                const T lF = cs * (lz[q + 1] * p.rdz[a + 1] - lz[q] * p.rdz[a]);
+                const int br = (B[(unsigned)a * plane + ox[2]] >> 4) & 3;
+                const T *ct = ctab + (mzf[q] >= T(0) ? 16 : 0) + br * 4;
+                T cf;
+                if (a >= 1 && a + 2 <= nz - 1) {
+                    cf = ct[3 - q];
+                } else {
+                    cf = T(0);
 #pragma unroll
-                for (int m = 0; m < 4; m++) {
-                    int cell = a + m - 1;
-                    cell = cell < 0 ? 0 : (cell > nz - 1 ? nz - 1 : cell);
-                    if (cell == k) cf += face_coef<T>(u, br, m);
+                    for (int m = 0; m < 4; m++) {
+                        int cell = a + m - 1;
+                        cell = cell < 0 ? 0 : (cell > nz - 1 ? nz - 1 : cell);
+                        if (cell == k) cf += ct[m];
+                    }
                 }
                 lphi += lF * mzf[q] * cf;
             }
             // gradient of M at the cell's own faces
             const T *Y = p.ys[f + 1];
-            const T *R0 = p.ys[0];
-            // phi as the forward stage saw it: stored as phi in the padded
-            // stage buffers, as rho*phi (converted with the reciprocal of rho) otherwise
-            const bool sphi = p.ys_phi != 0;
-            auto phi = [&](long long off) { return sphi ? Y[off] : Y[off] * recip(R0[off]); };
             const T ph = sphi ? Y[skb + sx[2]] : Y[skb + sx[2]] * rr;
             {
-                const T mx = mxf[2];
-                const T fx = face_val4<LIM>(phi(skb + sx[1]), ph, phi(skb + sx[3]), phi(skb + sx[4]), mx >= T(0));
-                gx += cs * (L[kb + ox[3]] - L[own]) * rdx * fx;
-                const T my = myf[2];
-                const T fy = face_val4<LIM>(phi(skb + sy[1]), ph, phi(skb + sy[3]), phi(skb + sy[4]), my >= T(0));
-                gy += cs * (L[kb + oy[3]] - L[own]) * rdy * fy;
+                const T fx = sphi ? face_val4<LIM>(Y[skb + sx[1]], ph, Y[skb + sx[3]], Y[skb + sx[4]], mxf[2] >= T(0))
+                                  : face_val4<LIM>(Y[skb + sx[1]] * rx[0], ph, Y[skb + sx[3]] * rx[2],
+                                                   Y[skb + sx[4]] * rx[3], mxf[2] >= T(0));
+                gx += cs * (lx[3] - lx[2]) * rdx * fx;
+                const T fy = sphi ? face_val4<LIM>(Y[skb + sy[1]], ph, Y[skb + sy[3]], Y[skb + sy[4]], myf[2] >= T(0))
+                                  : face_val4<LIM>(Y[skb + sy[1]] * ry[0], ph, Y[skb + sy[3]] * ry[1],
+                                                   Y[skb + sy[4]] * ry[2], myf[2] >= T(0));
+                gy += cs * (ly[3] - ly[2]) * rdy * fy;
                 if (k <= nz - 2) {
-                    const T mz = mzf[2];
-                    const long long km1 = (long long)(k > 0 ? k - 1 : 0) * p.ys_plane + sx[2];
-                    const long long kp1 = (long long)(k + 1) * p.ys_plane + sx[2];
-                    const long long kp2 = (long long)(k + 2 < nz ? k + 2 : nz - 1) * p.ys_plane + sx[2];
-                    const T fz = face_val4<LIM>(phi(km1), ph, phi(kp1), phi(kp2), mz >= T(0));
-                    gz += cs * (L[own + plane] * p.rdz[k + 1] - L[own] * p.rdz[k]) * fz;
+                    const T fz = sphi ? face_val4<LIM>(Y[zm1], ph, Y[zp1], Y[zp2], mzf[2] >= T(0))
+                                      : face_val4<LIM>(Y[zm1] * rz[0], ph, Y[zp1] * rz[1], Y[zp2] * rz[2],
+                                                       mzf[2] >= T(0));
+                    gz += cs * (lz[3] * p.rdz[k + 1] - lz[2] * p.rdz[k]) * fz;
                 }
             }
             vf[f] = lphi * rr;
@@ -175,147 +196,163 @@ __global__ void __launch_bounds__(128) adj_stage_kernel(const __grid_constant__ 
 //                               lambda_k = nu_k dz_k w_k,  w_k = 1/(dz_k + dt v);
 //   relaxation:  lambda_rho += lambda_rhotheta r theta_ref / (1 + r),
 //                lambda_rhotheta /= (1 + r).
-// Scratch per column and level: m, alpha, gamma, lambda_rho increment, and
-// phi and the elimination values e for every field.
+// A block takes 32 columns (the lanes) and one warp per field (rho*theta and
+// each tracer), so the fields' FP64 recurrences run in separate warps:
+//   A. warp 0 factorises the diffusion matrix of each column (m, alpha, gamma);
+//   B. the warp of field f recomputes its forward solve phi_f, runs the
+//      transposed solve, writes the field's adjoint and leaves its share of the
+//      lambda_rho increment per level in the scratch;
+//   C. the warps, dealt levels round-robin, add the shares to lambda_rho in
+//      field order (a fixed order, so the result does not depend on scheduling).
+// Scratch per column and level: m, alpha, gamma, then per field the
+// elimination value (reused for the field's lambda_rho share) and phi_f
+// (reused for the relaxation share of rho*theta).
 template <typename T, int NF>
-__global__ void __launch_bounds__(COL_TPB) adj_column_kernel(const __grid_constant__ AdjColParams<T> a) {
+__global__ void __launch_bounds__(32 * (NF - 1)) adj_column_kernel(const __grid_constant__ AdjColParams<T> a) {
     constexpr int NT = NF - 1;
-    constexpr int NQ = 4 + 2 * NT;
+    constexpr int NQ = 3 + 2 * NT;
     const ColumnParams<T> &p = a.c;
-    const long long ncol = p.plane, nslots = p.nslots, plane = p.plane;
-    const long long slot = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x, f = threadIdx.y;   // f: field f + 1 of the state
+    const long long plane = p.plane;
+    const long long nslots = (long long)gridDim.x * 32;
     const int nz = p.nz;
-    for (long long col = slot; col < ncol; col += nslots) {
-        double *sc = p.scratch + slot;
-        auto S = [&](int k, int q) -> double & { return sc[(long long)(k * NQ + q) * nslots]; };
-        // ---- forward: relaxation and sedimentation (in T), diffusion factorisation and solve (double)
-        double g_hi = 0.0, m_up = 0.0;
-        double e_up[NT];
-#pragma unroll
-        for (int f = 0; f < NT; f++) e_up[f] = 0.0;
-        T P = T(0);
-        for (int k = nz - 1; k >= 0; k--) {
-            const long long o = (long long)k * plane + col;
-            const T rho = p.y[0][o];
-            T x[NT];
-#pragma unroll
-            for (int f = 0; f < NT; f++) x[f] = p.y[f + 1][o];
-            if (p.do_relax) {
-                T th = x[0] / rho;
-                th = (th + p.relax_r * p.thref[k]) * p.relax_inv;
-                x[0] = rho * th;
-            }
-            if (p.do_sed) {
-#pragma unroll
-                for (int f = 1; f < NT; f++)
-                    if (f + 1 == p.sed) {
-                        x[f] = (x[f] * p.dzT[k] + p.sed_dt * P) * p.sedr[k];
-                        P = p.sed_v * x[f];
-                    }
-            }
-            if (p.do_diff) {
-                const double rd = to_f64(rho);
-                const double g_lo = (k > 0) ? p.kc[k - 1] * (to_f64(p.y[0][o - plane]) + rd) : 0.0;
+    double *const sc = p.scratch + (long long)blockIdx.x * 32 + lane;
+#define S(k, q) sc[(long long)((k) * NQ + (q)) * nslots]
+    const int qe = 3 + f, qp = 3 + NT + f;           // this field's elimination / share slot and phi slot
+    const bool is_th = f == 0, is_sed = p.do_sed && (f + 1 == p.sed);
+    const T *Y = p.y[f + 1];
+    const T *R = p.y[0];
+    T *lam = a.lam[f + 1];
+    const double sv = to_f64(p.sed_v), rr = to_f64(p.relax_r), ri = to_f64(p.relax_inv);
+
+    for (long long c0 = (long long)blockIdx.x * 32; c0 < plane; c0 += nslots) {
+        const long long col = c0 + lane;
+        const bool valid = col < plane;
+        __syncthreads();   // the previous group's phase C is done with the scratch
+        // ---- A: factorisation, top-down (warp 0)
+        if (p.do_diff && f == 0 && valid) {
+            double g_hi = 0.0, m_up = 0.0;
+            for (int k = nz - 1; k >= 0; k--) {
+                const long long o = (long long)k * plane + col;
+                const double rd = to_f64(R[o]);
+                const double g_lo = (k > 0) ? p.kc[k - 1] * (to_f64(R[o - plane]) + rd) : 0.0;
                 const double b = rd * p.dz[k] + (g_lo + g_hi);
                 const double t = g_hi * m_up;
                 const double m = rcp_newton(fma(-g_hi, t, b));
-                const double alpha = t * p.dzr_up[k];
                 S(k, 0) = m;
-                S(k, 1) = alpha;
+                S(k, 1) = t * p.dzr_up[k];
                 if (k < nz - 1) S(k + 1, 2) = g_hi * m * p.dzr_dn[k + 1];
-#pragma unroll
-                for (int f = 0; f < NT; f++) {
-                    const double e = fma(alpha, e_up[f], to_f64(x[f]));
-                    S(k, 4 + NT + f) = e;
-                    e_up[f] = e;
-                }
                 g_hi = g_lo;
                 m_up = m;
             }
         }
-        if (p.do_diff) {
-            double z[NT];
-#pragma unroll
-            for (int f = 0; f < NT; f++) z[f] = 0.0;
+        __syncthreads();
+        // ---- B: this warp's field
+        if (valid) {
+            if (p.do_diff) {
+                // forward: relaxation / sedimentation of the field, elimination top-down
+                double e_up = 0.0;
+                T P = T(0);
+                for (int k = nz - 1; k >= 0; k--) {
+                    const long long o = (long long)k * plane + col;
+                    T x = Y[o];
+                    if (is_th && p.do_relax) {
+                        const T rho = R[o];
+                        T th = x / rho;
+                        th = (th + p.relax_r * p.thref[k]) * p.relax_inv;
+                        x = rho * th;
+                    }
+                    if (is_sed) {
+                        x = (x * p.dzT[k] + p.sed_dt * P) * p.sedr[k];
+                        P = p.sed_v * x;
+                    }
+                    e_up = fma(S(k, 1), e_up, to_f64(x));
+                    S(k, qe) = e_up;
+                }
+                // back substitution bottom-up: phi_f
+                double z = 0.0;
+                for (int k = 0; k < nz; k++) {
+                    const double gk = k > 0 ? S(k, 2) : 0.0;
+                    z = fma(gk, z, S(k, qe));
+                    S(k, qp) = p.dz[k] * S(k, 0) * z;
+                }
+                // transpose of the diffusion: elimination top-down on rho lambda / dz
+                double eu = 0.0;
+                for (int k = nz - 1; k >= 0; k--) {
+                    const long long o = (long long)k * plane + col;
+                    const double rk = to_f64(R[o]) * p.rdz64[k];
+                    eu = fma(S(k, 1), eu, rk * to_f64(lam[o]));
+                    S(k, qe) = eu;
+                }
+            }
+            // bottom-up: transposed back substitution, the field's lambda_rho
+            // shares, then the sedimentation and relaxation transposes
+            double zp = 0.0, psi_prev = 0.0, phi_prev = 0.0, carry = 0.0, nu_prev = 0.0;
             for (int k = 0; k < nz; k++) {
-                const double gk = k > 0 ? S(k, 2) : 0.0, sk = p.dz[k] * S(k, 0);
-#pragma unroll
-                for (int f = 0; f < NT; f++) {
-                    z[f] = fma(gk, z[f], S(k, 4 + NT + f));
-                    S(k, 4 + f) = sk * z[f];          // phi_f,k
-                }
-                S(k, 3) = 0.0;                        // lambda_rho increment
-            }
-            // ---- transpose of the diffusion, every field in the same sweep over k
-            // (the fields' recurrences are independent, so their latencies overlap)
-            double eu[NT];
-#pragma unroll
-            for (int f = 0; f < NT; f++) eu[f] = 0.0;
-            for (int k = nz - 1; k >= 0; k--) {
                 const long long o = (long long)k * plane + col;
-                const double rk = to_f64(p.y[0][o]) * p.rdz64[k];   // rho_k / dz_k
-                const double al = S(k, 1);
-#pragma unroll
-                for (int f = 0; f < NT; f++) {
-                    eu[f] = fma(al, eu[f], rk * to_f64(a.lam[f + 1][o]));
-                    S(k, 4 + NT + f) = eu[f];
+                double lout;
+                bool write = false;
+                if (p.do_diff) {
+                    const double gk = k > 0 ? S(k, 2) : 0.0, kcl = k > 0 ? p.kc[k - 1] : 0.0;
+                    zp = fma(gk, zp, S(k, qe));
+                    const double psi = p.dz[k] * S(k, 0) * zp;
+                    const double ph = S(k, qp);
+                    const double lu = to_f64(lam[o]);
+                    const double A = (lu - p.dz[k] * psi) * ph;
+                    const double B = kcl * (psi - psi_prev) * (ph - phi_prev);   // face k-1/2
+                    // level k-1 takes A - B(k-1/2) - B(k+1/2); the last one now
+                    if (k > 0) S(k - 1, qe) = carry - B;
+                    carry = A - B;
+                    psi_prev = psi;
+                    phi_prev = ph;
+                    lout = to_f64(from_f64<T>(p.dz[k] * psi));
+                    write = true;
+                } else {
+                    lout = to_f64(lam[o]);
                 }
-            }
-            double zp[NT], psi_prev[NT], phi_prev[NT];
-#pragma unroll
-            for (int f = 0; f < NT; f++) zp[f] = psi_prev[f] = phi_prev[f] = 0.0;
-            double carry = 0.0;   // lambda_rho increment of level k-1 still to be stored
-            for (int k = 0; k < nz; k++) {
-                const long long o = (long long)k * plane + col;
-                const double gk = k > 0 ? S(k, 2) : 0.0, dmk = p.dz[k] * S(k, 0), kcl = k > 0 ? p.kc[k - 1] : 0.0;
-                double lr = 0.0, tsum = 0.0;
-#pragma unroll
-                for (int f = 0; f < NT; f++) {
-                    zp[f] = fma(gk, zp[f], S(k, 4 + NT + f));
-                    const double psi = dmk * zp[f];
-                    const double ph = S(k, 4 + f);
-                    const double lu = to_f64(a.lam[f + 1][o]);
-                    lr += (lu - p.dz[k] * psi) * ph;
-                    tsum += kcl * (psi - psi_prev[f]) * (ph - phi_prev[f]);
-                    a.lam[f + 1][o] = from_f64<T>(p.dz[k] * psi);
-                    psi_prev[f] = psi;
-                    phi_prev[f] = ph;
+                if (is_sed) {
+                    double nu = lout;
+                    if (k > 0) nu += p.dt * sv * to_f64(p.sedr[k - 1]) * nu_prev;
+                    nu_prev = nu;
+                    lout = to_f64(from_f64<T>(nu * p.dz[k] * to_f64(p.sedr[k])));
+                    write = true;
                 }
-                // the face k-1/2 term enters level k with a minus sign and level k-1 with a minus sign
-                if (k > 0) S(k - 1, 3) = carry - tsum;
-                carry = lr - tsum;
+                if (is_th && p.do_relax) {
+                    S(k, qp) = lout * rr * to_f64(p.thref[k]) * ri;   // relaxation share of lambda_rho
+                    lout = lout * ri;
+                    write = true;
+                }
+                if (write) lam[o] = from_f64<T>(lout);
             }
-            S(nz - 1, 3) = carry;
+            if (p.do_diff) S(nz - 1, qe) = carry;
         }
-        // ---- transpose of the sedimentation (bottom-up) and of the relaxation
-        double nu_prev = 0.0;
-        const double sv = to_f64(p.sed_v), rr = to_f64(p.relax_r), ri = to_f64(p.relax_inv);
-        for (int k = 0; k < nz; k++) {
-            const long long o = (long long)k * plane + col;
-            if (p.do_sed) {
-                double nu = to_f64(a.lam[p.sed][o]);
-                if (k > 0) nu += p.dt * sv * to_f64(p.sedr[k - 1]) * nu_prev;
-                nu_prev = nu;
-                a.lam[p.sed][o] = from_f64<T>(nu * p.dz[k] * to_f64(p.sedr[k]));
+        __syncthreads();
+        // ---- C: lambda_rho, levels dealt to the warps
+        if (valid) {
+            for (int k = f; k < nz; k += NT) {
+                const long long o = (long long)k * plane + col;
+                double lrho = to_f64(a.lam[0][o]);
+                if (p.do_diff) {
+                    double inc = 0.0;
+#pragma unroll
+                    for (int q = 0; q < NT; q++) inc += S(k, 3 + q);
+                    lrho += inc;
+                }
+                if (p.do_relax) lrho += S(k, 3 + NT);
+                a.lam[0][o] = from_f64<T>(lrho);
             }
-            double lrho = to_f64(a.lam[0][o]);
-            if (p.do_diff) lrho += S(k, 3);
-            if (p.do_relax) {
-                const double lt = to_f64(a.lam[1][o]);
-                lrho += lt * rr * to_f64(p.thref[k]) * ri;
-                a.lam[1][o] = from_f64<T>(lt * ri);
-            }
-            a.lam[0][o] = from_f64<T>(lrho);
         }
     }
 }
+#undef S
 
 // ------------------------------------------------------------------ launchers
 
 template <typename T, int NF, int LIM>
 static cudaError_t launch_adj_stage_lim(const AdjStageParams<T> &p, cudaStream_t s) {
+    if (p.kchunk < 1) return cudaErrorInvalidValue;
     dim3 block(32, 4);
-    dim3 grid((p.nx + 31) / 32, (p.ny + 3) / 4);
+    dim3 grid((p.nx + 31) / 32, (p.ny + 3) / 4, (p.nz + p.kchunk - 1) / p.kchunk);
     adj_stage_kernel<T, NF, LIM><<<grid, block, 0, s>>>(p);
     return cudaGetLastError();
 }
@@ -350,7 +387,7 @@ template <typename T>
 cudaError_t launch_adj_column(const AdjColParams<T> &p, int nf, int grid, cudaStream_t s) {
     switch (nf) {
 #define ASUCA_ADJ_COL_CASE(N) \
-        case N: adj_column_kernel<T, N><<<grid, COL_TPB, 0, s>>>(p); break;
+        case N: adj_column_kernel<T, N><<<grid, dim3(32, N - 1), 0, s>>>(p); break;
         ASUCA_ADJ_COL_CASE(2) ASUCA_ADJ_COL_CASE(3) ASUCA_ADJ_COL_CASE(4) ASUCA_ADJ_COL_CASE(5)
         ASUCA_ADJ_COL_CASE(6) ASUCA_ADJ_COL_CASE(7) ASUCA_ADJ_COL_CASE(8) ASUCA_ADJ_COL_CASE(9)
         ASUCA_ADJ_COL_CASE(10)

@@ -483,6 +483,23 @@ struct AdjLayout {
 
 int adj_col_grid(const asuca_grid *g) { return g->col_grid; }
 
+// Blocks of the column transpose: 32 columns each (one warp per field), at
+// most as many column slots as the scratch holds (adj_col_grid * COL_TPB).
+int adj_col_blocks(const asuca_grid *g) {
+    const long long need = (g->plane + 31) / 32, cap = (long long)adj_col_grid(g) * COL_TPB / 32;
+    return (int)(need < cap ? need : cap);
+}
+
+// Levels per thread of the stage transpose: enough level chunks that the
+// launch has at least 16 blocks of 128 threads per SM.
+int adj_stage_kchunk(const asuca_grid *g) {
+    const long long cols = (long long)((g->d.nx + 31) / 32) * ((g->d.ny + 3) / 4);
+    long long chunks = (16LL * g->nsm + cols - 1) / cols;
+    if (chunks > g->d.nz) chunks = g->d.nz;
+    if (chunks < 1) chunks = 1;
+    return (int)((g->d.nz + chunks - 1) / chunks);
+}
+
 AdjLayout adj_layout(const asuca_grid *g, int nsteps, int K) {
     AdjLayout L;
     const size_t s = elem_size(g);
@@ -655,7 +672,7 @@ asuca_status run_adjoint(asuca_grid *g, const asuca_state *init, const void *ten
             ac.c.scratch = (double *)(ws + L.scratch);
             ac.c.nslots = L.slots;
             for (int f = 0; f < MAXF; f++) ac.lam[f] = lam[f];
-            if (timed(g, ASUCA_KERNEL_ADJ_COLUMN, s, [&] { return launch_adj_column<T>(ac, F, adj_col_grid(g), s); }) !=
+            if (timed(g, ASUCA_KERNEL_ADJ_COLUMN, s, [&] { return launch_adj_column<T>(ac, F, adj_col_blocks(g), s); }) !=
                 cudaSuccess)
                 return ASUCA_ERR_CUDA;
             for (int stg = 2; stg >= 0; stg--) {
@@ -693,6 +710,7 @@ asuca_status run_adjoint(asuca_grid *g, const asuca_state *init, const void *ten
                 ap.nx = g->d.nx;
                 ap.ny = g->d.ny;
                 ap.nz = g->d.nz;
+                ap.kchunk = adj_stage_kchunk(g);
                 ap.plane = g->plane;
                 ap.rdx = (T)(1.0 / g->d.dx);
                 ap.rdy = (T)(1.0 / g->d.dy);
