@@ -176,6 +176,43 @@ def test_budgets_only_call(asuca):
     assert np.all(np.abs(bud.cpu().numpy() - rb) <= TOL64 * np.abs(rb) + 1e-300)
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_nan_in_host_input_reports_nonfinite(asuca, prec):
+    """Host-side fault injection: a NaN planted in the host copy of one tracer
+    reaches the device with the input, the budget reduction flags it, and the
+    next status read returns ASUCA_ERR_NONFINITE; the grid is usable after."""
+    import torch
+    c = gen.make_config_case("fp64_32x32x16")
+    c.rhoq = c.rhoq.copy()
+    c.rhoq[1, 3, 5, 7] = np.nan
+    g = asuca.Grid.from_case(c, prec=prec)
+    st = asuca.State.from_case(c, prec=prec)
+    asuca.step(g, st, c.dt, 1, budgets=True)
+    torch.cuda.synchronize()
+    assert asuca.get_status(g) == asuca.ERR_NONFINITE
+    assert asuca.get_status(g) == asuca.OK          # the word is cleared by the read
+    clean = asuca.State.from_case(gen.make_config_case("fp64_32x32x16"), prec=prec)
+    asuca.step(g, clean, c.dt, 1, budgets=True)
+    torch.cuda.synchronize()
+    assert asuca.get_status(g) == asuca.OK
+
+
+def test_short_or_misaligned_workspace_is_rejected(asuca):
+    import torch
+    c = gen.make_config_case("fp64_32x32x16")
+    g = asuca.Grid.from_case(c, prec=asuca.FP64)
+    st = asuca.State.from_case(c, prec=asuca.FP64)
+    need = g.workspace_bytes()
+    short = torch.empty(need - 256, dtype=torch.uint8, device=st.rho.device)
+    with pytest.raises(asuca.AsucaError) as e:
+        asuca.step(g, st, c.dt, 1, workspace=short)
+    assert e.value.status == asuca.ERR_WORKSPACE
+    big = torch.empty(need + 512, dtype=torch.uint8, device=st.rho.device)
+    with pytest.raises(asuca.AsucaError) as e:
+        asuca.step(g, st, c.dt, 1, workspace=big[8:8 + need])     # not 256-byte aligned
+    assert e.value.status == asuca.ERR_WORKSPACE
+
+
 # ------------------------------------------------------------------ precision workload, full size
 
 @pytest.fixture(scope="module")
