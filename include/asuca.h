@@ -213,7 +213,13 @@ typedef enum {
     ASUCA_TUNE_ENSEMBLE_TILE_ROWS = 3,  /* ensemble tile 32 x rows: 4 or 8 (default) for FP32; 8 for FP64 */
     ASUCA_TUNE_STEP_MODE = 4            /* asuca_step: 0 one launch per stage and column pass; 1 one persistent
                                            dataflow launch per 16 steps (tasks wait on per-tile counters, so the
-                                           FP64 column work overlaps the stencil stages); sizes the workspace */
+                                           FP64 column work overlaps the stencil stages); sizes the workspace */,
+    ASUCA_TUNE_FUSED_COLUMN = 5         /* asuca_step with step mode 0 and diffusion on: 1 (default) runs the third
+                                           stage marching downward together with the top-down half of the column
+                                           pass (relaxation, sedimentation, FP64 elimination), then a bottom-up
+                                           back-substitution kernel; 0 runs the stage and the column pass as two
+                                           launches.  Results are bit-identical; 1 adds an [nz][F+1][ny][nx]
+                                           double scratch to the workspace */
 } asuca_tune_key;
 asuca_status asuca_set_tuning(asuca_grid *grid, int key, int value);
 int asuca_get_tuning(const asuca_grid *grid, int key);
@@ -297,6 +303,8 @@ typedef enum {
     ASUCA_KERNEL_ADJ_COLUMN = 4,/* transpose of the column pass */
     ASUCA_KERNEL_ENSEMBLE = 5,  /* persistent ensemble kernel (all steps of a call) */
     ASUCA_KERNEL_DATAFLOW = 6,  /* persistent dataflow step kernel (up to 16 steps) */
+    ASUCA_KERNEL_STAGE_COLUMN = 7, /* third stage fused with the top-down column pass (its bottom-up half
+                                      is counted as ASUCA_KERNEL_COLUMN) */
     ASUCA_KERNEL_KINDS = 8
 } asuca_kernel_kind;
 

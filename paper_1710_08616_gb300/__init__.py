@@ -96,7 +96,9 @@ SIGNATURES = {
 }
 KERNEL_STAGE, KERNEL_COLUMN, KERNEL_REDUCE, KERNEL_ADJ_STAGE, KERNEL_ADJ_COLUMN, KERNEL_ENSEMBLE = 0, 1, 2, 3, 4, 5
 TUNE_COL_BLOCKS_PER_SM, TUNE_BARRIER_EXTRA, TUNE_STAGE_TILE_ROWS, TUNE_ENSEMBLE_TILE_ROWS, TUNE_STEP_MODE = 0, 1, 2, 3, 4
+TUNE_FUSED_COLUMN = 5
 KERNEL_DATAFLOW = 6
+KERNEL_STAGE_COLUMN = 7
 KERNEL_KINDS = 8
 
 

@@ -25,6 +25,7 @@ struct asuca_grid {
     int barrier_extra;            // test hook: extra arrivals the ensemble barrier waits for
     int stage_ty;                 // tile rows of the stage kernel (tuned; 8 for FP64)
     int step_mode;                // 0: one launch per stage and column pass; 1: persistent dataflow kernel
+    int fused_col;                // step mode 0: stage 3 fused with the top-down column pass (1) or not (0)
     int df_grid;                  // co-resident CTAs of the dataflow kernel (0 until queried)
     unsigned *df_order_host[2];   // pinned wave-order tables: a full chunk and the remainder chunk
     int df_order_q[2];
@@ -70,8 +71,16 @@ size_t elem_size(const asuca_grid *g) { return g->d.prec == ASUCA_FP64 ? 8 : 4; 
 long long col_slots(const asuca_grid *g) { return (long long)g->col_grid * COL_TPB; }
 
 struct StepLayout {
-    size_t ystar, ystar2, precip, partials, scratch, df_order, df_counter, df_flags, df_partials, df_scratch, total;
+    size_t ystar, ystar2, precip, partials, scratch, fscratch, df_order, df_counter, df_flags, df_partials, df_scratch,
+        total;
 };
+
+// the fused stage-3/column path is taken (step mode 0, diffusion on, not disabled)
+// (with 8-row stage tiles: the fused kernel is built for those, and the stage
+// buffers' tensor maps follow the tuned tile height)
+bool fused_path(const asuca_grid *g) {
+    return g->step_mode == 0 && g->fused_col && g->d.k0 > 0.0 && g->stage_ty == 8;
+}
 
 constexpr int DF_CHUNK = 16;   // steps per dataflow launch
 
@@ -97,6 +106,8 @@ StepLayout step_layout(const asuca_grid *g) {
     off = align_up(off + (size_t)g->col_grid * (g->F + 1) * sizeof(double));
     L.scratch = off;
     off = align_up(off + (size_t)g->d.nz * (g->F + 1) * col_slots(g) * sizeof(double));
+    L.fscratch = off;
+    if (fused_path(g)) off = align_up(off + (size_t)g->d.nz * (g->F + 1) * (size_t)g->plane * sizeof(double));
     L.df_order = L.df_counter = L.df_flags = L.df_partials = L.df_scratch = off;
     if (g->step_mode == 1) {
         const size_t R = (size_t)df_tiles_y(g), tiles = R * df_tiles_x(g);
@@ -317,8 +328,15 @@ asuca_status run_step(asuca_grid *g, asuca_state *st, const void *tend, double d
     const T cdt[3] = {(T)(dt / 3.0), (T)(dt / 2.0), (T)dt};
     for (int f = 0; f < MAXF; f++) sp.ybase[f] = yn[f];
     for (int q = 0; q < 3 && umaps; q++) sp.umap[q] = g->umap[q];
+    const bool fused = fused_path(g);
+    FusedParams<T> fp;
+    if (fused) {
+        fp.c = cp;
+        fp.c.scratch = (double *)(ws + L.fscratch);
+        fp.c.nslots = g->plane;
+    }
     for (int n = 0; n < nsteps; n++) {
-        for (int stg = 0; stg < 3; stg++) {
+        for (int stg = 0; stg < (fused ? 2 : 3); stg++) {
             // stage 1 reads the caller's fields (TMA for interior tiles, cp.async at the
             // periodic edges), stages 2 and 3 the padded buffers of phi the previous
             // stage wrote (TMA); stage 3 writes the caller's fields
@@ -337,8 +355,33 @@ asuca_status run_step(asuca_grid *g, asuca_state *st, const void *tend, double d
                 return ASUCA_ERR_CUDA;
         }
         cp.budgets = (budgets != nullptr) && (n == nsteps - 1);
-        if ((e = timed(g, ASUCA_KERNEL_COLUMN, s, [&] { return launch_column<T>(cp, F, g->col_grid, COL_TPB, s); })) != cudaSuccess)
+        if (fused) {
+            // stage 3 marching downward with the relaxation, sedimentation and
+            // elimination of every column, then the bottom-up back substitution
+            fp.s = sp;
+            fp.s.tma_in = 1;
+            fp.s.user_tma = 0;
+            fp.s.tmap = g->map_ystar2;
+            fp.s.out_padded = 0;
+            fp.s.ty = 8;
+            for (int f = 0; f < MAXF; f++) {
+                fp.s.yin[f] = yn[f];
+                fp.s.yout[f] = yn[f];
+            }
+            fp.s.cdt = cdt[2];
+            if ((e = timed(g, ASUCA_KERNEL_STAGE_COLUMN, s, [&] { return launch_stage3_column<T>(fp, F, s); })) !=
+                cudaSuccess)
+                return ASUCA_ERR_CUDA;
+            ColumnParams<T> cu = fp.c;
+            for (int f = 0; f < MAXF; f++) cu.y[f] = yn[f];
+            cu.budgets = cp.budgets;
+            if ((e = timed(g, ASUCA_KERNEL_COLUMN, s, [&] { return launch_column_up<T>(cu, F, g->col_grid, s); })) !=
+                cudaSuccess)
+                return ASUCA_ERR_CUDA;
+        } else if ((e = timed(g, ASUCA_KERNEL_COLUMN, s,
+                              [&] { return launch_column<T>(cp, F, g->col_grid, COL_TPB, s); })) != cudaSuccess) {
             return ASUCA_ERR_CUDA;
+        }
     }
     if (budgets) {
         if (nsteps == 0) {
@@ -1053,6 +1096,7 @@ asuca_status asuca_init_grid(const asuca_grid_desc *desc, asuca_grid **out) {
     g->stage_ty = 8;
     g->ens_ty = 8;
     g->step_mode = 0;
+    g->fused_col = 1;
     set_col_grid(g);
     void *h = nullptr;
     if (cudaHostAlloc(&h, 64, cudaHostAllocMapped) != cudaSuccess) {
@@ -1322,6 +1366,10 @@ asuca_status asuca_set_tuning(asuca_grid *g, int key, int value) {
             if (value != 0 && value != 1) return ASUCA_ERR_ARG;
             g->step_mode = value;
             return ASUCA_OK;
+        case ASUCA_TUNE_FUSED_COLUMN:
+            if (value != 0 && value != 1) return ASUCA_ERR_ARG;
+            g->fused_col = value;
+            return ASUCA_OK;
         default: return ASUCA_ERR_ARG;
     }
 }
@@ -1334,6 +1382,7 @@ int asuca_get_tuning(const asuca_grid *g, int key) {
         case ASUCA_TUNE_STAGE_TILE_ROWS: return g->stage_ty;
         case ASUCA_TUNE_ENSEMBLE_TILE_ROWS: return g->ens_ty;
         case ASUCA_TUNE_STEP_MODE: return g->step_mode;
+        case ASUCA_TUNE_FUSED_COLUMN: return g->fused_col;
         default: return -1;
     }
 }

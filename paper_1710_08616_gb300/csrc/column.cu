@@ -41,6 +41,85 @@ __global__ void __launch_bounds__(COL_TPB, 3) column_kernel(const __grid_constan
     }
 }
 
+// The bottom-up half of the column pass after ColDownHook: back substitution
+// from the full-size scratch ([nz][F + 1][plane]), (rho phi)_k = sigma_k z_k
+// for rho*theta and every tracer (column_one's bottom-up pass, operation for
+// operation), and the column budget partials.  Grid-stride over columns,
+// one thread per column.
+template <typename T, int NF>
+__global__ void __launch_bounds__(COL_TPB, 3) column_up_kernel(const __grid_constant__ ColumnParams<T> p) {
+    constexpr int NT = NF - 1;
+    constexpr int NQ = NF + 1;
+    const long long ncol = p.plane;
+    const size_t pl = (size_t)p.plane;
+    const int nz = p.nz;
+    double bsum[NF + 1];
+#pragma unroll
+    for (int q = 0; q <= NF; q++) bsum[q] = 0.0;
+
+    for (long long col = (long long)blockIdx.x * blockDim.x + threadIdx.x; col < ncol;
+         col += (long long)gridDim.x * blockDim.x) {
+        ColSum<T> cs[NF];
+        const double *sc = p.scratch + col;
+        double z[NT];
+#pragma unroll
+        for (int f = 0; f < NT; f++) z[f] = 0.0;
+        size_t ob = (size_t)col;
+        double mk = sc[0], gk = 0.0;
+        double ek[NT];
+#pragma unroll
+        for (int f = 0; f < NT; f++) ek[f] = sc[(size_t)(2 + f) * pl];
+        T rk = p.y[0][ob];
+        for (int k = 0; k < nz; k++, ob += pl) {
+            double mn = 0.0, gn = 0.0, en[NT];
+            T rn = T(0);
+            if (k + 1 < nz) {   // prefetch level k+1
+                mn = sc[(size_t)((k + 1) * NQ + 0) * pl];
+                gn = sc[(size_t)((k + 1) * NQ + 1) * pl];
+#pragma unroll
+                for (int f = 0; f < NT; f++) en[f] = sc[(size_t)((k + 1) * NQ + 2 + f) * pl];
+                rn = p.y[0][ob + pl];
+            }
+            const double sigma = to_f64(rk) * p.dz[k] * mk;
+            const float sf = (sizeof(T) == 4) ? (float)rk * (float)p.dzT[k] * d2f_bits(mk) : 0.f;
+            if (p.budgets) cs[0].add(rk, p.dz[k], p.dzT[k], p.dzlo[k]);
+#pragma unroll
+            for (int f = 0; f < NT; f++) {
+                z[f] = fma(gk, z[f], ek[f]);
+                const T u = scale_out<T>(z[f], sigma, sf);
+                p.y[f + 1][ob] = u;
+                if (p.budgets) cs[f + 1].add(u, p.dz[k], p.dzT[k], p.dzlo[k]);
+            }
+            if (k + 1 < nz) {
+                mk = mn;
+                gk = gn;
+#pragma unroll
+                for (int f = 0; f < NT; f++) ek[f] = en[f];
+                rk = rn;
+            }
+        }
+        if (p.budgets) {
+#pragma unroll
+            for (int f = 0; f < NF; f++) bsum[f] += cs[f].value();
+            if (p.precip_col) bsum[NF] += p.precip_col[col];
+        }
+    }
+
+    if (!p.budgets) return;
+    __shared__ double red[COL_TPB];
+#pragma unroll
+    for (int q = 0; q <= NF; q++) {
+        red[threadIdx.x] = bsum[q];
+        __syncthreads();
+        for (int s = COL_TPB / 2; s > 0; s >>= 1) {
+            if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) p.partials[(long long)blockIdx.x * (NF + 1) + q] = red[0];
+        __syncthreads();
+    }
+}
+
 // Sum the block partials in a fixed order, scale the field sums by dx*dy,
 // and flag a non-finite result in the status word.
 __global__ void budget_reduce_kernel(const double *partials, int nblocks, int nq, int nf,
@@ -96,6 +175,22 @@ cudaError_t launch_column(const ColumnParams<T> &p, int nf, int grid, int block,
     return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_column_up(const ColumnParams<T> &p, int nf, int grid, cudaStream_t s) {
+    switch (nf) {
+#define ASUCA_COLUP_CASE(N) \
+        case N: column_up_kernel<T, N><<<grid, COL_TPB, 0, s>>>(p); break;
+        ASUCA_COLUP_CASE(2) ASUCA_COLUP_CASE(3) ASUCA_COLUP_CASE(4) ASUCA_COLUP_CASE(5)
+        ASUCA_COLUP_CASE(6) ASUCA_COLUP_CASE(7) ASUCA_COLUP_CASE(8) ASUCA_COLUP_CASE(9)
+        ASUCA_COLUP_CASE(10)
+#undef ASUCA_COLUP_CASE
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_column_up<float>(const ColumnParams<float> &, int, int, cudaStream_t);
+template cudaError_t launch_column_up<double>(const ColumnParams<double> &, int, int, cudaStream_t);
 template cudaError_t launch_column<float>(const ColumnParams<float> &, int, int, int, cudaStream_t);
 template cudaError_t launch_column<double>(const ColumnParams<double> &, int, int, int, cudaStream_t);
 

@@ -207,3 +207,88 @@ __device__ __forceinline__ void column_one(const ColumnParams<T> &p, long long c
 }
 
 }  // namespace asuca
+
+namespace asuca {
+
+// ------------------------------------------------------------------ column pass fused into stage 3
+
+// The top-down half of the column pass, run by the thread that computes the
+// column in the third RK stage while that stage marches downward: each level's
+// stage result goes through relaxation and sedimentation and into the
+// elimination (column_one's top-down pass, operation for operation), and the
+// per-level values m, gamma, e_f go to a scratch laid out [nz][F + 1][plane]
+// (entry (k, q) of column col at (k (F + 1) + q) plane + col), for
+// column_up_kernel's bottom-up back substitution.  The density result is
+// written to the state here; rho*theta and the tracers are written by the back
+// substitution.  The elimination of level k needs rho of level k - 1, which
+// the stage hands over as rho_next.
+template <typename T, int NF>
+struct ColDownHook {
+    static constexpr bool active = true;
+    static constexpr int NT = NF - 1;
+    static constexpr int NQ = NF + 1;   // m, gamma, e[NT]
+    const ColumnParams<T> &c;
+    T *rho_out;
+    double *sc;
+    size_t pl;
+    unsigned own;
+    double g_hi, m_up;
+    double e_up[NT];
+    T P;
+
+    __device__ __forceinline__ ColDownHook(const ColumnParams<T> &cp, T *rho, unsigned own_)
+        : c(cp), rho_out(rho), sc(cp.scratch + own_), pl((size_t)cp.plane), own(own_), g_hi(0.0), m_up(0.0), P(T(0)) {
+#pragma unroll
+        for (int f = 0; f < NT; f++) e_up[f] = 0.0;
+    }
+
+    template <typename U, int NF2>
+    __device__ __forceinline__ void level(int k, const U (&out)[NF2], bool valid, U rho_next) {
+        static_assert(NF2 == NF, "field count");
+        if (!valid) return;
+        const T rho = out[0];
+        rho_out[(size_t)k * pl + own] = rho;
+        T x[NT];
+#pragma unroll
+        for (int f = 0; f < NT; f++) x[f] = out[f + 1];
+        // (i) relaxation of theta
+        if (c.do_relax) {
+            T th = x[0] / rho;
+            th = (th + c.relax_r * c.thref[k]) * c.relax_inv;
+            x[0] = rho * th;
+        }
+        // (ii) sedimentation of one tracer, top-down
+        if (c.do_sed) {
+#pragma unroll
+            for (int f = 1; f < NT; f++) {
+                if (f + 1 == c.sed) {
+                    x[f] = (x[f] * c.dzT[k] + c.sed_dt * P) * c.sedr[k];
+                    P = c.sed_v * x[f];
+                }
+            }
+            if (k == 0) c.precip_col[own] += c.dt * to_f64(P) * c.dxdy;
+        }
+        // (iii) forward elimination on scaled unknowns
+        const double rd = to_f64(rho);
+        const double rd_dn = (k > 0) ? to_f64(rho_next) : 0.0;
+        const double g_lo = (k > 0) ? c.kc[k - 1] * (rd_dn + rd) : 0.0;
+        const double rdz = rd * c.dz[k];
+        const double b = rdz + (g_lo + g_hi);
+        const double t = g_hi * m_up;
+        const double m = rcp_newton(fma(-g_hi, t, b));
+        const double alpha = t * c.dzr_up[k];
+        sc[(size_t)(k * NQ + 0) * pl] = m;
+        if (k < c.nz - 1) sc[(size_t)((k + 1) * NQ + 1) * pl] = g_hi * m * c.dzr_dn[k + 1];
+#pragma unroll
+        for (int f = 0; f < NT; f++) {
+            const double e = fma(alpha, e_up[f], to_f64(x[f]));
+            sc[(size_t)(k * NQ + 2 + f) * pl] = e;
+            e_up[f] = e;
+        }
+        g_hi = g_lo;
+        m_up = m;
+    }
+    __device__ __forceinline__ void done(bool) {}
+};
+
+}  // namespace asuca

@@ -296,6 +296,18 @@ cudaError_t launch_stage_ty(const StageParams<T> &p, int nf, cudaStream_t s);
 template <typename T>
 cudaError_t launch_column(const ColumnParams<T> &p, int nf, int grid, int block, cudaStream_t s);
 
+// Stage 3 with the top-down half of the column pass (downward march), and
+// the bottom-up half (fused_impl.cuh, column.cu).
+template <typename T>
+struct FusedParams {
+    StageParams<T> s;       // stage 3: padded phi input (TMA), unpadded output
+    ColumnParams<T> c;      // column constants; scratch is the full-size [nz][F + 1][plane] area
+};
+template <typename T>
+cudaError_t launch_stage3_column(const FusedParams<T> &p, int nf, cudaStream_t s);
+template <typename T>
+cudaError_t launch_column_up(const ColumnParams<T> &p, int nf, int grid, cudaStream_t s);
+
 cudaError_t launch_budget_reduce(const double *partials, int nblocks, int nq, int nf,
                                  double dxdy, double *out, int *status, cudaStream_t s);
 

@@ -115,9 +115,25 @@ __device__ __forceinline__ void cp_async_wait() {
 // wait limit (the status word has been set).  The caller's CTA owns smem_raw;
 // the function begins and ends with a CTA-wide barrier, so consecutive tiles
 // may reuse the same shared memory and mbarriers.
-template <typename T, int NF, int LIM, bool REC, int TYV = 8>
-__device__ __forceinline__ bool stage_tile(const StageParams<T> &p, const CUtensorMap *tmap, int i0, int j0,
-                                           unsigned char *smem_raw) {
+// The default output of a tile: the stage result is written to p.yout.
+struct NoHook {
+    static constexpr bool active = false;
+    template <typename T, int NF>
+    __device__ __forceinline__ void level(int, const T (&)[NF], bool, T) {}
+    __device__ __forceinline__ void done(bool) {}
+};
+
+// DOWN marches the levels from the top down (the ring, the faces and the
+// carried flux all run in march order; level k = nz - 1 - t at march step t),
+// which gives the same arithmetic per cell, so the result is bit-identical to
+// the upward march.  An active Hook takes each level's result instead of the
+// writes to p.yout: hook.level(k, out, valid, rho_next), where rho_next is the
+// density result of the next level of the march (the same expression that
+// level will evaluate), then hook.done(valid) after the last level.
+template <typename T, int NF, int LIM, bool REC, int TYV, bool DOWN, typename Hook>
+__device__ __forceinline__ bool stage_tile_h(const StageParams<T> &p, const CUtensorMap *tmap, int i0, int j0,
+                                             unsigned char *smem_raw, Hook &hook) {
+    static_assert(!(DOWN && REC), "branch recording marches upward");
     using S = StageShape<T, NF, TYV>;
     constexpr int TX = S::TX, TY = S::TY, D = S::D, SX = S::SX, SY = S::SY, NT = S::NT;
     constexpr int NTHR = TX * TY;
@@ -186,13 +202,15 @@ __device__ __forceinline__ bool stage_tile(const StageParams<T> &p, const CUtens
     auto slot = [&](int lev) -> T * { return ring + (size_t)(lev % D) * S::SLOT_ELEMS; };
 
     int issued = 0, seen = 0;   // TMA levels [0, issued) requested, [0, seen) seen complete
-    auto issue = [&](int lev) {
+    auto level_of = [&](int t) { return DOWN ? nz - 1 - t : t; };
+    auto issue = [&](int t) {
+        const int lev = level_of(t);
         if (tma) {
-            if (lev < nz) {
-                issued = lev + 1;
+            if (t < nz) {
+                issued = t + 1;
                 if (tid == 0) {
-                    uint64_t *bar = &bars[lev % D];
-                    T *dst = slot(lev);
+                    uint64_t *bar = &bars[t % D];
+                    T *dst = slot(t);
                     mbar_expect_tx(bar, S::TX_BYTES);
                     if (pad_in) {
                         tma_load_4d(dst, tmap, i0, j0, lev, 0, bar);
@@ -204,8 +222,8 @@ __device__ __forceinline__ bool stage_tile(const StageParams<T> &p, const CUtens
                 }
             }
         } else {
-            if (lev < nz) {
-                T *sl = slot(lev);
+            if (t < nz) {
+                T *sl = slot(t);
                 const unsigned lb = (unsigned)lev * plane;
 #pragma unroll
                 for (int q = 0; q < MAXC; q++) {
@@ -270,22 +288,26 @@ __device__ __forceinline__ bool stage_tile(const StageParams<T> &p, const CUtens
     for (int f = 0; f < NF; f++) zlo[f] = T(0);
 
     // per-level mass fluxes, requested one level ahead (the faces need them first)
+    // mwp is the flux through the face the march reaches next: k+1/2 upward
+    // (mw[k + 1]), k-1/2 downward (mw[k]); zero at the lid
     T mup, mum, mvp, mvm, mwp, meb, mel;
-    T nmup, nmum, nmvp, nmvm, nmwp, nmeb, nmel;
+    T nmup, nmum, nmvp, nmvm, nmwp, nmeb, nmel, nrho;
     auto prefetch = [&](int k) {
         const unsigned kb = (unsigned)k * plane;
         nmup = p.mu[kb + own];
         nmum = p.mu[kb + left];
         nmvp = p.mv[kb + own];
         nmvm = p.mv[kb + down];
-        nmwp = (k < nz - 1) ? p.mw[kb + plane + own] : T(0);
+        if (DOWN) nmwp = (k > 0) ? p.mw[kb + own] : T(0);
+        else nmwp = (k < nz - 1) ? p.mw[kb + plane + own] : T(0);
         nmeb = p.mv[kb + edge_b];
         nmel = p.mu[kb + edge_l];
+        if (Hook::active) nrho = p.ybase[0][kb + own];
     };
     auto advance = [&]() {
         mup = nmup; mum = nmum; mvp = nmvp; mvm = nmvm; mwp = nmwp; meb = nmeb; mel = nmel;
     };
-    prefetch(0);
+    prefetch(level_of(0));
     advance();
 
     const int cy = ty + 2, cx = tx + 4, cc = cy * SX + cx;
@@ -293,19 +315,23 @@ __device__ __forceinline__ bool stage_tile(const StageParams<T> &p, const CUtens
     constexpr bool PACK = std::is_same<T, float>::value && !REC;
 
 #pragma unroll 1
-    for (int k = 0; k < nz; k++) {
-        // ---- level k+2 must be resident (and hold phi) before anyone computes level k
-        if (k + 2 < nz) {
+    for (int t = 0; t < nz; t++) {
+        const int k = level_of(t);
+        // ---- march step t+2 must be resident (and hold phi) before anyone computes step t
+        if (t + 2 < nz) {
             if (tma) {
-                if (!arrive(k + 2)) timed_out = true;
+                if (!arrive(t + 2)) timed_out = true;
             } else {
                 cp_async_wait<(D >= 5 ? D - 5 : 0)>();
-                convert(k + 2);
+                convert(t + 2);
             }
         }
         if (tma) fence_proxy_async();
-        if (__syncthreads_or(timed_out)) break;
-        issue(k + D - 2);   // into the slot of level k-2, which nobody reads any more
+        if (__syncthreads_or(timed_out)) {
+            timed_out = true;
+            break;
+        }
+        issue(t + D - 2);   // into the slot of march step t-2, which nobody reads any more
         // Y^n of this level: used after the faces, which cover the load latency
         T yb[NF];
         {
@@ -313,15 +339,18 @@ __device__ __forceinline__ bool stage_tile(const StageParams<T> &p, const CUtens
 #pragma unroll
             for (int f = 0; f < NF; f++) yb[f] = p.ybase[f][kb];
         }
-        if (k + 1 < nz) prefetch(k + 1);
+        if (t + 1 < nz) prefetch(level_of(t + 1));
 
         // ---- faces: upwind cell c, downwind cell o and far upwind cell by address
-        const T *Sk = slot(k);
-        const T *Skm = slot(k > 0 ? k - 1 : 0);
-        const T *Skp = slot(k + 1 < nz ? k + 1 : nz - 1);
-        const T *Skp2 = slot(k + 2 < nz ? k + 2 : nz - 1);
-        const bool top = (k == nz - 1);
-        const bool ux = mup >= T(0), uy = mvp >= T(0), uz = mwp >= T(0);
+        // march steps t-1 .. t+2 (ghost levels copy the boundary cell)
+        const T *Sk = slot(t);
+        const T *Skm = slot(t > 0 ? t - 1 : 0);
+        const T *Skp = slot(t + 1 < nz ? t + 1 : nz - 1);
+        const T *Skp2 = slot(t + 2 < nz ? t + 2 : nz - 1);
+        const bool top = (t == nz - 1);   // no face ahead of the last step
+        // upwind cell of the face ahead: step t when the flux points along the
+        // march (upward march: M >= 0; downward: M < 0, since M = 0 counts as upward)
+        const bool ux = mup >= T(0), uy = mvp >= T(0), uz = DOWN ? (mwp < T(0)) : (mwp >= T(0));
         const int xc = cc + (ux ? 0 : 1), xo = cc + (ux ? 1 : 0), xf = cc + (ux ? -1 : 2);
         const int yc = cc + (uy ? 0 : SX), yo = cc + (uy ? SX : 0), yf = cc + (uy ? -SX : 2 * SX);
         const T *zc = (uz ? Sk : Skp) + cc, *zo = (uz ? Skp : Sk) + cc, *zf = (uz ? Skm : Skp2) + cc;
@@ -401,7 +430,9 @@ __device__ __forceinline__ bool stage_tile(const StageParams<T> &p, const CUtens
         // each step one FMA on an exact difference
         const T az = -cdt * p.rdz[k];
         T out[NF];
-        out[0] = fma(az, mwp - zlo[0], fma(ay, mvp - mvm, fma(ax, mup - mum, yb[0])));
+        // z flux difference F(k+1/2) - F(k-1/2): ahead minus carried upward,
+        // carried minus ahead downward (the same operands either way)
+        out[0] = fma(az, DOWN ? zlo[0] - mwp : mwp - zlo[0], fma(ay, mvp - mvm, fma(ax, mup - mum, yb[0])));
         zlo[0] = mwp;
         T xm[NT], ym[NT];
 #pragma unroll
@@ -418,25 +449,37 @@ __device__ __forceinline__ bool stage_tile(const StageParams<T> &p, const CUtens
                 float2 o = __ffma2_rn(ax2, __ffma2_rn(make_float2(xm[f], xm[f + 1]), neg1, make_float2(xp[f], xp[f + 1])),
                                       make_float2(yb[f + 1], yb[f + 2]));
                 o = __ffma2_rn(ay2, __ffma2_rn(make_float2(ym[f], ym[f + 1]), neg1, make_float2(yp[f], yp[f + 1])), o);
-                o = __ffma2_rn(az2, __ffma2_rn(make_float2(zlo[f + 1], zlo[f + 2]), neg1, make_float2(zp[f], zp[f + 1])), o);
+                o = DOWN ? __ffma2_rn(az2, __ffma2_rn(make_float2(zp[f], zp[f + 1]), neg1, make_float2(zlo[f + 1], zlo[f + 2])), o)
+                         : __ffma2_rn(az2, __ffma2_rn(make_float2(zlo[f + 1], zlo[f + 2]), neg1, make_float2(zp[f], zp[f + 1])), o);
                 out[f + 1] = o.x;
                 out[f + 2] = o.y;
             }
             if (NT & 1) {
                 constexpr int f = NT - 1;
-                out[f + 1] = fma(az, zp[f] - zlo[f + 1], fma(ay, yp[f] - ym[f], fma(ax, xp[f] - xm[f], yb[f + 1])));
+                out[f + 1] = fma(az, DOWN ? zlo[f + 1] - zp[f] : zp[f] - zlo[f + 1],
+                                 fma(ay, yp[f] - ym[f], fma(ax, xp[f] - xm[f], yb[f + 1])));
             }
         } else {
 #pragma unroll
             for (int f = 0; f < NT; f++)
-                out[f + 1] = fma(az, zp[f] - zlo[f + 1], fma(ay, yp[f] - ym[f], fma(ax, xp[f] - xm[f], yb[f + 1])));
+                out[f + 1] = fma(az, DOWN ? zlo[f + 1] - zp[f] : zp[f] - zlo[f + 1],
+                                 fma(ay, yp[f] - ym[f], fma(ax, xp[f] - xm[f], yb[f + 1])));
         }
 #pragma unroll
         for (int f = 0; f < NT; f++) {
             if (p.tend) out[f + 1] = fma(cdt, p.tend[(long long)f * nz * plane + (unsigned)k * plane + own], out[f + 1]);
             zlo[f + 1] = zp[f];
         }
-        if (valid) {
+        if (Hook::active) {
+            // the density result of the next march step, evaluated as that step will
+            T rho_next = T(0);
+            if (t + 1 < nz) {
+                const T az_n = -cdt * p.rdz[level_of(t + 1)];
+                rho_next = fma(az_n, DOWN ? mwp - nmwp : nmwp - mwp,
+                               fma(ay, nmvp - nmvm, fma(ax, nmup - nmum, nrho)));
+            }
+            hook.template level<T, NF>(k, out, valid, rho_next);
+        } else if (valid) {
             if (p.out_padded) {
                 // the next stage reads phi = (rho phi) / rho
                 const T r = recip(out[0]);
@@ -461,8 +504,9 @@ __device__ __forceinline__ bool stage_tile(const StageParams<T> &p, const CUtens
                 for (int f = 0; f < NF; f++) p.yout[f][o] = out[f];
             }
         }
-        if (k + 1 < nz) advance();
+        if (t + 1 < nz) advance();
     }
+    if (Hook::active && !timed_out) hook.done(valid);
 
     if (timed_out) {
         if (tid == 0 && p.status) atomicCAS(p.status, 0, (int)ASUCA_ERR_TIMEOUT);
@@ -475,6 +519,13 @@ __device__ __forceinline__ bool stage_tile(const StageParams<T> &p, const CUtens
     if (!tma) cp_async_wait<0>();
     __syncthreads();
     return timed_out;
+}
+
+template <typename T, int NF, int LIM, bool REC, int TYV = 8>
+__device__ __forceinline__ bool stage_tile(const StageParams<T> &p, const CUtensorMap *tmap, int i0, int j0,
+                                           unsigned char *smem_raw) {
+    NoHook h;
+    return stage_tile_h<T, NF, LIM, REC, TYV, false, NoHook>(p, tmap, i0, j0, smem_raw, h);
 }
 
 template <typename T, int NF, int LIM, bool REC, int TYV>
