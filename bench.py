@@ -244,9 +244,12 @@ def adjoint_cost(asuca, dev, reps=3):
     case = gen.make_config_case("adjoint_128x128x58")
     nsteps, K = gen.CONFIGS["adjoint_128x128x58"]["nsteps"], 10
     out = {"workload": "adjoint_128x128x58", "nsteps": nsteps, "checkpoint_every": K}
+    from paper_1710_08616_gb300 import autotune
     for name, prec in (("fp64", asuca.FP64), ("fp32", asuca.FP32_MIXED)):
         g = asuca.Grid.from_case(case, prec=prec)
         st0 = asuca.State.from_case(case, prec=prec, device=dev)
+        # the forward it is compared with runs in its fastest launch configuration
+        tuned = autotune.tune_step(g, st0, case.dt, steps=2, reps=2, save=False)["best"]
         ws = g.workspace(device=dev)
         nadj = asuca.adjoint_workspace_bytes(g, nsteps, K)
         wsa = torch.empty(nadj, dtype=torch.uint8, device=dev)
@@ -297,7 +300,7 @@ def adjoint_cost(asuca, dev, reps=3):
         ta = min(timed(alone) for _ in range(reps))
         assert asuca.get_status(g) == asuca.OK
         names = {0: "stage", 1: "column", 2: "budget_reduce", 3: "adj_stage", 4: "adj_column"}
-        out[name] = {"forward_ms": tf, "forward_checkpointed_ms": tfc, "backward_ms": tb,
+        out[name] = {"forward_config": tuned, "forward_ms": tf, "forward_checkpointed_ms": tfc, "backward_ms": tb,
                      "adjoint_over_forward": tb / tf,
                      "forward_plus_backward_over_forward": (tfc + tb) / tf,
                      "standalone_adjoint_step_ms": ta, "standalone_over_forward": ta / tf,
@@ -444,12 +447,24 @@ def run_ours(args):
     # ---- roofline of the dominant kernel, from the live per-kernel events
     hbm_peak, peak_kind = _peaks()
     s = 4
-    kinds = {asuca.KERNEL_STAGE: "stage", asuca.KERNEL_COLUMN: "column", asuca.KERNEL_REDUCE: "budget_reduce"}
-    # algorithmic bytes per launch (values per cell): stage 1 reads Yn and M, writes Y*;
-    # stages 2 and 3 read Y^(s-1), Yn and M and write; the column pass reads F and writes F-1.
-    algo = {asuca.KERNEL_STAGE: ((2 * F + 3) + 2 * (3 * F + 3)) / 3.0 * C * s,
-            asuca.KERNEL_COLUMN: (2 * F - 1) * C * s,
-            asuca.KERNEL_REDUCE: 0.0}
+    kinds = {asuca.KERNEL_STAGE: "stage", asuca.KERNEL_COLUMN: "column", asuca.KERNEL_REDUCE: "budget_reduce",
+             asuca.KERNEL_STAGE_COLUMN: "stage3_column"}
+    fused = asuca.get_tuning(g, asuca.TUNE_FUSED_COLUMN) == 1
+    # algorithmic bytes per launch.  Stage 1 reads Yn and M and writes Y* (2F+3 values);
+    # stage 2 reads Y*, Yn and M and writes Y** (3F+3).  With the fused path, stage 3
+    # with the top-down column pass reads Y**, Yn and M and writes rho plus the
+    # elimination values (m, gamma, e_f: F+1 doubles), and the bottom-up pass reads
+    # those and rho and writes the F-1 other fields; without it, stage 3 is a stage
+    # launch (3F+3) and the column pass reads F and writes F-1 values.
+    if fused:
+        algo = {asuca.KERNEL_STAGE: ((2 * F + 3) + (3 * F + 3)) / 2.0 * C * s,
+                asuca.KERNEL_STAGE_COLUMN: ((2 * F + 3 + 1) * s + (F + 1) * 8) * C,
+                asuca.KERNEL_COLUMN: ((F + 1) * 8 + F * s) * C,
+                asuca.KERNEL_REDUCE: 0.0}
+    else:
+        algo = {asuca.KERNEL_STAGE: ((2 * F + 3) + 2 * (3 * F + 3)) / 3.0 * C * s,
+                asuca.KERNEL_COLUMN: (2 * F - 1) * C * s,
+                asuca.KERNEL_REDUCE: 0.0}
     kern = {}
     for k, (tot, n) in (prof or {}).items():
         avg = tot / n
@@ -539,7 +554,7 @@ def run_ours(args):
                           "precision": "fp32 fields/stencils/physics, fp64 Thomas solve and budget sums",
                           "limiter": "koren", "l2": "inputs larger than L2 (2.4 GB state), no flush",
                           "parallelism": f"{world} independent replica(s), one per GPU"},
-               "clocks": clocks, "gpu_launches": 5 * args.steps, "roofline": roofline,
+               "clocks": clocks, "gpu_launches": sum(n for _t, n in (prof or {}).values()), "roofline": roofline,
                "e2e": e2e, "fp64": fp64, "precision": precision, "adjoint": adjoint, "ensemble": ensemble,
                "fp32_over_fp64_speedup": (value / fp64["value"]) if fp64 else None,
                "cpu_baseline": cpu}

@@ -5,7 +5,8 @@ state (CUDA events, best of a few repetitions) and keeps the fastest per
 (GPU name, operation, domain sizes, field count, precision) in a JSON cache:
   step:      one launch per stage and column pass, with the stage tile rows
              (32 x 4 / 8 / 16 for FP32, 8 for FP64) and the column kernel's
-             resident blocks per SM (1..4); or the persistent dataflow kernel;
+             resident blocks per SM (1..4), the third stage fused with the
+             top-down column pass or not; or the persistent dataflow kernel;
   ensemble:  ensemble tile rows (32 x 4 / 8 for FP32, 8 for FP64).
 Every shape computes the same arithmetic per cell, so results do not depend
 on the choice (a GPU test checks this bit for bit).  The cache file is
@@ -16,8 +17,8 @@ from __future__ import annotations
 import json
 import os
 
-from . import (FP64, TUNE_COL_BLOCKS_PER_SM, TUNE_ENSEMBLE_TILE_ROWS, TUNE_STAGE_TILE_ROWS, TUNE_STEP_MODE,
-               ensemble_step, ensemble_workspace_bytes, get_tuning, set_tuning, step)
+from . import (FP64, TUNE_COL_BLOCKS_PER_SM, TUNE_ENSEMBLE_TILE_ROWS, TUNE_FUSED_COLUMN, TUNE_STAGE_TILE_ROWS,
+               TUNE_STEP_MODE, ensemble_step, ensemble_workspace_bytes, get_tuning, set_tuning, step)
 
 TUNE_STAGE_TILE_ROWS_FP32 = (4, 8, 16)
 TUNE_ENS_TILE_ROWS_FP32 = (4, 8)
@@ -80,9 +81,14 @@ def _timed(fn, reps):
 
 
 def step_candidates(grid):
+    """Per-stage launches for every tile height and column-kernel occupancy, with
+    the fused third-stage/column path (8-row tiles only) and without it, and the
+    persistent dataflow kernel."""
     rows = (8,) if grid.prec == FP64 else TUNE_STAGE_TILE_ROWS_FP32
-    out = [{"step_mode": 0, "stage_tile_rows": r, "col_blocks_per_sm": b} for r in rows for b in COL_BLOCKS]
-    out.append({"step_mode": 1, "stage_tile_rows": 8, "col_blocks_per_sm": 3})
+    out = [{"step_mode": 0, "stage_tile_rows": r, "col_blocks_per_sm": b, "fused_column": 0}
+           for r in rows for b in COL_BLOCKS]
+    out += [{"step_mode": 0, "stage_tile_rows": 8, "col_blocks_per_sm": b, "fused_column": 1} for b in COL_BLOCKS]
+    out.append({"step_mode": 1, "stage_tile_rows": 8, "col_blocks_per_sm": 3, "fused_column": 0})
     return out
 
 
@@ -90,6 +96,7 @@ def apply_step(grid, cfg: dict) -> None:
     set_tuning(grid, TUNE_STEP_MODE, cfg.get("step_mode", 0))
     set_tuning(grid, TUNE_STAGE_TILE_ROWS, cfg["stage_tile_rows"])
     set_tuning(grid, TUNE_COL_BLOCKS_PER_SM, cfg["col_blocks_per_sm"])
+    set_tuning(grid, TUNE_FUSED_COLUMN, cfg.get("fused_column", 1))
 
 
 def tune_step(grid, state, dt, *, steps: int = 2, reps: int = 3, save: bool = True) -> dict:
@@ -159,6 +166,7 @@ def apply_cached_ensemble(grids) -> bool:
 
 def current(grid) -> dict:
     return {"step_mode": get_tuning(grid, TUNE_STEP_MODE),
+            "fused_column": get_tuning(grid, TUNE_FUSED_COLUMN),
             "stage_tile_rows": get_tuning(grid, TUNE_STAGE_TILE_ROWS),
             "col_blocks_per_sm": get_tuning(grid, TUNE_COL_BLOCKS_PER_SM),
             "ensemble_tile_rows": get_tuning(grid, TUNE_ENSEMBLE_TILE_ROWS)}

@@ -13,6 +13,8 @@
 // It is written as a gather: the thread of cell c visits the four faces per
 // direction whose stencil can hold c, so no two threads write the same value
 // and the result does not depend on scheduling.
+#include <type_traits>
+
 #include "adjoint_params.cuh"
 
 namespace asuca {
@@ -198,19 +200,26 @@ __global__ void __launch_bounds__(128, 4) adj_stage_kernel(const __grid_constant
 //                lambda_rhotheta /= (1 + r).
 // A block takes 32 columns (the lanes) and one warp per field (rho*theta and
 // each tracer), so the fields' FP64 recurrences run in separate warps:
-//   A. warp 0 factorises the diffusion matrix of each column (m, alpha, gamma);
+//   A. warp 0 factorises the diffusion matrix of each column (s = dz m,
+//      alpha, gamma);
 //   B. the warp of field f recomputes its forward solve phi_f, runs the
 //      transposed solve, writes the field's adjoint and leaves its share of the
 //      lambda_rho increment per level in the scratch;
 //   C. the warps, dealt levels round-robin, add the shares to lambda_rho in
 //      field order (a fixed order, so the result does not depend on scheduling).
-// Scratch per column and level: m, alpha, gamma, then per field the
+// Both sweeps of both solves run in double in both precisions.  With float
+// fields the arithmetic around them is float, as in the forward step: the
+// transposed right-hand side rho lambda / dz is formed in float and widened,
+// and the lambda_rho shares are products of the double differences rounded
+// to float once.
+// Scratch per column and level: s, alpha, gamma, then per field the
 // elimination value (reused for the field's lambda_rho share) and phi_f
 // (reused for the relaxation share of rho*theta).
 template <typename T, int NF>
 __global__ void __launch_bounds__(32 * (NF - 1)) adj_column_kernel(const __grid_constant__ AdjColParams<T> a) {
     constexpr int NT = NF - 1;
     constexpr int NQ = 3 + 2 * NT;
+    constexpr bool F32 = std::is_same<T, float>::value;
     const ColumnParams<T> &p = a.c;
     const int lane = threadIdx.x, f = threadIdx.y;   // f: field f + 1 of the state
     const long long plane = p.plane;
@@ -229,21 +238,26 @@ __global__ void __launch_bounds__(32 * (NF - 1)) adj_column_kernel(const __grid_
         const long long col = c0 + lane;
         const bool valid = col < plane;
         __syncthreads();   // the previous group's phase C is done with the scratch
-        // ---- A: factorisation, top-down (warp 0)
+        // ---- A: factorisation, top-down (warp 0); every sweep below loads the
+        // next level's inputs before it works on the current one
         if (p.do_diff && f == 0 && valid) {
             double g_hi = 0.0, m_up = 0.0;
-            for (int k = nz - 1; k >= 0; k--) {
-                const long long o = (long long)k * plane + col;
-                const double rd = to_f64(R[o]);
-                const double g_lo = (k > 0) ? p.kc[k - 1] * (to_f64(R[o - plane]) + rd) : 0.0;
+            long long o = (long long)(nz - 1) * plane + col;
+            T r = R[o], rdn = R[o - plane];
+            for (int k = nz - 1; k >= 0; k--, o -= plane) {
+                const T rdn2 = (k > 1) ? R[o - 2 * plane] : T(0);
+                const double rd = to_f64(r);
+                const double g_lo = (k > 0) ? p.kc[k - 1] * (to_f64(rdn) + rd) : 0.0;
                 const double b = rd * p.dz[k] + (g_lo + g_hi);
                 const double t = g_hi * m_up;
                 const double m = rcp_newton(fma(-g_hi, t, b));
-                S(k, 0) = m;
+                S(k, 0) = p.dz[k] * m;
                 S(k, 1) = t * p.dzr_up[k];
                 if (k < nz - 1) S(k + 1, 2) = g_hi * m * p.dzr_dn[k + 1];
                 g_hi = g_lo;
                 m_up = m;
+                r = rdn;
+                rdn = rdn2;
             }
         }
         __syncthreads();
@@ -253,11 +267,18 @@ __global__ void __launch_bounds__(32 * (NF - 1)) adj_column_kernel(const __grid_
                 // forward: relaxation / sedimentation of the field, elimination top-down
                 double e_up = 0.0;
                 T P = T(0);
-                for (int k = nz - 1; k >= 0; k--) {
-                    const long long o = (long long)k * plane + col;
-                    T x = Y[o];
+                long long o = (long long)(nz - 1) * plane + col;
+                double al = S(nz - 1, 1);
+                T x = Y[o], rho = (is_th && p.do_relax) ? R[o] : T(1);
+                for (int k = nz - 1; k >= 0; k--, o -= plane) {
+                    double al_n = 0.0;
+                    T x_n = T(0), rho_n = T(1);
+                    if (k > 0) {
+                        al_n = S(k - 1, 1);
+                        x_n = Y[o - plane];
+                        if (is_th && p.do_relax) rho_n = R[o - plane];
+                    }
                     if (is_th && p.do_relax) {
-                        const T rho = R[o];
                         T th = x / rho;
                         th = (th + p.relax_r * p.thref[k]) * p.relax_inv;
                         x = rho * th;
@@ -266,85 +287,206 @@ __global__ void __launch_bounds__(32 * (NF - 1)) adj_column_kernel(const __grid_
                         x = (x * p.dzT[k] + p.sed_dt * P) * p.sedr[k];
                         P = p.sed_v * x;
                     }
-                    e_up = fma(S(k, 1), e_up, to_f64(x));
+                    e_up = fma(al, e_up, to_f64(x));
                     S(k, qe) = e_up;
+                    al = al_n;
+                    x = x_n;
+                    rho = rho_n;
                 }
-                // back substitution bottom-up: phi_f
-                double z = 0.0;
-                for (int k = 0; k < nz; k++) {
-                    const double gk = k > 0 ? S(k, 2) : 0.0;
-                    z = fma(gk, z, S(k, qe));
-                    S(k, qp) = p.dz[k] * S(k, 0) * z;
+                // back substitution bottom-up: phi_f = s z
+                {
+                    double z = 0.0, gk = 0.0, ek = S(0, qe), sk = S(0, 0);
+                    for (int k = 0; k < nz; k++) {
+                        double gn = 0.0, en = 0.0, sn = 0.0;
+                        if (k + 1 < nz) {
+                            gn = S(k + 1, 2);
+                            en = S(k + 1, qe);
+                            sn = S(k + 1, 0);
+                        }
+                        z = fma(gk, z, ek);
+                        S(k, qp) = sk * z;
+                        gk = gn;
+                        ek = en;
+                        sk = sn;
+                    }
                 }
                 // transpose of the diffusion: elimination top-down on rho lambda / dz
-                double eu = 0.0;
-                for (int k = nz - 1; k >= 0; k--) {
-                    const long long o = (long long)k * plane + col;
-                    const double rk = to_f64(R[o]) * p.rdz64[k];
-                    eu = fma(S(k, 1), eu, rk * to_f64(lam[o]));
-                    S(k, qe) = eu;
+                {
+                    double eu = 0.0;
+                    o = (long long)(nz - 1) * plane + col;
+                    al = S(nz - 1, 1);
+                    T r = R[o], l = lam[o];
+                    for (int k = nz - 1; k >= 0; k--, o -= plane) {
+                        double al_n = 0.0;
+                        T r_n = T(0), l_n = T(0);
+                        if (k > 0) {
+                            al_n = S(k - 1, 1);
+                            r_n = R[o - plane];
+                            l_n = lam[o - plane];
+                        }
+                        double rhs;
+                        if constexpr (F32) rhs = to_f64(r * p.rdzT[k] * l);
+                        else rhs = to_f64(r) * p.rdz64[k] * to_f64(l);
+                        eu = fma(al, eu, rhs);
+                        S(k, qe) = eu;
+                        al = al_n;
+                        r = r_n;
+                        l = l_n;
+                    }
                 }
             }
             // bottom-up: transposed back substitution, the field's lambda_rho
             // shares, then the sedimentation and relaxation transposes
-            double zp = 0.0, psi_prev = 0.0, phi_prev = 0.0, carry = 0.0, nu_prev = 0.0;
-            for (int k = 0; k < nz; k++) {
-                const long long o = (long long)k * plane + col;
-                double lout;
-                bool write = false;
-                if (p.do_diff) {
-                    const double gk = k > 0 ? S(k, 2) : 0.0, kcl = k > 0 ? p.kc[k - 1] : 0.0;
-                    zp = fma(gk, zp, S(k, qe));
-                    const double psi = p.dz[k] * S(k, 0) * zp;
-                    const double ph = S(k, qp);
-                    const double lu = to_f64(lam[o]);
-                    const double A = (lu - p.dz[k] * psi) * ph;
-                    const double B = kcl * (psi - psi_prev) * (ph - phi_prev);   // face k-1/2
-                    // level k-1 takes A - B(k-1/2) - B(k+1/2); the last one now
-                    if (k > 0) S(k - 1, qe) = carry - B;
-                    carry = A - B;
-                    psi_prev = psi;
-                    phi_prev = ph;
-                    lout = to_f64(from_f64<T>(p.dz[k] * psi));
-                    write = true;
-                } else {
-                    lout = to_f64(lam[o]);
-                }
-                if (is_sed) {
-                    double nu = lout;
-                    if (k > 0) nu += p.dt * sv * to_f64(p.sedr[k - 1]) * nu_prev;
-                    nu_prev = nu;
-                    lout = to_f64(from_f64<T>(nu * p.dz[k] * to_f64(p.sedr[k])));
-                    write = true;
-                }
-                if (is_th && p.do_relax) {
-                    S(k, qp) = lout * rr * to_f64(p.thref[k]) * ri;   // relaxation share of lambda_rho
-                    lout = lout * ri;
-                    write = true;
-                }
-                if (write) lam[o] = from_f64<T>(lout);
+            double zp = 0.0, psi_prev = 0.0, phi_prev = 0.0;
+            double gk = 0.0, ek = 0.0, sk = 0.0, phk = 0.0;
+            if (p.do_diff) {
+                ek = S(0, qe);
+                sk = S(0, 0);
+                phk = S(0, qp);
             }
-            if (p.do_diff) S(nz - 1, qe) = carry;
+            T lk = lam[col];
+            long long o = col;
+            if constexpr (F32) {
+                float carry = 0.f, nu_prev = 0.f;
+                const float svf = p.sed_v, rrf = p.relax_r, rif = p.relax_inv, dtf = p.sed_dt;
+                for (int k = 0; k < nz; k++, o += plane) {
+                    double gn = 0.0, en = 0.0, sn = 0.0, pn = 0.0;
+                    T ln = T(0);
+                    if (k + 1 < nz) {
+                        if (p.do_diff) {
+                            gn = S(k + 1, 2);
+                            en = S(k + 1, qe);
+                            sn = S(k + 1, 0);
+                            pn = S(k + 1, qp);
+                        }
+                        ln = lam[o + plane];
+                    }
+                    float lout;
+                    bool write = false;
+                    if (p.do_diff) {
+                        zp = fma(gk, zp, ek);
+                        const double psi = sk * zp;
+                        const double ph = phk;
+                        // A = (lambda_u - dz psi) phi, B = (dg/drho)(psi - psi_prev)(phi - phi_prev)
+                        const float A = d2f_bits(fma(-p.dz[k], psi, to_f64(lk))) * d2f_bits(ph);
+                        const float B = k > 0 ? p.kcT[k - 1] * d2f_bits(psi - psi_prev) * d2f_bits(ph - phi_prev) : 0.f;
+                        // level k-1 takes A - B(k-1/2) - B(k+1/2); the last one now
+                        if (k > 0) S(k - 1, qe) = f2d_bits_any(carry - B);
+                        carry = A - B;
+                        psi_prev = psi;
+                        phi_prev = ph;
+                        lout = p.dzT[k] * d2f_bits(psi);
+                        write = true;
+                    } else {
+                        lout = lk;
+                    }
+                    if (is_sed) {
+                        float nu = lout;
+                        if (k > 0) nu += dtf * svf * p.sedr[k - 1] * nu_prev;
+                        nu_prev = nu;
+                        lout = nu * p.dzT[k] * p.sedr[k];
+                        write = true;
+                    }
+                    if (is_th && p.do_relax) {
+                        S(k, qp) = f2d_bits_any(lout * rrf * p.thref[k] * rif);   // relaxation share
+                        lout = lout * rif;
+                        write = true;
+                    }
+                    if (write) lam[o] = lout;
+                    gk = gn;
+                    ek = en;
+                    sk = sn;
+                    phk = pn;
+                    lk = ln;
+                }
+                if (p.do_diff) S(nz - 1, qe) = f2d_bits_any(carry);
+            } else {
+                double carry = 0.0, nu_prev = 0.0;
+                for (int k = 0; k < nz; k++, o += plane) {
+                    double gn = 0.0, en = 0.0, sn = 0.0, pn = 0.0;
+                    T ln = T(0);
+                    if (k + 1 < nz) {
+                        if (p.do_diff) {
+                            gn = S(k + 1, 2);
+                            en = S(k + 1, qe);
+                            sn = S(k + 1, 0);
+                            pn = S(k + 1, qp);
+                        }
+                        ln = lam[o + plane];
+                    }
+                    double lout;
+                    bool write = false;
+                    if (p.do_diff) {
+                        const double kcl = k > 0 ? p.kc[k - 1] : 0.0;
+                        zp = fma(gk, zp, ek);
+                        const double psi = sk * zp;
+                        const double ph = phk;
+                        const double lu = to_f64(lk);
+                        const double A = (lu - p.dz[k] * psi) * ph;
+                        const double B = kcl * (psi - psi_prev) * (ph - phi_prev);   // face k-1/2
+                        // level k-1 takes A - B(k-1/2) - B(k+1/2); the last one now
+                        if (k > 0) S(k - 1, qe) = carry - B;
+                        carry = A - B;
+                        psi_prev = psi;
+                        phi_prev = ph;
+                        lout = to_f64(from_f64<T>(p.dz[k] * psi));
+                        write = true;
+                    } else {
+                        lout = to_f64(lk);
+                    }
+                    if (is_sed) {
+                        double nu = lout;
+                        if (k > 0) nu += p.dt * sv * to_f64(p.sedr[k - 1]) * nu_prev;
+                        nu_prev = nu;
+                        lout = to_f64(from_f64<T>(nu * p.dz[k] * to_f64(p.sedr[k])));
+                        write = true;
+                    }
+                    if (is_th && p.do_relax) {
+                        S(k, qp) = lout * rr * to_f64(p.thref[k]) * ri;   // relaxation share of lambda_rho
+                        lout = lout * ri;
+                        write = true;
+                    }
+                    if (write) lam[o] = from_f64<T>(lout);
+                    gk = gn;
+                    ek = en;
+                    sk = sn;
+                    phk = pn;
+                    lk = ln;
+                }
+                if (p.do_diff) S(nz - 1, qe) = carry;
+            }
         }
         __syncthreads();
         // ---- C: lambda_rho, levels dealt to the warps
         if (valid) {
             for (int k = f; k < nz; k += NT) {
                 const long long o = (long long)k * plane + col;
-                double lrho = to_f64(a.lam[0][o]);
-                if (p.do_diff) {
-                    double inc = 0.0;
+                if constexpr (F32) {
+                    float lrho = a.lam[0][o];
+                    if (p.do_diff) {
+                        float inc = 0.f;
 #pragma unroll
-                    for (int q = 0; q < NT; q++) inc += S(k, 3 + q);
-                    lrho += inc;
+                        for (int q = 0; q < NT; q++) inc += d2f_bits(S(k, 3 + q));
+                        lrho += inc;
+                    }
+                    if (p.do_relax) lrho += d2f_bits(S(k, 3 + NT));
+                    a.lam[0][o] = lrho;
+                } else {
+                    double lrho = to_f64(a.lam[0][o]);
+                    if (p.do_diff) {
+                        double inc = 0.0;
+#pragma unroll
+                        for (int q = 0; q < NT; q++) inc += S(k, 3 + q);
+                        lrho += inc;
+                    }
+                    if (p.do_relax) lrho += S(k, 3 + NT);
+                    a.lam[0][o] = from_f64<T>(lrho);
                 }
-                if (p.do_relax) lrho += S(k, 3 + NT);
-                a.lam[0][o] = from_f64<T>(lrho);
             }
         }
     }
-}
 #undef S
+}
 
 // ------------------------------------------------------------------ launchers
 

@@ -210,12 +210,14 @@ ColumnParams<T> column_params(const asuca_grid *g, double dt) {
         p.dzr_up[k] = (k + 1 < nz) ? g->dz[k + 1] / g->dz[k] : 0.0;
         p.dzr_dn[k] = (k > 0) ? g->dz[k - 1] / g->dz[k] : 0.0;
         p.rdz64[k] = 1.0 / g->dz[k];
+        p.rdzT[k] = (T)(1.0 / g->dz[k]);
         if (k + 1 < nz && p.do_diff) {
             const double K = d.k0 * std::exp(-g->zf[k + 1] / d.k_h);
             p.kc[k] = 0.5 * dt * K / (g->zc[k + 1] - g->zc[k]);
         } else {
             p.kc[k] = 0.0;
         }
+        p.kcT[k] = (T)p.kc[k];
     }
     return p;
 }
@@ -526,6 +528,10 @@ struct AdjLayout {
 
 int adj_col_grid(const asuca_grid *g) { return g->col_grid; }
 
+// Tile rows of the branch-recording stage launches: the grid's tuned stage
+// tile height where a recording variant exists (4 or 8 rows), else 8.
+int rec_tile_rows(const asuca_grid *g) { return g->stage_ty == 4 ? 4 : 8; }
+
 // Blocks of the column transpose: 32 columns each (one warp per field), at
 // most as many column slots as the scratch holds (adj_col_grid * COL_TPB).
 int adj_col_blocks(const asuca_grid *g) {
@@ -649,12 +655,14 @@ asuca_status run_adjoint(asuca_grid *g, const asuca_state *init, const void *ten
     const T cdt[3] = {(T)(dt / 3.0), (T)(dt / 2.0), (T)dt};
     const StepLayout SL = step_layout(g);
     char *sws = ws + L.step;
+    // the recomputation records branches with the grid's tuned tile height (4 or 8 rows)
+    const int rty = rec_tile_rows(g);
     std::vector<CUtensorMap> maps(2 * (size_t)K);
     for (int q = 0; q < K; q++) {
         if (encode_stage_map<T>(&maps[2 * q], ws + L.segY1 + (size_t)q * align_up(L.pstate), F, g->d.nx, g->d.ny,
-                                g->d.nz, 8) != cudaSuccess ||
+                                g->d.nz, rty) != cudaSuccess ||
             encode_stage_map<T>(&maps[2 * q + 1], ws + L.segY2 + (size_t)q * align_up(L.pstate), F, g->d.nx,
-                                g->d.ny, g->d.nz, 8) != cudaSuccess)
+                                g->d.ny, g->d.nz, rty) != cudaSuccess)
             return ASUCA_ERR_CUDA;
     }
     for (int c = L.ncp - 1; c >= 0; c--) {
@@ -678,7 +686,7 @@ asuca_status run_adjoint(asuca_grid *g, const asuca_state *init, const void *ten
             workspace_fields<T>(g, segY2(q), 0, y2);
             block_fields<T>(g, segY3(q), y3);
             StageParams<T> sp = stage_params<T>(g, init, tend);
-            sp.ty = 8;   // branch recording runs with 8-row tiles
+            sp.ty = rty;
             for (int f = 0; f < MAXF; f++) sp.ybase[f] = yn[f];
             for (int stg = 0; stg < 3; stg++) {
                 sp.tma_in = stg > 0;

@@ -93,6 +93,8 @@ struct ColumnParams {
     double dzr_up[MAXNZ];   // dz_{k+1} / dz_k
     double dzr_dn[MAXNZ];   // dz_{k-1} / dz_k
     double rdz64[MAXNZ];    // 1 / dz_k
+    T rdzT[MAXNZ];          // 1 / dz_k (rounded to T)
+    T kcT[MAXNZ];           // kc rounded to T
 };
 
 // ------------------------------------------------------------------ helpers
@@ -137,6 +139,10 @@ __device__ __forceinline__ float d2f_bits(double x) {
     mag += (rem > 0x10000000u || (rem == 0x10000000u && (mag & 1u))) ? 1u : 0u;
     return __uint_as_float((hi & 0x80000000u) | mag);
 }
+
+// Widening of any float (zero, subnormal, inf, NaN included), for values that
+// are only stored: the bit path, else the hardware conversion.
+__device__ __forceinline__ double f2d_bits_any(float x) { return f2d_bits(x); }
 
 template <typename T> __device__ __forceinline__ double to_f64(T x);
 template <> __device__ __forceinline__ double to_f64<double>(double x) { return x; }

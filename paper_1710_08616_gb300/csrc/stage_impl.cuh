@@ -552,12 +552,13 @@ static cudaError_t launch_rec(const StageParams<T> &p, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// branch recording is instantiated for 8-row tiles only (the adjoint's forward pass)
+// branch recording (the adjoint's forward pass) is instantiated for 4- and
+// 8-row tiles
 template <typename T, int NF, int LIM, int TYV>
 static cudaError_t launch_lim(const StageParams<T> &p, cudaStream_t s) {
     if (p.branch) {
-        if (TYV != 8) return cudaErrorInvalidValue;
-        return launch_rec<T, NF, LIM, true, 8>(p, s);
+        if constexpr (TYV == 4 || TYV == 8) return launch_rec<T, NF, LIM, true, TYV>(p, s);
+        else return cudaErrorInvalidValue;
     }
     return launch_rec<T, NF, LIM, false, TYV>(p, s);
 }

@@ -38,3 +38,5 @@ def test_candidates():
     assert {c["stage_tile_rows"] for c in c64} == {8}
     assert {c["col_blocks_per_sm"] for c in c32} == {1, 2, 3, 4}
     assert {c["step_mode"] for c in c32} == {0, 1}
+    assert {c["fused_column"] for c in c32} == {0, 1}
+    assert all(c["stage_tile_rows"] == 8 and c["step_mode"] == 0 for c in c32 if c["fused_column"])

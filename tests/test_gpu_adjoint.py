@@ -54,9 +54,11 @@ def _gpu_branches(asuca, case, nsteps, lim=0, tend=None, prec=0):
     return out
 
 
-def _gpu_adjoint(asuca, case, lam, nsteps, K, prec=0, lim=0, tend=None):
+def _gpu_adjoint(asuca, case, lam, nsteps, K, prec=0, lim=0, tend=None, tile_rows=None):
     import torch
     g = asuca.Grid.from_case(case, prec=prec, lim=lim)
+    if tile_rows is not None:
+        asuca.set_tuning(g, asuca.TUNE_STAGE_TILE_ROWS, tile_rows)
     st = asuca.State.from_case(case, prec=prec)
     dt_ = g.torch_dtype
     td = None if tend is None else torch.tensor(tend, dtype=dt_, device="cuda")
@@ -95,6 +97,17 @@ def test_adjoint_independent_of_checkpoint_interval(asuca):
         b = _gpu_adjoint(asuca, c, lam, 7, K)
         for x, y in zip(a, b):
             assert np.array_equal(x, y)
+
+
+def test_adjoint_independent_of_recording_tile_rows(asuca):
+    """The recomputation records branches with the grid's tile height; 4- and
+    8-row tiles give the same trajectory, hence the same gradients bit for bit."""
+    c = gen.make_case(70, 21, 9, 3, seed=12)
+    lam = np.random.default_rng(2).standard_normal(c.state().shape)
+    a = _gpu_adjoint(asuca, c, lam, 4, 2, prec=1, tile_rows=8)
+    b = _gpu_adjoint(asuca, c, lam, 4, 2, prec=1, tile_rows=4)
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
 
 
 @pytest.mark.parametrize("prec", [0, 1])
