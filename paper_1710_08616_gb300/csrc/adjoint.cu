@@ -10,9 +10,9 @@
 //   lambda_phi(c) = sum over faces whose stencil holds c of lambda_F M dface/dphi(c)
 //   lambda(rho phi)(c) = lambda_phi / rho,   lambda(rho)(c) -= lambda_phi phi / rho
 //   gradient of M at the face += lambda_F(rho) + sum_f lambda_F(f) face_f
-// It is written as a gather: the thread of cell c visits the four faces per
-// direction whose stencil can hold c, so no two threads write the same value
-// and the result does not depend on scheduling.
+// It is written as a gather: the thread of cell c and field f visits the four
+// faces per direction whose stencil can hold c, so no two threads write the
+// same value and the result does not depend on scheduling.
 #include <type_traits>
 
 #include "adjoint_params.cuh"
@@ -20,44 +20,59 @@
 namespace asuca {
 
 template <typename T, int NF, int LIM>
-__global__ void __launch_bounds__(128, 4) adj_stage_kernel(const __grid_constant__ AdjStageParams<T> p) {
+__global__ void __launch_bounds__(32 * (NF - 1)) adj_stage_kernel(const __grid_constant__ AdjStageParams<T> p) {
     constexpr int NT = NF - 1;
+    // A block takes 32 cells of one row at one level (the lanes) and one warp
+    // per field f + 1; the density's terms and the cross-field sums are added
+    // by warp 0 through shared memory, in field order.
     // d face / d phi of the four stencil cells of a face for each upwind side
     // and limiter branch, ctab[u * 16 + br * 4 + q] (u = 1 for M >= 0)
     __shared__ T ctab[32];
-    {
-        const int t = threadIdx.y * blockDim.x + threadIdx.x;
-        if (t < 32) ctab[t] = face_coef<T>((t >> 4) != 0, (t >> 2) & 3, t & 3);
-        __syncthreads();
-    }
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    __shared__ T rcs[10][32];        // 1/rho at the cell and at its faces' stencil cells
+    __shared__ T part[4][NT][32];    // per field: lphi phi / rho and its M-gradient terms in x, y, z
+    const int lane = threadIdx.x, f = threadIdx.y, tid = f * 32 + lane;
+    if (tid < 32) ctab[tid] = face_coef<T>((tid >> 4) != 0, (tid >> 2) & 3, tid & 3);
+    const int i = blockIdx.x * 32 + lane, j = blockIdx.y, k = blockIdx.z;
     const int nx = p.nx, ny = p.ny, nz = p.nz;
-    if (i >= nx || j >= ny) return;
+    const bool valid = i < nx;
     // offsets within a field fit in 32 bits (the host checks)
     const unsigned plane = (unsigned)p.plane, ysp = (unsigned)p.ys_plane;
     // planar offsets (caller layout) of the cells i-2..i+2 (row j) and j-2..j+2
     // (column i), and the same cells in the layout of the stage input
+    // (the neighbours are at most 2 cells away and nx, ny >= 4, so one add or
+    // subtract wraps them)
     unsigned ox[5], oy[5], sx[5], sy[5];
+    const unsigned yrow = (unsigned)(j * nx), srow = (unsigned)((j + p.ys_oy) * p.ys_pitch + p.ys_ox);
+    const unsigned spitch = (unsigned)p.ys_pitch;
 #pragma unroll
     for (int q = 0; q < 5; q++) {
-        const int ix = wrap_index(i + q - 2, nx), jy = wrap_index(j + q - 2, ny);
-        ox[q] = (unsigned)(j * nx + ix);
+        int ix = i + q - 2, jy = j + q - 2;
+        ix = ix < 0 ? ix + nx : (ix >= nx ? ix - nx : ix);
+        jy = jy < 0 ? jy + ny : (jy >= ny ? jy - ny : jy);
+        ox[q] = yrow + (unsigned)ix;
         oy[q] = (unsigned)(jy * nx + i);
-        sx[q] = (unsigned)((j + p.ys_oy) * p.ys_pitch + ix + p.ys_ox);
-        sy[q] = (unsigned)((jy + p.ys_oy) * p.ys_pitch + i + p.ys_ox);
+        sx[q] = srow + (unsigned)ix;
+        sy[q] = (unsigned)(jy + p.ys_oy) * spitch + (unsigned)(i + p.ys_ox);
     }
-    const T cs = p.cs, rdx = p.rdx, rdy = p.rdy;
+    const unsigned kb = (unsigned)k * plane, skb = (unsigned)k * ysp;
+    const unsigned own = kb + ox[2];
+    // stencil cells of the cell's own +1/2 faces in the stage input
+    const unsigned zm1 = (unsigned)(k > 0 ? k - 1 : 0) * ysp + sx[2];
+    const unsigned zp1 = (unsigned)(k + 1 < nz ? k + 1 : nz - 1) * ysp + sx[2];
+    const unsigned zp2 = (unsigned)(k + 2 < nz ? k + 2 : nz - 1) * ysp + sx[2];
     const bool sphi = p.ys_phi != 0;
     const T *R0 = p.ys[0];
-    // every cell is independent in this gather form, so the levels are split
-    // into chunks of kchunk, one chunk per blockIdx.z (parallel over i, j and k)
-    const int kbeg = blockIdx.z * p.kchunk;
-    const int kend = min(nz, kbeg + p.kchunk);
-
-    for (int k = kbeg; k < kend; k++) {
-        const unsigned kb = (unsigned)k * plane, skb = (unsigned)k * ysp;
-        const unsigned own = kb + ox[2];
+    // reciprocals of rho, dealt to the warps: phi as the forward stage saw it is
+    // stored as phi in the padded stage buffers, as rho*phi in the caller layout
+    if (valid) {
+        const unsigned at[10] = {skb + sx[2], skb + sx[1], skb + sx[3], skb + sx[4], skb + sy[1],
+                                 skb + sy[3], skb + sy[4], zm1, zp1, zp2};
+        for (int q = f; q < (sphi ? 1 : 10); q += NT) rcs[q][lane] = recip(R0[at[q]]);
+    }
+    __syncthreads();
+    if (valid) {
+        const T cs = p.cs, rdx = p.rdx, rdy = p.rdy;
+        const T rr = rcs[0][lane];
         // mass fluxes of the four faces per direction that touch cell c; face a+1/2 is stored at cell a
         T mxf[4], myf[4], mzf[4];
 #pragma unroll
@@ -67,121 +82,113 @@ __global__ void __launch_bounds__(128, 4) adj_stage_kernel(const __grid_constant
             const int a = k + q - 2;
             mzf[q] = (a >= 0 && a <= nz - 2) ? p.mw[(unsigned)(a + 1) * plane + ox[2]] : T(0);
         }
-        // stencil cells of the cell's own +1/2 faces in the stage input
-        const unsigned zm1 = (unsigned)(k > 0 ? k - 1 : 0) * ysp + sx[2];
-        const unsigned zp1 = (unsigned)(k + 1 < nz ? k + 1 : nz - 1) * ysp + sx[2];
-        const unsigned zp2 = (unsigned)(k + 2 < nz ? k + 2 : nz - 1) * ysp + sx[2];
-        const T rho = R0[skb + sx[2]];
-        const T rr = recip(rho);
-        // phi as the forward stage saw it: stored as phi in the padded stage
-        // buffers; as rho*phi in the caller layout, converted with 1/rho of each
-        // stencil cell (taken once per cell, shared by the fields)
-        T rx[4], ry[3], rz[3];
-        if (!sphi) {
-            rx[0] = recip(R0[skb + sx[1]]); rx[1] = rr; rx[2] = recip(R0[skb + sx[3]]); rx[3] = recip(R0[skb + sx[4]]);
-            ry[0] = recip(R0[skb + sy[1]]); ry[1] = recip(R0[skb + sy[3]]); ry[2] = recip(R0[skb + sy[4]]);
-            rz[0] = recip(R0[zm1]); rz[1] = recip(R0[zp1]); rz[2] = recip(R0[zp2]);
+        const T *L = p.lam[f + 1];
+        const uint8_t *B = p.branch + (size_t)f * nz * plane;
+        T lx[5], ly[5], lz[5];
+#pragma unroll
+        for (int q = 0; q < 5; q++) {
+            lx[q] = L[kb + ox[q]];
+            ly[q] = L[kb + oy[q]];
+            const int lev = k + q - 2;
+            lz[q] = (lev >= 0 && lev < nz) ? L[(unsigned)lev * plane + ox[2]] : T(0);
         }
-        T vrho = T(0);
-        // --- density: no phi, only the gradient of M
-        T gx, gy, gz;
+        T lphi = T(0);
+        // i direction: faces a = i-2 .. i+1; cell c is stencil member 3, 2, 1, 0 of them
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const T lF = cs * (lx[q + 1] - lx[q]) * rdx;
+            const int br = B[kb + ox[q]] & 3;
+            lphi += lF * mxf[q] * ctab[(mxf[q] >= T(0) ? 16 : 0) + br * 4 + (3 - q)];
+        }
+        // j direction
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const T lF = cs * (ly[q + 1] - ly[q]) * rdy;
+            const int br = (B[kb + oy[q]] >> 2) & 3;
+            lphi += lF * myf[q] * ctab[(myf[q] >= T(0) ? 16 : 0) + br * 4 + (3 - q)];
+        }
+        // k direction: faces a = k-2 .. k+1 that exist; next to a lid the ghost
+        // levels fold several stencil members into the boundary cell
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const int a = k + q - 2;
+            if (a < 0 || a > nz - 2) continue;
+            const T lF = cs * (lz[q + 1] * p.rdz[a + 1] - lz[q] * p.rdz[a]);
+            const int br = (B[(unsigned)a * plane + ox[2]] >> 4) & 3;
+            const T *ct = ctab + (mzf[q] >= T(0) ? 16 : 0) + br * 4;
+            T cf;
+            if (a >= 1 && a + 2 <= nz - 1) {
+                cf = ct[3 - q];
+            } else {
+                cf = T(0);
+#pragma unroll
+                for (int m = 0; m < 4; m++) {
+                    int cell = a + m - 1;
+                    cell = cell < 0 ? 0 : (cell > nz - 1 ? nz - 1 : cell);
+                    if (cell == k) cf += ct[m];
+                }
+            }
+            lphi += lF * mzf[q] * cf;
+        }
+        // this field's share of the gradient of M at the cell's own faces
+        const T *Y = p.ys[f + 1];
+        const T ph = sphi ? Y[skb + sx[2]] : Y[skb + sx[2]] * rr;
+        T gx, gy, gz = T(0);
         {
-            const T m0 = p.lam[0][own], mxp = p.lam[0][kb + ox[3]], myp = p.lam[0][kb + oy[3]];
-            gx = cs * (mxp - m0) * rdx;
-            gy = cs * (myp - m0) * rdy;
-            gz = (k <= nz - 2) ? cs * (p.lam[0][own + plane] * p.rdz[k + 1] - m0 * p.rdz[k]) : T(0);
+            const T fx = sphi ? face_val4<LIM>(Y[skb + sx[1]], ph, Y[skb + sx[3]], Y[skb + sx[4]], mxf[2] >= T(0))
+                              : face_val4<LIM>(Y[skb + sx[1]] * rcs[1][lane], ph, Y[skb + sx[3]] * rcs[2][lane],
+                                               Y[skb + sx[4]] * rcs[3][lane], mxf[2] >= T(0));
+            gx = cs * (lx[3] - lx[2]) * rdx * fx;
+            const T fy = sphi ? face_val4<LIM>(Y[skb + sy[1]], ph, Y[skb + sy[3]], Y[skb + sy[4]], myf[2] >= T(0))
+                              : face_val4<LIM>(Y[skb + sy[1]] * rcs[4][lane], ph, Y[skb + sy[3]] * rcs[5][lane],
+                                               Y[skb + sy[4]] * rcs[6][lane], myf[2] >= T(0));
+            gy = cs * (ly[3] - ly[2]) * rdy * fy;
+            if (k <= nz - 2) {
+                const T fz = sphi ? face_val4<LIM>(Y[zm1], ph, Y[zp1], Y[zp2], mzf[2] >= T(0))
+                                  : face_val4<LIM>(Y[zm1] * rcs[7][lane], ph, Y[zp1] * rcs[8][lane],
+                                                   Y[zp2] * rcs[9][lane], mzf[2] >= T(0));
+                gz = cs * (lz[3] * p.rdz[k + 1] - lz[2] * p.rdz[k]) * fz;
+            }
         }
-        T vf[NT];
-#pragma unroll
-        for (int f = 0; f < NT; f++) {
-            const T *L = p.lam[f + 1];
-            const uint8_t *B = p.branch + (size_t)f * nz * plane;
-            T lx[5], ly[5], lz[5];
-#pragma unroll
-            for (int q = 0; q < 5; q++) {
-                lx[q] = L[kb + ox[q]];
-                ly[q] = L[kb + oy[q]];
-                const int lev = k + q - 2;
-                lz[q] = (lev >= 0 && lev < nz) ? L[(unsigned)lev * plane + ox[2]] : T(0);
-            }
-            T lphi = T(0);
-            // i direction: faces a = i-2 .. i+1; cell c is stencil member 3, 2, 1, 0 of them
-#pragma unroll
-            for (int q = 0; q < 4; q++) {
-                const T lF = cs * (lx[q + 1] - lx[q]) * rdx;
-                const int br = B[kb + ox[q]] & 3;
-                lphi += lF * mxf[q] * ctab[(mxf[q] >= T(0) ? 16 : 0) + br * 4 + (3 - q)];
-            }
-            // j direction
-#pragma unroll
-            for (int q = 0; q < 4; q++) {
-                const T lF = cs * (ly[q + 1] - ly[q]) * rdy;
-                const int br = (B[kb + oy[q]] >> 2) & 3;
-                lphi += lF * myf[q] * ctab[(myf[q] >= T(0) ? 16 : 0) + br * 4 + (3 - q)];
-            }
-            // k direction: faces a = k-2 .. k+1 that exist; next to a lid the ghost
-            // levels fold several stencil members into the boundary cell
-#pragma unroll
-            for (int q = 0; q < 4; q++) {
-                const int a = k + q - 2;
-                if (a < 0 || a > nz - 2) continue;
-                const T lF = cs * (lz[q + 1] * p.rdz[a + 1] - lz[q] * p.rdz[a]);
-                const int br = (B[(unsigned)a * plane + ox[2]] >> 4) & 3;
-                const T *ct = ctab + (mzf[q] >= T(0) ? 16 : 0) + br * 4;
-                T cf;
-                if (a >= 1 && a + 2 <= nz - 1) {
-                    cf = ct[3 - q];
-                } else {
-                    cf = T(0);
-#pragma unroll
-                    for (int m = 0; m < 4; m++) {
-                        int cell = a + m - 1;
-                        cell = cell < 0 ? 0 : (cell > nz - 1 ? nz - 1 : cell);
-                        if (cell == k) cf += ct[m];
-                    }
-                }
-                lphi += lF * mzf[q] * cf;
-            }
-            // gradient of M at the cell's own faces
-            const T *Y = p.ys[f + 1];
-            const T ph = sphi ? Y[skb + sx[2]] : Y[skb + sx[2]] * rr;
-            {
-                const T fx = sphi ? face_val4<LIM>(Y[skb + sx[1]], ph, Y[skb + sx[3]], Y[skb + sx[4]], mxf[2] >= T(0))
-                                  : face_val4<LIM>(Y[skb + sx[1]] * rx[0], ph, Y[skb + sx[3]] * rx[2],
-                                                   Y[skb + sx[4]] * rx[3], mxf[2] >= T(0));
-                gx += cs * (lx[3] - lx[2]) * rdx * fx;
-                const T fy = sphi ? face_val4<LIM>(Y[skb + sy[1]], ph, Y[skb + sy[3]], Y[skb + sy[4]], myf[2] >= T(0))
-                                  : face_val4<LIM>(Y[skb + sy[1]] * ry[0], ph, Y[skb + sy[3]] * ry[1],
-                                                   Y[skb + sy[4]] * ry[2], myf[2] >= T(0));
-                gy += cs * (ly[3] - ly[2]) * rdy * fy;
-                if (k <= nz - 2) {
-                    const T fz = sphi ? face_val4<LIM>(Y[zm1], ph, Y[zp1], Y[zp2], mzf[2] >= T(0))
-                                      : face_val4<LIM>(Y[zm1] * rz[0], ph, Y[zp1] * rz[1], Y[zp2] * rz[2],
-                                                       mzf[2] >= T(0));
-                    gz += cs * (lz[3] * p.rdz[k + 1] - lz[2] * p.rdz[k]) * fz;
-                }
-            }
-            vf[f] = lphi * rr;
-            vrho -= lphi * ph * rr;
+        // the field's output
+        const T v = lphi * rr;
+        if (p.out1[0]) p.out1[f + 1][own] = v;
+        if (p.out2[0]) {
+            T o = v;
+            if (p.base2[0]) o += p.base2[f + 1][own];
+            if (p.add_self) o += L[own];
+            p.out2[f + 1][own] = o;
         }
-        // gradients of the mass fluxes through the cell's own +1/2 faces
+        part[0][f][lane] = lphi * ph * rr;
+        part[1][f][lane] = gx;
+        part[2][f][lane] = gy;
+        part[3][f][lane] = gz;
+    }
+    __syncthreads();
+    // ---- warp 0: the density's output and the gradients of the cell's own faces
+    if (f == 0 && valid) {
+        const T cs = p.cs;
+        const T m0 = p.lam[0][own], mxp = p.lam[0][kb + ox[3]], myp = p.lam[0][kb + oy[3]];
+        T gx = cs * (mxp - m0) * p.rdx;
+        T gy = cs * (myp - m0) * p.rdy;
+        T gz = (k <= nz - 2) ? cs * (p.lam[0][own + plane] * p.rdz[k + 1] - m0 * p.rdz[k]) : T(0);
+        T vrho = T(0);
+#pragma unroll
+        for (int q = 0; q < NT; q++) {
+            vrho -= part[0][q][lane];
+            gx += part[1][q][lane];
+            gy += part[2][q][lane];
+            gz += part[3][q][lane];
+        }
         p.gmu[own] += gx;
         p.gmv[own] += gy;
         if (k <= nz - 2) p.gmw[own + plane] += gz;
-        // outputs
-        T v[NF];
-        v[0] = vrho;
-#pragma unroll
-        for (int f = 0; f < NT; f++) v[f + 1] = vf[f];
-#pragma unroll
-        for (int f = 0; f < NF; f++) {
-            if (p.out1[0]) p.out1[f][own] = v[f];
-            if (p.out2[0]) {
-                T o = v[f];
-                if (p.base2[0]) o += p.base2[f][own];
-                if (p.add_self) o += p.lam[f][own];
-                p.out2[f][own] = o;
-            }
+        if (p.out1[0]) p.out1[0][own] = vrho;
+        if (p.out2[0]) {
+            T o = vrho;
+            if (p.base2[0]) o += p.base2[0][own];
+            if (p.add_self) o += m0;
+            p.out2[0][own] = o;
         }
     }
 }
@@ -492,9 +499,8 @@ __global__ void __launch_bounds__(32 * (NF - 1)) adj_column_kernel(const __grid_
 
 template <typename T, int NF, int LIM>
 static cudaError_t launch_adj_stage_lim(const AdjStageParams<T> &p, cudaStream_t s) {
-    if (p.kchunk < 1) return cudaErrorInvalidValue;
-    dim3 block(32, 4);
-    dim3 grid((p.nx + 31) / 32, (p.ny + 3) / 4, (p.nz + p.kchunk - 1) / p.kchunk);
+    dim3 block(32, NF - 1);
+    dim3 grid((p.nx + 31) / 32, p.ny, p.nz);
     adj_stage_kernel<T, NF, LIM><<<grid, block, 0, s>>>(p);
     return cudaGetLastError();
 }

@@ -21,7 +21,6 @@ struct AdjStageParams {
     int add_self;
     T *gmu, *gmv, *gmw;           // += R_M^T (cs lam)
     int nx, ny, nz;
-    int kchunk;                   // levels per thread (the launch has ceil(nz / kchunk) blocks in z)
     long long plane;
     T rdx, rdy;
     T rdz[MAXNZ];

@@ -539,15 +539,6 @@ int adj_col_blocks(const asuca_grid *g) {
     return (int)(need < cap ? need : cap);
 }
 
-// Levels per thread of the stage transpose: enough level chunks that the
-// launch has at least 16 blocks of 128 threads per SM.
-int adj_stage_kchunk(const asuca_grid *g) {
-    const long long cols = (long long)((g->d.nx + 31) / 32) * ((g->d.ny + 3) / 4);
-    long long chunks = (16LL * g->nsm + cols - 1) / cols;
-    if (chunks > g->d.nz) chunks = g->d.nz;
-    if (chunks < 1) chunks = 1;
-    return (int)((g->d.nz + chunks - 1) / chunks);
-}
 
 AdjLayout adj_layout(const asuca_grid *g, int nsteps, int K) {
     AdjLayout L;
@@ -761,7 +752,6 @@ asuca_status run_adjoint(asuca_grid *g, const asuca_state *init, const void *ten
                 ap.nx = g->d.nx;
                 ap.ny = g->d.ny;
                 ap.nz = g->d.nz;
-                ap.kchunk = adj_stage_kchunk(g);
                 ap.plane = g->plane;
                 ap.rdx = (T)(1.0 / g->d.dx);
                 ap.rdy = (T)(1.0 / g->d.dy);
