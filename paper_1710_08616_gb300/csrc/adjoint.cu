@@ -10,9 +10,9 @@
 //   lambda_phi(c) = sum over faces whose stencil holds c of lambda_F M dface/dphi(c)
 //   lambda(rho phi)(c) = lambda_phi / rho,   lambda(rho)(c) -= lambda_phi phi / rho
 //   gradient of M at the face += lambda_F(rho) + sum_f lambda_F(f) face_f
-// It is written as a gather: the thread of cell c and field f visits the four
-// faces per direction whose stencil can hold c, so no two threads write the
-// same value and the result does not depend on scheduling.
+// It is written as a gather: the thread of cell c visits the four faces per
+// direction whose stencil can hold c, so no two threads write the same value
+// and the result does not depend on scheduling.
 #include <type_traits>
 
 #include "adjoint_params.cuh"
@@ -20,166 +20,205 @@
 namespace asuca {
 
 template <typename T, int NF, int LIM>
-__global__ void __launch_bounds__(32 * (NF - 1)) adj_stage_kernel(const __grid_constant__ AdjStageParams<T> p) {
+__global__ void __launch_bounds__(256) adj_stage_kernel(const __grid_constant__ AdjStageParams<T> p) {
     constexpr int NT = NF - 1;
-    // A block takes 32 cells of one row at one level (the lanes) and one warp
-    // per field f + 1; the density's terms and the cross-field sums are added
-    // by warp 0 through shared memory, in field order.
-    // d face / d phi of the four stencil cells of a face for each upwind side
-    // and limiter branch, ctab[u * 16 + br * 4 + q] (u = 1 for M >= 0)
+    // A block takes a 32 x 8 tile of cells at one level.  Per field, the
+    // adjoint fluxes lambda_F M of the tile's i and j faces are formed once,
+    // from tiles of lambda and the recorded branches in shared memory, and
+    // every cell gathers the four faces per direction whose stencil holds it;
+    // the k faces of the cell's own column are taken directly.
+    constexpr int TW = 36, TH = 12, TN = TW * TH;   // tile with a halo of 2 (i: -2..33, j: -2..9)
+    constexpr int NXF = 35, NYF = 11;               // i faces i0-2..i0+32 (8 rows), j faces j0-2..j0+8 (32 columns)
     __shared__ T ctab[32];
-    __shared__ T rcs[10][32];        // 1/rho at the cell and at its faces' stencil cells
-    __shared__ T part[4][NT][32];    // per field: lphi phi / rho and its M-gradient terms in x, y, z
-    const int lane = threadIdx.x, f = threadIdx.y, tid = f * 32 + lane;
-    if (tid < 32) ctab[tid] = face_coef<T>((tid >> 4) != 0, (tid >> 2) & 3, tid & 3);
-    const int i = blockIdx.x * 32 + lane, j = blockIdx.y, k = blockIdx.z;
+    __shared__ T sMU[TN], sMV[TN], sRI[TN];         // MU, MV and 1/rho over the tile
+    __shared__ T sL[TN], sP[TN];                    // lambda and phi of the current field
+    __shared__ uint8_t sB[TN];                      // its branch bytes
+    __shared__ T sWx[8 * NXF], sWy[NYF * 32];       // lambda_F M of the i and j faces
+    __shared__ uint8_t sCx[8 * NXF], sCy[NYF * 32]; // their (upwind side, branch) as u * 4 + br
+    const int lane = threadIdx.x, row = threadIdx.y, tid = row * 32 + lane;
+    const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 8, k = blockIdx.z;
     const int nx = p.nx, ny = p.ny, nz = p.nz;
-    const bool valid = i < nx;
+    const int i = i0 + lane, j = j0 + row;
+    const bool valid = i < nx && j < ny;
     // offsets within a field fit in 32 bits (the host checks)
     const unsigned plane = (unsigned)p.plane, ysp = (unsigned)p.ys_plane;
-    // planar offsets (caller layout) of the cells i-2..i+2 (row j) and j-2..j+2
-    // (column i), and the same cells in the layout of the stage input
-    // (the neighbours are at most 2 cells away and nx, ny >= 4, so one add or
-    // subtract wraps them)
-    unsigned ox[5], oy[5], sx[5], sy[5];
-    const unsigned yrow = (unsigned)(j * nx), srow = (unsigned)((j + p.ys_oy) * p.ys_pitch + p.ys_ox);
-    const unsigned spitch = (unsigned)p.ys_pitch;
-#pragma unroll
-    for (int q = 0; q < 5; q++) {
-        int ix = i + q - 2, jy = j + q - 2;
-        ix = ix < 0 ? ix + nx : (ix >= nx ? ix - nx : ix);
-        jy = jy < 0 ? jy + ny : (jy >= ny ? jy - ny : jy);
-        ox[q] = yrow + (unsigned)ix;
-        oy[q] = (unsigned)(jy * nx + i);
-        sx[q] = srow + (unsigned)ix;
-        sy[q] = (unsigned)(jy + p.ys_oy) * spitch + (unsigned)(i + p.ys_ox);
-    }
     const unsigned kb = (unsigned)k * plane, skb = (unsigned)k * ysp;
-    const unsigned own = kb + ox[2];
-    // stencil cells of the cell's own +1/2 faces in the stage input
-    const unsigned zm1 = (unsigned)(k > 0 ? k - 1 : 0) * ysp + sx[2];
-    const unsigned zp1 = (unsigned)(k + 1 < nz ? k + 1 : nz - 1) * ysp + sx[2];
-    const unsigned zp2 = (unsigned)(k + 2 < nz ? k + 2 : nz - 1) * ysp + sx[2];
     const bool sphi = p.ys_phi != 0;
-    const T *R0 = p.ys[0];
-    // reciprocals of rho, dealt to the warps: phi as the forward stage saw it is
-    // stored as phi in the padded stage buffers, as rho*phi in the caller layout
+    const T cs = p.cs, rdx = p.rdx, rdy = p.rdy;
+    if (tid < 32) ctab[tid] = face_coef<T>((tid >> 4) != 0, (tid >> 2) & 3, tid & 3);
+    // the tile cells this thread loads (caller layout and stage-input layout offsets)
+    constexpr int PER = (TN + 255) / 256;
+    unsigned to[PER], ts[PER];
+#pragma unroll
+    for (int q = 0; q < PER; q++) {
+        const int c = tid + q * 256;
+        to[q] = ts[q] = 0;
+        if (c < TN) {
+            const int ii = wrap_index(i0 - 2 + c % TW, nx), jj = wrap_index(j0 - 2 + c / TW, ny);
+            to[q] = kb + (unsigned)(jj * nx + ii);
+            ts[q] = skb + (unsigned)((jj + p.ys_oy) * p.ys_pitch + ii + p.ys_ox);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < PER; q++) {
+        const int c = tid + q * 256;
+        if (c < TN) {
+            sMU[c] = p.mu[to[q]];
+            sMV[c] = p.mv[to[q]];
+            sRI[c] = recip(p.ys[0][ts[q]]);
+        }
+    }
+    const int cc = (row + 2) * TW + lane + 2;       // the thread's cell in the tile
+    const unsigned own = kb + (unsigned)(j * nx + i);
+    const unsigned sown = skb + (unsigned)((j + p.ys_oy) * p.ys_pitch + i + p.ys_ox);
+    // the cell's own column: k faces a = k-2 .. k+1 and the stencil of face k+1/2
+    T mzf[4];
+    T rz[3];
+    const unsigned zm1 = (unsigned)(k > 0 ? k - 1 : 0) * ysp - skb + sown;
+    const unsigned zp1 = (unsigned)(k + 1 < nz ? k + 1 : nz - 1) * ysp - skb + sown;
+    const unsigned zp2 = (unsigned)(k + 2 < nz ? k + 2 : nz - 1) * ysp - skb + sown;
     if (valid) {
-        const unsigned at[10] = {skb + sx[2], skb + sx[1], skb + sx[3], skb + sx[4], skb + sy[1],
-                                 skb + sy[3], skb + sy[4], zm1, zp1, zp2};
-        for (int q = f; q < (sphi ? 1 : 10); q += NT) rcs[q][lane] = recip(R0[at[q]]);
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const int a = k + q - 2;
+            mzf[q] = (a >= 0 && a <= nz - 2) ? p.mw[(unsigned)(a + 1) * plane + own - kb] : T(0);
+        }
+        if (!sphi) {
+            rz[0] = recip(p.ys[0][zm1]);
+            rz[1] = recip(p.ys[0][zp1]);
+            rz[2] = recip(p.ys[0][zp2]);
+        }
     }
     __syncthreads();
-    if (valid) {
-        const T cs = p.cs, rdx = p.rdx, rdy = p.rdy;
-        const T rr = rcs[0][lane];
-        // mass fluxes of the four faces per direction that touch cell c; face a+1/2 is stored at cell a
-        T mxf[4], myf[4], mzf[4];
-#pragma unroll
-        for (int q = 0; q < 4; q++) {
-            mxf[q] = p.mu[kb + ox[q]];
-            myf[q] = p.mv[kb + oy[q]];
-            const int a = k + q - 2;
-            mzf[q] = (a >= 0 && a <= nz - 2) ? p.mw[(unsigned)(a + 1) * plane + ox[2]] : T(0);
-        }
+    const T rr = sRI[cc];
+    T gx = T(0), gy = T(0), gz = T(0), vrho = T(0);
+
+    // tiles of lambda, phi and the branch bytes of field f, loaded into
+    // registers one field ahead so that the loads overlap the previous field's work
+    T nL[PER], nP[PER];
+    uint8_t nB[PER];
+    auto fetch = [&](int f) {
         const T *L = p.lam[f + 1];
+        const T *Y = p.ys[f + 1];
         const uint8_t *B = p.branch + (size_t)f * nz * plane;
-        T lx[5], ly[5], lz[5];
 #pragma unroll
-        for (int q = 0; q < 5; q++) {
-            lx[q] = L[kb + ox[q]];
-            ly[q] = L[kb + oy[q]];
-            const int lev = k + q - 2;
-            lz[q] = (lev >= 0 && lev < nz) ? L[(unsigned)lev * plane + ox[2]] : T(0);
+        for (int q = 0; q < PER; q++) {
+            const int c = tid + q * 256;
+            if (c < TN) {
+                nL[q] = L[to[q]];
+                nP[q] = Y[ts[q]];
+                nB[q] = B[to[q]];
+            }
         }
-        T lphi = T(0);
-        // i direction: faces a = i-2 .. i+1; cell c is stencil member 3, 2, 1, 0 of them
+    };
+    fetch(0);
+    for (int f = 0; f < NT; f++) {
+        const T *L = p.lam[f + 1];
+        const T *Y = p.ys[f + 1];
+        const uint8_t *B = p.branch + (size_t)f * nz * plane;
 #pragma unroll
-        for (int q = 0; q < 4; q++) {
-            const T lF = cs * (lx[q + 1] - lx[q]) * rdx;
-            const int br = B[kb + ox[q]] & 3;
-            lphi += lF * mxf[q] * ctab[(mxf[q] >= T(0) ? 16 : 0) + br * 4 + (3 - q)];
+        for (int q = 0; q < PER; q++) {
+            const int c = tid + q * 256;
+            if (c < TN) {
+                sL[c] = nL[q];
+                sP[c] = sphi ? nP[q] : nP[q] * sRI[c];
+                sB[c] = nB[q];
+            }
         }
-        // j direction
-#pragma unroll
-        for (int q = 0; q < 4; q++) {
-            const T lF = cs * (ly[q + 1] - ly[q]) * rdy;
-            const int br = (B[kb + oy[q]] >> 2) & 3;
-            lphi += lF * myf[q] * ctab[(myf[q] >= T(0) ? 16 : 0) + br * 4 + (3 - q)];
+        __syncthreads();
+        if (f + 1 < NT) fetch(f + 1);
+        // ---- lambda_F M of the tile's faces, once each
+        for (int t = tid; t < 8 * NXF + NYF * 32; t += 256) {
+            if (t < 8 * NXF) {          // i face a = i0 - 2 + x at row r (cells x, x+1 of tile row r+2)
+                const int r = t / NXF, x = t % NXF, c = (r + 2) * TW + x;
+                const T m = sMU[c];
+                sWx[t] = cs * (sL[c + 1] - sL[c]) * rdx * m;
+                sCx[t] = (uint8_t)((m >= T(0) ? 4 : 0) | (sB[c] & 3));
+            } else {                    // j face b = j0 - 2 + y at column x (cells y, y+1 of tile column x+2)
+                const int t2 = t - 8 * NXF, y = t2 / 32, x = t2 % 32, c = y * TW + x + 2;
+                const T m = sMV[c];
+                sWy[t2] = cs * (sL[c + TW] - sL[c]) * rdy * m;
+                sCy[t2] = (uint8_t)((m >= T(0) ? 4 : 0) | ((sB[c] >> 2) & 3));
+            }
         }
-        // k direction: faces a = k-2 .. k+1 that exist; next to a lid the ghost
-        // levels fold several stencil members into the boundary cell
+        __syncthreads();
+        if (valid) {
+            T lphi = T(0);
+            // i direction: faces a = i-2 .. i+1 (tile face index lane .. lane+3); c is member 3-q
 #pragma unroll
-        for (int q = 0; q < 4; q++) {
-            const int a = k + q - 2;
-            if (a < 0 || a > nz - 2) continue;
-            const T lF = cs * (lz[q + 1] * p.rdz[a + 1] - lz[q] * p.rdz[a]);
-            const int br = (B[(unsigned)a * plane + ox[2]] >> 4) & 3;
-            const T *ct = ctab + (mzf[q] >= T(0) ? 16 : 0) + br * 4;
-            T cf;
-            if (a >= 1 && a + 2 <= nz - 1) {
-                cf = ct[3 - q];
-            } else {
-                cf = T(0);
+            for (int q = 0; q < 4; q++) {
+                const int t = row * NXF + lane + q;
+                lphi += sWx[t] * ctab[sCx[t] * 4 + (3 - q)];
+            }
+            // j direction
 #pragma unroll
-                for (int m = 0; m < 4; m++) {
-                    int cell = a + m - 1;
-                    cell = cell < 0 ? 0 : (cell > nz - 1 ? nz - 1 : cell);
-                    if (cell == k) cf += ct[m];
+            for (int q = 0; q < 4; q++) {
+                const int t = (row + q) * 32 + lane;
+                lphi += sWy[t] * ctab[sCy[t] * 4 + (3 - q)];
+            }
+            // k direction: faces a = k-2 .. k+1 that exist; next to a lid the ghost
+            // levels fold several stencil members into the boundary cell
+            T lz[5];
+#pragma unroll
+            for (int q = 0; q < 5; q++) {
+                const int lev = k + q - 2;
+                lz[q] = (lev >= 0 && lev < nz) ? L[(unsigned)lev * plane + own - kb] : T(0);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const int a = k + q - 2;
+                if (a < 0 || a > nz - 2) continue;
+                const T lF = cs * (lz[q + 1] * p.rdz[a + 1] - lz[q] * p.rdz[a]);
+                const int br = (B[(unsigned)a * plane + own - kb] >> 4) & 3;
+                const T *ct = ctab + (mzf[q] >= T(0) ? 16 : 0) + br * 4;
+                T cf;
+                if (a >= 1 && a + 2 <= nz - 1) {
+                    cf = ct[3 - q];
+                } else {
+                    cf = T(0);
+#pragma unroll
+                    for (int m = 0; m < 4; m++) {
+                        int cell = a + m - 1;
+                        cell = cell < 0 ? 0 : (cell > nz - 1 ? nz - 1 : cell);
+                        if (cell == k) cf += ct[m];
+                    }
+                }
+                lphi += lF * mzf[q] * cf;
+            }
+            // gradient of M at the cell's own faces, this field's share
+            const T ph = sP[cc];
+            {
+                const T mx = sMU[cc], my = sMV[cc];
+                const T fx = face_val4<LIM>(sP[cc - 1], ph, sP[cc + 1], sP[cc + 2], mx >= T(0));
+                gx += cs * (sL[cc + 1] - sL[cc]) * rdx * fx;
+                const T fy = face_val4<LIM>(sP[cc - TW], ph, sP[cc + TW], sP[cc + 2 * TW], my >= T(0));
+                gy += cs * (sL[cc + TW] - sL[cc]) * rdy * fy;
+                if (k <= nz - 2) {
+                    const T fz = sphi ? face_val4<LIM>(Y[zm1], ph, Y[zp1], Y[zp2], mzf[2] >= T(0))
+                                      : face_val4<LIM>(Y[zm1] * rz[0], ph, Y[zp1] * rz[1], Y[zp2] * rz[2],
+                                                       mzf[2] >= T(0));
+                    gz += cs * (lz[3] * p.rdz[k + 1] - lz[2] * p.rdz[k]) * fz;
                 }
             }
-            lphi += lF * mzf[q] * cf;
-        }
-        // this field's share of the gradient of M at the cell's own faces
-        const T *Y = p.ys[f + 1];
-        const T ph = sphi ? Y[skb + sx[2]] : Y[skb + sx[2]] * rr;
-        T gx, gy, gz = T(0);
-        {
-            const T fx = sphi ? face_val4<LIM>(Y[skb + sx[1]], ph, Y[skb + sx[3]], Y[skb + sx[4]], mxf[2] >= T(0))
-                              : face_val4<LIM>(Y[skb + sx[1]] * rcs[1][lane], ph, Y[skb + sx[3]] * rcs[2][lane],
-                                               Y[skb + sx[4]] * rcs[3][lane], mxf[2] >= T(0));
-            gx = cs * (lx[3] - lx[2]) * rdx * fx;
-            const T fy = sphi ? face_val4<LIM>(Y[skb + sy[1]], ph, Y[skb + sy[3]], Y[skb + sy[4]], myf[2] >= T(0))
-                              : face_val4<LIM>(Y[skb + sy[1]] * rcs[4][lane], ph, Y[skb + sy[3]] * rcs[5][lane],
-                                               Y[skb + sy[4]] * rcs[6][lane], myf[2] >= T(0));
-            gy = cs * (ly[3] - ly[2]) * rdy * fy;
-            if (k <= nz - 2) {
-                const T fz = sphi ? face_val4<LIM>(Y[zm1], ph, Y[zp1], Y[zp2], mzf[2] >= T(0))
-                                  : face_val4<LIM>(Y[zm1] * rcs[7][lane], ph, Y[zp1] * rcs[8][lane],
-                                                   Y[zp2] * rcs[9][lane], mzf[2] >= T(0));
-                gz = cs * (lz[3] * p.rdz[k + 1] - lz[2] * p.rdz[k]) * fz;
+            // the field's output
+            const T v = lphi * rr;
+            if (p.out1[0]) p.out1[f + 1][own] = v;
+            if (p.out2[0]) {
+                T o = v;
+                if (p.base2[0]) o += p.base2[f + 1][own];
+                if (p.add_self) o += lz[2];
+                p.out2[f + 1][own] = o;
             }
+            vrho -= lphi * ph * rr;
         }
-        // the field's output
-        const T v = lphi * rr;
-        if (p.out1[0]) p.out1[f + 1][own] = v;
-        if (p.out2[0]) {
-            T o = v;
-            if (p.base2[0]) o += p.base2[f + 1][own];
-            if (p.add_self) o += L[own];
-            p.out2[f + 1][own] = o;
-        }
-        part[0][f][lane] = lphi * ph * rr;
-        part[1][f][lane] = gx;
-        part[2][f][lane] = gy;
-        part[3][f][lane] = gz;
+        __syncthreads();   // the tiles are reloaded for the next field
     }
-    __syncthreads();
-    // ---- warp 0: the density's output and the gradients of the cell's own faces
-    if (f == 0 && valid) {
-        const T cs = p.cs;
-        const T m0 = p.lam[0][own], mxp = p.lam[0][kb + ox[3]], myp = p.lam[0][kb + oy[3]];
-        T gx = cs * (mxp - m0) * p.rdx;
-        T gy = cs * (myp - m0) * p.rdy;
-        T gz = (k <= nz - 2) ? cs * (p.lam[0][own + plane] * p.rdz[k + 1] - m0 * p.rdz[k]) : T(0);
-        T vrho = T(0);
-#pragma unroll
-        for (int q = 0; q < NT; q++) {
-            vrho -= part[0][q][lane];
-            gx += part[1][q][lane];
-            gy += part[2][q][lane];
-            gz += part[3][q][lane];
-        }
+    // ---- density: its output and its terms of the gradients of the cell's own faces
+    if (valid) {
+        const T m0 = p.lam[0][own];
+        gx += cs * (p.lam[0][own - (unsigned)i + (unsigned)wrap_index(i + 1, nx)] - m0) * rdx;
+        gy += cs * (p.lam[0][kb + (unsigned)(wrap_index(j + 1, ny) * nx + i)] - m0) * rdy;
+        if (k <= nz - 2) gz += cs * (p.lam[0][own + plane] * p.rdz[k + 1] - m0 * p.rdz[k]);
         p.gmu[own] += gx;
         p.gmv[own] += gy;
         if (k <= nz - 2) p.gmw[own + plane] += gz;
@@ -499,8 +538,8 @@ __global__ void __launch_bounds__(32 * (NF - 1)) adj_column_kernel(const __grid_
 
 template <typename T, int NF, int LIM>
 static cudaError_t launch_adj_stage_lim(const AdjStageParams<T> &p, cudaStream_t s) {
-    dim3 block(32, NF - 1);
-    dim3 grid((p.nx + 31) / 32, p.ny, p.nz);
+    dim3 block(32, 8);
+    dim3 grid((p.nx + 31) / 32, (p.ny + 7) / 8, p.nz);
     adj_stage_kernel<T, NF, LIM><<<grid, block, 0, s>>>(p);
     return cudaGetLastError();
 }
