@@ -234,8 +234,7 @@ __global__ void __launch_bounds__(256) adj_stage_kernel(const __grid_constant__ 
 
 // ------------------------------------------------------------------ column transpose
 
-// Per column: recompute the forward relaxation and sedimentation and the
-// diffusion solution phi_f, then apply the transposes in reverse order:
+// Per column, the transposes of the column pass in reverse order:
 //   diffusion:  psi = A^{-1} (rho lambda_u)  (A is symmetric),
 //               lambda_x = dz psi,
 //               lambda_rho_k += lambda_u phi - dz psi phi - sum over the faces of k of
@@ -244,38 +243,37 @@ __global__ void __launch_bounds__(256) adj_stage_kernel(const __grid_constant__ 
 //                               lambda_k = nu_k dz_k w_k,  w_k = 1/(dz_k + dt v);
 //   relaxation:  lambda_rho += lambda_rhotheta r theta_ref / (1 + r),
 //                lambda_rhotheta /= (1 + r).
+// The factorisation of A (m, alpha, gamma per level, with the scaled
+// unknowns of the forward pass) and the forward solution (z per field, phi
+// = dz m z) come from the record the forward column pass of the same step
+// left (ColumnParams::rec), so only the transposed solve runs here.
 // A block takes 32 columns (the lanes) and one warp per field (rho*theta and
-// each tracer), so the fields' FP64 recurrences run in separate warps:
-//   A. warp 0 factorises the diffusion matrix of each column (s = dz m,
-//      alpha, gamma);
-//   B. the warp of field f recomputes its forward solve phi_f, runs the
-//      transposed solve, writes the field's adjoint and leaves its share of the
-//      lambda_rho increment per level in the scratch;
-//   C. the warps, dealt levels round-robin, add the shares to lambda_rho in
-//      field order (a fixed order, so the result does not depend on scheduling).
-// Both sweeps of both solves run in double in both precisions.  With float
+// each tracer): the warp of field f runs the transposed solve, writes the
+// field's adjoint and leaves its share of the lambda_rho increment per level
+// in the scratch; then the warps, dealt levels round-robin, add the shares to
+// lambda_rho in field order (a fixed order, so the result does not depend on
+// scheduling).  Both sweeps run in double in both precisions.  With float
 // fields the arithmetic around them is float, as in the forward step: the
-// transposed right-hand side rho lambda / dz is formed in float and widened,
-// and the lambda_rho shares are products of the double differences rounded
-// to float once.
-// Scratch per column and level: s, alpha, gamma, then per field the
-// elimination value (reused for the field's lambda_rho share) and phi_f
-// (reused for the relaxation share of rho*theta).
+// right-hand side rho lambda / dz is formed in float and widened, and the
+// lambda_rho shares are products of the double differences rounded to float
+// once.  Scratch per column and level: per field the elimination value
+// (reused for the field's lambda_rho share), and the relaxation share.
 template <typename T, int NF>
 __global__ void __launch_bounds__(32 * (NF - 1)) adj_column_kernel(const __grid_constant__ AdjColParams<T> a) {
     constexpr int NT = NF - 1;
     constexpr int NQ = 3 + 2 * NT;
+    constexpr int NR = NF + 2;                      // record entries per level: m, alpha, gamma, z[NT]
     constexpr bool F32 = std::is_same<T, float>::value;
     const ColumnParams<T> &p = a.c;
     const int lane = threadIdx.x, f = threadIdx.y;   // f: field f + 1 of the state
     const long long plane = p.plane;
+    const size_t pl = (size_t)plane;
     const long long nslots = (long long)gridDim.x * 32;
     const int nz = p.nz;
     double *const sc = p.scratch + (long long)blockIdx.x * 32 + lane;
 #define S(k, q) sc[(long long)((k) * NQ + (q)) * nslots]
-    const int qe = 3 + f, qp = 3 + NT + f;           // this field's elimination / share slot and phi slot
+    const int qe = 3 + f, qr = 3 + NT;               // this field's elimination / share slot; relaxation share
     const bool is_th = f == 0, is_sed = p.do_sed && (f + 1 == p.sed);
-    const T *Y = p.y[f + 1];
     const T *R = p.y[0];
     T *lam = a.lam[f + 1];
     const double sv = to_f64(p.sed_v), rr = to_f64(p.relax_r), ri = to_f64(p.relax_inv);
@@ -283,112 +281,42 @@ __global__ void __launch_bounds__(32 * (NF - 1)) adj_column_kernel(const __grid_
     for (long long c0 = (long long)blockIdx.x * 32; c0 < plane; c0 += nslots) {
         const long long col = c0 + lane;
         const bool valid = col < plane;
-        __syncthreads();   // the previous group's phase C is done with the scratch
-        // ---- A: factorisation, top-down (warp 0); every sweep below loads the
-        // next level's inputs before it works on the current one
-        if (p.do_diff && f == 0 && valid) {
-            double g_hi = 0.0, m_up = 0.0;
-            long long o = (long long)(nz - 1) * plane + col;
-            T r = R[o], rdn = R[o - plane];
-            for (int k = nz - 1; k >= 0; k--, o -= plane) {
-                const T rdn2 = (k > 1) ? R[o - 2 * plane] : T(0);
-                const double rd = to_f64(r);
-                const double g_lo = (k > 0) ? p.kc[k - 1] * (to_f64(rdn) + rd) : 0.0;
-                const double b = rd * p.dz[k] + (g_lo + g_hi);
-                const double t = g_hi * m_up;
-                const double m = rcp_newton(fma(-g_hi, t, b));
-                S(k, 0) = p.dz[k] * m;
-                S(k, 1) = t * p.dzr_up[k];
-                if (k < nz - 1) S(k + 1, 2) = g_hi * m * p.dzr_dn[k + 1];
-                g_hi = g_lo;
-                m_up = m;
-                r = rdn;
-                rdn = rdn2;
-            }
-        }
-        __syncthreads();
-        // ---- B: this warp's field
+        const double *rc = p.rec + col;
+#define RC(k, q) rc[(size_t)((k) * NR + (q)) * pl]
+        __syncthreads();   // the previous group's shares have been added
         if (valid) {
             if (p.do_diff) {
-                // forward: relaxation / sedimentation of the field, elimination top-down
-                double e_up = 0.0;
-                T P = T(0);
+                // transpose of the diffusion: elimination top-down on rho lambda / dz
+                double eu = 0.0;
                 long long o = (long long)(nz - 1) * plane + col;
-                double al = S(nz - 1, 1);
-                T x = Y[o], rho = (is_th && p.do_relax) ? R[o] : T(1);
+                double al = RC(nz - 1, 1);
+                T r = R[o], l = lam[o];
                 for (int k = nz - 1; k >= 0; k--, o -= plane) {
                     double al_n = 0.0;
-                    T x_n = T(0), rho_n = T(1);
+                    T r_n = T(0), l_n = T(0);
                     if (k > 0) {
-                        al_n = S(k - 1, 1);
-                        x_n = Y[o - plane];
-                        if (is_th && p.do_relax) rho_n = R[o - plane];
+                        al_n = RC(k - 1, 1);
+                        r_n = R[o - plane];
+                        l_n = lam[o - plane];
                     }
-                    if (is_th && p.do_relax) {
-                        T th = x / rho;
-                        th = (th + p.relax_r * p.thref[k]) * p.relax_inv;
-                        x = rho * th;
-                    }
-                    if (is_sed) {
-                        x = (x * p.dzT[k] + p.sed_dt * P) * p.sedr[k];
-                        P = p.sed_v * x;
-                    }
-                    e_up = fma(al, e_up, to_f64(x));
-                    S(k, qe) = e_up;
+                    double rhs;
+                    if constexpr (F32) rhs = to_f64(r * p.rdzT[k] * l);
+                    else rhs = to_f64(r) * p.rdz64[k] * to_f64(l);
+                    eu = fma(al, eu, rhs);
+                    S(k, qe) = eu;
                     al = al_n;
-                    x = x_n;
-                    rho = rho_n;
-                }
-                // back substitution bottom-up: phi_f = s z
-                {
-                    double z = 0.0, gk = 0.0, ek = S(0, qe), sk = S(0, 0);
-                    for (int k = 0; k < nz; k++) {
-                        double gn = 0.0, en = 0.0, sn = 0.0;
-                        if (k + 1 < nz) {
-                            gn = S(k + 1, 2);
-                            en = S(k + 1, qe);
-                            sn = S(k + 1, 0);
-                        }
-                        z = fma(gk, z, ek);
-                        S(k, qp) = sk * z;
-                        gk = gn;
-                        ek = en;
-                        sk = sn;
-                    }
-                }
-                // transpose of the diffusion: elimination top-down on rho lambda / dz
-                {
-                    double eu = 0.0;
-                    o = (long long)(nz - 1) * plane + col;
-                    al = S(nz - 1, 1);
-                    T r = R[o], l = lam[o];
-                    for (int k = nz - 1; k >= 0; k--, o -= plane) {
-                        double al_n = 0.0;
-                        T r_n = T(0), l_n = T(0);
-                        if (k > 0) {
-                            al_n = S(k - 1, 1);
-                            r_n = R[o - plane];
-                            l_n = lam[o - plane];
-                        }
-                        double rhs;
-                        if constexpr (F32) rhs = to_f64(r * p.rdzT[k] * l);
-                        else rhs = to_f64(r) * p.rdz64[k] * to_f64(l);
-                        eu = fma(al, eu, rhs);
-                        S(k, qe) = eu;
-                        al = al_n;
-                        r = r_n;
-                        l = l_n;
-                    }
+                    r = r_n;
+                    l = l_n;
                 }
             }
             // bottom-up: transposed back substitution, the field's lambda_rho
             // shares, then the sedimentation and relaxation transposes
             double zp = 0.0, psi_prev = 0.0, phi_prev = 0.0;
-            double gk = 0.0, ek = 0.0, sk = 0.0, phk = 0.0;
+            double gk = 0.0, ek = 0.0, mk = 0.0, zk = 0.0;
             if (p.do_diff) {
                 ek = S(0, qe);
-                sk = S(0, 0);
-                phk = S(0, qp);
+                mk = RC(0, 0);
+                zk = RC(0, 3 + f);
             }
             T lk = lam[col];
             long long o = col;
@@ -396,23 +324,24 @@ __global__ void __launch_bounds__(32 * (NF - 1)) adj_column_kernel(const __grid_
                 float carry = 0.f, nu_prev = 0.f;
                 const float svf = p.sed_v, rrf = p.relax_r, rif = p.relax_inv, dtf = p.sed_dt;
                 for (int k = 0; k < nz; k++, o += plane) {
-                    double gn = 0.0, en = 0.0, sn = 0.0, pn = 0.0;
+                    double gn = 0.0, en = 0.0, mn = 0.0, zn = 0.0;
                     T ln = T(0);
                     if (k + 1 < nz) {
                         if (p.do_diff) {
-                            gn = S(k + 1, 2);
+                            gn = RC(k + 1, 2);
                             en = S(k + 1, qe);
-                            sn = S(k + 1, 0);
-                            pn = S(k + 1, qp);
+                            mn = RC(k + 1, 0);
+                            zn = RC(k + 1, 3 + f);
                         }
                         ln = lam[o + plane];
                     }
                     float lout;
                     bool write = false;
                     if (p.do_diff) {
+                        const double sk = p.dz[k] * mk;
                         zp = fma(gk, zp, ek);
                         const double psi = sk * zp;
-                        const double ph = phk;
+                        const double ph = sk * zk;
                         // A = (lambda_u - dz psi) phi, B = (dg/drho)(psi - psi_prev)(phi - phi_prev)
                         const float A = d2f_bits(fma(-p.dz[k], psi, to_f64(lk))) * d2f_bits(ph);
                         const float B = k > 0 ? p.kcT[k - 1] * d2f_bits(psi - psi_prev) * d2f_bits(ph - phi_prev) : 0.f;
@@ -434,29 +363,29 @@ __global__ void __launch_bounds__(32 * (NF - 1)) adj_column_kernel(const __grid_
                         write = true;
                     }
                     if (is_th && p.do_relax) {
-                        S(k, qp) = f2d_bits_any(lout * rrf * p.thref[k] * rif);   // relaxation share
+                        S(k, qr) = f2d_bits_any(lout * rrf * p.thref[k] * rif);   // relaxation share
                         lout = lout * rif;
                         write = true;
                     }
                     if (write) lam[o] = lout;
                     gk = gn;
                     ek = en;
-                    sk = sn;
-                    phk = pn;
+                    mk = mn;
+                    zk = zn;
                     lk = ln;
                 }
                 if (p.do_diff) S(nz - 1, qe) = f2d_bits_any(carry);
             } else {
                 double carry = 0.0, nu_prev = 0.0;
                 for (int k = 0; k < nz; k++, o += plane) {
-                    double gn = 0.0, en = 0.0, sn = 0.0, pn = 0.0;
+                    double gn = 0.0, en = 0.0, mn = 0.0, zn = 0.0;
                     T ln = T(0);
                     if (k + 1 < nz) {
                         if (p.do_diff) {
-                            gn = S(k + 1, 2);
+                            gn = RC(k + 1, 2);
                             en = S(k + 1, qe);
-                            sn = S(k + 1, 0);
-                            pn = S(k + 1, qp);
+                            mn = RC(k + 1, 0);
+                            zn = RC(k + 1, 3 + f);
                         }
                         ln = lam[o + plane];
                     }
@@ -464,9 +393,10 @@ __global__ void __launch_bounds__(32 * (NF - 1)) adj_column_kernel(const __grid_
                     bool write = false;
                     if (p.do_diff) {
                         const double kcl = k > 0 ? p.kc[k - 1] : 0.0;
+                        const double sk = p.dz[k] * mk;
                         zp = fma(gk, zp, ek);
                         const double psi = sk * zp;
-                        const double ph = phk;
+                        const double ph = sk * zk;
                         const double lu = to_f64(lk);
                         const double A = (lu - p.dz[k] * psi) * ph;
                         const double B = kcl * (psi - psi_prev) * (ph - phi_prev);   // face k-1/2
@@ -488,22 +418,23 @@ __global__ void __launch_bounds__(32 * (NF - 1)) adj_column_kernel(const __grid_
                         write = true;
                     }
                     if (is_th && p.do_relax) {
-                        S(k, qp) = lout * rr * to_f64(p.thref[k]) * ri;   // relaxation share of lambda_rho
+                        S(k, qr) = lout * rr * to_f64(p.thref[k]) * ri;   // relaxation share of lambda_rho
                         lout = lout * ri;
                         write = true;
                     }
                     if (write) lam[o] = from_f64<T>(lout);
                     gk = gn;
                     ek = en;
-                    sk = sn;
-                    phk = pn;
+                    mk = mn;
+                    zk = zn;
                     lk = ln;
                 }
                 if (p.do_diff) S(nz - 1, qe) = carry;
             }
         }
+#undef RC
         __syncthreads();
-        // ---- C: lambda_rho, levels dealt to the warps
+        // ---- lambda_rho, levels dealt to the warps
         if (valid) {
             for (int k = f; k < nz; k += NT) {
                 const long long o = (long long)k * plane + col;
@@ -515,7 +446,7 @@ __global__ void __launch_bounds__(32 * (NF - 1)) adj_column_kernel(const __grid_
                         for (int q = 0; q < NT; q++) inc += d2f_bits(S(k, 3 + q));
                         lrho += inc;
                     }
-                    if (p.do_relax) lrho += d2f_bits(S(k, 3 + NT));
+                    if (p.do_relax) lrho += d2f_bits(S(k, qr));
                     a.lam[0][o] = lrho;
                 } else {
                     double lrho = to_f64(a.lam[0][o]);
@@ -525,7 +456,7 @@ __global__ void __launch_bounds__(32 * (NF - 1)) adj_column_kernel(const __grid_
                         for (int q = 0; q < NT; q++) inc += S(k, 3 + q);
                         lrho += inc;
                     }
-                    if (p.do_relax) lrho += S(k, 3 + NT);
+                    if (p.do_relax) lrho += S(k, qr);
                     a.lam[0][o] = from_f64<T>(lrho);
                 }
             }

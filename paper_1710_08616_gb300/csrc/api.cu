@@ -520,7 +520,8 @@ asuca_status run_step_dataflow(asuca_grid *g, asuca_state *st, const void *tend,
 // ---- adjoint -------------------------------------------------------------
 
 struct AdjLayout {
-    size_t step, W, ckpt, segYn, segY1, segY2, segY3, branch, lam, l2, l1, acc, scratch, total;
+    size_t step, W, ckpt, segYn, segY1, segY2, segY3, branch, rec, lam, l2, l1, acc, scratch, total;
+    size_t nrec_step;
     int ncp;
     size_t ustate, pstate, nbranch_step;
     long long slots;
@@ -565,6 +566,10 @@ AdjLayout adj_layout(const asuca_grid *g, int nsteps, int K) {
     off = align_up(off + (size_t)K * align_up(L.ustate));
     L.branch = off;
     off = align_up(off + (size_t)K * align_up(L.nbranch_step));
+    // per recorded step: the column pass's factorisation and solution, [nz][F + 2][ny][nx] doubles
+    L.nrec_step = (size_t)g->d.nz * (g->F + 2) * (size_t)g->plane * sizeof(double);
+    L.rec = off;
+    off = align_up(off + (g->d.k0 > 0.0 ? (size_t)K * align_up(L.nrec_step) : 0));
     L.lam = off;
     off = align_up(off + L.ustate);
     L.l2 = off;
@@ -662,6 +667,7 @@ asuca_status run_adjoint(asuca_grid *g, const asuca_state *init, const void *ten
         auto segY1 = [&](int q) { return ws + L.segY1 + (size_t)q * align_up(L.pstate); };
         auto segY2 = [&](int q) { return ws + L.segY2 + (size_t)q * align_up(L.pstate); };
         auto segY3 = [&](int q) { return ws + L.segY3 + (size_t)q * align_up(L.ustate); };
+        auto rec = [&](int q) { return (double *)(ws + L.rec + (size_t)q * align_up(L.nrec_step)); };
         auto brs = [&](int q, int stg) {
             return (uint8_t *)(ws + L.branch + (size_t)q * align_up(L.nbranch_step)) +
                    (size_t)stg * (F - 1) * g->cells;
@@ -700,6 +706,7 @@ asuca_status run_adjoint(asuca_grid *g, const asuca_state *init, const void *ten
             cp.partials = (double *)(sws + SL.partials);
             cp.scratch = (double *)(sws + SL.scratch);
             cp.budgets = 0;
+            cp.rec = cp.do_diff ? rec(q) : nullptr;
             if (e != cudaSuccess ||
                 timed(g, ASUCA_KERNEL_COLUMN, s, [&] { return launch_column<T>(cp, F, g->col_grid, COL_TPB, s); }) !=
                     cudaSuccess)
@@ -713,6 +720,7 @@ asuca_status run_adjoint(asuca_grid *g, const asuca_state *init, const void *ten
             block_fields<T>(g, segY3(q), ac.c.y);
             ac.c.scratch = (double *)(ws + L.scratch);
             ac.c.nslots = L.slots;
+            ac.c.rec = ac.c.do_diff ? rec(q) : nullptr;
             for (int f = 0; f < MAXF; f++) ac.lam[f] = lam[f];
             if (timed(g, ASUCA_KERNEL_ADJ_COLUMN, s, [&] { return launch_adj_column<T>(ac, F, adj_col_blocks(g), s); }) !=
                 cudaSuccess)

@@ -128,7 +128,14 @@ __device__ __forceinline__ void column_one(const ColumnParams<T> &p, long long c
                 const double m = rcp_newton(fma(-g_hi, t, b));
                 const double alpha = t * p.dzr_up[k];
                 sc[(long long)(k * NQ + 0) * nslots] = m;
-                if (k < nz - 1) sc[(long long)((k + 1) * NQ + 1) * nslots] = g_hi * m * p.dzr_dn[k + 1];
+                const double gam = (k < nz - 1) ? g_hi * m * p.dzr_dn[k + 1] : 0.0;
+                if (k < nz - 1) sc[(long long)((k + 1) * NQ + 1) * nslots] = gam;
+                if (p.rec) {   // the adjoint's record of the factorisation
+                    double *r = p.rec + col;
+                    r[(size_t)(k * (NF + 2) + 0) * plane] = m;
+                    r[(size_t)(k * (NF + 2) + 1) * plane] = alpha;
+                    if (k < nz - 1) r[(size_t)((k + 1) * (NF + 2) + 2) * plane] = gam;
+                }
 #pragma unroll
                 for (int f = 0; f < NT; f++) {
                     const double e = fma(alpha, e_up[f], to_f64(x[f]));
@@ -184,6 +191,7 @@ __device__ __forceinline__ void column_one(const ColumnParams<T> &p, long long c
 #pragma unroll
                 for (int f = 0; f < NT; f++) {
                     z[f] = fma(gk, z[f], ek[f]);
+                    if (p.rec) p.rec[(size_t)(k * (NF + 2) + 3 + f) * plane + col] = z[f];
                     const T u = scale_out<T>(z[f], sigma, sf);
                     p.y[f + 1][ob] = u;
                     if (p.budgets) cs[f + 1].add(u, p.dz[k], p.dzT[k], p.dzlo[k]);

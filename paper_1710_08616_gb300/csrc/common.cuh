@@ -84,6 +84,8 @@ struct ColumnParams {
     double *partials;       // [gridDim.x][F + 1] budget partials (sum over columns of sum_k f dz)
     double *scratch;        // [nz][F + 1][nslots]
     long long nslots;
+    double *rec;            // if set: [nz][F + 2][plane] record of the diffusion solve for the adjoint:
+                            // m, alpha, gamma of each level and the scaled solution z of each field
     T dzT[MAXNZ];           // dz_k (rounded to T)
     float dzlo[MAXNZ];      // dz_k - (float)dz_k, the low part for float budget sums
     T sedr[MAXNZ];          // 1 / (dz_k + dt v)
