@@ -10,6 +10,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "asuca.h"
 
 namespace asuca {
@@ -201,8 +203,20 @@ __device__ __forceinline__ T face_val(T c, T o, T far) {
     if (LIM == ASUCA_LIM_LINEAR) return c + fma(d1, T(1.0 / 3.0), d0 * T(1.0 / 6.0));
     const T x = sign_transfer(d1, d0);
     const T a = fabs(d0);
-    T h = fmin(fmin(x, a), fma(x, T(1.0 / 3.0), a * T(1.0 / 6.0)));
-    h = fmax(h, T(0));
+    const T t = fma(x, T(1.0 / 3.0), a * T(1.0 / 6.0));
+    T h;
+    if constexpr (std::is_same<T, double>::value) {
+        // For x > 0, x, a and t are non-negative doubles, whose order is the
+        // order of their bit patterns read as integers, so the minimum is taken
+        // on the integer pipe (the FP64 pipe bounds the double path); x <= 0
+        // gives 0.  Equal to max(0, min(x, a, t)) for every non-NaN input.
+        const long long xi = __double_as_longlong(x), ai = __double_as_longlong(a), ti = __double_as_longlong(t);
+        long long mi = xi < ai ? xi : ai;
+        mi = mi < ti ? mi : ti;
+        h = xi > 0 ? __longlong_as_double(mi) : 0.0;
+    } else {
+        h = fmax(fmin(fmin(x, a), t), T(0));
+    }
     return c + copysign(h, d0);
 }
 
