@@ -468,16 +468,18 @@ def run_ours(args):
     kern = {}
     for k, (tot, n) in (prof or {}).items():
         avg = tot / n
-        kern[kinds.get(k, str(k))] = {"launches": n, "total_ms": tot, "avg_ms": avg,
-                                      "share": tot / max(sum(v[0] for v in prof.values()), 1e-30),
-                                      "algo_bytes_per_launch": algo.get(k, 0.0),
-                                      "achieved_gbs": algo.get(k, 0.0) / (avg * 1e-3) / 1e9 if avg else None}
+        kname = kinds.get(k, str(k))
+        kern[kname] = {"launches": n, "total_ms": tot, "avg_ms": avg,
+                       "share": tot / max(sum(v[0] for v in prof.values()), 1e-30),
+                       "algo_bytes_per_launch": algo.get(k, 0.0),
+                       "achieved_gbs": algo.get(k, 0.0) / (avg * 1e-3) / 1e9 if avg else None,
+                       "traffic_bytes_per_launch": _recorded_traffic(kname, C)}
     dom = max(prof.items(), key=lambda kv: kv[1][0])[0] if prof else asuca.KERNEL_STAGE
     dname = kinds.get(dom, str(dom))
     ach = kern[dname]["achieved_gbs"] if dname in kern else None
     roofline = {"kernel": dname, "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
                 "frac": (ach / hbm_peak) if ach else None, "peak_source": peak_kind,
-                "traffic": _recorded_traffic(dname, C) if dname == "stage" else None,
+                "traffic": _recorded_traffic(dname, C),
                 "step_frac": (10 * F + 8) * s * C / (ms / args.steps * 1e-3) / 1e9 / hbm_peak,
                 "step_model_bytes_per_cell": (10 * F + 8) * s, "kernels": kern}
 
