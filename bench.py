@@ -401,6 +401,28 @@ def ensemble_throughput(asuca, dev, nsteps=10, reps=3):
             "speedup_over_sequential": t_seq / t_ens}
 
 
+def adjoint_probe(prec_name):
+    """One adjoint step (K = 1) of the 128x128x58, 4-tracer workload, twice: per call
+    3 recording stage launches, 1 column launch, 1 column transpose and 3 stage
+    transposes."""
+    import torch
+    from paper_1710_08616_gb300 import build as _b
+    _b.build()
+    import paper_1710_08616_gb300 as asuca
+    import gen
+    torch.cuda.set_device(0)
+    prec = asuca.FP64 if prec_name == "fp64" else asuca.FP32_MIXED
+    case = gen.make_config_case("adjoint_128x128x58")
+    g = asuca.Grid.from_case(case, prec=prec)
+    st = asuca.State.from_case(case, prec=prec)
+    lam = torch.randn((case.nfields,) + tuple(st.rho.shape), dtype=g.torch_dtype, device=st.rho.device)
+    for _ in range(2):
+        asuca.adjoint_step(g, st, case.dt, 1, lam.contiguous(), checkpoint_every=1)
+    torch.cuda.synchronize()
+    assert asuca.get_status(g) == asuca.OK
+    return 0
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -586,9 +608,14 @@ def main():
     ap.add_argument("--nx", type=int, default=1024,
                     help="nx = ny of the timed case; anything but 1024 is a smaller case of the same "
                          "workload for profiler captures, not a bench line")
+    ap.add_argument("--adjoint-probe", choices=["fp32", "fp64"], default=None,
+                    help="run one adjoint step of the 128x128x58 workload twice (recomputed from one "
+                         "checkpoint) and exit: a small fixed launch sequence for profiler captures")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.adjoint_probe:
+        return adjoint_probe(args.adjoint_probe)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
