@@ -276,6 +276,39 @@ __device__ __forceinline__ float2 face_flux2(float2 c, float2 o, float2 far, flo
     return __fmul2_rn(m2, __fadd2_rn(c, make_float2(copysignf(hx, d0.x), copysignf(hy, d0.y))));
 }
 
+// face_flux2 that also returns both fields' limiter branches (as face_val_br,
+// whose value it equals bit for bit).
+template <int LIM>
+__device__ __forceinline__ float2 face_flux2_br(float2 c, float2 o, float2 far, float m, int2 &br) {
+    const float2 m2 = make_float2(m, m);
+    if (LIM == ASUCA_LIM_UPWIND1) {
+        br = make_int2(0, 0);
+        return __fmul2_rn(m2, c);
+    }
+    const float2 neg1 = make_float2(-1.f, -1.f);
+    const float2 d1 = __ffma2_rn(c, neg1, o);
+    const float2 d0 = __ffma2_rn(far, neg1, c);
+    if (LIM == ASUCA_LIM_LINEAR) {
+        br = make_int2(2, 2);
+        const float2 t = __ffma2_rn(d1, make_float2(1.f / 3.f, 1.f / 3.f), __fmul2_rn(d0, make_float2(1.f / 6.f, 1.f / 6.f)));
+        return __fmul2_rn(m2, __fadd2_rn(c, t));
+    }
+    const float2 x = make_float2(sign_transfer(d1.x, d0.x), sign_transfer(d1.y, d0.y));
+    const float2 a = make_float2(fabsf(d0.x), fabsf(d0.y));
+    const float2 t = __ffma2_rn(x, make_float2(1.f / 3.f, 1.f / 3.f), __fmul2_rn(a, make_float2(1.f / 6.f, 1.f / 6.f)));
+    auto pick = [](float xv, float av, float tv, int &b) {
+        float h = xv;
+        b = 1;
+        if (tv < h) { h = tv; b = 2; }
+        if (av < h) { h = av; b = 3; }
+        if (!(xv > 0.f && av > 0.f)) { h = 0.f; b = 0; }
+        return h;
+    };
+    const float hx = pick(x.x, a.x, t.x, br.x);
+    const float hy = pick(x.y, a.y, t.y, br.y);
+    return __fmul2_rn(m2, __fadd2_rn(c, make_float2(copysignf(hx, d0.x), copysignf(hy, d0.y))));
+}
+
 // Face value at i+1/2 from the four cells i-1 .. i+2 and the upwind predicate u = (M >= 0).
 template <int LIM, typename T>
 __device__ __forceinline__ T face_val4(T pm1, T p0, T p1, T p2, bool u) {

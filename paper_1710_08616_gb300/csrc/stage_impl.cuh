@@ -312,7 +312,7 @@ __device__ __forceinline__ bool stage_tile_h(const StageParams<T> &p, const CUte
 
     const int cy = ty + 2, cx = tx + 4, cc = cy * SX + cx;
     // float stages evaluate faces and the divergence two fields at a time (FP32x2)
-    constexpr bool PACK = std::is_same<T, float>::value && !REC;
+    constexpr bool PACK = std::is_same<T, float>::value;
 
 #pragma unroll 1
     for (int t = 0; t < nz; t++) {
@@ -359,15 +359,30 @@ __device__ __forceinline__ bool stage_tile_h(const StageParams<T> &p, const CUte
 #pragma unroll
             for (int f = 0; f + 1 < NT; f += 2) {
                 const int f0 = (f + 1) * FE, f1 = (f + 2) * FE;
-                const float2 rx = face_flux2<LIM>(make_float2(Sk[f0 + xc], Sk[f1 + xc]),
-                                                  make_float2(Sk[f0 + xo], Sk[f1 + xo]),
-                                                  make_float2(Sk[f0 + xf], Sk[f1 + xf]), mup);
-                const float2 ry = face_flux2<LIM>(make_float2(Sk[f0 + yc], Sk[f1 + yc]),
-                                                  make_float2(Sk[f0 + yo], Sk[f1 + yo]),
-                                                  make_float2(Sk[f0 + yf], Sk[f1 + yf]), mvp);
-                const float2 rz = top ? make_float2(0.f, 0.f)
-                                      : face_flux2<LIM>(make_float2(zc[f0], zc[f1]), make_float2(zo[f0], zo[f1]),
-                                                        make_float2(zf[f0], zf[f1]), mwp);
+                float2 rx, ry, rz;
+                if constexpr (REC) {
+                    int2 bx, by, bz = make_int2(0, 0);
+                    rx = face_flux2_br<LIM>(make_float2(Sk[f0 + xc], Sk[f1 + xc]), make_float2(Sk[f0 + xo], Sk[f1 + xo]),
+                                            make_float2(Sk[f0 + xf], Sk[f1 + xf]), mup, bx);
+                    ry = face_flux2_br<LIM>(make_float2(Sk[f0 + yc], Sk[f1 + yc]), make_float2(Sk[f0 + yo], Sk[f1 + yo]),
+                                            make_float2(Sk[f0 + yf], Sk[f1 + yf]), mvp, by);
+                    rz = top ? make_float2(0.f, 0.f)
+                             : face_flux2_br<LIM>(make_float2(zc[f0], zc[f1]), make_float2(zo[f0], zo[f1]),
+                                                  make_float2(zf[f0], zf[f1]), mwp, bz);
+                    if (valid) {
+                        uint8_t *br = p.branch + (long long)f * nz * plane + (long long)k * plane + own;
+                        br[0] = (uint8_t)(bx.x | (by.x << 2) | (bz.x << 4));
+                        br[(long long)nz * plane] = (uint8_t)(bx.y | (by.y << 2) | (bz.y << 4));
+                    }
+                } else {
+                    rx = face_flux2<LIM>(make_float2(Sk[f0 + xc], Sk[f1 + xc]), make_float2(Sk[f0 + xo], Sk[f1 + xo]),
+                                         make_float2(Sk[f0 + xf], Sk[f1 + xf]), mup);
+                    ry = face_flux2<LIM>(make_float2(Sk[f0 + yc], Sk[f1 + yc]), make_float2(Sk[f0 + yo], Sk[f1 + yo]),
+                                         make_float2(Sk[f0 + yf], Sk[f1 + yf]), mvp);
+                    rz = top ? make_float2(0.f, 0.f)
+                             : face_flux2<LIM>(make_float2(zc[f0], zc[f1]), make_float2(zo[f0], zo[f1]),
+                                               make_float2(zf[f0], zf[f1]), mwp);
+                }
                 xp[f] = rx.x; xp[f + 1] = rx.y;
                 yp[f] = ry.x; yp[f + 1] = ry.y;
                 zp[f] = rz.x; zp[f + 1] = rz.y;
@@ -377,9 +392,17 @@ __device__ __forceinline__ bool stage_tile_h(const StageParams<T> &p, const CUte
             if (NT & 1) {
                 constexpr int f = NT - 1;
                 const int fo = (f + 1) * FE;
-                xp[f] = face_flux<LIM>(Sk[fo + xc], Sk[fo + xo], Sk[fo + xf], mup);
-                yp[f] = face_flux<LIM>(Sk[fo + yc], Sk[fo + yo], Sk[fo + yf], mvp);
-                zp[f] = top ? T(0) : face_flux<LIM>(zc[fo], zo[fo], zf[fo], mwp);
+                if constexpr (REC) {
+                    int bx, by, bz = 0;
+                    xp[f] = face_flux_br<LIM>(Sk[fo + xc], Sk[fo + xo], Sk[fo + xf], mup, bx);
+                    yp[f] = face_flux_br<LIM>(Sk[fo + yc], Sk[fo + yo], Sk[fo + yf], mvp, by);
+                    zp[f] = top ? T(0) : face_flux_br<LIM>(zc[fo], zo[fo], zf[fo], mwp, bz);
+                    if (valid) p.branch[(long long)f * nz * plane + (long long)k * plane + own] = (uint8_t)(bx | (by << 2) | (bz << 4));
+                } else {
+                    xp[f] = face_flux<LIM>(Sk[fo + xc], Sk[fo + xo], Sk[fo + xf], mup);
+                    yp[f] = face_flux<LIM>(Sk[fo + yc], Sk[fo + yo], Sk[fo + yf], mvp);
+                    zp[f] = top ? T(0) : face_flux<LIM>(zc[fo], zo[fo], zf[fo], mwp);
+                }
                 ysm[(f * (TY + 1) + ty + 1) * TX + tx] = yp[f];
             }
         } else {
