@@ -240,9 +240,20 @@ __device__ __forceinline__ T face_val_br(T c, T o, T far, int &br) {
     const T t2 = fma(x, T(1.0 / 3.0), a * T(1.0 / 6.0));
     T h = x;
     br = 1;
-    if (t2 < h) { h = t2; br = 2; }
-    if (a < h) { h = a; br = 3; }
-    if (!(x > T(0) && a > T(0))) { h = T(0); br = 0; }
+    if constexpr (std::is_same<T, double>::value) {
+        // the comparisons on the integer pipe, as in face_val: for x > 0 the
+        // operands are non-negative doubles, ordered as their bit patterns
+        const long long xi = __double_as_longlong(x), ai = __double_as_longlong(a), ti = __double_as_longlong(t2);
+        long long hi = xi;
+        if (ti < hi) { hi = ti; br = 2; }
+        if (ai < hi) { hi = ai; br = 3; }
+        h = __longlong_as_double(hi);
+        if (!(xi > 0 && ai > 0)) { h = T(0); br = 0; }
+    } else {
+        if (t2 < h) { h = t2; br = 2; }
+        if (a < h) { h = a; br = 3; }
+        if (!(x > T(0) && a > T(0))) { h = T(0); br = 0; }
+    }
     return c + copysign(h, d0);
 }
 
