@@ -299,4 +299,55 @@ struct ColDownHook {
     __device__ __forceinline__ void done(bool) {}
 };
 
+// The bottom-up half of the column pass after ColDownHook, for one column:
+// back substitution from the full-size scratch (p.scratch, [nz][F + 1][plane]),
+// (rho phi)_k = sigma_k z_k for rho*theta and every tracer (column_one's
+// bottom-up pass, operation for operation), and the column's budget partials
+// in cs when p.budgets is set.
+template <typename T, int NF>
+__device__ __forceinline__ void column_up_one(const ColumnParams<T> &p, long long col, ColSum<T> (&cs)[NF]) {
+    constexpr int NT = NF - 1;
+    constexpr int NQ = NF + 1;
+    const size_t pl = (size_t)p.plane;
+    const int nz = p.nz;
+    const double *sc = p.scratch + col;
+    double z[NT];
+#pragma unroll
+    for (int f = 0; f < NT; f++) z[f] = 0.0;
+    size_t ob = (size_t)col;
+    double mk = sc[0], gk = 0.0;
+    double ek[NT];
+#pragma unroll
+    for (int f = 0; f < NT; f++) ek[f] = sc[(size_t)(2 + f) * pl];
+    T rk = p.y[0][ob];
+    for (int k = 0; k < nz; k++, ob += pl) {
+        double mn = 0.0, gn = 0.0, en[NT];
+        T rn = T(0);
+        if (k + 1 < nz) {   // prefetch level k+1
+            mn = sc[(size_t)((k + 1) * NQ + 0) * pl];
+            gn = sc[(size_t)((k + 1) * NQ + 1) * pl];
+#pragma unroll
+            for (int f = 0; f < NT; f++) en[f] = sc[(size_t)((k + 1) * NQ + 2 + f) * pl];
+            rn = p.y[0][ob + pl];
+        }
+        const double sigma = to_f64(rk) * p.dz[k] * mk;
+        const float sf = (sizeof(T) == 4) ? (float)rk * (float)p.dzT[k] * d2f_bits(mk) : 0.f;
+        if (p.budgets) cs[0].add(rk, p.dz[k], p.dzT[k], p.dzlo[k]);
+#pragma unroll
+        for (int f = 0; f < NT; f++) {
+            z[f] = fma(gk, z[f], ek[f]);
+            const T u = scale_out<T>(z[f], sigma, sf);
+            p.y[f + 1][ob] = u;
+            if (p.budgets) cs[f + 1].add(u, p.dz[k], p.dzT[k], p.dzlo[k]);
+        }
+        if (k + 1 < nz) {
+            mk = mn;
+            gk = gn;
+#pragma unroll
+            for (int f = 0; f < NT; f++) ek[f] = en[f];
+            rk = rn;
+        }
+    }
+}
+
 }  // namespace asuca
