@@ -508,36 +508,95 @@ def run_ours(args):
     # ---- e2e through the C ABI with pinned host buffers, copies inside the timed region
     e2e = None
     if not args.no_e2e:
-        host = {k: getattr(st, k).cpu().pin_memory() for k in ("rho", "rhotheta", "rhoq", "mu", "mv", "mw")}
+        # End to end: every step copies its inputs (state and mass fluxes) from pinned
+        # host memory, advances them through the C ABI and copies the state and the
+        # budgets back.  Copies in, the step and copies out run on separate streams
+        # with two device buffer sets, so step n's copies overlap the neighbouring
+        # steps' work; the timed region spans the first copy in to the last copy out.
+        names = ("rho", "rhotheta", "rhoq", "mu", "mv", "mw")
+        host = {k: getattr(st, k).cpu().pin_memory() for k in names}
+        hout = {k: torch.empty_like(host[k]).pin_memory() for k in ("rho", "rhotheta", "rhoq")}
         hbud = torch.empty(F + 1, dtype=torch.float64).pin_memory()
         h2d = sum(t.numel() * t.element_size() for t in host.values())
-        d2h = sum(host[k].numel() * host[k].element_size() for k in ("rho", "rhotheta", "rhoq")) + hbud.numel() * 8
+        d2h = sum(t.numel() * t.element_size() for t in hout.values()) + hbud.numel() * 8
         ne = max(1, min(args.steps, args.e2e_steps))
+        bufs = [st, asuca.State(*[torch.empty_like(getattr(st, k)) for k in names])]
+        buds = [bud, torch.empty_like(bud)]
+        # copies may be split over several streams per direction (one was the
+        # fastest: the host link, not the copy engines, is the bound)
+        NCOPY = max(1, args.e2e_copy_streams)
+        s_in = [torch.cuda.Stream() for _ in range(NCOPY)]
+        s_out = [torch.cuda.Stream() for _ in range(NCOPY)]
+        s_run = torch.cuda.Stream()
+        ev_in = [[torch.cuda.Event() for _ in range(NCOPY)] for _ in range(2)]
+        ev_out = [[torch.cuda.Event() for _ in range(NCOPY)] for _ in range(2)]
+        ev_run = [torch.cuda.Event(), torch.cuda.Event()]
+        # pieces of about equal size: every tensor cut along its slowest dimension
+        def pieces(tensors):
+            if NCOPY == 1:
+                return list(tensors)
+            out = []
+            for dst, src in tensors:
+                n = dst.shape[0]
+                step = max(1, -(-n // NCOPY))
+                for a in range(0, n, step):
+                    out.append((dst[a:a + step], src[a:a + step]))
+            return out
 
-        def e2e_step():
-            for k, t in host.items():
-                getattr(st, k).copy_(t, non_blocking=True)
-            asuca.step(g, st, case.dt, 1, workspace=ws_t, budgets=bud)
-            for k in ("rho", "rhotheta", "rhoq"):
-                host[k].copy_(getattr(st, k), non_blocking=True)
-            hbud.copy_(bud, non_blocking=True)
+        def e2e_steps(n):
+            for q in range(n):
+                b = q % 2
+                ins = pieces([(getattr(bufs[b], k), host[k]) for k in names])
+                for c, sx in enumerate(s_in):
+                    if q >= 2:
+                        for c2 in range(NCOPY):       # buffer set b has been read back
+                            sx.wait_event(ev_out[b][c2])
+                    with torch.cuda.stream(sx):
+                        for dst, src in ins[c::NCOPY]:
+                            dst.copy_(src, non_blocking=True)
+                    ev_in[b][c].record(sx)
+                for c in range(NCOPY):
+                    s_run.wait_event(ev_in[b][c])
+                asuca.step(g, bufs[b], case.dt, 1, workspace=ws_t, budgets=buds[b], stream=s_run)
+                ev_run[b].record(s_run)
+                outs = pieces([(hout[k], getattr(bufs[b], k)) for k in hout]) + [(hbud, buds[b])]
+                for c, sx in enumerate(s_out):
+                    sx.wait_event(ev_run[b])
+                    with torch.cuda.stream(sx):
+                        for dst, src in outs[c::NCOPY]:
+                            dst.copy_(src, non_blocking=True)
+                    ev_out[b][c].record(sx)
 
-        for _ in range(2):
-            e2e_step()
+        cur = torch.cuda.current_stream()
+        streams = s_in + [s_run] + s_out
+
+        def join():
+            for sx in streams:
+                cur.wait_stream(sx)
+
+        for sx in streams:
+            sx.wait_stream(cur)
+        e2e_steps(2)
+        join()
         torch.cuda.synchronize()
         _barrier(world)
         a0 = torch.cuda.Event(enable_timing=True)
         a1 = torch.cuda.Event(enable_timing=True)
-        a0.record()
-        for _ in range(ne):
-            e2e_step()
-        a1.record()
+        a0.record(cur)
+        for sx in streams:
+            sx.wait_stream(cur)
+        e2e_steps(ne)
+        join()
+        a1.record(cur)
         torch.cuda.synchronize()
         _barrier(world)
+        assert asuca.get_status(g) == asuca.OK
         ems = _max_over_ranks(world, a0.elapsed_time(a1))
         e2e = {"value": world * C * ne / (ems * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h, "steps": ne, "ms_per_step": ems / ne}
-        del host
+               "d2h_bytes_per_step": d2h, "steps": ne, "ms_per_step": ems / ne,
+               "overlap": f"copies in ({NCOPY} stream(s)), the step, copies out ({NCOPY} stream(s)); "
+                          "two device buffer sets"}
+        del host, hout, bufs
     del st, ws_t
     torch.cuda.empty_cache()
 
@@ -597,6 +656,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--fp64-steps", type=int, default=5)
     ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--e2e-copy-streams", type=int, default=1,
+                    help="streams per copy direction in the end-to-end measurement (1 was fastest on GB300)")
     ap.add_argument("--ref-n", type=int, default=128, help="reference arm sample size (n x n x 58)")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
