@@ -43,9 +43,10 @@ def _peaks():
     return 6800.0, "fallback"
 
 
-def _recorded_traffic(kernel, cells):
-    """DRAM bytes per launch of `kernel` from the recorded ncu capture, scaled to
-    `cells`; None when the record is missing or the kernel's sources changed since."""
+def _recorded(kernel, key, cells):
+    """A per-cell figure (`key`) of `kernel` from the recorded ncu captures
+    (profiles/traffic.json), scaled to `cells`; None when the record is missing
+    or the kernel's sources changed since."""
     import hashlib
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
@@ -57,9 +58,19 @@ def _recorded_traffic(kernel, cells):
                 h.update(fh.read())
         if h.hexdigest()[:16] != rec["source_sha256_16"]:
             return None
-        return rec["bytes_per_cell"] * cells
+        return rec[key] * cells
     except (OSError, KeyError, ValueError):
         return None
+
+
+def _recorded_traffic(kernel, cells):
+    """DRAM bytes per launch of `kernel` (dram__bytes_read.sum + dram__bytes_write.sum)."""
+    return _recorded(kernel, "bytes_per_cell", cells)
+
+
+# FP64 pipe: 2 DFMA/DADD/DMUL per clock per SM (ncu's
+# sm__sass_thread_inst_executed_op_dfma_pred_on peak), 152 SMs, 2070 MHz maximum clock
+FP64_INST_PEAK = 2 * 152 * 2.07e9
 
 
 # ---------------------------------------------------------------- clocks
@@ -612,6 +623,14 @@ def run_ours(args):
         ms64 = _max_over_ranks(world, ms64)
         fp64 = {"value": world * C * n64 / (ms64 * 1e-3), "ms_per_step": ms64 / n64, "steps": n64,
                 "kernels": {kinds.get(k, str(k)): {"launches": n, "avg_ms": t / n} for k, (t, n) in prof64.items()}}
+        # the FP64 stage launches are bound by the FP64 pipe: its instruction rate
+        # (FP64 instructions per cell from the recorded capture) against the pipe's peak
+        st64k = fp64["kernels"].get("stage")
+        inst = _recorded("stage_fp64", "fp64_inst_per_cell", C)
+        fp64["roofline"] = {"kernel": "stage", "bound": "fp64", "unit": "FP64 inst/s", "peak": FP64_INST_PEAK,
+                            "achieved": (inst / (st64k["avg_ms"] * 1e-3)) if (inst and st64k) else None,
+                            "frac": (inst / (st64k["avg_ms"] * 1e-3) / FP64_INST_PEAK) if (inst and st64k) else None,
+                            "peak_source": "recipe unit counts and maximum SM clock"}
         del st64, ws64
 
     precision = None
