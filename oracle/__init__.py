@@ -74,6 +74,7 @@ def lib():
         L.orc_step_window.restype = ctypes.c_int
         L.orc_step_window.argtypes = [G, _D, _D, _D, _D, _D, ctypes.c_double, ctypes.c_int,
                                       ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D]
+        L.orc_stencil7.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, _D, _D]
         L.orc_set_threads.argtypes = [ctypes.c_int]
         L.orc_get_threads.restype = ctypes.c_int
         _lib = L
@@ -171,6 +172,16 @@ def thomas(a, b, c, d):
     x = np.empty_like(d)
     lib().orc_thomas(len(d), _p(a), _p(b), _p(c), _p(d), _p(x))
     return x
+
+
+def stencil7(field, c):
+    """One explicit 7-point diffusion step of a [nz][ny][nx] field (periodic in i
+    and j, zero flux through the lids)."""
+    f = np.ascontiguousarray(_f64(field))
+    nz, ny, nx = f.shape
+    out = np.empty_like(f)
+    lib().orc_stencil7(nx, ny, nz, float(c), _p(f), _p(out))
+    return out
 
 
 def budgets(g: Grid, Y, precip=0.0):

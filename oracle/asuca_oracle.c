@@ -990,3 +990,30 @@ void orc_trajectory_branches(const orc_grid *g, const double *Y0, const double *
     }
     free(Y); free(S); free(R);
 }
+
+/* ---- 7-point diffusion stencil (Sec. 4, reduced weather application) ---------
+ * The paper names the kernel but prints no formula; the reading is the
+ * textbook explicit diffusion step with one diffusion number c for all three
+ * directions: out = in + c (in(i-1) + in(i+1) + in(j-1) + in(j+1) + in(k-1)
+ * + in(k+1) - 6 in), periodic in i and j, and zero flux through the lids
+ * (the ghost level copies the boundary cell, so its difference vanishes). */
+void orc_stencil7(int nx, int ny, int nz, double c, const double *in, double *out) {
+    const long long plane = (long long)nx * ny;
+#ifdef _OPENMP
+#pragma omp parallel for
+#endif
+    for (int k = 0; k < nz; k++) {
+        const int kd = k > 0 ? k - 1 : 0, ku = k < nz - 1 ? k + 1 : nz - 1;
+        for (int j = 0; j < ny; j++) {
+            const int jd = wrap(j - 1, ny), ju = wrap(j + 1, ny);
+            for (int i = 0; i < nx; i++) {
+                const int id = wrap(i - 1, nx), iu = wrap(i + 1, nx);
+                const double v = in[k * plane + (long long)j * nx + i];
+                const double sum = in[k * plane + (long long)j * nx + id] + in[k * plane + (long long)j * nx + iu] +
+                                   in[k * plane + (long long)jd * nx + i] + in[k * plane + (long long)ju * nx + i] +
+                                   in[kd * plane + (long long)j * nx + i] + in[ku * plane + (long long)j * nx + i];
+                out[k * plane + (long long)j * nx + i] = v + c * (sum - 6.0 * v);
+            }
+        }
+    }
+}

@@ -76,6 +76,11 @@ void orc_step_adj_br(const orc_grid *g, const double *Y0, const double *mu, cons
 void orc_trajectory_branches(const orc_grid *g, const double *Y0, const double *mu,
                              const double *mv, const double *mw, const double *tend, double dt,
                              int nsteps, unsigned char *out);
+/* One explicit step of 7-point diffusion (the reduced weather application's
+ * kernel, Sec. 4): out = in + c (sum of the six neighbours - 6 in), periodic in
+ * i and j, zero flux through both lids (ghost levels copy the boundary cell);
+ * fields [nz][ny][nx]. */
+void orc_stencil7(int nx, int ny, int nz, double c, const double *in, double *out);
 void orc_set_threads(int n);
 int orc_get_threads(void);
 

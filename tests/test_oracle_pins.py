@@ -423,3 +423,41 @@ def test_vertical_kappa_third_exact_for_quadratics_and_ghosts(w):
     R = oracle.rhs(g, Y, mu, mv, mw)
     got = R[1, :, 2, 1]
     assert np.abs(got - np.array([float(e) for e in expect])).max() < 1e-12
+
+
+# ------------------------------------------------------------------ 7-point diffusion stencil (Sec. 4)
+
+def test_stencil7_constant_and_conservation():
+    """A constant field is a fixed point; periodic sides and zero-flux lids
+    conserve the total (every interior difference enters two cells with opposite
+    signs), to rounding."""
+    c = 0.12
+    const = np.full((6, 9, 11), 3.25)
+    assert np.array_equal(oracle.stencil7(const, c), const)
+    f = np.random.default_rng(3).standard_normal((7, 10, 13))
+    out = oracle.stencil7(f, c)
+    assert abs(out.sum() - f.sum()) <= 1e-13 * np.abs(f).sum()
+
+
+@pytest.mark.parametrize("axis", [0, 1])
+def test_stencil7_fourier_mode_closed_form(axis):
+    """A level-uniform periodic Fourier mode cos(2 pi m x / n) along i (or j) is an
+    eigenvector with eigenvalue 1 + c (2 cos(2 pi m / n) - 2)."""
+    nz, ny, nx, m, c = 4, 12, 16, 3, 0.09
+    n = nx if axis == 0 else ny
+    x = np.arange(n)
+    mode = np.cos(2 * np.pi * m * x / n + 0.4)
+    f = np.broadcast_to(mode[None, None, :] if axis == 0 else mode[None, :, None], (nz, ny, nx)).copy()
+    lam = 1.0 + c * (2.0 * np.cos(2 * np.pi * m / n) - 2.0)
+    assert np.max(np.abs(oracle.stencil7(f, c) - lam * f)) <= 1e-13
+
+
+def test_stencil7_linear_in_k_with_zero_flux_lids():
+    """f = k: the interior Laplacian of a linear profile is zero; at the bottom the
+    ghost copies level 0, so out = 0 + c (1 - 0), at the top out = (nz-1) - c."""
+    nz, ny, nx, c = 9, 5, 6, 0.2
+    f = np.broadcast_to(np.arange(nz, dtype=float)[:, None, None], (nz, ny, nx)).copy()
+    out = oracle.stencil7(f, c)
+    assert np.array_equal(out[1:-1], f[1:-1])
+    assert np.allclose(out[0], c, rtol=0, atol=1e-15)
+    assert np.allclose(out[-1], (nz - 1) - c, rtol=0, atol=1e-14)
