@@ -363,6 +363,49 @@ def precision_report(asuca, dev):
             "ms_per_step": times, "fp32_over_fp64_speedup": times["fp64"] / times["fp32"]}
 
 
+def layout_ablation(asuca, dev, reps=10):
+    """The reduced weather application's 7-point diffusion step (Sec. 4) on the
+    1024x1024x58 rho*theta field, same kernel and thread mapping in IJK (i fastest)
+    and KIJ (k fastest) storage (Sec. 1.3: KIJ 7.7x slower on GPU), FP32 and FP64.
+    Reported against the paper's two bandwidth models at the measured HBM peak:
+    perfect cache (read and write each value once) and no cache (7 reads + 1
+    write per cell).  The 243 MB (FP32) field is larger than L2."""
+    import torch
+    import gen
+    case = gen.make_config_case(WORKLOAD)
+    peak, _ = _peaks()
+    C = case.cells
+    out = {"workload": "stencil7_1024x1024x58", "paper_kij_over_ijk": 7.7}
+    for name, dt in (("fp32", torch.float32), ("fp64", torch.float64)):
+        s = dt.itemsize
+        f = torch.tensor(case.rhotheta, dtype=dt, device=dev).contiguous()
+        res = {}
+        for lname, layout in (("ijk", asuca.LAYOUT_IJK), ("kij", asuca.LAYOUT_KIJ)):
+            x = f if layout == asuca.LAYOUT_IJK else f.permute(1, 2, 0).contiguous()
+            y = torch.empty_like(x)
+            for _ in range(3):
+                asuca.stencil7(x, y, 0.1, layout)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                asuca.stencil7(x, y, 0.1, layout)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            t_perfect = 2 * s * C / (peak * 1e9) * 1e3
+            t_nocache = 8 * s * C / (peak * 1e9) * 1e3
+            res[lname] = {"ms": ms, "achieved_gbs_perfect_cache_bytes": 2 * s * C / (ms * 1e-3) / 1e9,
+                          "frac_of_perfect_cache_model": t_perfect / ms,
+                          "speedup_over_no_cache_model": t_nocache / ms}
+            del x, y
+        res["kij_over_ijk"] = res["kij"]["ms"] / res["ijk"]["ms"]
+        out[name] = res
+        del f
+    torch.cuda.empty_cache()
+    return out
+
+
 def ensemble_throughput(asuca, dev, nsteps=10, reps=3):
     """32 members with nx = ny drawn from U{64..320}, 58 levels, 4 tracers, FP32:
     cell-updates/s of one persistent launch per call (graph-replayed) against the
@@ -642,6 +685,9 @@ def run_ours(args):
     ensemble = None
     if not args.no_ensemble:
         ensemble = ensemble_throughput(asuca, dev, args.ens_steps)
+    layout = None
+    if not args.no_layout:
+        layout = layout_ablation(asuca, dev)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -658,6 +704,7 @@ def run_ours(args):
                           "parallelism": f"{world} independent replica(s), one per GPU"},
                "clocks": clocks, "gpu_launches": sum(n for _t, n in (prof or {}).values()), "roofline": roofline,
                "e2e": e2e, "fp64": fp64, "precision": precision, "adjoint": adjoint, "ensemble": ensemble,
+               "layout_ablation": layout,
                "fp32_over_fp64_speedup": (value / fp64["value"]) if fp64 else None,
                "cpu_baseline": cpu}
         print(json.dumps(out), flush=True)
@@ -684,6 +731,7 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-precision", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--no-layout", action="store_true")
     ap.add_argument("--ens-steps", type=int, default=10)
     ap.add_argument("--nx", type=int, default=1024,
                     help="nx = ny of the timed case; anything but 1024 is a smaller case of the same "

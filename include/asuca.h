@@ -293,6 +293,22 @@ asuca_status asuca_debug_numerics(const float *in_f, const double *in_d, int n, 
 asuca_status asuca_column_noalloc(asuca_grid *grid, asuca_state *state, double dt,
                                   double *precip_col_dev, void *cuda_stream);
 
+/* ---- storage-order experiment ------------------------------------------
+ * One explicit 7-point diffusion step, the kernel of the reduced weather
+ * application of Sec. 4 ("Productivity- and Performance Results"), run with
+ * the same thread mapping on two storage orders, to measure the effect Sec. 1.3
+ * ("Memory Layout") reports (KIJ order 7.7x slower than IJK on GPU):
+ *   out = in + c (in(i-1) + in(i+1) + in(j-1) + in(j+1) + in(k-1) + in(k+1) - 6 in),
+ * periodic in i and j, zero flux through the lids (ghost levels copy the
+ * boundary cell).  layout 0 (IJK): element (i, j, k) at (k ny + j) nx + i;
+ * layout 1 (KIJ): at (j nx + i) nz + k.  in and out are caller-owned device
+ * arrays of nx ny nz elements of the precision's type (double for ASUCA_FP64,
+ * float for ASUCA_FP32_MIXED) and must not overlap.  Asynchronous on the
+ * stream; ASUCA_ERR_ARG for null or equal pointers, nx, ny < 2, nz < 1, or an
+ * unknown layout or precision. */
+asuca_status asuca_stencil7(const void *in, void *out, int nx, int ny, int nz, int layout, int prec, double c,
+                            void *cuda_stream);
+
 /* ---- per-kernel timing ------------------------------------------------- */
 
 typedef enum {

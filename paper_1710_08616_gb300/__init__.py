@@ -71,6 +71,8 @@ SIGNATURES = {
                                           _VP, ctypes.c_size_t, _VP]),
     "asuca_debug_numerics": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP, _VP, _VP, _VP]),
     "asuca_column_noalloc": (ctypes.c_int, [_VP, ctypes.POINTER(StateStruct), ctypes.c_double, _VP, _VP]),
+    "asuca_stencil7": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_double, _VP]),
     "asuca_adjoint_workspace_bytes": (ctypes.c_size_t, [_VP, ctypes.c_int, ctypes.c_int]),
     "asuca_adjoint_step": (ctypes.c_int, [_VP, ctypes.POINTER(StateStruct), _VP, ctypes.c_double, ctypes.c_int,
                                           ctypes.c_int, _VP, _VP, _VP, _VP, _VP, _VP, ctypes.c_size_t, _VP]),
@@ -294,6 +296,28 @@ def column_noalloc(grid: Grid, state: State, dt: float, precip_col, *, stream=No
     s = state.struct()
     _check(lib().asuca_column_noalloc(grid.handle, ctypes.byref(s), float(dt), _ptr(precip_col),
                                       _stream_ptr(stream)), "asuca_column_noalloc")
+
+
+LAYOUT_IJK, LAYOUT_KIJ = 0, 1
+
+
+def stencil7(inp, out, c: float, layout: int = LAYOUT_IJK, *, stream=None):
+    """One explicit 7-point diffusion step (asuca_stencil7): out = in + c (sum of
+    the six neighbours - 6 in).  inp, out: contiguous CUDA tensors of nx ny nz
+    float32 or float64 elements, [nz][ny][nx] for LAYOUT_IJK, [ny][nx][nz] for
+    LAYOUT_KIJ; the shape gives (nx, ny, nz)."""
+    import torch
+    if inp.dtype not in (torch.float32, torch.float64) or out.dtype != inp.dtype or inp.shape != out.shape \
+            or inp.dim() != 3 or not inp.is_contiguous() or not out.is_contiguous() or not inp.is_cuda:
+        raise ValueError("stencil7: need two contiguous CUDA float tensors of the same 3D shape")
+    if layout == LAYOUT_IJK:
+        nz, ny, nx = inp.shape
+    else:
+        ny, nx, nz = inp.shape
+    prec = FP64 if inp.dtype == torch.float64 else FP32_MIXED
+    _check(lib().asuca_stencil7(_ptr(inp), _ptr(out), nx, ny, nz, int(layout), prec, float(c), _stream_ptr(stream)),
+           "asuca_stencil7")
+    return out
 
 
 def profile_enable(grid: Grid, on: bool = True):

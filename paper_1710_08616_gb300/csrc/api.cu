@@ -1520,6 +1520,18 @@ asuca_status asuca_profile_enable(asuca_grid *g, int on) {
     return ASUCA_OK;
 }
 
+asuca_status asuca_stencil7(const void *in, void *out, int nx, int ny, int nz, int layout, int prec, double c,
+                            void *cuda_stream) {
+    if (!in || !out || in == out || nx < 2 || ny < 2 || nz < 1 || (layout != 0 && layout != 1) ||
+        (prec != ASUCA_FP64 && prec != ASUCA_FP32_MIXED) || !std::isfinite(c))
+        return ASUCA_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const cudaError_t e = prec == ASUCA_FP64
+                              ? launch_stencil7<double>((const double *)in, (double *)out, nx, ny, nz, layout, c, s)
+                              : launch_stencil7<float>((const float *)in, (float *)out, nx, ny, nz, layout, (float)c, s);
+    return cuda_status(e);
+}
+
 asuca_status asuca_profile_read(asuca_grid *g, double *ms, int *launches, int nkinds) {
     if (!g || !ms || !launches || nkinds <= 0) return ASUCA_ERR_ARG;
     for (int k = 0; k < nkinds; k++) {

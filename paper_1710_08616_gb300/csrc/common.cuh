@@ -380,6 +380,9 @@ cudaError_t launch_budget_reduce(const double *partials, int nblocks, int nq, in
 cudaError_t launch_numerics(const float *in_f, const double *in_d, int n, double *widen, float *narrow,
                             double *rcp, cudaStream_t s);
 
+template <typename T>
+cudaError_t launch_stencil7(const T *in, T *out, int nx, int ny, int nz, int layout, T c, cudaStream_t s);
+
 constexpr int COL_TPB = 128;
 
 }  // namespace asuca
