@@ -7,6 +7,8 @@
 #include <mutex>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "adjoint_params.cuh"
 #include "ensemble_params.cuh"
 #include "dataflow_params.cuh"
@@ -49,6 +51,14 @@ struct asuca_grid {
 };
 
 namespace {
+
+// A named range on the host timeline of a profiler (NVTX; free when no tool is attached).
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range &) = delete;
+    Range &operator=(const Range &) = delete;
+};
 
 constexpr size_t ALIGN = 256;
 // column-kernel blocks resident per SM; the Thomas scratch is sized to match
@@ -338,7 +348,9 @@ asuca_status run_step(asuca_grid *g, asuca_state *st, const void *tend, double d
         fp.c.nslots = g->plane;
     }
     for (int n = 0; n < nsteps; n++) {
+        Range step_range("asuca step");
         for (int stg = 0; stg < (fused ? 2 : 3); stg++) {
+            Range stage_range(stg == 0 ? "RK stage 1" : (stg == 1 ? "RK stage 2" : "RK stage 3"));
             // stage 1 reads the caller's fields (TMA for interior tiles, cp.async at the
             // periodic edges), stages 2 and 3 the padded buffers of phi the previous
             // stage wrote (TMA); stage 3 writes the caller's fields
@@ -357,6 +369,7 @@ asuca_status run_step(asuca_grid *g, asuca_state *st, const void *tend, double d
                 return ASUCA_ERR_CUDA;
         }
         cp.budgets = (budgets != nullptr) && (n == nsteps - 1);
+        Range col_range(fused ? "RK stage 3 + column pass" : "column pass");
         if (fused) {
             // stage 3 marching downward with the relaxation, sedimentation and
             // elimination of every column, then the bottom-up back substitution
@@ -676,7 +689,9 @@ asuca_status run_adjoint(asuca_grid *g, const asuca_state *init, const void *ten
                            cudaMemcpyDeviceToDevice, s));
         if (e != cudaSuccess) return ASUCA_ERR_CUDA;
         // ---- recompute the segment, recording stage states and limiter branches
+        Range seg_range("adjoint segment");
         for (int q = 0; q < len; q++) {
+            Range rec_range("adjoint recompute step");
             T *yn[MAXF], *y1[MAXF], *y2[MAXF], *y3[MAXF];
             block_fields<T>(g, segYn(q), yn);
             workspace_fields<T>(g, segY1(q), 0, y1);
@@ -714,6 +729,7 @@ asuca_status run_adjoint(asuca_grid *g, const asuca_state *init, const void *ten
         }
         // ---- reverse through the segment
         for (int q = len - 1; q >= 0; q--) {
+            Range rev_range("adjoint reverse step");
             AdjColParams<T> ac;
             std::memset(&ac, 0, sizeof(ac));
             ac.c = column_params<T>(g, dt);
