@@ -382,3 +382,26 @@ def test_fused_stage3_column_equals_separate_launches(asuca, prec, lim, shape, n
     assert torch.equal(a.fields(), b.fields())
     rel = (ba - bb).abs() / ba.abs().clamp_min(1e-300)
     assert float(rel.max()) <= 1e-13
+
+
+@pytest.mark.parametrize("prec,tol", [(0, TOL64), (1, TOL32)])
+def test_full_step_at_the_level_limit(asuca, prec, tol):
+    """nz = ASUCA_MAX_NZ levels with the most tracers: every level table of the
+    kernels is full; the default (fused) path against the oracle and against the
+    separate stage and column launches bit for bit."""
+    import torch
+    c = gen.make_case(40, 24, asuca.MAX_NZ, asuca.MAX_TRACERS, seed=128)
+    og = oracle.Grid.from_case(c)
+    ref, rbud = oracle.step(og, c.state(), c.mu, c.mv, c.mw, c.dt, 2)
+    g0 = asuca.Grid.from_case(c, prec=prec)
+    g1 = asuca.Grid.from_case(c, prec=prec)
+    asuca.set_tuning(g1, asuca.TUNE_FUSED_COLUMN, 0)
+    a = asuca.State.from_case(c, prec=prec)
+    b = a.clone()
+    ba = asuca.step(g0, a, c.dt, 2, budgets=True)
+    bb = asuca.step(g1, b, c.dt, 2, budgets=True)
+    torch.cuda.synchronize()
+    assert asuca.get_status(g0) == asuca.OK and asuca.get_status(g1) == asuca.OK
+    assert torch.equal(a.fields(), b.fields())
+    _assert_fields(_np(a), ref, tol, f"nz={asuca.MAX_NZ} prec={prec}", both=prec == 0)
+    assert np.all(np.abs(ba.cpu().numpy() - rbud) <= tol * np.abs(rbud) + 1e-300)
