@@ -4,7 +4,8 @@
 //   R = -[dX/dx + dY/dy + dZ/dz] + tendency,  Y_out = Y_base + cdt R
 //
 // Mapping: a CTA owns a 32 x TY tile of (i, j) columns, one warp per row, and
-// marches k upward (parallel in I/J, sequential in K; Sec. 1.1, Sec. 1.2).
+// marches k (parallel in I/J, sequential in K; Sec. 1.1, Sec. 1.2): upward, or
+// downward for the third stage that carries the top-down column pass.
 // Level planes of the stage input stream through a ring of D shared-memory
 // slots, each holding every field of the tile plus a halo of 4 columns in i
 // (the TMA box must start on a 16-byte boundary; 2 are used) and 2 rows in j:
@@ -19,8 +20,9 @@
 //     to phi, once per cell.
 // Levels are requested D-2 levels ahead.  Every face is reconstructed once:
 // i+1/2 by each thread (the i-1/2 flux comes from the neighbouring lane by
-// shuffle), j+1/2 by each thread into shared memory, k+1/2 by each thread with
-// the k-1/2 flux carried in registers; the faces on the tile's left and
+// shuffle), j+1/2 by each thread into shared memory, the vertical face ahead of
+// the march by each thread with the one behind carried in registers; the faces
+// on the tile's left and
 // bottom edges are computed by warps dealt round-robin.  A face's upwind,
 // downwind and far cells are picked by address from the sign of M, so the
 // limiter arithmetic has no per-field selects.
