@@ -129,8 +129,10 @@ asuca_status asuca_step(asuca_grid *grid, asuca_state *state, const void *tenden
                         void *cuda_stream);
 
 /* Workspace of asuca_adjoint_step: the step workspace, ceil(nsteps / K)
- * checkpoints, one segment of K recorded steps (stage states and limiter
- * branches), four adjoint fields and the column-transpose scratch. */
+ * checkpoints, one segment of K recorded steps (stage states, limiter
+ * branches, the face values of every stage and the column pass's
+ * factorisation and solution), four adjoint fields and the column-transpose
+ * scratch. */
 size_t asuca_adjoint_workspace_bytes(const asuca_grid *grid, int nsteps, int checkpoint_every);
 
 /* Adjoint (vector-Jacobian product) of nsteps calls of asuca_step's time

@@ -26,12 +26,13 @@ __global__ void __launch_bounds__(256) adj_stage_kernel(const __grid_constant__ 
     // adjoint fluxes lambda_F M of the tile's i and j faces are formed once,
     // from tiles of lambda and the recorded branches in shared memory, and
     // every cell gathers the four faces per direction whose stencil holds it;
-    // the k faces of the cell's own column are taken directly.
+    // the k faces of the cell's own column are taken directly.  The face values
+    // the gradient of M needs are the ones the forward stage recorded.
     constexpr int TW = 36, TH = 12, TN = TW * TH;   // tile with a halo of 2 (i: -2..33, j: -2..9)
     constexpr int NXF = 35, NYF = 11;               // i faces i0-2..i0+32 (8 rows), j faces j0-2..j0+8 (32 columns)
     __shared__ T ctab[32];
-    __shared__ T sMU[TN], sMV[TN], sRI[TN];         // MU, MV and 1/rho over the tile
-    __shared__ T sL[TN], sP[TN];                    // lambda and phi of the current field
+    __shared__ T sMU[TN], sMV[TN];                  // MU, MV over the tile
+    __shared__ T sL[TN];                            // lambda of the current field
     __shared__ uint8_t sB[TN];                      // its branch bytes
     __shared__ T sWx[8 * NXF], sWy[NYF * 32];       // lambda_F M of the i and j faces
     __shared__ uint8_t sCx[8 * NXF], sCy[NYF * 32]; // their (upwind side, branch) as u * 4 + br
@@ -41,22 +42,21 @@ __global__ void __launch_bounds__(256) adj_stage_kernel(const __grid_constant__ 
     const int i = i0 + lane, j = j0 + row;
     const bool valid = i < nx && j < ny;
     // offsets within a field fit in 32 bits (the host checks)
-    const unsigned plane = (unsigned)p.plane, ysp = (unsigned)p.ys_plane;
-    const unsigned kb = (unsigned)k * plane, skb = (unsigned)k * ysp;
+    const unsigned plane = (unsigned)p.plane;
+    const unsigned kb = (unsigned)k * plane;
     const bool sphi = p.ys_phi != 0;
     const T cs = p.cs, rdx = p.rdx, rdy = p.rdy;
     if (tid < 32) ctab[tid] = face_coef<T>((tid >> 4) != 0, (tid >> 2) & 3, tid & 3);
-    // the tile cells this thread loads (caller layout and stage-input layout offsets)
+    // the tile cells this thread loads
     constexpr int PER = (TN + 255) / 256;
-    unsigned to[PER], ts[PER];
+    unsigned to[PER];
 #pragma unroll
     for (int q = 0; q < PER; q++) {
         const int c = tid + q * 256;
-        to[q] = ts[q] = 0;
+        to[q] = 0;
         if (c < TN) {
             const int ii = wrap_index(i0 - 2 + c % TW, nx), jj = wrap_index(j0 - 2 + c / TW, ny);
             to[q] = kb + (unsigned)(jj * nx + ii);
-            ts[q] = skb + (unsigned)((jj + p.ys_oy) * p.ys_pitch + ii + p.ys_ox);
         }
     }
 #pragma unroll
@@ -65,48 +65,39 @@ __global__ void __launch_bounds__(256) adj_stage_kernel(const __grid_constant__ 
         if (c < TN) {
             sMU[c] = p.mu[to[q]];
             sMV[c] = p.mv[to[q]];
-            sRI[c] = recip(p.ys[0][ts[q]]);
         }
     }
     const int cc = (row + 2) * TW + lane + 2;       // the thread's cell in the tile
-    const unsigned own = kb + (unsigned)(j * nx + i);
-    const unsigned sown = skb + (unsigned)((j + p.ys_oy) * p.ys_pitch + i + p.ys_ox);
-    // the cell's own column: k faces a = k-2 .. k+1 and the stencil of face k+1/2
+    const unsigned col = (unsigned)(j * nx + i);
+    const unsigned own = kb + col;
+    const unsigned sown = (unsigned)k * (unsigned)p.ys_plane + (unsigned)((j + p.ys_oy) * p.ys_pitch + i + p.ys_ox);
+    // the cell's own column: k faces a = k-2 .. k+1
     T mzf[4];
-    T rz[3];
-    const unsigned zm1 = (unsigned)(k > 0 ? k - 1 : 0) * ysp - skb + sown;
-    const unsigned zp1 = (unsigned)(k + 1 < nz ? k + 1 : nz - 1) * ysp - skb + sown;
-    const unsigned zp2 = (unsigned)(k + 2 < nz ? k + 2 : nz - 1) * ysp - skb + sown;
+    T rr = T(1);
     if (valid) {
 #pragma unroll
         for (int q = 0; q < 4; q++) {
             const int a = k + q - 2;
-            mzf[q] = (a >= 0 && a <= nz - 2) ? p.mw[(unsigned)(a + 1) * plane + own - kb] : T(0);
+            mzf[q] = (a >= 0 && a <= nz - 2) ? p.mw[(unsigned)(a + 1) * plane + col] : T(0);
         }
-        if (!sphi) {
-            rz[0] = recip(p.ys[0][zm1]);
-            rz[1] = recip(p.ys[0][zp1]);
-            rz[2] = recip(p.ys[0][zp2]);
-        }
+        rr = recip(p.ys[0][sown]);
     }
     __syncthreads();
-    const T rr = sRI[cc];
     T gx = T(0), gy = T(0), gz = T(0), vrho = T(0);
+    const size_t fs = (size_t)nz * plane, ds = (size_t)NT * fs;
 
-    // tiles of lambda, phi and the branch bytes of field f, loaded into
-    // registers one field ahead so that the loads overlap the previous field's work
-    T nL[PER], nP[PER];
+    // tiles of lambda and the branch bytes of field f, loaded into registers one
+    // field ahead so that the loads overlap the previous field's work
+    T nL[PER];
     uint8_t nB[PER];
     auto fetch = [&](int f) {
         const T *L = p.lam[f + 1];
-        const T *Y = p.ys[f + 1];
-        const uint8_t *B = p.branch + (size_t)f * nz * plane;
+        const uint8_t *B = p.branch + (size_t)f * fs;
 #pragma unroll
         for (int q = 0; q < PER; q++) {
             const int c = tid + q * 256;
             if (c < TN) {
                 nL[q] = L[to[q]];
-                nP[q] = Y[ts[q]];
                 nB[q] = B[to[q]];
             }
         }
@@ -114,14 +105,12 @@ __global__ void __launch_bounds__(256) adj_stage_kernel(const __grid_constant__ 
     fetch(0);
     for (int f = 0; f < NT; f++) {
         const T *L = p.lam[f + 1];
-        const T *Y = p.ys[f + 1];
-        const uint8_t *B = p.branch + (size_t)f * nz * plane;
+        const uint8_t *B = p.branch + (size_t)f * fs;
 #pragma unroll
         for (int q = 0; q < PER; q++) {
             const int c = tid + q * 256;
             if (c < TN) {
                 sL[c] = nL[q];
-                sP[c] = sphi ? nP[q] : nP[q] * sRI[c];
                 sB[c] = nB[q];
             }
         }
@@ -162,14 +151,14 @@ __global__ void __launch_bounds__(256) adj_stage_kernel(const __grid_constant__ 
 #pragma unroll
             for (int q = 0; q < 5; q++) {
                 const int lev = k + q - 2;
-                lz[q] = (lev >= 0 && lev < nz) ? L[(unsigned)lev * plane + own - kb] : T(0);
+                lz[q] = (lev >= 0 && lev < nz) ? L[(unsigned)lev * plane + col] : T(0);
             }
 #pragma unroll
             for (int q = 0; q < 4; q++) {
                 const int a = k + q - 2;
                 if (a < 0 || a > nz - 2) continue;
                 const T lF = cs * (lz[q + 1] * p.rdz[a + 1] - lz[q] * p.rdz[a]);
-                const int br = (B[(unsigned)a * plane + own - kb] >> 4) & 3;
+                const int br = (B[(unsigned)a * plane + col] >> 4) & 3;
                 const T *ct = ctab + (mzf[q] >= T(0) ? 16 : 0) + br * 4;
                 T cf;
                 if (a >= 1 && a + 2 <= nz - 1) {
@@ -185,21 +174,14 @@ __global__ void __launch_bounds__(256) adj_stage_kernel(const __grid_constant__ 
                 }
                 lphi += lF * mzf[q] * cf;
             }
-            // gradient of M at the cell's own faces, this field's share
-            const T ph = sP[cc];
-            {
-                const T mx = sMU[cc], my = sMV[cc];
-                const T fx = face_val4<LIM>(sP[cc - 1], ph, sP[cc + 1], sP[cc + 2], mx >= T(0));
-                gx += cs * (sL[cc + 1] - sL[cc]) * rdx * fx;
-                const T fy = face_val4<LIM>(sP[cc - TW], ph, sP[cc + TW], sP[cc + 2 * TW], my >= T(0));
-                gy += cs * (sL[cc + TW] - sL[cc]) * rdy * fy;
-                if (k <= nz - 2) {
-                    const T fz = sphi ? face_val4<LIM>(Y[zm1], ph, Y[zp1], Y[zp2], mzf[2] >= T(0))
-                                      : face_val4<LIM>(Y[zm1] * rz[0], ph, Y[zp1] * rz[1], Y[zp2] * rz[2],
-                                                       mzf[2] >= T(0));
-                    gz += cs * (lz[3] * p.rdz[k + 1] - lz[2] * p.rdz[k]) * fz;
-                }
-            }
+            // gradient of M at the cell's own faces, this field's share, with the
+            // recorded face values
+            const T *Y = p.ys[f + 1];
+            const T ph = sphi ? Y[sown] : Y[sown] * rr;
+            const T *fv = p.facev + (size_t)f * fs + own;
+            gx += cs * (sL[cc + 1] - sL[cc]) * rdx * fv[0];
+            gy += cs * (sL[cc + TW] - sL[cc]) * rdy * fv[ds];
+            if (k <= nz - 2) gz += cs * (lz[3] * p.rdz[k + 1] - lz[2] * p.rdz[k]) * fv[2 * ds];
             // the field's output
             const T v = lphi * rr;
             if (p.out1[0]) p.out1[f + 1][own] = v;
@@ -216,7 +198,7 @@ __global__ void __launch_bounds__(256) adj_stage_kernel(const __grid_constant__ 
     // ---- density: its output and its terms of the gradients of the cell's own faces
     if (valid) {
         const T m0 = p.lam[0][own];
-        gx += cs * (p.lam[0][own - (unsigned)i + (unsigned)wrap_index(i + 1, nx)] - m0) * rdx;
+        gx += cs * (p.lam[0][kb + (unsigned)(j * nx + wrap_index(i + 1, nx))] - m0) * rdx;
         gy += cs * (p.lam[0][kb + (unsigned)(wrap_index(j + 1, ny) * nx + i)] - m0) * rdy;
         if (k <= nz - 2) gz += cs * (p.lam[0][own + plane] * p.rdz[k + 1] - m0 * p.rdz[k]);
         p.gmu[own] += gx;

@@ -14,6 +14,7 @@ struct AdjStageParams {
     const T *lam[MAXF];           // adjoint of the stage output, [nz][ny][nx]
     T cs;                         // c_s * dt
     const uint8_t *branch;        // [F-1][nz][ny][nx], recorded by the forward stage
+    const T *facev;               // [3][F-1][nz][ny][nx] face values of each cell's +1/2 faces, recorded too
     const T *mu, *mv, *mw;
     T *out1[MAXF];                // if set: R_Y^T (cs lam)
     T *out2[MAXF];                // if set: base2 + R_Y^T (cs lam) (+ lam if add_self)

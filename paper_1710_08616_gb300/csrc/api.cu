@@ -533,8 +533,8 @@ asuca_status run_step_dataflow(asuca_grid *g, asuca_state *st, const void *tend,
 // ---- adjoint -------------------------------------------------------------
 
 struct AdjLayout {
-    size_t step, W, ckpt, segYn, segY1, segY2, segY3, branch, rec, lam, l2, l1, acc, scratch, total;
-    size_t nrec_step;
+    size_t step, W, ckpt, segYn, segY1, segY2, segY3, branch, facev, rec, lam, l2, l1, acc, scratch, total;
+    size_t nrec_step, nfacev_stage;
     int ncp;
     size_t ustate, pstate, nbranch_step;
     long long slots;
@@ -579,6 +579,10 @@ AdjLayout adj_layout(const asuca_grid *g, int nsteps, int K) {
     off = align_up(off + (size_t)K * align_up(L.ustate));
     L.branch = off;
     off = align_up(off + (size_t)K * align_up(L.nbranch_step));
+    // per recorded stage: the face values of every cell's three +1/2 faces, [3][F-1][nz][ny][nx]
+    L.nfacev_stage = (size_t)3 * (g->F - 1) * g->cells * elem_size(g);
+    L.facev = off;
+    off = align_up(off + (size_t)K * 3 * align_up(L.nfacev_stage));
     // per recorded step: the column pass's factorisation and solution, [nz][F + 2][ny][nx] doubles
     L.nrec_step = (size_t)g->d.nz * (g->F + 2) * (size_t)g->plane * sizeof(double);
     L.rec = off;
@@ -681,6 +685,7 @@ asuca_status run_adjoint(asuca_grid *g, const asuca_state *init, const void *ten
         auto segY2 = [&](int q) { return ws + L.segY2 + (size_t)q * align_up(L.pstate); };
         auto segY3 = [&](int q) { return ws + L.segY3 + (size_t)q * align_up(L.ustate); };
         auto rec = [&](int q) { return (double *)(ws + L.rec + (size_t)q * align_up(L.nrec_step)); };
+        auto fvs = [&](int q, int stg) { return (T *)(ws + L.facev + ((size_t)q * 3 + stg) * align_up(L.nfacev_stage)); };
         auto brs = [&](int q, int stg) {
             return (uint8_t *)(ws + L.branch + (size_t)q * align_up(L.nbranch_step)) +
                    (size_t)stg * (F - 1) * g->cells;
@@ -711,6 +716,7 @@ asuca_status run_adjoint(asuca_grid *g, const asuca_state *init, const void *ten
                 }
                 sp.cdt = cdt[stg];
                 sp.branch = brs(q, stg);
+                sp.facev = fvs(q, stg);
                 if (timed(g, ASUCA_KERNEL_STAGE, s, [&] { return launch_stage<T>(sp, F, s); }) != cudaSuccess)
                     return ASUCA_ERR_CUDA;
             }
@@ -761,6 +767,7 @@ asuca_status run_adjoint(asuca_grid *g, const asuca_state *init, const void *ten
                 for (int f = 0; f < MAXF; f++) ap.lam[f] = lin[f];
                 ap.cs = cdt[stg];
                 ap.branch = brs(q, stg);
+                ap.facev = fvs(q, stg);
                 ap.mu = (const T *)init->mu;
                 ap.mv = (const T *)init->mv;
                 ap.mw = (const T *)init->mw;

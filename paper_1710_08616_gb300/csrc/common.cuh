@@ -65,6 +65,8 @@ struct StageParams {
     int user_tma;           // unpadded input through umap for tiles whose halo lies inside the domain
     int ty;                 // tile rows of the instantiation to launch (the TMA box height follows it)
     uint8_t *branch;        // when recording: [F-1][nz][ny][nx] branch bytes (2 bits per direction)
+    T *facev;               // when recording, if set: [3][F-1][nz][ny][nx] face values of the cell's
+                            // i+1/2, j+1/2 and k+1/2 faces (k+1/2 of the top level: 0)
     long long plane;        // nx * ny
     long long opitch, oplane;   // padded output: row pitch and level stride (elements)
     T cdt, rdx, rdy;
@@ -287,14 +289,13 @@ __device__ __forceinline__ float2 face_flux2(float2 c, float2 o, float2 far, flo
     return __fmul2_rn(m2, __fadd2_rn(c, make_float2(copysignf(hx, d0.x), copysignf(hy, d0.y))));
 }
 
-// face_flux2 that also returns both fields' limiter branches (as face_val_br,
-// whose value it equals bit for bit).
+// Two fields' face values with their limiter branches (as face_val_br, whose
+// value it equals bit for bit); times M they equal face_flux2's fluxes.
 template <int LIM>
-__device__ __forceinline__ float2 face_flux2_br(float2 c, float2 o, float2 far, float m, int2 &br) {
-    const float2 m2 = make_float2(m, m);
+__device__ __forceinline__ float2 face_val2_br(float2 c, float2 o, float2 far, int2 &br) {
     if (LIM == ASUCA_LIM_UPWIND1) {
         br = make_int2(0, 0);
-        return __fmul2_rn(m2, c);
+        return c;
     }
     const float2 neg1 = make_float2(-1.f, -1.f);
     const float2 d1 = __ffma2_rn(c, neg1, o);
@@ -302,7 +303,7 @@ __device__ __forceinline__ float2 face_flux2_br(float2 c, float2 o, float2 far, 
     if (LIM == ASUCA_LIM_LINEAR) {
         br = make_int2(2, 2);
         const float2 t = __ffma2_rn(d1, make_float2(1.f / 3.f, 1.f / 3.f), __fmul2_rn(d0, make_float2(1.f / 6.f, 1.f / 6.f)));
-        return __fmul2_rn(m2, __fadd2_rn(c, t));
+        return __fadd2_rn(c, t);
     }
     const float2 x = make_float2(sign_transfer(d1.x, d0.x), sign_transfer(d1.y, d0.y));
     const float2 a = make_float2(fabsf(d0.x), fabsf(d0.y));
@@ -317,7 +318,7 @@ __device__ __forceinline__ float2 face_flux2_br(float2 c, float2 o, float2 far, 
     };
     const float hx = pick(x.x, a.x, t.x, br.x);
     const float hy = pick(x.y, a.y, t.y, br.y);
-    return __fmul2_rn(m2, __fadd2_rn(c, make_float2(copysignf(hx, d0.x), copysignf(hy, d0.y))));
+    return __fadd2_rn(c, make_float2(copysignf(hx, d0.x), copysignf(hy, d0.y)));
 }
 
 // Face value at i+1/2 from the four cells i-1 .. i+2 and the upwind predicate u = (M >= 0).

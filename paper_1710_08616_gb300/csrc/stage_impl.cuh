@@ -364,17 +364,29 @@ __device__ __forceinline__ bool stage_tile_h(const StageParams<T> &p, const CUte
                 float2 rx, ry, rz;
                 if constexpr (REC) {
                     int2 bx, by, bz = make_int2(0, 0);
-                    rx = face_flux2_br<LIM>(make_float2(Sk[f0 + xc], Sk[f1 + xc]), make_float2(Sk[f0 + xo], Sk[f1 + xo]),
-                                            make_float2(Sk[f0 + xf], Sk[f1 + xf]), mup, bx);
-                    ry = face_flux2_br<LIM>(make_float2(Sk[f0 + yc], Sk[f1 + yc]), make_float2(Sk[f0 + yo], Sk[f1 + yo]),
-                                            make_float2(Sk[f0 + yf], Sk[f1 + yf]), mvp, by);
-                    rz = top ? make_float2(0.f, 0.f)
-                             : face_flux2_br<LIM>(make_float2(zc[f0], zc[f1]), make_float2(zo[f0], zo[f1]),
-                                                  make_float2(zf[f0], zf[f1]), mwp, bz);
+                    const float2 vx = face_val2_br<LIM>(make_float2(Sk[f0 + xc], Sk[f1 + xc]),
+                                                        make_float2(Sk[f0 + xo], Sk[f1 + xo]),
+                                                        make_float2(Sk[f0 + xf], Sk[f1 + xf]), bx);
+                    const float2 vy = face_val2_br<LIM>(make_float2(Sk[f0 + yc], Sk[f1 + yc]),
+                                                        make_float2(Sk[f0 + yo], Sk[f1 + yo]),
+                                                        make_float2(Sk[f0 + yf], Sk[f1 + yf]), by);
+                    const float2 vz = top ? make_float2(0.f, 0.f)
+                                          : face_val2_br<LIM>(make_float2(zc[f0], zc[f1]), make_float2(zo[f0], zo[f1]),
+                                                              make_float2(zf[f0], zf[f1]), bz);
+                    rx = __fmul2_rn(make_float2(mup, mup), vx);
+                    ry = __fmul2_rn(make_float2(mvp, mvp), vy);
+                    rz = top ? make_float2(0.f, 0.f) : __fmul2_rn(make_float2(mwp, mwp), vz);
                     if (valid) {
                         uint8_t *br = p.branch + (long long)f * nz * plane + (long long)k * plane + own;
                         br[0] = (uint8_t)(bx.x | (by.x << 2) | (bz.x << 4));
                         br[(long long)nz * plane] = (uint8_t)(bx.y | (by.y << 2) | (bz.y << 4));
+                        if (p.facev) {
+                            const long long fs = (long long)nz * plane, ds = (long long)NT * fs;
+                            T *fv = p.facev + (long long)f * fs + (long long)k * plane + own;
+                            fv[0] = vx.x; fv[fs] = vx.y;
+                            fv[ds] = vy.x; fv[ds + fs] = vy.y;
+                            fv[2 * ds] = vz.x; fv[2 * ds + fs] = vz.y;
+                        }
                     }
                 } else {
                     rx = face_flux2<LIM>(make_float2(Sk[f0 + xc], Sk[f1 + xc]), make_float2(Sk[f0 + xo], Sk[f1 + xo]),
@@ -396,10 +408,22 @@ __device__ __forceinline__ bool stage_tile_h(const StageParams<T> &p, const CUte
                 const int fo = (f + 1) * FE;
                 if constexpr (REC) {
                     int bx, by, bz = 0;
-                    xp[f] = face_flux_br<LIM>(Sk[fo + xc], Sk[fo + xo], Sk[fo + xf], mup, bx);
-                    yp[f] = face_flux_br<LIM>(Sk[fo + yc], Sk[fo + yo], Sk[fo + yf], mvp, by);
-                    zp[f] = top ? T(0) : face_flux_br<LIM>(zc[fo], zo[fo], zf[fo], mwp, bz);
-                    if (valid) p.branch[(long long)f * nz * plane + (long long)k * plane + own] = (uint8_t)(bx | (by << 2) | (bz << 4));
+                    const T vx = face_val_br<LIM>(Sk[fo + xc], Sk[fo + xo], Sk[fo + xf], bx);
+                    const T vy = face_val_br<LIM>(Sk[fo + yc], Sk[fo + yo], Sk[fo + yf], by);
+                    const T vz = top ? T(0) : face_val_br<LIM>(zc[fo], zo[fo], zf[fo], bz);
+                    xp[f] = mup * vx;
+                    yp[f] = mvp * vy;
+                    zp[f] = top ? T(0) : mwp * vz;
+                    if (valid) {
+                        p.branch[(long long)f * nz * plane + (long long)k * plane + own] = (uint8_t)(bx | (by << 2) | (bz << 4));
+                        if (p.facev) {
+                            const long long fs = (long long)nz * plane, ds = (long long)NT * fs;
+                            T *fv = p.facev + (long long)f * fs + (long long)k * plane + own;
+                            fv[0] = vx;
+                            fv[ds] = vy;
+                            fv[2 * ds] = vz;
+                        }
+                    }
                 } else {
                     xp[f] = face_flux<LIM>(Sk[fo + xc], Sk[fo + xo], Sk[fo + xf], mup);
                     yp[f] = face_flux<LIM>(Sk[fo + yc], Sk[fo + yo], Sk[fo + yf], mvp);
@@ -413,10 +437,22 @@ __device__ __forceinline__ bool stage_tile_h(const StageParams<T> &p, const CUte
                 const int fo = (f + 1) * FE;
                 if (REC) {
                     int bx, by, bz = 0;
-                    xp[f] = face_flux_br<LIM>(Sk[fo + xc], Sk[fo + xo], Sk[fo + xf], mup, bx);
-                    yp[f] = face_flux_br<LIM>(Sk[fo + yc], Sk[fo + yo], Sk[fo + yf], mvp, by);
-                    zp[f] = top ? T(0) : face_flux_br<LIM>(zc[fo], zo[fo], zf[fo], mwp, bz);
-                    if (valid) p.branch[(long long)f * nz * plane + (long long)k * plane + own] = (uint8_t)(bx | (by << 2) | (bz << 4));
+                    const T vx = face_val_br<LIM>(Sk[fo + xc], Sk[fo + xo], Sk[fo + xf], bx);
+                    const T vy = face_val_br<LIM>(Sk[fo + yc], Sk[fo + yo], Sk[fo + yf], by);
+                    const T vz = top ? T(0) : face_val_br<LIM>(zc[fo], zo[fo], zf[fo], bz);
+                    xp[f] = mup * vx;
+                    yp[f] = mvp * vy;
+                    zp[f] = top ? T(0) : mwp * vz;
+                    if (valid) {
+                        p.branch[(long long)f * nz * plane + (long long)k * plane + own] = (uint8_t)(bx | (by << 2) | (bz << 4));
+                        if (p.facev) {
+                            const long long fs = (long long)nz * plane, ds = (long long)NT * fs;
+                            T *fv = p.facev + (long long)f * fs + (long long)k * plane + own;
+                            fv[0] = vx;
+                            fv[ds] = vy;
+                            fv[2 * ds] = vz;
+                        }
+                    }
                 } else {
                     xp[f] = face_flux<LIM>(Sk[fo + xc], Sk[fo + xo], Sk[fo + xf], mup);
                     yp[f] = face_flux<LIM>(Sk[fo + yc], Sk[fo + yo], Sk[fo + yf], mvp);
