@@ -301,3 +301,25 @@ def make_ensemble_cases(members: int | None = None, *, sizes=None, nz=None, ntra
                              seed + 1000 * (m + 1), pattern_seed=seed,
                              perturb_seed=seed + 1000 * (m + 1), dtype=dtype))
     return out
+
+
+# Damping zone of the limited-area workloads: 16 edge cells (32 km), the top 8
+# levels, relaxation times of 5 and 10 minutes, a quarter into the boundary interval.
+DAMPING = dict(width=16, ntop=8, nu_lat=1.0 / 300.0, nu_top=1.0 / 600.0, tratio=0.25)
+
+
+def make_boundary_data(Y: np.ndarray, seed: int, *, dtype=np.float64):
+    """Reference state and two boundary datasets for a [F][nz][ny][nx] state Y:
+    ref = the level mean of each field (horizontally uniform, like a reference
+    atmosphere); bnd0 = Y - ref plus 1% noise (the perturbation at the start of
+    the boundary interval); bnd1 = bnd0 shifted by three cells in i and one in j
+    plus fresh noise (the perturbation moved on by the end of the interval).
+    Returns (ref, bnd0, bnd1), each [F][nz][ny][nx] of dtype."""
+    rng = np.random.default_rng(seed)
+    Y = np.asarray(Y)
+    ref = np.broadcast_to(Y.mean(axis=(2, 3), dtype=np.float64)[:, :, None, None], Y.shape).astype(dtype)
+    dev = Y.astype(dtype) - ref
+    scale = (0.01 * np.abs(ref[:, :, :1, :1])).astype(dtype)      # 1% of each field's level mean
+    b0 = dev + scale * rng.standard_normal(Y.shape, dtype=np.float32).astype(dtype)
+    b1 = np.roll(dev, (1, 3), axis=(2, 3)) + scale * rng.standard_normal(Y.shape, dtype=np.float32).astype(dtype)
+    return np.ascontiguousarray(ref), np.ascontiguousarray(b0), np.ascontiguousarray(b1)

@@ -75,6 +75,8 @@ def lib():
         L.orc_step_window.argtypes = [G, _D, _D, _D, _D, _D, ctypes.c_double, ctypes.c_int,
                                       ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D]
         L.orc_stencil7.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, _D, _D]
+        L.orc_damping.argtypes = [ctypes.c_int] * 6 + [ctypes.c_double] * 5 + [ctypes.c_longlong,
+                                  ctypes.POINTER(ctypes.c_int), _D, _D, _D, _D]
         L.orc_set_threads.argtypes = [ctypes.c_int]
         L.orc_get_threads.restype = ctypes.c_int
         _lib = L
@@ -182,6 +184,30 @@ def stencil7(field, c):
     out = np.empty_like(f)
     lib().orc_stencil7(nx, ny, nz, float(c), _p(f), _p(out))
     return out
+
+
+def damping(Y, ref, b0, b1, tratio, dt, *, width, ntop, nu_lat, nu_top, mtratio=None, ijk=None, shape=None):
+    """Lateral and upper damping toward boundary data (Sec. 2.1's damping kernel
+    target, relaxed implicitly).  Whole domain: Y, ref, b0, b1 are [F][nz][ny][nx].
+    Sampled cells: ijk is an [n][3] int array of (i, j, k), the arrays are
+    [F][n], and shape = (nx, ny, nz) gives the domain.  Returns the new Y."""
+    if mtratio is None:
+        mtratio = 1.0 - tratio
+    y = np.array(_f64(Y), dtype=np.float64, order="C", copy=True)
+    r, p0, p1 = (np.ascontiguousarray(_f64(a)) for a in (ref, b0, b1))
+    assert r.shape == y.shape and p0.shape == y.shape and p1.shape == y.shape
+    if ijk is None:
+        F, nz, ny, nx = y.shape
+        n, ip = 0, None
+    else:
+        nx, ny, nz = shape
+        idx = np.ascontiguousarray(ijk, dtype=np.int32)
+        F, n = y.shape
+        assert idx.shape == (n, 3)
+        ip = idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    lib().orc_damping(nx, ny, nz, F, int(width), int(ntop), float(nu_lat), float(nu_top), float(mtratio),
+                      float(tratio), float(dt), int(n), ip, _p(y), _p(r), _p(p0), _p(p1))
+    return y
 
 
 def budgets(g: Grid, Y, precip=0.0):

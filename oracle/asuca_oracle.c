@@ -1017,3 +1017,57 @@ void orc_stencil7(int nx, int ny, int nz, double c, const double *in, double *ou
         }
     }
 }
+
+/* ---- lateral and upper damping (Sec. 2.1, the damping kernel) --------------
+ * The paper's kernel forms the damping target: the reference state plus the
+ * boundary perturbation, weighted between two boundary datasets by mtratio
+ * and tratio.  It prints no damping operator; the reading is an implicit
+ * (backward Euler) Rayleigh relaxation toward that target,
+ * dy/dt = -nu (y - target), with a rate that grows quadratically toward the
+ * lateral edges over `width` cells and toward the model top over ntop levels,
+ * the larger of the two where the zones overlap. */
+static double damping_rate(int nx, int ny, int nz, int width, int ntop, double nu_lat, double nu_top, int i, int j,
+                           int k) {
+    int d = i;
+    if (nx - 1 - i < d) d = nx - 1 - i;
+    if (j < d) d = j;
+    if (ny - 1 - j < d) d = ny - 1 - j;
+    double lat = 0.0, top = 0.0;
+    if (d < width) {
+        const double x = (double)(width - d) / width;
+        lat = nu_lat * (x * x);
+    }
+    if (ntop > 0 && k >= nz - ntop) {
+        const double x = (double)(k - (nz - ntop) + 1) / ntop;
+        top = nu_top * (x * x);
+    }
+    return lat > top ? lat : top;
+}
+
+void orc_damping(int nx, int ny, int nz, int F, int width, int ntop, double nu_lat, double nu_top,
+                 double mtratio, double tratio, double dt, long long ncell, const int *ijk, double *y,
+                 const double *ref, const double *b0, const double *b1) {
+    const long long n = ijk ? ncell : (long long)nx * ny * nz;
+#ifdef _OPENMP
+#pragma omp parallel for
+#endif
+    for (long long c = 0; c < n; c++) {
+        int i, j, k;
+        if (ijk) {
+            i = ijk[3 * c];
+            j = ijk[3 * c + 1];
+            k = ijk[3 * c + 2];
+        } else {
+            i = (int)(c % nx);
+            j = (int)((c / nx) % ny);
+            k = (int)(c / ((long long)nx * ny));
+        }
+        const double a = dt * damping_rate(nx, ny, nz, width, ntop, nu_lat, nu_top, i, j, k);
+        for (int f = 0; f < F; f++) {
+            const long long q = (long long)f * n + c;
+            const double ptb = mtratio * (ref[q] + b0[q]) + tratio * (ref[q] + b1[q]) - ref[q];
+            const double target = ref[q] + ptb;
+            y[q] = (y[q] + a * target) / (1.0 + a);
+        }
+    }
+}

@@ -81,6 +81,18 @@ void orc_trajectory_branches(const orc_grid *g, const double *Y0, const double *
  * i and j, zero flux through both lids (ghost levels copy the boundary cell);
  * fields [nz][ny][nx]. */
 void orc_stencil7(int nx, int ny, int nz, double c, const double *in, double *out);
+/* Lateral and upper damping toward boundary data (Sec. 2.1, the damping
+ * kernel): for each listed cell (i, j, k) and field f,
+ *   ptb = mtratio (ref + b0) + tratio (ref + b1) - ref,  target = ref + ptb,
+ *   y <- (y + a target) / (1 + a),  a = dt max(nu_lat w_lat, nu_top w_top),
+ * w_lat = ((width - d) / width)^2 for d = min(i, nx-1-i, j, ny-1-j) < width,
+ * w_top = ((k - (nz - ntop) + 1) / ntop)^2 for k >= nz - ntop, else 0.
+ * ijk == NULL: every cell of the domain, arrays [F][nz][ny][nx] (ncell is
+ * ignored); else ijk holds ncell (i, j, k) triples and the arrays are
+ * [F][ncell], one column of values per listed cell. */
+void orc_damping(int nx, int ny, int nz, int F, int width, int ntop, double nu_lat, double nu_top,
+                 double mtratio, double tratio, double dt, long long ncell, const int *ijk, double *y,
+                 const double *ref, const double *b0, const double *b1);
 void orc_set_threads(int n);
 int orc_get_threads(void);
 

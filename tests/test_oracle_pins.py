@@ -461,3 +461,102 @@ def test_stencil7_linear_in_k_with_zero_flux_lids():
     assert np.array_equal(out[1:-1], f[1:-1])
     assert np.allclose(out[0], c, rtol=0, atol=1e-15)
     assert np.allclose(out[-1], (nz - 1) - c, rtol=0, atol=1e-14)
+
+
+# ------------------------------------------------------------------ lateral and upper damping (Sec. 2.1)
+
+def _damp_fields(F, nz, ny, nx, seed):
+    rng = np.random.default_rng(seed)
+    return [rng.standard_normal((F, nz, ny, nx)) for _ in range(4)]
+
+
+def test_damping_touches_exactly_the_zone():
+    """Only cells fewer than `width` cells from an i or j edge, or on the top
+    ntop levels, change; their number is the closed-form zone size
+    ntop nx ny + (nz - ntop) (nx ny - (nx - 2 width)(ny - 2 width))."""
+    F, nz, ny, nx, W, ntop = 3, 7, 11, 17, 3, 2
+    Y, R, B0, B1 = _damp_fields(F, nz, ny, nx, 1)
+    out = oracle.damping(Y, R, B0, B1, 0.3, 40.0, width=W, ntop=ntop, nu_lat=1e-2, nu_top=5e-3)
+    changed = np.any(out != Y, axis=0)
+    assert changed.sum() == ntop * nx * ny + (nz - ntop) * (nx * ny - (nx - 2 * W) * (ny - 2 * W))
+    kk, jj, ii = np.nonzero(changed)
+    d = np.minimum(np.minimum(ii, nx - 1 - ii), np.minimum(jj, ny - 1 - jj))
+    assert np.all((d < W) | (kk >= nz - ntop))
+
+
+def test_damping_zero_rate_is_the_identity():
+    Y, R, B0, B1 = _damp_fields(2, 5, 9, 10, 2)
+    out = oracle.damping(Y, R, B0, B1, 0.7, 30.0, width=4, ntop=5, nu_lat=0.0, nu_top=0.0)
+    assert np.array_equal(out, Y)
+
+
+@pytest.mark.parametrize("tratio", [0.0, 0.3, 1.0])
+def test_damping_strong_limit_is_the_interpolated_boundary_state(tratio):
+    """With a very large rate the implicit relaxation lands on its target, and
+    with mtratio = 1 - tratio the reference terms of the paper's target cancel:
+    target = ref + (1 - tratio) bnd0 + tratio bnd1."""
+    F, nz, ny, nx = 2, 4, 8, 9
+    Y, R, B0, B1 = _damp_fields(F, nz, ny, nx, 3)
+    out = oracle.damping(Y, R, B0, B1, tratio, 1.0, width=1, ntop=1, nu_lat=1e15, nu_top=1e15)
+    want = R + (1.0 - tratio) * B0 + tratio * B1
+    edge = np.zeros((nz, ny, nx), bool)
+    edge[:, 0, :] = edge[:, -1, :] = edge[:, :, 0] = edge[:, :, -1] = True
+    edge[-1] = True
+    assert np.max(np.abs(out[:, edge] - want[:, edge])) <= 1e-12
+    assert np.array_equal(out[:, ~edge], Y[:, ~edge])
+
+
+def test_damping_is_backward_euler_of_the_relaxation_ode():
+    """Repeated calls with a fixed target integrate dy/dt = -nu (y - target):
+    the result stays between y0 and the target for any step (unconditionally
+    stable, monotone), and converges at first order to the exact
+    target + (y0 - target) exp(-nu t)."""
+    nu, t, y0, T = 1.0 / 300.0, 900.0, 2.0, -1.0
+    shape = (1, 1, 2, 2)                   # every cell is an edge cell (d = 0, full rate)
+    R = np.full(shape, T)
+    Z = np.zeros(shape)
+    exact = T + (y0 - T) * math.exp(-nu * t)
+    errs = []
+    for n in (8, 16, 32, 64):
+        y = np.full(shape, y0)
+        for _ in range(n):
+            y = oracle.damping(y, R, Z, Z, 0.5, t / n, width=1, ntop=0, nu_lat=nu, nu_top=0.0)
+            assert np.all((y > T) & (y < y0))
+        errs.append(abs(y[0, 0, 0, 0] - exact))
+    for a, b in zip(errs, errs[1:]):
+        assert 1.8 < a / b < 2.2
+    y = oracle.damping(np.full(shape, y0), R, Z, Z, 0.5, 1e9, width=1, ntop=0, nu_lat=nu, nu_top=0.0)
+    assert T < y[0, 0, 0, 0] < T + 1e-6
+
+
+def test_damping_mirror_symmetry_and_profile_shape():
+    """The zone is symmetric under i -> nx-1-i and j -> ny-1-j, and the rate
+    falls off from the edges: with y = 1, target = 0 the damped value rises
+    strictly from the outermost cell inward (and from the top level down)
+    and reaches 1 outside the zone."""
+    F, nz, ny, nx, W, ntop = 2, 6, 12, 14, 4, 3
+    Y, R, B0, B1 = _damp_fields(F, nz, ny, nx, 4)
+    kw = dict(width=W, ntop=ntop, nu_lat=2e-2, nu_top=1e-2)
+    out = oracle.damping(Y, R, B0, B1, 0.4, 25.0, **kw)
+    flip = lambda a: a[:, :, ::-1, ::-1]
+    assert np.array_equal(flip(oracle.damping(flip(Y), flip(R), flip(B0), flip(B1), 0.4, 25.0, **kw)), out)
+    one, zero = np.ones((1, nz, ny, nx)), np.zeros((1, nz, ny, nx))
+    p = oracle.damping(one, zero, zero, zero, 0.5, 25.0, **kw)[0]
+    row = p[0, ny // 2, :nx // 2]          # bottom level, middle row, from the left edge inward
+    assert np.all(np.diff(row[:W + 1]) > 0) and np.all(row[W:] == 1.0)
+    col = p[nz - ntop - 1:, ny // 2, nx // 2]    # centre column, from below the top zone upward
+    assert col[0] == 1.0 and np.all(np.diff(col) < 0)
+
+
+def test_damping_sampled_cells_equal_the_whole_domain():
+    """The sampled-cell form (explicit (i, j, k) list, [F][n] arrays) gives the
+    whole-domain result at those cells."""
+    F, nz, ny, nx = 3, 5, 9, 11
+    Y, R, B0, B1 = _damp_fields(F, nz, ny, nx, 5)
+    kw = dict(width=3, ntop=2, nu_lat=1e-2, nu_top=3e-3)
+    full = oracle.damping(Y, R, B0, B1, 0.6, 20.0, **kw)
+    rng = np.random.default_rng(6)
+    ijk = np.stack([rng.integers(0, nx, 40), rng.integers(0, ny, 40), rng.integers(0, nz, 40)], axis=1)
+    g = lambda a: a[:, ijk[:, 2], ijk[:, 1], ijk[:, 0]]
+    part = oracle.damping(g(Y), g(R), g(B0), g(B1), 0.6, 20.0, ijk=ijk, shape=(nx, ny, nz), **kw)
+    assert np.array_equal(part, g(full))
