@@ -406,6 +406,51 @@ def layout_ablation(asuca, dev, reps=10):
     return out
 
 
+def damping_report(asuca, dev, reps=10, nx=None, precs=("fp32", "fp64")):
+    """Lateral and upper damping toward boundary data (asuca_damping) on the
+    1024x1024x58, 8-tracer state with the workload's zone (16 edge cells, top 8
+    levels), FP32 and FP64.  The kernel streams ref, bnd0, bnd1 and the state in
+    and the state out for every zone cell: 5 F values per zone cell, against the
+    measured HBM peak.  Its inputs (1.7 GB FP32 per launch) exceed L2."""
+    import torch
+    import gen
+    case = gen.make_config_case(WORKLOAD, nx=nx, ny=nx)
+    D = gen.DAMPING
+    peak, _ = _peaks()
+    nx, ny, nz, W, ntop, F = case.nx, case.ny, case.nz, D["width"], D["ntop"], case.nfields
+    zone = ntop * nx * ny + (nz - ntop) * (nx * ny - (nx - 2 * W) * (ny - 2 * W))
+    Y = case.state()
+    bnd = [torch.from_numpy(a).to(dev) for a in gen.make_boundary_data(Y, case.seed + 17)]
+    out = {"workload": f"damping_{nx}x{ny}x{nz}_width{W}_top{ntop}", "zone_cells": zone,
+           "zone_fraction": zone / case.cells, "algorithmic_bytes": "5 F values per zone cell"}
+    for name, prec, dt in (("fp32", asuca.FP32_MIXED, torch.float32), ("fp64", asuca.FP64, torch.float64)):
+        if name not in precs:
+            continue
+        g = asuca.Grid.from_case(case, prec=prec)
+        st = asuca.State.from_case(case, prec=prec, device=dev)
+        ref, b0, b1 = (b.to(dt) for b in bnd)
+        call = lambda: asuca.damping(g, st, ref, b0, b1, D["tratio"], case.dt, width=W, ntop=ntop,
+                                     nu_lat=D["nu_lat"], nu_top=D["nu_top"])
+        for _ in range(3):
+            call()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            call()
+        e1.record()
+        torch.cuda.synchronize()
+        assert asuca.get_status(g) == asuca.OK
+        ms = e0.elapsed_time(e1) / reps
+        algo = 5 * F * dt.itemsize * zone
+        out[name] = {"ms": ms, "launches": reps, "achieved_gbs": algo / (ms * 1e-3) / 1e9,
+                     "frac": algo / (ms * 1e-3) / 1e9 / peak, "peak_gbs": peak}
+        del st, ref, b0, b1
+    del bnd
+    torch.cuda.empty_cache()
+    return out
+
+
 def ensemble_throughput(asuca, dev, nsteps=10, reps=3):
     """32 members with nx = ny drawn from U{64..320}, 58 levels, 4 tracers, FP32:
     cell-updates/s of one persistent launch per call (graph-replayed) against the
@@ -688,6 +733,9 @@ def run_ours(args):
     layout = None
     if not args.no_layout:
         layout = layout_ablation(asuca, dev)
+    damping = None
+    if not args.no_damping:
+        damping = damping_report(asuca, dev)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -704,7 +752,7 @@ def run_ours(args):
                           "parallelism": f"{world} independent replica(s), one per GPU"},
                "clocks": clocks, "gpu_launches": sum(n for _t, n in (prof or {}).values()), "roofline": roofline,
                "e2e": e2e, "fp64": fp64, "precision": precision, "adjoint": adjoint, "ensemble": ensemble,
-               "layout_ablation": layout,
+               "layout_ablation": layout, "damping": damping,
                "fp32_over_fp64_speedup": (value / fp64["value"]) if fp64 else None,
                "cpu_baseline": cpu}
         print(json.dumps(out), flush=True)
@@ -732,6 +780,7 @@ def main():
     ap.add_argument("--no-precision", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-layout", action="store_true")
+    ap.add_argument("--no-damping", action="store_true")
     ap.add_argument("--ens-steps", type=int, default=10)
     ap.add_argument("--nx", type=int, default=1024,
                     help="nx = ny of the timed case; anything but 1024 is a smaller case of the same "
@@ -739,11 +788,23 @@ def main():
     ap.add_argument("--adjoint-probe", choices=["fp32", "fp64"], default=None,
                     help="run one adjoint step of the 128x128x58 workload twice (recomputed from one "
                          "checkpoint) and exit: a small fixed launch sequence for profiler captures")
+    ap.add_argument("--damping-probe", choices=["fp32", "fp64"], default=None,
+                    help="time the damping alone on the nx x nx x 58 case in one precision and exit "
+                         "(a small launch sequence for profiler captures)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.adjoint_probe:
         return adjoint_probe(args.adjoint_probe)
+    if args.damping_probe:
+        import torch
+        from paper_1710_08616_gb300 import build as _b
+        _b.build()
+        import paper_1710_08616_gb300 as asuca
+        torch.cuda.set_device(0)
+        print(json.dumps(damping_report(asuca, torch.device("cuda", 0), reps=3, nx=args.nx,
+                                        precs=(args.damping_probe,))), flush=True)
+        return 0
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

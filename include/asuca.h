@@ -311,6 +311,42 @@ asuca_status asuca_column_noalloc(asuca_grid *grid, asuca_state *state, double d
 asuca_status asuca_stencil7(const void *in, void *out, int nx, int ny, int nz, int layout, int prec, double c,
                             void *cuda_stream);
 
+/* ---- lateral and upper damping -----------------------------------------
+ * Relaxation of the prognostic fields toward boundary data in a damping zone,
+ * the kernel Sec. 2.1 ("Parallel Loop Abstraction") takes from the dynamical
+ * core: the damping target is the reference state plus the boundary
+ * perturbation interpolated in time between two boundary datasets,
+ *   ptb_damp = mtratio (ref + bnd0) + tratio (ref + bnd1) - ref,
+ *   target   = ref + ptb_damp,
+ * (mtratio = 1 - tratio for an interpolation at the fraction tratio of the
+ * boundary interval), and every field relaxes toward it implicitly:
+ *   y <- (y + a target) / (1 + a),   a = dt nu(i, j, k),
+ *   nu = max(nu_lat w_lat, nu_top w_top),
+ *   w_lat = ((width - d) / width)^2 for d < width, d = min(i, nx-1-i, j, ny-1-j),
+ *   w_top = ((k - (nz - ntop) + 1) / ntop)^2 on the top ntop levels,
+ * both zero elsewhere.  Cells outside the zone are not read or written.
+ * The paper prints the target formula only; the relaxation form and the
+ * quadratic profiles are this library's choice.
+ *   - state: the grid's fields (rho, rho theta, rho q; mu, mv, mw unused),
+ *     updated in place; ref, bnd0, bnd1: caller-owned device arrays of
+ *     [F][nz][ny][nx] values in the grid's precision, F = 2 + N in the order
+ *     rho, rho theta, tracers (conserved variables, like the state).
+ *   - 0 <= width <= ASUCA_DAMP_MAX_WIDTH, 2 width <= min(nx, ny);
+ *     0 <= ntop <= nz; nu_lat, nu_top, dt >= 0 and finite; mtratio, tratio
+ *     finite.  Otherwise (or a null pointer) ASUCA_ERR_ARG.
+ *   - Asynchronous on the stream; the grid's device must be current. */
+#define ASUCA_DAMP_MAX_WIDTH 64
+typedef struct {
+    int width;       /* lateral zone: cells fewer than `width` cells from an i or j edge */
+    int ntop;        /* upper zone: the top ntop levels */
+    double nu_lat;   /* damping rate (1/s) at the outermost cells */
+    double nu_top;   /* damping rate (1/s) at the top level */
+} asuca_damping_desc;
+
+asuca_status asuca_damping(asuca_grid *grid, asuca_state *state, const void *ref, const void *bnd0,
+                           const void *bnd1, double mtratio, double tratio, double dt,
+                           const asuca_damping_desc *desc, void *cuda_stream);
+
 /* ---- per-kernel timing ------------------------------------------------- */
 
 typedef enum {

@@ -53,6 +53,11 @@ class StateStruct(ctypes.Structure):
                 ("mu", ctypes.c_void_p), ("mv", ctypes.c_void_p), ("mw", ctypes.c_void_p)]
 
 
+class DampingDesc(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int), ("ntop", ctypes.c_int), ("nu_lat", ctypes.c_double),
+                ("nu_top", ctypes.c_double)]
+
+
 _lib = None
 _VP = ctypes.c_void_p
 
@@ -73,6 +78,8 @@ SIGNATURES = {
     "asuca_column_noalloc": (ctypes.c_int, [_VP, ctypes.POINTER(StateStruct), ctypes.c_double, _VP, _VP]),
     "asuca_stencil7": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                       ctypes.c_double, _VP]),
+    "asuca_damping": (ctypes.c_int, [_VP, ctypes.POINTER(StateStruct), _VP, _VP, _VP, ctypes.c_double,
+                                     ctypes.c_double, ctypes.c_double, ctypes.POINTER(DampingDesc), _VP]),
     "asuca_adjoint_workspace_bytes": (ctypes.c_size_t, [_VP, ctypes.c_int, ctypes.c_int]),
     "asuca_adjoint_step": (ctypes.c_int, [_VP, ctypes.POINTER(StateStruct), _VP, ctypes.c_double, ctypes.c_int,
                                           ctypes.c_int, _VP, _VP, _VP, _VP, _VP, _VP, ctypes.c_size_t, _VP]),
@@ -203,7 +210,7 @@ class State:
     def from_case(cls, case, prec=FP32_MIXED, device="cuda"):
         import torch
         dt = torch.float64 if prec == FP64 else torch.float32
-        t = lambda a: torch.as_tensor(np.ascontiguousarray(a)).to(device=device, dtype=dt).contiguous()
+        t = lambda a: torch.as_tensor(np.require(a, requirements=['C', 'W'])).to(device=device, dtype=dt).contiguous()
         rhoq = case.rhoq if case.ntracers > 0 else np.zeros((0,) + case.rho.shape)
         return cls(t(case.rho), t(case.rhotheta), t(rhoq), t(case.mu), t(case.mv), t(case.mw))
 
@@ -318,6 +325,29 @@ def stencil7(inp, out, c: float, layout: int = LAYOUT_IJK, *, stream=None):
     _check(lib().asuca_stencil7(_ptr(inp), _ptr(out), nx, ny, nz, int(layout), prec, float(c), _stream_ptr(stream)),
            "asuca_stencil7")
     return out
+
+
+DAMP_MAX_WIDTH = 64
+
+
+def damping(grid: Grid, state: State, ref, bnd0, bnd1, tratio: float, dt: float, *, width: int, ntop: int,
+            nu_lat: float, nu_top: float, mtratio=None, stream=None):
+    """Lateral and upper damping toward boundary data (asuca_damping), in place:
+    target = ref + mtratio (ref + bnd0) + tratio (ref + bnd1) - ref, y relaxed
+    implicitly toward it with rate nu in the zone of `width` edge cells and
+    `ntop` top levels.  ref, bnd0, bnd1: contiguous CUDA [F][nz][ny][nx] tensors
+    of the grid's dtype; mtratio defaults to 1 - tratio."""
+    _check_state(grid, state)
+    shape = (grid.nfields, grid.nz, grid.ny, grid.nx)
+    for name, t in (("ref", ref), ("bnd0", bnd0), ("bnd1", bnd1)):
+        if tuple(t.shape) != shape or t.dtype != grid.torch_dtype or not t.is_contiguous() or not t.is_cuda:
+            raise ValueError(f"{name}: need contiguous CUDA {grid.torch_dtype} of shape {shape}")
+    if mtratio is None:
+        mtratio = 1.0 - tratio
+    d = DampingDesc(int(width), int(ntop), float(nu_lat), float(nu_top))
+    s = state.struct()
+    _check(lib().asuca_damping(grid.handle, ctypes.byref(s), _ptr(ref), _ptr(bnd0), _ptr(bnd1), float(mtratio),
+                               float(tratio), float(dt), ctypes.byref(d), _stream_ptr(stream)), "asuca_damping")
 
 
 def profile_enable(grid: Grid, on: bool = True):

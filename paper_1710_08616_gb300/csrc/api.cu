@@ -1,6 +1,7 @@
 // Host side of the C ABI declared in include/asuca.h: argument checks,
 // level tables, workspace layout and the launch sequence of one call.
 #include <cmath>
+#include <algorithm>
 #include <cstring>
 #include <new>
 #include <cstdlib>
@@ -12,6 +13,7 @@
 #include "adjoint_params.cuh"
 #include "ensemble_params.cuh"
 #include "dataflow_params.cuh"
+#include "damping.cuh"
 #include "common.cuh"
 
 using namespace asuca;
@@ -1552,6 +1554,38 @@ asuca_status asuca_stencil7(const void *in, void *out, int nx, int ny, int nz, i
     const cudaError_t e = prec == ASUCA_FP64
                               ? launch_stencil7<double>((const double *)in, (double *)out, nx, ny, nz, layout, c, s)
                               : launch_stencil7<float>((const float *)in, (float *)out, nx, ny, nz, layout, (float)c, s);
+    return cuda_status(e);
+}
+
+asuca_status asuca_damping(asuca_grid *g, asuca_state *st, const void *ref, const void *bnd0, const void *bnd1,
+                           double mtratio, double tratio, double dt, const asuca_damping_desc *desc,
+                           void *cuda_stream) {
+    if (!g || !st || !st->rho || !st->rhotheta || (g->d.ntracers && !st->rhoq) || !ref || !bnd0 || !bnd1 || !desc)
+        return ASUCA_ERR_ARG;
+    const int nx = g->d.nx, ny = g->d.ny, nz = g->d.nz;
+    const asuca_damping_desc &dd = *desc;
+    if (dd.width < 0 || dd.width > ASUCA_DAMP_MAX_WIDTH || 2 * dd.width > std::min(nx, ny) || dd.ntop < 0 ||
+        dd.ntop > nz || !std::isfinite(dd.nu_lat) || dd.nu_lat < 0.0 || !std::isfinite(dd.nu_top) ||
+        dd.nu_top < 0.0 || !std::isfinite(dt) || dt < 0.0 || !std::isfinite(mtratio) || !std::isfinite(tratio))
+        return ASUCA_ERR_ARG;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return ASUCA_ERR_CUDA;
+    if (dev != g->device) return ASUCA_ERR_ARG;
+    asuca_status prev = take_status(g);
+    if (prev != ASUCA_OK) return prev;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    cudaError_t e;
+    if (g->d.prec == ASUCA_FP64) {
+        double *y[MAXF];
+        field_ptrs<double>(g, st->rho, st->rhotheta, st->rhoq, y);
+        e = launch_damping<double>(y, g->F, (const double *)ref, (const double *)bnd0, (const double *)bnd1, nx, ny,
+                                   nz, dd.width, dd.ntop, dd.nu_lat, dd.nu_top, mtratio, tratio, dt, g->nsm, s);
+    } else {
+        float *y[MAXF];
+        field_ptrs<float>(g, st->rho, st->rhotheta, st->rhoq, y);
+        e = launch_damping<float>(y, g->F, (const float *)ref, (const float *)bnd0, (const float *)bnd1, nx, ny,
+                                  nz, dd.width, dd.ntop, dd.nu_lat, dd.nu_top, mtratio, tratio, dt, g->nsm, s);
+    }
     return cuda_status(e);
 }
 
