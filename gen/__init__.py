@@ -7,4 +7,5 @@ and the time step length that both implementations take as inputs.
 from .fields import (  # noqa: F401
     CONFIGS, SEED_BASE, Case, make_dz, make_case, make_config_case,
     make_ensemble_cases, ensemble_sizes, DAMPING, make_boundary_data,
+    ACOUSTIC, make_acoustic_state,
 )

@@ -323,3 +323,29 @@ def make_boundary_data(Y: np.ndarray, seed: int, *, dtype=np.float64):
     b0 = dev + scale * rng.standard_normal(Y.shape, dtype=np.float32).astype(dtype)
     b1 = np.roll(dev, (1, 3), axis=(2, 3)) + scale * rng.standard_normal(Y.shape, dtype=np.float32).astype(dtype)
     return np.ascontiguousarray(ref), np.ascontiguousarray(b0), np.ascontiguousarray(b1)
+
+
+# Acoustic short steps: sound speed 340 m/s, off-centred implicit weight 0.6,
+# 2 s short steps (horizontal acoustic Courant number 0.34 at 2 km), six short
+# steps per call.
+ACOUSTIC = dict(cs2=340.0 ** 2, beta=0.6, dtau=2.0, nshort=6, g=9.81, rho_s=1.2)
+
+
+def make_acoustic_state(case: Case, *, dtype=np.float64):
+    """Inputs of the acoustic short steps on a case's grid: the base density
+    rho0 = rho_s exp(-g z / c^2) at level centres and faces (a base state in
+    hydrostatic balance with p0 = c^2 rho0), and perturbations taken from the
+    case: s = rho'/rho0 = 5e-4 (theta - theta_ref) from its theta bubbles
+    (|s| <= 1e-3), momenta U, V, W = 0.05 MU, MV, MW (|u'| about 1 m/s).
+    Returns (U, V, W, S, rho0c, rho0f)."""
+    A = ACOUSTIC
+    dz = np.asarray(case.dz, dtype=np.float64)
+    zf = np.concatenate([[0.0], np.cumsum(dz)])
+    zc = zf[:-1] + 0.5 * dz
+    rho0c = A["rho_s"] * np.exp(-A["g"] * zc / A["cs2"])
+    rho0f = A["rho_s"] * np.exp(-A["g"] * zf / A["cs2"])
+    theta = np.asarray(case.rhotheta, np.float64) / np.asarray(case.rho, np.float64)
+    S = 5e-4 * (theta - (300.0 + 0.004 * zc)[:, None, None])
+    cast = (lambda a: np.ascontiguousarray(a, dtype=dtype))
+    return (cast(0.05 * np.asarray(case.mu)), cast(0.05 * np.asarray(case.mv)), cast(0.05 * np.asarray(case.mw)),
+            cast(S), rho0c, rho0f)

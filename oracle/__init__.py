@@ -75,6 +75,8 @@ def lib():
         L.orc_step_window.argtypes = [G, _D, _D, _D, _D, _D, ctypes.c_double, ctypes.c_int,
                                       ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D]
         L.orc_stencil7.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, _D, _D]
+        L.orc_acoustic.argtypes = [ctypes.c_int] * 3 + [ctypes.c_double] * 2 + [_D, _D, _D] + \
+            [ctypes.c_double] * 3 + [ctypes.c_int, _D, _D, _D, _D]
         L.orc_damping.argtypes = [ctypes.c_int] * 6 + [ctypes.c_double] * 5 + [ctypes.c_longlong,
                                   ctypes.POINTER(ctypes.c_int), _D, _D, _D, _D]
         L.orc_set_threads.argtypes = [ctypes.c_int]
@@ -208,6 +210,20 @@ def damping(Y, ref, b0, b1, tratio, dt, *, width, ntop, nu_lat, nu_top, mtratio=
     lib().orc_damping(nx, ny, nz, F, int(width), int(ntop), float(nu_lat), float(nu_top), float(mtratio),
                       float(tratio), float(dt), int(n), ip, _p(y), _p(r), _p(p0), _p(p1))
     return y
+
+
+def acoustic(U, V, W, S, dz, rho0c, rho0f, cs2, beta, dtau, nshort, dx=2000.0, dy=2000.0):
+    """nshort HEVI short steps of the linear acoustic-gravity system (Sec. 1.1).
+    U, V, S: [nz][ny][nx]; W: [nz+1][ny][nx] (W[0], W[nz] rigid lids, kept).
+    Returns new (U, V, W, S) arrays."""
+    U, V, W, S = (np.array(_f64(a), dtype=np.float64, order="C", copy=True) for a in (U, V, W, S))
+    nz, ny, nx = S.shape
+    assert U.shape == S.shape and V.shape == S.shape and W.shape == (nz + 1, ny, nx)
+    dz, r0c, r0f = (np.ascontiguousarray(_f64(a)) for a in (dz, rho0c, rho0f))
+    assert dz.shape == (nz,) and r0c.shape == (nz,) and r0f.shape == (nz + 1,)
+    lib().orc_acoustic(nx, ny, nz, float(dx), float(dy), _p(dz), _p(r0c), _p(r0f), float(cs2), float(beta),
+                       float(dtau), int(nshort), _p(U), _p(V), _p(W), _p(S))
+    return U, V, W, S
 
 
 def budgets(g: Grid, Y, precip=0.0):

@@ -1071,3 +1071,123 @@ void orc_damping(int nx, int ny, int nz, int F, int width, int ntop, double nu_l
         }
     }
 }
+
+/* ---- HEVI acoustic short steps (Sec. 1.1: sound and gravity waves in a
+ * second-order Runge-Kutta scheme, horizontally explicit, vertically implicit)
+ * The paper names the scheme only.  The reading: the linear acoustic-gravity
+ * system about a resting, horizontally uniform base state rho0(z), written
+ * for the momenta U, V (faces i+1/2, j+1/2), W (faces k-1/2, rigid lids) and
+ * s = rho'/rho0 at the centres,
+ *   dU/dt = -c^2 rho0_k (s_{i+1} - s_i) / dx,   dV/dt likewise in j,
+ *   dW_f/dt = -c^2 rho0f_f (s_f - s_{f-1}) / dzc_f,   dzc_f = (dz_{f-1} + dz_f) / 2,
+ *   rho0_k ds/dt = -[(U_{i+1/2} - U_{i-1/2})/dx + (V_{j+1/2} - V_{j-1/2})/dy + (W_{k+1} - W_k)/dz_k],
+ * (for rho0 = rho_s exp(-g z / c^2) the W equation is dW/dt = -dp'/dz - g rho').
+ * A short step of length h is two stages from the same start (U, V, W, s):
+ *   stage 1 (tau = h/2): U* = U - tau G_x(s); (W*, s*) implicit with Dh(U*, V*);
+ *   stage 2 (tau = h):   U+ = U - tau G_x(s*); (W+, s+) implicit with Dh(U*, V*);
+ * the implicit part weights the new and old vertical terms by beta, 1 - beta:
+ *   W'_f = W_f - tau c^2 rho0f_f [beta (s'_f - s'_{f-1}) + (1-beta)(s_f - s_{f-1})] / dzc_f
+ *   rho0_k s'_k = rho0_k s_k - tau [Dh_k + (beta (W'_{k+1} - W'_k) + (1-beta)(W_{k+1} - W_k)) / dz_k]
+ * Here the two implicit equations are solved together as written: with the
+ * unknowns interleaved (s'_0, W'_1, s'_1, ..., W'_{nz-1}, s'_{nz-1}) the
+ * system is tridiagonal, solved by plain Gaussian elimination. */
+static void acoustic_column(int nz, const double *dz, const double *rho0c, const double *rho0f, double cs2,
+                            double beta, double tau, const double *Dh, const double *W, const double *s,
+                            double *Wn, double *sn, double *lo, double *di, double *up, double *rhs) {
+    /* row 2k: the s'_k equation, row 2f-1: the W'_f equation */
+    const int n = 2 * nz - 1;
+    for (int k = 0; k < nz; k++) {
+        const int r = 2 * k;
+        const double Wk = k > 0 ? W[k] : 0.0, Wk1 = k < nz - 1 ? W[k + 1] : 0.0;
+        /* rho0 s' + tau beta (W'_{k+1} - W'_k)/dz = rho0 s - tau Dh - tau (1-beta)(W_{k+1} - W_k)/dz */
+        di[r] = rho0c[k];
+        lo[r] = k > 0 ? -tau * beta / dz[k] : 0.0;
+        up[r] = k < nz - 1 ? tau * beta / dz[k] : 0.0;
+        rhs[r] = rho0c[k] * s[k] - tau * Dh[k] - tau * (1.0 - beta) * (Wk1 - Wk) / dz[k];
+    }
+    for (int f = 1; f < nz; f++) {
+        const int r = 2 * f - 1;
+        const double dzc = 0.5 * (dz[f - 1] + dz[f]);
+        const double g = tau * cs2 * rho0f[f] / dzc;
+        /* W'_f + g beta (s'_f - s'_{f-1}) = W_f - g (1-beta)(s_f - s_{f-1}) */
+        di[r] = 1.0;
+        lo[r] = -g * beta;
+        up[r] = g * beta;
+        rhs[r] = W[f] - g * (1.0 - beta) * (s[f] - s[f - 1]);
+    }
+    /* forward elimination, no pivoting, then back substitution */
+    for (int r = 1; r < n; r++) {
+        const double m = lo[r] / di[r - 1];
+        di[r] -= m * up[r - 1];
+        rhs[r] -= m * rhs[r - 1];
+    }
+    double x = rhs[n - 1] / di[n - 1];
+    sn[nz - 1] = x;
+    for (int r = n - 2; r >= 0; r--) {
+        x = (rhs[r] - up[r] * x) / di[r];
+        if (r % 2 == 0) sn[r / 2] = x;
+        else Wn[(r + 1) / 2] = x;
+    }
+    Wn[0] = 0.0;
+    Wn[nz] = 0.0;
+}
+
+/* nshort HEVI short steps of length h, in place (fields as in the header) */
+void orc_acoustic(int nx, int ny, int nz, double dx, double dy, const double *dz, const double *rho0c,
+                  const double *rho0f, double cs2, double beta, double h, int nshort, double *U, double *V,
+                  double *W, double *S) {
+    const long long plane = (long long)nx * ny, n = plane * nz;
+    double *Us = (double *)malloc(n * sizeof(double)), *Vs = (double *)malloc(n * sizeof(double));
+    double *Ss = (double *)malloc(n * sizeof(double));
+    double *Up = (double *)malloc(n * sizeof(double)), *Vp = (double *)malloc(n * sizeof(double));
+    for (int step = 0; step < nshort; step++) {
+        for (int stage = 0; stage < 2; stage++) {
+            const double tau = stage == 0 ? 0.5 * h : h;
+            const double *se = stage == 0 ? S : Ss;        /* s that drives the horizontal momenta */
+            double *Uo = stage == 0 ? Us : Up, *Vo = stage == 0 ? Vs : Vp;
+            for (int k = 0; k < nz; k++)
+                for (int j = 0; j < ny; j++)
+                    for (int i = 0; i < nx; i++) {
+                        const long long c = k * plane + (long long)j * nx + i;
+                        const long long e = k * plane + (long long)j * nx + wrap(i + 1, nx);
+                        const long long no = k * plane + (long long)wrap(j + 1, ny) * nx + i;
+                        Uo[c] = U[c] - tau * cs2 * rho0c[k] * (se[e] - se[c]) / dx;
+                        Vo[c] = V[c] - tau * cs2 * rho0c[k] * (se[no] - se[c]) / dy;
+                    }
+#ifdef _OPENMP
+#pragma omp parallel
+#endif
+            {
+                /* per column: Dh nz, Wc nz+1, sc nz, Wn nz+1, sn nz, and the four rows of
+                 * the interleaved system, 2 nz - 1 each (2 nz allotted): 13 nz + 2 doubles */
+                double *col = (double *)malloc((size_t)(13 * nz + 2) * sizeof(double));
+                double *Dh = col, *Wc = Dh + nz, *sc = Wc + nz + 1, *Wn = sc + nz, *sn = Wn + nz + 1;
+                double *lo = sn + nz, *di = lo + 2 * nz, *up = di + 2 * nz, *rhs = up + 2 * nz;
+#ifdef _OPENMP
+#pragma omp for
+#endif
+                for (long long q = 0; q < plane; q++) {
+                    const int j = (int)(q / nx), i = (int)(q % nx);
+                    const long long w = (long long)j * nx + wrap(i - 1, nx), so = (long long)wrap(j - 1, ny) * nx + i;
+                    for (int k = 0; k < nz; k++) {
+                        const long long c = k * plane + q;
+                        Dh[k] = (Us[c] - Us[k * plane + w]) / dx + (Vs[c] - Vs[k * plane + so]) / dy;
+                        sc[k] = S[c];
+                    }
+                    for (int f = 0; f <= nz; f++) Wc[f] = W[f * plane + q];
+                    acoustic_column(nz, dz, rho0c, rho0f, cs2, beta, tau, Dh, Wc, sc, Wn, sn, lo, di, up, rhs);
+                    if (stage == 0) {
+                        for (int k = 0; k < nz; k++) Ss[k * plane + q] = sn[k];
+                    } else {
+                        for (int k = 0; k < nz; k++) S[k * plane + q] = sn[k];
+                        for (int f = 1; f < nz; f++) W[f * plane + q] = Wn[f];
+                    }
+                }
+                free(col);
+            }
+        }
+        memcpy(U, Up, n * sizeof(double));
+        memcpy(V, Vp, n * sizeof(double));
+    }
+    free(Us); free(Vs); free(Ss); free(Up); free(Vp);
+}

@@ -93,6 +93,14 @@ void orc_stencil7(int nx, int ny, int nz, double c, const double *in, double *ou
 void orc_damping(int nx, int ny, int nz, int F, int width, int ntop, double nu_lat, double nu_top,
                  double mtratio, double tratio, double dt, long long ncell, const int *ijk, double *y,
                  const double *ref, const double *b0, const double *b1);
+/* nshort HEVI short steps of the linear acoustic-gravity system (Sec. 1.1), in
+ * place: U, V, S [nz][ny][nx] (U at faces i+1/2, V at j+1/2, S = rho'/rho0 at
+ * the centres), W [nz+1][ny][nx] (face below cell k; W[0] and W[nz] are rigid
+ * lids, never read, left as they are).  rho0c[nz], rho0f[nz+1] base density at
+ * centres and faces, cs2 the squared sound speed, beta the implicit weight. */
+void orc_acoustic(int nx, int ny, int nz, double dx, double dy, const double *dz, const double *rho0c,
+                  const double *rho0f, double cs2, double beta, double h, int nshort, double *U, double *V,
+                  double *W, double *S);
 void orc_set_threads(int n);
 int orc_get_threads(void);
 

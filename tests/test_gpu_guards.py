@@ -2,8 +2,8 @@
 a larger allocation whose guard bands (4 KiB on each side) hold a fixed bit
 pattern, and after the call the bands must be unchanged.  This covers every
 kernel of the step (fused and separate column pass, dataflow mode), the
-adjoint, the checkpointed forward, the ensemble, the sub-step entry points
-and the storage-order stencil, on ragged and limit sizes."""
+adjoint, the checkpointed forward, the ensemble, the sub-step entry points,
+the storage-order stencil and the damping, on ragged and limit sizes."""
 import ctypes
 
 import numpy as np
@@ -149,5 +149,9 @@ def test_substep_entry_points_write_in_bounds(asuca, prec):
     for layout, shp in ((asuca.LAYOUT_IJK, (7, 13, 37)), (asuca.LAYOUT_KIJ, (13, 37, 7))):
         x = G.make(shp, dt_, f if layout == asuca.LAYOUT_IJK else np.transpose(f, (1, 2, 0)))
         asuca.stencil7(x, G.make(shp, dt_), 0.1, layout)
+    Y = c.state()
+    ref, b0, b1 = (G.make(Y.shape, dt_, a) for a in gen.make_boundary_data(Y, 5))
+    for width, ntop in ((3, 2), (6, 7), (0, 1), (2, 0)):
+        asuca.damping(g, o, ref, b0, b1, 0.4, c.dt, width=width, ntop=ntop, nu_lat=1e-2, nu_top=1e-2)
     G.check()
     assert asuca.get_status(g) == asuca.OK

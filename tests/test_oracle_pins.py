@@ -560,3 +560,129 @@ def test_damping_sampled_cells_equal_the_whole_domain():
     g = lambda a: a[:, ijk[:, 2], ijk[:, 1], ijk[:, 0]]
     part = oracle.damping(g(Y), g(R), g(B0), g(B1), 0.6, 20.0, ijk=ijk, shape=(nx, ny, nz), **kw)
     assert np.array_equal(part, g(full))
+
+
+# ------------------------------------------------------------------ HEVI acoustic short steps (Sec. 1.1)
+
+CS2 = 340.0 ** 2
+
+
+def _acoustic_base(nz, dz=None, gravity=True):
+    dz = np.linspace(60.0, 500.0, nz) if dz is None else np.asarray(dz, float)
+    zf = np.concatenate([[0.0], np.cumsum(dz)])
+    zc = zf[:-1] + 0.5 * dz
+    if not gravity:
+        return dz, np.full(nz, 1.2), np.full(nz + 1, 1.2)
+    return dz, 1.2 * np.exp(-9.81 * zc / CS2), 1.2 * np.exp(-9.81 * zf / CS2)
+
+
+def _acoustic_random(nz, ny, nx, seed, uniform=False):
+    rng = np.random.default_rng(seed)
+    shape = (nz, 1, 1) if uniform else (nz, ny, nx)
+    S = np.broadcast_to(rng.standard_normal(shape) * 1e-3, (nz, ny, nx)).copy()
+    W = np.broadcast_to(rng.standard_normal((nz + 1,) + shape[1:]) * 0.5, (nz + 1, ny, nx)).copy()
+    W[0] = W[-1] = 0.0
+    if uniform:
+        return np.zeros((nz, ny, nx)), np.zeros((nz, ny, nx)), W, S
+    return rng.standard_normal((nz, ny, nx)), rng.standard_normal((nz, ny, nx)), W, S
+
+
+def _acoustic_energy(W, S, dz, r0c, r0f):
+    dzc = 0.5 * (dz[:-1] + dz[1:])
+    ew = 0.5 * np.sum(W[1:-1] ** 2 * (dzc / (CS2 * r0f[1:-1]))[:, None, None])
+    es = 0.5 * np.sum(S ** 2 * (r0c * dz)[:, None, None])
+    return ew + es
+
+
+def test_acoustic_rest_state_and_mass():
+    """The resting state stays at rest, and the flux form with periodic sides and
+    rigid lids conserves the perturbation mass sum rho0 s dz (to rounding)."""
+    nz, ny, nx = 7, 6, 9
+    dz, r0c, r0f = _acoustic_base(nz)
+    z = [np.zeros((nz, ny, nx)), np.zeros((nz, ny, nx)), np.zeros((nz + 1, ny, nx)), np.zeros((nz, ny, nx))]
+    out = oracle.acoustic(*z, dz, r0c, r0f, CS2, 0.6, 2.0, 3)
+    assert all(np.array_equal(a, b) for a, b in zip(out, z))
+    U, V, W, S = _acoustic_random(nz, ny, nx, 1)
+    mass = lambda s: np.sum(s * (r0c * dz)[:, None, None])
+    scale = np.sum(np.abs(S) * (r0c * dz)[:, None, None])
+    out = oracle.acoustic(U, V, W, S, dz, r0c, r0f, CS2, 0.6, 2.0, 5)
+    assert abs(mass(out[3]) - mass(S)) <= 1e-13 * scale
+
+
+def test_acoustic_vertical_mode_is_crank_nicolson_exact():
+    """Horizontally uniform, constant rho0 and dz, beta = 1/2: the lid-bounded
+    mode s_k = cos(theta (k + 1/2)), theta = pi m / nz, is an eigenvector of the
+    vertical operator with frequency omega = 2 c sin(theta / 2) / dz, and the
+    trapezoidal (Crank-Nicolson) step turns it by exactly 2 atan(omega h / 2)."""
+    nz, ny, nx, m, h, n = 12, 3, 4, 3, 5.0, 9
+    dz, r0c, r0f = _acoustic_base(nz, dz=np.full(nz, 250.0), gravity=False)
+    th = math.pi * m / nz
+    mode = np.cos(th * (np.arange(nz) + 0.5))
+    S = np.broadcast_to(mode[:, None, None], (nz, ny, nx)).copy() * 1e-3
+    zeros = np.zeros((nz, ny, nx))
+    out = oracle.acoustic(zeros, zeros, np.zeros((nz + 1, ny, nx)), S, dz, r0c, r0f, CS2, 0.5, h, n)
+    omega = 2.0 * math.sqrt(CS2) * math.sin(th / 2) / 250.0
+    phi = 2.0 * math.atan(omega * h / 2)
+    assert np.max(np.abs(out[3] - math.cos(n * phi) * S)) <= 1e-15
+    # W carries the quadrature part: b_n = sin(n phi) c rho0 a_0 in energy-normalised units
+    wmode = np.sin(th * np.arange(nz + 1))
+    want_w = math.sin(n * phi) * math.sqrt(CS2) * 1.2 * 1e-3 * wmode
+    assert np.max(np.abs(out[2][:, 0, 0] - want_w)) <= 1e-12
+    assert np.array_equal(out[0], zeros) and np.array_equal(out[1], zeros)
+
+
+@pytest.mark.parametrize("beta", [0.5, 0.7])
+def test_acoustic_vertical_energy(beta):
+    """Horizontally uniform states (gravity base state, stretched levels): the
+    discrete acoustic energy sum W^2 dzc / (2 c^2 rho0f) + rho0 dz s^2 / 2 is
+    conserved by the centred implicit step and decays for beta > 1/2."""
+    nz, ny, nx = 20, 2, 3
+    dz, r0c, r0f = _acoustic_base(nz)
+    U, V, W, S = _acoustic_random(nz, ny, nx, 2, uniform=True)
+    e = [_acoustic_energy(W, S, dz, r0c, r0f)]
+    for _ in range(30):
+        U, V, W, S = oracle.acoustic(U, V, W, S, dz, r0c, r0f, CS2, beta, 4.0, 1)
+        e.append(_acoustic_energy(W, S, dz, r0c, r0f))
+    e = np.array(e)
+    if beta == 0.5:
+        assert np.max(np.abs(e / e[0] - 1.0)) <= 1e-12
+    else:
+        assert np.all(np.diff(e) < 0) and e[-1] < 0.9 * e[0]
+
+
+def test_acoustic_horizontal_mode_converges_at_second_order():
+    """A horizontal acoustic mode s = cos(2 pi m i / nx) (constant rho0) has the
+    centred-difference frequency omega = 2 c sin(pi m / nx) / dx; the two-stage
+    short step converges to cos(omega t) s at second order in the step."""
+    nz, ny, nx, m, T, dx = 3, 2, 16, 2, 10.0, 2000.0     # omega T = 1.3, away from an extremum of cos
+    dz, r0c, r0f = _acoustic_base(nz, gravity=False)
+    mode = np.cos(2 * math.pi * m * np.arange(nx) / nx)
+    S0 = np.broadcast_to(mode[None, None, :], (nz, ny, nx)).copy() * 1e-3
+    omega = 2.0 * math.sqrt(CS2) * math.sin(math.pi * m / nx) / dx
+    errs = []
+    for n in (8, 16, 32, 64):
+        z = np.zeros((nz, ny, nx))
+        out = oracle.acoustic(z, z, np.zeros((nz + 1, ny, nx)), S0, dz, r0c, r0f, CS2, 0.6, T / n, n)
+        errs.append(np.max(np.abs(out[3] - math.cos(omega * T) * S0)))
+        assert np.max(np.abs(out[2])) <= 1e-15      # no vertical motion from a k-uniform mode
+    for a, b in zip(errs, errs[1:]):
+        assert 3.9 < a / b < 4.1
+
+
+def test_acoustic_i_j_transposition_symmetry():
+    """With dx = dy, transposing i and j (and swapping U and V) transposes the
+    result bit for bit; the lids of W are left as they are."""
+    nz, n = 5, 8
+    dz, r0c, r0f = _acoustic_base(nz)
+    U, V, W, S = _acoustic_random(nz, n, n, 3)
+    W[0], W[-1] = 5.0, -3.0
+    t = lambda a: np.ascontiguousarray(np.swapaxes(a, 1, 2))
+    a = oracle.acoustic(U, V, W, S, dz, r0c, r0f, CS2, 0.6, 2.0, 2)
+    b = oracle.acoustic(t(V), t(U), t(W), t(S), dz, r0c, r0f, CS2, 0.6, 2.0, 2)
+    assert np.array_equal(t(b[1]), a[0]) and np.array_equal(t(b[0]), a[1])
+    assert np.array_equal(t(b[2]), a[2]) and np.array_equal(t(b[3]), a[3])
+    assert np.all(a[2][0] == 5.0) and np.all(a[2][-1] == -3.0)
+    W0 = W.copy()
+    W0[0] = W0[-1] = 0.0
+    c = oracle.acoustic(U, V, W0, S, dz, r0c, r0f, CS2, 0.6, 2.0, 2)
+    assert np.array_equal(c[3], a[3]) and np.array_equal(c[2][1:-1], a[2][1:-1])
