@@ -25,6 +25,8 @@ import subprocess
 import sys
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -451,6 +453,51 @@ def damping_report(asuca, dev, reps=10, nx=None, precs=("fp32", "fp64")):
     return out
 
 
+def acoustic_report(asuca, dev, reps=5, nx=None, precs=("fp32", "fp64")):
+    """HEVI acoustic short steps (asuca_acoustic_steps) on the 1024x1024x58 grid,
+    6 short steps of 2 s per call, FP32 and FP64.  A short step is two launches,
+    one thread per column each; the algorithmic bytes count every array once per
+    launch: stage 1 reads S, U, V, W and writes U*, V*, s* (7 values per cell),
+    stage 2 reads S, W, U, V, s*, U*, V* and writes U, V, W, S (11): 18 values
+    per cell and short step, against the measured HBM peak.  The 4 fields
+    (1 GB in FP32) exceed L2."""
+    import torch
+    import gen
+    case = gen.make_config_case(WORKLOAD, nx=nx, ny=nx, ntracers=1)
+    A = gen.ACOUSTIC
+    peak, _ = _peaks()
+    C = case.cells
+    arrays = gen.make_acoustic_state(case)
+    out = {"workload": f"acoustic_{case.nx}x{case.ny}x{case.nz}", "nshort_per_call": A["nshort"],
+           "dtau_s": A["dtau"], "beta": A["beta"], "algorithmic_bytes": "18 values per cell and short step"}
+    for name, prec, dt in (("fp32", asuca.FP32_MIXED, torch.float32), ("fp64", asuca.FP64, torch.float64)):
+        if name not in precs:
+            continue
+        g = asuca.Grid.from_case(case, prec=prec)
+        U, V, W, S = (torch.from_numpy(np.ascontiguousarray(a)).to(device=dev, dtype=dt) for a in arrays[:4])
+        ws = torch.empty(asuca.acoustic_workspace_bytes(g), dtype=torch.uint8, device=dev)
+        call = lambda: asuca.acoustic_steps(g, U, V, W, S, arrays[4], arrays[5], A["cs2"], A["beta"], A["dtau"],
+                                            A["nshort"], workspace=ws)
+        for _ in range(3):
+            call()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            call()
+        e1.record()
+        torch.cuda.synchronize()
+        assert asuca.get_status(g) == asuca.OK
+        ms = e0.elapsed_time(e1) / (reps * A["nshort"])
+        algo = 18 * dt.itemsize * C
+        out[name] = {"ms_per_short_step": ms, "launches": 2 * reps * A["nshort"],
+                     "cell_updates_per_s": C / (ms * 1e-3), "achieved_gbs": algo / (ms * 1e-3) / 1e9,
+                     "frac": algo / (ms * 1e-3) / 1e9 / peak, "peak_gbs": peak}
+        del U, V, W, S, ws
+    torch.cuda.empty_cache()
+    return out
+
+
 def ensemble_throughput(asuca, dev, nsteps=10, reps=3):
     """32 members with nx = ny drawn from U{64..320}, 58 levels, 4 tracers, FP32:
     cell-updates/s of one persistent launch per call (graph-replayed) against the
@@ -736,6 +783,9 @@ def run_ours(args):
     damping = None
     if not args.no_damping:
         damping = damping_report(asuca, dev)
+    acoustic = None
+    if not args.no_acoustic:
+        acoustic = acoustic_report(asuca, dev)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -752,7 +802,7 @@ def run_ours(args):
                           "parallelism": f"{world} independent replica(s), one per GPU"},
                "clocks": clocks, "gpu_launches": sum(n for _t, n in (prof or {}).values()), "roofline": roofline,
                "e2e": e2e, "fp64": fp64, "precision": precision, "adjoint": adjoint, "ensemble": ensemble,
-               "layout_ablation": layout, "damping": damping,
+               "layout_ablation": layout, "damping": damping, "acoustic": acoustic,
                "fp32_over_fp64_speedup": (value / fp64["value"]) if fp64 else None,
                "cpu_baseline": cpu}
         print(json.dumps(out), flush=True)
@@ -781,6 +831,10 @@ def main():
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-layout", action="store_true")
     ap.add_argument("--no-damping", action="store_true")
+    ap.add_argument("--no-acoustic", action="store_true")
+    ap.add_argument("--acoustic-probe", choices=["fp32", "fp64"], default=None,
+                    help="time the acoustic short steps alone on the nx x nx x 58 grid in one precision and "
+                         "exit (a small launch sequence for profiler captures)")
     ap.add_argument("--ens-steps", type=int, default=10)
     ap.add_argument("--nx", type=int, default=1024,
                     help="nx = ny of the timed case; anything but 1024 is a smaller case of the same "
@@ -796,6 +850,15 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.adjoint_probe:
         return adjoint_probe(args.adjoint_probe)
+    if args.acoustic_probe:
+        import torch
+        from paper_1710_08616_gb300 import build as _b
+        _b.build()
+        import paper_1710_08616_gb300 as asuca
+        torch.cuda.set_device(0)
+        print(json.dumps(acoustic_report(asuca, torch.device("cuda", 0), reps=1, nx=args.nx,
+                                         precs=(args.acoustic_probe,))), flush=True)
+        return 0
     if args.damping_probe:
         import torch
         from paper_1710_08616_gb300 import build as _b

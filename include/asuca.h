@@ -347,6 +347,46 @@ asuca_status asuca_damping(asuca_grid *grid, asuca_state *state, const void *ref
                            const void *bnd1, double mtratio, double tratio, double dt,
                            const asuca_damping_desc *desc, void *cuda_stream);
 
+/* ---- HEVI acoustic short steps ------------------------------------------
+ * Sound and gravity waves advanced in short steps by a two-stage Runge-Kutta
+ * scheme, horizontally explicit and vertically implicit (Sec. 1.1, "ASUCA on
+ * GPU"), for the linear acoustic-gravity system about a resting, horizontally
+ * uniform base state rho0(z):
+ *   dU/dt = -c^2 rho0_k (s_{i+1} - s_i)/dx,  dV/dt = -c^2 rho0_k (s_{j+1} - s_j)/dy,
+ *   dW_f/dt = -c^2 rho0f_f (s_f - s_{f-1})/dzc_f,  dzc_f = (dz_{f-1} + dz_f)/2,
+ *   rho0_k ds/dt = -[(U_{i+1/2} - U_{i-1/2})/dx + (V_{j+1/2} - V_{j-1/2})/dy + (W_{k+1} - W_k)/dz_k],
+ * s = rho'/rho0 (for rho0 = rho_s exp(-g z / c^2) the W equation is
+ * dW/dt = -dp'/dz - g rho').  A short step of length dtau: stage 1 over
+ * dtau/2, U* = U - (dtau/2) G(s), then W*, s* from the implicit vertical
+ * system with the horizontal divergence of U*, V*; stage 2 over dtau from the
+ * same start, U+ = U - dtau G(s*), then W+, s+ implicit with the divergence
+ * of U*, V*.  The implicit system weights the new and old vertical terms by
+ * beta and 1 - beta (beta = 1/2: Crank-Nicolson; larger: damped).  The paper
+ * names the scheme only; these equations are this library's reading.
+ *   - U, V, S: [nz][ny][nx] (U at the faces i+1/2, V at j+1/2, S at the
+ *     centres); W: [nz+1][ny][nx] (W[k] the face below cell k; W[0] and W[nz]
+ *     are rigid lids, never read or written).  Device arrays of the grid's
+ *     precision, updated in place; the grid's dx, dy, dz.
+ *   - desc: rho0c (nz values) and rho0f (nz + 1, entries 1..nz-1 used), host
+ *     arrays, > 0; cs2 > 0 the squared sound speed; 1/2 <= beta <= 1.
+ *   - The FP64 path computes in double; the FP32 path in float, with the
+ *     column systems' factorisation computed in double on the host.
+ *   - workspace: asuca_acoustic_workspace_bytes(grid) bytes, 256-byte
+ *     aligned, else ASUCA_ERR_WORKSPACE.  dtau >= 0, nshort >= 0, else (or a
+ *     null pointer) ASUCA_ERR_ARG.  Two launches per short step, asynchronous
+ *     on the stream. */
+typedef struct {
+    const double *rho0c;   /* nz base densities at the level centres */
+    const double *rho0f;   /* nz + 1 base densities at the faces */
+    double cs2;            /* squared sound speed (m^2/s^2) */
+    double beta;           /* implicit weight */
+} asuca_acoustic_desc;
+
+size_t asuca_acoustic_workspace_bytes(const asuca_grid *grid);
+asuca_status asuca_acoustic_steps(asuca_grid *grid, void *U, void *V, void *W, void *S,
+                                  const asuca_acoustic_desc *desc, double dtau, int nshort, void *workspace,
+                                  size_t workspace_bytes, void *cuda_stream);
+
 /* ---- per-kernel timing ------------------------------------------------- */
 
 typedef enum {

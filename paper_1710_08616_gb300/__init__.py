@@ -58,6 +58,11 @@ class DampingDesc(ctypes.Structure):
                 ("nu_top", ctypes.c_double)]
 
 
+class AcousticDesc(ctypes.Structure):
+    _fields_ = [("rho0c", ctypes.POINTER(ctypes.c_double)), ("rho0f", ctypes.POINTER(ctypes.c_double)),
+                ("cs2", ctypes.c_double), ("beta", ctypes.c_double)]
+
+
 _lib = None
 _VP = ctypes.c_void_p
 
@@ -80,6 +85,9 @@ SIGNATURES = {
                                       ctypes.c_double, _VP]),
     "asuca_damping": (ctypes.c_int, [_VP, ctypes.POINTER(StateStruct), _VP, _VP, _VP, ctypes.c_double,
                                      ctypes.c_double, ctypes.c_double, ctypes.POINTER(DampingDesc), _VP]),
+    "asuca_acoustic_workspace_bytes": (ctypes.c_size_t, [_VP]),
+    "asuca_acoustic_steps": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, ctypes.POINTER(AcousticDesc), ctypes.c_double,
+                                            ctypes.c_int, _VP, ctypes.c_size_t, _VP]),
     "asuca_adjoint_workspace_bytes": (ctypes.c_size_t, [_VP, ctypes.c_int, ctypes.c_int]),
     "asuca_adjoint_step": (ctypes.c_int, [_VP, ctypes.POINTER(StateStruct), _VP, ctypes.c_double, ctypes.c_int,
                                           ctypes.c_int, _VP, _VP, _VP, _VP, _VP, _VP, ctypes.c_size_t, _VP]),
@@ -348,6 +356,34 @@ def damping(grid: Grid, state: State, ref, bnd0, bnd1, tratio: float, dt: float,
     s = state.struct()
     _check(lib().asuca_damping(grid.handle, ctypes.byref(s), _ptr(ref), _ptr(bnd0), _ptr(bnd1), float(mtratio),
                                float(tratio), float(dt), ctypes.byref(d), _stream_ptr(stream)), "asuca_damping")
+
+
+def acoustic_workspace_bytes(grid: Grid) -> int:
+    return int(lib().asuca_acoustic_workspace_bytes(grid.handle))
+
+
+def acoustic_steps(grid: Grid, U, V, W, S, rho0c, rho0f, cs2: float, beta: float, dtau: float, nshort: int, *,
+                   workspace=None, stream=None):
+    """nshort HEVI acoustic short steps (asuca_acoustic_steps), in place.  U, V, S:
+    contiguous CUDA [nz][ny][nx] tensors of the grid's dtype; W: [nz+1][ny][nx]
+    (W[0], W[nz] rigid lids, untouched); rho0c (nz) and rho0f (nz+1): host arrays."""
+    import torch
+    nz, ny, nx = grid.nz, grid.ny, grid.nx
+    for name, t, shape in (("U", U, (nz, ny, nx)), ("V", V, (nz, ny, nx)), ("W", W, (nz + 1, ny, nx)),
+                           ("S", S, (nz, ny, nx))):
+        if tuple(t.shape) != shape or t.dtype != grid.torch_dtype or not t.is_contiguous() or not t.is_cuda:
+            raise ValueError(f"{name}: need contiguous CUDA {grid.torch_dtype} of shape {shape}")
+    r0c = np.ascontiguousarray(rho0c, dtype=np.float64)
+    r0f = np.ascontiguousarray(rho0f, dtype=np.float64)
+    if r0c.shape != (nz,) or r0f.shape != (nz + 1,):
+        raise ValueError("rho0c: nz values, rho0f: nz + 1 values")
+    if workspace is None:
+        workspace = torch.empty(max(acoustic_workspace_bytes(grid), 256), dtype=torch.uint8, device=S.device)
+    dp = ctypes.POINTER(ctypes.c_double)
+    d = AcousticDesc(r0c.ctypes.data_as(dp), r0f.ctypes.data_as(dp), float(cs2), float(beta))
+    _check(lib().asuca_acoustic_steps(grid.handle, _ptr(U), _ptr(V), _ptr(W), _ptr(S), ctypes.byref(d), float(dtau),
+                                      int(nshort), _ptr(workspace), workspace.numel(), _stream_ptr(stream)),
+           "asuca_acoustic_steps")
 
 
 def profile_enable(grid: Grid, on: bool = True):

@@ -14,6 +14,7 @@
 #include "ensemble_params.cuh"
 #include "dataflow_params.cuh"
 #include "damping.cuh"
+#include "acoustic.cuh"
 #include "common.cuh"
 
 using namespace asuca;
@@ -1586,6 +1587,113 @@ asuca_status asuca_damping(asuca_grid *g, asuca_state *st, const void *ref, cons
         e = launch_damping<float>(y, g->F, (const float *)ref, (const float *)bnd0, (const float *)bnd1, nx, ny,
                                   nz, dd.width, dd.ntop, dd.nu_lat, dd.nu_top, mtratio, tratio, dt, g->nsm, s);
     }
+    return cuda_status(e);
+}
+
+size_t asuca_acoustic_workspace_bytes(const asuca_grid *g) {
+    if (!g) return 0;
+    const size_t s = g->d.prec == ASUCA_FP64 ? sizeof(double) : sizeof(float);
+    const size_t plane = (size_t)g->plane;
+    auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+    return 3 * al(plane * g->d.nz * s) + al(plane * (g->d.nz + 1) * s);
+}
+
+}  // extern "C"
+
+namespace {
+// the per-level coefficients and the factorisation of one stage (length tau)
+template <typename T>
+void acoustic_tables(const asuca_grid *g, const asuca_acoustic_desc &a, double tau, AcousticParams<T> &p) {
+    const int nz = g->d.nz;
+    double Bd[MAXNZ];
+    for (int k = 0; k < nz; k++) {
+        const double r0 = a.rho0c[k], dz = g->dz[k];
+        p.gx[k] = (T)(tau * a.cs2 * r0 / g->d.dx);
+        p.gy[k] = (T)(tau * a.cs2 * r0 / g->d.dy);
+        p.cr[k] = (T)(tau / r0);
+        p.cw[k] = (T)((1.0 - a.beta) / dz);
+        Bd[k] = tau * a.beta / (r0 * dz);
+        p.B[k] = (T)Bd[k];
+    }
+    double cprev = 0.0;
+    for (int f = 0; f <= nz; f++) {
+        p.cq[f] = p.A[f] = p.lo[f] = p.inv[f] = p.cp[f] = T(0);
+        if (f < 1 || f > nz - 1) continue;
+        const double dzc = 0.5 * (g->dz[f - 1] + g->dz[f]);
+        const double G = tau * a.cs2 * a.rho0f[f] / dzc;
+        const double A = G * a.beta;
+        const double lower = f >= 2 ? -A * Bd[f - 1] : 0.0;
+        const double diag = 1.0 + A * (Bd[f] + Bd[f - 1]);
+        const double upper = f <= nz - 2 ? -A * Bd[f] : 0.0;
+        const double inv = 1.0 / (diag - lower * cprev);
+        cprev = upper * inv;
+        p.cq[f] = (T)(G * (1.0 - a.beta));
+        p.A[f] = (T)A;
+        p.lo[f] = (T)lower;
+        p.inv[f] = (T)inv;
+        p.cp[f] = (T)cprev;
+    }
+}
+
+template <typename T>
+cudaError_t run_acoustic(const asuca_grid *g, void *U, void *V, void *W, void *S, const asuca_acoustic_desc &a,
+                         double h, int nshort, char *ws, cudaStream_t s) {
+    const size_t plane = (size_t)g->plane;
+    auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+    const size_t fb = al(plane * g->d.nz * sizeof(T));
+    AcousticParams<T> p[2];
+    for (int q = 0; q < 2; q++) {
+        std::memset(&p[q], 0, sizeof(p[q]));
+        p[q].U = (T *)U;
+        p[q].V = (T *)V;
+        p[q].W = (T *)W;
+        p[q].S = (T *)S;
+        p[q].Us = (T *)ws;
+        p[q].Vs = (T *)(ws + fb);
+        p[q].Ss = (T *)(ws + 2 * fb);
+        p[q].Ws = (T *)(ws + 3 * fb);
+        p[q].nx = g->d.nx;
+        p[q].ny = g->d.ny;
+        p[q].nz = g->d.nz;
+        p[q].plane = (unsigned)plane;
+        p[q].rdx = (T)(1.0 / g->d.dx);
+        p[q].rdy = (T)(1.0 / g->d.dy);
+        acoustic_tables<T>(g, a, q == 0 ? 0.5 * h : h, p[q]);
+    }
+    for (int n = 0; n < nshort; n++)
+        for (int q = 0; q < 2; q++) {
+            const cudaError_t e = launch_acoustic_stage<T>(p[q], q + 1, s);
+            if (e != cudaSuccess) return e;
+        }
+    return cudaSuccess;
+}
+}  // namespace
+
+extern "C" {
+
+asuca_status asuca_acoustic_steps(asuca_grid *g, void *U, void *V, void *W, void *S, const asuca_acoustic_desc *desc,
+                                  double dtau, int nshort, void *workspace, size_t workspace_bytes,
+                                  void *cuda_stream) {
+    if (!g || !U || !V || !W || !S || !desc || !desc->rho0c || !desc->rho0f || !std::isfinite(dtau) || dtau < 0.0 ||
+        nshort < 0 || !std::isfinite(desc->cs2) || desc->cs2 <= 0.0 || !(desc->beta >= 0.5 && desc->beta <= 1.0))
+        return ASUCA_ERR_ARG;
+    const int nz = g->d.nz;
+    for (int k = 0; k < nz; k++)
+        if (!(desc->rho0c[k] > 0.0) || !std::isfinite(desc->rho0c[k])) return ASUCA_ERR_ARG;
+    for (int f = 1; f < nz; f++)
+        if (!(desc->rho0f[f] > 0.0) || !std::isfinite(desc->rho0f[f])) return ASUCA_ERR_ARG;
+    if (!workspace || workspace_bytes < asuca_acoustic_workspace_bytes(g) || ((uintptr_t)workspace & 255))
+        return ASUCA_ERR_WORKSPACE;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return ASUCA_ERR_CUDA;
+    if (dev != g->device) return ASUCA_ERR_ARG;
+    asuca_status prev = take_status(g);
+    if (prev != ASUCA_OK) return prev;
+    if (nshort == 0) return ASUCA_OK;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const cudaError_t e = g->d.prec == ASUCA_FP64
+                              ? run_acoustic<double>(g, U, V, W, S, *desc, dtau, nshort, (char *)workspace, s)
+                              : run_acoustic<float>(g, U, V, W, S, *desc, dtau, nshort, (char *)workspace, s);
     return cuda_status(e);
 }
 

@@ -3,7 +3,7 @@ a larger allocation whose guard bands (4 KiB on each side) hold a fixed bit
 pattern, and after the call the bands must be unchanged.  This covers every
 kernel of the step (fused and separate column pass, dataflow mode), the
 adjoint, the checkpointed forward, the ensemble, the sub-step entry points,
-the storage-order stencil and the damping, on ragged and limit sizes."""
+the storage-order stencil, the damping and the acoustic short steps, on ragged and limit sizes."""
 import ctypes
 
 import numpy as np
@@ -153,5 +153,9 @@ def test_substep_entry_points_write_in_bounds(asuca, prec):
     ref, b0, b1 = (G.make(Y.shape, dt_, a) for a in gen.make_boundary_data(Y, 5))
     for width, ntop in ((3, 2), (6, 7), (0, 1), (2, 0)):
         asuca.damping(g, o, ref, b0, b1, 0.4, c.dt, width=width, ntop=ntop, nu_lat=1e-2, nu_top=1e-2)
+    U, V, W, S, r0c, r0f = gen.make_acoustic_state(c)
+    ac = [G.make(a.shape, dt_, a) for a in (U, V, W, S)]
+    wsa = G.make((asuca.acoustic_workspace_bytes(g),), torch.uint8)
+    asuca.acoustic_steps(g, *ac, r0c, r0f, gen.ACOUSTIC["cs2"], 0.6, 2.0, 3, workspace=wsa)
     G.check()
     assert asuca.get_status(g) == asuca.OK
