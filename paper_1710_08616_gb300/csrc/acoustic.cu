@@ -21,6 +21,9 @@
 // Mapping: one thread per (i, j) column (32 x 8 blocks), marching up (the
 // horizontal terms, the explicit parts and the forward elimination, whose
 // values wait in the output arrays) and back down (back substitution and s').
+// In stage 1 the up pass's inputs arrive through a per-thread cp.async ring
+// in shared memory, requested two levels ahead; stage 2 prefetches one level
+// into registers.
 // The thread recomputes the neighbouring face's stage-1 momentum it needs for
 // the divergence (the same operations as the neighbour's own), so a stage is
 // one launch with no grid-wide dependency.  Stage 2 updates the caller's
@@ -30,9 +33,22 @@
 // in double on the host and rounded).
 #include "acoustic.cuh"
 
+#ifndef ACOUSTIC_RING
+#define ACOUSTIC_RING 3   // levels in the shared-memory ring (2 requested ahead)
+#endif
+
 namespace asuca {
 
-template <typename T, int STAGE>
+template <int N>
+__device__ __forceinline__ void ac_cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+__device__ __forceinline__ void ac_cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <typename T>
+__device__ __forceinline__ void ac_cp_async(T *dst, const T *src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d), "l"(src), "n"(sizeof(T)) : "memory");
+}
+
+template <typename T, int STAGE, int D>
 __global__ void __launch_bounds__(256) acoustic_kernel(const __grid_constant__ AcousticParams<T> p) {
     const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y;
     if (i >= p.nx || j >= p.ny) return;
@@ -47,31 +63,121 @@ __global__ void __launch_bounds__(256) acoustic_kernel(const __grid_constant__ A
     T *Wo = STAGE == 1 ? p.Ws : p.W;
     T *So = STAGE == 1 ? p.Ss : p.S;
 
-    // ---- up: horizontal momenta, explicit parts, forward elimination
+    // ---- up: horizontal momenta, explicit parts, forward elimination.  The
+    // inputs of each level stream through a ring of D shared-memory slots
+    // filled by per-thread cp.async copies, requested D - 1 levels ahead
+    // (every thread copies and reads only its own slots, so no barrier is
+    // needed; no store of this thread or of another one touches what a
+    // request loads).  The ring keeps several levels' loads in flight without
+    // holding them in registers.
+    extern __shared__ __align__(16) unsigned char ac_smem[];
+    T *ring = reinterpret_cast<T *>(ac_smem);
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    constexpr int NV = 11;   // values per level: s, W_{k+2}, s at e, n, own (stage 2), w, s; U, U_w, V, V_s
+    constexpr int DR = D > 0 ? D : 1;
+    auto sl = [&](int k, int v) -> T * { return ring + ((k % DR) * NV + v) * 256 + tid; };
+    auto request = [&](int k) {
+        if (k < nz) {
+            const unsigned b = (unsigned)k * plane;
+            ac_cp_async(sl(k, 0), p.S + b + own);
+            if (k + 2 < nz) ac_cp_async(sl(k, 1), p.W + b + 2 * plane + own);
+            else *sl(k, 1) = T(0);             // W_{k+2} at or above the lid
+            ac_cp_async(sl(k, 2), se + b + oe);
+            ac_cp_async(sl(k, 3), se + b + on);
+            ac_cp_async(sl(k, 7), p.U + b + own);
+            ac_cp_async(sl(k, 9), p.V + b + own);
+            if (STAGE == 1) {
+                ac_cp_async(sl(k, 5), se + b + ow);
+                ac_cp_async(sl(k, 6), se + b + os);
+                ac_cp_async(sl(k, 8), p.U + b + ow);
+                ac_cp_async(sl(k, 10), p.V + b + os);
+            } else {
+                ac_cp_async(sl(k, 4), se + b + own);
+                ac_cp_async(sl(k, 5), p.Us + b + own);   // stage 2: the stage-1 momenta on both faces
+                ac_cp_async(sl(k, 8), p.Us + b + ow);
+                ac_cp_async(sl(k, 6), p.Vs + b + own);
+                ac_cp_async(sl(k, 10), p.Vs + b + os);
+            }
+        }
+        ac_cp_commit();
+    };
+    struct Level { T sk, w2, c, e, w, n, s, u, uw, v, vs; };
+    // without a ring (D = 0): the next level's values are loaded into registers
+    auto load = [&](int k) {
+        Level L;
+        const unsigned b = (unsigned)k * plane;
+        L.sk = p.S[b + own];
+        L.w2 = (k + 2 < nz) ? p.W[b + 2 * plane + own] : T(0);
+        L.e = se[b + oe];
+        L.n = se[b + on];
+        L.u = p.U[b + own];
+        L.v = p.V[b + own];
+        if (STAGE == 1) {
+            L.c = L.sk;
+            L.w = se[b + ow];
+            L.s = se[b + os];
+            L.uw = p.U[b + ow];
+            L.vs = p.V[b + os];
+        } else {
+            L.c = se[b + own];
+            L.w = p.Us[b + own];
+            L.uw = p.Us[b + ow];
+            L.s = p.Vs[b + own];
+            L.vs = p.Vs[b + os];
+        }
+        return L;
+    };
+    auto read = [&](int k) {
+        Level L;
+        L.sk = *sl(k, 0);
+        L.w2 = *sl(k, 1);
+        L.e = *sl(k, 2);
+        L.n = *sl(k, 3);
+        L.c = STAGE == 1 ? L.sk : *sl(k, 4);
+        L.w = *sl(k, 5);
+        L.s = *sl(k, 6);
+        L.u = *sl(k, 7);
+        L.uw = *sl(k, 8);
+        L.v = *sl(k, 9);
+        L.vs = *sl(k, 10);
+        return L;
+    };
+    Level ahead;
+    if constexpr (D > 0) {
+#pragma unroll 1
+        for (int k = 0; k < D - 1; k++) request(k);
+    } else {
+        ahead = load(0);
+    }
     T Wk = T(0);                               // W_k of the start state (W_0: the lid)
     T s_prev = T(0), r_prev = T(0), d_prev = T(0);
     T Wk1 = nz > 1 ? p.W[plane + own] : T(0);
 #pragma unroll 1
     for (int k = 0; k < nz; k++) {
         const unsigned b = (unsigned)k * plane;
-        const T sk = p.S[b + own];
-        // W_{k+2} one level ahead (the lid at nz reads as zero)
-        const T Wk2 = (k + 2 < nz) ? p.W[b + 2 * plane + own] : T(0);
+        Level cur;
+        if constexpr (D > 0) {
+            request(k + D - 1);                // into the slot level k-1 used
+            ac_cp_wait<D - 1>();               // level k has landed
+            cur = read(k);
+        } else {
+            cur = ahead;
+            if (k + 1 < nz) ahead = load(k + 1);
+        }
+        const T sk = cur.sk;
         T Dh;
         if (STAGE == 1) {
-            const T sE = se[b + oe], sW = se[b + ow], sN = se[b + on], sS = se[b + os];
-            const T ue = p.U[b + own] - p.gx[k] * (sE - sk);
-            const T uw = p.U[b + ow] - p.gx[k] * (sk - sW);
-            const T vn = p.V[b + own] - p.gy[k] * (sN - sk);
-            const T vs = p.V[b + os] - p.gy[k] * (sk - sS);
+            const T ue = cur.u - p.gx[k] * (cur.e - sk);
+            const T uw = cur.uw - p.gx[k] * (sk - cur.w);
+            const T vn = cur.v - p.gy[k] * (cur.n - sk);
+            const T vs = cur.vs - p.gy[k] * (sk - cur.s);
             p.Us[b + own] = ue;
             p.Vs[b + own] = vn;
             Dh = (ue - uw) * p.rdx + (vn - vs) * p.rdy;
         } else {
-            const T sc = se[b + own], sE = se[b + oe], sN = se[b + on];
-            p.U[b + own] = p.U[b + own] - p.gx[k] * (sE - sc);
-            p.V[b + own] = p.V[b + own] - p.gy[k] * (sN - sc);
-            Dh = (p.Us[b + own] - p.Us[b + ow]) * p.rdx + (p.Vs[b + own] - p.Vs[b + os]) * p.rdy;
+            p.U[b + own] = cur.u - p.gx[k] * (cur.e - cur.c);
+            p.V[b + own] = cur.v - p.gy[k] * (cur.n - cur.c);
+            Dh = (cur.w - cur.uw) * p.rdx + (cur.s - cur.vs) * p.rdy;
         }
         const T r = sk - p.cr[k] * (Dh + p.cw[k] * (Wk1 - Wk));
         if (k >= 1) {
@@ -85,29 +191,51 @@ __global__ void __launch_bounds__(256) acoustic_kernel(const __grid_constant__ A
         r_prev = r;
         s_prev = sk;
         Wk = Wk1;
-        Wk1 = Wk2;
+        Wk1 = cur.w2;
     }
-    // ---- down: back substitution and s'
+    // ---- down: back substitution and s' (the values of level k-1 loaded
+    // while level k is finished)
     T Wup = T(0);                              // W'_{k+1} (the lid at nz)
+    T dk = nz > 1 ? Wo[(unsigned)(nz - 1) * plane + own] : T(0);
+    T rk = So[(unsigned)(nz - 1) * plane + own];
 #pragma unroll 1
     for (int k = nz - 1; k >= 0; k--) {
         const unsigned b = (unsigned)k * plane;
+        T dn = T(0), rn = T(0);
+        if (k >= 1) {
+            rn = So[b - plane + own];
+            if (k >= 2) dn = Wo[b - plane + own];
+        }
         T Wn = T(0);
         if (k >= 1) {
-            const T d = Wo[b + own];
-            Wn = (k == nz - 1) ? d : d - p.cp[k] * Wup;
+            Wn = (k == nz - 1) ? dk : dk - p.cp[k] * Wup;
             if (STAGE == 2) Wo[b + own] = Wn;  // stage 2 only: nothing reads W*
         }
-        So[b + own] = So[b + own] - p.B[k] * (Wup - Wn);
+        So[b + own] = rk - p.B[k] * (Wup - Wn);
         Wup = Wn;
+        dk = dn;
+        rk = rn;
     }
 }
 
 template <typename T>
 cudaError_t launch_acoustic_stage(const AcousticParams<T> &p, int stage, cudaStream_t s) {
+    // stage 1 streams its inputs through the shared-memory ring; stage 2, whose
+    // neighbour reads hit the stage-1 values in L1, keeps L1 whole and
+    // prefetches one level into registers (measured faster each way)
+    constexpr int D = ACOUSTIC_RING;
+    constexpr size_t smem = (size_t)D * 11 * 256 * sizeof(T);
     dim3 block(32, 8), grid((p.nx + 31) / 32, (p.ny + 7) / 8);
-    if (stage == 1) acoustic_kernel<T, 1><<<grid, block, 0, s>>>(p);
-    else acoustic_kernel<T, 2><<<grid, block, 0, s>>>(p);
+    if (stage == 1) {
+        if (smem > 48 * 1024) {   // set on every call: the attribute belongs to the current device
+            const cudaError_t e = cudaFuncSetAttribute(acoustic_kernel<T, 1, D>,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        acoustic_kernel<T, 1, D><<<grid, block, smem, s>>>(p);
+    } else {
+        acoustic_kernel<T, 2, 0><<<grid, block, 0, s>>>(p);
+    }
     return cudaGetLastError();
 }
 
