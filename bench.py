@@ -664,8 +664,10 @@ def run_ours(args):
         # End to end: every step copies its inputs (state and mass fluxes) from pinned
         # host memory, advances them through the C ABI and copies the state and the
         # budgets back.  Copies in, the step and copies out run on separate streams
-        # with two device buffer sets, so step n's copies overlap the neighbouring
-        # steps' work; the timed region spans the first copy in to the last copy out.
+        # with NB device buffer sets, so step n's copies overlap the neighbouring
+        # steps' work (with two sets the copy in of step n waits for the copy out
+        # of step n - 2, which chains copy in, step and copy out); the timed
+        # region spans the first copy in to the last copy out.
         names = ("rho", "rhotheta", "rhoq", "mu", "mv", "mw")
         host = {k: getattr(st, k).cpu().pin_memory() for k in names}
         hout = {k: torch.empty_like(host[k]).pin_memory() for k in ("rho", "rhotheta", "rhoq")}
@@ -673,17 +675,18 @@ def run_ours(args):
         h2d = sum(t.numel() * t.element_size() for t in host.values())
         d2h = sum(t.numel() * t.element_size() for t in hout.values()) + hbud.numel() * 8
         ne = max(1, min(args.steps, args.e2e_steps))
-        bufs = [st, asuca.State(*[torch.empty_like(getattr(st, k)) for k in names])]
-        buds = [bud, torch.empty_like(bud)]
+        NB = max(2, args.e2e_buffers)
+        bufs = [st] + [asuca.State(*[torch.empty_like(getattr(st, k)) for k in names]) for _ in range(NB - 1)]
+        buds = [bud] + [torch.empty_like(bud) for _ in range(NB - 1)]
         # copies may be split over several streams per direction (one was the
         # fastest: the host link, not the copy engines, is the bound)
         NCOPY = max(1, args.e2e_copy_streams)
         s_in = [torch.cuda.Stream() for _ in range(NCOPY)]
         s_out = [torch.cuda.Stream() for _ in range(NCOPY)]
         s_run = torch.cuda.Stream()
-        ev_in = [[torch.cuda.Event() for _ in range(NCOPY)] for _ in range(2)]
-        ev_out = [[torch.cuda.Event() for _ in range(NCOPY)] for _ in range(2)]
-        ev_run = [torch.cuda.Event(), torch.cuda.Event()]
+        ev_in = [[torch.cuda.Event() for _ in range(NCOPY)] for _ in range(NB)]
+        ev_out = [[torch.cuda.Event() for _ in range(NCOPY)] for _ in range(NB)]
+        ev_run = [torch.cuda.Event() for _ in range(NB)]
         # pieces of about equal size: every tensor cut along its slowest dimension
         def pieces(tensors):
             if NCOPY == 1:
@@ -698,10 +701,10 @@ def run_ours(args):
 
         def e2e_steps(n):
             for q in range(n):
-                b = q % 2
+                b = q % NB
                 ins = pieces([(getattr(bufs[b], k), host[k]) for k in names])
                 for c, sx in enumerate(s_in):
-                    if q >= 2:
+                    if q >= NB:
                         for c2 in range(NCOPY):       # buffer set b has been read back
                             sx.wait_event(ev_out[b][c2])
                     with torch.cuda.stream(sx):
@@ -748,7 +751,7 @@ def run_ours(args):
         e2e = {"value": world * C * ne / (ems * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "steps": ne, "ms_per_step": ems / ne,
                "overlap": f"copies in ({NCOPY} stream(s)), the step, copies out ({NCOPY} stream(s)); "
-                          "two device buffer sets"}
+                          f"{NB} device buffer sets"}
         del host, hout, bufs
     del st, ws_t
     torch.cuda.empty_cache()
@@ -829,6 +832,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--e2e-copy-streams", type=int, default=1,
                     help="streams per copy direction in the end-to-end measurement (1 was fastest on GB300)")
+    ap.add_argument("--e2e-buffers", type=int, default=4,
+                    help="device buffer sets the end-to-end pipeline rotates through (>= 2)")
     ap.add_argument("--ref-n", type=int, default=128, help="reference arm sample size (n x n x 58)")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
