@@ -32,6 +32,7 @@
 // The FP32 path computes in float throughout (the factorisation is computed
 // in double on the host and rounded).
 #include "acoustic.cuh"
+#include "smem_attr.cuh"
 
 #ifndef ACOUSTIC_RING
 #define ACOUSTIC_RING 3   // levels in the shared-memory ring (2 requested ahead)
@@ -227,9 +228,9 @@ cudaError_t launch_acoustic_stage(const AcousticParams<T> &p, int stage, cudaStr
     constexpr size_t smem = (size_t)D * 11 * 256 * sizeof(T);
     dim3 block(32, 8), grid((p.nx + 31) / 32, (p.ny + 7) / 8);
     if (stage == 1) {
-        if (smem > 48 * 1024) {   // set on every call: the attribute belongs to the current device
-            const cudaError_t e = cudaFuncSetAttribute(acoustic_kernel<T, 1, D>,
-                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (smem > 48 * 1024) {
+            static std::atomic<unsigned long long> attr_done{0};   // devices whose attribute is set
+            const cudaError_t e = set_smem_once(acoustic_kernel<T, 1, D>, (int)smem, attr_done);
             if (e != cudaSuccess) return e;
         }
         acoustic_kernel<T, 1, D><<<grid, block, smem, s>>>(p);

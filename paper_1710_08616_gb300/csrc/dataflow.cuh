@@ -18,6 +18,7 @@
 #pragma once
 
 #include "column_impl.cuh"
+#include "smem_attr.cuh"
 #include "dataflow_params.cuh"
 #include "stage_impl.cuh"
 
@@ -123,13 +124,9 @@ __global__ void __launch_bounds__(32 * TYV, StageShape<T, NF, TYV>::MIN_BLOCKS)
 template <typename T, int NF, int LIM, int TYV>
 static cudaError_t df_launch_lim(const DfParams<T> &p, int grid, cudaStream_t s, int *grid_out) {
     using S = StageShape<T, NF, TYV>;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t r = cudaFuncSetAttribute(dataflow_kernel<T, NF, LIM, TYV>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM_BYTES);
-        if (r != cudaSuccess) return r;
-        attr_set = true;
-    }
+    static std::atomic<unsigned long long> attr_done{0};   // devices whose attribute is set
+    const cudaError_t r = set_smem_once(dataflow_kernel<T, NF, LIM, TYV>, (int)S::SMEM_BYTES, attr_done);
+    if (r != cudaSuccess) return r;
     if (grid_out) {
         int per_sm = 0, dev = 0, nsm = 0;
         cudaError_t r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dataflow_kernel<T, NF, LIM, TYV>,

@@ -12,6 +12,7 @@
 #pragma once
 
 #include "ensemble_params.cuh"
+#include "smem_attr.cuh"
 #include "column_impl.cuh"
 #include "stage_impl.cuh"
 
@@ -97,13 +98,9 @@ __global__ void __launch_bounds__(32 * TYV, StageShape<T, NF, TYV>::MIN_BLOCKS)
 template <typename T, int NF, int LIM, int TYV>
 static cudaError_t ens_launch_lim(const EnsParams<T> &e, int grid, cudaStream_t s, int *grid_out) {
     using S = StageShape<T, NF, TYV>;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t r = cudaFuncSetAttribute(ensemble_kernel<T, NF, LIM, TYV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)S::SMEM_BYTES);
-        if (r != cudaSuccess) return r;
-        attr_set = true;
-    }
+    static std::atomic<unsigned long long> attr_done{0};   // devices whose attribute is set
+    const cudaError_t r = set_smem_once(ensemble_kernel<T, NF, LIM, TYV>, (int)S::SMEM_BYTES, attr_done);
+    if (r != cudaSuccess) return r;
     if (grid_out) {   // size query: resident CTAs per SM times SMs
         int per_sm = 0, dev = 0, nsm = 0;
         cudaError_t r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ensemble_kernel<T, NF, LIM, TYV>,

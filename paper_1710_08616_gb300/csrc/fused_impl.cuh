@@ -7,6 +7,7 @@
 #pragma once
 
 #include "column_impl.cuh"
+#include "smem_attr.cuh"
 #include "stage_impl.cuh"
 
 namespace asuca {
@@ -26,13 +27,9 @@ __global__ void __launch_bounds__(32 * TYV, StageShape<T, NF, TYV>::MIN_BLOCKS)
 template <typename T, int NF, int LIM, int TYV>
 static cudaError_t fused_launch_lim(const FusedParams<T> &p, cudaStream_t s) {
     using S = StageShape<T, NF, TYV>;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(stage3_column_kernel<T, NF, LIM, TYV>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM_BYTES);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    static std::atomic<unsigned long long> attr_done{0};   // devices whose attribute is set
+    const cudaError_t e = set_smem_once(stage3_column_kernel<T, NF, LIM, TYV>, (int)S::SMEM_BYTES, attr_done);
+    if (e != cudaSuccess) return e;
     dim3 block(S::TX, S::TY);
     dim3 grid((p.s.nx + S::TX - 1) / S::TX, (p.s.ny + S::TY - 1) / S::TY);
     stage3_column_kernel<T, NF, LIM, TYV><<<grid, block, S::SMEM_BYTES, s>>>(p);

@@ -35,6 +35,7 @@
 #include <type_traits>
 
 #include "common.cuh"
+#include "smem_attr.cuh"
 
 namespace asuca {
 
@@ -600,13 +601,9 @@ __global__ void __launch_bounds__(32 * TYV, StageShape<T, NF, TYV>::MIN_BLOCKS)
 template <typename T, int NF, int LIM, bool REC, int TYV>
 static cudaError_t launch_rec(const StageParams<T> &p, cudaStream_t s) {
     using S = StageShape<T, NF, TYV>;
-    static bool attr_set = false;   // one attribute call per instantiation
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(stage_kernel<T, NF, LIM, REC, TYV>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM_BYTES);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    static std::atomic<unsigned long long> attr_done{0};   // devices whose attribute is set
+    const cudaError_t e = set_smem_once(stage_kernel<T, NF, LIM, REC, TYV>, (int)S::SMEM_BYTES, attr_done);
+    if (e != cudaSuccess) return e;
     dim3 block(S::TX, S::TY);
     dim3 grid((p.nx + S::TX - 1) / S::TX, (p.ny + S::TY - 1) / S::TY);
     stage_kernel<T, NF, LIM, REC, TYV><<<grid, block, S::SMEM_BYTES, s>>>(p);
