@@ -88,6 +88,10 @@ def test_null_arguments(lib):
     assert lib.asuca_free_grid(None) == asuca.ERR_ARG
     assert lib.asuca_workspace_bytes(None, 0, 0) == 0
     assert lib.asuca_step(None, None, None, 1.0, 1, None, 0, None, None) == asuca.ERR_ARG
+    assert lib.asuca_stencil7(None, None, 8, 8, 4, 0, 0, 0.1, None) == asuca.ERR_ARG
+    assert lib.asuca_damping(None, None, None, None, None, 0.5, 0.5, 1.0, None, None) == asuca.ERR_ARG
+    assert lib.asuca_acoustic_workspace_bytes(None) == 0
+    assert lib.asuca_acoustic_steps(None, None, None, None, None, None, 1.0, 1, None, 0, None) == asuca.ERR_ARG
 
 
 @pytest.mark.parametrize("Q,R", [(4, 1), (4, 2), (8, 3), (64, 5), (64, 128), (12, 129)])
