@@ -13,7 +13,13 @@ stand-ins of the same shape:
   streamfunction scaled to max |u|, |v| = 20 m/s, plus one x-z overturning
   mode (max 2 m/s) whose vertical mass flux MW follows from discrete
   continuity, so the 3D mass divergence is zero up to rounding;
-* dt from a Courant number of 0.8.
+* dt from a Courant number of 0.8;
+* for the damping: a level-mean reference state and two boundary datasets
+  (the state's deviation from it, the second one shifted, both with 1%
+  noise);
+* for the acoustic short steps: a base density rho_s exp(-g z / c^2) and
+  perturbations taken from the case (s from the theta bubbles, momenta
+  from 5% of the mass fluxes).
 
 Array layout (all C order, i fastest):
   rho, rhotheta : [nz][ny][nx]
