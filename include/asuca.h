@@ -347,6 +347,15 @@ asuca_status asuca_damping(asuca_grid *grid, asuca_state *state, const void *ref
                            const void *bnd1, double mtratio, double tratio, double dt,
                            const asuca_damping_desc *desc, void *cuda_stream);
 
+/* Host-only views of the zone asuca_damping touches (no device work): the
+ * number of zone cells (0 for arguments asuca_damping would reject), and the
+ * kernel's enumeration of them.  ijk: caller-owned host array of 3 n
+ * unsigned values, (i, j, k) of the zone's cells in the order the kernel's
+ * flat index visits them; n must equal the zone's cell count, else
+ * ASUCA_ERR_ARG. */
+size_t asuca_damping_zone_cells(int nx, int ny, int nz, int width, int ntop);
+asuca_status asuca_debug_damping_cells(int nx, int ny, int nz, int width, int ntop, unsigned *ijk, size_t n);
+
 /* ---- HEVI acoustic short steps ------------------------------------------
  * Sound and gravity waves advanced in short steps by a two-stage Runge-Kutta
  * scheme, horizontally explicit and vertically implicit (Sec. 1.1, "ASUCA on

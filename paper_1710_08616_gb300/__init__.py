@@ -85,6 +85,8 @@ SIGNATURES = {
                                       ctypes.c_double, _VP]),
     "asuca_damping": (ctypes.c_int, [_VP, ctypes.POINTER(StateStruct), _VP, _VP, _VP, ctypes.c_double,
                                      ctypes.c_double, ctypes.c_double, ctypes.POINTER(DampingDesc), _VP]),
+    "asuca_damping_zone_cells": (ctypes.c_size_t, [ctypes.c_int] * 5),
+    "asuca_debug_damping_cells": (ctypes.c_int, [ctypes.c_int] * 5 + [_VP, ctypes.c_size_t]),
     "asuca_acoustic_workspace_bytes": (ctypes.c_size_t, [_VP]),
     "asuca_acoustic_steps": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, ctypes.POINTER(AcousticDesc), ctypes.c_double,
                                             ctypes.c_int, _VP, ctypes.c_size_t, _VP]),

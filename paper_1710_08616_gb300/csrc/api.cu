@@ -1558,6 +1558,25 @@ asuca_status asuca_stencil7(const void *in, void *out, int nx, int ny, int nz, i
     return cuda_status(e);
 }
 
+asuca_status asuca_debug_damping_cells(int nx, int ny, int nz, int width, int ntop, unsigned *ijk, size_t n) {
+    if (nx < 1 || ny < 1 || nz < 1 || width < 0 || width > ASUCA_DAMP_MAX_WIDTH || 2 * width > std::min(nx, ny) ||
+        ntop < 0 || ntop > nz || (double)nx * ny * nz >= 4294967296.0)
+        return ASUCA_ERR_ARG;
+    const DampZone z = damping_zone(nx, ny, nz, width, ntop);
+    if (!ijk || n != (size_t)z.total) return ASUCA_ERR_ARG;
+    for (unsigned u = 0; u < z.total; u++)
+        damping_cell(u, (unsigned)width, (unsigned)nx, (unsigned)ny, (unsigned)nz, (unsigned)ntop, z.frame, z.nlow,
+                     z.plane, ijk[3 * (size_t)u], ijk[3 * (size_t)u + 1], ijk[3 * (size_t)u + 2]);
+    return ASUCA_OK;
+}
+
+size_t asuca_damping_zone_cells(int nx, int ny, int nz, int width, int ntop) {
+    if (nx < 1 || ny < 1 || nz < 1 || width < 0 || width > ASUCA_DAMP_MAX_WIDTH || 2 * width > std::min(nx, ny) ||
+        ntop < 0 || ntop > nz || (double)nx * ny * nz >= 4294967296.0)
+        return 0;
+    return damping_zone(nx, ny, nz, width, ntop).total;
+}
+
 asuca_status asuca_damping(asuca_grid *g, asuca_state *st, const void *ref, const void *bnd0, const void *bnd1,
                            double mtratio, double tratio, double dt, const asuca_damping_desc *desc,
                            void *cuda_stream) {

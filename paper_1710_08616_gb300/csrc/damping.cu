@@ -44,31 +44,7 @@ __global__ void __launch_bounds__(256) damping_kernel(const __grid_constant__ Da
     const unsigned W = (unsigned)p.width, nx = (unsigned)p.nx;
     for (unsigned u = blockIdx.x * blockDim.x + threadIdx.x; u < p.total; u += gridDim.x * blockDim.x) {
         unsigned i, j, k;
-        if (u < p.nlow) {   // lateral frame of a level below the top zone
-            k = u / p.frame;
-            unsigned r = u - k * p.frame;
-            const unsigned wn = W * nx;
-            if (r < wn) {                       // bottom rows j < width
-                j = r / nx;
-                i = r - j * nx;
-            } else if (r < 2 * wn) {            // top rows j >= ny - width
-                r -= wn;
-                const unsigned jj = r / nx;
-                i = r - jj * nx;
-                j = (unsigned)p.ny - W + jj;
-            } else {                            // left and right segments of the rows between
-                r -= 2 * wn;
-                const unsigned jj = r / (2 * W), c = r - jj * (2 * W);
-                j = W + jj;
-                i = c < W ? c : nx - 2 * W + c;
-            }
-        } else {            // a whole level of the top zone
-            const unsigned r = u - p.nlow;
-            const unsigned kk = r / p.plane, c = r - kk * p.plane;
-            k = (unsigned)(p.nz - p.ntop) + kk;
-            j = c / nx;
-            i = c - j * nx;
-        }
+        damping_cell(u, W, nx, (unsigned)p.ny, (unsigned)p.nz, (unsigned)p.ntop, p.frame, p.nlow, p.plane, i, j, k);
         const int d = min(min((int)i, p.nx - 1 - (int)i), min((int)j, p.ny - 1 - (int)j));
         const int kk = (int)k - (p.nz - p.ntop);
         T a = T(0), c = T(1), ac = T(0);
@@ -108,11 +84,12 @@ cudaError_t launch_damping(T *const *y, int nf, const T *ref, const T *b0, const
     p.ref = ref;
     p.b0 = b0;
     p.b1 = b1;
-    p.plane = (unsigned)nx * (unsigned)ny;
+    const DampZone z = damping_zone(nx, ny, nz, width, ntop);
+    p.plane = z.plane;
     p.fs = (size_t)p.plane * nz;
-    p.frame = 2u * width * nx + (unsigned)(ny - 2 * width) * 2u * width;
-    p.nlow = (unsigned)(nz - ntop) * p.frame;
-    p.total = p.nlow + (unsigned)ntop * p.plane;
+    p.frame = z.frame;
+    p.nlow = z.nlow;
+    p.total = z.total;
     p.nx = nx;
     p.ny = ny;
     p.nz = nz;

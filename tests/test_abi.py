@@ -109,3 +109,41 @@ def test_dataflow_task_order_is_topological(lib, Q, R):
             if q > 0:
                 assert pos[(q - 1, (r + dr) % R)] < k
     assert lib.asuca_debug_dataflow_order(65, 4, out.ctypes.data_as(ctypes.c_void_p)) == asuca.ERR_ARG
+
+
+@pytest.mark.parametrize("nx,ny,nz,width,ntop", [(17, 11, 7, 3, 2), (4, 4, 3, 2, 3), (70, 9, 5, 4, 0),
+                                                 (32, 32, 16, 0, 5), (300, 130, 12, 64, 1), (512, 256, 20, 16, 8),
+                                                 (5, 7, 4, 0, 0)])
+def test_damping_zone_enumeration(lib, nx, ny, nz, width, ntop):
+    """Host logic of the damping kernel: its flat index visits every cell of
+    the zone (fewer than `width` cells from an i or j edge, or on the top ntop
+    levels) exactly once and nothing else, consecutive indices mostly on
+    consecutive i (coalesced)."""
+    import numpy as np
+    n = lib.asuca_damping_zone_cells(nx, ny, nz, width, ntop)
+    k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    d = np.minimum(np.minimum(i, nx - 1 - i), np.minimum(j, ny - 1 - j))
+    zone = (d < width) | (k >= nz - ntop)
+    assert n == int(zone.sum())
+    if n == 0:
+        return
+    out = np.zeros(3 * n, dtype=np.uint32)
+    assert lib.asuca_debug_damping_cells(nx, ny, nz, width, ntop, out.ctypes.data_as(ctypes.c_void_p), n) == asuca.OK
+    ijk = out.reshape(n, 3).astype(np.int64)
+    assert ijk[:, 0].max() < nx and ijk[:, 1].max() < ny and ijk[:, 2].max() < nz
+    flat = (ijk[:, 2] * ny + ijk[:, 1]) * nx + ijk[:, 0]
+    assert len(np.unique(flat)) == n
+    assert zone.reshape(-1)[flat].all()
+    steps = np.diff(flat)
+    assert np.mean(steps == 1) > 0.5
+
+
+def test_damping_zone_arguments(lib):
+    import numpy as np
+    assert lib.asuca_damping_zone_cells(16, 12, 5, 7, 1) == 0        # 2 width > ny
+    assert lib.asuca_damping_zone_cells(16, 12, 5, 2, 6) == 0        # ntop > nz
+    assert lib.asuca_damping_zone_cells(200, 200, 5, 65, 1) == 0     # wider than the library takes
+    n = lib.asuca_damping_zone_cells(16, 12, 5, 2, 1)
+    out = np.zeros(3 * n, dtype=np.uint32)
+    assert lib.asuca_debug_damping_cells(16, 12, 5, 2, 1, out.ctypes.data_as(ctypes.c_void_p), n - 1) == asuca.ERR_ARG
+    assert lib.asuca_debug_damping_cells(16, 12, 5, 2, 1, None, n) == asuca.ERR_ARG
