@@ -55,15 +55,17 @@ def gather_budgets(local: dict, nmembers: int, nbudget: int, group=None):
     return buf.cpu().numpy()
 
 
-def ensemble_step_sharded(grids, states, dts, nsteps: int, *, group=None, workspace=None):
+def ensemble_step_sharded(grids, states, dts, nsteps: int, *, group=None, workspace=None, step=None):
     """Advance this rank's share of the ensemble (members from shard_members over
     all members' cells) with one persistent launch and return every member's
     budgets, gathered over the ranks.  `grids`, `states`, `dts` list all members
     on every rank; only this rank's members are touched.  `workspace`, if given,
-    is sized for this rank's members (ensemble_workspace_bytes of that subset)."""
-    import torch
+    is sized for this rank's members (ensemble_workspace_bytes of that subset).
+    `step` replaces asuca_ensemble_step (same arguments and result); it lets the
+    host-side sharding and gather run on CPU ranks in tests."""
     import torch.distributed as dist
-    from . import ensemble_step
+    if step is None:
+        from . import ensemble_step as step
 
     world = dist.get_world_size(group)
     rank = dist.get_rank(group)
@@ -72,9 +74,9 @@ def ensemble_step_sharded(grids, states, dts, nsteps: int, *, group=None, worksp
     nb = grids[0].nfields + 1
     local = {}
     if mine:
-        bud = ensemble_step([grids[m] for m in mine], [states[m] for m in mine], [dts[m] for m in mine],
-                            nsteps, workspace=workspace, budgets=True)
-        torch.cuda.synchronize()
+        bud = step([grids[m] for m in mine], [states[m] for m in mine], [dts[m] for m in mine],
+                   nsteps, workspace=workspace, budgets=True)
+        # the copy to the host waits for the step on its stream
         b = bud.cpu().numpy().reshape(len(mine), nb)
         local = {m: b[q] for q, m in enumerate(mine)}
     return gather_budgets(local, len(grids), nb, group)

@@ -1,6 +1,9 @@
 """Multi-rank host logic on CPU (gloo, world size 2): sharding ensemble members
-over ranks, the exact FP64 budget gather, and the benchmark's max-over-ranks
-timing.  The GPU-side step of each rank is the single-GPU path tested elsewhere."""
+over ranks, the exact FP64 budget gather, ensemble_step_sharded with a
+stand-in member step (each rank steps only its own members; every rank ends
+with every member's budgets), and the benchmark's max-over-ranks timing.  The
+GPU-side step of each rank is the single-GPU path tested elsewhere (and
+ensemble_step_sharded itself at world size 1 on the GPU)."""
 import os
 import socket
 
@@ -76,3 +79,61 @@ def test_gloo_world2_budget_gather_and_max_over_ranks():
     for rank, exact, tmax in res:
         assert exact, f"rank {rank}: gathered budgets differ"
         assert tmax == 2.5
+
+
+def _sharded_worker(rank, world, port, q):
+    import types
+    import torch
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        from paper_1710_08616_gb300.distributed import ensemble_step_sharded
+        sizes = [64, 97, 40, 71, 33, 120, 58]
+        nf = 6
+        grids = [types.SimpleNamespace(nx=n, ny=n, nz=12, nfields=nf) for n in sizes]
+        states = [{"member": m, "steps": 0} for m in range(len(sizes))]
+        dts = [10.0 + m for m in range(len(sizes))]
+        seen = []
+
+        def fake_step(gs, sts, ds, nsteps, workspace=None, budgets=False):
+            # stand-in for the persistent launch: advance each given member and
+            # return its budgets as a deterministic function of the member
+            assert budgets
+            out = []
+            for g, st, dt in zip(gs, sts, ds):
+                st["steps"] += nsteps
+                seen.append(st["member"])
+                m = st["member"]
+                out.append([g.nx * g.ny * g.nz * 1e-3 + m, dt * nsteps] + [m * 0.1 + f for f in range(nf - 1)])
+            return torch.tensor(out, dtype=torch.float64).reshape(-1)
+
+        got = ensemble_step_sharded(grids, states, dts, 3, step=fake_step)
+        q.put((rank, sorted(seen), [st["steps"] for st in states], got.tobytes()))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_gloo_world2_ensemble_step_sharded_host_logic():
+    import multiprocessing as mp
+    from paper_1710_08616_gb300.distributed import shard_members
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_sharded_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    sizes = [64, 97, 40, 71, 33, 120, 58]
+    share = shard_members([n * n * 12 for n in sizes], 2)
+    nf = 6
+    expect = np.array([[n * n * 12 * 1e-3 + m, (10.0 + m) * 3] + [m * 0.1 + f for f in range(nf - 1)]
+                       for m, n in enumerate(sizes)])
+    for rank, seen, steps, got in res:
+        assert seen == share[rank]                      # this rank stepped exactly its members
+        assert steps == [3 if m in share[rank] else 0 for m in range(len(sizes))]
+        assert np.frombuffer(got, dtype=np.float64).reshape(expect.shape).tolist() == expect.tolist()

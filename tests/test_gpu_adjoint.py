@@ -1,15 +1,17 @@
 """GPU adjoint (asuca_adjoint_step) against the oracle and against the forward map.
 
-* FP64 adjoint vs the oracle's FP64 adjoint, element by element (1e-11
-  relative), with the oracle linearised along the limiter branches the GPU
-  forward pass recorded.  Where a limiter's arguments are pure rounding noise
-  (theta is horizontally uniform away from its bubbles) the two forward passes
-  can legitimately take different branches, and each adjoint is the exact
-  transpose of its own forward pass; fixing the branches compares the
-  transposes themselves.  The fraction of faces whose branch differs is
-  checked to stay small;
+* FP64 adjoint vs the oracle's FP64 adjoint, element by element (1e-12
+  relative, the FP64 parity bar), with the oracle linearised along its own
+  forward pass's limiter branches.  The GPU's forward pass may take another
+  branch only at a face whose limiter decision is a rounding tie: the two
+  competing limiter terms (or, for the zero branch, d0 or d1 themselves) lie
+  within TIE_ULP units in the last place of the field's scale in the oracle's
+  own trajectory.  Only at those faces is the GPU's branch substituted; a
+  differing branch anywhere else fails the test, and the mismatch fraction is
+  printed;
 * results independent of the checkpoint interval (bit for bit);
-* dot-product test between the oracle's tangent-linear model and the GPU adjoint;
+* dot-product test between the oracle's tangent-linear model and the GPU
+  adjoint, along the oracle's branches with the same tie substitution;
 * central differences of J = 1/2 sum (q - q_target)^2 through the GPU forward
   (eps = 1e-6, 20 seeded directions scaled by field RMS, relative 1e-6), with
   the Koren limiter on a grid where kink-free directions exist (checked with the
@@ -54,6 +56,94 @@ def _gpu_branches(asuca, case, nsteps, lim=0, tend=None, prec=0):
     return out
 
 
+# A branch differing between the GPU and the oracle is accepted only where the
+# limiter's decision is a rounding tie in the oracle's own trajectory: the
+# competing terms within TIE_ULP ulp of the field's scale (max |phi| of the
+# field at that stage).  The two FP64 trajectories differ by a few ulp per
+# operation (different but exact-to-rounding evaluation orders).
+TIE_ULP = 64
+EPS64 = np.finfo(np.float64).eps
+
+
+def _oracle_stage_inputs(og, c, nsteps, tend=None):
+    """The oracle's stage inputs (Y^n, Y*, Y**) of every step, in its own
+    arithmetic: Y^(s) = Y^n + c_s R(Y^(s-1)) in double, then the column pass."""
+    Y = c.state().astype(np.float64)
+    cs = (c.dt / 3.0, c.dt / 2.0, c.dt)
+    out = []
+    for _ in range(nsteps):
+        st = [Y]
+        S = Y
+        for q in range(3):
+            S = Y + cs[q] * oracle.rhs(og, S, c.mu, c.mv, c.mw, tend=tend)
+            if q < 2:
+                st.append(S)
+        out.append(st)
+        Y, _ = oracle.column(og, S, c.dt)
+    return out
+
+
+def _face_margins(Y, mu, mv, mw):
+    """Per direction (i, j, k), the limiter arguments' distances from the branch
+    boundaries at every face i+1/2, j+1/2, k+1/2 of fields 1..F-1:
+    (zero-branch margin min(|d0|, |d1|), |t1 - t2|, |t2 - t3|, |t1 - t3|) with
+    t1 = 2|d1|, t2 = (|d0| + 2|d1|)/3, t3 = 2|d0| and the upwind side by sign(M)."""
+    phi = Y[1:] / Y[0]
+    nz = phi.shape[1]
+    out = []
+    for d in range(3):
+        if d < 2:
+            ax = 3 - d
+            pm1, p1, p2 = (np.roll(phi, s, axis=ax) for s in (1, -1, -2))
+            m = (mu if d == 0 else mv)[None]
+        else:
+            up = lambda s: phi[:, np.clip(np.arange(nz) + s, 0, nz - 1)]
+            pm1, p1, p2 = up(-1), up(1), up(2)
+            m = np.concatenate([mw[1:nz], np.zeros_like(mw[:1])])[None]
+        pos = m >= 0
+        d0 = np.where(pos, phi - pm1, p1 - p2)
+        d1 = np.where(pos, p1 - phi, phi - p1)
+        a0, a1 = np.abs(d0), np.abs(d1)
+        t1, t2, t3 = 2 * a1, (a0 + 2 * a1) / 3, 2 * a0
+        out.append((np.minimum(a0, a1), np.abs(t1 - t2), np.abs(t2 - t3), np.abs(t1 - t3)))
+    return out
+
+
+def _tie_substituted_branches(og, c, nsteps, gpu_br, own_br, tend=None):
+    """own_br with the GPU's branch at tie faces; asserts that every face where
+    the two differ is a tie.  Returns (branches, mismatch fraction, worst margin
+    of a mismatch in ulp of the field's scale)."""
+    states = _oracle_stage_inputs(og, c, nsteps, tend)
+    out = own_br.copy()
+    nmis, worst = 0, 0.0
+    for s in range(nsteps):
+        for q in range(3):
+            Y = states[s][q]
+            scale = np.abs(Y[1:] / Y[0]).reshape(Y.shape[0] - 1, -1).max(axis=1)[:, None, None, None]
+            margins = _face_margins(Y, c.mu, c.mv, c.mw)
+            bg, bo = gpu_br[s, q, 1:], own_br[s, q, 1:]
+            for d in range(3):
+                xg, xo = (bg >> (2 * d)) & 3, (bo >> (2 * d)) & 3
+                mis = xg != xo
+                if not mis.any():
+                    continue
+                zero, m12, m23, m13 = margins[d]
+                lo, hi = np.minimum(xg, xo), np.maximum(xg, xo)
+                marg = np.where(lo == 0, zero, np.where((lo == 1) & (hi == 2), m12,
+                                                        np.where((lo == 2) & (hi == 3), m23, m13)))
+                ulp = marg / (EPS64 * scale)
+                bad = mis & (ulp > TIE_ULP)
+                assert not bad.any(), (
+                    f"step {s} stage {q} dir {d}: {int(bad.sum())} faces differ outside a rounding tie "
+                    f"(worst {float(ulp[bad].max()):.3g} ulp of the field's scale)")
+                worst = max(worst, float(ulp[mis].max()))
+                nmis += int(mis.sum())
+                sub = out[s, q, 1:]
+                sub[mis] = (sub[mis] & ~np.uint8(3 << (2 * d))) | (xg[mis] << (2 * d)).astype(np.uint8)
+    frac = nmis / float(3 * own_br[:, :, 1:].size)
+    return out, frac, worst
+
+
 def _gpu_adjoint(asuca, case, lam, nsteps, K, prec=0, lim=0, tend=None, tile_rows=None):
     import torch
     g = asuca.Grid.from_case(case, prec=prec, lim=lim)
@@ -81,12 +171,15 @@ def test_adjoint_fp64_matches_oracle(asuca, lim, shape, ntr, nsteps):
     og = oracle.Grid.from_case(c, lim=lim)
     br = _gpu_branches(asuca, c, nsteps, lim=lim, tend=tend)
     own = oracle.trajectory_branches(og, c.state(), c.mu, c.mv, c.mw, c.dt, nsteps, tend=tend)
-    assert np.mean(br != own) <= 0.05
-    ref = oracle.step_adj(og, c.state(), c.mu, c.mv, c.mw, c.dt, nsteps, lam, tend=tend, traj_br=br)
+    traj, frac, worst = _tie_substituted_branches(og, c, nsteps, br, own, tend=tend)
+    print(f"lim {lim} {shape}: branch mismatch fraction {frac:.3e} (all rounding ties, "
+          f"worst {worst:.3g} ulp of the field's scale)")
+    ref = oracle.step_adj(og, c.state(), c.mu, c.mv, c.mw, c.dt, nsteps, lam, tend=tend, traj_br=traj)
     got = _gpu_adjoint(asuca, c, lam, nsteps, nsteps, lim=lim, tend=tend)
     for name, a, b in zip(("lam0", "gmu", "gmv", "gmw"), got, ref):
         l2, mx = _rel(a, b)
-        assert l2 <= 1e-11 and mx <= 1e-11, (name, l2, mx)
+        print(f"  {name}: rel L2 {l2:.3e}, rel max {mx:.3e}")
+        assert l2 <= 1e-12 and mx <= 1e-12, (name, l2, mx)
 
 
 def test_adjoint_independent_of_checkpoint_interval(asuca):
@@ -153,11 +246,14 @@ def test_dot_product_oracle_tangent_linear_vs_gpu_adjoint(asuca):
     lam = rng.standard_normal(Y.shape)
     n = 4
     br = _gpu_branches(asuca, c, n)
-    tl = oracle.step_tl(og, Y, c.mu, c.mv, c.mw, c.dt, n, dY, dmu, dmv, dmw, traj_br=br)
+    own = oracle.trajectory_branches(og, Y, c.mu, c.mv, c.mw, c.dt, n)
+    traj, _, _ = _tie_substituted_branches(og, c, n, br, own)
+    tl = oracle.step_tl(og, Y, c.mu, c.mv, c.mw, c.dt, n, dY, dmu, dmv, dmw, traj_br=traj)
     g0, gmu, gmv, gmw = _gpu_adjoint(asuca, c, lam, n, n)
     lhs = float(np.sum(tl * lam))
     rhs = float(np.sum(dY * g0) + np.sum(dmu * gmu) + np.sum(dmv * gmv) + np.sum(dmw * gmw))
-    assert abs(lhs - rhs) <= 1e-11 * max(abs(lhs), abs(rhs))
+    print(f"dot product: lhs {lhs:.17g}, rhs {rhs:.17g}, rel {abs(lhs - rhs) / max(abs(lhs), abs(rhs)):.3e}")
+    assert abs(lhs - rhs) <= 1e-12 * max(abs(lhs), abs(rhs))
 
 
 def _fd_check(asuca, case, nsteps, lim, K, ndir=20, check_kinks=True, max_draws=60):

@@ -80,6 +80,7 @@ def test_fp64_member_against_oracle(asuca):
         got = ens[m].fields().cpu().numpy()
         for f in range(ref.shape[0]):
             assert np.linalg.norm(got[f] - ref[f]) <= 1e-12 * np.linalg.norm(ref[f])
+            assert np.abs(got[f] - ref[f]).max() <= 1e-12 * np.abs(ref[f]).max()
 
 
 def test_barrier_timeout_reports_status(asuca):
@@ -133,3 +134,28 @@ def test_tile_shapes_give_identical_results_and_autotuner_picks_one(asuca, tmp_p
     assert all(torch.equal(a, b) for a, b in zip(*outs))
     e = autotune.tune_ensemble(grids, [asuca.State.from_case(m) for m in cases], [m.dt for m in cases], steps=1, reps=1)
     assert e["best"]["ensemble_tile_rows"] in (4, 8)
+
+
+def test_ensemble_step_sharded_world_size_1_equals_ensemble_step(asuca, tmp_path):
+    """ensemble_step_sharded on a one-rank group (gloo, budgets gathered on the
+    host) advances every member as ensemble_step does, bit for bit, and returns
+    the same budgets."""
+    import torch
+    import torch.distributed as dist
+    from paper_1710_08616_gb300.distributed import ensemble_step_sharded
+    cases = _members([64, 40, 71], ntr=3, nz=10)
+    grids = [asuca.Grid.from_case(c, prec=1) for c in cases]
+    a = [asuca.State.from_case(c, prec=1) for c in cases]
+    b = [s.clone() for s in a]
+    dts = [c.dt for c in cases]
+    ref = asuca.ensemble_step(grids, a, dts, 3, budgets=True).cpu().numpy().reshape(len(cases), -1)
+    dist.init_process_group("gloo", init_method=f"file://{tmp_path / 'pg'}", rank=0, world_size=1)
+    try:
+        got = ensemble_step_sharded(grids, b, dts, 3)
+    finally:
+        dist.destroy_process_group()
+    torch.cuda.synchronize()
+    assert asuca.get_status(grids[0]) == asuca.OK
+    for x, y in zip(a, b):
+        assert torch.equal(x.fields(), y.fields())
+    assert np.array_equal(got, ref)
