@@ -264,8 +264,9 @@ asuca_status asuca_debug_dataflow_order(int nphases, int nrows, unsigned *out);
 /* Test hook for the arithmetic helpers of the column solve (device arrays of
  * n values; any output may be NULL): widen[i] = in_f[i] as double, narrow[i]
  * = in_d[i] rounded to float (nearest-even), both computed on the integer
- * pipe from the IEEE-754 bit fields; rcp[i] = 1 / in_d[i] by two
- * Newton-Raphson steps from the hardware approximation. */
+ * pipe from the IEEE-754 bit fields; rcp[i] = 1 / in_d[i] from a float
+ * reciprocal seed and one third-order correction (within an ulp; |in_d| in
+ * the float normal range). */
 asuca_status asuca_debug_numerics(const float *in_f, const double *in_d, int n, double *widen,
                                   float *narrow, double *rcp, void *cuda_stream);
 

@@ -102,14 +102,14 @@ __global__ void budget_reduce_kernel(const double *partials, int nblocks, int nq
     }
 }
 
-// Test hook: the integer-pipe conversions and the Newton reciprocal on n values.
+// Test hook: the integer-pipe conversions and the double reciprocal on n values.
 __global__ void numerics_kernel(const float *in_f, const double *in_d, int n, double *widen,
                                 float *narrow, double *rcp) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     if (widen) widen[i] = f2d_bits(in_f[i]);
     if (narrow) narrow[i] = d2f_bits(in_d[i]);
-    if (rcp) rcp[i] = rcp_newton(in_d[i]);
+    if (rcp) rcp[i] = rcp_f64(in_d[i]);
 }
 
 cudaError_t launch_numerics(const float *in_f, const double *in_d, int n, double *widen, float *narrow,

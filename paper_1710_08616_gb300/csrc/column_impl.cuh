@@ -19,7 +19,7 @@
 //   z_k = e_k + gamma_k z_{k-1},  gamma_k = g_{k-1/2} m_{k-1} dz_{k-1} / dz_k
 //   (rho phi)_k = sigma_k z_k,    sigma_k = rho_k dz_k m_k,   m_k = 1 / pivot_k
 // Per field and level that is two FP64 operations; the shared factorisation
-// costs about fifteen.  Float inputs are widened and the result narrowed on
+// costs about twelve (its reciprocal three of them).  Float inputs are widened and the result narrowed on
 // the integer pipe (the hardware conversions issue on the slow FP64 pipe);
 // for float fields the final multiply by sigma_k is done in float.
 // (x_k is the incoming rho*phi; d''_k = dz_k m_k e_k and phi_k = dz_k m_k z_k
@@ -122,10 +122,9 @@ __device__ __forceinline__ void column_one(const ColumnParams<T> &p, long long c
             if (p.do_diff) {
                 // (iii) forward elimination, top-down, on scaled unknowns
                 const double g_lo = (k > 0) ? p.kc[k - 1] * (rd_dn + rd) : 0.0;
-                const double rdz = rd * p.dz[k];
-                const double b = rdz + (g_lo + g_hi);
+                const double b = fma(rd, p.dz[k], g_lo + g_hi);
                 const double t = g_hi * m_up;
-                const double m = rcp_newton(fma(-g_hi, t, b));
+                const double m = rcp_f64(fma(-g_hi, t, b));
                 const double alpha = t * p.dzr_up[k];
                 sc[(long long)(k * NQ + 0) * nslots] = m;
                 const double gam = (k < nz - 1) ? g_hi * m * p.dzr_dn[k + 1] : 0.0;
@@ -280,10 +279,9 @@ struct ColDownHook {
         const double rd = to_f64(rho);
         const double rd_dn = (k > 0) ? to_f64(rho_next) : 0.0;
         const double g_lo = (k > 0) ? c.kc[k - 1] * (rd_dn + rd) : 0.0;
-        const double rdz = rd * c.dz[k];
-        const double b = rdz + (g_lo + g_hi);
+        const double b = fma(rd, c.dz[k], g_lo + g_hi);
         const double t = g_hi * m_up;
-        const double m = rcp_newton(fma(-g_hi, t, b));
+        const double m = rcp_f64(fma(-g_hi, t, b));
         const double alpha = t * c.dzr_up[k];
         sc[(size_t)(k * NQ + 0) * pl] = m;
         if (k < c.nz - 1) sc[(size_t)((k + 1) * NQ + 1) * pl] = g_hi * m * c.dzr_dn[k + 1];

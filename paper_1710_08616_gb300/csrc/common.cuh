@@ -38,6 +38,9 @@ struct StageShape {
     static constexpr int SLOT_RAW = NF * SY * SX;
     static constexpr int SLOT_ELEMS = (SLOT_RAW * (int)sizeof(T) + 127) / 128 * 128 / (int)sizeof(T);
     static constexpr unsigned TX_BYTES = (unsigned)(SLOT_RAW * sizeof(T));
+    // a padded stage input lands phi only (fields 1 .. NF-1): the stencil never
+    // reads the density, whose update depends on M alone
+    static constexpr unsigned TX_BYTES_PHI = (unsigned)((NF - 1) * SY * SX * sizeof(T));
     static constexpr size_t RING_BYTES = (size_t)D * SLOT_ELEMS * sizeof(T);
     static constexpr size_t YS_BYTES = ((size_t)NT * (TY + 1) * TX * sizeof(T) + 15) / 16 * 16;
     static constexpr size_t XB_BYTES = ((size_t)NT * TY * sizeof(T) + 15) / 16 * 16;
@@ -157,23 +160,31 @@ template <typename T> __device__ __forceinline__ T from_f64(double x);
 template <> __device__ __forceinline__ double from_f64<double>(double x) { return x; }
 template <> __device__ __forceinline__ float from_f64<float>(double x) { return d2f_bits(x); }
 
-// Reciprocal in double by Newton-Raphson iteration on f(y) = 1/y - x,
-// y <- y (2 - x y), started from the hardware reciprocal approximation of the
-// high word.  Each iteration squares the relative error, so two iterations
-// reach double precision (within a few ulp).  Valid for normal, finite,
-// non-zero x (densities and the diagonally dominant pivots of the solve).
-__device__ __forceinline__ double rcp_newton(double x) {
-    double y;
-    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
-    double e = fma(-x, y, 1.0);
-    y = fma(y, e, y);
-    e = fma(-x, y, 1.0);
-    y = fma(y, e, y);
-    return y;
+// Reciprocal in double from a float seed and one third-order correction.
+// The seed y0 is the float reciprocal (rcp.approx, relative error below
+// 2^-22 with the truncated operand) of x's leading 23 mantissa bits, built
+// and widened on the integer pipe.  With e = 1 - x y0 (exact to rounding by
+// FMA), 1/x = y0 / (1 - e) = y0 (1 + e + e^2 + e^3 + ...), so
+// y = y0 + y0 (e + e^2) leaves a truncation error of order e^3 < 2^-66: the
+// result is within an ulp of 1/x after three FP64 FMAs (the FP64 pipe bounds
+// the column solve).  Valid for normal, finite, non-zero x whose magnitude
+// lies in the float normal range (densities and the diagonally dominant
+// pivots of the solve).
+__device__ __forceinline__ double rcp_f64(double x) {
+    const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+    // binary64 -> binary32 by truncation: exponent rebiased by 896, 20 + 3 mantissa bits
+    const uint32_t xf = (hi & 0x80000000u) | ((((hi & 0x7fffffffu) - (896u << 20)) << 3) | (lo >> 29));
+    float rf;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(__uint_as_float(xf)));
+    const uint32_t u = __float_as_uint(rf);
+    const double y0 = __hiloint2double((int)((u & 0x80000000u) | (((u & 0x7fffffffu) >> 3) + (896u << 20))),
+                                       (int)(u << 29));
+    const double e = fma(-x, y0, 1.0);
+    return fma(y0, fma(e, e, e), y0);
 }
 
 template <typename T> __device__ __forceinline__ T recip(T x);
-template <> __device__ __forceinline__ double recip<double>(double x) { return rcp_newton(x); }
+template <> __device__ __forceinline__ double recip<double>(double x) { return rcp_f64(x); }
 template <> __device__ __forceinline__ float recip<float>(float x) { return __frcp_rn(x); }
 
 // v with its sign flipped when s has its sign bit set (v * sgn(s) as a bit operation)
@@ -197,12 +208,31 @@ __device__ __forceinline__ double sign_transfer(double v, double s) {
 //   L / 2 = sgn(d0) max(0, min(x, a, x/3 + a/6)).
 // The caller picks the three cells by address, so nothing here depends on
 // the flow direction.
+// min(|a|, |b|) carrying the sign sgn(a) sgn(b) (one instruction: PTX
+// min.xorsign.abs): non-negative exactly when a and b share a sign (or one of
+// them is zero, where the magnitude is 0).
+__device__ __forceinline__ float min_xorsign_abs(float a, float b) {
+    float d;
+    asm("min.xorsign.abs.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(b));
+    return d;
+}
+
 template <int LIM, typename T>
 __device__ __forceinline__ T face_val(T c, T o, T far) {
     if (LIM == ASUCA_LIM_UPWIND1) return c;
     const T d1 = o - c;
     const T d0 = c - far;
     if (LIM == ASUCA_LIM_LINEAR) return c + fma(d1, T(1.0 / 3.0), d0 * T(1.0 / 6.0));
+    if constexpr (std::is_same<T, float>::value) {
+        // The same value in fewer instructions: u = sgn(d0 d1) min(|d0|, |d1|)
+        // equals min(x, a) when d0 and d1 share a sign and is <= 0 otherwise,
+        // and |d1/3 + d0/6| equals t when they share a sign (round-to-nearest is
+        // symmetric in sign, so the rounding is the same); the outer max gives 0
+        // for opposite signs either way.
+        const float u = min_xorsign_abs(d1, d0);
+        const float t = fabsf(fmaf(d1, 1.f / 3.f, d0 * (1.f / 6.f)));
+        return c + copysignf(fmaxf(fminf(u, t), 0.f), d0);
+    }
     const T x = sign_transfer(d1, d0);
     const T a = fabs(d0);
     const T t = fma(x, T(1.0 / 3.0), a * T(1.0 / 6.0));
@@ -281,11 +311,10 @@ __device__ __forceinline__ float2 face_flux2(float2 c, float2 o, float2 far, flo
         const float2 t = __ffma2_rn(d1, make_float2(1.f / 3.f, 1.f / 3.f), __fmul2_rn(d0, make_float2(1.f / 6.f, 1.f / 6.f)));
         return __fmul2_rn(m2, __fadd2_rn(c, t));
     }
-    const float2 x = make_float2(sign_transfer(d1.x, d0.x), sign_transfer(d1.y, d0.y));
-    const float2 a = make_float2(fabsf(d0.x), fabsf(d0.y));
-    const float2 t = __ffma2_rn(x, make_float2(1.f / 3.f, 1.f / 3.f), __fmul2_rn(a, make_float2(1.f / 6.f, 1.f / 6.f)));
-    const float hx = fmaxf(fminf(fminf(x.x, a.x), t.x), 0.f);
-    const float hy = fmaxf(fminf(fminf(x.y, a.y), t.y), 0.f);
+    // the min.xorsign.abs form of face_val<float> (the same value)
+    const float2 t = __ffma2_rn(d1, make_float2(1.f / 3.f, 1.f / 3.f), __fmul2_rn(d0, make_float2(1.f / 6.f, 1.f / 6.f)));
+    const float hx = fmaxf(fminf(min_xorsign_abs(d1.x, d0.x), fabsf(t.x)), 0.f);
+    const float hy = fmaxf(fminf(min_xorsign_abs(d1.y, d0.y), fabsf(t.y)), 0.f);
     return __fmul2_rn(m2, __fadd2_rn(c, make_float2(copysignf(hx, d0.x), copysignf(hy, d0.y))));
 }
 

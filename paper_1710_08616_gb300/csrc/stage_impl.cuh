@@ -141,8 +141,13 @@ __device__ __forceinline__ bool stage_tile_h(const StageParams<T> &p, const CUte
     constexpr int TX = S::TX, TY = S::TY, D = S::D, SX = S::SX, SY = S::SY, NT = S::NT;
     constexpr int NTHR = TX * TY;
     constexpr int FE = SY * SX;                   // elements of one field in a slot
-    constexpr int NCELL = TY * (TX + 4) + 4 * TX; // the slot cells the stencil reads (no corners)
-    constexpr int MAXC = (NCELL + NTHR - 1) / NTHR;
+    // The slot cells the stencil reads (no corners), dealt to the threads in
+    // pairs of neighbours along i for the copies and the conversion to phi:
+    // TY rows of TX + 4 cells (i0-2 .. i0+TX+1) and 4 halo rows of TX cells.
+    constexpr int PR = (TX + 4) / 2, PH = TX / 2;
+    constexpr int NPAIR = TY * PR + 4 * PH;
+    constexpr int MAXC = (NPAIR + NTHR - 1) / NTHR;
+    using T2 = typename std::conditional<std::is_same<T, float>::value, float2, double2>::type;
     static_assert((FE * sizeof(T)) % 128 == 0, "each field of a slot must start on a 128-byte boundary");
 
     T *ring = reinterpret_cast<T *>(smem_raw);
@@ -175,28 +180,31 @@ __device__ __forceinline__ bool stage_tile_h(const StageParams<T> &p, const CUte
         fence_proxy_async();
     }
 
-    // slot cells this thread copies (cp.async path) and converts
+    // slot cell pairs (sx even, so a pair is one aligned 2-element vector)
+    // this thread copies (cp.async path) and converts
     int soff[MAXC];
-    unsigned goff[MAXC];
+    unsigned goff[MAXC], goff1[MAXC];
     int nc = 0;
 #pragma unroll
     for (int q = 0; q < MAXC; q++) {
         const int c = tid + q * NTHR;
         soff[q] = 0;
-        goff[q] = 0;
-        if (c < NCELL) {
+        goff[q] = goff1[q] = 0;
+        if (c < NPAIR) {
             int sy, sx;
-            if (c < TY * (TX + 4)) {
-                sy = 2 + c / (TX + 4);
-                sx = 2 + c % (TX + 4);
+            if (c < TY * PR) {
+                sy = 2 + c / PR;
+                sx = 2 + 2 * (c % PR);
             } else {
-                const int c2 = c - TY * (TX + 4);
-                const int r = c2 / TX;
-                sx = 4 + c2 % TX;
+                const int c2 = c - TY * PR;
+                const int r = c2 / PH;
+                sx = 4 + 2 * (c2 % PH);
                 sy = r < 2 ? r : TY + r;
             }
             soff[q] = sy * SX + sx;
-            goff[q] = (unsigned)(wrap_index(j0 + sy - 2, ny) * nx + wrap_index(i0 + sx - 4, nx));
+            const int gj = wrap_index(j0 + sy - 2, ny) * nx;
+            goff[q] = (unsigned)(gj + wrap_index(i0 + sx - 4, nx));
+            goff1[q] = (unsigned)(gj + wrap_index(i0 + sx - 3, nx));
             nc = q + 1;
         }
     }
@@ -214,10 +222,12 @@ __device__ __forceinline__ bool stage_tile_h(const StageParams<T> &p, const CUte
                 if (tid == 0) {
                     uint64_t *bar = &bars[t % D];
                     T *dst = slot(t);
-                    mbar_expect_tx(bar, S::TX_BYTES);
                     if (pad_in) {
-                        tma_load_4d(dst, tmap, i0, j0, lev, 0, bar);
+                        // phi only: the map covers fields 1 .. NF-1
+                        mbar_expect_tx(bar, S::TX_BYTES_PHI);
+                        tma_load_4d(dst + FE, tmap, i0, j0, lev, 0, bar);
                     } else {
+                        mbar_expect_tx(bar, S::TX_BYTES);
                         tma_load_3d(dst, &p.umap[0], i0 - 4, j0 - 2, lev, bar);
                         tma_load_3d(dst + FE, &p.umap[1], i0 - 4, j0 - 2, lev, bar);
                         if (NF > 2) tma_load_4d(dst + 2 * FE, &p.umap[2], i0 - 4, j0 - 2, lev, 0, bar);
@@ -232,7 +242,10 @@ __device__ __forceinline__ bool stage_tile_h(const StageParams<T> &p, const CUte
                 for (int q = 0; q < MAXC; q++) {
                     if (q < nc) {
 #pragma unroll
-                        for (int f = 0; f < NF; f++) cp_async<sizeof(T)>(sl + f * FE + soff[q], p.yin[f] + lb + goff[q]);
+                        for (int f = 0; f < NF; f++) {
+                            cp_async<sizeof(T)>(sl + f * FE + soff[q], p.yin[f] + lb + goff[q]);
+                            cp_async<sizeof(T)>(sl + f * FE + soff[q] + 1, p.yin[f] + lb + goff1[q]);
+                        }
                     }
                 }
             }
@@ -240,15 +253,27 @@ __device__ __forceinline__ bool stage_tile_h(const StageParams<T> &p, const CUte
         }
     };
 
-    // convert the cells this thread owns in the slot of level lev from rho*phi to phi
+    // convert the cell pairs this thread owns in the slot of level lev from
+    // rho*phi to phi (one reciprocal of rho per cell, one vector multiply per field)
     auto convert = [&](int lev) {
         T *sl = slot(lev);
 #pragma unroll
         for (int q = 0; q < MAXC; q++) {
             if (q < nc) {
-                const T r = recip(sl[soff[q]]);
+                const T2 rho = *reinterpret_cast<const T2 *>(sl + soff[q]);
+                const T r0 = recip(rho.x), r1 = recip(rho.y);
 #pragma unroll
-                for (int f = 1; f < NF; f++) sl[f * FE + soff[q]] *= r;
+                for (int f = 1; f < NF; f++) {
+                    T2 *v = reinterpret_cast<T2 *>(sl + f * FE + soff[q]);
+                    T2 w = *v;
+                    if constexpr (std::is_same<T, float>::value) {
+                        w = __fmul2_rn(w, make_float2(r0, r1));
+                    } else {
+                        w.x *= r0;
+                        w.y *= r1;
+                    }
+                    *v = w;
+                }
             }
         }
     };
@@ -664,15 +689,20 @@ template <typename T>
 cudaError_t encode_stage_map(CUtensorMap *map, void *base, int nf, int nx, int ny, int nz, int ty) {
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (!enc) return cudaErrorNotSupported;
+    if (nf < 2) return cudaErrorInvalidValue;
     using S = StageShape<T, 2>;   // SX does not depend on the field count or the tile height
     const long long P = padded_pitch(nx);
-    const cuuint64_t dims[4] = {(cuuint64_t)P, (cuuint64_t)(ny + 4), (cuuint64_t)nz, (cuuint64_t)nf};
+    // the map covers the phi fields 1 .. nf-1 (the stage kernel never reads the
+    // density of a padded buffer; field 0 stays in the buffer for the adjoint)
+    const long long fe = P * (ny + 4) * (long long)nz;
+    void *phi = static_cast<T *>(base) + fe;
+    const cuuint64_t dims[4] = {(cuuint64_t)P, (cuuint64_t)(ny + 4), (cuuint64_t)nz, (cuuint64_t)(nf - 1)};
     const cuuint64_t strides[3] = {(cuuint64_t)(P * sizeof(T)), (cuuint64_t)(P * (ny + 4) * sizeof(T)),
-                                   (cuuint64_t)(P * (ny + 4) * (long long)nz * sizeof(T))};
-    const cuuint32_t box[4] = {(cuuint32_t)S::SX, (cuuint32_t)(ty + 4), 1u, (cuuint32_t)nf};
+                                   (cuuint64_t)(fe * sizeof(T))};
+    const cuuint32_t box[4] = {(cuuint32_t)S::SX, (cuuint32_t)(ty + 4), 1u, (cuuint32_t)(nf - 1)};
     const cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
     CUresult r = enc(map, sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4,
-                     base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                     phi, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
