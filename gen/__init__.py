@@ -7,5 +7,6 @@ and the time step length that both implementations take as inputs.
 from .fields import (  # noqa: F401
     CONFIGS, SEED_BASE, Case, make_dz, make_case, make_config_case,
     make_ensemble_cases, ensemble_sizes, DAMPING, make_boundary_data,
-    ACOUSTIC, make_acoustic_state,
+    ACOUSTIC, make_acoustic_state, halo_periodic, halo_strips, extend_fluxes, split_extent,
+    subdomain, make_open_boundary,
 )

@@ -355,3 +355,89 @@ def make_acoustic_state(case: Case, *, dtype=np.float64):
     cast = (lambda a: np.ascontiguousarray(a, dtype=dtype))
     return (cast(0.05 * np.asarray(case.mu)), cast(0.05 * np.asarray(case.mv)), cast(0.05 * np.asarray(case.mw)),
             cast(S), rho0c, rho0f)
+
+
+# ---------------------------------------------------------------- open lateral boundaries
+#
+# Halo layout of the ghost cells of an open domain (limited-area or one block
+# of a decomposed domain): four strips one after another,
+#   W: i = c - 2,  E: i = nx + c  (c = 0, 1; every j), each [T][nz][2][ny]
+#   S: j = c - 2,  N: j = ny + c  (c = 0, 1; every i), each [T][nz][2][nx]
+# for T fields.  Face mass fluxes of an open domain: mu_x [nz][ny][nx+1] and
+# mv_x [nz][ny+1][nx], index i (j) holding face i-1/2 (j-1/2).
+
+def halo_periodic(fields: np.ndarray) -> np.ndarray:
+    """The halo-layout ghosts of [T][nz][ny][nx] values continued periodically."""
+    f = np.asarray(fields)
+    nx, ny = f.shape[3], f.shape[2]
+    w = np.stack([f[..., :, nx - 2], f[..., :, nx - 1]], axis=2)      # [T][nz][2][ny]
+    e = np.stack([f[..., :, 0], f[..., :, 1]], axis=2)
+    s = np.stack([f[..., ny - 2, :], f[..., ny - 1, :]], axis=2)      # [T][nz][2][nx]
+    n = np.stack([f[..., 0, :], f[..., 1, :]], axis=2)
+    return np.concatenate([a.reshape(-1) for a in (w, e, s, n)])
+
+
+def halo_strips(halo: np.ndarray, T: int, nz: int, ny: int, nx: int):
+    """(W, E, S, N) views of a halo-layout array: [T][nz][2][ny] twice, then [T][nz][2][nx] twice."""
+    sw, ss = T * nz * 2 * ny, T * nz * 2 * nx
+    h = np.asarray(halo).reshape(-1)
+    return (h[:sw].reshape(T, nz, 2, ny), h[sw:2 * sw].reshape(T, nz, 2, ny),
+            h[2 * sw:2 * sw + ss].reshape(T, nz, 2, nx), h[2 * sw + ss:].reshape(T, nz, 2, nx))
+
+
+def extend_fluxes(mu: np.ndarray, mv: np.ndarray):
+    """Open-domain face fluxes (mu_x, mv_x) of periodic ones: face -1/2 is face nx-1/2."""
+    mu_x = np.concatenate([mu[:, :, -1:], mu], axis=2)
+    mv_x = np.concatenate([mv[:, -1:, :], mv], axis=1)
+    return np.ascontiguousarray(mu_x), np.ascontiguousarray(mv_x)
+
+
+def split_extent(n: int, parts: int) -> list[tuple[int, int]]:
+    """[start, stop) of each of `parts` blocks of n cells, sizes differing by at most 1."""
+    if parts < 1 or parts > n:
+        raise ValueError("bad block count")
+    base, extra = divmod(n, parts)
+    out, s = [], 0
+    for p in range(parts):
+        e = s + base + (1 if p < extra else 0)
+        out.append((s, e))
+        s = e
+    return out
+
+
+def subdomain(case: Case, px: int, py: int, rx: int, ry: int) -> dict:
+    """Block (rx, ry) of a px x py decomposition of a periodic case: its state
+    [F][nz][h][w], its open-domain face fluxes (the faces on its low edges
+    taken from the neighbouring block, periodically) and mw."""
+    (i0, i1), (j0, j1) = split_extent(case.nx, px)[rx], split_extent(case.ny, py)[ry]
+    Y = case.state()[:, :, j0:j1, i0:i1]
+    ii = np.arange(i0 - 1, i1) % case.nx
+    jj = np.arange(j0 - 1, j1) % case.ny
+    mu_x = case.mu[:, j0:j1, :][:, :, ii]
+    mv_x = case.mv[:, :, i0:i1][:, jj, :]
+    mw = case.mw[:, j0:j1, i0:i1]
+    c = lambda a: np.ascontiguousarray(a)
+    return dict(i0=i0, i1=i1, j0=j0, j1=j1, nx=i1 - i0, ny=j1 - j0, Y=c(Y), mu_x=c(mu_x), mv_x=c(mv_x),
+                mw=c(mw))
+
+
+def make_open_boundary(case: Case, seed: int, *, dtype=np.float64):
+    """Two boundary datasets of a limited-area domain in the halo layout, for
+    the F-1 transported quantities (theta and the mixing ratios): the case's
+    own values continued periodically past its edges (so that the boundary
+    joins the interior smoothly), with 1% noise, the second one shifted by
+    one cell in i and with fresh noise (a later time of the outer model)."""
+    rng = np.random.default_rng(seed)
+    phi = case.state()[1:] / case.state()[0][None]
+    h0 = halo_periodic(phi)
+    h1 = halo_periodic(np.roll(phi, 1, axis=3))
+    scale = np.abs(phi).reshape(phi.shape[0], -1).max(axis=1)
+    T = phi.shape[0]
+
+    def noisy(h):
+        out = []
+        for a in halo_strips(h, T, case.nz, case.ny, case.nx):
+            out.append((a + 0.01 * scale[:, None, None, None] * rng.standard_normal(a.shape)).reshape(-1))
+        return np.concatenate(out)
+
+    return np.ascontiguousarray(noisy(h0), dtype=dtype), np.ascontiguousarray(noisy(h1), dtype=dtype)

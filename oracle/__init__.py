@@ -79,6 +79,8 @@ def lib():
             [ctypes.c_double] * 3 + [ctypes.c_int, _D, _D, _D, _D]
         L.orc_damping.argtypes = [ctypes.c_int] * 6 + [ctypes.c_double] * 5 + [ctypes.c_longlong,
                                   ctypes.POINTER(ctypes.c_int), _D, _D, _D, _D]
+        L.orc_rhs_open.argtypes = [G, _D, _D, _D, _D, _D, _D, _D]
+        L.orc_step_open.argtypes = [G, _D, _D, _D, _D, _D, _D, ctypes.c_double, ctypes.c_int, _D]
         L.orc_set_threads.argtypes = [ctypes.c_int]
         L.orc_get_threads.restype = ctypes.c_int
         _lib = L
@@ -239,6 +241,34 @@ def step(g: Grid, Y, mu, mv, mw, dt, nsteps, tend=None):
     tend = None if tend is None else _f64(tend)
     bud = np.empty(g.F + 1)
     lib().orc_step(g.ref, _p(Y), _p(mu), _p(mv), _p(mw), _p(tend), dt, nsteps, _p(bud))
+    return Y, bud
+
+
+def halo_size(g: Grid) -> int:
+    """values of one halo-layout array: 2 (2 ny + 2 nx) nz (F - 1)"""
+    return 2 * (2 * g.ny + 2 * g.nx) * g.nz * (g.F - 1)
+
+
+def rhs_open(g: Grid, Y, mu_x, mv_x, mw, ghost, tend=None):
+    """R of an open domain (ghost phi in the halo layout, extended face fluxes)."""
+    Y, mu_x, mv_x, mw, ghost = map(_f64, (Y, mu_x, mv_x, mw, ghost))
+    assert mu_x.shape == (g.nz, g.ny, g.nx + 1) and mv_x.shape == (g.nz, g.ny + 1, g.nx)
+    assert ghost.size == halo_size(g)
+    tend = None if tend is None else _f64(tend)
+    R = np.empty(g.shape)
+    lib().orc_rhs_open(g.ref, _p(Y), _p(mu_x), _p(mv_x), _p(mw), _p(tend), _p(ghost), _p(R))
+    return R
+
+
+def step_open(g: Grid, Y, mu_x, mv_x, mw, ghost, dt, nsteps, tend=None):
+    """nsteps steps of an open domain; returns (Y, budgets[F+1])."""
+    Y = _f64(Y).copy()
+    mu_x, mv_x, mw, ghost = map(_f64, (mu_x, mv_x, mw, ghost))
+    assert mu_x.shape == (g.nz, g.ny, g.nx + 1) and mv_x.shape == (g.nz, g.ny + 1, g.nx)
+    assert ghost.size == halo_size(g)
+    tend = None if tend is None else _f64(tend)
+    bud = np.empty(g.F + 1)
+    lib().orc_step_open(g.ref, _p(Y), _p(mu_x), _p(mv_x), _p(mw), _p(tend), _p(ghost), dt, nsteps, _p(bud))
     return Y, bud
 
 

@@ -991,6 +991,128 @@ void orc_trajectory_branches(const orc_grid *g, const double *Y0, const double *
     free(Y); free(S); free(R);
 }
 
+/* ---- open (non-periodic) lateral boundaries -------------------------------
+ * A domain whose edge cells have no periodic neighbours: a limited-area
+ * domain fed by boundary data (the boundary datasets of the damping kernel,
+ * Sec. 2.1), or one block of a horizontally decomposed domain (Sec. 1.1:
+ * horizontal blocks exchanging halos).  The lateral neighbours outside the
+ * domain are two ghost columns (rows) per side whose phi values, for fields
+ * 1 .. F-1, are given in the halo layout: four strips one after another,
+ *   W: phi at i = c - 2,   E: phi at i = nx + c   (c = 0, 1; every j)
+ *   S: phi at j = c - 2,   N: phi at j = ny + c   (c = 0, 1; every i)
+ * each [F-1][nz][2][len], len = ny for W and E, nx for S and N.  The
+ * density needs no ghost: its flux is M itself.  Every face of the domain,
+ * the outer ones included, has its own mass flux:
+ *   mu_x[k][j][i], i = 0 .. nx: face i - 1/2 of cell i  ([nz][ny][nx+1]);
+ *   mv_x[k][j][i], j = 0 .. ny: face j - 1/2 of cell j  ([nz][ny+1][nx]);
+ *   mw as in the periodic domain.
+ * The faces are the periodic domain's Koren reconstruction, reading a ghost
+ * wherever the four-cell stencil leaves the domain; the ghosts are held for
+ * the whole call.  Vertical faces are unchanged. */
+
+static size_t halo_index(const orc_grid *g, int strip, int f1, int k, int c, int pos) {
+    const size_t T = (size_t)(1 + g->ntr), nz = (size_t)g->nz;
+    const size_t sw = T * nz * 2 * (size_t)g->ny, ss = T * nz * 2 * (size_t)g->nx;
+    const size_t base = strip == 0 ? 0 : (strip == 1 ? sw : (strip == 2 ? 2 * sw : 2 * sw + ss));
+    const size_t len = strip < 2 ? (size_t)g->ny : (size_t)g->nx;
+    return base + (((size_t)f1 * nz + k) * 2 + c) * len + pos;
+}
+
+/* phi of field f >= 1 at (k, j, i), i in [-2, nx+1] or j in [-2, ny+1] (not both outside) */
+static double phi_open(const orc_grid *g, const double *Y, const double *ghost, int f, int k, int j, int i) {
+    if (i < 0) return ghost[halo_index(g, 0, f - 1, k, i + 2, j)];
+    if (i >= g->nx) return ghost[halo_index(g, 1, f - 1, k, i - g->nx, j)];
+    if (j < 0) return ghost[halo_index(g, 2, f - 1, k, j + 2, i)];
+    if (j >= g->ny) return ghost[halo_index(g, 3, f - 1, k, j - g->ny, i)];
+    const size_t C = (size_t)g->nz * g->ny * g->nx, o = ((size_t)k * g->ny + j) * g->nx + i;
+    return Y[(size_t)f * C + o] / Y[o];
+}
+
+/* flux through face i+1/2 (dir 0, i = -1 .. nx-1), j+1/2 (dir 1, j = -1 .. ny-1)
+ * or k+1/2 (dir 2) of cell (i, j, k) */
+static double flux_open(const orc_grid *g, const double *Y, const double *ghost, const double *mu_x,
+                        const double *mv_x, const double *mw, int f, int dir, int k, int j, int i) {
+    const int nx = g->nx, ny = g->ny, nz = g->nz;
+    double m;
+    if (dir == 0) {
+        m = mu_x[((size_t)k * ny + j) * (nx + 1) + (i + 1)];
+        if (f == 0) return m;
+        return m * orc_face(phi_open(g, Y, ghost, f, k, j, i - 1), phi_open(g, Y, ghost, f, k, j, i),
+                            phi_open(g, Y, ghost, f, k, j, i + 1), phi_open(g, Y, ghost, f, k, j, i + 2),
+                            m, g->lim, NULL);
+    } else if (dir == 1) {
+        m = mv_x[((size_t)k * (ny + 1) + (j + 1)) * nx + i];
+        if (f == 0) return m;
+        return m * orc_face(phi_open(g, Y, ghost, f, k, j - 1, i), phi_open(g, Y, ghost, f, k, j, i),
+                            phi_open(g, Y, ghost, f, k, j + 1, i), phi_open(g, Y, ghost, f, k, j + 2, i),
+                            m, g->lim, NULL);
+    }
+    if (k < 0 || k >= nz - 1) return 0.0;    /* rigid lids: no flux */
+    m = mw[((size_t)(k + 1) * ny + j) * nx + i];
+    if (f == 0) return m;
+    const int km1 = k - 1 < 0 ? 0 : k - 1, kp2 = k + 2 > nz - 1 ? nz - 1 : k + 2;
+    return m * orc_face(phi_open(g, Y, ghost, f, km1, j, i), phi_open(g, Y, ghost, f, k, j, i),
+                        phi_open(g, Y, ghost, f, k + 1, j, i), phi_open(g, Y, ghost, f, kp2, j, i),
+                        m, g->lim, NULL);
+}
+
+void orc_rhs_open(const orc_grid *g, const double *Y, const double *mu_x, const double *mv_x,
+                  const double *mw, const double *tend, const double *ghost, double *R) {
+    const int F = 2 + g->ntr, nz = g->nz, ny = g->ny, nx = g->nx;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
+    for (int j = 0; j < ny; j++)
+        for (int f = 0; f < F; f++)
+            for (int k = 0; k < nz; k++)
+                for (int i = 0; i < nx; i++) {
+                    double xp = flux_open(g, Y, ghost, mu_x, mv_x, mw, f, 0, k, j, i);
+                    double xm = flux_open(g, Y, ghost, mu_x, mv_x, mw, f, 0, k, j, i - 1);
+                    double yp = flux_open(g, Y, ghost, mu_x, mv_x, mw, f, 1, k, j, i);
+                    double ym = flux_open(g, Y, ghost, mu_x, mv_x, mw, f, 1, k, j - 1, i);
+                    double zp = flux_open(g, Y, ghost, mu_x, mv_x, mw, f, 2, k, j, i);
+                    double zm = flux_open(g, Y, ghost, mu_x, mv_x, mw, f, 2, k - 1, j, i);
+                    double r = -((xp - xm) / g->dx + (yp - ym) / g->dy + (zp - zm) / g->dz[k]);
+                    const size_t o = (((size_t)f * nz + k) * ny + j) * nx + i;
+                    if (tend && f > 0) r += tend[o - (size_t)nz * ny * nx];
+                    R[o] = r;
+                }
+}
+
+/* nsteps steps of the open domain: the three RK stages with the ghosts held,
+ * then the column pass and, if budgets is set, the budgets as orc_step
+ * (the mass budget then changes by the mass that crossed the outer faces). */
+void orc_step_open(const orc_grid *g, double *Y, const double *mu_x, const double *mv_x, const double *mw,
+                   const double *tend, const double *ghost, double dt, int nsteps, double *budgets) {
+    const size_t n = (size_t)(2 + g->ntr) * g->nz * g->ny * g->nx;
+    double *Yn = (double *)malloc(n * sizeof(double));
+    double *Ys = (double *)malloc(n * sizeof(double));
+    double *R = (double *)malloc(n * sizeof(double));
+    double *pc = (double *)calloc((size_t)g->ny * g->nx, sizeof(double));
+    const double c[3] = {dt / 3.0, dt / 2.0, dt};
+    for (int s = 0; s < nsteps; s++) {
+        memcpy(Yn, Y, n * sizeof(double));
+        const double *in = Yn;
+        for (int q = 0; q < 3; q++) {
+            orc_rhs_open(g, in, mu_x, mv_x, mw, tend, ghost, R);
+            double *dst = q == 2 ? Y : Ys;
+            for (size_t e = 0; e < n; e++) dst[e] = Yn[e] + c[q] * R[e];
+            in = Ys;
+        }
+        orc_column(g, Y, dt, pc);
+    }
+    if (budgets) {
+        csum tot = {0.0, 0.0};
+        for (int j = 0; j < g->ny; j++)
+            for (int i = 0; i < g->nx; i++) csum_add(&tot, pc[(size_t)j * g->nx + i]);
+        orc_budgets(g, Y, csum_value(&tot), budgets);
+    }
+    free(Yn);
+    free(Ys);
+    free(R);
+    free(pc);
+}
+
 /* ---- 7-point diffusion stencil (Sec. 4, reduced weather application) ---------
  * The paper names the kernel but prints no formula; the reading is the
  * textbook explicit diffusion step with one diffusion number c for all three

@@ -76,6 +76,17 @@ void orc_step_adj_br(const orc_grid *g, const double *Y0, const double *mu, cons
 void orc_trajectory_branches(const orc_grid *g, const double *Y0, const double *mu,
                              const double *mv, const double *mw, const double *tend, double dt,
                              int nsteps, unsigned char *out);
+/* Open (non-periodic) lateral boundaries: a limited-area domain or one block
+ * of a decomposed domain.  ghost holds phi (fields 1..F-1) of the two ghost
+ * columns/rows per side in the halo layout (strips W: i = c-2, E: i = nx+c,
+ * S: j = c-2, N: j = ny+c, c = 0, 1; each [F-1][nz][2][len], len = ny, ny,
+ * nx, nx); mu_x [nz][ny][nx+1] and mv_x [nz][ny+1][nx] hold the mass flux of
+ * every face, index i (j) being face i-1/2 (j-1/2).  The ghosts are held for
+ * the call. */
+void orc_rhs_open(const orc_grid *g, const double *Y, const double *mu_x, const double *mv_x,
+                  const double *mw, const double *tend, const double *ghost, double *R);
+void orc_step_open(const orc_grid *g, double *Y, const double *mu_x, const double *mv_x, const double *mw,
+                   const double *tend, const double *ghost, double dt, int nsteps, double *budgets);
 /* One explicit step of 7-point diffusion (the reduced weather application's
  * kernel, Sec. 4): out = in + c (sum of the six neighbours - 6 in), periodic in
  * i and j, zero flux through both lids (ghost levels copy the boundary cell);
