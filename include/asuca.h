@@ -397,6 +397,72 @@ asuca_status asuca_acoustic_steps(asuca_grid *grid, void *U, void *V, void *W, v
                                   const asuca_acoustic_desc *desc, double dtau, int nshort, void *workspace,
                                   size_t workspace_bytes, void *cuda_stream);
 
+/* ---- open lateral boundaries: limited-area domains, decomposed domains --
+ * The periodic step's lateral wrap replaced by ghost cells: the edge cells'
+ * lateral neighbours are two ghost columns (rows) per side, written from
+ * outside the stage kernels, either from boundary data (a limited-area
+ * domain: the boundary datasets of the damping kernel, Sec. 2.1 "Parallel
+ * Loop Abstraction") or by a halo exchange between the blocks of a
+ * horizontally decomposed domain (Sec. 1.1 "ASUCA on GPU": horizontal blocks
+ * with halo communication; Sec. 2.2 "Device Data Region": halo updates every
+ * time step).  The face reconstruction is the periodic step's, reading a ghost
+ * wherever its four-cell stencil leaves the domain; the density needs no
+ * ghost (its flux is M).  The stencil is a cross, so the ghost corners are
+ * never read.
+ *   - state: the block's or domain's fields as for asuca_step, but mu and mv
+ *     are the open domain's face fluxes: mu [nz][ny][nx+1], entry i the face
+ *     i-1/2 of cell i (i = nx: the east face of the last cell); mv
+ *     [nz][ny+1][nx], entry j the face j-1/2; mw as for asuca_step.
+ *   - Halo layout (received strips, boundary data, send buffers): four
+ *     strips one after another, W and E ([F-1][nz][2][ny] each), then S and
+ *     N ([F-1][nz][2][nx] each), for the F-1 quantities phi = rho phi / rho
+ *     (theta, then the mixing ratios).  As ghosts, strip W holds the cells
+ *     i = c-2, E i = nx+c, S j = c-2, N j = ny+c (c = 0, 1); as packed by
+ *     asuca_halo_pack, strip W holds the block's cells i = c, E i = nx-2+c,
+ *     S j = c, N j = ny-2+c, so a block's received W strip is its west
+ *     neighbour's packed E strip, and so on.  asuca_halo_count gives the
+ *     values of one such array, 2 (2 nx + 2 ny) nz (F-1).
+ *   - workspace: asuca_open_workspace_bytes(grid) bytes, 256-byte aligned,
+ *     else ASUCA_ERR_WORKSPACE; it holds the three padded stage inputs
+ *     (buffer 0: phi^n, 1: phi*, 2: phi**), whose ghosts the calls below
+ *     fill and read.  Halo and boundary arrays are caller-owned device arrays
+ *     in the grid's precision.
+ *   - One step is: asuca_open_prepare (buffer 0 from the state); fill buffer
+ *     0's ghosts; asuca_open_stage 0; fill buffer 1's ghosts; stage 1; fill
+ *     buffer 2's ghosts; stage 2 (the third stage, the column pass and, if
+ *     budgets_dev is set, this block's budgets as for asuca_step, the
+ *     precipitation summed since the last prepare with first_of_call set).
+ *     Ghosts are filled with asuca_halo_unpack, from received strips (a
+ *     decomposed domain: pack, exchange, unpack) or from boundary data.
+ *     asuca_step_open runs whole steps of a limited-area domain, the
+ *     boundary data held for the call.
+ *   - Asynchronous on the stream; null pointers, a stage or buffer outside
+ *     0..2, or a non-finite dt or tratio give ASUCA_ERR_ARG; a grid whose
+ *     open face-flux arrays do not fit 32-bit offsets ASUCA_ERR_UNSUPPORTED. */
+size_t asuca_open_workspace_bytes(const asuca_grid *grid);
+size_t asuca_halo_count(const asuca_grid *grid);
+/* buffer 0's interior = phi of the state; first_of_call != 0 also restarts
+ * the precipitation sum of the budgets */
+asuca_status asuca_open_prepare(asuca_grid *grid, const asuca_state *state, int first_of_call, void *workspace,
+                                size_t workspace_bytes, void *cuda_stream);
+/* RK stage `stage` (0, 1, 2: weights dt/3, dt/2, dt) from buffer `stage`
+ * (ghosts filled); stages 0 and 1 write the interior of buffer stage+1,
+ * stage 2 writes the state and runs the column pass */
+asuca_status asuca_open_stage(asuca_grid *grid, asuca_state *state, const void *tendencies, double dt, int stage,
+                              void *workspace, size_t workspace_bytes, double *budgets_dev, void *cuda_stream);
+/* send: halo-layout array filled with the block's edge strips of buffer `buffer` */
+asuca_status asuca_halo_pack(asuca_grid *grid, const void *workspace, size_t workspace_bytes, int buffer,
+                             void *send, void *cuda_stream);
+/* ghosts of buffer `buffer` = recv (bnd1 NULL), else (1 - tratio) recv + tratio bnd1 (two
+ * boundary datasets interpolated in time) */
+asuca_status asuca_halo_unpack(asuca_grid *grid, void *workspace, size_t workspace_bytes, int buffer,
+                               const void *recv, const void *bnd1, double tratio, void *cuda_stream);
+/* nsteps steps of a limited-area domain whose ghosts are (1 - tratio) bnd0 + tratio bnd1
+ * (bnd1 may be NULL: bnd0 alone) in every stage */
+asuca_status asuca_step_open(asuca_grid *grid, asuca_state *state, const void *tendencies, double dt, int nsteps,
+                             const void *bnd0, const void *bnd1, double tratio, void *workspace,
+                             size_t workspace_bytes, double *budgets_dev, void *cuda_stream);
+
 /* ---- per-kernel timing ------------------------------------------------- */
 
 typedef enum {

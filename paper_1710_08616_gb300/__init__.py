@@ -109,6 +109,16 @@ SIGNATURES = {
     "asuca_set_tuning": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int]),
     "asuca_get_tuning": (ctypes.c_int, [_VP, ctypes.c_int]),
     "asuca_debug_dataflow_order": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _VP]),
+    "asuca_open_workspace_bytes": (ctypes.c_size_t, [_VP]),
+    "asuca_halo_count": (ctypes.c_size_t, [_VP]),
+    "asuca_open_prepare": (ctypes.c_int, [_VP, ctypes.POINTER(StateStruct), ctypes.c_int, _VP, ctypes.c_size_t,
+                                          _VP]),
+    "asuca_open_stage": (ctypes.c_int, [_VP, ctypes.POINTER(StateStruct), _VP, ctypes.c_double, ctypes.c_int, _VP,
+                                        ctypes.c_size_t, _VP, _VP]),
+    "asuca_halo_pack": (ctypes.c_int, [_VP, _VP, ctypes.c_size_t, ctypes.c_int, _VP, _VP]),
+    "asuca_halo_unpack": (ctypes.c_int, [_VP, _VP, ctypes.c_size_t, ctypes.c_int, _VP, _VP, ctypes.c_double, _VP]),
+    "asuca_step_open": (ctypes.c_int, [_VP, ctypes.POINTER(StateStruct), _VP, ctypes.c_double, ctypes.c_int, _VP,
+                                       _VP, ctypes.c_double, _VP, ctypes.c_size_t, _VP, _VP]),
     "asuca_profile_enable": (ctypes.c_int, [_VP, ctypes.c_int]),
     "asuca_profile_read": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
@@ -268,6 +278,94 @@ def step(grid: Grid, state: State, dt: float, nsteps: int, *, tendencies=None, w
     _check(lib().asuca_step(grid.handle, ctypes.byref(s), _ptr(tendencies), float(dt), int(nsteps),
                             _ptr(workspace), workspace.numel() * workspace.element_size(),
                             _ptr(budgets), _stream_ptr(stream)), "asuca_step")
+    return budgets
+
+
+# ---------------------------------------------------------------- open lateral boundaries
+
+def _check_open_state(grid: Grid, st: State):
+    """Fields as for step; mu, mv are the open domain's face fluxes
+    [nz][ny][nx+1] and [nz][ny+1][nx] (entry i, j: face i-1/2, j-1/2)."""
+    dt = grid.torch_dtype
+    nz, ny, nx, N = grid.nz, grid.ny, grid.nx, grid.ntracers
+    for name, shape in (("rho", (nz, ny, nx)), ("rhotheta", (nz, ny, nx)), ("rhoq", (N, nz, ny, nx)),
+                        ("mu", (nz, ny, nx + 1)), ("mv", (nz, ny + 1, nx)), ("mw", (nz + 1, ny, nx))):
+        t = getattr(st, name)
+        if tuple(t.shape) != shape or t.dtype != dt or not t.is_contiguous() or not t.is_cuda:
+            raise ValueError(f"open state.{name}: need contiguous CUDA {dt} of shape {shape}, "
+                             f"got {t.dtype} {tuple(t.shape)}")
+
+
+def _check_halo(grid: Grid, t, what):
+    n = halo_count(grid)
+    if t is None or t.numel() != n or t.dtype != grid.torch_dtype or not t.is_contiguous() or not t.is_cuda:
+        raise ValueError(f"{what}: need a contiguous CUDA {grid.torch_dtype} halo array of {n} values")
+
+
+def open_workspace_bytes(grid: Grid) -> int:
+    return int(lib().asuca_open_workspace_bytes(grid.handle))
+
+
+def open_workspace(grid: Grid, device="cuda"):
+    import torch
+    return torch.empty(open_workspace_bytes(grid), dtype=torch.uint8, device=device)
+
+
+def halo_count(grid: Grid) -> int:
+    """values of one halo-layout array: 2 (2 nx + 2 ny) nz (F - 1)"""
+    return int(lib().asuca_halo_count(grid.handle))
+
+
+def open_prepare(grid: Grid, state: State, workspace, *, first: bool = True, stream=None):
+    """Buffer 0's interior = phi of the state (asuca_open_prepare)."""
+    _check_open_state(grid, state)
+    s = state.struct()
+    _check(lib().asuca_open_prepare(grid.handle, ctypes.byref(s), int(bool(first)), _ptr(workspace),
+                                    workspace.numel(), _stream_ptr(stream)), "asuca_open_prepare")
+
+
+def open_stage(grid: Grid, state: State, dt: float, stage: int, workspace, *, tendencies=None, budgets=None,
+               stream=None):
+    """RK stage 0, 1 or 2 of an open domain (asuca_open_stage); stage 2 runs the column pass."""
+    _check_open_state(grid, state)
+    s = state.struct()
+    _check(lib().asuca_open_stage(grid.handle, ctypes.byref(s), _ptr(tendencies), float(dt), int(stage),
+                                  _ptr(workspace), workspace.numel(), _ptr(budgets), _stream_ptr(stream)),
+           "asuca_open_stage")
+    return budgets
+
+
+def halo_pack(grid: Grid, workspace, buffer: int, send, *, stream=None):
+    _check_halo(grid, send, "send")
+    _check(lib().asuca_halo_pack(grid.handle, _ptr(workspace), workspace.numel(), int(buffer), _ptr(send),
+                                 _stream_ptr(stream)), "asuca_halo_pack")
+
+
+def halo_unpack(grid: Grid, workspace, buffer: int, recv, *, bnd1=None, tratio: float = 0.0, stream=None):
+    _check_halo(grid, recv, "recv")
+    if bnd1 is not None:
+        _check_halo(grid, bnd1, "bnd1")
+    _check(lib().asuca_halo_unpack(grid.handle, _ptr(workspace), workspace.numel(), int(buffer), _ptr(recv),
+                                   _ptr(bnd1), float(tratio), _stream_ptr(stream)), "asuca_halo_unpack")
+
+
+def step_open(grid: Grid, state: State, dt: float, nsteps: int, bnd0, *, bnd1=None, tratio: float = 0.0,
+              tendencies=None, workspace=None, budgets=None, stream=None):
+    """nsteps steps of a limited-area domain (asuca_step_open): the ghosts of every
+    stage are (1 - tratio) bnd0 + tratio bnd1 (bnd0 alone without bnd1)."""
+    import torch
+    _check_open_state(grid, state)
+    _check_halo(grid, bnd0, "bnd0")
+    if bnd1 is not None:
+        _check_halo(grid, bnd1, "bnd1")
+    if workspace is None:
+        workspace = open_workspace(grid, device=state.rho.device)
+    if budgets is True:
+        budgets = torch.empty(grid.nfields + 1, dtype=torch.float64, device=state.rho.device)
+    s = state.struct()
+    _check(lib().asuca_step_open(grid.handle, ctypes.byref(s), _ptr(tendencies), float(dt), int(nsteps),
+                                 _ptr(bnd0), _ptr(bnd1), float(tratio), _ptr(workspace), workspace.numel(),
+                                 _ptr(budgets), _stream_ptr(stream)), "asuca_step_open")
     return budgets
 
 

@@ -16,6 +16,7 @@
 #include "damping.cuh"
 #include "acoustic.cuh"
 #include "common.cuh"
+#include "open.cuh"
 
 using namespace asuca;
 
@@ -46,6 +47,10 @@ struct asuca_grid {
     const void *umap_key[3];      // caller fields the cached user maps describe (rho, rho theta, rho q)
     int umap_ty, umap_ok;
     CUtensorMap umap[3];
+    // TMA descriptors of the open domain's three padded stage inputs, for the workspace they were made for
+    void *omap_ws;
+    int omap_ty;
+    CUtensorMap omap[3];
     // opt-in per-kernel timing: events recorded around every launch
     bool prof_on;
     cudaEvent_t *prof_ev;
@@ -182,6 +187,7 @@ StageParams<T> stage_params(const asuca_grid *g, const asuca_state *fl, const vo
     p.nz = g->d.nz;
     p.lim = (int)g->d.lim;
     p.plane = g->plane;
+    p.plane_u = p.plane_v = g->plane;
     p.status = g->status_dev;
     p.ty = g->stage_ty;
     p.opitch = padded_pitch(g->d.nx);
@@ -1027,6 +1033,158 @@ asuca_status ens_enqueue(asuca_grid *const *grids, asuca_state *states, const do
     return ASUCA_OK;
 }
 
+// ---- open lateral boundaries ----------------------------------------------
+// Workspace of an open domain: the step workspace (its two padded stage
+// buffers hold phi* and phi**) followed by a third padded buffer for phi^n.
+size_t open_b0_offset(const asuca_grid *g) { return step_layout(g).total; }
+size_t open_total(const asuca_grid *g) {
+    return align_up(open_b0_offset(g) + (size_t)g->F * padded_field_elems(g) * elem_size(g));
+}
+size_t open_buffer_offset(const asuca_grid *g, int b) {
+    const StepLayout L = step_layout(g);
+    return b == 0 ? open_b0_offset(g) : (b == 1 ? L.ystar : L.ystar2);
+}
+bool open_fits(const asuca_grid *g) {
+    return (long long)g->d.nz * (g->d.ny + 1) * (long long)(g->d.nx + 1) < (1LL << 32);
+}
+
+template <typename T>
+bool open_maps(asuca_grid *g, char *ws) {
+    if (g->omap_ws == (void *)ws && g->omap_ty == g->stage_ty) return true;
+    for (int b = 0; b < 3; b++)
+        if (encode_stage_map<T>(&g->omap[b], ws + open_buffer_offset(g, b), g->F, g->d.nx, g->d.ny, g->d.nz,
+                                g->stage_ty) != cudaSuccess) {
+            g->omap_ws = nullptr;
+            return false;
+        }
+    g->omap_ws = (void *)ws;
+    g->omap_ty = g->stage_ty;
+    return true;
+}
+
+template <typename T>
+OpenParams<T> open_params(const asuca_grid *g, char *ws, int b) {
+    OpenParams<T> p;
+    std::memset(&p, 0, sizeof(p));
+    workspace_fields<T>(g, ws, open_buffer_offset(g, b), p.pad);
+    p.pitch = padded_pitch(g->d.nx);
+    p.pplane = (long long)(g->d.ny + 4) * p.pitch;
+    p.nx = g->d.nx;
+    p.ny = g->d.ny;
+    p.nz = g->d.nz;
+    p.nt = g->F - 1;
+    return p;
+}
+
+template <typename T>
+asuca_status run_open_prepare(asuca_grid *g, const asuca_state *st, bool first, char *ws, cudaStream_t s) {
+    if (first && cudaMemsetAsync(ws + step_layout(g).precip, 0, (size_t)g->plane * sizeof(double), s) != cudaSuccess)
+        return ASUCA_ERR_CUDA;
+    OpenParams<T> p = open_params<T>(g, ws, 0);
+    T *y[MAXF];
+    field_ptrs<T>(g, st->rho, st->rhotheta, st->rhoq, y);
+    for (int f = 0; f < MAXF; f++) p.y[f] = y[f];
+    return cuda_status(timed(g, ASUCA_KERNEL_STAGE, s, [&] { return launch_open_prepare<T>(p, s); }));
+}
+
+template <typename T>
+asuca_status run_open_halo(asuca_grid *g, char *ws, int b, bool pack, const void *in0, const void *in1,
+                           double tratio, void *out, cudaStream_t s) {
+    OpenParams<T> p = open_params<T>(g, ws, b);
+    p.hin0 = (const T *)in0;
+    p.hin1 = (const T *)in1;
+    p.hout = (T *)out;
+    p.w0 = (T)(1.0 - tratio);
+    p.w1 = (T)tratio;
+    return cuda_status(launch_halo<T>(p, pack, g->nsm, s));
+}
+
+template <typename T>
+asuca_status run_open_stage(asuca_grid *g, asuca_state *st, const void *tend, double dt, int stage, char *ws,
+                            double *budgets, cudaStream_t s) {
+    if (!open_maps<T>(g, ws)) return ASUCA_ERR_CUDA;
+    const StepLayout L = step_layout(g);
+    const int F = g->F;
+    T *yn[MAXF], *next[MAXF];
+    field_ptrs<T>(g, st->rho, st->rhotheta, st->rhoq, yn);
+    StageParams<T> sp = stage_params<T>(g, st, tend);
+    sp.open = 1;
+    sp.plane_u = (long long)g->d.ny * (g->d.nx + 1);
+    sp.plane_v = (long long)(g->d.ny + 1) * g->d.nx;
+    sp.tma_in = 1;
+    sp.user_tma = 0;
+    sp.tmap = g->omap[stage];
+    for (int f = 0; f < MAXF; f++) sp.ybase[f] = sp.yin[f] = yn[f];
+    const T cdt[3] = {(T)(dt / 3.0), (T)(dt / 2.0), (T)dt};
+    sp.cdt = cdt[stage];
+    cudaError_t e;
+    if (stage < 2) {
+        workspace_fields<T>(g, ws, open_buffer_offset(g, stage + 1), next);
+        sp.out_padded = 1;
+        for (int f = 0; f < MAXF; f++) sp.yout[f] = next[f];
+        return cuda_status(timed(g, ASUCA_KERNEL_STAGE, s, [&] { return launch_stage<T>(sp, F, s); }));
+    }
+    ColumnParams<T> cp = column_params<T>(g, dt);
+    for (int f = 0; f < MAXF; f++) cp.y[f] = yn[f];
+    cp.precip_col = (double *)(ws + L.precip);
+    cp.partials = (double *)(ws + L.partials);
+    cp.scratch = (double *)(ws + L.scratch);
+    cp.budgets = budgets != nullptr;
+    sp.out_padded = 0;
+    for (int f = 0; f < MAXF; f++) sp.yout[f] = yn[f];
+    if (fused_path(g)) {
+        FusedParams<T> fp;
+        fp.c = cp;
+        fp.c.scratch = (double *)(ws + L.fscratch);
+        fp.c.nslots = g->plane;
+        fp.s = sp;
+        fp.s.ty = 8;
+        if ((e = timed(g, ASUCA_KERNEL_STAGE_COLUMN, s, [&] { return launch_stage3_column<T>(fp, F, s); })) !=
+            cudaSuccess)
+            return ASUCA_ERR_CUDA;
+        ColumnParams<T> cu = fp.c;
+        cu.budgets = cp.budgets;
+        if ((e = timed(g, ASUCA_KERNEL_COLUMN, s, [&] { return launch_column_up<T>(cu, F, g->col_grid, s); })) !=
+            cudaSuccess)
+            return ASUCA_ERR_CUDA;
+    } else {
+        if ((e = timed(g, ASUCA_KERNEL_STAGE, s, [&] { return launch_stage<T>(sp, F, s); })) != cudaSuccess)
+            return ASUCA_ERR_CUDA;
+        if ((e = timed(g, ASUCA_KERNEL_COLUMN, s,
+                       [&] { return launch_column<T>(cp, F, g->col_grid, COL_TPB, s); })) != cudaSuccess)
+            return ASUCA_ERR_CUDA;
+    }
+    if (budgets) {
+        e = timed(g, ASUCA_KERNEL_REDUCE, s, [&] {
+            return launch_budget_reduce(cp.partials, g->col_grid, F + 1, F, g->d.dx * g->d.dy, budgets,
+                                        g->status_dev, s);
+        });
+        if (e != cudaSuccess) return ASUCA_ERR_CUDA;
+    }
+    return ASUCA_OK;
+}
+
+template <typename T>
+asuca_status run_step_open(asuca_grid *g, asuca_state *st, const void *tend, double dt, int nsteps, const void *b0,
+                           const void *b1, double tratio, char *ws, double *budgets, cudaStream_t s) {
+    if (nsteps == 0) return run_step<T>(g, st, tend, dt, 0, ws, budgets, s);
+    for (int n = 0; n < nsteps; n++) {
+        Range step_range("asuca open step");
+        asuca_status r = run_open_prepare<T>(g, st, n == 0, ws, s);
+        for (int stg = 0; stg < 3 && r == ASUCA_OK; stg++) {
+            r = run_open_halo<T>(g, ws, stg, false, b0, b1, tratio, nullptr, s);
+            if (r == ASUCA_OK)
+                r = run_open_stage<T>(g, st, tend, dt, stg, ws, n == nsteps - 1 ? budgets : nullptr, s);
+        }
+        if (r != ASUCA_OK) return r;
+    }
+    return ASUCA_OK;
+}
+
+bool open_ws_ok(const asuca_grid *g, const void *ws, size_t bytes) {
+    return ws && ((uintptr_t)ws % ALIGN) == 0 && bytes >= open_total(g);
+}
+
 }  // namespace
 
 // ---- column pass without a caller workspace ------------------------------
@@ -1537,6 +1695,81 @@ asuca_status asuca_debug_dataflow_order(int nphases, int nrows, unsigned *out) {
     if (nphases < 1 || nrows < 1 || nrows > 4095 || nphases > 4 * DF_CHUNK || !out) return ASUCA_ERR_ARG;
     df_fill_order(out, nphases, nrows);
     return ASUCA_OK;
+}
+
+size_t asuca_open_workspace_bytes(const asuca_grid *g) { return g ? open_total(g) : 0; }
+
+size_t asuca_halo_count(const asuca_grid *g) {
+    return g ? (size_t)2 * (2 * (size_t)g->d.nx + 2 * (size_t)g->d.ny) * g->d.nz * (g->F - 1) : 0;
+}
+
+asuca_status asuca_open_prepare(asuca_grid *g, const asuca_state *st, int first, void *ws, size_t ws_bytes,
+                                void *cuda_stream) {
+    if (!g || !st || !st->rho || !st->rhotheta || (g->d.ntracers && !st->rhoq)) return ASUCA_ERR_ARG;
+    if (!open_fits(g)) return ASUCA_ERR_UNSUPPORTED;
+    asuca_status prev = take_status(g);
+    if (prev != ASUCA_OK) return prev;
+    if (!open_ws_ok(g, ws, ws_bytes)) return ASUCA_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    g->last_stream = s;
+    return g->d.prec == ASUCA_FP64 ? run_open_prepare<double>(g, st, first != 0, (char *)ws, s)
+                                   : run_open_prepare<float>(g, st, first != 0, (char *)ws, s);
+}
+
+asuca_status asuca_open_stage(asuca_grid *g, asuca_state *st, const void *tend, double dt, int stage, void *ws,
+                              size_t ws_bytes, double *budgets, void *cuda_stream) {
+    if (!g || !state_ok(g, st) || stage < 0 || stage > 2 || !std::isfinite(dt) || dt < 0.0) return ASUCA_ERR_ARG;
+    if (!open_fits(g)) return ASUCA_ERR_UNSUPPORTED;
+    asuca_status prev = take_status(g);
+    if (prev != ASUCA_OK) return prev;
+    if (!open_ws_ok(g, ws, ws_bytes)) return ASUCA_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    g->last_stream = s;
+    return g->d.prec == ASUCA_FP64 ? run_open_stage<double>(g, st, tend, dt, stage, (char *)ws, budgets, s)
+                                   : run_open_stage<float>(g, st, tend, dt, stage, (char *)ws, budgets, s);
+}
+
+asuca_status asuca_halo_pack(asuca_grid *g, const void *ws, size_t ws_bytes, int buffer, void *send,
+                             void *cuda_stream) {
+    if (!g || !send || buffer < 0 || buffer > 2) return ASUCA_ERR_ARG;
+    asuca_status prev = take_status(g);
+    if (prev != ASUCA_OK) return prev;
+    if (!open_ws_ok(g, ws, ws_bytes)) return ASUCA_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    g->last_stream = s;
+    char *w = (char *)const_cast<void *>(ws);
+    return g->d.prec == ASUCA_FP64 ? run_open_halo<double>(g, w, buffer, true, nullptr, nullptr, 0.0, send, s)
+                                   : run_open_halo<float>(g, w, buffer, true, nullptr, nullptr, 0.0, send, s);
+}
+
+asuca_status asuca_halo_unpack(asuca_grid *g, void *ws, size_t ws_bytes, int buffer, const void *recv,
+                               const void *bnd1, double tratio, void *cuda_stream) {
+    if (!g || !recv || buffer < 0 || buffer > 2 || !std::isfinite(tratio)) return ASUCA_ERR_ARG;
+    asuca_status prev = take_status(g);
+    if (prev != ASUCA_OK) return prev;
+    if (!open_ws_ok(g, ws, ws_bytes)) return ASUCA_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    g->last_stream = s;
+    return g->d.prec == ASUCA_FP64
+               ? run_open_halo<double>(g, (char *)ws, buffer, false, recv, bnd1, tratio, nullptr, s)
+               : run_open_halo<float>(g, (char *)ws, buffer, false, recv, bnd1, tratio, nullptr, s);
+}
+
+asuca_status asuca_step_open(asuca_grid *g, asuca_state *st, const void *tend, double dt, int nsteps,
+                             const void *bnd0, const void *bnd1, double tratio, void *ws, size_t ws_bytes,
+                             double *budgets, void *cuda_stream) {
+    if (!g || !state_ok(g, st) || nsteps < 0 || !std::isfinite(dt) || dt < 0.0 || !bnd0 || !std::isfinite(tratio))
+        return ASUCA_ERR_ARG;
+    if (!open_fits(g)) return ASUCA_ERR_UNSUPPORTED;
+    asuca_status prev = take_status(g);
+    if (prev != ASUCA_OK) return prev;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    g->last_stream = s;
+    if (nsteps == 0 && !budgets) return ASUCA_OK;
+    if (!open_ws_ok(g, ws, ws_bytes)) return ASUCA_ERR_WORKSPACE;
+    return g->d.prec == ASUCA_FP64
+               ? run_step_open<double>(g, st, tend, dt, nsteps, bnd0, bnd1, tratio, (char *)ws, budgets, s)
+               : run_step_open<float>(g, st, tend, dt, nsteps, bnd0, bnd1, tratio, (char *)ws, budgets, s);
 }
 
 asuca_status asuca_profile_enable(asuca_grid *g, int on) {

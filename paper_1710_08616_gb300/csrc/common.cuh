@@ -67,6 +67,11 @@ struct StageParams {
     int out_padded;         // output to a padded stage buffer: phi for f >= 1, with periodic ghosts
     int user_tma;           // unpadded input through umap for tiles whose halo lies inside the domain
     int ty;                 // tile rows of the instantiation to launch (the TMA box height follows it)
+    int open;               // open lateral boundaries: the padded input's ghost columns/rows hold the
+                            // lateral neighbours (a halo exchange or boundary data wrote them), nothing
+                            // wraps, the output's ghosts are not written, and mu, mv are the open
+                            // domain's face fluxes [nz][ny][nx+1] (face i-1/2 at i) and [nz][ny+1][nx]
+    long long plane_u, plane_v;   // level strides of mu and mv (the plane, or its open-domain sizes)
     uint8_t *branch;        // when recording: [F-1][nz][ny][nx] branch bytes (2 bits per direction)
     T *facev;               // when recording, if set: [3][F-1][nz][ny][nx] face values of the cell's
                             // i+1/2, j+1/2 and k+1/2 faces (k+1/2 of the top level: 0)

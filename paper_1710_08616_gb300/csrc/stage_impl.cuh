@@ -162,14 +162,23 @@ __device__ __forceinline__ bool stage_tile_h(const StageParams<T> &p, const CUte
     const unsigned plane = (unsigned)p.plane;
     const int i = i0 + tx, j = j0 + ty;
     const bool valid = (i < nx) && (j < ny);
-    const int ic = wrap_index(i, nx), jc = wrap_index(j, ny);
+    const bool open = p.open != 0;
+    // threads past the domain's edge compute nothing they keep: periodic tiles
+    // wrap their indices, open ones clamp them (nothing lies beyond the edge)
+    const int ic = open ? min(i, nx - 1) : wrap_index(i, nx), jc = open ? min(j, ny - 1) : wrap_index(j, ny);
     const unsigned own = (unsigned)(jc * nx + ic);
-    const unsigned left = (unsigned)(jc * nx + wrap_index(ic - 1, nx));
-    const unsigned down = (unsigned)(wrap_index(jc - 1, ny) * nx + ic);
+    // mass-flux indices: periodic, mu and mv share the cell's index (faces
+    // i+1/2, j+1/2) and the faces i-1/2, j-1/2 wrap; open, face i-1/2 of cell i
+    // is mu[j][i] of a row of nx+1 faces and face j-1/2 is mv[j][i]
+    const unsigned u_own = open ? (unsigned)(jc * (nx + 1) + ic + 1) : own;
+    const unsigned u_left = open ? (unsigned)(jc * (nx + 1) + ic) : (unsigned)(jc * nx + wrap_index(ic - 1, nx));
+    const unsigned v_own = open ? (unsigned)((jc + 1) * nx + ic) : own;
+    const unsigned v_down = open ? own : (unsigned)(wrap_index(jc - 1, ny) * nx + ic);
+    const unsigned plane_u = (unsigned)p.plane_u, plane_v = (unsigned)p.plane_v;
     // Input paths: a padded stage buffer (phi, one 4D TMA box per level); the
     // caller's fields (rho*phi) by TMA when the tile's halo lies inside the
     // domain, else by per-thread cp.async with the periodic wrap.
-    const bool pad_in = p.tma_in != 0;
+    const bool pad_in = p.tma_in != 0;   // always set for open boundaries
     const bool user_tma = !pad_in && p.user_tma && i0 >= 4 && i0 + TX + 4 <= nx && j0 >= 2 && j0 + TY + 2 <= ny;
     const bool tma = pad_in || user_tma;
     const bool conv = !pad_in;
@@ -304,12 +313,14 @@ __device__ __forceinline__ bool stage_tile_h(const StageParams<T> &p, const CUte
     const int warp = ty, lane = tx;
     // Edge faces (j0-1/2 for the tile's 32 columns, i0-1/2 for its TY rows),
     // one task per (field, edge), dealt round-robin to the warps.
-    const unsigned edge_b = (unsigned)(wrap_index(j0 - 1, ny) * nx + ic);                 // MV below the tile
     const int er = lane % TY;   // the tile row whose i0-1/2 faces this lane computes
-    const unsigned edge_l = (unsigned)(wrap_index(j0 + er, ny) * nx + wrap_index(i0 - 1, nx));  // MU left of row er
+    // MV through face j0-1/2 of column ic, MU through face i0-1/2 of row er
+    const unsigned edge_b = open ? (unsigned)(j0 * nx + ic) : (unsigned)(wrap_index(j0 - 1, ny) * nx + ic);
+    const unsigned edge_l = open ? (unsigned)(min(j0 + er, ny - 1) * (nx + 1) + i0)
+                                 : (unsigned)(wrap_index(j0 + er, ny) * nx + wrap_index(i0 - 1, nx));
     // tiles that hold cells whose values are also periodic ghosts of the padded output
-    const bool ghost_x = (i0 < 2) || (i0 + TX > nx - 2);
-    const bool ghost_y = (j0 < 2) || (j0 + TY > ny - 2);
+    const bool ghost_x = !open && ((i0 < 2) || (i0 + TX > nx - 2));
+    const bool ghost_y = !open && ((j0 < 2) || (j0 + TY > ny - 2));
 
     T zlo[NF];
 #pragma unroll
@@ -321,15 +332,15 @@ __device__ __forceinline__ bool stage_tile_h(const StageParams<T> &p, const CUte
     T mup, mum, mvp, mvm, mwp, meb, mel;
     T nmup, nmum, nmvp, nmvm, nmwp, nmeb, nmel, nrho;
     auto prefetch = [&](int k) {
-        const unsigned kb = (unsigned)k * plane;
-        nmup = p.mu[kb + own];
-        nmum = p.mu[kb + left];
-        nmvp = p.mv[kb + own];
-        nmvm = p.mv[kb + down];
+        const unsigned kb = (unsigned)k * plane, kbu = (unsigned)k * plane_u, kbv = (unsigned)k * plane_v;
+        nmup = p.mu[kbu + u_own];
+        nmum = p.mu[kbu + u_left];
+        nmvp = p.mv[kbv + v_own];
+        nmvm = p.mv[kbv + v_down];
         if (DOWN) nmwp = (k > 0) ? p.mw[kb + own] : T(0);
         else nmwp = (k < nz - 1) ? p.mw[kb + plane + own] : T(0);
-        nmeb = p.mv[kb + edge_b];
-        nmel = p.mu[kb + edge_l];
+        nmeb = p.mv[kbv + edge_b];
+        nmel = p.mu[kbu + edge_l];
         if (Hook::active) nrho = p.ybase[0][kb + own];
     };
     auto advance = [&]() {

@@ -137,3 +137,106 @@ def test_gloo_world2_ensemble_step_sharded_host_logic():
         assert seen == share[rank]                      # this rank stepped exactly its members
         assert steps == [3 if m in share[rank] else 0 for m in range(len(sizes))]
         assert np.frombuffer(got, dtype=np.float64).reshape(expect.shape).tolist() == expect.tolist()
+
+
+# ---------------------------------------------------------------- decomposed domain: halo exchange
+
+def _np_block(field, decomp, r):
+    """A host-side stand-in of a block: its padded buffer [T][nz][ny+4][nx+8]
+    (interior at (j+2, i+4)) holding its part of the global field, ghosts NaN."""
+    import types
+    i0, i1, j0, j1 = decomp.extent(r)
+    T, nz = field.shape[0], field.shape[1]
+    nx, ny = i1 - i0, j1 - j0
+    pad = np.full((T, nz, ny + 4, nx + 8), np.nan)
+    pad[:, :, 2:ny + 2, 4:nx + 4] = field[:, :, j0:j1, i0:i1]
+    grid = types.SimpleNamespace(nx=nx, ny=ny, nz=nz, nfields=T + 1)
+    return types.SimpleNamespace(grid=grid, pad=pad, extent=(i0, i1, j0, j1))
+
+
+def _np_pack(b):
+    """The halo layout's packed strips: W cells i = c, E i = nx-2+c, S j = c, N j = ny-2+c."""
+    import torch
+    nx, ny, p = b.grid.nx, b.grid.ny, b.pad
+    w = np.moveaxis(p[:, :, 2:ny + 2, 4:6], 3, 2)
+    e = np.moveaxis(p[:, :, 2:ny + 2, nx + 2:nx + 4], 3, 2)
+    s = p[:, :, 2:4, 4:nx + 4]
+    n = p[:, :, ny:ny + 2, 4:nx + 4]
+    return torch.tensor(np.concatenate([a.reshape(-1) for a in (w, e, s, n)]))
+
+
+def _np_unpack(b, t):
+    """Received strips into the ghosts: W i = c-2, E i = nx+c, S j = c-2, N j = ny+c."""
+    from paper_1710_08616_gb300.distributed import halo_strips
+    nx, ny, nz, T = b.grid.nx, b.grid.ny, b.grid.nz, b.grid.nfields - 1
+    w, e, s, n = (x.numpy() for x in halo_strips(t, T, nz, ny, nx))
+    b.pad[:, :, 2:ny + 2, 2:4] = np.moveaxis(w.reshape(T, nz, 2, ny), 2, 3)
+    b.pad[:, :, 2:ny + 2, nx + 4:nx + 6] = np.moveaxis(e.reshape(T, nz, 2, ny), 2, 3)
+    b.pad[:, :, 0:2, 4:nx + 4] = s.reshape(T, nz, 2, nx)
+    b.pad[:, :, ny + 2:ny + 4, 4:nx + 4] = n.reshape(T, nz, 2, nx)
+
+
+def _check_ghosts(field, b):
+    """Every ghost of the cross equals the periodic continuation of the global field."""
+    i0, i1, j0, j1 = b.extent
+    nx, ny = i1 - i0, j1 - j0
+    gx, gy = field.shape[3], field.shape[2]
+    cols = [(i0 + i) % gx for i in (-2, -1, nx, nx + 1)]
+    for q, i in zip(cols, (2, 3, nx + 4, nx + 5)):
+        assert np.array_equal(b.pad[:, :, 2:ny + 2, i], field[:, :, j0:j1, q])
+    rows = [(j0 + j) % gy for j in (-2, -1, ny, ny + 1)]
+    for q, j in zip(rows, (0, 1, ny + 2, ny + 3)):
+        assert np.array_equal(b.pad[:, :, j, 4:nx + 4], field[:, :, q, i0:i1])
+
+
+def _field():
+    return np.random.default_rng(5).standard_normal((3, 4, 11, 13))
+
+
+def test_halo_exchange_single_process_blocks_continue_the_plane_periodically():
+    from paper_1710_08616_gb300.distributed import Decomposition, exchange_halos
+    f = _field()
+    for px, py in ((1, 1), (2, 1), (1, 2), (3, 2), (2, 3)):
+        d = Decomposition(f.shape[3], f.shape[2], px, py)
+        blocks = {r: _np_block(f, d, r) for r in range(d.nblocks)}
+        exchange_halos(blocks, d, 0, pack=_np_pack, unpack=_np_unpack)
+        for b in blocks.values():
+            _check_ghosts(f, b)
+
+
+def _halo_worker(rank, world, port, px, py, q):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        from paper_1710_08616_gb300.distributed import Decomposition, exchange_halos
+        f = _field()
+        d = Decomposition(f.shape[3], f.shape[2], px, py)
+        blocks = {rank: _np_block(f, d, rank)}
+        exchange_halos(blocks, d, 1, pack=_np_pack, unpack=_np_unpack)
+        _check_ghosts(f, blocks[rank])
+        q.put((rank, True))
+    except AssertionError:
+        q.put((rank, False))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("px,py", [(2, 1), (1, 2)])
+def test_gloo_world2_halo_exchange(px, py):
+    """Two ranks, one block each: with two blocks along a direction, a rank's
+    west and east neighbour is the same rank, so both directions' messages
+    travel between the same pair (one direction at a time)."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_halo_worker, args=(r, 2, port, px, py, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert res == [(0, True), (1, True)]
