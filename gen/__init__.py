@@ -8,5 +8,5 @@ from .fields import (  # noqa: F401
     CONFIGS, SEED_BASE, Case, make_dz, make_case, make_config_case,
     make_ensemble_cases, ensemble_sizes, DAMPING, make_boundary_data,
     ACOUSTIC, make_acoustic_state, halo_periodic, halo_strips, extend_fluxes, split_extent,
-    subdomain, make_open_boundary,
+    subdomain, make_open_boundary, HEVI, make_hevi_state,
 )

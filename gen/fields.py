@@ -357,6 +357,27 @@ def make_acoustic_state(case: Case, *, dtype=np.float64):
             cast(S), rho0c, rho0f)
 
 
+HEVI = dict(dt=12.0, nshort=6)   # long step and short steps of the coupled workload (h = 2 s)
+
+
+def make_hevi_state(case: Case, *, dtype=np.float64):
+    """Inputs of the long step with nested acoustic short steps on a case's grid:
+    the acoustic base state of make_acoustic_state, the density
+    rho = rho0 (1 + s) with s = 5e-4 (theta - theta_ref) (|s| <= 1e-3), the
+    case's theta and mixing ratios carried by that density, and the case's
+    mass fluxes as the initial momenta U, V, W.  A 12 s long step of six 2 s
+    short steps keeps the horizontal acoustic Courant number at 0.34.
+    Returns (Y [F][nz][ny][nx], U, V, W, rho0c, rho0f, dt, nshort)."""
+    _, _, _, S, rho0c, rho0f = make_acoustic_state(case)
+    rho_case = np.asarray(case.rho, np.float64)
+    theta = np.asarray(case.rhotheta, np.float64) / rho_case
+    q = np.asarray(case.rhoq, np.float64) / rho_case[None]
+    rho = rho0c[:, None, None] * (1.0 + S)
+    Y = np.concatenate([rho[None], (rho * theta)[None], rho[None] * q])
+    cast = (lambda a: np.ascontiguousarray(a, dtype=dtype))
+    return (cast(Y), cast(case.mu), cast(case.mv), cast(case.mw), rho0c, rho0f, HEVI["dt"], HEVI["nshort"])
+
+
 # ---------------------------------------------------------------- open lateral boundaries
 #
 # Halo layout of the ghost cells of an open domain (limited-area or one block

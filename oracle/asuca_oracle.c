@@ -1254,10 +1254,13 @@ static void acoustic_column(int nz, const double *dz, const double *rho0c, const
     Wn[nz] = 0.0;
 }
 
-/* nshort HEVI short steps of length h, in place (fields as in the header) */
-void orc_acoustic(int nx, int ny, int nz, double dx, double dy, const double *dz, const double *rho0c,
-                  const double *rho0f, double cs2, double beta, double h, int nshort, double *U, double *V,
-                  double *W, double *S) {
+/* nshort HEVI short steps of length h, in place (fields as in the header).
+ * When Mu is set, each short step also adds wgt times the mass fluxes its
+ * density equation applies, (U*, V*, (1 - beta) W + beta W') on every face
+ * (W' the new vertical momentum, interior faces only), to Mu, Mv, Mw. */
+static void acoustic_run(int nx, int ny, int nz, double dx, double dy, const double *dz, const double *rho0c,
+                         const double *rho0f, double cs2, double beta, double h, int nshort, double *U, double *V,
+                         double *W, double *S, double *Mu, double *Mv, double *Mw, double wgt) {
     const long long plane = (long long)nx * ny, n = plane * nz;
     double *Us = (double *)malloc(n * sizeof(double)), *Vs = (double *)malloc(n * sizeof(double));
     double *Ss = (double *)malloc(n * sizeof(double));
@@ -1301,6 +1304,14 @@ void orc_acoustic(int nx, int ny, int nz, double dx, double dy, const double *dz
                     if (stage == 0) {
                         for (int k = 0; k < nz; k++) Ss[k * plane + q] = sn[k];
                     } else {
+                        if (Mu) {
+                            for (int k = 0; k < nz; k++) {
+                                Mu[k * plane + q] += wgt * Us[k * plane + q];
+                                Mv[k * plane + q] += wgt * Vs[k * plane + q];
+                            }
+                            for (int f = 1; f < nz; f++)
+                                Mw[f * plane + q] += wgt * ((1.0 - beta) * Wc[f] + beta * Wn[f]);
+                        }
                         for (int k = 0; k < nz; k++) S[k * plane + q] = sn[k];
                         for (int f = 1; f < nz; f++) W[f * plane + q] = Wn[f];
                     }
@@ -1312,4 +1323,80 @@ void orc_acoustic(int nx, int ny, int nz, double dx, double dy, const double *dz
         memcpy(V, Vp, n * sizeof(double));
     }
     free(Us); free(Vs); free(Ss); free(Up); free(Vp);
+}
+
+void orc_acoustic(int nx, int ny, int nz, double dx, double dy, const double *dz, const double *rho0c,
+                  const double *rho0f, double cs2, double beta, double h, int nshort, double *U, double *V,
+                  double *W, double *S) {
+    acoustic_run(nx, ny, nz, dx, dy, dz, rho0c, rho0f, cs2, beta, h, nshort, U, V, W, S, NULL, NULL, NULL, 0.0);
+}
+
+/* short steps of RK stage q (weights 1/3, 1/2, 1) for ns short steps per long step */
+int orc_hevi_short_steps(int ns, int q) {
+    const double frac = q == 0 ? 1.0 / 3.0 : (q == 1 ? 0.5 : 1.0);
+    const int n = (int)floor(frac * ns + 0.5);
+    return n < 1 ? 1 : n;
+}
+
+/* ---- HEVI short steps nested in the RK3 long step (Sec. 1.1) --------------
+ * The momenta U, V, W (the mass fluxes of the C grid) are prognostic and
+ * evolve by the linear acoustic-gravity system of orc_acoustic; the scalar
+ * fields are advected by them.  Wicker-Skamarock splitting: RK stage q
+ * (weight c_q = 1/3, 1/2, 1) integrates the fast system from t^n over c_q dt
+ * in n_q short steps (orc_hevi_short_steps) from (U, V, W)^n and
+ * s^n = rho^n / rho0 - 1, and its scalar update Y^(q) = Y^n + c_q dt R(Y^(q-1))
+ * advects with the short steps' mean effective mass fluxes
+ *   Mbar = (1 / n_q) sum_m (U*_m, V*_m, (1 - beta) W_m + beta W_(m+1)),
+ * the fluxes whose divergence the acoustic density equation applies, so the
+ * advected density stays rho0 (1 + s) of the acoustic integration.  The third
+ * stage's integration gives (U, V, W)^{n+1} (and s_final, if set).  Then the
+ * column pass.  Fields: U, V [nz][ny][nx], W [nz+1][ny][nx] (lids kept). */
+void orc_step_hevi(const orc_grid *g, double *Y, double *U, double *V, double *W, const double *tend,
+                   const double *rho0c, const double *rho0f, double cs2, double beta, int ns, double dt,
+                   int nsteps, double *s_final, double *budgets) {
+    const int nx = g->nx, ny = g->ny, nz = g->nz;
+    const size_t plane = (size_t)nx * ny, C = plane * nz, n = (size_t)(2 + g->ntr) * C, CW = C + plane;
+    double *Yn = (double *)malloc(n * sizeof(double)), *Ys = (double *)malloc(n * sizeof(double));
+    double *R = (double *)malloc(n * sizeof(double));
+    double *pc = (double *)calloc(plane, sizeof(double));
+    double *Sn = (double *)malloc(C * sizeof(double)), *Sa = (double *)malloc(C * sizeof(double));
+    double *Ua = (double *)malloc(C * sizeof(double)), *Va = (double *)malloc(C * sizeof(double));
+    double *Wa = (double *)malloc(CW * sizeof(double));
+    double *Mu = (double *)malloc(C * sizeof(double)), *Mv = (double *)malloc(C * sizeof(double));
+    double *Mw = (double *)malloc(CW * sizeof(double));
+    const double c[3] = {dt / 3.0, dt / 2.0, dt};
+    for (int step = 0; step < nsteps; step++) {
+        memcpy(Yn, Y, n * sizeof(double));
+        for (int k = 0; k < nz; k++)
+            for (size_t q = 0; q < plane; q++) Sn[k * plane + q] = Y[k * plane + q] / rho0c[k] - 1.0;
+        const double *in = Yn;
+        for (int q = 0; q < 3; q++) {
+            const int nq = orc_hevi_short_steps(ns, q);
+            memcpy(Ua, U, C * sizeof(double));
+            memcpy(Va, V, C * sizeof(double));
+            memcpy(Wa, W, CW * sizeof(double));
+            memcpy(Sa, Sn, C * sizeof(double));
+            memset(Mu, 0, C * sizeof(double));
+            memset(Mv, 0, C * sizeof(double));
+            memset(Mw, 0, CW * sizeof(double));
+            acoustic_run(nx, ny, nz, g->dx, g->dy, g->dz, rho0c, rho0f, cs2, beta, c[q] / nq, nq, Ua, Va, Wa, Sa,
+                         Mu, Mv, Mw, 1.0 / nq);
+            orc_rhs(g, in, Mu, Mv, Mw, tend, R, NULL);
+            double *dst = q == 2 ? Y : Ys;
+            for (size_t e = 0; e < n; e++) dst[e] = Yn[e] + c[q] * R[e];
+            in = Ys;
+        }
+        memcpy(U, Ua, C * sizeof(double));
+        memcpy(V, Va, C * sizeof(double));
+        memcpy(W, Wa, CW * sizeof(double));
+        if (s_final) memcpy(s_final, Sa, C * sizeof(double));
+        orc_column(g, Y, dt, pc);
+    }
+    if (budgets) {
+        csum tot = {0.0, 0.0};
+        for (size_t q = 0; q < plane; q++) csum_add(&tot, pc[q]);
+        orc_budgets(g, Y, csum_value(&tot), budgets);
+    }
+    free(Yn); free(Ys); free(R); free(pc); free(Sn); free(Sa); free(Ua); free(Va); free(Wa);
+    free(Mu); free(Mv); free(Mw);
 }

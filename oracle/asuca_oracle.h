@@ -112,6 +112,21 @@ void orc_damping(int nx, int ny, int nz, int F, int width, int ntop, double nu_l
 void orc_acoustic(int nx, int ny, int nz, double dx, double dy, const double *dz, const double *rho0c,
                   const double *rho0f, double cs2, double beta, double h, int nshort, double *U, double *V,
                   double *W, double *S);
+/* Short steps of RK stage q (0, 1, 2: weights 1/3, 1/2, 1) when a long step
+ * has ns: max(1, round(weight ns)). */
+int orc_hevi_short_steps(int ns, int q);
+/* nsteps long steps with the acoustic short steps nested in every RK3 stage
+ * (Wicker-Skamarock splitting): U, V [nz][ny][nx] and W [nz+1][ny][nx] are
+ * the prognostic momenta (mass fluxes), updated in place; RK stage q
+ * integrates them with orc_acoustic from t^n over its weight times dt, in
+ * orc_hevi_short_steps(ns, q) short steps from s^n = rho^n / rho0c - 1, and
+ * advects the scalars with the short steps' mean effective mass fluxes
+ * (U*, V*, (1 - beta) W + beta W'); stage 3's integration is the new
+ * momentum state (and s_final [nz][ny][nx], if set).  Then the column pass;
+ * budgets as orc_step. */
+void orc_step_hevi(const orc_grid *g, double *Y, double *U, double *V, double *W, const double *tend,
+                   const double *rho0c, const double *rho0f, double cs2, double beta, int ns, double dt,
+                   int nsteps, double *s_final, double *budgets);
 void orc_set_threads(int n);
 int orc_get_threads(void);
 
