@@ -463,6 +463,38 @@ asuca_status asuca_step_open(asuca_grid *grid, asuca_state *state, const void *t
                              const void *bnd0, const void *bnd1, double tratio, void *workspace,
                              size_t workspace_bytes, double *budgets_dev, void *cuda_stream);
 
+/* ---- acoustic short steps nested in the RK3 long step -------------------
+ * The two halves of the dynamical core together (Sec. 1.1 "ASUCA on GPU":
+ * the long step by RK3, sound and gravity waves by the HEVI short steps):
+ * the momenta are prognostic and the scalars are advected by them.  Wicker-
+ * Skamarock splitting: RK stage q (weight c_q = 1/3, 1/2, 1) integrates the
+ * acoustic system of asuca_acoustic_steps from t^n over c_q dt in
+ * n_q = max(1, round(c_q nshort)) short steps of c_q dt / n_q, starting from
+ * the momenta at t^n and s^n = rho^n / rho0c - 1 (the acoustic density
+ * perturbation of the advected density), and the scalar stage
+ * Y^(q) = Y^n + c_q dt R(Y^(q-1)) advects with the short steps' mean
+ * effective mass fluxes (1/n_q) sum (U*, V*, (1 - beta) W + beta W'), the
+ * fluxes whose divergence the acoustic density equation applies, so that the
+ * advected density equals rho0c (1 + s) of the integration to rounding.  The
+ * third stage's integration is the new momentum state.  Then the column pass
+ * and budgets as asuca_step.  The coupling of the acoustic system to the
+ * scalars beyond the density (a buoyancy from theta) is not modelled: the
+ * base state is resting and horizontally uniform.
+ *   - state: as for asuca_step, but mu, mv, mw are the prognostic momenta
+ *     U, V ([nz][ny][nx], faces i+1/2, j+1/2) and W ([nz+1][ny][nx], the face
+ *     below cell k; the lids are never read or written), updated in place.
+ *   - desc: the acoustic base state and constants as for asuca_acoustic_steps;
+ *     nshort >= 1 short steps per long step.
+ *   - s_final: NULL, or a device array [nz][ny][nx] that receives s of the
+ *     last step's third-stage integration.
+ *   - workspace: asuca_hevi_workspace_bytes(grid) bytes, 256-byte aligned,
+ *     else ASUCA_ERR_WORKSPACE.  Argument errors as asuca_step and
+ *     asuca_acoustic_steps.  Asynchronous on the stream. */
+size_t asuca_hevi_workspace_bytes(const asuca_grid *grid);
+asuca_status asuca_step_hevi(asuca_grid *grid, asuca_state *state, const void *tendencies, double dt, int nsteps,
+                             const asuca_acoustic_desc *desc, int nshort, void *s_final, void *workspace,
+                             size_t workspace_bytes, double *budgets_dev, void *cuda_stream);
+
 /* ---- per-kernel timing ------------------------------------------------- */
 
 typedef enum {
@@ -475,7 +507,9 @@ typedef enum {
     ASUCA_KERNEL_DATAFLOW = 6,  /* persistent dataflow step kernel (up to 16 steps) */
     ASUCA_KERNEL_STAGE_COLUMN = 7, /* third stage fused with the top-down column pass (its bottom-up half
                                       is counted as ASUCA_KERNEL_COLUMN) */
-    ASUCA_KERNEL_KINDS = 8
+    ASUCA_KERNEL_ACOUSTIC = 8,  /* a stage of an acoustic short step nested in a long step (and the
+                                   density perturbation it starts from) */
+    ASUCA_KERNEL_KINDS = 9
 } asuca_kernel_kind;
 
 /* When on, every kernel launch of later calls on this grid is bracketed by

@@ -119,6 +119,9 @@ SIGNATURES = {
     "asuca_halo_unpack": (ctypes.c_int, [_VP, _VP, ctypes.c_size_t, ctypes.c_int, _VP, _VP, ctypes.c_double, _VP]),
     "asuca_step_open": (ctypes.c_int, [_VP, ctypes.POINTER(StateStruct), _VP, ctypes.c_double, ctypes.c_int, _VP,
                                        _VP, ctypes.c_double, _VP, ctypes.c_size_t, _VP, _VP]),
+    "asuca_hevi_workspace_bytes": (ctypes.c_size_t, [_VP]),
+    "asuca_step_hevi": (ctypes.c_int, [_VP, ctypes.POINTER(StateStruct), _VP, ctypes.c_double, ctypes.c_int,
+                                       ctypes.POINTER(AcousticDesc), ctypes.c_int, _VP, _VP, ctypes.c_size_t, _VP, _VP]),
     "asuca_profile_enable": (ctypes.c_int, [_VP, ctypes.c_int]),
     "asuca_profile_read": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
@@ -128,7 +131,8 @@ TUNE_COL_BLOCKS_PER_SM, TUNE_BARRIER_EXTRA, TUNE_STAGE_TILE_ROWS, TUNE_ENSEMBLE_
 TUNE_FUSED_COLUMN = 5
 KERNEL_DATAFLOW = 6
 KERNEL_STAGE_COLUMN = 7
-KERNEL_KINDS = 8
+KERNEL_ACOUSTIC = 8
+KERNEL_KINDS = 9
 
 
 def library_path() -> str:
@@ -484,6 +488,33 @@ def acoustic_steps(grid: Grid, U, V, W, S, rho0c, rho0f, cs2: float, beta: float
     _check(lib().asuca_acoustic_steps(grid.handle, _ptr(U), _ptr(V), _ptr(W), _ptr(S), ctypes.byref(d), float(dtau),
                                       int(nshort), _ptr(workspace), workspace.numel(), _stream_ptr(stream)),
            "asuca_acoustic_steps")
+
+
+def hevi_workspace_bytes(grid: Grid) -> int:
+    return int(lib().asuca_hevi_workspace_bytes(grid.handle))
+
+
+def step_hevi(grid: Grid, state: State, dt: float, nsteps: int, rho0c, rho0f, cs2: float, beta: float, nshort: int,
+              *, tendencies=None, s_final=None, workspace=None, budgets=None, stream=None):
+    """nsteps long steps with the acoustic short steps nested in the RK3 stages
+    (asuca_step_hevi): state.mu, mv, mw are the prognostic momenta U, V, W,
+    updated in place with the scalars.  s_final, if given ([nz][ny][nx] of the
+    grid's dtype), receives s of the last third-stage integration."""
+    import torch
+    _check_state(grid, state)
+    if workspace is None:
+        workspace = torch.empty(hevi_workspace_bytes(grid), dtype=torch.uint8, device=state.rho.device)
+    if budgets is True:
+        budgets = torch.empty(grid.nfields + 1, dtype=torch.float64, device=state.rho.device)
+    r0c = np.ascontiguousarray(rho0c, dtype=np.float64)
+    r0f = np.ascontiguousarray(rho0f, dtype=np.float64)
+    dp = ctypes.POINTER(ctypes.c_double)
+    d = AcousticDesc(r0c.ctypes.data_as(dp), r0f.ctypes.data_as(dp), float(cs2), float(beta))
+    s = state.struct()
+    _check(lib().asuca_step_hevi(grid.handle, ctypes.byref(s), _ptr(tendencies), float(dt), int(nsteps),
+                                 ctypes.byref(d), int(nshort), _ptr(s_final), _ptr(workspace), workspace.numel(),
+                                 _ptr(budgets), _stream_ptr(stream)), "asuca_step_hevi")
+    return budgets
 
 
 def profile_enable(grid: Grid, on: bool = True):

@@ -31,6 +31,10 @@
 // column there, and reads neighbours only from the stage-1 values.
 // The FP32 path computes in float throughout (the factorisation is computed
 // in double on the host and rounded).
+// Nested in the RK3 long step, stage 2 may write the new state to other
+// arrays than its start state and adds the mass fluxes its density equation
+// applies, (U*, V*, (1 - beta) W + beta W'), to the stage's mean-flux
+// accumulators; the advection of the scalars then uses those means.
 #include "acoustic.cuh"
 #include "smem_attr.cuh"
 
@@ -61,8 +65,9 @@ __global__ void __launch_bounds__(256) acoustic_kernel(const __grid_constant__ A
     const unsigned os = (unsigned)((j > 0 ? j - 1 : p.ny - 1) * nx + i);
     const unsigned on = (unsigned)((j < p.ny - 1 ? j + 1 : 0) * nx + i);
     const T *se = STAGE == 1 ? p.S : p.Ss;     // the s that drives the horizontal momenta
-    T *Wo = STAGE == 1 ? p.Ws : p.W;
-    T *So = STAGE == 1 ? p.Ss : p.S;
+    T *Wo = STAGE == 1 ? p.Ws : p.Wo;
+    T *So = STAGE == 1 ? p.Ss : p.So;
+    const bool acc = STAGE == 2 && p.Mu != nullptr;
 
     // ---- up: horizontal momenta, explicit parts, forward elimination.  The
     // inputs of each level stream through a ring of D shared-memory slots
@@ -176,9 +181,14 @@ __global__ void __launch_bounds__(256) acoustic_kernel(const __grid_constant__ A
             p.Vs[b + own] = vn;
             Dh = (ue - uw) * p.rdx + (vn - vs) * p.rdy;
         } else {
-            p.U[b + own] = cur.u - p.gx[k] * (cur.e - cur.c);
-            p.V[b + own] = cur.v - p.gy[k] * (cur.n - cur.c);
+            p.Uo[b + own] = cur.u - p.gx[k] * (cur.e - cur.c);
+            p.Vo[b + own] = cur.v - p.gy[k] * (cur.n - cur.c);
             Dh = (cur.w - cur.uw) * p.rdx + (cur.s - cur.vs) * p.rdy;
+            if (acc) {   // U*, V* of the cell's own faces
+                p.Mu[b + own] = (p.acc_init ? T(0) : p.Mu[b + own]) + p.wacc * cur.w;
+                p.Mv[b + own] = (p.acc_init ? T(0) : p.Mv[b + own]) + p.wacc * cur.s;
+                if (k >= 1) p.Mw[b + own] = (p.acc_init ? T(0) : p.Mw[b + own]) + p.wlo * Wk;   // old W of face k
+            }
         }
         const T r = sk - p.cr[k] * (Dh + p.cw[k] * (Wk1 - Wk));
         if (k >= 1) {
@@ -211,6 +221,7 @@ __global__ void __launch_bounds__(256) acoustic_kernel(const __grid_constant__ A
         if (k >= 1) {
             Wn = (k == nz - 1) ? dk : dk - p.cp[k] * Wup;
             if (STAGE == 2) Wo[b + own] = Wn;  // stage 2 only: nothing reads W*
+            if (acc) p.Mw[b + own] += p.whi * Wn;   // new W of face k
         }
         So[b + own] = rk - p.B[k] * (Wup - Wn);
         Wup = Wn;
@@ -240,6 +251,37 @@ cudaError_t launch_acoustic_stage(const AcousticParams<T> &p, int stage, cudaStr
     return cudaGetLastError();
 }
 
+template <typename T>
+struct HeviInit {
+    const T *rho;
+    T *S;
+    int nx, ny;
+    T rho0c[MAXNZ];
+};
+
+template <typename T>
+__global__ void hevi_init_kernel(const __grid_constant__ HeviInit<T> p) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= p.nx) return;
+    const size_t o = ((size_t)blockIdx.z * p.ny + blockIdx.y) * p.nx + i;
+    p.S[o] = p.rho[o] / p.rho0c[blockIdx.z] - T(1);
+}
+
+template <typename T>
+cudaError_t launch_hevi_init(const T *rho, const double *rho0c, T *S, int nx, int ny, int nz, cudaStream_t s) {
+    HeviInit<T> p;
+    p.rho = rho;
+    p.S = S;
+    p.nx = nx;
+    p.ny = ny;
+    for (int k = 0; k < MAXNZ; k++) p.rho0c[k] = k < nz ? (T)rho0c[k] : T(1);
+    dim3 grid((nx + 127) / 128, ny, nz);
+    hevi_init_kernel<T><<<grid, 128, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_hevi_init<float>(const float *, const double *, float *, int, int, int, cudaStream_t);
+template cudaError_t launch_hevi_init<double>(const double *, const double *, double *, int, int, int, cudaStream_t);
 template cudaError_t launch_acoustic_stage<float>(const AcousticParams<float> &, int, cudaStream_t);
 template cudaError_t launch_acoustic_stage<double>(const AcousticParams<double> &, int, cudaStream_t);
 

@@ -11,8 +11,16 @@ namespace asuca {
 // for every column).
 template <typename T>
 struct AcousticParams {
-    T *U, *V, *W, *S;        // the caller's fields ([nz][ny][nx]; W [nz+1][ny][nx])
+    T *U, *V, *W, *S;        // the short step's start state ([nz][ny][nx]; W [nz+1][ny][nx])
+    T *Uo, *Vo, *Wo, *So;    // where stage 2 writes the new state (the start state's arrays, or others)
     T *Us, *Vs, *Ws, *Ss;    // stage-1 values (workspace; Ws holds the stage-1 elimination only)
+    // stage 2, when Mu is set: the mass fluxes the density equation applies,
+    // (U*, V*, (1 - beta) W + beta W'), weighted by wacc, are added to (or, with
+    // acc_init, stored in) Mu, Mv and the interior faces of Mw; wlo = wacc (1 - beta),
+    // whi = wacc beta
+    T *Mu, *Mv, *Mw;
+    T wacc, wlo, whi;
+    int acc_init;
     int nx, ny, nz;
     unsigned plane;
     T rdx, rdy;
@@ -26,5 +34,10 @@ struct AcousticParams {
 
 template <typename T>
 cudaError_t launch_acoustic_stage(const AcousticParams<T> &p, int stage, cudaStream_t s);
+
+// s = rho / rho0_k - 1 of every cell (the acoustic density perturbation of the
+// advected density); rho0c: nz host values
+template <typename T>
+cudaError_t launch_hevi_init(const T *rho, const double *rho0c, T *S, int nx, int ny, int nz, cudaStream_t s);
 
 }  // namespace asuca

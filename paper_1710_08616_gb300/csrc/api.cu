@@ -315,12 +315,23 @@ template <typename T>
 asuca_status run_step_dataflow(asuca_grid *g, asuca_state *st, const void *tend, double dt, int nsteps,
                                char *ws, double *budgets, cudaStream_t s);
 
+// No work before the stages: the mass fluxes are the caller's.
+struct NoPre {
+    static constexpr bool none = true;
+    template <typename T>
+    cudaError_t operator()(int, int, StageParams<T> &) { return cudaSuccess; }
+};
+
 // zero_precip = false continues the precipitation total of a previous call
 // on the same workspace (the checkpointed forward runs one call per segment).
-template <typename T>
+// pre(n, -1, sp) runs at the start of step n and pre(n, stage, sp) before each
+// RK stage's launch; it may launch work of its own and set the stage's mass
+// fluxes (the nested acoustic short steps do both).
+template <typename T, typename Pre = NoPre>
 asuca_status run_step(asuca_grid *g, asuca_state *st, const void *tend, double dt, int nsteps,
-                      char *ws, double *budgets, cudaStream_t s, bool zero_precip = true) {
-    if (g->step_mode == 1 && zero_precip) return run_step_dataflow<T>(g, st, tend, dt, nsteps, ws, budgets, s);
+                      char *ws, double *budgets, cudaStream_t s, bool zero_precip = true, Pre pre = Pre()) {
+    if (g->step_mode == 1 && zero_precip && Pre::none)
+        return run_step_dataflow<T>(g, st, tend, dt, nsteps, ws, budgets, s);
     const StepLayout L = step_layout(g);
     const int F = g->F;
     T *yn[MAXF], *y1[MAXF], *y2[MAXF];
@@ -358,6 +369,7 @@ asuca_status run_step(asuca_grid *g, asuca_state *st, const void *tend, double d
     }
     for (int n = 0; n < nsteps; n++) {
         Range step_range("asuca step");
+        if ((e = pre(n, -1, sp)) != cudaSuccess) return ASUCA_ERR_CUDA;
         for (int stg = 0; stg < (fused ? 2 : 3); stg++) {
             Range stage_range(stg == 0 ? "RK stage 1" : (stg == 1 ? "RK stage 2" : "RK stage 3"));
             // stage 1 reads the caller's fields (TMA for interior tiles, cp.async at the
@@ -374,12 +386,14 @@ asuca_status run_step(asuca_grid *g, asuca_state *st, const void *tend, double d
                 sp.yout[f] = out[f];
             }
             sp.cdt = cdt[stg];
+            if ((e = pre(n, stg, sp)) != cudaSuccess) return ASUCA_ERR_CUDA;
             if ((e = timed(g, ASUCA_KERNEL_STAGE, s, [&] { return launch_stage<T>(sp, F, s); })) != cudaSuccess)
                 return ASUCA_ERR_CUDA;
         }
         cp.budgets = (budgets != nullptr) && (n == nsteps - 1);
         Range col_range(fused ? "RK stage 3 + column pass" : "column pass");
         if (fused) {
+            if ((e = pre(n, 2, sp)) != cudaSuccess) return ASUCA_ERR_CUDA;
             // stage 3 marching downward with the relaxation, sedimentation and
             // elimination of every column, then the bottom-up back substitution
             fp.s = sp;
@@ -1887,6 +1901,114 @@ void acoustic_tables(const asuca_grid *g, const asuca_acoustic_desc &a, double t
     }
 }
 
+// ---- acoustic short steps nested in the RK3 stages --------------------------
+
+// short steps of RK stage q (weights 1/3, 1/2, 1) when a long step has ns
+int hevi_short_steps(int ns, int q) {
+    const double frac = q == 0 ? 1.0 / 3.0 : (q == 1 ? 0.5 : 1.0);
+    const int n = (int)std::floor(frac * ns + 0.5);
+    return n < 1 ? 1 : n;
+}
+
+struct HeviLayout {
+    size_t Sn, Ua, Va, Wa, Sa, Mu, Mv, Mw, Us, Vs, Ws, Ss, total;
+};
+
+// the step workspace, then the acoustic arrays: s^n, a stage's integration
+// (Ua, Va, Wa, Sa), its mean mass fluxes (Mu, Mv, Mw) and the short steps'
+// stage-1 values (Us, Vs, Ws, Ss)
+HeviLayout hevi_layout(const asuca_grid *g) {
+    HeviLayout L;
+    const size_t es = elem_size(g), C = (size_t)g->cells * es, CW = ((size_t)g->cells + (size_t)g->plane) * es;
+    size_t off = step_layout(g).total;
+    size_t *slot[12] = {&L.Sn, &L.Ua, &L.Va, &L.Wa, &L.Sa, &L.Mu, &L.Mv, &L.Mw, &L.Us, &L.Vs, &L.Ws, &L.Ss};
+    const bool wface[12] = {false, false, false, true, false, false, false, true, false, false, true, false};
+    for (int q = 0; q < 12; q++) {
+        *slot[q] = off;
+        off = align_up(off + (wface[q] ? CW : C));
+    }
+    L.total = off;
+    return L;
+}
+
+// The work before each RK stage of a step with nested short steps: stage q
+// integrates the acoustic system from t^n (the caller's momenta, s^n from the
+// density) over its weight times dt in hevi_short_steps(ns, q) short steps,
+// accumulating the mean mass fluxes the scalar stage then advects with; stage
+// 3 integrates the caller's momenta in place (the new momentum state).
+template <typename T>
+struct HeviPre {
+    static constexpr bool none = false;
+    asuca_grid *g;
+    asuca_state *st;
+    asuca_acoustic_desc a;
+    int ns;
+    double dt;
+    cudaStream_t s;
+    char *ws;
+    T *s_final;
+    HeviLayout L;
+
+    T *at(size_t off) const { return (T *)(ws + off); }
+
+    cudaError_t operator()(int, int stg, StageParams<T> &sp) {
+        if (stg < 0)
+            return timed(g, ASUCA_KERNEL_ACOUSTIC, s, [&] {
+                return launch_hevi_init<T>((const T *)st->rho, a.rho0c, at(L.Sn), g->d.nx, g->d.ny, g->d.nz, s);
+            });
+        const double w = stg == 0 ? dt / 3.0 : (stg == 1 ? dt / 2.0 : dt);
+        const int nq = hevi_short_steps(ns, stg);
+        const double h = w / nq;
+        T *U0 = (T *)const_cast<void *>(st->mu), *V0 = (T *)const_cast<void *>(st->mv),
+          *W0 = (T *)const_cast<void *>(st->mw);
+        T *Uq = stg < 2 ? at(L.Ua) : U0, *Vq = stg < 2 ? at(L.Va) : V0, *Wq = stg < 2 ? at(L.Wa) : W0;
+        T *Sq = (stg == 2 && s_final) ? s_final : at(L.Sa);
+        AcousticParams<T> p[2];
+        for (int q = 0; q < 2; q++) {
+            std::memset(&p[q], 0, sizeof(p[q]));
+            p[q].Us = at(L.Us);
+            p[q].Vs = at(L.Vs);
+            p[q].Ws = at(L.Ws);
+            p[q].Ss = at(L.Ss);
+            p[q].Uo = Uq;
+            p[q].Vo = Vq;
+            p[q].Wo = Wq;
+            p[q].So = Sq;
+            p[q].nx = g->d.nx;
+            p[q].ny = g->d.ny;
+            p[q].nz = g->d.nz;
+            p[q].plane = (unsigned)g->plane;
+            p[q].rdx = (T)(1.0 / g->d.dx);
+            p[q].rdy = (T)(1.0 / g->d.dy);
+            acoustic_tables<T>(g, a, q == 0 ? 0.5 * h : h, p[q]);
+        }
+        p[1].Mu = at(L.Mu);
+        p[1].Mv = at(L.Mv);
+        p[1].Mw = at(L.Mw);
+        p[1].wacc = (T)(1.0 / nq);
+        p[1].wlo = (T)((1.0 - a.beta) / nq);
+        p[1].whi = (T)(a.beta / nq);
+        for (int m = 0; m < nq; m++) {
+            for (int q = 0; q < 2; q++) {
+                p[q].U = m == 0 ? U0 : Uq;
+                p[q].V = m == 0 ? V0 : Vq;
+                p[q].W = m == 0 ? W0 : Wq;
+                p[q].S = m == 0 ? at(L.Sn) : Sq;
+            }
+            p[1].acc_init = m == 0;
+            for (int q = 0; q < 2; q++) {
+                const cudaError_t e =
+                    timed(g, ASUCA_KERNEL_ACOUSTIC, s, [&] { return launch_acoustic_stage<T>(p[q], q + 1, s); });
+                if (e != cudaSuccess) return e;
+            }
+        }
+        sp.mu = at(L.Mu);
+        sp.mv = at(L.Mv);
+        sp.mw = at(L.Mw);
+        return cudaSuccess;
+    }
+};
+
 template <typename T>
 cudaError_t run_acoustic(const asuca_grid *g, void *U, void *V, void *W, void *S, const asuca_acoustic_desc &a,
                          double h, int nshort, char *ws, cudaStream_t s) {
@@ -1900,6 +2022,10 @@ cudaError_t run_acoustic(const asuca_grid *g, void *U, void *V, void *W, void *S
         p[q].V = (T *)V;
         p[q].W = (T *)W;
         p[q].S = (T *)S;
+        p[q].Uo = (T *)U;
+        p[q].Vo = (T *)V;
+        p[q].Wo = (T *)W;
+        p[q].So = (T *)S;
         p[q].Us = (T *)ws;
         p[q].Vs = (T *)(ws + fb);
         p[q].Ss = (T *)(ws + 2 * fb);
@@ -1947,6 +2073,36 @@ asuca_status asuca_acoustic_steps(asuca_grid *g, void *U, void *V, void *W, void
                               ? run_acoustic<double>(g, U, V, W, S, *desc, dtau, nshort, (char *)workspace, s)
                               : run_acoustic<float>(g, U, V, W, S, *desc, dtau, nshort, (char *)workspace, s);
     return cuda_status(e);
+}
+
+size_t asuca_hevi_workspace_bytes(const asuca_grid *g) { return g ? hevi_layout(g).total : 0; }
+
+asuca_status asuca_step_hevi(asuca_grid *g, asuca_state *st, const void *tend, double dt, int nsteps,
+                             const asuca_acoustic_desc *desc, int nshort, void *s_final, void *workspace,
+                             size_t workspace_bytes, double *budgets, void *cuda_stream) {
+    if (!g || !state_ok(g, st) || nsteps < 0 || !std::isfinite(dt) || dt < 0.0 || nshort < 1 || !desc ||
+        !desc->rho0c || !desc->rho0f || !std::isfinite(desc->cs2) || desc->cs2 <= 0.0 ||
+        !(desc->beta >= 0.5 && desc->beta <= 1.0))
+        return ASUCA_ERR_ARG;
+    const int nz = g->d.nz;
+    for (int k = 0; k < nz; k++)
+        if (!(desc->rho0c[k] > 0.0) || !std::isfinite(desc->rho0c[k])) return ASUCA_ERR_ARG;
+    for (int f = 1; f < nz; f++)
+        if (!(desc->rho0f[f] > 0.0) || !std::isfinite(desc->rho0f[f])) return ASUCA_ERR_ARG;
+    asuca_status prev = take_status(g);
+    if (prev != ASUCA_OK) return prev;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    g->last_stream = s;
+    if (nsteps == 0 && !budgets) return ASUCA_OK;
+    if (!workspace || ((uintptr_t)workspace % ALIGN) != 0 || workspace_bytes < hevi_layout(g).total)
+        return ASUCA_ERR_WORKSPACE;
+    char *ws = (char *)workspace;
+    if (g->d.prec == ASUCA_FP64) {
+        HeviPre<double> pre{g, st, *desc, nshort, dt, s, ws, (double *)s_final, hevi_layout(g)};
+        return run_step<double, HeviPre<double>>(g, st, tend, dt, nsteps, ws, budgets, s, true, pre);
+    }
+    HeviPre<float> pre{g, st, *desc, nshort, dt, s, ws, (float *)s_final, hevi_layout(g)};
+    return run_step<float, HeviPre<float>>(g, st, tend, dt, nsteps, ws, budgets, s, true, pre);
 }
 
 asuca_status asuca_profile_read(asuca_grid *g, double *ms, int *launches, int nkinds) {
