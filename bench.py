@@ -165,6 +165,53 @@ def _max_over_ranks(ws, v):
     return float(t.item())
 
 
+def _gpu_local_cpus(gpu_id: str):
+    """The CPUs of the GPU's host NUMA node (its PCI function's local_cpulist),
+    or None when nvidia-smi or sysfs do not say."""
+    try:
+        out = subprocess.run(["nvidia-smi", "-i", gpu_id, "--query-gpu=pci.bus_id", "--format=csv,noheader"],
+                             capture_output=True, text=True, timeout=20).stdout.strip().splitlines()[0].lower()
+        dom, rest = out.split(":", 1)
+        with open(f"/sys/bus/pci/devices/{int(dom, 16):04x}:{rest}/local_cpulist") as fh:
+            txt = fh.read().strip()
+        cpus = set()
+        for part in txt.split(","):
+            a, _, b = part.partition("-")
+            cpus.update(range(int(a), int(b or a) + 1))
+        return cpus & os.sched_getaffinity(0) or None
+    except Exception:
+        return None
+
+
+def _link_gbs(dev, nbytes=1 << 30, reps=3):
+    """Pinned host <-> device copy rates (GB/s): host to device, device to
+    host, and each direction while both run at once (two streams)."""
+    import torch
+    h = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    h2 = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    d = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    d2 = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    sa, sb = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def run(pairs):
+        best = None
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for (dst, src), sx in zip(pairs, (sa, sb)):
+                with torch.cuda.stream(sx):
+                    dst.copy_(src, non_blocking=True)
+            torch.cuda.synchronize()
+            el = time.perf_counter() - t0
+            best = el if best is None else min(best, el)
+        return nbytes / best / 1e9
+
+    out = {"h2d": run([(d, h)]), "d2h": run([(h, d)])}
+    out["each_way_concurrent"] = run([(d, h), (h2, d2)])
+    del h, h2, d, d2
+    return out
+
+
 def cpu_oracle_rate(min_seconds=10.0, nx=256, ny=256, steps_cap=50):
     """The FP64 oracle as it stands on the host cores: 256x256x58, 8 tracers."""
     import gen
@@ -330,15 +377,55 @@ def adjoint_cost(asuca, dev, reps=3):
     return out
 
 
-def precision_report(asuca, dev):
+PRECISION = "precision_256x256x58"
+
+
+def _oracle_precision_job(path, threads):
+    """Child process: the oracle's 100 steps of the precision workload, saved to path (.npy)."""
+    import gen
+    import oracle
+    if threads:
+        oracle.set_threads(threads)
+    case = gen.make_config_case(PRECISION)
+    g = oracle.Grid.from_case(case)
+    Y, _ = oracle.step(g, case.state(), case.mu, case.mv, case.mw, case.dt, gen.CONFIGS[PRECISION]["nsteps"])
+    np.save(path, Y)
+
+
+def start_oracle_precision():
+    """Start the oracle's run of the precision workload in a spawned process
+    (the host cores are otherwise idle while the GPU reports run); returns a
+    handle for precision_report."""
+    import multiprocessing as mp
+    import tempfile
+    fd, path = tempfile.mkstemp(prefix="asuca_oracle_precision_", suffix=".npy")
+    os.close(fd)
+    threads = max(1, (os.cpu_count() or 2) - 2)     # leave the launching thread a core
+    proc = mp.get_context("spawn").Process(target=_oracle_precision_job, args=(path, threads))
+    proc.start()
+    return {"proc": proc, "path": path, "threads": threads, "t0": time.perf_counter()}
+
+
+def _field_errors(a, b, names):
+    out = {}
+    for f, nm in enumerate(names):
+        d = a[f] - b[f]
+        out[nm] = {"rel_l2": float(np.linalg.norm(d) / np.linalg.norm(b[f])),
+                   "rel_max": float(np.abs(d).max() / np.abs(b[f]).max())}
+    return out
+
+
+def precision_report(asuca, dev, oracle_job=None):
     """256x256x58, 6 tracers, 100 steps from the same initial state in FP32-mixed
-    and in FP64 on the GPU: per-field relative L2 and max error of FP32 against
-    FP64, and the drift of the FP64 budgets over the run (mass; each tracer plus
-    its precipitation for the sedimenting one) in both precisions."""
-    import numpy as np
+    and in FP64 on the GPU and in the FP64 oracle: per-field relative L2 and max
+    error of both GPU paths against the oracle (rho, rho*theta, each rho*q_n and
+    theta' = theta - theta_ref, the perturbation that rho*theta's magnitude
+    hides), FP32 against the GPU FP64 path, and the drift of the FP64 budgets
+    over the run (mass; each tracer plus its precipitation for the sedimenting
+    one) in both precisions."""
     import torch
     import gen
-    name = "precision_256x256x58"
+    name = PRECISION
     case = gen.make_config_case(name)
     nsteps = gen.CONFIGS[name]["nsteps"]
     res, buds, times = {}, {}, {}
@@ -356,11 +443,7 @@ def precision_report(asuca, dev):
         res[label] = st.fields().double().cpu().numpy()
         buds[label] = (b0, b1.cpu().numpy())
     names = ["rho", "rhotheta"] + [f"rhoq{n + 1}" for n in range(case.ntracers)]
-    errs = {}
-    for f, nm in enumerate(names):
-        d = res["fp32"][f] - res["fp64"][f]
-        errs[nm] = {"rel_l2": float(np.linalg.norm(d) / np.linalg.norm(res["fp64"][f])),
-                    "rel_max": float(np.abs(d).max() / np.abs(res["fp64"][f]).max())}
+    errs = _field_errors(res["fp32"], res["fp64"], names)
     drift = {}
     F = case.nfields
     for label, (b0, b1) in buds.items():
@@ -368,8 +451,34 @@ def precision_report(asuca, dev):
         tr[-1] += b1[F]      # the sedimenting (last) tracer: mass aloft + precipitation
         drift[label] = {"mass": float((b1[0] - b0[0]) / b0[0]),
                         "tracers_plus_precip": [float(v) for v in (tr - b0[2:F]) / b0[2:F]]}
-    return {"workload": name, "nsteps": nsteps, "fp32_vs_fp64_gpu": errs, "budget_drift": drift,
-            "ms_per_step": times, "fp32_over_fp64_speedup": times["fp64"] / times["fp32"]}
+    out = {"workload": name, "nsteps": nsteps, "fp32_vs_fp64_gpu": errs, "budget_drift": drift,
+           "ms_per_step": times, "fp32_over_fp64_speedup": times["fp64"] / times["fp32"]}
+    if oracle_job is not None:
+        oracle_job["proc"].join()
+        if oracle_job["proc"].exitcode == 0:
+            ref = np.load(oracle_job["path"])
+            zf = np.concatenate([[0.0], np.cumsum(case.dz)])
+            thref = (300.0 + 0.004 * (zf[:-1] + 0.5 * case.dz))[:, None, None]
+            prime = lambda Y: Y[1] / Y[0] - thref
+
+            def vs_oracle(Y):
+                e = _field_errors(Y, ref, names)
+                d = prime(Y) - prime(ref)
+                e["theta_prime"] = {"rel_l2": float(np.linalg.norm(d) / np.linalg.norm(prime(ref))),
+                                    "rel_max": float(np.abs(d).max() / np.abs(prime(ref)).max())}
+                return e
+
+            out["fp32_vs_oracle"] = vs_oracle(res["fp32"])
+            out["fp64_vs_oracle"] = vs_oracle(res["fp64"])
+            out["oracle"] = {"threads": oracle_job["threads"],
+                             "wall_s_incl_waiting": time.perf_counter() - oracle_job["t0"]}
+        else:
+            out["oracle"] = {"failed": f"exit code {oracle_job['proc'].exitcode}"}
+        try:
+            os.remove(oracle_job["path"])
+        except OSError:
+            pass
+    return out
 
 
 def layout_ablation(asuca, dev, reps=10):
@@ -460,6 +569,124 @@ def damping_report(asuca, dev, reps=10, nx=None, precs=("fp32", "fp64")):
     return out
 
 
+def open_report(asuca, dev, case, reps=3):
+    """Open lateral boundaries on the 1024x1024x58, 8-tracer state, FP32, against
+    the periodic step on the same state:
+      * limited area (asuca_step_open): every stage's ghosts filled from two
+        boundary datasets interpolated in time (gen.make_open_boundary), the
+        outer faces' own fluxes; per step three ghost fills and a prepare
+        launch more than the periodic step;
+      * decomposed: the domain as 2 x 2 blocks of 512 x 512 on this GPU, halos
+        of width 2 exchanged by device copies before every stage
+        (distributed.step_decomposed: pack, copy, unpack); the time a
+        multi-GPU run would add for the exchange is the copies' time here plus
+        the link's."""
+    import torch
+    import gen
+    from paper_1710_08616_gb300.distributed import Block, Decomposition, step_decomposed
+    prec, dt_ = asuca.FP32_MIXED, torch.float32
+    t = lambda a: torch.as_tensor(np.array(a, copy=True)).to(device=dev, dtype=dt_).contiguous()
+
+    def best(fn, nsteps):
+        fn(1)
+        torch.cuda.synchronize()
+        r = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn(nsteps)
+            e1.record()
+            torch.cuda.synchronize()
+            r.append(e0.elapsed_time(e1) / nsteps)
+        return min(r)
+
+    g = asuca.Grid.from_case(case, prec=prec)
+    st = asuca.State.from_case(case, prec=prec, device=dev)
+    ws = g.workspace(device=dev)
+    t_per = best(lambda n: asuca.step(g, st, case.dt, n, workspace=ws), 5)
+    del ws
+    mu_x, mv_x = gen.extend_fluxes(case.mu, case.mv)
+    sto = asuca.State(st.rho, st.rhotheta, st.rhoq, t(mu_x), t(mv_x), st.mw)
+    b0, b1 = (t(b) for b in gen.make_open_boundary(case, seed=case.seed + 1))
+    wso = asuca.open_workspace(g, device=dev)
+    t_open = best(lambda n: asuca.step_open(g, sto, case.dt, n, b0, bnd1=b1, tratio=0.3, workspace=wso), 5)
+    assert asuca.get_status(g) == asuca.OK
+    del sto, wso, b0, b1, mu_x, mv_x
+    torch.cuda.empty_cache()
+    d = Decomposition(case.nx, case.ny, 2, 2)
+    blocks = {}
+    for r in range(d.nblocks):
+        rx, ry = d.coords(r)
+        sd = gen.subdomain(case, 2, 2, rx, ry)
+        gb = asuca.Grid(sd["nx"], sd["ny"], case.nz, case.ntracers, case.dz, case.dx, case.dy, prec=prec)
+        Y = sd["Y"]
+        blocks[r] = Block(gb, asuca.State(t(Y[0]), t(Y[1]), t(Y[2:]), t(sd["mu_x"]), t(sd["mv_x"]), t(sd["mw"])))
+    t_dec = best(lambda n: step_decomposed(blocks, d, case.dt, n), 3)
+    for b in blocks.values():
+        assert asuca.get_status(b.grid) == asuca.OK
+    halo = sum(asuca.halo_count(b.grid) for b in blocks.values()) * 4
+    del blocks
+    torch.cuda.empty_cache()
+    C = case.cells
+    return {"workload": "large_1024x1024x58 fp32", "periodic_ms_per_step": t_per,
+            "limited_area": {"ms_per_step": t_open, "cell_updates_per_s": C / (t_open * 1e-3),
+                             "over_periodic": t_open / t_per},
+            "decomposed_2x2_one_gpu": {"ms_per_step": t_dec, "cell_updates_per_s": C / (t_dec * 1e-3),
+                                       "over_periodic": t_dec / t_per,
+                                       "halo_bytes_per_stage": halo,
+                                       "exchange": "device copies between the blocks' halo buffers"}}
+
+
+def hevi_report(asuca, dev, case, reps=3):
+    """The long step with nested acoustic short steps (asuca_step_hevi) on the
+    1024x1024x58 grid with 8 tracers: 12 s long step, 6 short steps (2, 3 and 6
+    per RK stage: 11 short steps per long step), FP32 and FP64.  Algorithmic
+    values per cell and long step: the stage model (10 F + 8) plus, per short
+    step, the 18 of the acoustic kernels and 8 of the mean-flux accumulation,
+    plus 2 for the acoustic density perturbation at the start: 396 at F = 10."""
+    import torch
+    import gen
+    peak, _ = _peaks()
+    Y, U, V, W, r0c, r0f, dt, ns = gen.make_hevi_state(case)
+    A = gen.ACOUSTIC
+    nshort_total = sum(max(1, int(np.floor(fr * ns + 0.5))) for fr in (1 / 3, 1 / 2, 1.0))
+    F = case.nfields
+    values = (10 * F + 8) + 26 * nshort_total + 2
+    out = {"workload": "hevi_1024x1024x58", "dt_s": dt, "short_steps_per_long_step": nshort_total,
+           "algorithmic_values_per_cell": values}
+    names = {asuca.KERNEL_STAGE: "stage", asuca.KERNEL_COLUMN: "column", asuca.KERNEL_REDUCE: "budget_reduce",
+             asuca.KERNEL_STAGE_COLUMN: "stage3_column", asuca.KERNEL_ACOUSTIC: "acoustic"}
+    for name, prec, dt_ in (("fp32", asuca.FP32_MIXED, torch.float32), ("fp64", asuca.FP64, torch.float64)):
+        t = lambda a: torch.as_tensor(np.array(a, copy=True)).to(device=dev, dtype=dt_).contiguous()
+        g = asuca.Grid.from_case(case, prec=prec)
+        st = asuca.State(t(Y[0]), t(Y[1]), t(Y[2:]), t(U), t(V), t(W))
+        ws = torch.empty(asuca.hevi_workspace_bytes(g), dtype=torch.uint8, device=dev)
+        nsteps = 3 if name == "fp32" else 1
+        asuca.step_hevi(g, st, dt, 1, r0c, r0f, A["cs2"], A["beta"], ns, workspace=ws)
+        torch.cuda.synchronize()
+        best, prof = None, None
+        for _ in range(reps):
+            asuca.profile_enable(g, True)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            asuca.step_hevi(g, st, dt, nsteps, r0c, r0f, A["cs2"], A["beta"], ns, workspace=ws)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / nsteps
+            p_ = asuca.profile_read(g)
+            asuca.profile_enable(g, False)
+            if best is None or ms < best:
+                best, prof = ms, p_
+        assert asuca.get_status(g) == asuca.OK
+        s = dt_.itemsize
+        out[name] = {"ms_per_step": best, "cell_updates_per_s": case.cells / (best * 1e-3),
+                     "frac": values * s * case.cells / (best * 1e-3) / 1e9 / peak,
+                     "kernels_ms_per_step": {names.get(k, str(k)): v[0] / nsteps for k, v in prof.items()}}
+        del st, ws
+        torch.cuda.empty_cache()
+    return out
+
+
 def acoustic_report(asuca, dev, reps=5, nx=None, precs=("fp32", "fp64")):
     """HEVI acoustic short steps (asuca_acoustic_steps) on the 1024x1024x58 grid,
     6 short steps of 2 s per call, FP32 and FP64.  A short step is two launches,
@@ -546,7 +773,12 @@ def ensemble_throughput(asuca, dev, nsteps=10, reps=3):
     seq()
     t_ens, t_seq = timed(ens), timed(seq)
     assert asuca.get_status(grids[0]) == asuca.OK
+    peak, _ = _peaks()
+    F = cases[0].nfields
+    frac = (10 * F + 8) * 4 * cells * nsteps / (t_ens * 1e-3) / 1e9 / peak
     return {"workload": "ensemble_32x_64to320x58", "members": len(cases), "cells": cells, "nsteps_per_call": nsteps,
+            "frac": frac, "frac_model": f"(10 F + 8) x 4 B = {(10 * F + 8) * 4} B per member cell and step "
+                                        "over the measured HBM peak",
             "sizes": [c.nx for c in cases], "ensemble_tile_rows": tune["best"]["ensemble_tile_rows"],
             "ensemble_cell_updates_per_s": cells * nsteps / (t_ens * 1e-3),
             "sequential_members_cell_updates_per_s": cells * nsteps / (t_seq * 1e-3),
@@ -669,6 +901,13 @@ def run_ours(args):
         # of step n - 2, which chains copy in, step and copy out); the timed
         # region spans the first copy in to the last copy out.
         names = ("rho", "rhotheta", "rhoq", "mu", "mv", "mw")
+        # pinned buffers on the GPU's own host NUMA node: the allocating thread
+        # runs on that node's CPUs, so the pages land there
+        aff0 = os.sched_getaffinity(0)
+        local_cpus = _gpu_local_cpus(gpu_id if rank == 0 else str(local))
+        if local_cpus:
+            os.sched_setaffinity(0, local_cpus)
+        link = _link_gbs(dev)
         host = {k: getattr(st, k).cpu().pin_memory() for k in names}
         hout = {k: torch.empty_like(host[k]).pin_memory() for k in ("rho", "rhotheta", "rhoq")}
         hbud = torch.empty(F + 1, dtype=torch.float64).pin_memory()
@@ -751,7 +990,12 @@ def run_ours(args):
         e2e = {"value": world * C * ne / (ems * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "steps": ne, "ms_per_step": ems / ne,
                "overlap": f"copies in ({NCOPY} stream(s)), the step, copies out ({NCOPY} stream(s)); "
-                          f"{NB} device buffer sets"}
+                          f"{NB} device buffer sets",
+               "link_gbs": link,
+               "link_bound_ms_per_step": max(h2d, d2h) / (link["each_way_concurrent"] * 1e9) * 1e3,
+               "host_numa": ({"bound_to_gpu_local_cpus": len(local_cpus)} if local_cpus
+                             else {"bound_to_gpu_local_cpus": None, "why": "GPU's local CPUs not found"})}
+        os.sched_setaffinity(0, aff0)
         del host, hout, bufs
     del st, ws_t
     torch.cuda.empty_cache()
@@ -778,9 +1022,17 @@ def run_ours(args):
                             "peak_source": "recipe unit counts and maximum SM clock"}
         del st64, ws64
 
-    precision = None
-    if not args.no_precision:
-        precision = precision_report(asuca, dev)
+    # the oracle's run of the precision workload, on the host cores while the
+    # GPU reports below run (started after the headline and end-to-end timings)
+    ojob = None
+    if not args.no_precision and rank == 0 and world == 1:
+        ojob = start_oracle_precision()
+    open_rep = None
+    if not args.no_open:
+        open_rep = open_report(asuca, dev, case)
+    hevi = None
+    if not args.no_hevi:
+        hevi = hevi_report(asuca, dev, case)
     adjoint = None
     if not args.no_adjoint:
         adjoint = adjoint_cost(asuca, dev)
@@ -796,6 +1048,9 @@ def run_ours(args):
     acoustic = None
     if not args.no_acoustic:
         acoustic = acoustic_report(asuca, dev)
+    precision = None
+    if not args.no_precision:
+        precision = precision_report(asuca, dev, ojob)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -812,7 +1067,8 @@ def run_ours(args):
                           "parallelism": f"{world} independent replica(s), one per GPU"},
                "clocks": clocks, "gpu_launches": sum(n for _t, n in (prof or {}).values()), "roofline": roofline,
                "e2e": e2e, "fp64": fp64, "precision": precision, "adjoint": adjoint, "ensemble": ensemble,
-               "layout_ablation": layout, "damping": damping, "acoustic": acoustic,
+               "layout_ablation": layout, "damping": damping, "acoustic": acoustic, "open": open_rep,
+               "hevi": hevi,
                "fp32_over_fp64_speedup": (value / fp64["value"]) if fp64 else None,
                "cpu_baseline": cpu}
         print(json.dumps(out), flush=True)
@@ -844,6 +1100,8 @@ def main():
     ap.add_argument("--no-layout", action="store_true")
     ap.add_argument("--no-damping", action="store_true")
     ap.add_argument("--no-acoustic", action="store_true")
+    ap.add_argument("--no-open", action="store_true")
+    ap.add_argument("--no-hevi", action="store_true")
     ap.add_argument("--acoustic-probe", choices=["fp32", "fp64"], default=None,
                     help="time the acoustic short steps alone on the nx x nx x 58 grid in one precision and "
                          "exit (a small launch sequence for profiler captures)")
