@@ -70,7 +70,8 @@ __global__ void __launch_bounds__(256) adj_stage_kernel(const __grid_constant__ 
     const int cc = (row + 2) * TW + lane + 2;       // the thread's cell in the tile
     const unsigned col = (unsigned)(j * nx + i);
     const unsigned own = kb + col;
-    const unsigned sown = (unsigned)k * (unsigned)p.ys_plane + (unsigned)((j + p.ys_oy) * p.ys_pitch + i + p.ys_ox);
+    const unsigned sown = (unsigned)k * (unsigned)p.ys_plane +
+                          (unsigned)((j + p.ys_oy) * p.ys_pitch + (i + p.ys_ox) * p.ys_xs);
     // the cell's own column: k faces a = k-2 .. k+1
     T mzf[4];
     T rr = T(1);

@@ -7,9 +7,9 @@ namespace asuca {
 
 template <typename T>
 struct AdjStageParams {
-    const T *ys[MAXF];            // stage input Y (element (k,j,i) at k*ys_plane + (j+ys_oy)*ys_pitch + i+ys_ox)
+    const T *ys[MAXF];            // stage input Y (element (k,j,i) at k*ys_plane + (j+ys_oy)*ys_pitch + (i+ys_ox)*ys_xs)
     long long ys_pitch, ys_plane;
-    int ys_ox, ys_oy;
+    int ys_ox, ys_oy, ys_xs;
     int ys_phi;                   // 1: fields 1.. of ys hold phi (padded stage buffers); 0: rho*phi
     const T *lam[MAXF];           // adjoint of the stage output, [nz][ny][nx]
     T cs;                         // c_s * dt

@@ -110,9 +110,12 @@ size_t padded_field_elems(const asuca_grid *g) {
     return (size_t)g->d.nz * (g->d.ny + 4) * padded_pitch(g->d.nx);
 }
 
+// elements of a padded stage buffer: the F fields in pairs (pair layout)
+size_t padded_state_elems(const asuca_grid *g) { return 2 * (size_t)pair_count(g->F) * padded_field_elems(g); }
+
 StepLayout step_layout(const asuca_grid *g) {
     StepLayout L;
-    const size_t state = (size_t)g->F * padded_field_elems(g) * elem_size(g);
+    const size_t state = padded_state_elems(g) * elem_size(g);
     size_t off = 0;
     L.ystar = off;
     off = align_up(off + state);
@@ -167,12 +170,22 @@ void field_ptrs(const asuca_grid *g, void *rho, void *rhotheta, void *rhoq, T **
     for (int f = g->F; f < MAXF; f++) out[f] = nullptr;
 }
 
-// field bases (padded origin) of a padded stage buffer in the workspace
+// per-field views of a padded stage buffer in the workspace (pair layout):
+// field f's element (k, j, i) at view[f][k plev + (j + 2) prow + 2 (i + 4)];
+// field 1 (pair 0, lane 0) is the buffer's base
 template <typename T>
 void workspace_fields(const asuca_grid *g, char *ws, size_t off, T **out) {
-    for (int f = 0; f < g->F; f++) out[f] = (T *)(ws + off) + (size_t)f * padded_field_elems(g);
+    const long long P = padded_pitch(g->d.nx);
+    for (int f = 0; f < g->F; f++) {
+        const int pos = pair_pos(f, g->F);
+        out[f] = (T *)(ws + off) + (pos / 2) * 2 * P + (pos % 2);
+    }
     for (int f = g->F; f < MAXF; f++) out[f] = nullptr;
 }
+
+// row and level strides (elements) of the pair layout
+long long pair_row(const asuca_grid *g) { return 2LL * pair_count(g->F) * padded_pitch(g->d.nx); }
+long long pair_level(const asuca_grid *g) { return pair_row(g) * (g->d.ny + 4); }
 
 template <typename T>
 StageParams<T> stage_params(const asuca_grid *g, const asuca_state *fl, const void *tend) {
@@ -192,6 +205,8 @@ StageParams<T> stage_params(const asuca_grid *g, const asuca_state *fl, const vo
     p.ty = g->stage_ty;
     p.opitch = padded_pitch(g->d.nx);
     p.oplane = (long long)(g->d.ny + 4) * p.opitch;
+    p.prow = pair_row(g);
+    p.plev = pair_level(g);
     p.rdx = (T)(1.0 / g->d.dx);
     p.rdy = (T)(1.0 / g->d.dy);
     for (int k = 0; k < g->d.nz; k++) p.rdz[k] = (T)(1.0 / g->dz[k]);
@@ -581,7 +596,7 @@ AdjLayout adj_layout(const asuca_grid *g, int nsteps, int K) {
     AdjLayout L;
     const size_t s = elem_size(g);
     L.ustate = (size_t)g->F * g->cells * s;
-    L.pstate = (size_t)g->F * padded_field_elems(g) * s;
+    L.pstate = padded_state_elems(g) * s;
     L.nbranch_step = (size_t)3 * (g->F - 1) * g->cells;
     L.ncp = nsteps > 0 ? (nsteps + K - 1) / K : 0;
     L.slots = (long long)adj_col_grid(g) * COL_TPB;
@@ -777,11 +792,13 @@ asuca_status run_adjoint(asuca_grid *g, const asuca_state *init, const void *ten
                     block_fields<T>(g, segYn(q), (T **)ap.ys);
                     ap.ys_pitch = g->d.nx;
                     ap.ys_plane = g->plane;
+                    ap.ys_xs = 1;
                     ap.ys_ox = ap.ys_oy = 0;
                 } else {
                     workspace_fields<T>(g, stg == 1 ? segY1(q) : segY2(q), 0, (T **)ap.ys);
-                    ap.ys_pitch = padded_pitch(g->d.nx);
-                    ap.ys_plane = (long long)(g->d.ny + 4) * ap.ys_pitch;
+                    ap.ys_pitch = pair_row(g);
+                    ap.ys_plane = pair_level(g);
+                    ap.ys_xs = 2;
                     ap.ys_ox = 4;
                     ap.ys_oy = 2;
                     ap.ys_phi = 1;
@@ -930,7 +947,7 @@ bool ens_layout(asuca_grid *const *grids, int M, EnsLayout *L) {
     L->precip.resize(M);
     int maxcol = 0;
     for (int m = 0; m < M; m++) {
-        const size_t ps = (size_t)grids[m]->F * padded_field_elems(grids[m]) * elem_size(grids[m]);
+        const size_t ps = padded_state_elems(grids[m]) * elem_size(grids[m]);
         L->ystar[m] = off;
         off = align_up(off + ps);
         L->ystar2[m] = off;
@@ -1052,7 +1069,7 @@ asuca_status ens_enqueue(asuca_grid *const *grids, asuca_state *states, const do
 // buffers hold phi* and phi**) followed by a third padded buffer for phi^n.
 size_t open_b0_offset(const asuca_grid *g) { return step_layout(g).total; }
 size_t open_total(const asuca_grid *g) {
-    return align_up(open_b0_offset(g) + (size_t)g->F * padded_field_elems(g) * elem_size(g));
+    return align_up(open_b0_offset(g) + padded_state_elems(g) * elem_size(g));
 }
 size_t open_buffer_offset(const asuca_grid *g, int b) {
     const StepLayout L = step_layout(g);
@@ -1081,8 +1098,8 @@ OpenParams<T> open_params(const asuca_grid *g, char *ws, int b) {
     OpenParams<T> p;
     std::memset(&p, 0, sizeof(p));
     workspace_fields<T>(g, ws, open_buffer_offset(g, b), p.pad);
-    p.pitch = padded_pitch(g->d.nx);
-    p.pplane = (long long)(g->d.ny + 4) * p.pitch;
+    p.pitch = pair_row(g);
+    p.pplane = pair_level(g);
     p.nx = g->d.nx;
     p.ny = g->d.ny;
     p.nz = g->d.nz;
@@ -1274,7 +1291,7 @@ asuca_status asuca_init_grid(const asuca_grid_desc *desc, asuca_grid **out) {
     // element offsets within one field (caller layout with nz + 1 levels of MW,
     // and the padded stage buffers) are 32-bit in the kernels
     if ((long long)d.nx * d.ny * (d.nz + 1) >= (1LL << 32) ||
-        padded_pitch(d.nx) * (d.ny + 4) * (long long)d.nz >= (1LL << 32))
+        2LL * pair_count(2 + d.ntracers) * padded_pitch(d.nx) * (d.ny + 4) * (long long)d.nz >= (1LL << 32))
         return ASUCA_ERR_UNSUPPORTED;
 
     asuca_grid *g = new (std::nothrow) asuca_grid;

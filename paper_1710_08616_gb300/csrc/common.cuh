@@ -22,9 +22,14 @@ constexpr int MAXNZ = ASUCA_MAX_NZ;
 // ------------------------------------------------------------------ params
 
 // Tile, ring depth and shared-memory layout of the stage kernel.  A CTA is
-// 32 x TY columns (one warp per row); a ring slot holds every field of one
-// level plane of the tile with a 4-column halo in i (2 used; the TMA box must
-// start on a 16-byte boundary) and a 2-row halo in j.
+// 32 x TY columns (one warp per row); a ring slot holds one level plane of the
+// tile with a 4-column halo in i (2 used; the TMA box must start on a 16-byte
+// boundary) and a 2-row halo in j, in one of two layouts:
+//   raw (the caller's fields, stage 1): [F][SY][SX], every field a plane;
+//   pair (the library's padded stage buffers): [SY][NPF][SX][2], the phi
+//     fields in pairs (1, 2), (3, 4), ... with a pair's two values of a cell
+//     side by side, so one 2-element load fetches both operands of a packed
+//     operation.
 template <typename T, int NF, int TYV = 8>
 struct StageShape {
     static constexpr int TX = 32;
@@ -34,23 +39,33 @@ struct StageShape {
     static constexpr int MIN_BLOCKS = sizeof(T) == 8 ? 1 : (TYV >= 16 ? 1 : (TYV >= 8 ? 2 : 3));
     static constexpr int SX = TX + 8;
     static constexpr int SY = TY + 4;
-    static constexpr int NT = NF - 1;
-    static constexpr int SLOT_RAW = NF * SY * SX;
+    static constexpr int NT = NF - 1;                    // transported fields (phi)
+    static constexpr int NPF = (NT + 1) / 2;             // pairs holding them
+    static constexpr int SLOT_RAW = NF * SY * SX;        // >= 2 NPF SY SX, the pair layout's slot
     static constexpr int SLOT_ELEMS = (SLOT_RAW * (int)sizeof(T) + 127) / 128 * 128 / (int)sizeof(T);
     static constexpr unsigned TX_BYTES = (unsigned)(SLOT_RAW * sizeof(T));
-    // a padded stage input lands phi only (fields 1 .. NF-1): the stencil never
-    // reads the density, whose update depends on M alone
-    static constexpr unsigned TX_BYTES_PHI = (unsigned)((NF - 1) * SY * SX * sizeof(T));
+    // a padded stage input lands its phi pairs only: the stencil never reads
+    // the density, whose update depends on M alone
+    static constexpr unsigned TX_BYTES_PAIR = (unsigned)(2 * NPF * SY * SX * sizeof(T));
     static constexpr size_t RING_BYTES = (size_t)D * SLOT_ELEMS * sizeof(T);
-    static constexpr size_t YS_BYTES = ((size_t)NT * (TY + 1) * TX * sizeof(T) + 15) / 16 * 16;
-    static constexpr size_t XB_BYTES = ((size_t)NT * TY * sizeof(T) + 15) / 16 * 16;
+    // j-face fluxes of the tile's rows and the row below, and the i0-1/2 face
+    // fluxes of its rows, both per pair ([NPF][TY+1][TX], [NPF][TY] of pairs)
+    static constexpr size_t YS_BYTES = ((size_t)NPF * (TY + 1) * TX * 2 * sizeof(T) + 15) / 16 * 16;
+    static constexpr size_t XB_BYTES = ((size_t)NPF * TY * 2 * sizeof(T) + 15) / 16 * 16;
     static constexpr size_t SMEM_BYTES = RING_BYTES + YS_BYTES + XB_BYTES + (size_t)D * 8;
 };
 
-// Padded layout of the library's own stage buffers: [F][nz][ny + 4][pitch],
-// logical (i, j) at (i + 4, j + 2), pitch = nx + 8 rounded up to 8 elements;
-// the 2-wide periodic ghosts are written by the producing stage.
+// Padded layout of the library's own stage buffers (the inputs of stages 2
+// and 3), pitch = nx + 8 rounded up to 8 elements, logical (i, j) at
+// (i + 4, j + 2), the 2-wide periodic ghosts written by the producing stage:
+// the F fields in NP = ceil(F / 2) pairs, in the order 1, 2, ..., F-1, 0
+// (phi of theta and the tracers, then the density), each pair's two values
+// of a cell side by side:
+//   element of field f at ((k (ny + 4) + j + 2) NP + q) 2 pitch + 2 (i + 4) + lane,
+//   q = pos / 2, lane = pos % 2, pos = f - 1 (f >= 1) or F - 1 (f = 0).
 __host__ __device__ __forceinline__ long long padded_pitch(int nx) { return ((long long)nx + 8 + 7) / 8 * 8; }
+__host__ __device__ __forceinline__ int pair_count(int nf) { return (nf + 1) / 2; }
+__host__ __device__ __forceinline__ int pair_pos(int f, int nf) { return f == 0 ? nf - 1 : f - 1; }
 
 template <typename T>
 struct StageParams {
@@ -58,13 +73,14 @@ struct StageParams {
     CUtensorMap umap[3];    // caller's unpadded rho, rho*theta, rho*q (3D, 3D, 4D), when user_tma
     const T *yin[MAXF];     // unpadded stage input (rho, rho*phi), when !tma_in
     const T *ybase[MAXF];   // Y^n (unpadded)
-    T *yout[MAXF];          // Y^(s) = Y^n + cdt * R(Y^(s-1)); padded origin when out_padded
+    T *yout[MAXF];          // Y^(s) = Y^n + cdt * R(Y^(s-1)); for a padded output the per-field views of
+                            // the buffer (pair layout), yout[1] (field 1: pair 0, lane 0) its base
     const T *mu, *mv, *mw;
     const T *tend;          // [F-1][nz][ny][nx] or nullptr
     int *status;            // device status word (mapped host memory)
     int nx, ny, nz, lim;
     int tma_in;             // input is a padded stage buffer holding phi (TMA)
-    int out_padded;         // output to a padded stage buffer: phi for f >= 1, with periodic ghosts
+    int out_padded;         // output to a padded stage buffer: phi for f >= 1 and rho, with periodic ghosts
     int user_tma;           // unpadded input through umap for tiles whose halo lies inside the domain
     int ty;                 // tile rows of the instantiation to launch (the TMA box height follows it)
     int open;               // open lateral boundaries: the padded input's ghost columns/rows hold the
@@ -76,7 +92,8 @@ struct StageParams {
     T *facev;               // when recording, if set: [3][F-1][nz][ny][nx] face values of the cell's
                             // i+1/2, j+1/2 and k+1/2 faces (k+1/2 of the top level: 0)
     long long plane;        // nx * ny
-    long long opitch, oplane;   // padded output: row pitch and level stride (elements)
+    long long opitch, oplane;   // padded buffers: pitch, and level stride (elements) of one field plane
+    long long prow, plev;       // padded output: row and level strides of the pair layout (elements)
     T cdt, rdx, rdy;
     T rdz[MAXNZ];           // 1 / dz_k
 };
@@ -379,8 +396,8 @@ __device__ __forceinline__ T face_coef(bool u, int br, int q) {
 template <typename T>
 cudaError_t launch_stage(const StageParams<T> &p, int nf, cudaStream_t s);
 
-// Encode the TMA descriptor of a padded stage buffer (F fields at base) for
-// tiles of ty rows.
+// Encode the TMA descriptor of a padded stage buffer (F fields at base, pair
+// layout) for tiles of ty rows: the phi pairs only.
 template <typename T>
 cudaError_t encode_stage_map(CUtensorMap *map, void *base, int nf, int nx, int ny, int nz, int ty);
 // Tensor maps over the caller's unpadded rho, rho*theta and rho*q (N fields)

@@ -21,7 +21,8 @@ __global__ void __launch_bounds__(32 * TYV, StageShape<T, NF, TYV>::MIN_BLOCKS)
     const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
     const unsigned own = (i < p.nx && j < p.ny) ? (unsigned)(j * p.nx + i) : 0u;
     ColDownHook<T, NF> hook(fp.c, p.yout[0], own);
-    (void)stage_tile_h<T, NF, LIM, false, TYV, true, ColDownHook<T, NF>>(p, &p.tmap, i0, j0, smem_raw, hook);
+    (void)stage_tile_h<T, NF, LIM, false, TYV, true, ColDownHook<T, NF>, LAYOUT_PAIR>(p, &p.tmap, i0, j0, smem_raw,
+                                                                                     hook);
 }
 
 template <typename T, int NF, int LIM, int TYV>

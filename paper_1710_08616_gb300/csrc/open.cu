@@ -5,7 +5,7 @@
 // halo updates every time step).
 //
 // The stage kernel reads its lateral neighbours from the two ghost columns
-// and rows of its padded input buffer (layout [F][nz][ny+4][pitch], logical
+// and rows of its padded input buffer (the pair layout of common.cuh, logical
 // (i, j) at (i+4, j+2)); in the open mode nothing wraps and no stage writes
 // those ghosts.  The kernels here fill and read them:
 //   * open_prepare_kernel: the stage-1 input, phi = (rho phi) / rho of every
@@ -62,7 +62,7 @@ __global__ void open_prepare_kernel(const __grid_constant__ OpenParams<T> p) {
     const int k = blockIdx.z;
     if (i >= p.nx) return;
     const size_t o = ((size_t)k * p.ny + j) * p.nx + i;
-    const size_t po = (size_t)k * p.pplane + (size_t)(j + 2) * p.pitch + (i + 4);
+    const size_t po = (size_t)k * p.pplane + (size_t)(j + 2) * p.pitch + 2 * (i + 4);
     const T r = recip(p.y[0][o]);
     for (int f = 1; f <= p.nt; f++) p.pad[f][po] = p.y[f][o] * r;
 }
@@ -80,7 +80,7 @@ __global__ void halo_pack_kernel(const __grid_constant__ OpenParams<T> p, long l
             i = h.pos;
             j = h.strip == 2 ? h.c : p.ny - 2 + h.c;
         }
-        p.hout[u] = p.pad[1 + h.f][(size_t)h.k * p.pplane + (size_t)(j + 2) * p.pitch + (i + 4)];
+        p.hout[u] = p.pad[1 + h.f][(size_t)h.k * p.pplane + (size_t)(j + 2) * p.pitch + 2 * (i + 4)];
     }
 }
 
@@ -99,7 +99,7 @@ __global__ void halo_unpack_kernel(const __grid_constant__ OpenParams<T> p, long
         }
         T v = p.hin0[u];
         if (p.hin1) v = p.w0 * v + p.w1 * p.hin1[u];
-        p.pad[1 + h.f][(size_t)h.k * p.pplane + (size_t)(j + 2) * p.pitch + (i + 4)] = v;
+        p.pad[1 + h.f][(size_t)h.k * p.pplane + (size_t)(j + 2) * p.pitch + 2 * (i + 4)] = v;
     }
 }
 

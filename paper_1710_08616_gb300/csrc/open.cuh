@@ -9,10 +9,11 @@ namespace asuca {
 template <typename T>
 struct OpenParams {
     const T *y[MAXF];        // caller fields (rho, rho*phi), unpadded [nz][ny][nx]
-    T *pad[MAXF];            // padded buffer field bases (padded origin)
+    T *pad[MAXF];            // padded buffer: per-field views (pair layout; element (k, j, i) at
+                             // k pplane + (j + 2) pitch + 2 (i + 4))
     const T *hin0, *hin1;    // halo-layout input: received strips / boundary data (hin1: second dataset or null)
     T *hout;                 // halo-layout output (pack)
-    long long pitch, pplane; // padded row pitch and level stride (elements)
+    long long pitch, pplane; // the pair layout's row and level strides (elements)
     int nx, ny, nz, nt;      // nt = F - 1 transported fields
     T w0, w1;                // time weights of hin0, hin1 (1 - tratio, tratio)
 };

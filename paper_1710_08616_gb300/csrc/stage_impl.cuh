@@ -126,6 +126,14 @@ struct NoHook {
     __device__ __forceinline__ void done(bool) {}
 };
 
+// Slot layouts of the ring (StageShape): the caller's fields (stage 1) land
+// as planes, the library's padded stage buffers as phi pairs.
+constexpr int LAYOUT_RAW = 0, LAYOUT_PAIR = 1;
+
+template <typename T> struct Vec2;
+template <> struct Vec2<float> { using type = float2; };
+template <> struct Vec2<double> { using type = double2; };
+
 // DOWN marches the levels from the top down (the ring, the faces and the
 // carried flux all run in march order; level k = nz - 1 - t at march step t),
 // which gives the same arithmetic per cell, so the result is bit-identical to
@@ -133,26 +141,37 @@ struct NoHook {
 // writes to p.yout: hook.level(k, out, valid, rho_next), where rho_next is the
 // density result of the next level of the march (the same expression that
 // level will evaluate), then hook.done(valid) after the last level.
-template <typename T, int NF, int LIM, bool REC, int TYV, bool DOWN, typename Hook>
+// The fields are processed in pairs (1, 2), (3, 4), ...: a pair shares every
+// operation of its face reconstruction and divergence (packed FP32x2 for
+// float), and with the pair layout its operands arrive in one load.
+template <typename T, int NF, int LIM, bool REC, int TYV, bool DOWN, typename Hook, int LAY>
 __device__ __forceinline__ bool stage_tile_h(const StageParams<T> &p, const CUtensorMap *tmap, int i0, int j0,
                                              unsigned char *smem_raw, Hook &hook) {
     static_assert(!(DOWN && REC), "branch recording marches upward");
     using S = StageShape<T, NF, TYV>;
-    constexpr int TX = S::TX, TY = S::TY, D = S::D, SX = S::SX, SY = S::SY, NT = S::NT;
+    using T2 = typename Vec2<T>::type;
+    constexpr int TX = S::TX, TY = S::TY, D = S::D, SX = S::SX, SY = S::SY, NT = S::NT, NPF = S::NPF;
     constexpr int NTHR = TX * TY;
-    constexpr int FE = SY * SX;                   // elements of one field in a slot
+    constexpr int FE = SY * SX;                   // raw layout: elements of one field in a slot
+    constexpr bool PAIRL = LAY == LAYOUT_PAIR;
+    // a slot cell (sy, sx): raw field f at f FE + sy SX + sx; pair layout pair q
+    // at (sy NPF + q) 2 SX + 2 sx (two values)
+    constexpr int XS = PAIRL ? 2 : 1;             // one cell along i
+    constexpr int YS = PAIRL ? 2 * NPF * SX : SX; // one row
+    constexpr int QS = 2 * SX;                    // one pair (pair layout)
     // The slot cells the stencil reads (no corners), dealt to the threads in
-    // pairs of neighbours along i for the copies and the conversion to phi:
-    // TY rows of TX + 4 cells (i0-2 .. i0+TX+1) and 4 halo rows of TX cells.
+    // pairs of neighbours along i for the copies and the conversion to phi
+    // (raw layout only): TY rows of TX + 4 cells (i0-2 .. i0+TX+1) and 4 halo
+    // rows of TX cells.
     constexpr int PR = (TX + 4) / 2, PH = TX / 2;
     constexpr int NPAIR = TY * PR + 4 * PH;
-    constexpr int MAXC = (NPAIR + NTHR - 1) / NTHR;
-    using T2 = typename std::conditional<std::is_same<T, float>::value, float2, double2>::type;
+    constexpr int MAXC = PAIRL ? 1 : (NPAIR + NTHR - 1) / NTHR;
     static_assert((FE * sizeof(T)) % 128 == 0, "each field of a slot must start on a 128-byte boundary");
+    constexpr bool PACK = std::is_same<T, float>::value;
 
     T *ring = reinterpret_cast<T *>(smem_raw);
-    T *ysm = reinterpret_cast<T *>(smem_raw + S::RING_BYTES);            // [NT][TY+1][TX]
-    T *xbs = reinterpret_cast<T *>(smem_raw + S::RING_BYTES + S::YS_BYTES); // [NT][TY]
+    T2 *ysm = reinterpret_cast<T2 *>(smem_raw + S::RING_BYTES);               // [NPF][TY+1][TX]
+    T2 *xbs = reinterpret_cast<T2 *>(smem_raw + S::RING_BYTES + S::YS_BYTES); // [NPF][TY]
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw + S::RING_BYTES + S::YS_BYTES + S::XB_BYTES);
 
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
@@ -175,13 +194,13 @@ __device__ __forceinline__ bool stage_tile_h(const StageParams<T> &p, const CUte
     const unsigned v_own = open ? (unsigned)((jc + 1) * nx + ic) : own;
     const unsigned v_down = open ? own : (unsigned)(wrap_index(jc - 1, ny) * nx + ic);
     const unsigned plane_u = (unsigned)p.plane_u, plane_v = (unsigned)p.plane_v;
-    // Input paths: a padded stage buffer (phi, one 4D TMA box per level); the
-    // caller's fields (rho*phi) by TMA when the tile's halo lies inside the
+    // Input paths: a padded stage buffer (phi pairs, one 4D TMA box per level);
+    // the caller's fields (rho*phi) by TMA when the tile's halo lies inside the
     // domain, else by per-thread cp.async with the periodic wrap.
-    const bool pad_in = p.tma_in != 0;   // always set for open boundaries
+    constexpr bool pad_in = PAIRL;   // the pair layout is the padded input's (always so for open boundaries)
     const bool user_tma = !pad_in && p.user_tma && i0 >= 4 && i0 + TX + 4 <= nx && j0 >= 2 && j0 + TY + 2 <= ny;
     const bool tma = pad_in || user_tma;
-    const bool conv = !pad_in;
+    constexpr bool conv = !pad_in;
 
     __syncthreads();   // the previous tile (if any) is done with the shared memory
     if (tma && tid == 0) {
@@ -190,7 +209,7 @@ __device__ __forceinline__ bool stage_tile_h(const StageParams<T> &p, const CUte
     }
 
     // slot cell pairs (sx even, so a pair is one aligned 2-element vector)
-    // this thread copies (cp.async path) and converts
+    // this thread copies (cp.async path) and converts (raw layout)
     int soff[MAXC];
     unsigned goff[MAXC], goff1[MAXC];
     int nc = 0;
@@ -199,7 +218,7 @@ __device__ __forceinline__ bool stage_tile_h(const StageParams<T> &p, const CUte
         const int c = tid + q * NTHR;
         soff[q] = 0;
         goff[q] = goff1[q] = 0;
-        if (c < NPAIR) {
+        if (!PAIRL && c < NPAIR) {
             int sy, sx;
             if (c < TY * PR) {
                 sy = 2 + c / PR;
@@ -219,6 +238,8 @@ __device__ __forceinline__ bool stage_tile_h(const StageParams<T> &p, const CUte
     }
     __syncthreads();
 
+    // ring slots of march steps t-1 .. t+2 and of the request t+D-2, rotated
+    // by one slot per step (slot(n) = ring + (n mod D) SLOT_ELEMS)
     auto slot = [&](int lev) -> T * { return ring + (size_t)(lev % D) * S::SLOT_ELEMS; };
 
     int issued = 0, seen = 0;   // TMA levels [0, issued) requested, [0, seen) seen complete
@@ -232,9 +253,9 @@ __device__ __forceinline__ bool stage_tile_h(const StageParams<T> &p, const CUte
                     uint64_t *bar = &bars[t % D];
                     T *dst = slot(t);
                     if (pad_in) {
-                        // phi only: the map covers fields 1 .. NF-1
-                        mbar_expect_tx(bar, S::TX_BYTES_PHI);
-                        tma_load_4d(dst + FE, tmap, i0, j0, lev, 0, bar);
+                        // the phi pairs: the map's dimensions are (2 pitch, pairs, rows, levels)
+                        mbar_expect_tx(bar, S::TX_BYTES_PAIR);
+                        tma_load_4d(dst, tmap, 2 * i0, 0, j0, lev, bar);
                     } else {
                         mbar_expect_tx(bar, S::TX_BYTES);
                         tma_load_3d(dst, &p.umap[0], i0 - 4, j0 - 2, lev, bar);
@@ -275,7 +296,7 @@ __device__ __forceinline__ bool stage_tile_h(const StageParams<T> &p, const CUte
                 for (int f = 1; f < NF; f++) {
                     T2 *v = reinterpret_cast<T2 *>(sl + f * FE + soff[q]);
                     T2 w = *v;
-                    if constexpr (std::is_same<T, float>::value) {
+                    if constexpr (PACK) {
                         w = __fmul2_rn(w, make_float2(r0, r1));
                     } else {
                         w.x *= r0;
@@ -292,6 +313,19 @@ __device__ __forceinline__ bool stage_tile_h(const StageParams<T> &p, const CUte
         seen = lev + 1;
         if (conv) convert(lev);
         return true;
+    };
+
+    // the two values of pair q at offset off of a slot (raw layout: fields
+    // 2q+1 and 2q+2, the second 0 past the last field)
+    auto ld2 = [&](const T *sl, int q, int off) -> T2 {
+        if constexpr (PAIRL) {
+            return *reinterpret_cast<const T2 *>(sl + q * QS + off);
+        } else {
+            T2 v;
+            v.x = sl[(2 * q + 1) * FE + off];
+            v.y = (2 * q + 2 <= NT) ? sl[(2 * q + 2) * FE + off] : T(0);
+            return v;
+        }
     };
 
     bool timed_out = false;
@@ -311,8 +345,6 @@ __device__ __forceinline__ bool stage_tile_h(const StageParams<T> &p, const CUte
     const T cdt = p.cdt;
     const T ax = -cdt * p.rdx, ay = -cdt * p.rdy;   // out = base + ax dX + ay dY + az dZ + cdt t
     const int warp = ty, lane = tx;
-    // Edge faces (j0-1/2 for the tile's 32 columns, i0-1/2 for its TY rows),
-    // one task per (field, edge), dealt round-robin to the warps.
     const int er = lane % TY;   // the tile row whose i0-1/2 faces this lane computes
     // MV through face j0-1/2 of column ic, MU through face i0-1/2 of row er
     const unsigned edge_b = open ? (unsigned)(j0 * nx + ic) : (unsigned)(wrap_index(j0 - 1, ny) * nx + ic);
@@ -322,9 +354,10 @@ __device__ __forceinline__ bool stage_tile_h(const StageParams<T> &p, const CUte
     const bool ghost_x = !open && ((i0 < 2) || (i0 + TX > nx - 2));
     const bool ghost_y = !open && ((j0 < 2) || (j0 + TY > ny - 2));
 
-    T zlo[NF];
+    T zlo0 = T(0);    // the density's flux through the face behind the march (M itself)
+    T2 zlo[NPF];      // the pairs' fluxes through that face
 #pragma unroll
-    for (int f = 0; f < NF; f++) zlo[f] = T(0);
+    for (int q = 0; q < NPF; q++) zlo[q].x = zlo[q].y = T(0);
 
     // per-level mass fluxes, requested one level ahead (the faces need them first)
     // mwp is the flux through the face the march reaches next: k+1/2 upward
@@ -349,9 +382,22 @@ __device__ __forceinline__ bool stage_tile_h(const StageParams<T> &p, const CUte
     prefetch(level_of(0));
     advance();
 
-    const int cy = ty + 2, cx = tx + 4, cc = cy * SX + cx;
-    // float stages evaluate faces and the divergence two fields at a time (FP32x2)
-    constexpr bool PACK = std::is_same<T, float>::value;
+    const int cy = ty + 2, cx = tx + 4, cc = cy * YS + cx * XS;
+    // padded output (pair layout): the cell's element offset, and the pair stride
+    const long long q2 = 2 * p.opitch;
+    const bool has_tend = p.tend != nullptr;
+
+    // the flux of pair q through a face from its upwind cell c, downwind cell
+    // o and far upwind cell f; one field only for the last pair of an odd count
+    auto flux2 = [&](int q, T2 c, T2 o, T2 f, T m) -> T2 {
+        T2 r;
+        if constexpr (PACK) {
+            if (2 * q + 2 <= NT) return face_flux2<LIM>(c, o, f, m);
+        }
+        r.x = face_flux<LIM>(c.x, o.x, f.x, m);
+        r.y = (2 * q + 2 <= NT) ? face_flux<LIM>(c.y, o.y, f.y, m) : T(0);
+        return r;
+    };
 
 #pragma unroll 1
     for (int t = 0; t < nz; t++) {
@@ -372,11 +418,16 @@ __device__ __forceinline__ bool stage_tile_h(const StageParams<T> &p, const CUte
         }
         issue(t + D - 2);   // into the slot of march step t-2, which nobody reads any more
         // Y^n of this level: used after the faces, which cover the load latency
-        T yb[NF];
+        T yb0;
+        T2 yb[NPF];
         {
             const unsigned kb = (unsigned)k * plane + own;
+            yb0 = p.ybase[0][kb];
 #pragma unroll
-            for (int f = 0; f < NF; f++) yb[f] = p.ybase[f][kb];
+            for (int q = 0; q < NPF; q++) {
+                yb[q].x = p.ybase[2 * q + 1][kb];
+                yb[q].y = (2 * q + 2 <= NT) ? p.ybase[2 * q + 2][kb] : T(0);
+            }
         }
         if (t + 1 < nz) prefetch(level_of(t + 1));
 
@@ -390,135 +441,89 @@ __device__ __forceinline__ bool stage_tile_h(const StageParams<T> &p, const CUte
         // upwind cell of the face ahead: step t when the flux points along the
         // march (upward march: M >= 0; downward: M < 0, since M = 0 counts as upward)
         const bool ux = mup >= T(0), uy = mvp >= T(0), uz = DOWN ? (mwp < T(0)) : (mwp >= T(0));
-        const int xc = cc + (ux ? 0 : 1), xo = cc + (ux ? 1 : 0), xf = cc + (ux ? -1 : 2);
-        const int yc = cc + (uy ? 0 : SX), yo = cc + (uy ? SX : 0), yf = cc + (uy ? -SX : 2 * SX);
+        const int xc = cc + (ux ? 0 : XS), xo = cc + (ux ? XS : 0), xf = cc + (ux ? -XS : 2 * XS);
+        const int yc = cc + (uy ? 0 : YS), yo = cc + (uy ? YS : 0), yf = cc + (uy ? -YS : 2 * YS);
         const T *zc = (uz ? Sk : Skp) + cc, *zo = (uz ? Skp : Sk) + cc, *zf = (uz ? Skm : Skp2) + cc;
-        T xp[NT], yp[NT], zp[NT];
-        if constexpr (PACK) {
+        T2 xp[NPF], yp[NPF], zp[NPF];
 #pragma unroll
-            for (int f = 0; f + 1 < NT; f += 2) {
-                const int f0 = (f + 1) * FE, f1 = (f + 2) * FE;
-                float2 rx, ry, rz;
-                if constexpr (REC) {
-                    int2 bx, by, bz = make_int2(0, 0);
-                    const float2 vx = face_val2_br<LIM>(make_float2(Sk[f0 + xc], Sk[f1 + xc]),
-                                                        make_float2(Sk[f0 + xo], Sk[f1 + xo]),
-                                                        make_float2(Sk[f0 + xf], Sk[f1 + xf]), bx);
-                    const float2 vy = face_val2_br<LIM>(make_float2(Sk[f0 + yc], Sk[f1 + yc]),
-                                                        make_float2(Sk[f0 + yo], Sk[f1 + yo]),
-                                                        make_float2(Sk[f0 + yf], Sk[f1 + yf]), by);
-                    const float2 vz = top ? make_float2(0.f, 0.f)
-                                          : face_val2_br<LIM>(make_float2(zc[f0], zc[f1]), make_float2(zo[f0], zo[f1]),
-                                                              make_float2(zf[f0], zf[f1]), bz);
-                    rx = __fmul2_rn(make_float2(mup, mup), vx);
-                    ry = __fmul2_rn(make_float2(mvp, mvp), vy);
-                    rz = top ? make_float2(0.f, 0.f) : __fmul2_rn(make_float2(mwp, mwp), vz);
-                    if (valid) {
-                        uint8_t *br = p.branch + (long long)f * nz * plane + (long long)k * plane + own;
-                        br[0] = (uint8_t)(bx.x | (by.x << 2) | (bz.x << 4));
-                        br[(long long)nz * plane] = (uint8_t)(bx.y | (by.y << 2) | (bz.y << 4));
-                        if (p.facev) {
-                            const long long fs = (long long)nz * plane, ds = (long long)NT * fs;
-                            T *fv = p.facev + (long long)f * fs + (long long)k * plane + own;
-                            fv[0] = vx.x; fv[fs] = vx.y;
-                            fv[ds] = vy.x; fv[ds + fs] = vy.y;
-                            fv[2 * ds] = vz.x; fv[2 * ds + fs] = vz.y;
+        for (int q = 0; q < NPF; q++) {
+            const T2 cxv = ld2(Sk, q, xc), oxv = ld2(Sk, q, xo), fxv = ld2(Sk, q, xf);
+            const T2 cyv = ld2(Sk, q, yc), oyv = ld2(Sk, q, yo), fyv = ld2(Sk, q, yf);
+            T2 czv, ozv, fzv;
+            if (!top) {
+                czv = ld2(zc, q, 0);
+                ozv = ld2(zo, q, 0);
+                fzv = ld2(zf, q, 0);
+            }
+            if constexpr (REC) {
+                // the adjoint's record: each face's value and limiter branch
+                int2 bx, by, bz = make_int2(0, 0);
+                T2 vx, vy, vz;
+                if constexpr (PACK) {
+                    vx = face_val2_br<LIM>(cxv, oxv, fxv, bx);
+                    vy = face_val2_br<LIM>(cyv, oyv, fyv, by);
+                    if (!top) vz = face_val2_br<LIM>(czv, ozv, fzv, bz);
+                    else vz = make_float2(0.f, 0.f);
+                } else {
+                    vx.x = face_val_br<LIM>(cxv.x, oxv.x, fxv.x, bx.x);
+                    vx.y = face_val_br<LIM>(cxv.y, oxv.y, fxv.y, bx.y);
+                    vy.x = face_val_br<LIM>(cyv.x, oyv.x, fyv.x, by.x);
+                    vy.y = face_val_br<LIM>(cyv.y, oyv.y, fyv.y, by.y);
+                    if (!top) {
+                        vz.x = face_val_br<LIM>(czv.x, ozv.x, fzv.x, bz.x);
+                        vz.y = face_val_br<LIM>(czv.y, ozv.y, fzv.y, bz.y);
+                    } else {
+                        vz.x = vz.y = T(0);
+                    }
+                }
+                xp[q].x = mup * vx.x; xp[q].y = mup * vx.y;
+                yp[q].x = mvp * vy.x; yp[q].y = mvp * vy.y;
+                zp[q].x = top ? T(0) : mwp * vz.x;
+                zp[q].y = top ? T(0) : mwp * vz.y;
+                if (valid) {
+                    const long long fs = (long long)nz * plane, ds = (long long)NT * fs;
+                    uint8_t *br = p.branch + (long long)(2 * q) * fs + (long long)k * plane + own;
+                    br[0] = (uint8_t)(bx.x | (by.x << 2) | (bz.x << 4));
+                    if (2 * q + 2 <= NT) br[fs] = (uint8_t)(bx.y | (by.y << 2) | (bz.y << 4));
+                    if (p.facev) {
+                        T *fv = p.facev + (long long)(2 * q) * fs + (long long)k * plane + own;
+                        fv[0] = vx.x;
+                        fv[ds] = vy.x;
+                        fv[2 * ds] = vz.x;
+                        if (2 * q + 2 <= NT) {
+                            fv[fs] = vx.y;
+                            fv[ds + fs] = vy.y;
+                            fv[2 * ds + fs] = vz.y;
                         }
                     }
-                } else {
-                    rx = face_flux2<LIM>(make_float2(Sk[f0 + xc], Sk[f1 + xc]), make_float2(Sk[f0 + xo], Sk[f1 + xo]),
-                                         make_float2(Sk[f0 + xf], Sk[f1 + xf]), mup);
-                    ry = face_flux2<LIM>(make_float2(Sk[f0 + yc], Sk[f1 + yc]), make_float2(Sk[f0 + yo], Sk[f1 + yo]),
-                                         make_float2(Sk[f0 + yf], Sk[f1 + yf]), mvp);
-                    rz = top ? make_float2(0.f, 0.f)
-                             : face_flux2<LIM>(make_float2(zc[f0], zc[f1]), make_float2(zo[f0], zo[f1]),
-                                               make_float2(zf[f0], zf[f1]), mwp);
                 }
-                xp[f] = rx.x; xp[f + 1] = rx.y;
-                yp[f] = ry.x; yp[f + 1] = ry.y;
-                zp[f] = rz.x; zp[f + 1] = rz.y;
-                ysm[(f * (TY + 1) + ty + 1) * TX + tx] = ry.x;
-                ysm[((f + 1) * (TY + 1) + ty + 1) * TX + tx] = ry.y;
+            } else {
+                xp[q] = flux2(q, cxv, oxv, fxv, mup);
+                yp[q] = flux2(q, cyv, oyv, fyv, mvp);
+                if (!top) zp[q] = flux2(q, czv, ozv, fzv, mwp);
+                else zp[q].x = zp[q].y = T(0);
             }
-            if (NT & 1) {
-                constexpr int f = NT - 1;
-                const int fo = (f + 1) * FE;
-                if constexpr (REC) {
-                    int bx, by, bz = 0;
-                    const T vx = face_val_br<LIM>(Sk[fo + xc], Sk[fo + xo], Sk[fo + xf], bx);
-                    const T vy = face_val_br<LIM>(Sk[fo + yc], Sk[fo + yo], Sk[fo + yf], by);
-                    const T vz = top ? T(0) : face_val_br<LIM>(zc[fo], zo[fo], zf[fo], bz);
-                    xp[f] = mup * vx;
-                    yp[f] = mvp * vy;
-                    zp[f] = top ? T(0) : mwp * vz;
-                    if (valid) {
-                        p.branch[(long long)f * nz * plane + (long long)k * plane + own] = (uint8_t)(bx | (by << 2) | (bz << 4));
-                        if (p.facev) {
-                            const long long fs = (long long)nz * plane, ds = (long long)NT * fs;
-                            T *fv = p.facev + (long long)f * fs + (long long)k * plane + own;
-                            fv[0] = vx;
-                            fv[ds] = vy;
-                            fv[2 * ds] = vz;
-                        }
-                    }
-                } else {
-                    xp[f] = face_flux<LIM>(Sk[fo + xc], Sk[fo + xo], Sk[fo + xf], mup);
-                    yp[f] = face_flux<LIM>(Sk[fo + yc], Sk[fo + yo], Sk[fo + yf], mvp);
-                    zp[f] = top ? T(0) : face_flux<LIM>(zc[fo], zo[fo], zf[fo], mwp);
-                }
-                ysm[(f * (TY + 1) + ty + 1) * TX + tx] = yp[f];
-            }
-        } else {
-#pragma unroll
-            for (int f = 0; f < NT; f++) {
-                const int fo = (f + 1) * FE;
-                if (REC) {
-                    int bx, by, bz = 0;
-                    const T vx = face_val_br<LIM>(Sk[fo + xc], Sk[fo + xo], Sk[fo + xf], bx);
-                    const T vy = face_val_br<LIM>(Sk[fo + yc], Sk[fo + yo], Sk[fo + yf], by);
-                    const T vz = top ? T(0) : face_val_br<LIM>(zc[fo], zo[fo], zf[fo], bz);
-                    xp[f] = mup * vx;
-                    yp[f] = mvp * vy;
-                    zp[f] = top ? T(0) : mwp * vz;
-                    if (valid) {
-                        p.branch[(long long)f * nz * plane + (long long)k * plane + own] = (uint8_t)(bx | (by << 2) | (bz << 4));
-                        if (p.facev) {
-                            const long long fs = (long long)nz * plane, ds = (long long)NT * fs;
-                            T *fv = p.facev + (long long)f * fs + (long long)k * plane + own;
-                            fv[0] = vx;
-                            fv[ds] = vy;
-                            fv[2 * ds] = vz;
-                        }
-                    }
-                } else {
-                    xp[f] = face_flux<LIM>(Sk[fo + xc], Sk[fo + xo], Sk[fo + xf], mup);
-                    yp[f] = face_flux<LIM>(Sk[fo + yc], Sk[fo + yo], Sk[fo + yf], mvp);
-                    zp[f] = top ? T(0) : face_flux<LIM>(zc[fo], zo[fo], zf[fo], mwp);
-                }
-                ysm[(f * (TY + 1) + ty + 1) * TX + tx] = yp[f];
-            }
+            ysm[(q * (TY + 1) + ty + 1) * TX + tx] = yp[q];
         }
         {
-            // Edge faces as warp tasks: one per field for the j0-1/2 faces of the
-            // 32 columns, and the NT x TY faces at i0-1/2 packed 32 to a task
+            // Edge faces as warp tasks: one per pair for the j0-1/2 faces of the
+            // 32 columns, and the NPF x TY faces at i0-1/2 packed 32 to a task
             // (lane l takes row l % TY, as 32 is a multiple of TY).
-            constexpr int NYT = NT, NXT = (NT * TY + 31) / 32;
+            constexpr int NYT = NPF, NXT = (NPF * TY + 31) / 32;
             const bool ub = meb >= T(0), ul = mel >= T(0);
-            const int bc = (ub ? 1 : 2) * SX, bo = (ub ? 2 : 1) * SX, bf = (ub ? 0 : 3) * SX;
-            const int lc = ul ? 3 : 4, lo = ul ? 4 : 3, lf = ul ? 2 : 5;
+            const int bc = (ub ? 1 : 2) * YS + cx * XS, bo = (ub ? 2 : 1) * YS + cx * XS,
+                      bf = (ub ? 0 : 3) * YS + cx * XS;
+            const int lr = (er + 2) * YS;
+            const int lc = lr + (ul ? 3 : 4) * XS, lo = lr + (ul ? 4 : 3) * XS, lf = lr + (ul ? 2 : 5) * XS;
 #pragma unroll 1
-            for (int t = warp; t < NYT + NXT; t += TY) {
-                if (t < NYT) {
+            for (int w = warp; w < NYT + NXT; w += TY) {
+                if (w < NYT) {
                     // flux at j0-1/2 for column lane: slot rows 0..3 (j0-2 .. j0+1)
-                    const int fo = (t + 1) * FE + cx;
-                    ysm[(t * (TY + 1)) * TX + tx] = face_flux<LIM>(Sk[fo + bc], Sk[fo + bo], Sk[fo + bf], meb);
+                    ysm[(w * (TY + 1)) * TX + tx] = flux2(w, ld2(Sk, w, bc), ld2(Sk, w, bo), ld2(Sk, w, bf), meb);
                 } else {
-                    // flux at i0-1/2 for row er of field f: slot columns 2..5 (i0-2 .. i0+1)
-                    const int f = ((t - NYT) * 32 + lane) / TY;
-                    if (f < NT) {
-                        const int fo = (f + 1) * FE + (er + 2) * SX;
-                        xbs[f * TY + er] = face_flux<LIM>(Sk[fo + lc], Sk[fo + lo], Sk[fo + lf], mel);
-                    }
+                    // flux at i0-1/2 for row er of pair q: slot columns 2..5 (i0-2 .. i0+1)
+                    const int q = ((w - NYT) * 32 + lane) / TY;
+                    if (q < NPF) xbs[q * TY + er] = flux2(q, ld2(Sk, q, lc), ld2(Sk, q, lo), ld2(Sk, q, lf), mel);
                 }
             }
         }
@@ -527,46 +532,41 @@ __device__ __forceinline__ bool stage_tile_h(const StageParams<T> &p, const CUte
         // ---- divergence and RK combine: out = Y^n + ax dX + ay dY + az dZ (+ cdt tendency),
         // each step one FMA on an exact difference
         const T az = -cdt * p.rdz[k];
-        T out[NF];
         // z flux difference F(k+1/2) - F(k-1/2): ahead minus carried upward,
         // carried minus ahead downward (the same operands either way)
-        out[0] = fma(az, DOWN ? zlo[0] - mwp : mwp - zlo[0], fma(ay, mvp - mvm, fma(ax, mup - mum, yb[0])));
-        zlo[0] = mwp;
-        T xm[NT], ym[NT];
+        const T out0 = fma(az, DOWN ? zlo0 - mwp : mwp - zlo0, fma(ay, mvp - mvm, fma(ax, mup - mum, yb0)));
+        zlo0 = mwp;
+        T2 out2[NPF];
 #pragma unroll
-        for (int f = 0; f < NT; f++) {
-            xm[f] = __shfl_up_sync(0xffffffffu, xp[f], 1);
-            if (lane == 0) xm[f] = xbs[f * TY + ty];
-            ym[f] = ysm[(f * (TY + 1) + ty) * TX + tx];
-        }
-        if constexpr (PACK) {
-            const float2 neg1 = make_float2(-1.f, -1.f), ax2 = make_float2(ax, ax), ay2 = make_float2(ay, ay),
-                         az2 = make_float2(az, az);
-#pragma unroll
-            for (int f = 0; f + 1 < NT; f += 2) {
-                float2 o = __ffma2_rn(ax2, __ffma2_rn(make_float2(xm[f], xm[f + 1]), neg1, make_float2(xp[f], xp[f + 1])),
-                                      make_float2(yb[f + 1], yb[f + 2]));
-                o = __ffma2_rn(ay2, __ffma2_rn(make_float2(ym[f], ym[f + 1]), neg1, make_float2(yp[f], yp[f + 1])), o);
-                o = DOWN ? __ffma2_rn(az2, __ffma2_rn(make_float2(zp[f], zp[f + 1]), neg1, make_float2(zlo[f + 1], zlo[f + 2])), o)
-                         : __ffma2_rn(az2, __ffma2_rn(make_float2(zlo[f + 1], zlo[f + 2]), neg1, make_float2(zp[f], zp[f + 1])), o);
-                out[f + 1] = o.x;
-                out[f + 2] = o.y;
+        for (int q = 0; q < NPF; q++) {
+            T2 xm;
+            xm.x = __shfl_up_sync(0xffffffffu, xp[q].x, 1);
+            xm.y = __shfl_up_sync(0xffffffffu, xp[q].y, 1);
+            if (lane == 0) xm = xbs[q * TY + ty];
+            const T2 ym = ysm[(q * (TY + 1) + ty) * TX + tx];
+            if constexpr (PACK) {
+                const float2 neg1 = make_float2(-1.f, -1.f);
+                float2 o = __ffma2_rn(make_float2(ax, ax), __ffma2_rn(xm, neg1, xp[q]), yb[q]);
+                o = __ffma2_rn(make_float2(ay, ay), __ffma2_rn(ym, neg1, yp[q]), o);
+                o = __ffma2_rn(make_float2(az, az), DOWN ? __ffma2_rn(zp[q], neg1, zlo[q]) : __ffma2_rn(zlo[q], neg1, zp[q]),
+                               o);
+                out2[q] = o;
+            } else {
+                out2[q].x = fma(az, DOWN ? zlo[q].x - zp[q].x : zp[q].x - zlo[q].x,
+                                fma(ay, yp[q].x - ym.x, fma(ax, xp[q].x - xm.x, yb[q].x)));
+                out2[q].y = fma(az, DOWN ? zlo[q].y - zp[q].y : zp[q].y - zlo[q].y,
+                                fma(ay, yp[q].y - ym.y, fma(ax, xp[q].y - xm.y, yb[q].y)));
             }
-            if (NT & 1) {
-                constexpr int f = NT - 1;
-                out[f + 1] = fma(az, DOWN ? zlo[f + 1] - zp[f] : zp[f] - zlo[f + 1],
-                                 fma(ay, yp[f] - ym[f], fma(ax, xp[f] - xm[f], yb[f + 1])));
-            }
-        } else {
-#pragma unroll
-            for (int f = 0; f < NT; f++)
-                out[f + 1] = fma(az, DOWN ? zlo[f + 1] - zp[f] : zp[f] - zlo[f + 1],
-                                 fma(ay, yp[f] - ym[f], fma(ax, xp[f] - xm[f], yb[f + 1])));
+            zlo[q] = zp[q];
         }
+        if (has_tend) {
+            const long long fs = (long long)nz * plane;
+            const T *tk = p.tend + (unsigned)k * plane + own;
 #pragma unroll
-        for (int f = 0; f < NT; f++) {
-            if (p.tend) out[f + 1] = fma(cdt, p.tend[(long long)f * nz * plane + (unsigned)k * plane + own], out[f + 1]);
-            zlo[f + 1] = zp[f];
+            for (int q = 0; q < NPF; q++) {
+                out2[q].x = fma(cdt, tk[(long long)(2 * q) * fs], out2[q].x);
+                if (2 * q + 2 <= NT) out2[q].y = fma(cdt, tk[(long long)(2 * q + 1) * fs], out2[q].y);
+            }
         }
         if (Hook::active) {
             // the density result of the next march step, evaluated as that step will
@@ -576,30 +576,55 @@ __device__ __forceinline__ bool stage_tile_h(const StageParams<T> &p, const CUte
                 rho_next = fma(az_n, DOWN ? mwp - nmwp : nmwp - mwp,
                                fma(ay, nmvp - nmvm, fma(ax, nmup - nmum, nrho)));
             }
+            T out[NF];
+            out[0] = out0;
+#pragma unroll
+            for (int q = 0; q < NPF; q++) {
+                out[2 * q + 1] = out2[q].x;
+                if (2 * q + 2 <= NT) out[2 * q + 2] = out2[q].y;
+            }
             hook.template level<T, NF>(k, out, valid, rho_next);
         } else if (valid) {
             if (p.out_padded) {
-                // the next stage reads phi = (rho phi) / rho
-                const T r = recip(out[0]);
+                // the next stage reads phi = (rho phi) / rho, in pairs; the
+                // density goes with the last pair (or a pair of its own)
+                const T r = recip(out0);
+                T *ob = p.yout[1] + (long long)k * p.plev + (long long)(j + 2) * p.prow + 2 * (i + 4);
+                T2 v[NPF + 1];
 #pragma unroll
-                for (int f = 1; f < NF; f++) out[f] *= r;
-                const unsigned ob = (unsigned)k * (unsigned)p.oplane + (unsigned)(j + 2) * (unsigned)p.opitch + (unsigned)(i + 4);
+                for (int q = 0; q < NPF; q++) {
+                    if constexpr (PACK) {
+                        v[q] = __fmul2_rn(out2[q], make_float2(r, r));
+                    } else {
+                        v[q].x = out2[q].x * r;
+                        v[q].y = out2[q].y * r;
+                    }
+                }
+                constexpr int NW = (NT & 1) ? NPF : NPF + 1;   // pairs written
+                if (NT & 1) v[NPF - 1].y = out0;
+                else {
+                    v[NPF].x = out0;
+                    v[NPF].y = T(0);
+                }
 #pragma unroll
-                for (int f = 0; f < NF; f++) p.yout[f][ob] = out[f];
+                for (int q = 0; q < NW; q++) *reinterpret_cast<T2 *>(ob + q * q2) = v[q];
                 if (ghost_x || ghost_y) {
-                    const int gx = (i < 2) ? nx : ((i >= nx - 2) ? -nx : 0);
-                    const int gy = (j < 2) ? ny * (int)p.opitch : ((j >= ny - 2) ? -ny * (int)p.opitch : 0);
+                    const long long gx = (i < 2) ? 2LL * nx : ((i >= nx - 2) ? -2LL * nx : 0);
+                    const long long gy = (j < 2) ? (long long)ny * p.prow : ((j >= ny - 2) ? -(long long)ny * p.prow : 0);
 #pragma unroll
-                    for (int f = 0; f < NF; f++) {
-                        T *o = p.yout[f] + ob;
-                        if (gx) o[gx] = out[f];
-                        if (gy) o[gy] = out[f];
+                    for (int q = 0; q < NW; q++) {
+                        if (gx) *reinterpret_cast<T2 *>(ob + q * q2 + gx) = v[q];
+                        if (gy) *reinterpret_cast<T2 *>(ob + q * q2 + gy) = v[q];
                     }
                 }
             } else {
                 const unsigned o = (unsigned)k * plane + own;
+                p.yout[0][o] = out0;
 #pragma unroll
-                for (int f = 0; f < NF; f++) p.yout[f][o] = out[f];
+                for (int q = 0; q < NPF; q++) {
+                    p.yout[2 * q + 1][o] = out2[q].x;
+                    if (2 * q + 2 <= NT) p.yout[2 * q + 2][o] = out2[q].y;
+                }
             }
         }
         if (t + 1 < nz) advance();
@@ -619,31 +644,41 @@ __device__ __forceinline__ bool stage_tile_h(const StageParams<T> &p, const CUte
     return timed_out;
 }
 
+// A tile of a stage, its input layout chosen by the input (padded stage
+// buffer: pairs; the caller's fields: raw).
 template <typename T, int NF, int LIM, bool REC, int TYV = 8>
 __device__ __forceinline__ bool stage_tile(const StageParams<T> &p, const CUtensorMap *tmap, int i0, int j0,
                                            unsigned char *smem_raw) {
     NoHook h;
-    return stage_tile_h<T, NF, LIM, REC, TYV, false, NoHook>(p, tmap, i0, j0, smem_raw, h);
+    if (p.tma_in) return stage_tile_h<T, NF, LIM, REC, TYV, false, NoHook, LAYOUT_PAIR>(p, tmap, i0, j0, smem_raw, h);
+    return stage_tile_h<T, NF, LIM, REC, TYV, false, NoHook, LAYOUT_RAW>(p, tmap, i0, j0, smem_raw, h);
 }
 
-template <typename T, int NF, int LIM, bool REC, int TYV>
+template <typename T, int NF, int LIM, bool REC, int TYV, int LAY>
 __global__ void __launch_bounds__(32 * TYV, StageShape<T, NF, TYV>::MIN_BLOCKS)
     stage_kernel(const __grid_constant__ StageParams<T> p) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    (void)stage_tile<T, NF, LIM, REC, TYV>(p, &p.tmap, blockIdx.x * StageShape<T, NF, TYV>::TX,
-                                           blockIdx.y * TYV, smem_raw);
+    NoHook h;
+    (void)stage_tile_h<T, NF, LIM, REC, TYV, false, NoHook, LAY>(p, &p.tmap, blockIdx.x * StageShape<T, NF, TYV>::TX,
+                                                                blockIdx.y * TYV, smem_raw, h);
+}
+
+template <typename T, int NF, int LIM, bool REC, int TYV, int LAY>
+static cudaError_t launch_lay(const StageParams<T> &p, cudaStream_t s) {
+    using S = StageShape<T, NF, TYV>;
+    static std::atomic<unsigned long long> attr_done{0};   // devices whose attribute is set
+    const cudaError_t e = set_smem_once(stage_kernel<T, NF, LIM, REC, TYV, LAY>, (int)S::SMEM_BYTES, attr_done);
+    if (e != cudaSuccess) return e;
+    dim3 block(S::TX, S::TY);
+    dim3 grid((p.nx + S::TX - 1) / S::TX, (p.ny + S::TY - 1) / S::TY);
+    stage_kernel<T, NF, LIM, REC, TYV, LAY><<<grid, block, S::SMEM_BYTES, s>>>(p);
+    return cudaGetLastError();
 }
 
 template <typename T, int NF, int LIM, bool REC, int TYV>
 static cudaError_t launch_rec(const StageParams<T> &p, cudaStream_t s) {
-    using S = StageShape<T, NF, TYV>;
-    static std::atomic<unsigned long long> attr_done{0};   // devices whose attribute is set
-    const cudaError_t e = set_smem_once(stage_kernel<T, NF, LIM, REC, TYV>, (int)S::SMEM_BYTES, attr_done);
-    if (e != cudaSuccess) return e;
-    dim3 block(S::TX, S::TY);
-    dim3 grid((p.nx + S::TX - 1) / S::TX, (p.ny + S::TY - 1) / S::TY);
-    stage_kernel<T, NF, LIM, REC, TYV><<<grid, block, S::SMEM_BYTES, s>>>(p);
-    return cudaGetLastError();
+    if (p.tma_in) return launch_lay<T, NF, LIM, REC, TYV, LAYOUT_PAIR>(p, s);
+    return launch_lay<T, NF, LIM, REC, TYV, LAYOUT_RAW>(p, s);
 }
 
 // branch recording (the adjoint's forward pass) is instantiated for 4- and
@@ -703,17 +738,17 @@ cudaError_t encode_stage_map(CUtensorMap *map, void *base, int nf, int nx, int n
     if (nf < 2) return cudaErrorInvalidValue;
     using S = StageShape<T, 2>;   // SX does not depend on the field count or the tile height
     const long long P = padded_pitch(nx);
-    // the map covers the phi fields 1 .. nf-1 (the stage kernel never reads the
-    // density of a padded buffer; field 0 stays in the buffer for the adjoint)
-    const long long fe = P * (ny + 4) * (long long)nz;
-    void *phi = static_cast<T *>(base) + fe;
-    const cuuint64_t dims[4] = {(cuuint64_t)P, (cuuint64_t)(ny + 4), (cuuint64_t)nz, (cuuint64_t)(nf - 1)};
-    const cuuint64_t strides[3] = {(cuuint64_t)(P * sizeof(T)), (cuuint64_t)(P * (ny + 4) * sizeof(T)),
-                                   (cuuint64_t)(fe * sizeof(T))};
-    const cuuint32_t box[4] = {(cuuint32_t)S::SX, (cuuint32_t)(ty + 4), 1u, (cuuint32_t)(nf - 1)};
+    // the pair layout as a 4D tensor (2 pitch elements, pairs, rows, levels);
+    // the map covers the phi pairs (the density, in the last pair or a pair of
+    // its own, stays in the buffer for the adjoint)
+    const int np = pair_count(nf), npf = (nf - 1 + 1) / 2;
+    const cuuint64_t dims[4] = {(cuuint64_t)(2 * P), (cuuint64_t)npf, (cuuint64_t)(ny + 4), (cuuint64_t)nz};
+    const cuuint64_t strides[3] = {(cuuint64_t)(2 * P * sizeof(T)), (cuuint64_t)(2 * P * np * sizeof(T)),
+                                   (cuuint64_t)(2 * P * np * (ny + 4) * sizeof(T))};
+    const cuuint32_t box[4] = {(cuuint32_t)(2 * S::SX), (cuuint32_t)npf, (cuuint32_t)(ty + 4), 1u};
     const cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
     CUresult r = enc(map, sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4,
-                     phi, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                     base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
