@@ -855,15 +855,25 @@ def run_ours(args):
     hbm_peak, peak_kind = _peaks()
     s = 4
     kinds = {asuca.KERNEL_STAGE: "stage", asuca.KERNEL_COLUMN: "column", asuca.KERNEL_REDUCE: "budget_reduce",
-             asuca.KERNEL_STAGE_COLUMN: "stage3_column"}
+             asuca.KERNEL_STAGE_COLUMN: "stage3_column", asuca.KERNEL_STAGE_FACTOR: "stage2_factor"}
     fused = asuca.get_tuning(g, asuca.TUNE_FUSED_COLUMN) == 1
+    split = bool(prof) and asuca.KERNEL_STAGE_FACTOR in prof
     # algorithmic bytes per launch.  Stage 1 reads Yn and M and writes Y* (2F+3 values);
     # stage 2 reads Y*, Yn and M and writes Y** (3F+3).  With the fused path, stage 3
     # with the top-down column pass reads Y**, Yn and M and writes rho plus the
     # elimination values (m, gamma, e_f: F+1 doubles), and the bottom-up pass reads
     # those and rho and writes the F-1 other fields; without it, stage 3 is a stage
     # launch (3F+3) and the column pass reads F and writes F-1 values.
-    if fused:
+    # With the column pass split over the stages (the plain step), stage 2 also
+    # writes m, gamma and alpha (3 doubles) and stage 3 reads alpha and writes rho
+    # and the nine e_f (F-1 doubles).
+    if fused and split:
+        algo = {asuca.KERNEL_STAGE: (2 * F + 3) * C * s,
+                asuca.KERNEL_STAGE_FACTOR: ((3 * F + 3) * s + 3 * 8) * C,
+                asuca.KERNEL_STAGE_COLUMN: ((2 * F + 3 + 1) * s + F * 8) * C,
+                asuca.KERNEL_COLUMN: ((F + 1) * 8 + F * s) * C,
+                asuca.KERNEL_REDUCE: 0.0}
+    elif fused:
         algo = {asuca.KERNEL_STAGE: ((2 * F + 3) + (3 * F + 3)) / 2.0 * C * s,
                 asuca.KERNEL_STAGE_COLUMN: ((2 * F + 3 + 1) * s + (F + 1) * 8) * C,
                 asuca.KERNEL_COLUMN: ((F + 1) * 8 + F * s) * C,

@@ -505,11 +505,13 @@ typedef enum {
     ASUCA_KERNEL_ADJ_COLUMN = 4,/* transpose of the column pass */
     ASUCA_KERNEL_ENSEMBLE = 5,  /* persistent ensemble kernel (all steps of a call) */
     ASUCA_KERNEL_DATAFLOW = 6,  /* persistent dataflow step kernel (up to 16 steps) */
-    ASUCA_KERNEL_STAGE_COLUMN = 7, /* third stage fused with the top-down column pass (its bottom-up half
-                                      is counted as ASUCA_KERNEL_COLUMN) */
+    ASUCA_KERNEL_STAGE_COLUMN = 7, /* third stage fused with the top-down column pass, or with its
+                                      elimination sweep (its bottom-up half is counted as
+                                      ASUCA_KERNEL_COLUMN) */
     ASUCA_KERNEL_ACOUSTIC = 8,  /* a stage of an acoustic short step nested in a long step (and the
                                    density perturbation it starts from) */
-    ASUCA_KERNEL_KINDS = 9
+    ASUCA_KERNEL_STAGE_FACTOR = 9, /* second stage carrying the FP64 factorisation of the column pass */
+    ASUCA_KERNEL_KINDS = 10
 } asuca_kernel_kind;
 
 /* When on, every kernel launch of later calls on this grid is bracketed by

@@ -132,7 +132,8 @@ TUNE_FUSED_COLUMN = 5
 KERNEL_DATAFLOW = 6
 KERNEL_STAGE_COLUMN = 7
 KERNEL_ACOUSTIC = 8
-KERNEL_KINDS = 9
+KERNEL_STAGE_FACTOR = 9
+KERNEL_KINDS = 10
 
 
 def library_path() -> str:

@@ -89,7 +89,7 @@ size_t elem_size(const asuca_grid *g) { return g->d.prec == ASUCA_FP64 ? 8 : 4; 
 long long col_slots(const asuca_grid *g) { return (long long)g->col_grid * COL_TPB; }
 
 struct StepLayout {
-    size_t ystar, ystar2, precip, partials, scratch, fscratch, df_order, df_counter, df_flags, df_partials, df_scratch,
+    size_t ystar, ystar2, precip, partials, scratch, fscratch, falpha, df_order, df_counter, df_flags, df_partials, df_scratch,
         total;
 };
 
@@ -128,7 +128,9 @@ StepLayout step_layout(const asuca_grid *g) {
     L.scratch = off;
     off = align_up(off + (size_t)g->d.nz * (g->F + 1) * col_slots(g) * sizeof(double));
     L.fscratch = off;
-    if (fused_path(g)) off = align_up(off + (size_t)g->d.nz * (g->F + 1) * (size_t)g->plane * sizeof(double));
+    if (fused_path(g)) off = align_up(off + (size_t)g->d.nz * fscratch_level(g->plane, g->F + 1) * sizeof(double));
+    L.falpha = off;
+    if (fused_path(g)) off = align_up(off + (size_t)g->d.nz * (size_t)g->plane * sizeof(double));
     L.df_order = L.df_counter = L.df_flags = L.df_partials = L.df_scratch = off;
     if (g->step_mode == 1) {
         const size_t R = (size_t)df_tiles_y(g), tiles = R * df_tiles_x(g);
@@ -376,10 +378,14 @@ asuca_status run_step(asuca_grid *g, asuca_state *st, const void *tend, double d
     for (int f = 0; f < MAXF; f++) sp.ybase[f] = yn[f];
     for (int q = 0; q < 3 && umaps; q++) sp.umap[q] = g->umap[q];
     const bool fused = fused_path(g);
+    // with the caller's mass fluxes (no per-stage work) the density after the
+    // step is known before stage 2, which then carries the factorisation
+    constexpr bool split = Pre::none;
     FusedParams<T> fp;
     if (fused) {
         fp.c = cp;
         fp.c.scratch = (double *)(ws + L.fscratch);
+        fp.c.alpha = (double *)(ws + L.falpha);
         fp.c.nslots = g->plane;
     }
     for (int n = 0; n < nsteps; n++) {
@@ -402,8 +408,16 @@ asuca_status run_step(asuca_grid *g, asuca_state *st, const void *tend, double d
             }
             sp.cdt = cdt[stg];
             if ((e = pre(n, stg, sp)) != cudaSuccess) return ASUCA_ERR_CUDA;
-            if ((e = timed(g, ASUCA_KERNEL_STAGE, s, [&] { return launch_stage<T>(sp, F, s); })) != cudaSuccess)
-                return ASUCA_ERR_CUDA;
+            if (fused && split && stg == 1) {
+                // stage 2 marching downward with the factorisation of every column
+                FusedParams<T> f2 = fp;
+                f2.s = sp;
+                f2.s.hcdt = cdt[2];
+                e = timed(g, ASUCA_KERNEL_STAGE_FACTOR, s, [&] { return launch_stage2_factor<T>(f2, F, s); });
+            } else {
+                e = timed(g, ASUCA_KERNEL_STAGE, s, [&] { return launch_stage<T>(sp, F, s); });
+            }
+            if (e != cudaSuccess) return ASUCA_ERR_CUDA;
         }
         cp.budgets = (budgets != nullptr) && (n == nsteps - 1);
         Range col_range(fused ? "RK stage 3 + column pass" : "column pass");
@@ -422,8 +436,9 @@ asuca_status run_step(asuca_grid *g, asuca_state *st, const void *tend, double d
                 fp.s.yout[f] = yn[f];
             }
             fp.s.cdt = cdt[2];
-            if ((e = timed(g, ASUCA_KERNEL_STAGE_COLUMN, s, [&] { return launch_stage3_column<T>(fp, F, s); })) !=
-                cudaSuccess)
+            if ((e = timed(g, ASUCA_KERNEL_STAGE_COLUMN, s, [&] {
+                     return split ? launch_stage3_sweep<T>(fp, F, s) : launch_stage3_column<T>(fp, F, s);
+                 })) != cudaSuccess)
                 return ASUCA_ERR_CUDA;
             ColumnParams<T> cu = fp.c;
             for (int f = 0; f < MAXF; f++) cu.y[f] = yn[f];
@@ -917,8 +932,8 @@ asuca_status run_record(asuca_grid *g, const asuca_state *init, const void *tend
 // ---- ensemble ------------------------------------------------------------
 
 struct EnsLayout {
-    size_t members, bar, per_member, partials, scratch, total;
-    std::vector<size_t> ystar, ystar2, precip;
+    size_t members, bar, per_member, partials, total;
+    std::vector<size_t> ystar, ystar2, precip, fscratch, falpha;
     int grid, threads;
 };
 
@@ -945,6 +960,8 @@ bool ens_layout(asuca_grid *const *grids, int M, EnsLayout *L) {
     L->ystar.resize(M);
     L->ystar2.resize(M);
     L->precip.resize(M);
+    L->fscratch.resize(M);
+    L->falpha.resize(M);
     int maxcol = 0;
     for (int m = 0; m < M; m++) {
         const size_t ps = padded_state_elems(grids[m]) * elem_size(grids[m]);
@@ -954,12 +971,15 @@ bool ens_layout(asuca_grid *const *grids, int M, EnsLayout *L) {
         off = align_up(off + ps);
         L->precip[m] = off;
         off = align_up(off + (size_t)grids[m]->plane * sizeof(double));
+        // the column pass split over stages 2 and 3 (fused scratch, alpha)
+        L->fscratch[m] = off;
+        off = align_up(off + (size_t)grids[m]->d.nz * fscratch_level(grids[m]->plane, g0->F + 1) * sizeof(double));
+        L->falpha[m] = off;
+        off = align_up(off + (size_t)grids[m]->d.nz * (size_t)grids[m]->plane * sizeof(double));
         if (grids[m]->col_grid > maxcol) maxcol = grids[m]->col_grid;
     }
     L->partials = off;
     off = align_up(off + (size_t)maxcol * (g0->F + 1) * sizeof(double));
-    L->scratch = off;
-    off = align_up(off + (size_t)g0->d.nz * (g0->F + 1) * (size_t)grid * L->threads * sizeof(double));
     L->total = off;
     return true;
 }
@@ -1009,11 +1029,15 @@ asuca_status ens_enqueue(asuca_grid *const *grids, asuca_state *states, const do
                 sp.yout[f] = out[f];
             }
             sp.cdt = cdt[stg];
+            sp.hcdt = cdt[2];   // stage 2's factorisation takes the density after the step
             mb[m].stage[stg] = sp;
         }
         ColumnParams<T> cp = column_params<T>(g, dt);
         for (int f = 0; f < MAXF; f++) cp.y[f] = yn[f];
         cp.precip_col = (double *)(ws + L.precip[m]);
+        cp.scratch = (double *)(ws + L.fscratch[m]);
+        cp.alpha = (double *)(ws + L.falpha[m]);
+        cp.nslots = g->plane;
         cp.budgets = 0;
         mb[m].col = cp;
         const int tx = (g->d.nx + TX - 1) / TX, ty = (g->d.ny + TY - 1) / TY;
@@ -1040,7 +1064,6 @@ asuca_status ens_enqueue(asuca_grid *const *grids, asuca_state *states, const do
     ep.bar_gen = ep.bar_count + 1;
     ep.bar_extra = g0->barrier_extra;
     ep.status = g0->status_dev;
-    ep.scratch = (double *)(ws + L.scratch);
     if (nsteps > 0 &&
         timed(g0, ASUCA_KERNEL_ENSEMBLE, s, [&] { return launch_ensemble<T>(ep, F, (int)g0->d.lim, TY, L.grid, s, nullptr); }) !=
             cudaSuccess)

@@ -217,98 +217,249 @@ __device__ __forceinline__ void column_one(const ColumnParams<T> &p, long long c
 
 namespace asuca {
 
-// ------------------------------------------------------------------ column pass fused into stage 3
+// The per-level constants of the top-down column pass, gathered into one
+// record per level (ColDownHook reads a level's record from shared memory in
+// three 16-byte loads instead of one constant-bank load per value).
+template <typename T>
+struct __align__(16) ColLevel {
+    double kc_lo;     // kc[k - 1]: dt K / dzc / 2 of face k - 1/2 (0 at k = 0)
+    double dz;        // dz_k
+    double dzr_up;    // dz_{k+1} / dz_k
+    double dzr_dn1;   // dzr_dn[k + 1] = dz_k / dz_{k+1} (0 at the top level)
+    T thref, dzT, sedr, pad;   // theta_ref(z_k), dz_k and 1 / (dz_k + dt v) in T
+};
 
-// The top-down half of the column pass, run by the thread that computes the
-// column in the third RK stage while that stage marches downward: each level's
-// stage result goes through relaxation and sedimentation and into the
-// elimination (column_one's top-down pass, operation for operation), and the
-// per-level values m, gamma, e_f go to a scratch laid out [nz][F + 1][plane]
-// (entry (k, q) of column col at (k (F + 1) + q) plane + col), for
-// column_up_kernel's bottom-up back substitution.  The density result is
-// written to the state here; rho*theta and the tracers are written by the back
-// substitution.  The elimination of level k needs rho of level k - 1, which
-// the stage hands over as rho_next.
+// Fill the records of levels 0 .. nz-1 (threads tid of nthr share the work).
+template <typename T>
+__device__ __forceinline__ void fill_col_levels(const ColumnParams<T> &c, ColLevel<T> *tab, int tid, int nthr) {
+    for (int k = tid; k < c.nz; k += nthr) {
+        ColLevel<T> L;
+        L.kc_lo = k > 0 ? c.kc[k - 1] : 0.0;
+        L.dz = c.dz[k];
+        L.dzr_up = c.dzr_up[k];
+        L.dzr_dn1 = k + 1 < c.nz ? c.dzr_dn[k + 1] : 0.0;
+        L.thref = c.thref[k];
+        L.dzT = c.dzT[k];
+        L.sedr = c.sedr[k];
+        L.pad = T(0);
+        tab[k] = L;
+    }
+}
+
+// ------------------------------------------------------------------ column pass fused into the stages
+
+// The top-down half of the column pass runs inside the stage kernels, which
+// march the levels from the top down and hand each level's result to a hook:
+// hook.level(k, out, valid, rho_next, rho_h), where out is the stage's result,
+// rho_next the density result of the next level of the march, and rho_h the
+// density after the whole step when the hook asks for it (own_rho).  Hooks
+// with keep_output let the stage write its result as usual.
+//
+// The per-level values m, gamma, e_f go to the fused scratch (fscratch_level /
+// fscratch_col: quantity q = 0 m, 1 gamma, 2 + f e_f) for column_up_kernel's
+// bottom-up back substitution.  Two arrangements, with the same operations
+// as column_one's top-down pass and so the same results:
+//  * ColDownHook in stage 3: relaxation, sedimentation, factorisation and
+//    elimination of every level;
+//  * FactorHook in stage 2 and SweepHook in stage 3: the factorisation depends
+//    only on the density after the step, which the mass fluxes fix before the
+//    step begins (the density's flux is M), so stage 2 computes it (m, gamma
+//    to the scratch, alpha to an array of its own) and stage 3 keeps only the
+//    relaxation, the sedimentation and the nine-field elimination sweep.  The
+//    FP64 work is then split between two kernels whose FP32 stencils it
+//    overlaps.
+// tab holds the per-level records (ColLevel) in shared memory.
+
+// Relaxation and sedimentation of one level (top-down), in T.
+template <typename T, int NF>
+__device__ __forceinline__ void column_physics_level(const ColumnParams<T> &c, const ColLevel<T> &L, int k, T rho,
+                                                     T (&x)[NF - 1], T &P, unsigned own) {
+    constexpr int NT = NF - 1;
+    // (i) relaxation of theta
+    if (c.do_relax) {
+        T th = x[0] / rho;
+        th = (th + c.relax_r * L.thref) * c.relax_inv;
+        x[0] = rho * th;
+    }
+    // (ii) sedimentation of one tracer, top-down (the last tracer as a
+    // compile-time index, any other by compare)
+    if (c.do_sed) {
+        if (c.sed == NF - 1) {
+            x[NT - 1] = (x[NT - 1] * L.dzT + c.sed_dt * P) * L.sedr;
+            P = c.sed_v * x[NT - 1];
+        } else {
+#pragma unroll
+            for (int f = 1; f < NT; f++) {
+                if (f + 1 == c.sed) {
+                    x[f] = (x[f] * L.dzT + c.sed_dt * P) * L.sedr;
+                    P = c.sed_v * x[f];
+                }
+            }
+        }
+        if (k == 0) c.precip_col[own] += c.dt * to_f64(P) * c.dxdy;
+    }
+}
+
+// The factorisation of one level (top-down, scaled unknowns): stores m and
+// the next level's gamma at a (the level's scratch entries, ls the level
+// stride), carries g and m to the next level, returns alpha.
+template <typename T>
+__device__ __forceinline__ double factor_level(const ColLevel<T> &L, int k, int nz, T rho, T rho_next, double &g_hi,
+                                               double &m_up, double *a, size_t ls) {
+    const double rd = to_f64(rho);
+    const double rd_dn = (k > 0) ? to_f64(rho_next) : 0.0;
+    const double g_lo = (k > 0) ? L.kc_lo * (rd_dn + rd) : 0.0;
+    const double b = fma(rd, L.dz, g_lo + g_hi);
+    const double t = g_hi * m_up;
+    const double m = rcp_f64(fma(-g_hi, t, b));
+    const double alpha = t * L.dzr_up;
+    a[0] = m;
+    if (k < nz - 1) a[ls + 32] = g_hi * m * L.dzr_dn1;
+    g_hi = g_lo;
+    m_up = m;
+    return alpha;
+}
+
+// Relaxation, sedimentation, factorisation and elimination in stage 3.  The
+// density result is written to the state here; rho*theta and the tracers are
+// written by the back substitution.
 template <typename T, int NF>
 struct ColDownHook {
-    static constexpr bool active = true;
+    static constexpr bool active = true, keep_output = false, own_rho = false;
     static constexpr int NT = NF - 1;
     static constexpr int NQ = NF + 1;   // m, gamma, e[NT]
     const ColumnParams<T> &c;
+    const ColLevel<T> *tab;
     T *rho_out;
     double *sc;
-    size_t pl;
+    size_t pl, ls;
     unsigned own;
     double g_hi, m_up;
     double e_up[NT];
     T P;
 
-    __device__ __forceinline__ ColDownHook(const ColumnParams<T> &cp, T *rho, unsigned own_)
-        : c(cp), rho_out(rho), sc(cp.scratch + own_), pl((size_t)cp.plane), own(own_), g_hi(0.0), m_up(0.0), P(T(0)) {
+    __device__ __forceinline__ ColDownHook(const ColumnParams<T> &cp, const ColLevel<T> *tab_, T *rho, unsigned own_)
+        : c(cp), tab(tab_), rho_out(rho), sc(cp.scratch + fscratch_col(own_, NQ)), pl((size_t)cp.plane),
+          ls((size_t)fscratch_level(cp.plane, NQ)), own(own_), g_hi(0.0), m_up(0.0), P(T(0)) {
 #pragma unroll
         for (int f = 0; f < NT; f++) e_up[f] = 0.0;
     }
 
     template <typename U, int NF2>
-    __device__ __forceinline__ void level(int k, const U (&out)[NF2], bool valid, U rho_next) {
+    __device__ __forceinline__ void level(int k, const U (&out)[NF2], bool valid, U rho_next, U) {
         static_assert(NF2 == NF, "field count");
         if (!valid) return;
         const T rho = out[0];
         rho_out[(size_t)k * pl + own] = rho;
+        const ColLevel<T> L = tab[k];
         T x[NT];
 #pragma unroll
         for (int f = 0; f < NT; f++) x[f] = out[f + 1];
-        // (i) relaxation of theta
-        if (c.do_relax) {
-            T th = x[0] / rho;
-            th = (th + c.relax_r * c.thref[k]) * c.relax_inv;
-            x[0] = rho * th;
-        }
-        // (ii) sedimentation of one tracer, top-down
-        if (c.do_sed) {
-#pragma unroll
-            for (int f = 1; f < NT; f++) {
-                if (f + 1 == c.sed) {
-                    x[f] = (x[f] * c.dzT[k] + c.sed_dt * P) * c.sedr[k];
-                    P = c.sed_v * x[f];
-                }
-            }
-            if (k == 0) c.precip_col[own] += c.dt * to_f64(P) * c.dxdy;
-        }
+        column_physics_level<T, NF>(c, L, k, rho, x, P, own);
         // (iii) forward elimination on scaled unknowns
-        const double rd = to_f64(rho);
-        const double rd_dn = (k > 0) ? to_f64(rho_next) : 0.0;
-        const double g_lo = (k > 0) ? c.kc[k - 1] * (rd_dn + rd) : 0.0;
-        const double b = fma(rd, c.dz[k], g_lo + g_hi);
-        const double t = g_hi * m_up;
-        const double m = rcp_f64(fma(-g_hi, t, b));
-        const double alpha = t * c.dzr_up[k];
-        sc[(size_t)(k * NQ + 0) * pl] = m;
-        if (k < c.nz - 1) sc[(size_t)((k + 1) * NQ + 1) * pl] = g_hi * m * c.dzr_dn[k + 1];
+        double *a = sc + (size_t)k * ls;
+        const double alpha = factor_level<T>(L, k, c.nz, rho, rho_next, g_hi, m_up, a, ls);
 #pragma unroll
         for (int f = 0; f < NT; f++) {
             const double e = fma(alpha, e_up[f], to_f64(x[f]));
-            sc[(size_t)(k * NQ + 2 + f) * pl] = e;
+            a[32 * (2 + f)] = e;
             e_up[f] = e;
         }
-        g_hi = g_lo;
-        m_up = m;
+    }
+    __device__ __forceinline__ void done(bool) {}
+};
+
+// The factorisation in stage 2 (the stage's own result is written as usual):
+// from the density after the step (rho_h, rho_next), m and gamma to the fused
+// scratch and alpha to c.alpha ([nz][plane]).
+template <typename T, int NF>
+struct FactorHook {
+    static constexpr bool active = true, keep_output = true, own_rho = true;
+    static constexpr int NQ = NF + 1;
+    const ColumnParams<T> &c;
+    const ColLevel<T> *tab;
+    double *sc, *alpha_out;
+    size_t pl, ls;
+    double g_hi, m_up;
+
+    __device__ __forceinline__ FactorHook(const ColumnParams<T> &cp, const ColLevel<T> *tab_, unsigned own)
+        : c(cp), tab(tab_), sc(cp.scratch + fscratch_col(own, NQ)), alpha_out(cp.alpha + own),
+          pl((size_t)cp.plane), ls((size_t)fscratch_level(cp.plane, NQ)), g_hi(0.0), m_up(0.0) {}
+
+    template <typename U, int NF2>
+    __device__ __forceinline__ void level(int k, const U (&)[NF2], bool valid, U rho_next, U rho_h) {
+        if (!valid) return;
+        const ColLevel<T> L = tab[k];
+        alpha_out[(size_t)k * pl] = factor_level<T>(L, k, c.nz, rho_h, rho_next, g_hi, m_up, sc + (size_t)k * ls, ls);
+    }
+    __device__ __forceinline__ void done(bool) {}
+};
+
+// Relaxation, sedimentation and the elimination sweep in stage 3, after
+// FactorHook in stage 2 (alpha read from c.alpha one level ahead).
+template <typename T, int NF>
+struct SweepHook {
+    static constexpr bool active = true, keep_output = false, own_rho = false;
+    static constexpr int NT = NF - 1;
+    static constexpr int NQ = NF + 1;
+    const ColumnParams<T> &c;
+    const ColLevel<T> *tab;
+    T *rho_out;
+    double *sc;
+    const double *alpha_in;
+    size_t pl, ls;
+    unsigned own;
+    double alpha_k;   // alpha of the level the march reaches next
+    double e_up[NT];
+    T P;
+
+    __device__ __forceinline__ SweepHook(const ColumnParams<T> &cp, const ColLevel<T> *tab_, T *rho, unsigned own_)
+        : c(cp), tab(tab_), rho_out(rho), sc(cp.scratch + fscratch_col(own_, NQ)), alpha_in(cp.alpha + own_),
+          pl((size_t)cp.plane), ls((size_t)fscratch_level(cp.plane, NQ)), own(own_), P(T(0)) {
+        alpha_k = alpha_in[(size_t)(cp.nz - 1) * pl];
+#pragma unroll
+        for (int f = 0; f < NT; f++) e_up[f] = 0.0;
+    }
+
+    template <typename U, int NF2>
+    __device__ __forceinline__ void level(int k, const U (&out)[NF2], bool valid, U, U) {
+        static_assert(NF2 == NF, "field count");
+        if (!valid) return;
+        const double alpha = alpha_k;
+        if (k > 0) alpha_k = alpha_in[(size_t)(k - 1) * pl];
+        const T rho = out[0];
+        rho_out[(size_t)k * pl + own] = rho;
+        const ColLevel<T> L = tab[k];
+        T x[NT];
+#pragma unroll
+        for (int f = 0; f < NT; f++) x[f] = out[f + 1];
+        column_physics_level<T, NF>(c, L, k, rho, x, P, own);
+        double *a = sc + (size_t)k * ls;
+#pragma unroll
+        for (int f = 0; f < NT; f++) {
+            const double e = fma(alpha, e_up[f], to_f64(x[f]));
+            a[32 * (2 + f)] = e;
+            e_up[f] = e;
+        }
     }
     __device__ __forceinline__ void done(bool) {}
 };
 
 // The bottom-up half of the column pass after ColDownHook, for one column:
-// back substitution from the full-size scratch (p.scratch, [nz][F + 1][plane]),
+// back substitution from the fused scratch (fscratch_level / fscratch_col),
 // (rho phi)_k = sigma_k z_k for rho*theta and every tracer (column_one's
 // bottom-up pass, operation for operation), and the column's budget partials
-// in cs when p.budgets is set.
+// in cs when p.budgets is set.  Float results: the level's nine solutions and
+// its m are narrowed together (d2f_fast, the exact path for the whole level
+// when one of them lies outside the float normal range).
 template <typename T, int NF>
 __device__ __forceinline__ void column_up_one(const ColumnParams<T> &p, long long col, ColSum<T> (&cs)[NF]) {
     constexpr int NT = NF - 1;
     constexpr int NQ = NF + 1;
     const size_t pl = (size_t)p.plane;
+    const size_t ls = (size_t)fscratch_level(p.plane, NQ);
     const int nz = p.nz;
-    const double *sc = p.scratch + col;
+    const double *sc = p.scratch + fscratch_col(col, NQ);
     double z[NT];
 #pragma unroll
     for (int f = 0; f < NT; f++) z[f] = 0.0;
@@ -316,27 +467,47 @@ __device__ __forceinline__ void column_up_one(const ColumnParams<T> &p, long lon
     double mk = sc[0], gk = 0.0;
     double ek[NT];
 #pragma unroll
-    for (int f = 0; f < NT; f++) ek[f] = sc[(size_t)(2 + f) * pl];
+    for (int f = 0; f < NT; f++) ek[f] = sc[32 * (2 + f)];
     T rk = p.y[0][ob];
     for (int k = 0; k < nz; k++, ob += pl) {
         double mn = 0.0, gn = 0.0, en[NT];
         T rn = T(0);
         if (k + 1 < nz) {   // prefetch level k+1
-            mn = sc[(size_t)((k + 1) * NQ + 0) * pl];
-            gn = sc[(size_t)((k + 1) * NQ + 1) * pl];
+            const double *a = sc + (size_t)(k + 1) * ls;
+            mn = a[0];
+            gn = a[32];
 #pragma unroll
-            for (int f = 0; f < NT; f++) en[f] = sc[(size_t)((k + 1) * NQ + 2 + f) * pl];
+            for (int f = 0; f < NT; f++) en[f] = a[32 * (2 + f)];
             rn = p.y[0][ob + pl];
         }
-        const double sigma = to_f64(rk) * p.dz[k] * mk;
-        const float sf = (sizeof(T) == 4) ? (float)rk * (float)p.dzT[k] * d2f_bits(mk) : 0.f;
         if (p.budgets) cs[0].add(rk, p.dz[k], p.dzT[k], p.dzlo[k]);
 #pragma unroll
+        for (int f = 0; f < NT; f++) z[f] = fma(gk, z[f], ek[f]);
+        T u[NT];
+        if constexpr (sizeof(T) == 4) {
+            // sigma in float from rho, dz and m rounded once; z rounded once
+            bool ok = true;
+            float zf[NT];
+            float mf = d2f_fast(mk, ok);
+#pragma unroll
+            for (int f = 0; f < NT; f++) zf[f] = d2f_fast(z[f], ok);
+            if (!ok) {
+                mf = d2f_bits(mk);
+#pragma unroll
+                for (int f = 0; f < NT; f++) zf[f] = d2f_bits(z[f]);
+            }
+            const float sf = rk * p.dzT[k] * mf;
+#pragma unroll
+            for (int f = 0; f < NT; f++) u[f] = zf[f] * sf;
+        } else {
+            const double sigma = rk * p.dz[k] * mk;
+#pragma unroll
+            for (int f = 0; f < NT; f++) u[f] = sigma * z[f];
+        }
+#pragma unroll
         for (int f = 0; f < NT; f++) {
-            z[f] = fma(gk, z[f], ek[f]);
-            const T u = scale_out<T>(z[f], sigma, sf);
-            p.y[f + 1][ob] = u;
-            if (p.budgets) cs[f + 1].add(u, p.dz[k], p.dzT[k], p.dzlo[k]);
+            p.y[f + 1][ob] = u[f];
+            if (p.budgets) cs[f + 1].add(u[f], p.dz[k], p.dzT[k], p.dzlo[k]);
         }
         if (k + 1 < nz) {
             mk = mn;

@@ -95,6 +95,7 @@ struct StageParams {
     long long opitch, oplane;   // padded buffers: pitch, and level stride (elements) of one field plane
     long long prow, plev;       // padded output: row and level strides of the pair layout (elements)
     T cdt, rdx, rdy;
+    T hcdt;                 // a hook with own_rho: the density it receives is Y^n + hcdt R (the step's: dt)
     T rdz[MAXNZ];           // 1 / dz_k
 };
 
@@ -113,6 +114,7 @@ struct ColumnParams {
     double *partials;       // [gridDim.x][F + 1] budget partials (sum over columns of sum_k f dz)
     double *scratch;        // [nz][F + 1][nslots]
     long long nslots;
+    double *alpha;          // the fused column pass split over stages 2 and 3: [nz][plane] alpha of each level
     double *rec;            // if set: [nz][F + 2][plane] record of the diffusion solve for the adjoint:
                             // m, alpha, gamma of each level and the scaled solution z of each field
     T dzT[MAXNZ];           // dz_k (rounded to T)
@@ -165,6 +167,20 @@ __device__ __forceinline__ float d2f_bits(double x) {
     const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
     const uint32_t ea = (hi >> 20) & 0x7ffu;
     if (ea < 897u || ea > 1150u) return d2f_hw(x);
+    uint32_t mag = (((hi & 0x7fffffffu) - (896u << 20)) << 3) | (lo >> 29);
+    const uint32_t rem = lo & 0x1fffffffu;
+    mag += (rem > 0x10000000u || (rem == 0x10000000u && (mag & 1u))) ? 1u : 0u;
+    return __uint_as_float((hi & 0x80000000u) | mag);
+}
+
+// Narrowing without a branch, for the values a column level converts
+// together: exact for doubles in the float normal range (d2f_bits's bit
+// path); ok is cleared otherwise, and the caller then converts the whole level
+// again with d2f_bits (one branch per level instead of one per value).
+__device__ __forceinline__ float d2f_fast(double x, bool &ok) {
+    const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+    const uint32_t ea = (hi >> 20) & 0x7ffu;
+    ok = ok && (ea - 897u) < 254u;   // d2f_bits's bit path: ea in [897, 1150]
     uint32_t mag = (((hi & 0x7fffffffu) - (896u << 20)) << 3) | (lo >> 29);
     const uint32_t rem = lo & 0x1fffffffu;
     mag += (rem > 0x10000000u || (rem == 0x10000000u && (mag & 1u))) ? 1u : 0u;
@@ -423,6 +439,27 @@ struct FusedParams {
 };
 template <typename T>
 cudaError_t launch_stage3_column(const FusedParams<T> &p, int nf, cudaStream_t s);
+// The fused column pass split over two stages: stage 2 (padded output, as
+// launch_stage) with the FP64 factorisation into p.c.scratch and p.c.alpha,
+// then stage 3 with the relaxation, sedimentation and elimination sweep.
+template <typename T>
+cudaError_t launch_stage2_factor(const FusedParams<T> &p, int nf, cudaStream_t s);
+template <typename T>
+cudaError_t launch_stage3_sweep(const FusedParams<T> &p, int nf, cudaStream_t s);
+
+// Scratch of the fused column pass (ColDownHook writes it, column_up_kernel
+// reads it): per level, the columns in groups of 32, each group's F + 1
+// quantities as 32 consecutive doubles.  A warp's store or load of one
+// quantity is one contiguous 256-byte segment, and the F + 1 quantities of a
+// column and level lie at fixed offsets (32 q) from one address:
+//   entry (k, q, col) at k LS + (col / 32) (F + 1) 32 + 32 q + col % 32,
+//   LS = ceil(plane / 32) (F + 1) 32 doubles.
+__host__ __device__ __forceinline__ long long fscratch_level(long long plane, int nq) {
+    return (plane + 31) / 32 * nq * 32;
+}
+__host__ __device__ __forceinline__ long long fscratch_col(long long col, int nq) {
+    return (col >> 5) * nq * 32 + (col & 31);
+}
 template <typename T>
 cudaError_t launch_column_up(const ColumnParams<T> &p, int nf, int grid, cudaStream_t s);
 

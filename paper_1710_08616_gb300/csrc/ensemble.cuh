@@ -1,6 +1,8 @@
 // Ensemble of members with uneven horizontal domains advanced in one
 // persistent, cooperative launch.  For each step the kernel runs three stage
-// phases and one column phase; a phase walks a flattened list of work items
+// phases, the second and third carrying the top-down half of the column pass
+// (FactorHook, SweepHook), and one back-substitution phase; a phase walks a
+// flattened list of work items
 // (member, tile) or (member, column), dealt round-robin to the resident CTAs,
 // and ends at a device-wide barrier.  Members never share a tile, so each
 // member's result equals its own single-member step bit for bit.
@@ -13,8 +15,7 @@
 
 #include "ensemble_params.cuh"
 #include "smem_attr.cuh"
-#include "column_impl.cuh"
-#include "stage_impl.cuh"
+#include "fused_impl.cuh"
 
 namespace asuca {
 
@@ -61,14 +62,21 @@ __device__ __forceinline__ int member_of(const EnsMember<T> *m, int nm, long lon
     return lo;
 }
 
+// Per step: stage 1 (upward march); stage 2 marching downward with the FP64
+// factorisation of every column (FactorHook); stage 3 marching downward with
+// the relaxation, sedimentation and elimination sweep (SweepHook); then the
+// bottom-up back substitution over the flattened columns.  A tile of stages 2
+// and 3 first loads its member's per-level records into shared memory.
 template <typename T, int NF, int LIM, int TYV>
 __global__ void __launch_bounds__(32 * TYV, StageShape<T, NF, TYV>::MIN_BLOCKS)
     ensemble_kernel(const __grid_constant__ EnsParams<T> e) {
     using S = StageShape<T, NF, TYV>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
+    ColLevel<T> *tab = reinterpret_cast<ColLevel<T> *>(smem_raw + FusedSmem<T, NF, TYV>::TILE);
     const unsigned target = gridDim.x + (unsigned)e.bar_extra;
-    const long long nth = (long long)gridDim.x * blockDim.x * blockDim.y;
-    const long long gtid = (long long)blockIdx.x * blockDim.x * blockDim.y + threadIdx.y * blockDim.x + threadIdx.x;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x, nthr = blockDim.x * blockDim.y;
+    const long long nth = (long long)gridDim.x * nthr;
+    const long long gtid = (long long)blockIdx.x * nthr + tid;
     for (int n = 0; n < e.nsteps; n++) {
         for (int stg = 0; stg < 3; stg++) {
             bool bad = false;
@@ -76,12 +84,27 @@ __global__ void __launch_bounds__(32 * TYV, StageShape<T, NF, TYV>::MIN_BLOCKS)
                 const int m = member_of(e.members, e.nmembers, t, true);
                 const EnsMember<T> &mb = e.members[m];
                 const long long lt = t - mb.tile0;
-                const int tx = (int)(lt % mb.tiles_x), ty = (int)(lt / mb.tiles_x);
+                const int i0 = (int)(lt % mb.tiles_x) * S::TX, j0 = (int)(lt / mb.tiles_x) * S::TY;
                 const StageParams<T> &sp = mb.stage[stg];
-                if (stage_tile<T, NF, LIM, false, TYV>(sp, &sp.tmap, tx * S::TX, ty * S::TY, smem_raw)) {
-                    bad = true;
-                    break;
+                if (stg == 0) {
+                    bad = stage_tile<T, NF, LIM, false, TYV>(sp, &sp.tmap, i0, j0, smem_raw);
+                } else {
+                    __syncthreads();   // the previous tile is done with the records
+                    fill_col_levels(mb.col, tab, tid, nthr);
+                    __syncthreads();
+                    const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
+                    const unsigned own = (i < sp.nx && j < sp.ny) ? (unsigned)(j * sp.nx + i) : 0u;
+                    if (stg == 1) {
+                        FactorHook<T, NF> h(mb.col, tab, own);
+                        bad = stage_tile_h<T, NF, LIM, false, TYV, true, FactorHook<T, NF>, LAYOUT_PAIR>(
+                            sp, &sp.tmap, i0, j0, smem_raw, h);
+                    } else {
+                        SweepHook<T, NF> h(mb.col, tab, sp.yout[0], own);
+                        bad = stage_tile_h<T, NF, LIM, false, TYV, true, SweepHook<T, NF>, LAYOUT_PAIR>(
+                            sp, &sp.tmap, i0, j0, smem_raw, h);
+                    }
                 }
+                if (bad) break;
             }
             if (bad || !ens_barrier(e.bar_count, e.bar_gen, target, e.status)) return;
         }
@@ -89,7 +112,7 @@ __global__ void __launch_bounds__(32 * TYV, StageShape<T, NF, TYV>::MIN_BLOCKS)
             const int m = member_of(e.members, e.nmembers, c, false);
             const EnsMember<T> &mb = e.members[m];
             ColSum<T> cs[NF];
-            column_one<T, NF>(mb.col, c - mb.col0, e.scratch + gtid, nth, cs);
+            column_up_one<T, NF>(mb.col, c - mb.col0, cs);
         }
         if (!ens_barrier(e.bar_count, e.bar_gen, target, e.status)) return;
     }
@@ -99,12 +122,13 @@ template <typename T, int NF, int LIM, int TYV>
 static cudaError_t ens_launch_lim(const EnsParams<T> &e, int grid, cudaStream_t s, int *grid_out) {
     using S = StageShape<T, NF, TYV>;
     static std::atomic<unsigned long long> attr_done{0};   // devices whose attribute is set
-    const cudaError_t r = set_smem_once(ensemble_kernel<T, NF, LIM, TYV>, (int)S::SMEM_BYTES, attr_done);
+    constexpr size_t bytes = FusedSmem<T, NF, TYV>::MAX_BYTES;   // the tile's and the per-level records
+    const cudaError_t r = set_smem_once(ensemble_kernel<T, NF, LIM, TYV>, (int)bytes, attr_done);
     if (r != cudaSuccess) return r;
     if (grid_out) {   // size query: resident CTAs per SM times SMs
         int per_sm = 0, dev = 0, nsm = 0;
         cudaError_t r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ensemble_kernel<T, NF, LIM, TYV>,
-                                                                      32 * S::TY, S::SMEM_BYTES);
+                                                                      32 * S::TY, bytes);
         if (r != cudaSuccess) return r;
         if ((r = cudaGetDevice(&dev)) != cudaSuccess) return r;
         if ((r = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return r;
@@ -114,7 +138,7 @@ static cudaError_t ens_launch_lim(const EnsParams<T> &e, int grid, cudaStream_t 
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(32, S::TY);
-    cfg.dynamicSmemBytes = S::SMEM_BYTES;
+    cfg.dynamicSmemBytes = bytes;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;

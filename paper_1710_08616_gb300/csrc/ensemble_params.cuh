@@ -9,7 +9,7 @@ namespace asuca {
 template <typename T>
 struct EnsMember {
     StageParams<T> stage[3];   // the three stage launches of one step
-    ColumnParams<T> col;       // the column pass (scratch and slot count come from EnsParams)
+    ColumnParams<T> col;       // the column pass: its fused scratch and alpha array are the member's own
     long long tile0;           // first flattened tile of this member
     long long col0;            // first flattened column of this member
     int tiles_x;
@@ -23,7 +23,6 @@ struct EnsParams {
     unsigned *bar_count, *bar_gen;
     int bar_extra;             // 0; a test sets 1 so that the barrier can never complete
     int *status;
-    double *scratch;           // column-solve scratch, one slot per thread of the grid
 };
 
 // grid_out != nullptr: only store the co-resident grid size in *grid_out

@@ -1,0 +1,9 @@
+// Stage 2 with the FP64 factorisation of the column pass, double fields, 8-row tiles.
+#include "fused_impl.cuh"
+
+namespace asuca {
+template <>
+cudaError_t launch_stage2_factor<double>(const FusedParams<double> &p, int nf, cudaStream_t s) {
+    return launch_fused_ty<double, 8, 2>(p, nf, s);
+}
+}  // namespace asuca

@@ -120,9 +120,9 @@ __device__ __forceinline__ void cp_async_wait() {
 // may reuse the same shared memory and mbarriers.
 // The default output of a tile: the stage result is written to p.yout.
 struct NoHook {
-    static constexpr bool active = false;
+    static constexpr bool active = false, keep_output = true, own_rho = false;
     template <typename T, int NF>
-    __device__ __forceinline__ void level(int, const T (&)[NF], bool, T) {}
+    __device__ __forceinline__ void level(int, const T (&)[NF], bool, T, T) {}
     __device__ __forceinline__ void done(bool) {}
 };
 
@@ -137,10 +137,13 @@ template <> struct Vec2<double> { using type = double2; };
 // DOWN marches the levels from the top down (the ring, the faces and the
 // carried flux all run in march order; level k = nz - 1 - t at march step t),
 // which gives the same arithmetic per cell, so the result is bit-identical to
-// the upward march.  An active Hook takes each level's result instead of the
-// writes to p.yout: hook.level(k, out, valid, rho_next), where rho_next is the
-// density result of the next level of the march (the same expression that
-// level will evaluate), then hook.done(valid) after the last level.
+// the upward march.  An active Hook takes each level's result, instead
+// of the writes to p.yout unless it has keep_output: hook.level(k, out, valid,
+// rho_next, rho_h), where rho_next is the density result of the next level of
+// the march (the same expression that level will evaluate); a hook with
+// own_rho receives in rho_h and rho_next the density Y^n + hcdt R instead of
+// the stage's (the same expression with p.hcdt for cdt).  hook.done(valid)
+// follows the last level.
 // The fields are processed in pairs (1, 2), (3, 4), ...: a pair shares every
 // operation of its face reconstruction and divergence (packed FP32x2 for
 // float), and with the pair layout its operands arrive in one load.
@@ -534,7 +537,8 @@ __device__ __forceinline__ bool stage_tile_h(const StageParams<T> &p, const CUte
         const T az = -cdt * p.rdz[k];
         // z flux difference F(k+1/2) - F(k-1/2): ahead minus carried upward,
         // carried minus ahead downward (the same operands either way)
-        const T out0 = fma(az, DOWN ? zlo0 - mwp : mwp - zlo0, fma(ay, mvp - mvm, fma(ax, mup - mum, yb0)));
+        const T dzf0 = DOWN ? zlo0 - mwp : mwp - zlo0;
+        const T out0 = fma(az, dzf0, fma(ay, mvp - mvm, fma(ax, mup - mum, yb0)));
         zlo0 = mwp;
         T2 out2[NPF];
 #pragma unroll
@@ -569,12 +573,17 @@ __device__ __forceinline__ bool stage_tile_h(const StageParams<T> &p, const CUte
             }
         }
         if (Hook::active) {
-            // the density result of the next march step, evaluated as that step will
+            // the density result of the next march step, evaluated as that step
+            // will (with the hook's coefficient for an own_rho hook, which also
+            // receives this level's density so evaluated)
+            const T hc = Hook::own_rho ? p.hcdt : cdt;
+            const T hx = Hook::own_rho ? -hc * p.rdx : ax, hy = Hook::own_rho ? -hc * p.rdy : ay;
+            const T rho_h = Hook::own_rho ? fma(-hc * p.rdz[k], dzf0, fma(hy, mvp - mvm, fma(hx, mup - mum, yb0))) : out0;
             T rho_next = T(0);
             if (t + 1 < nz) {
-                const T az_n = -cdt * p.rdz[level_of(t + 1)];
+                const T az_n = -hc * p.rdz[level_of(t + 1)];
                 rho_next = fma(az_n, DOWN ? mwp - nmwp : nmwp - mwp,
-                               fma(ay, nmvp - nmvm, fma(ax, nmup - nmum, nrho)));
+                               fma(hy, nmvp - nmvm, fma(hx, nmup - nmum, nrho)));
             }
             T out[NF];
             out[0] = out0;
@@ -583,7 +592,10 @@ __device__ __forceinline__ bool stage_tile_h(const StageParams<T> &p, const CUte
                 out[2 * q + 1] = out2[q].x;
                 if (2 * q + 2 <= NT) out[2 * q + 2] = out2[q].y;
             }
-            hook.template level<T, NF>(k, out, valid, rho_next);
+            hook.template level<T, NF>(k, out, valid, rho_next, rho_h);
+        }
+        if (Hook::active && !Hook::keep_output) {
+            // the hook took the level
         } else if (valid) {
             if (p.out_padded) {
                 // the next stage reads phi = (rho phi) / rho, in pairs; the
