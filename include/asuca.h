@@ -58,7 +58,9 @@ typedef enum {
     ASUCA_ERR_WORKSPACE = 3,    /* workspace missing, misaligned or too small */
     ASUCA_ERR_NONFINITE = 4,    /* a budget sum was NaN or infinite */
     ASUCA_ERR_TIMEOUT = 5,      /* a device-wide barrier gave up waiting */
-    ASUCA_ERR_UNSUPPORTED = 6   /* sizes beyond the compiled limits */
+    ASUCA_ERR_UNSUPPORTED = 6,  /* sizes beyond the compiled limits */
+    ASUCA_ERR_BOUNDS = 7        /* a kernel index fell outside its buffer (recorded only by the
+                                   bounds-check build, see asuca_bounds_checked) */
 } asuca_status;
 
 typedef enum {
@@ -216,12 +218,15 @@ typedef enum {
     ASUCA_TUNE_STEP_MODE = 4            /* asuca_step: 0 one launch per stage and column pass; 1 one persistent
                                            dataflow launch per 16 steps (tasks wait on per-tile counters, so the
                                            FP64 column work overlaps the stencil stages); sizes the workspace */,
-    ASUCA_TUNE_FUSED_COLUMN = 5         /* asuca_step with step mode 0 and diffusion on: 1 (default) runs the third
-                                           stage marching downward together with the top-down half of the column
-                                           pass (relaxation, sedimentation, FP64 elimination), then a bottom-up
-                                           back-substitution kernel; 0 runs the stage and the column pass as two
-                                           launches.  Results are bit-identical; 1 adds an [nz][F+1][ny][nx]
-                                           double scratch to the workspace */
+    ASUCA_TUNE_FUSED_COLUMN = 5         /* asuca_step with step mode 0 and diffusion on: 1 (default) carries the
+                                           top-down half of the column pass in the stage kernels, marching
+                                           downward: the second stage computes the FP64 factorisation from the
+                                           density after the step, the third the relaxation, sedimentation and
+                                           elimination sweep (the nested acoustic step, whose mass fluxes change
+                                           per stage, keeps the whole top-down half in the third stage), then a
+                                           bottom-up back-substitution kernel; 0 runs the stages and the column
+                                           pass as separate launches.  Results are bit-identical; 1 adds
+                                           (F + 2) nz ny nx doubles of scratch to the workspace */
 } asuca_tune_key;
 asuca_status asuca_set_tuning(asuca_grid *grid, int key, int value);
 int asuca_get_tuning(const asuca_grid *grid, int key);
@@ -230,6 +235,20 @@ int asuca_get_tuning(const asuca_grid *grid, int key);
  * the device status word (ASUCA_OK when no device error was recorded). */
 asuca_status asuca_get_status(asuca_grid *grid);
 const char *asuca_status_string(asuca_status s);
+
+/* 1 when this library is the bounds-check build (compiled with
+ * ASUCA_BOUNDS_CHECK), else 0.  In that build the step's kernels (the stage
+ * kernels, the branch-recording stage, the column hooks of the stages, the
+ * column passes, also inside the ensemble kernel) test each global-memory
+ * index, and each offset into the stage's shared-memory ring, against its
+ * buffer's extent before the access; an index outside the buffer records
+ * ASUCA_ERR_BOUNDS in the device status word (asuca_get_status) and the
+ * access is redirected to the buffer's first element, so the kernel neither
+ * traps nor touches memory outside the buffer.  The results of a call that
+ * recorded ASUCA_ERR_BOUNDS are meaningless.  Built on request
+ * (paper_1710_08616_gb300.build.build(bounds_check=True)) as libasuca_bc.so;
+ * it is slower and meant for tests on small cases. */
+int asuca_bounds_checked(void);
 
 /* ---- sub-steps, exported for per-kernel parity tests ------------------ */
 

@@ -19,9 +19,14 @@ import os
 
 import numpy as np
 
-from .build import LIB as _LIB_PATH
+from .build import LIB as _DEFAULT_LIB
 
-OK, ERR_ARG, ERR_CUDA, ERR_WORKSPACE, ERR_NONFINITE, ERR_TIMEOUT, ERR_UNSUPPORTED = range(7)
+# ASUCA_LIBRARY selects another build of the library for this process (the
+# bounds-check build, libasuca_bc.so, in its tests); it must exist, as the
+# default must: there is no fallback.
+_LIB_PATH = os.environ.get("ASUCA_LIBRARY") or _DEFAULT_LIB
+
+OK, ERR_ARG, ERR_CUDA, ERR_WORKSPACE, ERR_NONFINITE, ERR_TIMEOUT, ERR_UNSUPPORTED, ERR_BOUNDS = range(8)
 FP64, FP32_MIXED = 0, 1
 LIM_KOREN, LIM_LINEAR, LIM_UPWIND1 = 0, 1, 2
 OP_STEP, OP_ADJOINT, OP_ENSEMBLE = 0, 1, 2
@@ -31,7 +36,7 @@ MAX_NZ = 128
 _STATUS = {OK: "ok", ERR_ARG: "invalid argument", ERR_CUDA: "CUDA runtime error",
            ERR_WORKSPACE: "workspace missing, misaligned or too small",
            ERR_NONFINITE: "non-finite budget", ERR_TIMEOUT: "device barrier timed out",
-           ERR_UNSUPPORTED: "unsupported size"}
+           ERR_UNSUPPORTED: "unsupported size", ERR_BOUNDS: "a kernel index fell outside its buffer"}
 
 
 class AsucaError(RuntimeError):
@@ -75,6 +80,7 @@ SIGNATURES = {
                                   ctypes.c_int, _VP, ctypes.c_size_t, _VP, _VP]),
     "asuca_get_status": (ctypes.c_int, [_VP]),
     "asuca_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "asuca_bounds_checked": (ctypes.c_int, []),
     "asuca_debug_stage": (ctypes.c_int, [_VP, ctypes.POINTER(StateStruct), ctypes.POINTER(StateStruct),
                                          ctypes.POINTER(StateStruct), _VP, ctypes.c_double, _VP]),
     "asuca_debug_column": (ctypes.c_int, [_VP, ctypes.POINTER(StateStruct), ctypes.c_double, _VP,
@@ -154,6 +160,11 @@ def lib():
             fn.argtypes = args
         _lib = L
     return _lib
+
+
+def bounds_checked() -> bool:
+    """Whether the loaded library is the bounds-check build (asuca_bounds_checked)."""
+    return bool(lib().asuca_bounds_checked())
 
 
 def _check(status: int, where: str):

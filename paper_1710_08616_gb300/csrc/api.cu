@@ -225,6 +225,7 @@ ColumnParams<T> column_params(const asuca_grid *g, double dt) {
     p.ny = d.ny;
     p.nz = nz;
     p.plane = g->plane;
+    p.status = g->status_dev;
     p.do_relax = d.tau_theta > 0.0;
     p.do_sed = d.v_sed > 0.0 && d.sed_tracer >= 0 && d.sed_tracer < d.ntracers;
     p.sed = p.do_sed ? 2 + d.sed_tracer : -1;
@@ -532,6 +533,10 @@ asuca_status run_step_dataflow(asuca_grid *g, asuca_state *st, const void *tend,
     p.scratch = (double *)(ws + L.df_scratch);
     p.partials = (double *)(ws + L.df_partials);
     p.status = g->status_dev;
+    // the column tasks' scratch: one slot per thread of the persistent grid
+    // (the column parameters carry it for the bounds-check build's extents)
+    p.col.scratch = p.col_last.scratch = p.scratch;
+    p.col.nslots = p.col_last.nslots = (long long)df_grid_size(g) * 32 * 8;
     const size_t tiles = (size_t)R * TXn;
     for (int c0 = 0; c0 < nsteps; c0 += DF_CHUNK) {
         const int n = (nsteps - c0) < DF_CHUNK ? (nsteps - c0) : DF_CHUNK;
@@ -938,16 +943,25 @@ struct EnsLayout {
 };
 
 template <typename T>
-cudaError_t ens_grid(const asuca_grid *g0, int *grid) {
+cudaError_t ens_grid(const asuca_grid *g0, int nzmax, int *grid) {
     EnsParams<T> dummy;
     std::memset(&dummy, 0, sizeof(dummy));
+    dummy.nzmax = nzmax;
     return launch_ensemble<T>(dummy, g0->F, (int)g0->d.lim, g0->ens_ty, 0, nullptr, grid);
+}
+
+int ens_nzmax(asuca_grid *const *grids, int M) {
+    int nz = 0;
+    for (int m = 0; m < M; m++) nz = grids[m]->d.nz > nz ? grids[m]->d.nz : nz;
+    return nz;
 }
 
 bool ens_layout(asuca_grid *const *grids, int M, EnsLayout *L) {
     const asuca_grid *g0 = grids[0];
     int grid = 0;
-    cudaError_t e = g0->d.prec == ASUCA_FP64 ? ens_grid<double>(g0, &grid) : ens_grid<float>(g0, &grid);
+    const int nzmax = ens_nzmax(grids, M);
+    cudaError_t e = g0->d.prec == ASUCA_FP64 ? ens_grid<double>(g0, nzmax, &grid)
+                                             : ens_grid<float>(g0, nzmax, &grid);
     if (e != cudaSuccess || grid <= 0) return false;
     L->grid = grid;
     L->threads = 32 * g0->ens_ty;
@@ -1038,6 +1052,7 @@ asuca_status ens_enqueue(asuca_grid *const *grids, asuca_state *states, const do
         cp.scratch = (double *)(ws + L.fscratch[m]);
         cp.alpha = (double *)(ws + L.falpha[m]);
         cp.nslots = g->plane;
+        cp.status = g0->status_dev;   // the ensemble reports through the first member's grid
         cp.budgets = 0;
         mb[m].col = cp;
         const int tx = (g->d.nx + TX - 1) / TX, ty = (g->d.ny + TY - 1) / TY;
@@ -1058,6 +1073,7 @@ asuca_status ens_enqueue(asuca_grid *const *grids, asuca_state *states, const do
     ep.members = (const EnsMember<T> *)(ws + L.members);
     ep.nmembers = M;
     ep.nsteps = nsteps;
+    ep.nzmax = ens_nzmax(grids, M);
     ep.total_tiles = tile0;
     ep.total_cols = col0;
     ep.bar_count = (unsigned *)(ws + L.bar);
@@ -1283,6 +1299,14 @@ cudaError_t launch_column_noalloc(asuca_grid *g, asuca_state *st, double dt, dou
 
 extern "C" {
 
+int asuca_bounds_checked(void) {
+#ifdef ASUCA_BOUNDS_CHECK
+    return 1;
+#else
+    return 0;
+#endif
+}
+
 const char *asuca_status_string(asuca_status s) {
     switch (s) {
         case ASUCA_OK: return "ok";
@@ -1292,6 +1316,7 @@ const char *asuca_status_string(asuca_status s) {
         case ASUCA_ERR_NONFINITE: return "non-finite budget";
         case ASUCA_ERR_TIMEOUT: return "device barrier timed out";
         case ASUCA_ERR_UNSUPPORTED: return "unsupported size";
+        case ASUCA_ERR_BOUNDS: return "a kernel index fell outside its buffer";
     }
     return "unknown status";
 }

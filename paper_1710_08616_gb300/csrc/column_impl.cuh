@@ -78,6 +78,27 @@ __device__ __forceinline__ void column_one(const ColumnParams<T> &p, long long c
     constexpr int NQ = NF + 1;                    // m, gamma, e[NT]
     const int nz = p.nz;
     const long long plane = p.plane;
+    // indices checked in the bounds-check build: fields [nz][plane], the
+    // thread's scratch slot (its entries nslots apart, nz NQ of them), the
+    // adjoint's record [nz][F + 2][plane], the precipitation [plane]
+    auto yi = [&](long long i) -> long long {
+        ASUCA_BC(i, (long long)nz * plane, p.status);
+        return i;
+    };
+    auto si = [&](long long i) -> long long {
+#ifdef ASUCA_BOUNDS_CHECK
+        long long t = (long long)(sc - p.scratch) + i;
+        ASUCA_BC(t, (long long)nz * NQ * nslots, p.status);
+        i = t - (long long)(sc - p.scratch);
+#endif
+        return i;
+    };
+    auto ri = [&](long long i) -> long long {
+        ASUCA_BC(i, (long long)nz * (NF + 2) * plane, p.status);
+        return i;
+    };
+    long long pc = col;
+    ASUCA_BC(pc, plane, p.status);
     if (p.do_phys) {
         double g_hi = 0.0, m_up = 0.0;
         double e_up[NT];
@@ -85,20 +106,20 @@ __device__ __forceinline__ void column_one(const ColumnParams<T> &p, long long c
         for (int f = 0; f < NT; f++) e_up[f] = 0.0;
         T P = T(0);
         long long o = (long long)(nz - 1) * plane + col;
-        T rho = p.y[0][o];
-        T rho_dn = (nz > 1) ? p.y[0][o - plane] : T(0);
+        T rho = p.y[0][yi(o)];
+        T rho_dn = (nz > 1) ? p.y[0][yi(o - plane)] : T(0);
         double rd = to_f64(rho);
         T x[NT];
 #pragma unroll
-        for (int f = 0; f < NT; f++) x[f] = p.y[f + 1][o];
+        for (int f = 0; f < NT; f++) x[f] = p.y[f + 1][yi(o)];
         for (int k = nz - 1; k >= 0; k--, o -= plane) {
             // prefetch the level below (and rho two below) while this level computes
             T xn[NT];
             T rho_dn2 = T(0);
             if (k > 0) {
 #pragma unroll
-                for (int f = 0; f < NT; f++) xn[f] = p.y[f + 1][o - plane];
-                if (k > 1) rho_dn2 = p.y[0][o - 2 * plane];
+                for (int f = 0; f < NT; f++) xn[f] = p.y[f + 1][yi(o - plane)];
+                if (k > 1) rho_dn2 = p.y[0][yi(o - 2 * plane)];
             }
             // (i) relaxation of theta
             if (p.do_relax) {
@@ -115,7 +136,7 @@ __device__ __forceinline__ void column_one(const ColumnParams<T> &p, long long c
                         P = p.sed_v * x[f];
                     }
                 }
-                if (k == 0) p.precip_col[col] += p.dt * to_f64(P) * p.dxdy;
+                if (k == 0) p.precip_col[pc] += p.dt * to_f64(P) * p.dxdy;
             }
             if (p.budgets) cs[0].add(rho, p.dz[k], p.dzT[k], p.dzlo[k]);
             const double rd_dn = (k > 0) ? to_f64(rho_dn) : 0.0;
@@ -126,29 +147,28 @@ __device__ __forceinline__ void column_one(const ColumnParams<T> &p, long long c
                 const double t = g_hi * m_up;
                 const double m = rcp_f64(fma(-g_hi, t, b));
                 const double alpha = t * p.dzr_up[k];
-                sc[(long long)(k * NQ + 0) * nslots] = m;
+                sc[si((long long)(k * NQ + 0) * nslots)] = m;
                 const double gam = (k < nz - 1) ? g_hi * m * p.dzr_dn[k + 1] : 0.0;
-                if (k < nz - 1) sc[(long long)((k + 1) * NQ + 1) * nslots] = gam;
+                if (k < nz - 1) sc[si((long long)((k + 1) * NQ + 1) * nslots)] = gam;
                 if (p.rec) {   // the adjoint's record of the factorisation
-                    double *r = p.rec + col;
-                    r[(size_t)(k * (NF + 2) + 0) * plane] = m;
-                    r[(size_t)(k * (NF + 2) + 1) * plane] = alpha;
-                    if (k < nz - 1) r[(size_t)((k + 1) * (NF + 2) + 2) * plane] = gam;
+                    p.rec[ri((long long)(k * (NF + 2) + 0) * plane + col)] = m;
+                    p.rec[ri((long long)(k * (NF + 2) + 1) * plane + col)] = alpha;
+                    if (k < nz - 1) p.rec[ri((long long)((k + 1) * (NF + 2) + 2) * plane + col)] = gam;
                 }
 #pragma unroll
                 for (int f = 0; f < NT; f++) {
                     const double e = fma(alpha, e_up[f], to_f64(x[f]));
-                    sc[(long long)(k * NQ + 2 + f) * nslots] = e;
+                    sc[si((long long)(k * NQ + 2 + f) * nslots)] = e;
                     e_up[f] = e;
                 }
                 g_hi = g_lo;
                 m_up = m;
             } else {
-                if (p.do_relax) p.y[1][o] = x[0];
+                if (p.do_relax) p.y[1][yi(o)] = x[0];
                 if (p.do_sed) {
 #pragma unroll
                     for (int f = 1; f < NT; f++)
-                        if (f + 1 == p.sed) p.y[f + 1][o] = x[f];
+                        if (f + 1 == p.sed) p.y[f + 1][yi(o)] = x[f];
                 }
                 if (p.budgets) {
 #pragma unroll
@@ -169,20 +189,20 @@ __device__ __forceinline__ void column_one(const ColumnParams<T> &p, long long c
 #pragma unroll
             for (int f = 0; f < NT; f++) z[f] = 0.0;
             long long ob = col;
-            double mk = sc[0], gk = 0.0;
+            double mk = sc[si(0)], gk = 0.0;
             double ek[NT];
 #pragma unroll
-            for (int f = 0; f < NT; f++) ek[f] = sc[(long long)(2 + f) * nslots];
-            T rk = p.y[0][ob];
+            for (int f = 0; f < NT; f++) ek[f] = sc[si((long long)(2 + f) * nslots)];
+            T rk = p.y[0][yi(ob)];
             for (int k = 0; k < nz; k++, ob += plane) {
                 double mn = 0.0, gn = 0.0, en[NT];
                 T rn = T(0);
                 if (k + 1 < nz) {   // prefetch level k+1
-                    mn = sc[(long long)((k + 1) * NQ + 0) * nslots];
-                    gn = sc[(long long)((k + 1) * NQ + 1) * nslots];
+                    mn = sc[si((long long)((k + 1) * NQ + 0) * nslots)];
+                    gn = sc[si((long long)((k + 1) * NQ + 1) * nslots)];
 #pragma unroll
-                    for (int f = 0; f < NT; f++) en[f] = sc[(long long)((k + 1) * NQ + 2 + f) * nslots];
-                    rn = p.y[0][ob + plane];
+                    for (int f = 0; f < NT; f++) en[f] = sc[si((long long)((k + 1) * NQ + 2 + f) * nslots)];
+                    rn = p.y[0][yi(ob + plane)];
                 }
                 const double sigma = to_f64(rk) * p.dz[k] * mk;
                 // float path: sigma in float from rho (float), dz and m rounded once
@@ -190,9 +210,9 @@ __device__ __forceinline__ void column_one(const ColumnParams<T> &p, long long c
 #pragma unroll
                 for (int f = 0; f < NT; f++) {
                     z[f] = fma(gk, z[f], ek[f]);
-                    if (p.rec) p.rec[(size_t)(k * (NF + 2) + 3 + f) * plane + col] = z[f];
+                    if (p.rec) p.rec[ri((size_t)(k * (NF + 2) + 3 + f) * plane + col)] = z[f];
                     const T u = scale_out<T>(z[f], sigma, sf);
-                    p.y[f + 1][ob] = u;
+                    p.y[f + 1][yi(ob)] = u;
                     if (p.budgets) cs[f + 1].add(u, p.dz[k], p.dzT[k], p.dzlo[k]);
                 }
                 if (k + 1 < nz) {
@@ -208,7 +228,7 @@ __device__ __forceinline__ void column_one(const ColumnParams<T> &p, long long c
         for (int k = 0; k < nz; k++) {
             const long long o = (long long)k * plane + col;
 #pragma unroll
-            for (int f = 0; f < NF; f++) cs[f].add(p.y[f][o], p.dz[k], p.dzT[k], p.dzlo[k]);
+            for (int f = 0; f < NF; f++) cs[f].add(p.y[f][yi(o)], p.dz[k], p.dzT[k], p.dzlo[k]);
         }
     }
 }
@@ -296,8 +316,28 @@ __device__ __forceinline__ void column_physics_level(const ColumnParams<T> &c, c
                 }
             }
         }
-        if (k == 0) c.precip_col[own] += c.dt * to_f64(P) * c.dxdy;
+        if (k == 0) {
+            unsigned o = own;
+            ASUCA_BC(o, c.plane, c.status);
+            c.precip_col[o] += c.dt * to_f64(P) * c.dxdy;
+        }
     }
+}
+
+// The scratch entries of level k of the column whose entries start at sc
+// (a pointer into c.scratch): the checked build tests that quantities 0 ..
+// hi_q of the level lie inside the fused scratch.
+template <typename T>
+__device__ __forceinline__ double *fscratch_at(const ColumnParams<T> &c, double *sc, int k, size_t ls, int hi_q) {
+#ifdef ASUCA_BOUNDS_CHECK
+    long long ai = (long long)(sc - c.scratch) + (long long)k * (long long)ls;
+    ASUCA_BC(ai, (long long)c.nz * (long long)ls - 32LL * hi_q, c.status);
+    return c.scratch + ai;
+#else
+    (void)c;
+    (void)hi_q;
+    return sc + (size_t)k * ls;
+#endif
 }
 
 // The factorisation of one level (top-down, scaled unknowns): stores m and
@@ -305,7 +345,11 @@ __device__ __forceinline__ void column_physics_level(const ColumnParams<T> &c, c
 // stride), carries g and m to the next level, returns alpha.
 template <typename T>
 __device__ __forceinline__ double factor_level(const ColLevel<T> &L, int k, int nz, T rho, T rho_next, double &g_hi,
-                                               double &m_up, double *a, size_t ls) {
+                                               double &m_up, double *a, size_t ls, const double *bc_base = nullptr,
+                                               long long bc_extent = 0, int *bc_status = nullptr) {
+    (void)bc_base;
+    (void)bc_extent;
+    (void)bc_status;
     const double rd = to_f64(rho);
     const double rd_dn = (k > 0) ? to_f64(rho_next) : 0.0;
     const double g_lo = (k > 0) ? L.kc_lo * (rd_dn + rd) : 0.0;
@@ -314,7 +358,16 @@ __device__ __forceinline__ double factor_level(const ColLevel<T> &L, int k, int 
     const double m = rcp_f64(fma(-g_hi, t, b));
     const double alpha = t * L.dzr_up;
     a[0] = m;
-    if (k < nz - 1) a[ls + 32] = g_hi * m * L.dzr_dn1;
+    if (k < nz - 1) {
+        size_t gi = ls + 32;   // gamma of level k + 1
+#ifdef ASUCA_BOUNDS_CHECK
+        // a + gi inside [base, base + extent)
+        long long ga = (long long)(a - bc_base) + (long long)gi;
+        ASUCA_BC(ga, bc_extent, bc_status);
+        gi = (size_t)(ga - (long long)(a - bc_base));
+#endif
+        a[gi] = g_hi * m * L.dzr_dn1;
+    }
     g_hi = g_lo;
     m_up = m;
     return alpha;
@@ -350,15 +403,18 @@ struct ColDownHook {
         static_assert(NF2 == NF, "field count");
         if (!valid) return;
         const T rho = out[0];
-        rho_out[(size_t)k * pl + own] = rho;
+        size_t ro = (size_t)k * pl + own;
+        ASUCA_BC(ro, (long long)c.nz * (long long)pl, c.status);
+        rho_out[ro] = rho;
         const ColLevel<T> L = tab[k];
         T x[NT];
 #pragma unroll
         for (int f = 0; f < NT; f++) x[f] = out[f + 1];
         column_physics_level<T, NF>(c, L, k, rho, x, P, own);
         // (iii) forward elimination on scaled unknowns
-        double *a = sc + (size_t)k * ls;
-        const double alpha = factor_level<T>(L, k, c.nz, rho, rho_next, g_hi, m_up, a, ls);
+        double *a = fscratch_at(c, sc, k, ls, NQ - 1);
+        const double alpha = factor_level<T>(L, k, c.nz, rho, rho_next, g_hi, m_up, a, ls, c.scratch,
+                                             (long long)c.nz * (long long)ls, c.status);
 #pragma unroll
         for (int f = 0; f < NT; f++) {
             const double e = fma(alpha, e_up[f], to_f64(x[f]));
@@ -390,7 +446,14 @@ struct FactorHook {
     __device__ __forceinline__ void level(int k, const U (&)[NF2], bool valid, U rho_next, U rho_h) {
         if (!valid) return;
         const ColLevel<T> L = tab[k];
-        alpha_out[(size_t)k * pl] = factor_level<T>(L, k, c.nz, rho_h, rho_next, g_hi, m_up, sc + (size_t)k * ls, ls);
+        size_t ao = (size_t)k * pl;
+#ifdef ASUCA_BOUNDS_CHECK
+        long long aa = (long long)(alpha_out - c.alpha) + (long long)ao;
+        ASUCA_BC(aa, (long long)c.nz * (long long)pl, c.status);
+        ao = (size_t)(aa - (long long)(alpha_out - c.alpha));
+#endif
+        alpha_out[ao] = factor_level<T>(L, k, c.nz, rho_h, rho_next, g_hi, m_up, fscratch_at(c, sc, k, ls, 1), ls,
+                                        c.scratch, (long long)c.nz * (long long)ls, c.status);
     }
     __device__ __forceinline__ void done(bool) {}
 };
@@ -416,9 +479,20 @@ struct SweepHook {
     __device__ __forceinline__ SweepHook(const ColumnParams<T> &cp, const ColLevel<T> *tab_, T *rho, unsigned own_)
         : c(cp), tab(tab_), rho_out(rho), sc(cp.scratch + fscratch_col(own_, NQ)), alpha_in(cp.alpha + own_),
           pl((size_t)cp.plane), ls((size_t)fscratch_level(cp.plane, NQ)), own(own_), P(T(0)) {
-        alpha_k = alpha_in[(size_t)(cp.nz - 1) * pl];
+        alpha_k = alpha_in[alpha_index(cp.nz - 1)];
 #pragma unroll
         for (int f = 0; f < NT; f++) e_up[f] = 0.0;
+    }
+
+    // offset of level k's alpha from alpha_in (checked against the [nz][plane] array)
+    __device__ __forceinline__ long long alpha_index(int k) const {
+        long long a = (long long)k * (long long)pl;
+#ifdef ASUCA_BOUNDS_CHECK
+        long long t = a + own;
+        ASUCA_BC(t, (long long)c.nz * (long long)pl, c.status);
+        a = t - own;
+#endif
+        return a;
     }
 
     template <typename U, int NF2>
@@ -426,15 +500,17 @@ struct SweepHook {
         static_assert(NF2 == NF, "field count");
         if (!valid) return;
         const double alpha = alpha_k;
-        if (k > 0) alpha_k = alpha_in[(size_t)(k - 1) * pl];
+        if (k > 0) alpha_k = alpha_in[alpha_index(k - 1)];
         const T rho = out[0];
-        rho_out[(size_t)k * pl + own] = rho;
+        size_t ro = (size_t)k * pl + own;
+        ASUCA_BC(ro, (long long)c.nz * (long long)pl, c.status);
+        rho_out[ro] = rho;
         const ColLevel<T> L = tab[k];
         T x[NT];
 #pragma unroll
         for (int f = 0; f < NT; f++) x[f] = out[f + 1];
         column_physics_level<T, NF>(c, L, k, rho, x, P, own);
-        double *a = sc + (size_t)k * ls;
+        double *a = fscratch_at(c, sc, k, ls, NQ - 1);
 #pragma unroll
         for (int f = 0; f < NT; f++) {
             const double e = fma(alpha, e_up[f], to_f64(x[f]));
@@ -459,26 +535,31 @@ __device__ __forceinline__ void column_up_one(const ColumnParams<T> &p, long lon
     const size_t pl = (size_t)p.plane;
     const size_t ls = (size_t)fscratch_level(p.plane, NQ);
     const int nz = p.nz;
-    const double *sc = p.scratch + fscratch_col(col, NQ);
+    double *sc = p.scratch + fscratch_col(col, NQ);
     double z[NT];
 #pragma unroll
     for (int f = 0; f < NT; f++) z[f] = 0.0;
     size_t ob = (size_t)col;
-    double mk = sc[0], gk = 0.0;
+    const double *a0 = fscratch_at(p, sc, 0, ls, NQ - 1);
+    double mk = a0[0], gk = 0.0;
     double ek[NT];
 #pragma unroll
-    for (int f = 0; f < NT; f++) ek[f] = sc[32 * (2 + f)];
-    T rk = p.y[0][ob];
+    for (int f = 0; f < NT; f++) ek[f] = a0[32 * (2 + f)];
+    size_t o0 = ob;
+    ASUCA_BC(o0, (long long)nz * (long long)pl, p.status);
+    T rk = p.y[0][o0];
     for (int k = 0; k < nz; k++, ob += pl) {
         double mn = 0.0, gn = 0.0, en[NT];
         T rn = T(0);
         if (k + 1 < nz) {   // prefetch level k+1
-            const double *a = sc + (size_t)(k + 1) * ls;
+            const double *a = fscratch_at(p, sc, k + 1, ls, NQ - 1);
             mn = a[0];
             gn = a[32];
 #pragma unroll
             for (int f = 0; f < NT; f++) en[f] = a[32 * (2 + f)];
-            rn = p.y[0][ob + pl];
+            size_t on = ob + pl;
+            ASUCA_BC(on, (long long)nz * (long long)pl, p.status);
+            rn = p.y[0][on];
         }
         if (p.budgets) cs[0].add(rk, p.dz[k], p.dzT[k], p.dzlo[k]);
 #pragma unroll
@@ -504,9 +585,11 @@ __device__ __forceinline__ void column_up_one(const ColumnParams<T> &p, long lon
 #pragma unroll
             for (int f = 0; f < NT; f++) u[f] = sigma * z[f];
         }
+        size_t os = ob;
+        ASUCA_BC(os, (long long)nz * (long long)pl, p.status);
 #pragma unroll
         for (int f = 0; f < NT; f++) {
-            p.y[f + 1][ob] = u[f];
+            p.y[f + 1][os] = u[f];
             if (p.budgets) cs[f + 1].add(u[f], p.dz[k], p.dzT[k], p.dzlo[k]);
         }
         if (k + 1 < nz) {

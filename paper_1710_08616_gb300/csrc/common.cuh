@@ -115,6 +115,7 @@ struct ColumnParams {
     double *scratch;        // [nz][F + 1][nslots]
     long long nslots;
     double *alpha;          // the fused column pass split over stages 2 and 3: [nz][plane] alpha of each level
+    int *status;            // device status word (the bounds-check build records out-of-range indices)
     double *rec;            // if set: [nz][F + 2][plane] record of the diffusion solve for the adjoint:
                             // m, alpha, gamma of each level and the scaled solution z of each field
     T dzT[MAXNZ];           // dz_k (rounded to T)
@@ -129,6 +130,25 @@ struct ColumnParams {
     T rdzT[MAXNZ];          // 1 / dz_k (rounded to T)
     T kcT[MAXNZ];           // kc rounded to T
 };
+
+// ------------------------------------------------------------------ bounds-check build
+
+// With ASUCA_BOUNDS_CHECK every instrumented index is tested against its
+// buffer's extent before the access: an index outside [0, n) records
+// ASUCA_ERR_BOUNDS in the status word and is replaced by 0, so the access
+// stays inside the buffer and the kernel carries on (no trap).  Without it
+// ASUCA_BC expands to nothing.
+#ifdef ASUCA_BOUNDS_CHECK
+template <typename I>
+__device__ __forceinline__ I bc_index(I idx, long long n, int *status) {
+    if ((long long)idx >= 0 && (long long)idx < n) return idx;
+    if (status) atomicCAS(status, 0, (int)ASUCA_ERR_BOUNDS);
+    return I(0);
+}
+#define ASUCA_BC(idx, n, status) ((idx) = bc_index((idx), (long long)(n), (status)))
+#else
+#define ASUCA_BC(idx, n, status) ((void)0)
+#endif
 
 // ------------------------------------------------------------------ helpers
 

@@ -62,6 +62,28 @@ __device__ __forceinline__ int member_of(const EnsMember<T> *m, int nm, long lon
     return lo;
 }
 
+// Shared memory of the ensemble kernel: the stage tile's, copies of the
+// current tile's stage parameters and of the scalar head of its column
+// parameters (everything before the per-level arrays), which the tile reads
+// many times per level, then the per-level records of the column pass (nz of
+// them, the largest level count of the members).
+template <typename T, int NF, int TYV>
+struct EnsSmem {
+    static constexpr size_t SP = FusedSmem<T, NF, TYV>::TILE;
+    static constexpr size_t CP = SP + (sizeof(StageParams<T>) + 127) / 128 * 128;
+    static constexpr size_t HEAD = (offsetof(ColumnParams<T>, dzT) + 7) / 8 * 8;
+    static constexpr size_t TAB = (CP + HEAD + 127) / 128 * 128;
+    static size_t bytes(int nz) { return TAB + (size_t)nz * sizeof(ColLevel<T>); }
+    static constexpr size_t MAX_BYTES = TAB + (size_t)MAXNZ * sizeof(ColLevel<T>);
+};
+
+// 8-byte copy of bytes (a multiple of 8) by the CTA's threads
+__device__ __forceinline__ void cta_copy8(void *dst, const void *src, size_t bytes, int tid, int nthr) {
+    long long *d = reinterpret_cast<long long *>(dst);
+    const long long *q = reinterpret_cast<const long long *>(src);
+    for (size_t i = tid; i < bytes / 8; i += nthr) d[i] = q[i];
+}
+
 // Per step: stage 1 (upward march); stage 2 marching downward with the FP64
 // factorisation of every column (FactorHook); stage 3 marching downward with
 // the relaxation, sedimentation and elimination sweep (SweepHook); then the
@@ -72,7 +94,11 @@ __global__ void __launch_bounds__(32 * TYV, StageShape<T, NF, TYV>::MIN_BLOCKS)
     ensemble_kernel(const __grid_constant__ EnsParams<T> e) {
     using S = StageShape<T, NF, TYV>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    ColLevel<T> *tab = reinterpret_cast<ColLevel<T> *>(smem_raw + FusedSmem<T, NF, TYV>::TILE);
+    using M = EnsSmem<T, NF, TYV>;
+    ColLevel<T> *tab = reinterpret_cast<ColLevel<T> *>(smem_raw + M::TAB);
+    StageParams<T> &sp = *reinterpret_cast<StageParams<T> *>(smem_raw + M::SP);
+    ColumnParams<T> &cp = *reinterpret_cast<ColumnParams<T> *>(smem_raw + M::CP);   // scalar head only
+    static_assert(M::SP % 64 == 0 && sizeof(StageParams<T>) % 8 == 0, "parameter copies");
     const unsigned target = gridDim.x + (unsigned)e.bar_extra;
     const int tid = threadIdx.y * blockDim.x + threadIdx.x, nthr = blockDim.x * blockDim.y;
     const long long nth = (long long)gridDim.x * nthr;
@@ -85,23 +111,29 @@ __global__ void __launch_bounds__(32 * TYV, StageShape<T, NF, TYV>::MIN_BLOCKS)
                 const EnsMember<T> &mb = e.members[m];
                 const long long lt = t - mb.tile0;
                 const int i0 = (int)(lt % mb.tiles_x) * S::TX, j0 = (int)(lt / mb.tiles_x) * S::TY;
-                const StageParams<T> &sp = mb.stage[stg];
-                if (stg == 0) {
-                    bad = stage_tile<T, NF, LIM, false, TYV>(sp, &sp.tmap, i0, j0, smem_raw);
-                } else {
-                    __syncthreads();   // the previous tile is done with the records
+                // the tile's parameters into shared memory (the tensor map is
+                // read from the member's copy in global memory)
+                __syncthreads();   // the previous tile is done with the copies and the records
+                cta_copy8(&sp, &mb.stage[stg], sizeof(StageParams<T>), tid, nthr);
+                if (stg > 0) {
+                    cta_copy8(&cp, &mb.col, M::HEAD, tid, nthr);
                     fill_col_levels(mb.col, tab, tid, nthr);
-                    __syncthreads();
+                }
+                __syncthreads();
+                const CUtensorMap *tmap = &mb.stage[stg].tmap;
+                if (stg == 0) {
+                    bad = stage_tile<T, NF, LIM, false, TYV>(sp, tmap, i0, j0, smem_raw);
+                } else {
                     const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
                     const unsigned own = (i < sp.nx && j < sp.ny) ? (unsigned)(j * sp.nx + i) : 0u;
                     if (stg == 1) {
-                        FactorHook<T, NF> h(mb.col, tab, own);
+                        FactorHook<T, NF> h(cp, tab, own);
                         bad = stage_tile_h<T, NF, LIM, false, TYV, true, FactorHook<T, NF>, LAYOUT_PAIR>(
-                            sp, &sp.tmap, i0, j0, smem_raw, h);
+                            sp, tmap, i0, j0, smem_raw, h);
                     } else {
-                        SweepHook<T, NF> h(mb.col, tab, sp.yout[0], own);
+                        SweepHook<T, NF> h(cp, tab, sp.yout[0], own);
                         bad = stage_tile_h<T, NF, LIM, false, TYV, true, SweepHook<T, NF>, LAYOUT_PAIR>(
-                            sp, &sp.tmap, i0, j0, smem_raw, h);
+                            sp, tmap, i0, j0, smem_raw, h);
                     }
                 }
                 if (bad) break;
@@ -122,8 +154,10 @@ template <typename T, int NF, int LIM, int TYV>
 static cudaError_t ens_launch_lim(const EnsParams<T> &e, int grid, cudaStream_t s, int *grid_out) {
     using S = StageShape<T, NF, TYV>;
     static std::atomic<unsigned long long> attr_done{0};   // devices whose attribute is set
-    constexpr size_t bytes = FusedSmem<T, NF, TYV>::MAX_BYTES;   // the tile's and the per-level records
-    const cudaError_t r = set_smem_once(ensemble_kernel<T, NF, LIM, TYV>, (int)bytes, attr_done);
+    // tile, parameter copies, per-level records (the attribute allows the largest level count)
+    const size_t bytes = EnsSmem<T, NF, TYV>::bytes(e.nzmax);
+    const cudaError_t r =
+        set_smem_once(ensemble_kernel<T, NF, LIM, TYV>, (int)EnsSmem<T, NF, TYV>::MAX_BYTES, attr_done);
     if (r != cudaSuccess) return r;
     if (grid_out) {   // size query: resident CTAs per SM times SMs
         int per_sm = 0, dev = 0, nsm = 0;

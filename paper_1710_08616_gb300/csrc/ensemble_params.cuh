@@ -19,6 +19,7 @@ template <typename T>
 struct EnsParams {
     const EnsMember<T> *members;
     int nmembers, nsteps;
+    int nzmax;                 // the largest level count of the members (sizes the per-level records)
     long long total_tiles, total_cols;
     unsigned *bar_count, *bar_gen;
     int bar_extra;             // 0; a test sets 1 so that the barrier can never complete

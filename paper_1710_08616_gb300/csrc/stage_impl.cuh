@@ -274,10 +274,15 @@ __device__ __forceinline__ bool stage_tile_h(const StageParams<T> &p, const CUte
 #pragma unroll
                 for (int q = 0; q < MAXC; q++) {
                     if (q < nc) {
+                        unsigned g0 = lb + goff[q], g1 = lb + goff1[q];
+                        int s0 = soff[q];
+                        ASUCA_BC(g0, (long long)nz * plane, p.status);
+                        ASUCA_BC(g1, (long long)nz * plane, p.status);
+                        ASUCA_BC(s0, S::SLOT_ELEMS - (NF - 1) * FE - 1, p.status);
 #pragma unroll
                         for (int f = 0; f < NF; f++) {
-                            cp_async<sizeof(T)>(sl + f * FE + soff[q], p.yin[f] + lb + goff[q]);
-                            cp_async<sizeof(T)>(sl + f * FE + soff[q] + 1, p.yin[f] + lb + goff1[q]);
+                            cp_async<sizeof(T)>(sl + f * FE + s0, p.yin[f] + g0);
+                            cp_async<sizeof(T)>(sl + f * FE + s0 + 1, p.yin[f] + g1);
                         }
                     }
                 }
@@ -322,8 +327,12 @@ __device__ __forceinline__ bool stage_tile_h(const StageParams<T> &p, const CUte
     // 2q+1 and 2q+2, the second 0 past the last field)
     auto ld2 = [&](const T *sl, int q, int off) -> T2 {
         if constexpr (PAIRL) {
-            return *reinterpret_cast<const T2 *>(sl + q * QS + off);
+            int e = q * QS + off;
+            ASUCA_BC(e, S::SLOT_ELEMS - 1, p.status);
+            return *reinterpret_cast<const T2 *>(sl + e);
         } else {
+            // fields 2q+1 and (when it exists) 2q+2 of the slot at off
+            ASUCA_BC(off, S::SLOT_ELEMS - (2 * q + 2 <= NT ? 2 * q + 2 : 2 * q + 1) * FE, p.status);
             T2 v;
             v.x = sl[(2 * q + 1) * FE + off];
             v.y = (2 * q + 2 <= NT) ? sl[(2 * q + 2) * FE + off] : T(0);
@@ -369,15 +378,25 @@ __device__ __forceinline__ bool stage_tile_h(const StageParams<T> &p, const CUte
     T nmup, nmum, nmvp, nmvm, nmwp, nmeb, nmel, nrho;
     auto prefetch = [&](int k) {
         const unsigned kb = (unsigned)k * plane, kbu = (unsigned)k * plane_u, kbv = (unsigned)k * plane_v;
-        nmup = p.mu[kbu + u_own];
-        nmum = p.mu[kbu + u_left];
-        nmvp = p.mv[kbv + v_own];
-        nmvm = p.mv[kbv + v_down];
-        if (DOWN) nmwp = (k > 0) ? p.mw[kb + own] : T(0);
-        else nmwp = (k < nz - 1) ? p.mw[kb + plane + own] : T(0);
-        nmeb = p.mv[kbv + edge_b];
-        nmel = p.mu[kbu + edge_l];
-        if (Hook::active) nrho = p.ybase[0][kb + own];
+        unsigned a_up = kbu + u_own, a_ul = kbu + u_left, a_vp = kbv + v_own, a_vd = kbv + v_down,
+                 a_w = DOWN ? kb + own : kb + plane + own, a_eb = kbv + edge_b, a_el = kbu + edge_l, a_r = kb + own;
+        ASUCA_BC(a_up, (long long)nz * plane_u, p.status);
+        ASUCA_BC(a_ul, (long long)nz * plane_u, p.status);
+        ASUCA_BC(a_el, (long long)nz * plane_u, p.status);
+        ASUCA_BC(a_vp, (long long)nz * plane_v, p.status);
+        ASUCA_BC(a_vd, (long long)nz * plane_v, p.status);
+        ASUCA_BC(a_eb, (long long)nz * plane_v, p.status);
+        ASUCA_BC(a_w, (long long)(nz + 1) * plane, p.status);
+        ASUCA_BC(a_r, (long long)nz * plane, p.status);
+        nmup = p.mu[a_up];
+        nmum = p.mu[a_ul];
+        nmvp = p.mv[a_vp];
+        nmvm = p.mv[a_vd];
+        if (DOWN) nmwp = (k > 0) ? p.mw[a_w] : T(0);
+        else nmwp = (k < nz - 1) ? p.mw[a_w] : T(0);
+        nmeb = p.mv[a_eb];
+        nmel = p.mu[a_el];
+        if (Hook::active) nrho = p.ybase[0][a_r];
     };
     auto advance = [&]() {
         mup = nmup; mum = nmum; mvp = nmvp; mvm = nmvm; mwp = nmwp; meb = nmeb; mel = nmel;
@@ -424,7 +443,8 @@ __device__ __forceinline__ bool stage_tile_h(const StageParams<T> &p, const CUte
         T yb0;
         T2 yb[NPF];
         {
-            const unsigned kb = (unsigned)k * plane + own;
+            unsigned kb = (unsigned)k * plane + own;
+            ASUCA_BC(kb, (long long)nz * plane, p.status);
             yb0 = p.ybase[0][kb];
 #pragma unroll
             for (int q = 0; q < NPF; q++) {
@@ -485,11 +505,15 @@ __device__ __forceinline__ bool stage_tile_h(const StageParams<T> &p, const CUte
                 zp[q].y = top ? T(0) : mwp * vz.y;
                 if (valid) {
                     const long long fs = (long long)nz * plane, ds = (long long)NT * fs;
-                    uint8_t *br = p.branch + (long long)(2 * q) * fs + (long long)k * plane + own;
+                    // the record of field 2q+1 (and 2q+2) of this cell, in [NT][nz][ny][nx]
+                    // (branches) and [3][NT][nz][ny][nx] (face values)
+                    long long bi = (long long)(2 * q) * fs + (long long)k * plane + own;
+                    ASUCA_BC(bi, (2 * q + 2 <= NT ? NT - 1 : NT) * fs, p.status);
+                    uint8_t *br = p.branch + bi;
                     br[0] = (uint8_t)(bx.x | (by.x << 2) | (bz.x << 4));
                     if (2 * q + 2 <= NT) br[fs] = (uint8_t)(bx.y | (by.y << 2) | (bz.y << 4));
                     if (p.facev) {
-                        T *fv = p.facev + (long long)(2 * q) * fs + (long long)k * plane + own;
+                        T *fv = p.facev + bi;
                         fv[0] = vx.x;
                         fv[ds] = vy.x;
                         fv[2 * ds] = vz.x;
@@ -565,7 +589,9 @@ __device__ __forceinline__ bool stage_tile_h(const StageParams<T> &p, const CUte
         }
         if (has_tend) {
             const long long fs = (long long)nz * plane;
-            const T *tk = p.tend + (unsigned)k * plane + own;
+            unsigned tb = (unsigned)k * plane + own;   // [F-1][nz][ny][nx]: fields at tb + f fs
+            ASUCA_BC(tb, fs, p.status);
+            const T *tk = p.tend + tb;
 #pragma unroll
             for (int q = 0; q < NPF; q++) {
                 out2[q].x = fma(cdt, tk[(long long)(2 * q) * fs], out2[q].x);
@@ -601,7 +627,12 @@ __device__ __forceinline__ bool stage_tile_h(const StageParams<T> &p, const CUte
                 // the next stage reads phi = (rho phi) / rho, in pairs; the
                 // density goes with the last pair (or a pair of its own)
                 const T r = recip(out0);
-                T *ob = p.yout[1] + (long long)k * p.plev + (long long)(j + 2) * p.prow + 2 * (i + 4);
+                constexpr int NW = (NT & 1) ? NPF : NPF + 1;   // pairs written
+                // the cell's first element; the pairs at + q q2 (+1 for the second value),
+                // the periodic ghost copies at + gx, + gy (buffer: nz plev elements)
+                long long oo = (long long)k * p.plev + (long long)(j + 2) * p.prow + 2 * (i + 4);
+                ASUCA_BC(oo, (long long)nz * p.plev - (NW - 1) * q2 - 1, p.status);
+                T *ob = p.yout[1] + oo;
                 T2 v[NPF + 1];
 #pragma unroll
                 for (int q = 0; q < NPF; q++) {
@@ -612,7 +643,6 @@ __device__ __forceinline__ bool stage_tile_h(const StageParams<T> &p, const CUte
                         v[q].y = out2[q].y * r;
                     }
                 }
-                constexpr int NW = (NT & 1) ? NPF : NPF + 1;   // pairs written
                 if (NT & 1) v[NPF - 1].y = out0;
                 else {
                     v[NPF].x = out0;
@@ -621,8 +651,17 @@ __device__ __forceinline__ bool stage_tile_h(const StageParams<T> &p, const CUte
 #pragma unroll
                 for (int q = 0; q < NW; q++) *reinterpret_cast<T2 *>(ob + q * q2) = v[q];
                 if (ghost_x || ghost_y) {
-                    const long long gx = (i < 2) ? 2LL * nx : ((i >= nx - 2) ? -2LL * nx : 0);
-                    const long long gy = (j < 2) ? (long long)ny * p.prow : ((j >= ny - 2) ? -(long long)ny * p.prow : 0);
+                    long long gx = (i < 2) ? 2LL * nx : ((i >= nx - 2) ? -2LL * nx : 0);
+                    long long gy = (j < 2) ? (long long)ny * p.prow : ((j >= ny - 2) ? -(long long)ny * p.prow : 0);
+#ifdef ASUCA_BOUNDS_CHECK
+                    {   // the ghost copies' first elements inside the buffer
+                        long long ox = oo + gx, oy = oo + gy;
+                        ASUCA_BC(ox, (long long)nz * p.plev - (NW - 1) * q2 - 1, p.status);
+                        ASUCA_BC(oy, (long long)nz * p.plev - (NW - 1) * q2 - 1, p.status);
+                        gx = ox - oo;
+                        gy = oy - oo;
+                    }
+#endif
 #pragma unroll
                     for (int q = 0; q < NW; q++) {
                         if (gx) *reinterpret_cast<T2 *>(ob + q * q2 + gx) = v[q];
@@ -630,7 +669,8 @@ __device__ __forceinline__ bool stage_tile_h(const StageParams<T> &p, const CUte
                     }
                 }
             } else {
-                const unsigned o = (unsigned)k * plane + own;
+                unsigned o = (unsigned)k * plane + own;
+                ASUCA_BC(o, (long long)nz * plane, p.status);
                 p.yout[0][o] = out0;
 #pragma unroll
                 for (int q = 0; q < NPF; q++) {
