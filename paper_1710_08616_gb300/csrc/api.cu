@@ -56,6 +56,11 @@ struct asuca_grid {
     cudaEvent_t *prof_ev;
     int prof_cap, prof_used;
     int *prof_kind;               // kind of the launch bracketed by events 2q, 2q+1
+    // the adjoint's second stream (the recomputation of the next segment runs on it
+    // while the caller's stream reverses the current one) and its events: fork, join,
+    // segment recomputed (two buffer sets), segment reversed (two buffer sets)
+    cudaStream_t aux_stream;
+    cudaEvent_t aux_ev[6];
 };
 
 namespace {
@@ -593,6 +598,8 @@ asuca_status run_step_dataflow(asuca_grid *g, asuca_state *st, const void *tend,
 struct AdjLayout {
     size_t step, W, ckpt, segYn, segY1, segY2, segY3, branch, facev, rec, lam, l2, l1, acc, scratch, total;
     size_t nrec_step, nfacev_stage;
+    size_t setbytes;   // one set of segment buffers (segYn .. rec); set b starts b * setbytes after segYn
+    int nsets;         // 2 when there are several segments (recompute and reverse overlap), else 1
     int ncp;
     size_t ustate, pstate, nbranch_step;
     long long slots;
@@ -627,6 +634,7 @@ AdjLayout adj_layout(const asuca_grid *g, int nsteps, int K) {
     off = align_up(off + L.ustate);
     L.ckpt = off;
     off = align_up(off + (size_t)L.ncp * align_up(L.ustate));
+    L.nsets = L.ncp >= 2 ? 2 : 1;
     L.segYn = off;
     off = align_up(off + (size_t)(K + 1) * align_up(L.ustate));
     L.segY1 = off;
@@ -645,6 +653,8 @@ AdjLayout adj_layout(const asuca_grid *g, int nsteps, int K) {
     L.nrec_step = (size_t)g->d.nz * (g->F + 2) * (size_t)g->plane * sizeof(double);
     L.rec = off;
     off = align_up(off + (g->d.k0 > 0.0 ? (size_t)K * align_up(L.nrec_step) : 0));
+    L.setbytes = off - L.segYn;
+    off = L.segYn + (size_t)L.nsets * L.setbytes;
     L.lam = off;
     off = align_up(off + L.ustate);
     L.l2 = off;
@@ -728,30 +738,48 @@ asuca_status run_adjoint(asuca_grid *g, const asuca_state *init, const void *ten
     char *sws = ws + L.step;
     // the recomputation records branches with the grid's tuned tile height (4 or 8 rows)
     const int rty = rec_tile_rows(g);
-    std::vector<CUtensorMap> maps(2 * (size_t)K);
-    for (int q = 0; q < K; q++) {
-        if (encode_stage_map<T>(&maps[2 * q], ws + L.segY1 + (size_t)q * align_up(L.pstate), F, g->d.nx, g->d.ny,
-                                g->d.nz, rty) != cudaSuccess ||
-            encode_stage_map<T>(&maps[2 * q + 1], ws + L.segY2 + (size_t)q * align_up(L.pstate), F, g->d.nx,
-                                g->d.ny, g->d.nz, rty) != cudaSuccess)
-            return ASUCA_ERR_CUDA;
-    }
+    // With several segments the buffers come in two sets: the recomputation of
+    // segment c - 1 runs on the grid's auxiliary stream into one set while the
+    // caller's stream reverses segment c from the other.  A set is recomputed
+    // only after the reversal that last read it (segment c + 2) has finished.
+    std::vector<CUtensorMap> maps(2 * (size_t)K * L.nsets);
+    for (int b = 0; b < L.nsets; b++)
+        for (int q = 0; q < K; q++) {
+            char *y1 = ws + L.segY1 + (size_t)b * L.setbytes + (size_t)q * align_up(L.pstate);
+            char *y2 = ws + L.segY2 + (size_t)b * L.setbytes + (size_t)q * align_up(L.pstate);
+            if (encode_stage_map<T>(&maps[2 * ((size_t)b * K + q)], y1, F, g->d.nx, g->d.ny, g->d.nz, rty) !=
+                    cudaSuccess ||
+                encode_stage_map<T>(&maps[2 * ((size_t)b * K + q) + 1], y2, F, g->d.nx, g->d.ny, g->d.nz, rty) !=
+                    cudaSuccess)
+                return ASUCA_ERR_CUDA;
+        }
+    cudaStream_t s2 = g->aux_stream;
+    cudaEvent_t ev_fork = g->aux_ev[0], ev_join = g->aux_ev[1];
+    cudaEvent_t ev_rec[2] = {g->aux_ev[2], g->aux_ev[3]}, ev_rev[2] = {g->aux_ev[4], g->aux_ev[5]};
+    ck(cudaEventRecord(ev_fork, s));
+    ck(cudaStreamWaitEvent(s2, ev_fork, 0));
+    if (e != cudaSuccess) return ASUCA_ERR_CUDA;
     for (int c = L.ncp - 1; c >= 0; c--) {
         const int start = c * K, len = (nsteps - start) < K ? (nsteps - start) : K;
-        auto segYn = [&](int q) { return ws + L.segYn + (size_t)q * align_up(L.ustate); };
-        auto segY1 = [&](int q) { return ws + L.segY1 + (size_t)q * align_up(L.pstate); };
-        auto segY2 = [&](int q) { return ws + L.segY2 + (size_t)q * align_up(L.pstate); };
-        auto segY3 = [&](int q) { return ws + L.segY3 + (size_t)q * align_up(L.ustate); };
-        auto rec = [&](int q) { return (double *)(ws + L.rec + (size_t)q * align_up(L.nrec_step)); };
-        auto fvs = [&](int q, int stg) { return (T *)(ws + L.facev + ((size_t)q * 3 + stg) * align_up(L.nfacev_stage)); };
+        const int b = L.nsets == 2 ? (c & 1) : 0;
+        const size_t so = (size_t)b * L.setbytes;
+        auto segYn = [&](int q) { return ws + L.segYn + so + (size_t)q * align_up(L.ustate); };
+        auto segY1 = [&](int q) { return ws + L.segY1 + so + (size_t)q * align_up(L.pstate); };
+        auto segY2 = [&](int q) { return ws + L.segY2 + so + (size_t)q * align_up(L.pstate); };
+        auto segY3 = [&](int q) { return ws + L.segY3 + so + (size_t)q * align_up(L.ustate); };
+        auto rec = [&](int q) { return (double *)(ws + L.rec + so + (size_t)q * align_up(L.nrec_step)); };
+        auto fvs = [&](int q, int stg) {
+            return (T *)(ws + L.facev + so + ((size_t)q * 3 + stg) * align_up(L.nfacev_stage));
+        };
         auto brs = [&](int q, int stg) {
-            return (uint8_t *)(ws + L.branch + (size_t)q * align_up(L.nbranch_step)) +
+            return (uint8_t *)(ws + L.branch + so + (size_t)q * align_up(L.nbranch_step)) +
                    (size_t)stg * (F - 1) * g->cells;
         };
+        if (c + L.nsets < L.ncp) ck(cudaStreamWaitEvent(s2, ev_rev[b], 0));
         ck(cudaMemcpyAsync(segYn(0), ckbase + (size_t)c * align_up(L.ustate), L.ustate,
-                           cudaMemcpyDeviceToDevice, s));
+                           cudaMemcpyDeviceToDevice, s2));
         if (e != cudaSuccess) return ASUCA_ERR_CUDA;
-        // ---- recompute the segment, recording stage states and limiter branches
+        // ---- recompute the segment (auxiliary stream), recording stage states and limiter branches
         Range seg_range("adjoint segment");
         for (int q = 0; q < len; q++) {
             Range rec_range("adjoint recompute step");
@@ -765,7 +793,7 @@ asuca_status run_adjoint(asuca_grid *g, const asuca_state *init, const void *ten
             for (int f = 0; f < MAXF; f++) sp.ybase[f] = yn[f];
             for (int stg = 0; stg < 3; stg++) {
                 sp.tma_in = stg > 0;
-                if (stg > 0) sp.tmap = maps[2 * q + (stg - 1)];
+                if (stg > 0) sp.tmap = maps[2 * ((size_t)b * K + q) + (stg - 1)];
                 sp.out_padded = stg < 2;
                 T **out = stg == 0 ? y1 : (stg == 1 ? y2 : y3);
                 for (int f = 0; f < MAXF; f++) {
@@ -775,10 +803,10 @@ asuca_status run_adjoint(asuca_grid *g, const asuca_state *init, const void *ten
                 sp.cdt = cdt[stg];
                 sp.branch = brs(q, stg);
                 sp.facev = fvs(q, stg);
-                if (timed(g, ASUCA_KERNEL_STAGE, s, [&] { return launch_stage<T>(sp, F, s); }) != cudaSuccess)
+                if (timed(g, ASUCA_KERNEL_STAGE, s2, [&] { return launch_stage<T>(sp, F, s2); }) != cudaSuccess)
                     return ASUCA_ERR_CUDA;
             }
-            ck(cudaMemcpyAsync(segYn(q + 1), segY3(q), L.ustate, cudaMemcpyDeviceToDevice, s));
+            ck(cudaMemcpyAsync(segYn(q + 1), segY3(q), L.ustate, cudaMemcpyDeviceToDevice, s2));
             ColumnParams<T> cp = column_params<T>(g, dt);
             block_fields<T>(g, segYn(q + 1), cp.y);
             cp.precip_col = (double *)(sws + SL.precip);
@@ -787,10 +815,13 @@ asuca_status run_adjoint(asuca_grid *g, const asuca_state *init, const void *ten
             cp.budgets = 0;
             cp.rec = cp.do_diff ? rec(q) : nullptr;
             if (e != cudaSuccess ||
-                timed(g, ASUCA_KERNEL_COLUMN, s, [&] { return launch_column<T>(cp, F, g->col_grid, COL_TPB, s); }) !=
-                    cudaSuccess)
+                timed(g, ASUCA_KERNEL_COLUMN, s2,
+                      [&] { return launch_column<T>(cp, F, g->col_grid, COL_TPB, s2); }) != cudaSuccess)
                 return ASUCA_ERR_CUDA;
         }
+        ck(cudaEventRecord(ev_rec[b], s2));
+        ck(cudaStreamWaitEvent(s, ev_rec[b], 0));
+        if (e != cudaSuccess) return ASUCA_ERR_CUDA;
         // ---- reverse through the segment
         for (int q = len - 1; q >= 0; q--) {
             Range rev_range("adjoint reverse step");
@@ -852,7 +883,11 @@ asuca_status run_adjoint(asuca_grid *g, const asuca_state *init, const void *ten
                     return ASUCA_ERR_CUDA;
             }
         }
+        ck(cudaEventRecord(ev_rev[b], s));
     }
+    // the auxiliary stream's work joins the caller's stream
+    ck(cudaEventRecord(ev_join, s2));
+    ck(cudaStreamWaitEvent(s, ev_join, 0));
     ck(cudaMemcpyAsync(grad0, ws + L.lam, L.ustate, cudaMemcpyDeviceToDevice, s));
     return e == cudaSuccess ? ASUCA_OK : ASUCA_ERR_CUDA;
 }
@@ -1380,6 +1415,14 @@ asuca_status asuca_init_grid(const asuca_grid_desc *desc, asuca_grid **out) {
         return ASUCA_ERR_CUDA;
     }
     g->last_stream = nullptr;
+    bool aux_ok = cudaStreamCreateWithFlags(&g->aux_stream, cudaStreamNonBlocking) == cudaSuccess;
+    for (int q = 0; q < 6; q++)
+        aux_ok = aux_ok && cudaEventCreateWithFlags(&g->aux_ev[q], cudaEventDisableTiming) == cudaSuccess;
+    if (!aux_ok) {
+        cudaFreeHost(h);
+        delete g;
+        return ASUCA_ERR_CUDA;
+    }
     *out = g;
     return ASUCA_OK;
 }
@@ -1396,6 +1439,8 @@ asuca_status asuca_free_grid(asuca_grid *g) {
     }
     std::free(g->prof_ev);
     std::free(g->prof_kind);
+    for (int q = 0; q < 6; q++) cudaEventDestroy(g->aux_ev[q]);
+    cudaStreamDestroy(g->aux_stream);
     delete g;
     return ASUCA_OK;
 }
