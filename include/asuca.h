@@ -112,8 +112,9 @@ asuca_status asuca_init_grid(const asuca_grid_desc *desc, asuca_grid **out);
 asuca_status asuca_free_grid(asuca_grid *grid);
 
 /* Bytes of device workspace op needs (256-byte aligned pointer required).
- * ASUCA_OP_STEP: two stage states plus the column-solve scratch, per-column
- * precipitation and budget partials.  ASUCA_OP_ADJOINT: param = nsteps with
+ * ASUCA_OP_STEP: two stage states plus the column-solve scratch (and, with
+ * the fused column pass of ASUCA_TUNE_FUSED_COLUMN, its (F + 2) nz ny nx
+ * doubles), per-column precipitation and budget partials.  ASUCA_OP_ADJOINT: param = nsteps with
  * checkpoints every 10 steps (asuca_adjoint_workspace_bytes takes any
  * interval).  Returns 0 for an invalid grid or op. */
 size_t asuca_workspace_bytes(const asuca_grid *grid, int op, int param);
@@ -133,7 +134,8 @@ asuca_status asuca_step(asuca_grid *grid, asuca_state *state, const void *tenden
 /* Workspace of asuca_adjoint_step: the step workspace, ceil(nsteps / K)
  * checkpoints, one segment of K recorded steps (stage states, limiter
  * branches, the face values of every stage and the column pass's
- * factorisation and solution), four adjoint fields and the column-transpose
+ * factorisation and solution), two such segments when there are several
+ * (see asuca_adjoint_step), four adjoint fields and the column-transpose
  * scratch. */
 size_t asuca_adjoint_workspace_bytes(const asuca_grid *grid, int nsteps, int checkpoint_every);
 
@@ -188,11 +190,19 @@ asuca_status asuca_adjoint_from_checkpoints(asuca_grid *grid, const void *checkp
                                             void *grad_mv, void *grad_mw, void *workspace, size_t workspace_bytes,
                                             void *cuda_stream);
 
+/* Both adjoint entries recompute segment c - 1 on a stream of the grid's own
+ * (made by asuca_init_grid) while cuda_stream reverses segment c; that
+ * stream waits for the work cuda_stream holds when the call begins, and
+ * cuda_stream waits for all of it before the call's last operation, so the
+ * call orders on cuda_stream like any other (also inside a stream capture).
+ * Calls on one grid must not run concurrently. */
+
 /* ---- ensemble -------------------------------------------------------------
  * Members are grids with the same nz, number of tracers, precision and
  * limiter and any horizontal size; they are advanced together by one
- * persistent cooperative kernel per call (three stage phases and one column
- * phase per step, each phase a flattened list of (member, tile) or (member,
+ * persistent cooperative kernel per call (three stage phases, the second and
+ * third carrying the top-down half of the column pass, and one
+ * back-substitution phase per step, each phase a flattened list of (member, tile) or (member,
  * column) work items, separated by device-wide barriers whose waits give up
  * after about one second and report ASUCA_ERR_TIMEOUT).  Members never share
  * a tile, so every member's result equals asuca_step on that member alone.
