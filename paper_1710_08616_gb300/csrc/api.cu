@@ -1079,6 +1079,12 @@ asuca_status ens_enqueue(asuca_grid *const *grids, asuca_state *states, const do
             }
             sp.cdt = cdt[stg];
             sp.hcdt = cdt[2];   // stage 2's factorisation takes the density after the step
+            // stage 1 reads the member's fields by TMA where their rows allow (the kernel
+            // takes the maps from the member table in global memory)
+            if (stg == 0 && user_maps<T>(g, &states[m], TY)) {
+                for (int q = 0; q < 3; q++) sp.umap[q] = g->umap[q];
+                sp.user_tma = 1;
+            }
             mb[m].stage[stg] = sp;
         }
         ColumnParams<T> cp = column_params<T>(g, dt);

@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(32 * TYV, StageShape<T, NF, TYV>::MIN_BLOCKS)
                 __syncthreads();
                 const CUtensorMap *tmap = &mb.stage[stg].tmap;
                 if (stg == 0) {
-                    bad = stage_tile<T, NF, LIM, false, TYV>(sp, tmap, i0, j0, smem_raw);
+                    bad = stage_tile<T, NF, LIM, false, TYV>(sp, tmap, i0, j0, smem_raw, mb.stage[0].umap);
                 } else {
                     const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
                     const unsigned own = (i < sp.nx && j < sp.ny) ? (unsigned)(j * sp.nx + i) : 0u;

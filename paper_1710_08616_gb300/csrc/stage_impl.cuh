@@ -149,7 +149,11 @@ template <> struct Vec2<double> { using type = double2; };
 // float), and with the pair layout its operands arrive in one load.
 template <typename T, int NF, int LIM, bool REC, int TYV, bool DOWN, typename Hook, int LAY>
 __device__ __forceinline__ bool stage_tile_h(const StageParams<T> &p, const CUtensorMap *tmap, int i0, int j0,
-                                             unsigned char *smem_raw, Hook &hook) {
+                                             unsigned char *smem_raw, Hook &hook,
+                                             const CUtensorMap *umaps = nullptr) {
+    // the tensor maps of the caller's fields: p.umap, or a copy in global
+    // memory when p itself lies in shared memory (TMA reads no map from there)
+    const CUtensorMap *um = umaps ? umaps : p.umap;
     static_assert(!(DOWN && REC), "branch recording marches upward");
     using S = StageShape<T, NF, TYV>;
     using T2 = typename Vec2<T>::type;
@@ -232,7 +236,7 @@ __device__ __forceinline__ bool stage_tile_h(const StageParams<T> &p, const CUte
                 sx = 4 + 2 * (c2 % PH);
                 sy = r < 2 ? r : TY + r;
             }
-            soff[q] = sy * SX + sx;
+            soff[q] = sy * SX + sx;   // sx even
             const int gj = wrap_index(j0 + sy - 2, ny) * nx;
             goff[q] = (unsigned)(gj + wrap_index(i0 + sx - 4, nx));
             goff1[q] = (unsigned)(gj + wrap_index(i0 + sx - 3, nx));
@@ -240,6 +244,12 @@ __device__ __forceinline__ bool stage_tile_h(const StageParams<T> &p, const CUte
         }
     }
     __syncthreads();
+
+    // every field of the caller's input aligned to a pair of elements (the
+    // cp.async path then copies adjacent cell pairs in one request)
+    bool yin_pairs = true;
+#pragma unroll
+    for (int f = 0; f < NF; f++) yin_pairs = yin_pairs && (reinterpret_cast<uintptr_t>(p.yin[f]) % (2 * sizeof(T))) == 0;
 
     // ring slots of march steps t-1 .. t+2 and of the request t+D-2, rotated
     // by one slot per step (slot(n) = ring + (n mod D) SLOT_ELEMS)
@@ -261,9 +271,9 @@ __device__ __forceinline__ bool stage_tile_h(const StageParams<T> &p, const CUte
                         tma_load_4d(dst, tmap, 2 * i0, 0, j0, lev, bar);
                     } else {
                         mbar_expect_tx(bar, S::TX_BYTES);
-                        tma_load_3d(dst, &p.umap[0], i0 - 4, j0 - 2, lev, bar);
-                        tma_load_3d(dst + FE, &p.umap[1], i0 - 4, j0 - 2, lev, bar);
-                        if (NF > 2) tma_load_4d(dst + 2 * FE, &p.umap[2], i0 - 4, j0 - 2, lev, 0, bar);
+                        tma_load_3d(dst, um + 0, i0 - 4, j0 - 2, lev, bar);
+                        tma_load_3d(dst + FE, um + 1, i0 - 4, j0 - 2, lev, bar);
+                        if (NF > 2) tma_load_4d(dst + 2 * FE, um + 2, i0 - 4, j0 - 2, lev, 0, bar);
                     }
                 }
             }
@@ -279,10 +289,17 @@ __device__ __forceinline__ bool stage_tile_h(const StageParams<T> &p, const CUte
                         ASUCA_BC(g0, (long long)nz * plane, p.status);
                         ASUCA_BC(g1, (long long)nz * plane, p.status);
                         ASUCA_BC(s0, S::SLOT_ELEMS - (NF - 1) * FE - 1, p.status);
+                        // the pair's two cells adjacent and aligned in every field:
+                        // one copy of both (s0 is even, so the slot side is aligned)
+                        if (yin_pairs && g1 == g0 + 1 && !(g0 & 1u)) {
 #pragma unroll
-                        for (int f = 0; f < NF; f++) {
-                            cp_async<sizeof(T)>(sl + f * FE + s0, p.yin[f] + g0);
-                            cp_async<sizeof(T)>(sl + f * FE + s0 + 1, p.yin[f] + g1);
+                            for (int f = 0; f < NF; f++) cp_async<2 * sizeof(T)>(sl + f * FE + s0, p.yin[f] + g0);
+                        } else {
+#pragma unroll
+                            for (int f = 0; f < NF; f++) {
+                                cp_async<sizeof(T)>(sl + f * FE + s0, p.yin[f] + g0);
+                                cp_async<sizeof(T)>(sl + f * FE + s0 + 1, p.yin[f] + g1);
+                            }
                         }
                     }
                 }
@@ -700,10 +717,10 @@ __device__ __forceinline__ bool stage_tile_h(const StageParams<T> &p, const CUte
 // buffer: pairs; the caller's fields: raw).
 template <typename T, int NF, int LIM, bool REC, int TYV = 8>
 __device__ __forceinline__ bool stage_tile(const StageParams<T> &p, const CUtensorMap *tmap, int i0, int j0,
-                                           unsigned char *smem_raw) {
+                                           unsigned char *smem_raw, const CUtensorMap *umaps = nullptr) {
     NoHook h;
     if (p.tma_in) return stage_tile_h<T, NF, LIM, REC, TYV, false, NoHook, LAYOUT_PAIR>(p, tmap, i0, j0, smem_raw, h);
-    return stage_tile_h<T, NF, LIM, REC, TYV, false, NoHook, LAYOUT_RAW>(p, tmap, i0, j0, smem_raw, h);
+    return stage_tile_h<T, NF, LIM, REC, TYV, false, NoHook, LAYOUT_RAW>(p, tmap, i0, j0, smem_raw, h, umaps);
 }
 
 template <typename T, int NF, int LIM, bool REC, int TYV, int LAY>
