@@ -42,7 +42,7 @@ __global__ void __launch_bounds__(COL_TPB, 3) column_kernel(const __grid_constan
 }
 
 // The bottom-up half of the column pass after ColDownHook: back substitution
-// from the full-size scratch ([nz][F + 1][plane]), (rho phi)_k = sigma_k z_k
+// from the fused scratch (fscratch_level / fscratch_col), (rho phi)_k = sigma_k z_k
 // for rho*theta and every tracer (column_one's bottom-up pass, operation for
 // operation), and the column budget partials.  Grid-stride over columns,
 // one thread per column.

@@ -455,7 +455,8 @@ cudaError_t launch_column(const ColumnParams<T> &p, int nf, int grid, int block,
 template <typename T>
 struct FusedParams {
     StageParams<T> s;       // stage 3: padded phi input (TMA), unpadded output
-    ColumnParams<T> c;      // column constants; scratch is the full-size [nz][F + 1][plane] area
+    ColumnParams<T> c;      // column constants; scratch is the fused scratch (fscratch_level layout), alpha
+                            // the [nz][plane] array of the split column pass
 };
 template <typename T>
 cudaError_t launch_stage3_column(const FusedParams<T> &p, int nf, cudaStream_t s);
