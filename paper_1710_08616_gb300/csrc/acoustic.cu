@@ -23,7 +23,10 @@
 // values wait in the output arrays) and back down (back substitution and s').
 // In stage 1 the up pass's inputs arrive through a per-thread cp.async ring
 // in shared memory, requested two levels ahead; stage 2 prefetches one level
-// into registers.
+// into registers.  The values that wait for the way down are stored with an
+// L2 evict-last policy and read back with evict-first (createpolicy and
+// L2::cache_hint), so they stay in L2 between the two passes instead of
+// making a round trip to HBM while the streamed inputs pass through.
 // The thread recomputes the neighbouring face's stage-1 momentum it needs for
 // the divergence (the same operations as the neighbour's own), so a stage is
 // one launch with no grid-wide dependency.  Stage 2 updates the caller's
@@ -53,8 +56,29 @@ __device__ __forceinline__ void ac_cp_async(T *dst, const T *src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d), "l"(src), "n"(sizeof(T)) : "memory");
 }
 
+// stores and loads with an L2 cache policy made by createpolicy
+__device__ __forceinline__ void st_keep(float *a, float v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(a), "f"(v), "l"(pol) : "memory");
+}
+__device__ __forceinline__ void st_keep(double *a, double v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(a), "d"(v), "l"(pol) : "memory");
+}
+__device__ __forceinline__ float ld_last(const float *a, uint64_t pol) {
+    float v;
+    asm volatile("ld.global.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(a), "l"(pol) : "memory");
+    return v;
+}
+__device__ __forceinline__ double ld_last(const double *a, uint64_t pol) {
+    double v;
+    asm volatile("ld.global.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(a), "l"(pol) : "memory");
+    return v;
+}
+
 template <typename T, int STAGE, int D>
 __global__ void __launch_bounds__(256) acoustic_kernel(const __grid_constant__ AcousticParams<T> p) {
+    uint64_t pol_keep, pol_drop;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol_keep));
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol_drop));
     const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y;
     if (i >= p.nx || j >= p.ny) return;
     const int nx = p.nx, nz = p.nz;
@@ -195,10 +219,10 @@ __global__ void __launch_bounds__(256) acoustic_kernel(const __grid_constant__ A
             const T q = Wk - p.cq[k] * (sk - s_prev);
             const T rhs = q - p.A[k] * (r - r_prev);
             const T d = (k == 1 ? rhs : rhs - p.lo[k] * d_prev) * p.inv[k];
-            Wo[b + own] = d;                   // face k waits here for the way down
+            st_keep(Wo + b + own, d, pol_keep);   // face k waits here for the way down
             d_prev = d;
         }
-        So[b + own] = r;
+        st_keep(So + b + own, r, pol_keep);
         r_prev = r;
         s_prev = sk;
         Wk = Wk1;
@@ -207,15 +231,15 @@ __global__ void __launch_bounds__(256) acoustic_kernel(const __grid_constant__ A
     // ---- down: back substitution and s' (the values of level k-1 loaded
     // while level k is finished)
     T Wup = T(0);                              // W'_{k+1} (the lid at nz)
-    T dk = nz > 1 ? Wo[(unsigned)(nz - 1) * plane + own] : T(0);
-    T rk = So[(unsigned)(nz - 1) * plane + own];
+    T dk = nz > 1 ? ld_last(Wo + (unsigned)(nz - 1) * plane + own, pol_drop) : T(0);
+    T rk = ld_last(So + (unsigned)(nz - 1) * plane + own, pol_drop);
 #pragma unroll 1
     for (int k = nz - 1; k >= 0; k--) {
         const unsigned b = (unsigned)k * plane;
         T dn = T(0), rn = T(0);
         if (k >= 1) {
-            rn = So[b - plane + own];
-            if (k >= 2) dn = Wo[b - plane + own];
+            rn = ld_last(So + b - plane + own, pol_drop);
+            if (k >= 2) dn = ld_last(Wo + b - plane + own, pol_drop);
         }
         T Wn = T(0);
         if (k >= 1) {
