@@ -378,7 +378,7 @@ __device__ __forceinline__ double factor_level(const ColLevel<T> &L, int k, int 
 // written by the back substitution.
 template <typename T, int NF>
 struct ColDownHook {
-    static constexpr bool active = true, keep_output = false, own_rho = false;
+    static constexpr bool active = true, keep_output = false, own_rho = false, defers = false;
     static constexpr int NT = NF - 1;
     static constexpr int NQ = NF + 1;   // m, gamma, e[NT]
     const ColumnParams<T> &c;
@@ -422,15 +422,19 @@ struct ColDownHook {
             e_up[f] = e;
         }
     }
+    __device__ __forceinline__ void early() {}
     __device__ __forceinline__ void done(bool) {}
 };
 
 // The factorisation in stage 2 (the stage's own result is written as usual):
 // from the density after the step (rho_h, rho_next), m and gamma to the fused
-// scratch and alpha to c.alpha ([nz][plane]).
-template <typename T, int NF>
+// scratch and alpha to c.alpha ([nz][plane]).  With LAG a level's
+// factorisation waits for the next level's early() and so runs beside that
+// level's faces (its dependent FP64 chain then interleaves with independent
+// stencil work); the last level's runs in done().
+template <typename T, int NF, bool LAG = false>
 struct FactorHook {
-    static constexpr bool active = true, keep_output = true, own_rho = true;
+    static constexpr bool active = true, keep_output = true, own_rho = true, defers = LAG;
     static constexpr int NQ = NF + 1;
     const ColumnParams<T> &c;
     const ColLevel<T> *tab;
@@ -442,9 +446,33 @@ struct FactorHook {
         : c(cp), tab(tab_), sc(cp.scratch + fscratch_col(own, NQ)), alpha_out(cp.alpha + own),
           pl((size_t)cp.plane), ls((size_t)fscratch_level(cp.plane, NQ)), g_hi(0.0), m_up(0.0) {}
 
+    struct Pending {   // LAG: the level whose factorisation is pending, and its densities
+        int k = -1;
+        T rh = T(0), rn = T(0);
+    };
+    struct NoPending {};
+    typename std::conditional<LAG, Pending, NoPending>::type pend;
+
     template <typename U, int NF2>
     __device__ __forceinline__ void level(int k, const U (&)[NF2], bool valid, U rho_next, U rho_h) {
         if (!valid) return;
+        if constexpr (LAG) {
+            pend.k = k;
+            pend.rh = rho_h;
+            pend.rn = rho_next;
+        } else {
+            run(k, rho_h, rho_next);
+        }
+    }
+    __device__ __forceinline__ void early() {
+        if constexpr (LAG) {
+            if (pend.k >= 0) {
+                run(pend.k, pend.rh, pend.rn);
+                pend.k = -1;
+            }
+        }
+    }
+    __device__ __forceinline__ void run(int k, T rho_h, T rho_next) {
         const ColLevel<T> L = tab[k];
         size_t ao = (size_t)k * pl;
 #ifdef ASUCA_BOUNDS_CHECK
@@ -455,14 +483,14 @@ struct FactorHook {
         alpha_out[ao] = factor_level<T>(L, k, c.nz, rho_h, rho_next, g_hi, m_up, fscratch_at(c, sc, k, ls, 1), ls,
                                         c.scratch, (long long)c.nz * (long long)ls, c.status);
     }
-    __device__ __forceinline__ void done(bool) {}
+    __device__ __forceinline__ void done(bool) { early(); }
 };
 
 // Relaxation, sedimentation and the elimination sweep in stage 3, after
 // FactorHook in stage 2 (alpha read from c.alpha one level ahead).
 template <typename T, int NF>
 struct SweepHook {
-    static constexpr bool active = true, keep_output = false, own_rho = false;
+    static constexpr bool active = true, keep_output = false, own_rho = false, defers = false;
     static constexpr int NT = NF - 1;
     static constexpr int NQ = NF + 1;
     const ColumnParams<T> &c;
@@ -518,6 +546,7 @@ struct SweepHook {
             e_up[f] = e;
         }
     }
+    __device__ __forceinline__ void early() {}
     __device__ __forceinline__ void done(bool) {}
 };
 

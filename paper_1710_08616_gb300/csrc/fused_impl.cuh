@@ -54,9 +54,9 @@ __global__ void __launch_bounds__(32 * TYV, StageShape<T, NF, TYV>::MIN_BLOCKS)
     const int i0 = blockIdx.x * S::TX, j0 = blockIdx.y * TYV;
     const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
     const unsigned own = (i < p.nx && j < p.ny) ? (unsigned)(j * p.nx + i) : 0u;
-    FactorHook<T, NF> hook(fp.c, tab, own);
-    (void)stage_tile_h<T, NF, LIM, false, TYV, true, FactorHook<T, NF>, LAYOUT_PAIR>(p, &p.tmap, i0, j0, smem_raw,
-                                                                                   hook);
+    FactorHook<T, NF, true> hook(fp.c, tab, own);
+    (void)stage_tile_h<T, NF, LIM, false, TYV, true, FactorHook<T, NF, true>, LAYOUT_PAIR>(p, &p.tmap, i0, j0,
+                                                                                         smem_raw, hook);
 }
 
 // KIND 0: stage 3 with the whole top-down pass, 1: stage 3 with the sweep

@@ -120,9 +120,10 @@ __device__ __forceinline__ void cp_async_wait() {
 // may reuse the same shared memory and mbarriers.
 // The default output of a tile: the stage result is written to p.yout.
 struct NoHook {
-    static constexpr bool active = false, keep_output = true, own_rho = false;
+    static constexpr bool active = false, keep_output = true, own_rho = false, defers = false;
     template <typename T, int NF>
     __device__ __forceinline__ void level(int, const T (&)[NF], bool, T, T) {}
+    __device__ __forceinline__ void early() {}
     __device__ __forceinline__ void done(bool) {}
 };
 
@@ -142,8 +143,10 @@ template <> struct Vec2<double> { using type = double2; };
 // rho_next, rho_h), where rho_next is the density result of the next level of
 // the march (the same expression that level will evaluate); a hook with
 // own_rho receives in rho_h and rho_next the density Y^n + hcdt R instead of
-// the stage's (the same expression with p.hcdt for cdt).  hook.done(valid)
-// follows the last level.
+// the stage's (the same expression with p.hcdt for cdt).  hook.early() runs
+// before each level's faces (a hook may defer a level's work to it, so that
+// the work interleaves with the next level's faces), hook.done(valid) after
+// the last level.
 // The fields are processed in pairs (1, 2), (3, 4), ...: a pair shares every
 // operation of its face reconstruction and divergence (packed FP32x2 for
 // float), and with the pair layout its operands arrive in one load.
@@ -470,6 +473,7 @@ __device__ __forceinline__ bool stage_tile_h(const StageParams<T> &p, const CUte
             }
         }
         if (t + 1 < nz) prefetch(level_of(t + 1));
+        if constexpr (Hook::defers) hook.early();   // a hook's work left from the previous level, beside these faces
 
         // ---- faces: upwind cell c, downwind cell o and far upwind cell by address
         // march steps t-1 .. t+2 (ghost levels copy the boundary cell)
