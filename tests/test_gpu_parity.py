@@ -278,6 +278,64 @@ def test_large_1024x1024x58_one_step_sampled_columns(asuca, large_case, prec, to
     del st
 
 
+# Conservation bar of the FP32-mixed path over three steps: every stored value
+# is rounded to float once per step (2^-24 relative) and the column pass's
+# output goes through up to four float roundings (the narrowed unknown and
+# its scaling), so the totals can drift by at most 3 * 5 * 2^-24 = 9e-7 of
+# their size if every rounding fell the same way.
+CONS32 = 2e-6
+
+
+@pytest.mark.parametrize("prec,tol,cons", [(1, TOL32, CONS32), (0, TOL64, TOL64)])
+def test_large_1024x1024x58_three_steps_windows_and_budgets(asuca, large_case, prec, tol, cons):
+    """Three steps at the full 1024x1024x58, 8-tracer size in the benchmark's
+    launch configuration.  Sampled 4x4 windows (corners, edges, random picks)
+    against the oracle on their three-step dependency cone; and the budgets
+    against properties that hold at any size: the device's budgets equal the
+    oracle's compensated sums over the device's own fields (1e-12 in both
+    paths, since floats widen to double exactly); total mass and every
+    tracer that does not sediment keep their totals (periodic domain, closed
+    lids, conservative advection and diffusion); the sedimenting tracer loses
+    exactly the precipitation."""
+    import torch
+    c = large_case
+    nsteps = 3
+    og, g = _grid_pair(asuca, c, prec)
+    st = asuca.State.from_case(c, prec=prec)
+    bud = asuca.step(g, st, c.dt, nsteps, budgets=True)
+    torch.cuda.synchronize()
+    assert asuca.get_status(g) == asuca.OK
+    bud = bud.cpu().numpy()
+    Y0 = c.state()
+    rng = np.random.default_rng(29)
+    picks = SAMPLES + [tuple(int(v) for v in rng.integers(0, 1024, 2)) for _ in range(3)]
+    for (i0, j0) in picks:
+        w = h = 4
+        ref = oracle.step_window(og, Y0, c.mu, c.mv, c.mw, c.dt, nsteps, i0, j0, w, h)
+        ii = torch.tensor([(i0 + q) % c.nx for q in range(w)], device="cuda")
+        jj = torch.tensor([(j0 + q) % c.ny for q in range(h)], device="cuda")
+        got = st.fields()[:, :, jj][:, :, :, ii].double().cpu().numpy()
+        _assert_fields(got, ref, tol, f"large prec={prec} {nsteps} steps window {(i0, j0)}", both=(prec == 0))
+    before = oracle.budgets(og, Y0)
+    del Y0
+    Y1 = _np(st)
+    del st
+    after = oracle.budgets(og, Y1, precip=float(bud[-1]))
+    del Y1
+    # the device's sums of its own fields
+    d = np.abs(bud - after) / np.abs(after).clip(1e-300)
+    assert d.max() <= 1e-12, f"prec={prec}: budgets vs sums of the fields {d}"
+    # conservation: mass and the tracers that do not sediment; the sedimenting
+    # tracer (the last, the oracle grid's default) loses the precipitation
+    F = c.nfields
+    sed = F - 1
+    assert bud[-1] > 0.0
+    for f in [0] + list(range(2, F)):
+        loss = bud[-1] if f == sed else 0.0
+        drift = abs(before[f] - after[f] - loss) / abs(before[f])
+        assert drift <= cons, f"prec={prec}: field {f} total drifts by {drift:.3e} > {cons}"
+
+
 # ------------------------------------------------------------------ arithmetic helpers
 
 def test_integer_pipe_conversions_match_hardware(asuca):
