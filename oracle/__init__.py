@@ -2,7 +2,8 @@
 
 Only tests/, the smoke check and the benchmark's CPU-baseline leg may import
 this package.  It compiles asuca_oracle.c (plain C, FP64, no fast-math, no FP
-contraction) into liborc.so next to the source and calls it through ctypes.
+contraction) into liborc.so next to the source and calls it through ctypes
+(ORACLE_LIBRARY, if set, names another build of the same source to load).
 It shares no code with the CUDA library.
 """
 from __future__ import annotations
@@ -26,17 +27,24 @@ LIM_KOREN, LIM_LINEAR, LIM_UPWIND1 = 0, 1, 2
 TAU, K0, KH, VSED = 3600.0, 50.0, 1000.0, 2.0
 
 
+def compile_library(src: str, out: str) -> str:
+    """Compile an oracle source file (including asuca_oracle.h from this
+    directory) into the shared library `out`, with the oracle's flags."""
+    cc = os.environ.get("CC", "cc")
+    cmd = [cc, "-O2", "-fno-fast-math", "-ffp-contract=off", "-fopenmp", "-std=c11",
+           "-shared", "-fPIC", "-I", _HERE, "-o", out, src, "-lm"]
+    subprocess.run(cmd, check=True)
+    return out
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle if the library is missing or older than its source."""
     with _lock:
         newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
         if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= newest:
             return _SO
-        cc = os.environ.get("CC", "cc")
         tmp = _SO + f".tmp{os.getpid()}"
-        cmd = [cc, "-O2", "-fno-fast-math", "-ffp-contract=off", "-fopenmp", "-std=c11",
-               "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"]
-        subprocess.run(cmd, check=True)
+        compile_library(_SRC, tmp)
         os.replace(tmp, _SO)
         return _SO
 
@@ -54,10 +62,16 @@ _U8 = ctypes.POINTER(ctypes.c_ubyte)
 
 
 def lib():
+    """The loaded oracle library: liborc.so built from the source beside this
+    file, or the library named by ORACLE_LIBRARY (the mutation test loads
+    copies of the oracle with one planted slip each through it)."""
     global _lib
     if _lib is None:
-        build()
-        L = ctypes.CDLL(_SO)
+        so = os.environ.get("ORACLE_LIBRARY")
+        if not so:
+            build()
+            so = _SO
+        L = ctypes.CDLL(so)
         G = ctypes.POINTER(OrcGrid)
         L.orc_limiter.restype = ctypes.c_double
         L.orc_limiter.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int,

@@ -12,7 +12,8 @@
 * The new momenta are the third stage's integration: orc_acoustic over n_3
   short steps of dt / n_3 from (U, V, W)^n and s^n = rho^n / rho0 - 1, bit
   for bit.
-* The short-step counts per stage are round(ns / 3), round(ns / 2), ns.
+* The short-step counts per stage are round(ns / 3), round(ns / 2), ns, each
+  the integer nearest to c_q ns (halves up), at least one, for ns = 1 .. 24.
 """
 import numpy as np
 import pytest
@@ -31,6 +32,14 @@ def test_short_step_counts():
     assert [oracle.hevi_short_steps(6, q) for q in range(3)] == [2, 3, 6]
     assert [oracle.hevi_short_steps(1, q) for q in range(3)] == [1, 1, 1]
     assert [oracle.hevi_short_steps(12, q) for q in range(3)] == [4, 6, 12]
+    # every count is the integer nearest to c_q ns (halves go up), at least one
+    for ns in range(1, 25):
+        for q, cq in enumerate((1 / 3, 1 / 2, 1.0)):
+            n = oracle.hevi_short_steps(ns, q)
+            x = cq * ns
+            assert n >= 1
+            if x >= 0.5:
+                assert abs(n - x) < 0.5 + 1e-12 and not (abs(n - x + 0.5) < 1e-12), (ns, q, n)
 
 
 @pytest.mark.parametrize("lim", [0, 1])

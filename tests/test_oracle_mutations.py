@@ -1,0 +1,191 @@
+"""Mutation check of the oracle's pins.
+
+Each entry below plants one plausible slip in a copy of the oracle's C source
+(a sign, an index, a weight, a transposed coefficient, a dropped factor), the
+copy is compiled with the oracle's own flags, and the CPU pin suites run
+against it in a child process (the oracle module loads the copy through
+ORACLE_LIBRARY).  Every mutant must make at least one pin fail; an
+unmutated copy, built and loaded the same way, must pass them all.  A slip
+that no pin notices would be a slip the oracle could carry into every GPU
+parity test unseen.
+
+Each slip is a literal text substitution that must match the source exactly
+once, so an edit of the oracle that moves a line fails here loudly instead of
+silently testing nothing.
+"""
+import concurrent.futures as cf
+import os
+import subprocess
+import sys
+
+import pytest
+
+import oracle
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+SRC = os.path.join(ROOT, "oracle", "asuca_oracle.c")
+PIN_FILES = ["tests/test_oracle_pins.py", "tests/test_oracle_adjoint.py", "tests/test_oracle_open.py",
+             "tests/test_oracle_hevi.py"]
+
+# (name, original text, slip): Koren limiter and upwind face
+MUTANTS = [
+    ("koren kappa weights swapped",
+     "double t2 = (a0 + 2.0 * a1) / 3.0;", "double t2 = (2.0 * a0 + a1) / 3.0;"),
+    ("koren 2r term on the wrong difference",
+     "double t1 = 2.0 * a1;", "double t1 = 2.0 * a0;"),
+    ("koren cap at 1 instead of 2",
+     "double t3 = 2.0 * a0;", "double t3 = a0;"),
+    ("koren sign of the increment",
+     "L = d0 > 0.0 ? m : -m;", "L = d0 > 0.0 ? -m : m;"),
+    ("koren limits only rising slopes",
+     "int same = (d0 > 0.0 && d1 > 0.0) || (d0 < 0.0 && d1 < 0.0);", "int same = (d0 > 0.0 && d1 > 0.0);"),
+    ("upwind tie M = 0 taken from the right",
+     "if (m >= 0.0) {\n        double d0 = p0 - pm1, d1 = p1 - p0;",
+     "if (m > 0.0) {\n        double d0 = p0 - pm1, d1 = p1 - p0;"),
+    ("negative-flow differences reversed",
+     "double d0 = p1 - p2, d1 = p0 - p1;", "double d0 = p2 - p1, d1 = p1 - p0;"),
+    ("half of the limited increment dropped",
+     "return p0 + 0.5 * orc_limiter(d0, d1, lim, branch);", "return p0 + orc_limiter(d0, d1, lim, branch);"),
+    # flux form and divergence
+    ("i flux difference reversed",
+     "double r = -((xp - xm) / g->dx + (yp - ym) / g->dy + (zp - zm) / g->dz[k]);\n"
+     "                    if (tend && f > 0) {",
+     "double r = -((xm - xp) / g->dx + (yp - ym) / g->dy + (zp - zm) / g->dz[k]);\n"
+     "                    if (tend && f > 0) {"),
+    ("j divergence divided by dx",
+     "double r = -((xp - xm) / g->dx + (yp - ym) / g->dy + (zp - zm) / g->dz[k]);\n"
+     "                    if (tend && f > 0) {",
+     "double r = -((xp - xm) / g->dx + (yp - ym) / g->dx + (zp - zm) / g->dz[k]);\n"
+     "                    if (tend && f > 0) {"),
+    ("k divergence divided by the level below's dz",
+     "double r = -((xp - xm) / g->dx + (yp - ym) / g->dy + (zp - zm) / g->dz[k]);\n"
+     "                    if (tend && f > 0) {",
+     "double r = -((xp - xm) / g->dx + (yp - ym) / g->dy + (zp - zm) / g->dz[k > 0 ? k - 1 : 0]);\n"
+     "                    if (tend && f > 0) {"),
+    ("j faces carry the i mass flux",
+     "m = mv[gidx(g, k, gj, gi)];", "m = mu[gidx(g, k, gj, gi)];"),
+    ("vertical mass flux one level low",
+     "m = mw[gidx(g, k + 1, gj, gi)];", "m = mw[gidx(g, k, gj, gi)];"),
+    ("top ghost mirrors instead of copying",
+     "int kp2 = k + 2 > nz - 1 ? nz - 1 : k + 2;", "int kp2 = k + 2 > nz - 1 ? nz - 2 : k + 2;"),
+    # RK3
+    ("first RK weight 1/2",
+     "const double c[3] = {dt / 3.0, dt / 2.0, dt};\n    const int F = 2 + g->ntr, nz = g->nz;",
+     "const double c[3] = {dt / 2.0, dt / 2.0, dt};\n    const int F = 2 + g->ntr, nz = g->nz;"),
+    ("RK stages start from the previous stage",
+     "dst[o] = Yn[o] + c[s] * R[o];", "dst[o] = Ys[o] + c[s] * R[o];"),
+    # column physics
+    ("Thomas elimination with the upper coefficient",
+     "dp[k] = (d[k] - a[k] * dp[k - 1]) / den;", "dp[k] = (d[k] - c[k] * dp[k - 1]) / den;"),
+    ("Thomas back substitution sign",
+     "x[k] = dp[k] - cp[k] * x[k + 1];", "x[k] = dp[k] + cp[k] * x[k + 1];"),
+    ("face density not averaged",
+     "double rhof = 0.5 * (Y[k * cs] + Y[(k + 1) * cs]);", "double rhof = Y[k * cs];"),
+    ("diffusion diagonal misses the lower face",
+     "b[k] = Y[k * cs] * g->dz[k] + gf[k] + gf[k + 1];", "b[k] = Y[k * cs] * g->dz[k] + gf[k + 1];"),
+    ("diffusivity taken at the cell centre",
+     "double K = g->k0 * exp(-zf[k + 1] / g->kh);\n            double dzc",
+     "double K = g->k0 * exp(-zc[k] / g->kh);\n            double dzc"),
+    ("sedimentation flux halved",
+     "P = g->vsed * q[k * cs];", "P = 0.5 * g->vsed * q[k * cs];"),
+    ("sedimentation denominator without dt",
+     "q[k * cs] = (q[k * cs] * dz + dt * P) / (dz + dt * g->vsed);",
+     "q[k * cs] = (q[k * cs] * dz + dt * P) / (dz + g->vsed);"),
+    ("precipitation without dt",
+     "*precip += dt * P * g->dx * g->dy;", "*precip += P * g->dx * g->dy;"),
+    ("relaxation target at the face height",
+     "th = (th + r * (THETA_REF0 + THETA_REF_LAPSE * zc[k])) / (1.0 + r);\n            Y[fs + k * cs]",
+     "th = (th + r * (THETA_REF0 + THETA_REF_LAPSE * zf[k])) / (1.0 + r);\n            Y[fs + k * cs]"),
+    ("relaxation implicit factor doubled",
+     "th = (th + r * (THETA_REF0 + THETA_REF_LAPSE * zc[k])) / (1.0 + r);\n            Y[fs + k * cs]",
+     "th = (th + r * (THETA_REF0 + THETA_REF_LAPSE * zc[k])) / (1.0 + 2.0 * r);\n            Y[fs + k * cs]"),
+    # budgets and the window
+    ("budget without the layer depth",
+     "Y[f * fs + k * cs + (size_t)j * g->nx + i] * g->dz[k] * g->dx * g->dy",
+     "Y[f * fs + k * cs + (size_t)j * g->nx + i] * g->dx * g->dy"),
+    ("compensation term of the wrong order",
+     "if (fabs(a->s) >= fabs(x)) a->c += (a->s - t) + x;", "if (fabs(a->s) >= fabs(x)) a->c += (x - t) + a->s;"),
+    ("window cone too narrow",
+     "const int F = 2 + g->ntr, nz = g->nz, r = 6 * nsteps;", "const int F = 2 + g->ntr, nz = g->nz, r = 4 * nsteps;"),
+    # tangent-linear and adjoint
+    ("frozen kappa branch weights swapped",
+     "case 2: *a = 1.0 / 3.0; *b = 2.0 / 3.0; break;", "case 2: *a = 2.0 / 3.0; *b = 1.0 / 3.0; break;"),
+    ("adjoint of phi = u / rho: density term sign",
+     "lamY[st[q]] -= lph * ph[q] / rho;", "lamY[st[q]] += lph * ph[q] / rho;"),
+    ("adjoint flux difference at the wrong level",
+     "const double lF = lamR[(size_t)f * C + b] * rdelta(g, dir, kb) -",
+     "const double lF = lamR[(size_t)f * C + b] * rdelta(g, dir, k) -"),
+    ("column tangent drops the density perturbation",
+     "dOut[(size_t)f * nz + k] = drho[k] * ph[k] + w->Yb[k] * x[k];",
+     "dOut[(size_t)f * nz + k] = w->Yb[k] * x[k];"),
+    ("sedimentation adjoint with the wrong layer",
+     "if (k > 0) nu += dt * g->vsed / (g->dz[k - 1] + dt * g->vsed) * nu_prev;",
+     "if (k > 0) nu += dt * g->vsed / (g->dz[k] + dt * g->vsed) * nu_prev;"),
+    # open boundaries
+    ("east ghosts read from the west strip",
+     "if (i >= g->nx) return ghost[halo_index(g, 1, f - 1, k, i - g->nx, j)];",
+     "if (i >= g->nx) return ghost[halo_index(g, 0, f - 1, k, i - g->nx, j)];"),
+    ("open j faces with the level pitch of the cells",
+     "m = mv_x[((size_t)k * (ny + 1) + (j + 1)) * nx + i];", "m = mv_x[((size_t)k * ny + (j + 1)) * nx + i];"),
+    # 7-point stencil, damping
+    ("7-point stencil wraps through the lids",
+     "ku = k < nz - 1 ? k + 1 : nz - 1;", "ku = k < nz - 1 ? k + 1 : 0;"),
+    ("7-point stencil centre weight of a 2-D Laplacian",
+     "v + c * (sum - 6.0 * v)", "v + c * (sum - 4.0 * v)"),
+    ("damping target with the boundary datasets swapped",
+     "mtratio * (ref[q] + b0[q]) + tratio * (ref[q] + b1[q]) - ref[q]",
+     "mtratio * (ref[q] + b1[q]) + tratio * (ref[q] + b0[q]) - ref[q]"),
+    ("damping ramp reversed",
+     "const double x = (double)(width - d) / width;", "const double x = (double)d / width;"),
+    ("damping explicit instead of implicit",
+     "y[q] = (y[q] + a * target) / (1.0 + a);", "y[q] = y[q] + a * (target - y[q]);"),
+    # acoustic short steps and their nesting
+    ("acoustic first stage of full length",
+     "const double tau = stage == 0 ? 0.5 * h : h;", "const double tau = h;"),
+    ("acoustic vertical spacing of the upper level only",
+     "const double dzc = 0.5 * (dz[f - 1] + dz[f]);\n        const double g = tau",
+     "const double dzc = dz[f];\n        const double g = tau"),
+    ("acoustic off-centring weights swapped",
+     "rhs[r] = W[f] - g * (1.0 - beta) * (s[f] - s[f - 1]);", "rhs[r] = W[f] - g * beta * (s[f] - s[f - 1]);"),
+    ("acoustic pressure gradient sign in i",
+     "Uo[c] = U[c] - tau * cs2 * rho0c[k] * (se[e] - se[c]) / dx;",
+     "Uo[c] = U[c] - tau * cs2 * rho0c[k] * (se[c] - se[e]) / dx;"),
+    ("short steps per stage truncated",
+     "const int n = (int)floor(frac * ns + 0.5);", "const int n = (int)floor(frac * ns);"),
+    ("mean vertical flux from the new momentum only",
+     "Mw[f * plane + q] += wgt * ((1.0 - beta) * Wc[f] + beta * Wn[f]);", "Mw[f * plane + q] += wgt * Wn[f];"),
+]
+
+
+def _run_pins(so, timeout=600):
+    env = dict(os.environ, ORACLE_LIBRARY=so, OMP_NUM_THREADS="2")
+    cmd = [sys.executable, "-m", "pytest", *PIN_FILES, "-x", "-q", "-m", "not gpu", "-p", "no:cacheprovider"]
+    r = subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, timeout=timeout)
+    return r.returncode, (r.stdout + r.stderr)[-2000:]
+
+
+def _mutant(tmp, idx, name, old, new, src):
+    c = os.path.join(tmp, f"mutant{idx}.c")
+    with open(c, "w") as fh:
+        fh.write(src.replace(old, new))
+    so = oracle.compile_library(c, os.path.join(tmp, f"libmutant{idx}.so"))
+    return name, _run_pins(so)
+
+
+def test_every_slip_fails_a_pin(tmp_path):
+    src = open(SRC).read()
+    for name, old, new in MUTANTS:
+        assert src.count(old) == 1, f"'{name}': the original text occurs {src.count(old)} times"
+        assert old != new
+    tmp = str(tmp_path)
+    # control: the unmutated source, built and loaded the same way, passes
+    control = oracle.compile_library(SRC, os.path.join(tmp, "libcontrol.so"))
+    rc, log = _run_pins(control)
+    assert rc == 0, "the unmutated copy fails the pins:\n" + log
+    with cf.ThreadPoolExecutor(max_workers=max(2, min(8, (os.cpu_count() or 2) // 2))) as ex:
+        futs = [ex.submit(_mutant, tmp, q, name, old, new, src) for q, (name, old, new) in enumerate(MUTANTS)]
+        results = [f.result() for f in futs]
+    # returncode 1: tests ran and at least one failed (not a crash or a collection error)
+    survived = [(name, rc, log) for name, (rc, log) in results if rc != 1]
+    assert not survived, "\n\n".join(f"'{n}' (rc {rc}):\n{log}" for n, rc, log in survived)

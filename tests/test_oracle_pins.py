@@ -97,12 +97,16 @@ def _uniform_case(nx, ny, nz, ntr, u=0.0, v=0.0, w=0.0, dz=None, rng=None, integ
 @pytest.mark.parametrize("axis,sign", [(0, 1), (0, -1), (1, 1), (1, -1)])
 def test_courant_one_upwind_shift_is_bit_exact(axis, sign):
     """One forward-Euler stage of first-order upwind at Courant 1 moves every
-    value exactly one cell downstream (powers of two keep all steps exact)."""
+    value exactly one cell downstream (powers of two keep all steps exact).
+    The spacing across the flow is half the spacing along it, so a flux
+    difference divided by the other direction's spacing moves values two
+    cells instead of one."""
     nx, ny, nz = 12, 10, 3
     u = 16.0 * sign if axis == 0 else 0.0
     v = 16.0 * sign if axis == 1 else 0.0
     Y, mu, mv, mw, dz = _uniform_case(nx, ny, nz, 2, u=u, v=v, integer=True)
-    g = oracle.Grid(nx, ny, nz, 2, dz, 2048.0, 2048.0, tau=0, k0=0, vsed=0, lim=oracle.LIM_UPWIND1)
+    dx, dy = (2048.0, 1024.0) if axis == 0 else (1024.0, 2048.0)
+    g = oracle.Grid(nx, ny, nz, 2, dz, dx, dy, tau=0, k0=0, vsed=0, lim=oracle.LIM_UPWIND1)
     out = oracle.euler(g, Y, mu, mv, mw, 128.0)
     expect = np.roll(Y, sign, axis=3 if axis == 0 else 2)
     assert np.array_equal(out, expect)
@@ -130,7 +134,8 @@ def test_courant_one_vertical_shift_with_lids():
 def test_linear_fourier_mode_rk3_closed_form(axis, mode, u):
     """kappa=1/3 upwind-biased fluxes with WS-RK3 on a single Fourier mode:
     the amplitude evolves exactly as P(lambda dt)^n, P(z) = 1 + z + z^2/2 + z^3/6,
-    lambda = -(u/dx)(1 - e^{-i th})(5 - e^{-i th} + 2 e^{i th})/6 for u >= 0."""
+    lambda = -(u/dx)(1 - e^{-i th})(5 - e^{-i th} + 2 e^{i th})/6 for u >= 0,
+    dx the spacing along the mode (the spacing across it is different)."""
     n, nz, nsteps = 32, 3, 7
     dx = 2000.0
     dt = 0.6 * dx / abs(u)
@@ -146,8 +151,8 @@ def test_linear_fourier_mode_rk3_closed_form(axis, mode, u):
     mu = np.full((nz, ny, nx), u if axis == 0 else 0.0)
     mv = np.full((nz, ny, nx), u if axis == 1 else 0.0)
     mw = np.zeros((nz + 1, ny, nx))
-    g = oracle.Grid(nx, ny, nz, 1, np.full(nz, 50.0), dx, dx, tau=0, k0=0, vsed=0,
-                    lim=oracle.LIM_LINEAR)
+    g = oracle.Grid(nx, ny, nz, 1, np.full(nz, 50.0), dx if axis == 0 else 1250.0,
+                    dx if axis == 1 else 1250.0, tau=0, k0=0, vsed=0, lim=oracle.LIM_LINEAR)
     for _ in range(nsteps):
         Y = oracle.rk3(g, Y, mu, mv, mw, dt)
     s = 1.0 if u >= 0 else -1.0
@@ -648,6 +653,26 @@ def test_acoustic_vertical_energy(beta):
         assert np.max(np.abs(e / e[0] - 1.0)) <= 1e-12
     else:
         assert np.all(np.diff(e) < 0) and e[-1] < 0.9 * e[0]
+
+
+def test_acoustic_off_centring_changes_the_step_at_second_order():
+    """beta only shares each implicit vertical term between the new and the
+    old state, so every beta gives the same tendency: a short step with
+    beta = 0.8 differs from the centred one (beta = 1/2) by O(h^2), while the
+    step itself changes W and s by O(h).  Their ratio therefore halves with
+    h.  (Weights that do not add to one change the vertical force itself,
+    and the ratio then stays of order one.)"""
+    nz, ny, nx = 8, 4, 5
+    dz, r0c, r0f = _acoustic_base(nz)
+    U, V, W, S = _acoustic_random(nz, ny, nx, 4)
+    rel = []
+    for h in (0.02, 0.01, 0.005, 0.0025):
+        a = oracle.acoustic(U, V, W, S, dz, r0c, r0f, CS2, 0.5, h, 1)
+        b = oracle.acoustic(U, V, W, S, dz, r0c, r0f, CS2, 0.8, h, 1)
+        rel.append(max(np.abs(b[q] - a[q]).max() / np.abs(a[q] - x0).max() for q, x0 in ((2, W), (3, S))))
+    for p, q in zip(rel, rel[1:]):
+        assert 1.8 < p / q < 2.3, rel
+    assert rel[-1] < 0.02
 
 
 def test_acoustic_horizontal_mode_converges_at_second_order():
