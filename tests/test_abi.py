@@ -38,8 +38,15 @@ def test_library_exports_every_declared_symbol(lib):
 
 
 def test_status_strings(lib):
-    for s in range(7):
-        assert lib.asuca_status_string(s)
+    """Every status the header declares has its own message; other values
+    read as unknown."""
+    src = open(os.path.join(ROOT, "include", "asuca.h")).read()
+    codes = {int(v) for v in re.findall(r"\bASUCA_(?:OK|ERR_[A-Z]+)\s*=\s*(\d+)", src)}
+    assert codes == set(range(len(codes))) and len(codes) >= 8
+    msgs = [lib.asuca_status_string(c) for c in sorted(codes)]
+    assert all(msgs) and len(set(msgs)) == len(msgs)
+    unknown = lib.asuca_status_string(max(codes) + 1)
+    assert unknown not in msgs and lib.asuca_status_string(-1) == unknown
 
 
 def test_oracle_is_not_linked_into_the_product():
