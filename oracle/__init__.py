@@ -98,7 +98,7 @@ def lib():
         L.orc_hevi_short_steps.restype = ctypes.c_int
         L.orc_hevi_short_steps.argtypes = [ctypes.c_int, ctypes.c_int]
         L.orc_step_hevi.argtypes = [G, _D, _D, _D, _D, _D, _D, _D, ctypes.c_double, ctypes.c_double, ctypes.c_int,
-                                    ctypes.c_double, ctypes.c_int, _D, _D]
+                                    ctypes.c_double, ctypes.c_int, _D, _D, _D]
         L.orc_set_threads.argtypes = [ctypes.c_int]
         L.orc_get_threads.restype = ctypes.c_int
         _lib = L
@@ -266,16 +266,20 @@ def hevi_short_steps(ns: int, q: int) -> int:
     return int(lib().orc_hevi_short_steps(int(ns), int(q)))
 
 
-def step_hevi(g: Grid, Y, U, V, W, rho0c, rho0f, cs2, beta, ns, dt, nsteps, tend=None):
+def step_hevi(g: Grid, Y, U, V, W, rho0c, rho0f, cs2, beta, ns, dt, nsteps, tend=None, stage_rho=False):
     """nsteps long steps with the acoustic short steps nested in the RK3 stages;
-    returns (Y, U, V, W, s_final, budgets[F+1])."""
+    returns (Y, U, V, W, s_final, budgets[F+1]), and with stage_rho the density
+    of the last step's first two RK stages ([2][nz][ny][nx]) as a seventh item."""
     Y, U, V, W = (_f64(a).copy() for a in (Y, U, V, W))
     rho0c, rho0f = _f64(rho0c), _f64(rho0f)
     tend = None if tend is None else _f64(tend)
     s_final = np.zeros(g.shape[1:])
     bud = np.empty(g.F + 1)
+    srho = np.zeros((2,) + tuple(g.shape[1:])) if stage_rho else None
     lib().orc_step_hevi(g.ref, _p(Y), _p(U), _p(V), _p(W), _p(tend), _p(rho0c), _p(rho0f), float(cs2),
-                        float(beta), int(ns), float(dt), int(nsteps), _p(s_final), _p(bud))
+                        float(beta), int(ns), float(dt), int(nsteps), _p(s_final), _p(bud), _p(srho))
+    if stage_rho:
+        return Y, U, V, W, s_final, bud, srho
     return Y, U, V, W, s_final, bud
 
 

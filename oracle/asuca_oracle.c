@@ -1353,7 +1353,7 @@ int orc_hevi_short_steps(int ns, int q) {
  * column pass.  Fields: U, V [nz][ny][nx], W [nz+1][ny][nx] (lids kept). */
 void orc_step_hevi(const orc_grid *g, double *Y, double *U, double *V, double *W, const double *tend,
                    const double *rho0c, const double *rho0f, double cs2, double beta, int ns, double dt,
-                   int nsteps, double *s_final, double *budgets) {
+                   int nsteps, double *s_final, double *budgets, double *stage_rho) {
     const int nx = g->nx, ny = g->ny, nz = g->nz;
     const size_t plane = (size_t)nx * ny, C = plane * nz, n = (size_t)(2 + g->ntr) * C, CW = C + plane;
     double *Yn = (double *)malloc(n * sizeof(double)), *Ys = (double *)malloc(n * sizeof(double));
@@ -1384,6 +1384,7 @@ void orc_step_hevi(const orc_grid *g, double *Y, double *U, double *V, double *W
             orc_rhs(g, in, Mu, Mv, Mw, tend, R, NULL);
             double *dst = q == 2 ? Y : Ys;
             for (size_t e = 0; e < n; e++) dst[e] = Yn[e] + c[q] * R[e];
+            if (stage_rho && q < 2) memcpy(stage_rho + q * C, Ys, C * sizeof(double));
             in = Ys;
         }
         memcpy(U, Ua, C * sizeof(double));

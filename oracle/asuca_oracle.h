@@ -123,10 +123,11 @@ int orc_hevi_short_steps(int ns, int q);
  * advects the scalars with the short steps' mean effective mass fluxes
  * (U*, V*, (1 - beta) W + beta W'); stage 3's integration is the new
  * momentum state (and s_final [nz][ny][nx], if set).  Then the column pass;
- * budgets as orc_step. */
+ * budgets as orc_step.  stage_rho, if set, receives the density of the first
+ * two RK stages of the last step ([2][nz][ny][nx]). */
 void orc_step_hevi(const orc_grid *g, double *Y, double *U, double *V, double *W, const double *tend,
                    const double *rho0c, const double *rho0f, double cs2, double beta, int ns, double dt,
-                   int nsteps, double *s_final, double *budgets);
+                   int nsteps, double *s_final, double *budgets, double *stage_rho);
 void orc_set_threads(int n);
 int orc_get_threads(void);
 

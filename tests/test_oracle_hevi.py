@@ -9,6 +9,8 @@
   the acoustic integration (1e-13), which holds only if every stage advects
   with exactly the fluxes the acoustic density equation applies, weighted and
   summed over the right short steps.
+* The same holds for the density of the first two RK stages, each against
+  an acoustic integration over its own weight times dt (1e-13).
 * The new momenta are the third stage's integration: orc_acoustic over n_3
   short steps of dt / n_3 from (U, V, W)^n and s^n = rho^n / rho0 - 1, bit
   for bit.
@@ -64,6 +66,26 @@ def test_advected_density_equals_acoustic_density(nsteps, ns, beta):
     assert np.abs(out[0] - rho_ac).max() <= 1e-13 * np.abs(out[0]).max()
     # and the density did move: the acoustic fluxes are not divergence free
     assert np.abs(out[0] - Y[0]).max() > 1e-9 * np.abs(Y[0]).max()
+
+
+@pytest.mark.parametrize("ns,beta", [(6, 0.6), (7, 0.5), (11, 1.0)])
+def test_every_stage_density_equals_its_acoustic_density(ns, beta):
+    """The same consistency inside the step: the density of RK stage q (q = 1,
+    2) equals rho0 (1 + s) after an acoustic integration over the stage's
+    weight times dt (1/3 dt, 1/2 dt) in its own short steps, from the
+    momenta and s at t^n (1e-13).  A stage integrated over the wrong length
+    or from the wrong start fails this."""
+    c, Y, U, V, W, r0c, r0f, dt, _ = _setup()
+    g = oracle.Grid.from_case(c)
+    cs2 = gen.ACOUSTIC["cs2"]
+    *_, srho = oracle.step_hevi(g, Y, U, V, W, r0c, r0f, cs2, beta, ns, dt, 1, stage_rho=True)
+    S0 = Y[0] / r0c[:, None, None] - 1.0
+    for q, cq in ((0, 1.0 / 3.0), (1, 0.5)):
+        nq = oracle.hevi_short_steps(ns, q)
+        Sq = oracle.acoustic(U, V, W, S0, c.dz, r0c, r0f, cs2, beta, cq * dt / nq, nq)[3]
+        rho_ac = r0c[:, None, None] * (1.0 + Sq)
+        assert np.abs(srho[q] - rho_ac).max() <= 1e-13 * np.abs(rho_ac).max(), q
+        assert np.abs(srho[q] - Y[0]).max() > 1e-9 * np.abs(Y[0]).max()
 
 
 def test_new_momenta_are_the_third_stage_integration():

@@ -155,6 +155,45 @@ MUTANTS = [
      "const int n = (int)floor(frac * ns + 0.5);", "const int n = (int)floor(frac * ns);"),
     ("mean vertical flux from the new momentum only",
      "Mw[f * plane + q] += wgt * ((1.0 - beta) * Wc[f] + beta * Wn[f]);", "Mw[f * plane + q] += wgt * Wn[f];"),
+    ("mean i flux of the stage-2 momentum",
+     "Mu[k * plane + q] += wgt * Us[k * plane + q];", "Mu[k * plane + q] += wgt * Up[k * plane + q];"),
+    ("every stage integrates over the whole long step",
+     "c[q] / nq, nq, Ua", "dt / nq, nq, Ua"),
+    ("acoustic j gradient divided by dx",
+     "Vo[c] = V[c] - tau * cs2 * rho0c[k] * (se[no] - se[c]) / dy;",
+     "Vo[c] = V[c] - tau * cs2 * rho0c[k] * (se[no] - se[c]) / dx;"),
+    ("acoustic i divergence divided by dy",
+     "Dh[k] = (Us[c] - Us[k * plane + w]) / dx + (Vs[c] - Vs[k * plane + so]) / dy;",
+     "Dh[k] = (Us[c] - Us[k * plane + w]) / dy + (Vs[c] - Vs[k * plane + so]) / dy;"),
+    ("acoustic lower coefficient with the level below's dz",
+     "lo[r] = k > 0 ? -tau * beta / dz[k] : 0.0;", "lo[r] = k > 0 ? -tau * beta / dz[k - 1] : 0.0;"),
+    ("acoustic face density taken at the centre",
+     "const double g = tau * cs2 * rho0f[f] / dzc;", "const double g = tau * cs2 * rho0c[f] / dzc;"),
+    # more of the step, the damping and the derivatives
+    ("forcing read with i and j swapped",
+     "r += tend[(size_t)(f - 1) * nz * g->ny * g->nx + gidx(g, k, gj, gi)];",
+     "r += tend[(size_t)(f - 1) * nz * g->ny * g->nx + gidx(g, k, gi, gj)];"),
+    ("column physics before the dynamics",
+     "        orc_rk3(g, Y, mu, mv, mw, tend, dt);\n        orc_column(g, Y, dt, pc);",
+     "        orc_column(g, Y, dt, pc);\n        orc_rk3(g, Y, mu, mv, mw, tend, dt);"),
+    ("linear scheme weights swapped",
+     "L = (d0 + 2.0 * d1) / 3.0;", "L = (2.0 * d0 + d1) / 3.0;"),
+    ("open domain reads rho phi as phi",
+     "return Y[(size_t)f * C + o] / Y[o];", "return Y[(size_t)f * C + o];"),
+    ("precipitation left out of the budget",
+     "        orc_budgets(g, Y, csum_value(&tot), budgets);\n    }\n    free(pc);\n}",
+     "        orc_budgets(g, Y, 0.0, budgets);\n    }\n    free(pc);\n}"),
+    ("7-point stencil wraps j by nx",
+     "ju = wrap(j + 1, ny);", "ju = wrap(j + 1, nx);"),
+    ("damping top zone one level short",
+     "if (ntop > 0 && k >= nz - ntop) {", "if (ntop > 0 && k > nz - ntop) {"),
+    ("damping top ramp linear",
+     "top = nu_top * (x * x);", "top = nu_top * x;"),
+    ("tangent of phi = u / rho: density term sign",
+     "dph[q] = (dY[(size_t)f * C + st[q]] - ph[q] * dY[st[q]]) / rho;",
+     "dph[q] = (dY[(size_t)f * C + st[q]] + ph[q] * dY[st[q]]) / rho;"),
+    ("relaxation adjoint without the implicit factor",
+     "lam[nz + k] = lt / (1.0 + r);", "lam[nz + k] = lt;"),
 ]
 
 

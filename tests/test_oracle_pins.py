@@ -553,6 +553,29 @@ def test_damping_mirror_symmetry_and_profile_shape():
     assert col[0] == 1.0 and np.all(np.diff(col) < 0)
 
 
+def test_damping_rate_profile_is_quadratic():
+    """The rate one call applies, recovered from y = 1, target = 0 as
+    nu = (1 / y' - 1) / dt: the full lateral rate on the edge cells, its square
+    root falling by equal amounts per cell to zero at `width` cells from the
+    edge; likewise from the top level down over ntop levels; the larger rate
+    where the zones overlap."""
+    nz, ny, nx, W, ntop, dt = 9, 20, 22, 5, 4, 30.0
+    nu_lat, nu_top = 2e-2, 8e-3
+    one, zero = np.ones((1, nz, ny, nx)), np.zeros((1, nz, ny, nx))
+    p = oracle.damping(one, zero, zero, zero, 0.5, dt, width=W, ntop=ntop, nu_lat=nu_lat, nu_top=nu_top)[0]
+    nu = (1.0 / p - 1.0) / dt
+    lat = nu[0, ny // 2, :W + 2]                     # bottom level, middle row, from the left edge
+    assert abs(lat[0] - nu_lat) <= 1e-12 * nu_lat
+    r = np.sqrt(lat[:W + 1] / nu_lat)
+    assert np.allclose(np.diff(r), -1.0 / W, rtol=0, atol=1e-9) and lat[W] == 0.0 and lat[W + 1] == 0.0
+    top = nu[::-1, ny // 2, nx // 2][:ntop + 1]      # centre column, from the top level down
+    assert abs(top[0] - nu_top) <= 1e-12 * nu_top
+    r = np.sqrt(top / nu_top)
+    assert np.allclose(np.diff(r), -1.0 / ntop, rtol=0, atol=1e-9) and top[ntop] == 0.0
+    corner = nu[nz - 1, 0, W - 2]                    # top level, edge row: lateral rate is the larger
+    assert abs(corner - nu_lat) <= 1e-12 * nu_lat
+
+
 def test_damping_sampled_cells_equal_the_whole_domain():
     """The sampled-cell form (explicit (i, j, k) list, [F][n] arrays) gives the
     whole-domain result at those cells."""
@@ -675,21 +698,29 @@ def test_acoustic_off_centring_changes_the_step_at_second_order():
     assert rel[-1] < 0.02
 
 
-def test_acoustic_horizontal_mode_converges_at_second_order():
-    """A horizontal acoustic mode s = cos(2 pi m i / nx) (constant rho0) has the
-    centred-difference frequency omega = 2 c sin(pi m / nx) / dx; the two-stage
-    short step converges to cos(omega t) s at second order in the step."""
-    nz, ny, nx, m, T, dx = 3, 2, 16, 2, 10.0, 2000.0     # omega T = 1.3, away from an extremum of cos
+@pytest.mark.parametrize("axis", [0, 1])
+def test_acoustic_horizontal_mode_converges_at_second_order(axis):
+    """A horizontal acoustic mode s = cos(2 pi m i / n) along i or j (constant
+    rho0) has the centred-difference frequency omega = 2 c sin(pi m / n) / d,
+    d the spacing along the mode (the other spacing differs); the two-stage
+    short step converges to cos(omega t) s at second order in the step, and
+    the momentum across the mode stays zero."""
+    nz, n, m, T = 3, 16, 2, 10.0                     # omega T = 1.3 / 1.7, away from an extremum of cos
+    dx, dy = (2000.0, 1500.0) if axis == 0 else (1500.0, 2000.0)
+    nx, ny = (n, 2) if axis == 0 else (2, n)
     dz, r0c, r0f = _acoustic_base(nz, gravity=False)
-    mode = np.cos(2 * math.pi * m * np.arange(nx) / nx)
-    S0 = np.broadcast_to(mode[None, None, :], (nz, ny, nx)).copy() * 1e-3
-    omega = 2.0 * math.sqrt(CS2) * math.sin(math.pi * m / nx) / dx
+    mode = np.cos(2 * math.pi * m * np.arange(n) / n)
+    shape = (1, 1, n) if axis == 0 else (1, n, 1)
+    S0 = np.broadcast_to(mode.reshape(shape), (nz, ny, nx)).copy() * 1e-3
+    omega = 2.0 * math.sqrt(CS2) * math.sin(math.pi * m / n) / (dx if axis == 0 else dy)
     errs = []
-    for n in (8, 16, 32, 64):
+    for ns in (8, 16, 32, 64):
         z = np.zeros((nz, ny, nx))
-        out = oracle.acoustic(z, z, np.zeros((nz + 1, ny, nx)), S0, dz, r0c, r0f, CS2, 0.6, T / n, n)
+        out = oracle.acoustic(z, z, np.zeros((nz + 1, ny, nx)), S0, dz, r0c, r0f, CS2, 0.6, T / ns, ns,
+                              dx=dx, dy=dy)
         errs.append(np.max(np.abs(out[3] - math.cos(omega * T) * S0)))
         assert np.max(np.abs(out[2])) <= 1e-15      # no vertical motion from a k-uniform mode
+        assert np.array_equal(out[1 - axis], z)     # none across the mode
     for a, b in zip(errs, errs[1:]):
         assert 3.9 < a / b < 4.1
 
