@@ -194,6 +194,37 @@ MUTANTS = [
      "dph[q] = (dY[(size_t)f * C + st[q]] + ph[q] * dY[st[q]]) / rho;"),
     ("relaxation adjoint without the implicit factor",
      "lam[nz + k] = lt / (1.0 + r);", "lam[nz + k] = lt;"),
+    ("column tangent's diffusion derivative doubled",
+     "w->kcf[k + 1] = 0.5 * dt * K / (zc[k + 1] - zc[k]);", "w->kcf[k + 1] = dt * K / (zc[k + 1] - zc[k]);"),
+    ("column adjoint's diffusion term sign",
+     "if (k > 0) lr -= w->kcf[k] * (psi[k] - psi[k - 1]) * (ph[k] - ph[k - 1]);",
+     "if (k > 0) lr += w->kcf[k] * (psi[k] - psi[k - 1]) * (ph[k] - ph[k - 1]);"),
+    ("step adjoint drops the path through stage 1",
+     "lam[e] += l2[e] + l1[e];", "lam[e] += l2[e];"),
+    ("step tangent builds each stage on the previous one",
+     "dS[e] = dY[e] + c[q] * dR[e];", "dS[e] = dS[e] + c[q] * dR[e];"),
+    ("tangent drops the mass-flux perturbation",
+     "dF = dm * face + m * dface;", "dF = m * dface;"),
+    ("west ghost columns in reverse order",
+     "halo_index(g, 0, f - 1, k, i + 2, j)", "halo_index(g, 0, f - 1, k, -1 - i, j)"),
+    ("north ghosts read from the south strip",
+     "if (j >= g->ny) return ghost[halo_index(g, 3, f - 1, k, j - g->ny, i)];",
+     "if (j >= g->ny) return ghost[halo_index(g, 2, f - 1, k, j - g->ny, i)];"),
+    ("open vertical mass flux one level low",
+     "m = mw[((size_t)(k + 1) * ny + j) * nx + i];", "m = mw[((size_t)k * ny + j) * nx + i];"),
+    ("7-point stencil's lower neighbour taken from above",
+     "in[kd * plane + (long long)j * nx + i] + in[ku * plane + (long long)j * nx + i];",
+     "in[ku * plane + (long long)j * nx + i] + in[ku * plane + (long long)j * nx + i];"),
+    ("damping zone ignores the j edges",
+     "if (j < d) d = j;", "if (j < 0) d = j;"),
+    ("damping overlap takes the smaller rate",
+     "return lat > top ? lat : top;", "return lat > top ? top : lat;"),
+    ("acoustic elimination with the lower coefficient",
+     "di[r] -= m * up[r - 1];", "di[r] -= m * lo[r - 1];"),
+    ("acoustic second stage driven by the starting s",
+     "const double *se = stage == 0 ? S : Ss;", "const double *se = S;"),
+    ("nested step's s without the -1",
+     "Y[k * plane + q] / rho0c[k] - 1.0;", "Y[k * plane + q] / rho0c[k];"),
 ]
 
 
@@ -222,7 +253,7 @@ def test_every_slip_fails_a_pin(tmp_path):
     control = oracle.compile_library(SRC, os.path.join(tmp, "libcontrol.so"))
     rc, log = _run_pins(control)
     assert rc == 0, "the unmutated copy fails the pins:\n" + log
-    with cf.ThreadPoolExecutor(max_workers=max(2, min(8, (os.cpu_count() or 2) // 2))) as ex:
+    with cf.ThreadPoolExecutor(max_workers=max(2, min(6, (os.cpu_count() or 4) - 2))) as ex:
         futs = [ex.submit(_mutant, tmp, q, name, old, new, src) for q, (name, old, new) in enumerate(MUTANTS)]
         results = [f.result() for f in futs]
     # returncode 1: tests ran and at least one failed (not a crash or a collection error)
