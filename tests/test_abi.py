@@ -154,3 +154,46 @@ def test_damping_zone_arguments(lib):
     out = np.zeros(3 * n, dtype=np.uint32)
     assert lib.asuca_debug_damping_cells(16, 12, 5, 2, 1, out.ctypes.data_as(ctypes.c_void_p), n - 1) == asuca.ERR_ARG
     assert lib.asuca_debug_damping_cells(16, 12, 5, 2, 1, None, n) == asuca.ERR_ARG
+
+
+def test_binding_matches_the_header_layouts_and_constants(tmp_path):
+    """A small C program compiled against include/asuca.h prints the size and
+    every member's offset and size of the structures the binding mirrors, and
+    the value of every ASUCA_ constant; the ctypes structures and the module's
+    constants of the same names must agree."""
+    import subprocess
+    structs = {"asuca_grid_desc": asuca.GridDesc, "asuca_state": asuca.StateStruct,
+               "asuca_damping_desc": asuca.DampingDesc, "asuca_acoustic_desc": asuca.AcousticDesc}
+    src = open(os.path.join(ROOT, "include", "asuca.h")).read()
+    names = sorted(set(re.findall(r"\bASUCA_([A-Z][A-Z0-9_]*)\b", src)) - {"H", "BOUNDS_CHECK"})
+    names = [n for n in names if hasattr(asuca, n)]
+    assert {"OK", "ERR_BOUNDS", "FP64", "FP32_MIXED", "LIM_KOREN", "MAX_NZ", "MAX_TRACERS",
+            "KERNEL_STAGE_FACTOR", "TUNE_FUSED_COLUMN", "OP_STEP"} <= set(names)
+    prog = ["#include <stdio.h>", "#include <stddef.h>", '#include "asuca.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        prog.append(f'printf("{cname} %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            prog.append(f'printf("{cname}.{fname} %zu %zu\\n", offsetof({cname}, {fname}), '
+                        f'sizeof((({cname} *)0)->{fname}));')
+    for n in names:
+        prog.append(f'printf("ASUCA_{n} %lld\\n", (long long)(ASUCA_{n}));')
+    prog.append("return 0; }")
+    c = tmp_path / "layout.c"
+    c.write_text("\n".join(prog) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["cc", "-std=c11", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(c)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    seen = 0
+    for line in filter(None, out):
+        key, *vals = line.split()
+        vals = [int(v) for v in vals]
+        if key.startswith("ASUCA_"):
+            assert getattr(asuca, key[len("ASUCA_"):]) == vals[0], key
+        elif "." in key:
+            cname, fname = key.split(".")
+            fld = getattr(structs[cname], fname)
+            assert (fld.offset, fld.size) == tuple(vals), key
+        else:
+            assert ctypes.sizeof(structs[key]) == vals[0], key
+        seen += 1
+    assert seen == len(names) + sum(1 + len(py._fields_) for py in structs.values())
