@@ -197,3 +197,50 @@ def test_binding_matches_the_header_layouts_and_constants(tmp_path):
             assert ctypes.sizeof(structs[key]) == vals[0], key
         seen += 1
     assert seen == len(names) + sum(1 + len(py._fields_) for py in structs.values())
+
+
+def _prototypes():
+    """{name: (return type, [parameter declarations])} from include/*.h"""
+    protos = {}
+    inc = os.path.join(ROOT, "include")
+    for f in os.listdir(inc):
+        if not f.endswith(".h"):
+            continue
+        src = re.sub(r"/\*.*?\*/", "", open(os.path.join(inc, f)).read(), flags=re.S)
+        src = re.sub(r"^\s*#.*$", "", src, flags=re.M)
+        for ret, name, params in re.findall(r"([A-Za-z_][\w \t\*]*?)\s*\b(asuca_[a-z0-9_]+)\s*\(([^;{}]*?)\)\s*;",
+                                            src, flags=re.S):
+            ps = [p.strip() for p in params.split(",")]
+            protos[name] = (" ".join(ret.split()), [] if ps == ["void"] or ps == [""] else ps)
+    return protos
+
+
+def test_binding_signatures_match_the_header_prototypes():
+    """Every ctypes signature has the header prototype's parameter count, a
+    pointer type where the prototype takes a pointer, and the scalar type it
+    declares (double, size_t, long long; int for int and the enums); the
+    return types agree likewise."""
+    protos = _prototypes()
+    assert set(protos) == set(asuca.SIGNATURES)
+
+    def is_ptr(t):
+        return t in (ctypes.c_void_p, ctypes.c_char_p) or isinstance(t, type) and issubclass(t, ctypes._Pointer)
+
+    def scalar(decl):
+        words = decl.replace("const", " ").split()[:-1]          # drop the parameter name
+        base = " ".join(words) if words else decl.split()[0]
+        return {"double": ctypes.c_double, "size_t": ctypes.c_size_t, "long long": ctypes.c_longlong,
+                "int": ctypes.c_int}.get(base, ctypes.c_int if base.startswith("asuca_") else None)
+
+    for name, (ret, params) in protos.items():
+        want_ret, args = asuca.SIGNATURES[name]
+        assert len(args) == len(params), f"{name}: {len(args)} ctypes arguments, header has {len(params)}"
+        for q, (decl, t) in enumerate(zip(params, args)):
+            if "*" in decl:
+                assert is_ptr(t), f"{name} argument {q} ({decl}) is a pointer, binding has {t}"
+            else:
+                assert t is scalar(decl), f"{name} argument {q} ({decl}): binding has {t}"
+        if "*" in ret:
+            assert want_ret is ctypes.c_char_p and "char" in ret, name
+        else:
+            assert want_ret is scalar(ret + " x"), f"{name} returns {ret}, binding has {want_ret}"
