@@ -166,8 +166,8 @@ def _winds_from_psi(psi, dx, dy):
 def make_case(nx: int, ny: int, nz: int, ntracers: int, seed: int, *,
               overturning: bool = True, pattern_seed: int | None = None,
               perturb_seed: int | None = None, smooth_tracers: bool = False,
-              dtype=np.float64) -> Case:
-    """Build one seeded case.
+              dx: float = DX, dy: float = DY, dtype=np.float64) -> Case:
+    """Build one seeded case (horizontal spacing dx, dy; 2 km by default).
 
     pattern_seed draws the bubble/blob/mode parameters (domain-relative, so
     domains of different sizes share a pattern); perturb_seed, when given, adds
@@ -178,7 +178,7 @@ def make_case(nx: int, ny: int, nz: int, ntracers: int, seed: int, *,
         raise ValueError("bad grid size")
     rng = np.random.default_rng(seed if pattern_seed is None else pattern_seed)
     pat = _draw_pattern(rng, ntracers)
-    dx, dy = DX, DY
+    dx, dy = float(dx), float(dy)
     dz = make_dz(nz)
     zf, zc = _levels(dz)
     H = zf[-1]

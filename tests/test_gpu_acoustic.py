@@ -71,6 +71,15 @@ def test_acoustic_matches_oracle(asuca, prec, shape, nshort):
 
 
 @pytest.mark.parametrize("prec", [0, 1])
+def test_acoustic_with_different_spacings_in_i_and_j(asuca, prec):
+    """dx = 2000 m, dy = 1600 m: the gradients and the divergence each take
+    their own direction's spacing."""
+    c = gen.make_case(37, 26, 9, 1, seed=901, dy=1600.0)
+    got, want, lids = _run(asuca, c, prec, 3)
+    _check(asuca, prec, got, want, lids)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("beta,dtau", [(0.5, 2.0), (1.0, 2.0), (0.6, 0.0), (0.55, 5.5)])
 def test_acoustic_weights_and_step_lengths(asuca, prec, beta, dtau):
     c = gen.make_case(29, 17, 9, 1, seed=71)

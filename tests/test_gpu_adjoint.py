@@ -163,10 +163,11 @@ def _gpu_adjoint(asuca, case, lam, nsteps, K, prec=0, lim=0, tend=None, tile_row
 
 
 @pytest.mark.parametrize("lim", [0, 1, 2])
-@pytest.mark.parametrize("shape,ntr,nsteps", [((20, 16, 10), 3, 5), ((37, 13, 7), 2, 4), ((32, 32, 16), 3, 3)])
-def test_adjoint_fp64_matches_oracle(asuca, lim, shape, ntr, nsteps):
+@pytest.mark.parametrize("shape,ntr,nsteps,dy", [((20, 16, 10), 3, 5, 2000.0), ((37, 13, 7), 2, 4, 2000.0),
+                                                 ((32, 32, 16), 3, 3, 2000.0), ((26, 22, 9), 2, 3, 1600.0)])
+def test_adjoint_fp64_matches_oracle(asuca, lim, shape, ntr, nsteps, dy):
     nx, ny, nz = shape
-    c = gen.make_case(nx, ny, nz, ntr, seed=100 + nx)
+    c = gen.make_case(nx, ny, nz, ntr, seed=100 + nx, dy=dy)
     rng = np.random.default_rng(nx)
     lam = rng.standard_normal(c.state().shape)
     tend = rng.uniform(-1e-6, 1e-6, (1 + ntr, nz, ny, nx)) if nx == 37 else None

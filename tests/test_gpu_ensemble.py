@@ -50,6 +50,31 @@ def test_members_equal_single_member_steps(asuca, prec):
         assert float(rel.max()) <= 1e-13
 
 
+@pytest.mark.parametrize("prec", [1, 0])
+def test_members_with_their_own_spacings_against_the_oracle(asuca, prec):
+    """Members whose horizontal spacings differ from each other and between i
+    and j (2000 x 1600 m, 1500 x 2000 m, 2000 x 2000 m): each member against
+    the oracle's step on its own grid."""
+    import torch
+    spacings = [(2000.0, 1600.0), (1500.0, 2000.0), (2000.0, 2000.0)]
+    cases = [gen.make_case(n, n - 5, 10, 2, seed=610 + q, dx=dx, dy=dy)
+             for q, (n, (dx, dy)) in enumerate(zip([36, 44, 29], spacings))]
+    grids = [asuca.Grid.from_case(c, prec=prec) for c in cases]
+    states = [asuca.State.from_case(c, prec=prec) for c in cases]
+    asuca.ensemble_step(grids, states, [c.dt for c in cases], 2)
+    torch.cuda.synchronize()
+    assert asuca.get_status(grids[0]) == asuca.OK
+    tol = 1e-12 if prec == 0 else 2e-5
+    for m, c in enumerate(cases):
+        ref, _ = oracle.step(oracle.Grid.from_case(c), c.state(), c.mu, c.mv, c.mw, c.dt, 2)
+        got = states[m].fields().double().cpu().numpy()
+        for f in range(ref.shape[0]):
+            l2 = np.linalg.norm(got[f] - ref[f]) / np.linalg.norm(ref[f])
+            assert l2 <= tol, (m, f, l2)
+            if prec == 0:
+                assert np.abs(got[f] - ref[f]).max() <= tol * np.abs(ref[f]).max(), (m, f)
+
+
 def test_graph_replay_matches(asuca):
     import torch
     cases = _members([50, 81, 64])

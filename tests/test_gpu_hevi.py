@@ -62,16 +62,17 @@ def _rel(a, b):
 
 
 @pytest.mark.parametrize("prec,tol", [(0, 1e-12), (1, 2e-5)])
-@pytest.mark.parametrize("shape,ntr,lim,ns,beta,nsteps,forced", [
-    ((20, 16, 10), 2, 0, 6, 0.6, 2, False),
-    ((37, 13, 7), 2, 0, 6, 0.6, 2, True),
-    ((32, 32, 16), 3, 1, 4, 0.5, 1, False),
-    ((45, 19, 12), 1, 0, 9, 1.0, 2, False),
-    ((64, 48, 58), 4, 0, 6, 0.6, 1, False),
+@pytest.mark.parametrize("shape,ntr,lim,ns,beta,nsteps,forced,dy", [
+    ((20, 16, 10), 2, 0, 6, 0.6, 2, False, 2000.0),
+    ((37, 13, 7), 2, 0, 6, 0.6, 2, True, 2000.0),
+    ((32, 32, 16), 3, 1, 4, 0.5, 1, False, 2000.0),
+    ((45, 19, 12), 1, 0, 9, 1.0, 2, False, 2000.0),
+    ((64, 48, 58), 4, 0, 6, 0.6, 1, False, 2000.0),
+    ((30, 22, 9), 2, 0, 6, 0.6, 2, False, 1600.0),     # dx != dy
 ])
-def test_hevi_step_against_oracle(asuca, prec, tol, shape, ntr, lim, ns, beta, nsteps, forced):
+def test_hevi_step_against_oracle(asuca, prec, tol, shape, ntr, lim, ns, beta, nsteps, forced, dy):
     nx, ny, nz = shape
-    case = gen.make_case(nx, ny, nz, ntr, seed=700 + nx)
+    case = gen.make_case(nx, ny, nz, ntr, seed=700 + nx, dy=dy)
     tend = np.random.default_rng(4).uniform(-1e-6, 1e-6, (1 + ntr, nz, ny, nx)) if forced else None
     got, ref, _ = _run(asuca, case, prec, lim, ns, beta, nsteps, tend)
     Yg, Ug, Vg, Wg, Sg, Bg = got

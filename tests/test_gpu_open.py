@@ -105,12 +105,13 @@ def test_decomposed_blocks_equal_periodic_step(asuca, prec, shape, ntr, lim, px,
 
 
 @pytest.mark.parametrize("prec,tol", [(0, 1e-12), (1, 2e-5)])
-@pytest.mark.parametrize("shape,ntr,lim", [((40, 24, 12), 3, 0), ((37, 26, 7), 2, 1), ((33, 18, 9), 2, 2),
-                                           ((70, 45, 16), 4, 0)])
-def test_limited_area_step_against_oracle(asuca, prec, tol, shape, ntr, lim):
+@pytest.mark.parametrize("shape,ntr,lim,dy", [((40, 24, 12), 3, 0, 2000.0), ((37, 26, 7), 2, 1, 2000.0),
+                                              ((33, 18, 9), 2, 2, 2000.0), ((70, 45, 16), 4, 0, 2000.0),
+                                              ((38, 22, 10), 2, 0, 1600.0)])
+def test_limited_area_step_against_oracle(asuca, prec, tol, shape, ntr, lim, dy):
     import torch
     nx, ny, nz = shape
-    case = gen.make_case(nx, ny, nz, ntr, seed=500 + nx)
+    case = gen.make_case(nx, ny, nz, ntr, seed=500 + nx, dy=dy)
     mu_x, mv_x = gen.extend_fluxes(case.mu, case.mv)
     mu_x = mu_x.copy()
     mv_x = mv_x.copy()

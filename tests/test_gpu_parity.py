@@ -157,6 +157,28 @@ def test_full_step_fp64_ragged_with_tendencies(asuca, shape, ntr, nsteps):
     assert np.all(np.abs(bud - rbud)[nz_b] <= TOL64 * np.abs(rbud)[nz_b])
 
 
+@pytest.mark.parametrize("prec,tol", [(0, TOL64), (1, TOL32)])
+@pytest.mark.parametrize("mode", ["fused", "separate", "dataflow"])
+def test_full_step_with_different_spacings_in_i_and_j(asuca, prec, tol, mode):
+    """dx = 2000 m, dy = 1600 m (every other case has dx = dy, where a swapped
+    spacing goes unseen): three steps of a ragged grid against the oracle, in
+    each arrangement of the column pass."""
+    import torch
+    c = gen.make_case(37, 26, 9, 2, seed=88, dx=2000.0, dy=1600.0)
+    og, g = _grid_pair(asuca, c, prec)
+    if mode == "separate":
+        asuca.set_tuning(g, asuca.TUNE_FUSED_COLUMN, 0)
+    elif mode == "dataflow":
+        asuca.set_tuning(g, asuca.TUNE_STEP_MODE, 1)
+    ref, rbud = oracle.step(og, c.state(), c.mu, c.mv, c.mw, c.dt, 3)
+    st = asuca.State.from_case(c, prec=prec)
+    bud = asuca.step(g, st, c.dt, 3, budgets=True)
+    torch.cuda.synchronize()
+    assert asuca.get_status(g) == asuca.OK
+    _assert_fields(_np(st), ref, tol, f"dx != dy prec={prec} {mode}", both=(prec == 0))
+    assert np.all(np.abs(bud.cpu().numpy() - rbud) <= tol * np.abs(rbud))
+
+
 @pytest.mark.parametrize("lim", [0, 1, 2])
 def test_full_step_fp32_mixed_32x32x16_20_steps(asuca, lim):
     c = gen.make_config_case("fp64_32x32x16")
