@@ -44,10 +44,10 @@ def _rel(got, ref):
             np.abs(got - ref).max() / max(np.abs(ref).max(), 1e-300))
 
 
-def _gpu_branches(asuca, case, nsteps, lim=0, tend=None, prec=0):
+def _gpu_branches(asuca, case, nsteps, lim=0, tend=None, prec=0, **gkw):
     """GPU-recorded branch bytes in the oracle's layout [nsteps][3][F][nz][ny][nx]."""
     import torch
-    g = asuca.Grid.from_case(case, prec=prec, lim=lim)
+    g = asuca.Grid.from_case(case, prec=prec, lim=lim, **gkw)
     st = asuca.State.from_case(case, prec=prec)
     td = None if tend is None else torch.tensor(tend, dtype=g.torch_dtype, device="cuda")
     b = asuca.record_branches(g, st, case.dt, nsteps, tendencies=td).cpu().numpy()
@@ -146,9 +146,9 @@ def _tie_substituted_branches(og, c, nsteps, gpu_br, own_br, tend=None):
     return out, frac, worst
 
 
-def _gpu_adjoint(asuca, case, lam, nsteps, K, prec=0, lim=0, tend=None, tile_rows=None):
+def _gpu_adjoint(asuca, case, lam, nsteps, K, prec=0, lim=0, tend=None, tile_rows=None, **gkw):
     import torch
-    g = asuca.Grid.from_case(case, prec=prec, lim=lim)
+    g = asuca.Grid.from_case(case, prec=prec, lim=lim, **gkw)
     if tile_rows is not None:
         asuca.set_tuning(g, asuca.TUNE_STAGE_TILE_ROWS, tile_rows)
     st = asuca.State.from_case(case, prec=prec)
@@ -182,6 +182,24 @@ def test_adjoint_fp64_matches_oracle(asuca, lim, shape, ntr, nsteps, dy):
     for name, a, b in zip(("lam0", "gmu", "gmv", "gmw"), got, ref):
         l2, mx = _rel(a, b)
         print(f"  {name}: rel L2 {l2:.3e}, rel max {mx:.3e}")
+        assert l2 <= 1e-12 and mx <= 1e-12, (name, l2, mx)
+
+
+@pytest.mark.parametrize("sed", [0, -1])
+def test_adjoint_fp64_with_another_sedimenting_tracer(asuca, sed):
+    """The first tracer sedimenting, or none (every other case sediments the
+    last one): the FP64 adjoint against the oracle's at 1e-12."""
+    c = gen.make_case(24, 18, 9, 3, seed=131)
+    nsteps = 3
+    lam = np.random.default_rng(17).standard_normal(c.state().shape)
+    og = oracle.Grid.from_case(c, sed=sed)
+    br = _gpu_branches(asuca, c, nsteps, sed_tracer=sed)
+    own = oracle.trajectory_branches(og, c.state(), c.mu, c.mv, c.mw, c.dt, nsteps)
+    traj, _, _ = _tie_substituted_branches(og, c, nsteps, br, own)
+    ref = oracle.step_adj(og, c.state(), c.mu, c.mv, c.mw, c.dt, nsteps, lam, traj_br=traj)
+    got = _gpu_adjoint(asuca, c, lam, nsteps, 2, sed_tracer=sed)
+    for name, a, b in zip(("lam0", "gmu", "gmv", "gmw"), got, ref):
+        l2, mx = _rel(a, b)
         assert l2 <= 1e-12 and mx <= 1e-12, (name, l2, mx)
 
 

@@ -75,6 +75,25 @@ def test_members_with_their_own_spacings_against_the_oracle(asuca, prec):
                 assert np.abs(got[f] - ref[f]).max() <= tol * np.abs(ref[f]).max(), (m, f)
 
 
+@pytest.mark.parametrize("sed", [0, -1])
+def test_members_with_another_sedimenting_tracer_equal_single_member_steps(asuca, sed):
+    """The first tracer sedimenting, or none: members equal their own
+    asuca_step runs bit for bit (those are checked against the oracle for
+    the same settings)."""
+    import torch
+    cases = _members([40, 57, 33], ntr=3, nz=10)
+    grids = [asuca.Grid.from_case(c, prec=asuca.FP32_MIXED, sed_tracer=sed) for c in cases]
+    ens = [asuca.State.from_case(c, prec=asuca.FP32_MIXED) for c in cases]
+    one = [s.clone() for s in ens]
+    asuca.ensemble_step(grids, ens, [c.dt for c in cases], 2)
+    torch.cuda.synchronize()
+    assert asuca.get_status(grids[0]) == asuca.OK
+    for m, (g, c) in enumerate(zip(grids, cases)):
+        asuca.step(g, one[m], c.dt, 2)
+        torch.cuda.synchronize()
+        assert torch.equal(ens[m].fields(), one[m].fields()), f"member {m}"
+
+
 def test_graph_replay_matches(asuca):
     import torch
     cases = _members([50, 81, 64])

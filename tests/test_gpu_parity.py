@@ -179,6 +179,32 @@ def test_full_step_with_different_spacings_in_i_and_j(asuca, prec, tol, mode):
     assert np.all(np.abs(bud.cpu().numpy() - rbud) <= tol * np.abs(rbud))
 
 
+@pytest.mark.parametrize("prec,tol", [(0, TOL64), (1, TOL32)])
+@pytest.mark.parametrize("mode", ["fused", "separate", "dataflow"])
+@pytest.mark.parametrize("sed", [0, 1, -1])
+def test_full_step_with_another_sedimenting_tracer(asuca, prec, tol, mode, sed):
+    """Every other case sediments the last tracer, which the column code takes
+    as a compile-time index: here the first, a middle one, or none, in each
+    arrangement of the column pass, against the oracle (precipitation
+    included)."""
+    import torch
+    c = gen.make_case(29, 21, 10, 3, seed=91)
+    og = oracle.Grid.from_case(c, sed=sed)
+    g = asuca.Grid.from_case(c, prec=prec, sed_tracer=sed)
+    if mode == "separate":
+        asuca.set_tuning(g, asuca.TUNE_FUSED_COLUMN, 0)
+    elif mode == "dataflow":
+        asuca.set_tuning(g, asuca.TUNE_STEP_MODE, 1)
+    ref, rbud = oracle.step(og, c.state(), c.mu, c.mv, c.mw, c.dt, 3)
+    st = asuca.State.from_case(c, prec=prec)
+    bud = asuca.step(g, st, c.dt, 3, budgets=True).cpu().numpy()
+    torch.cuda.synchronize()
+    assert asuca.get_status(g) == asuca.OK
+    _assert_fields(_np(st), ref, tol, f"sed={sed} prec={prec} {mode}", both=(prec == 0))
+    assert np.all(np.abs(bud - rbud) <= tol * np.abs(rbud))
+    assert (rbud[-1] > 0) == (sed >= 0)
+
+
 @pytest.mark.parametrize("lim", [0, 1, 2])
 def test_full_step_fp32_mixed_32x32x16_20_steps(asuca, lim):
     c = gen.make_config_case("fp64_32x32x16")
