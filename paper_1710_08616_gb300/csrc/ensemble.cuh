@@ -84,11 +84,35 @@ __device__ __forceinline__ void cta_copy8(void *dst, const void *src, size_t byt
     for (size_t i = tid; i < bytes / 8; i += nthr) d[i] = q[i];
 }
 
+// The last phase for a column of a member without vertical diffusion (k0 = 0).
+// Its factorisation has no coupling (alpha = gamma = 0), so the sweep left
+// each field's value after relaxation and sedimentation exactly (widened to
+// double) in the scratch; they go to the state as they are.  asuca_step's
+// separate column pass skips the solve for such a grid and leaves the same
+// values, where the back substitution's scaling by rho dz m (about 1) would
+// round them.
+template <typename T, int NF>
+__device__ __forceinline__ void ens_copy_swept(const ColumnParams<T> &p, long long col) {
+    constexpr int NT = NF - 1;
+    constexpr int NQ = NF + 1;
+    const size_t pl = (size_t)p.plane;
+    const size_t ls = (size_t)fscratch_level(p.plane, NQ);
+    double *sc = p.scratch + fscratch_col(col, NQ);
+    for (int k = 0; k < p.nz; k++) {
+        const double *a = fscratch_at(p, sc, k, ls, NQ - 1);
+        size_t o = (size_t)k * pl + (size_t)col;
+        ASUCA_BC(o, (long long)p.nz * (long long)pl, p.status);
+#pragma unroll
+        for (int f = 0; f < NT; f++) p.y[f + 1][o] = (T)a[32 * (2 + f)];
+    }
+}
+
 // Per step: stage 1 (upward march); stage 2 marching downward with the FP64
 // factorisation of every column (FactorHook); stage 3 marching downward with
 // the relaxation, sedimentation and elimination sweep (SweepHook); then the
-// bottom-up back substitution over the flattened columns.  A tile of stages 2
-// and 3 first loads its member's per-level records into shared memory.
+// bottom-up back substitution over the flattened columns (ens_copy_swept for a
+// member without vertical diffusion).  A tile of stages 2 and 3 first loads
+// its member's per-level records into shared memory.
 template <typename T, int NF, int LIM, int TYV>
 __global__ void __launch_bounds__(32 * TYV, StageShape<T, NF, TYV>::MIN_BLOCKS)
     ensemble_kernel(const __grid_constant__ EnsParams<T> e) {
@@ -143,8 +167,12 @@ __global__ void __launch_bounds__(32 * TYV, StageShape<T, NF, TYV>::MIN_BLOCKS)
         for (long long c = gtid; c < e.total_cols; c += nth) {
             const int m = member_of(e.members, e.nmembers, c, false);
             const EnsMember<T> &mb = e.members[m];
-            ColSum<T> cs[NF];
-            column_up_one<T, NF>(mb.col, c - mb.col0, cs);
+            if (mb.col.do_diff) {
+                ColSum<T> cs[NF];
+                column_up_one<T, NF>(mb.col, c - mb.col0, cs);
+            } else {
+                ens_copy_swept<T, NF>(mb.col, c - mb.col0);
+            }
         }
         if (!ens_barrier(e.bar_count, e.bar_gen, target, e.status)) return;
     }

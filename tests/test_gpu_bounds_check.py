@@ -10,7 +10,7 @@ top-down half in stage 3 (the nested acoustic step's arrangement, reached
 through the limited-area step) and as separate launches, ragged sizes, forcing,
 the 4x4x3 minimum and the 128-level, 8-tracer limit; the adjoint (branch-
 recording stages, the column pass with its record); the ensemble's persistent
-kernel.  Every call must leave the status word at ASUCA_OK, and every result
+kernel, with and without vertical diffusion.  Every call must leave the status word at ASUCA_OK, and every result
 must equal the normal build's bit for bit (the checks add integer work only).
 """
 import os
@@ -84,15 +84,16 @@ def _cases(asuca):
         ok(g, f"adjoint_p{prec}")
         for k, r in zip(("l0", "gmu", "gmv", "gmw"), res):
             out[f"adjoint_p{prec}_{k}"] = r.cpu().numpy()
-    # ensemble: the persistent kernel
+    # ensemble: the persistent kernel, with and without vertical diffusion
     cases = gen.make_ensemble_cases(sizes=[36, 50, 29], nz=9, ntracers=2)
     for prec in (asuca.FP64, asuca.FP32_MIXED):
-        grids = [asuca.Grid.from_case(cc, prec=prec) for cc in cases]
-        states = [asuca.State.from_case(cc, prec=prec) for cc in cases]
-        asuca.ensemble_step(grids, states, [cc.dt for cc in cases], 2)
-        ok(grids[0], f"ensemble_p{prec}")
-        for m, s in enumerate(states):
-            out[f"ensemble_p{prec}_m{m}"] = s.fields().cpu().numpy()
+        for k0 in (50.0, 0.0):
+            grids = [asuca.Grid.from_case(cc, prec=prec, k0=k0) for cc in cases]
+            states = [asuca.State.from_case(cc, prec=prec) for cc in cases]
+            asuca.ensemble_step(grids, states, [cc.dt for cc in cases], 2)
+            ok(grids[0], f"ensemble_p{prec}_k{k0:g}")
+            for m, s in enumerate(states):
+                out[f"ensemble_p{prec}_k{k0:g}_m{m}"] = s.fields().cpu().numpy()
     return out
 
 

@@ -94,6 +94,28 @@ def test_members_with_another_sedimenting_tracer_equal_single_member_steps(asuca
         assert torch.equal(ens[m].fields(), one[m].fields()), f"member {m}"
 
 
+@pytest.mark.parametrize("prec", [1, 0])
+@pytest.mark.parametrize("ntr,gkw", [(3, dict(lim=1)), (3, dict(lim=2)), (2, dict(tau_theta=0.0, k0=0.0, v_sed=0.0)),
+                                     (2, dict(k0=0.0)), (0, dict())])
+def test_members_equal_single_member_steps_across_settings(asuca, prec, ntr, gkw):
+    """The other limiters, the column physics switched off in part or whole,
+    and no tracers: members equal their own asuca_step runs bit for bit."""
+    import torch
+    cases = _members([44, 29, 61], ntr=ntr, nz=9)
+    grids = [asuca.Grid.from_case(c, prec=prec, **gkw) for c in cases]
+    ens = [asuca.State.from_case(c, prec=prec) for c in cases]
+    one = [s.clone() for s in ens]
+    bud = asuca.ensemble_step(grids, ens, [c.dt for c in cases], 2, budgets=True)
+    torch.cuda.synchronize()
+    assert asuca.get_status(grids[0]) == asuca.OK
+    for m, (g, c) in enumerate(zip(grids, cases)):
+        b1 = asuca.step(g, one[m], c.dt, 2, budgets=True)
+        torch.cuda.synchronize()
+        assert torch.equal(ens[m].fields(), one[m].fields()), f"member {m}"
+        rel = (bud[m] - b1).abs() / b1.abs().clamp_min(1e-300)
+        assert float(rel.max()) <= 1e-13
+
+
 def test_graph_replay_matches(asuca):
     import torch
     cases = _members([50, 81, 64])
