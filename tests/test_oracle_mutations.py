@@ -28,6 +28,10 @@ SRC = os.path.join(ROOT, "oracle", "asuca_oracle.c")
 PIN_FILES = ["tests/test_oracle_pins.py", "tests/test_oracle_adjoint.py", "tests/test_oracle_open.py",
              "tests/test_oracle_hevi.py"]
 
+# the RK3 stage weights, as written in each step of the oracle, and a slip of them
+W3 = "const double c[3] = {dt / 3.0, dt / 2.0, dt};"
+W2 = "const double c[3] = {dt / 2.0, dt / 2.0, dt};"
+
 # (name, original text, slip): Koren limiter and upwind face
 MUTANTS = [
     ("koren kappa weights swapped",
@@ -225,6 +229,43 @@ MUTANTS = [
      "const double *se = stage == 0 ? S : Ss;", "const double *se = S;"),
     ("nested step's s without the -1",
      "Y[k * plane + q] / rho0c[k] - 1.0;", "Y[k * plane + q] / rho0c[k];"),
+    # the RK weights and budgets of the other steps, forcing in the window and
+    # the open domain, the precipitation sum, the remaining index slips
+    ("stage states of the derivatives: first weight 1/2",
+     W3 + "\n    double *outs[3]", W2 + "\n    double *outs[3]"),
+    ("tangent-linear step: first weight 1/2",
+     W3 + "\n    memcpy(Y, Y0, n * sizeof(double));\n    memcpy(dY",
+     W2 + "\n    memcpy(Y, Y0, n * sizeof(double));\n    memcpy(dY"),
+    ("adjoint step: first weight 1/2",
+     W3 + "\n    memcpy(lam, lam_final", W2 + "\n    memcpy(lam, lam_final"),
+    ("branch trajectory: first weight 1/2",
+     W3 + "\n    memcpy(Y, Y0, n * sizeof(double));\n    for (int s = 0; s < nsteps; s++) {\n        const double *in = Y;",
+     W2 + "\n    memcpy(Y, Y0, n * sizeof(double));\n    for (int s = 0; s < nsteps; s++) {\n        const double *in = Y;"),
+    ("open step: first weight 1/2",
+     W3 + "\n    for (int s = 0; s < nsteps; s++) {\n        memcpy(Yn, Y",
+     W2 + "\n    for (int s = 0; s < nsteps; s++) {\n        memcpy(Yn, Y"),
+    ("nested step: first weight 1/2",
+     W3 + "\n    for (int step = 0; step < nsteps; step++) {", W2 + "\n    for (int step = 0; step < nsteps; step++) {"),
+    ("open budget without the precipitation",
+     "csum_add(&tot, pc[(size_t)j * g->nx + i]);\n        orc_budgets(g, Y, csum_value(&tot), budgets);\n    }\n    free(Yn);",
+     "csum_add(&tot, pc[(size_t)j * g->nx + i]);\n        orc_budgets(g, Y, 0.0, budgets);\n    }\n    free(Yn);"),
+    ("nested step's budget without the precipitation",
+     "for (size_t q = 0; q < plane; q++) csum_add(&tot, pc[q]);\n        orc_budgets(g, Y, csum_value(&tot), budgets);",
+     "for (size_t q = 0; q < plane; q++) csum_add(&tot, pc[q]);\n        orc_budgets(g, Y, 0.0, budgets);"),
+    ("7-point stencil wraps i by ny",
+     "iu = wrap(i + 1, nx);", "iu = wrap(i + 1, ny);"),
+    ("window without the forcing",
+     "rk3_patch(g, &p, P, mu, mv, mw, tend, dt, margin, 2);", "rk3_patch(g, &p, P, mu, mv, mw, NULL, dt, margin, 2);"),
+    ("open domain without the forcing",
+     "if (tend && f > 0) r += tend[o - (size_t)nz * ny * nx];",
+     "if (0 && tend && f > 0) r += tend[o - (size_t)nz * ny * nx];"),
+    ("precipitation of a column overwritten each step",
+     "if (precip_col) precip_col[(size_t)lj * p->pw + li] += pr;",
+     "if (precip_col) precip_col[(size_t)lj * p->pw + li] = pr;"),
+    ("mean j flux of the stage-2 momentum",
+     "Mv[k * plane + q] += wgt * Vs[k * plane + q];", "Mv[k * plane + q] += wgt * Vp[k * plane + q];"),
+    ("sampled damping cells with i and j swapped",
+     "i = ijk[3 * c];\n            j = ijk[3 * c + 1];", "j = ijk[3 * c];\n            i = ijk[3 * c + 1];"),
 ]
 
 

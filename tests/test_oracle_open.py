@@ -4,6 +4,9 @@ orc_step_open), CPU only.
 * With the periodic continuation as ghosts and the periodic face fluxes
   extended by the last face, the open right-hand side equals the periodic one
   bit for bit (every limiter, with forcing).
+* With no lateral mass flux the ghosts do not matter, and two open steps
+  (forcing, column physics) equal two periodic steps bit for bit, budgets
+  and precipitation included.
 * A constant mixing ratio, with the same constant in the ghosts, stays
   constant under non-divergent fluxes (3 steps, 1e-13).
 * Inflow: first-order upwind at Courant number 1 (u = 16, dt = 128,
@@ -37,6 +40,26 @@ def test_open_rhs_with_periodic_ghosts_equals_periodic_rhs(lim):
     a = oracle.rhs_open(g, Y, mu_x, mv_x, c.mw, ghost, tend=tend)
     b = oracle.rhs(g, Y, c.mu, c.mv, c.mw, tend=tend)
     assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("lim", [0, 1])
+def test_open_step_without_lateral_flow_equals_periodic_step(lim):
+    """With no mass crossing any lateral face (MU = MV = 0 everywhere, the outer
+    faces included) the ghosts enter only multiplied by a zero flux, so two
+    open steps with forcing and the column physics equal two periodic steps
+    bit for bit, budgets and precipitation included: the stage weights, the
+    column pass and the budget sums of the open step are the periodic one's."""
+    c = gen.make_case(18, 14, 10, 3, seed=8)
+    g = oracle.Grid.from_case(c, lim=lim)
+    Y = c.state()
+    tend = np.random.default_rng(2).uniform(-1e-6, 1e-6, (g.F - 1,) + Y.shape[1:])
+    zu, zv = np.zeros_like(c.mu), np.zeros_like(c.mv)
+    mu_x, mv_x = gen.extend_fluxes(zu, zv)
+    ghost = gen.halo_periodic(_phi(Y))
+    a, ba = oracle.step_open(g, Y, mu_x, mv_x, c.mw, ghost, c.dt, 2, tend=tend)
+    b, bb = oracle.step(g, Y, zu, zv, c.mw, c.dt, 2, tend=tend)
+    assert np.array_equal(a, b)
+    assert np.array_equal(ba, bb) and ba[-1] > 0.0
 
 
 def test_open_step_preserves_constant_mixing_ratio():

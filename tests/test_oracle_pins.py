@@ -344,13 +344,15 @@ def test_relaxation_closed_form_and_fixed_point():
 
 # ------------------------------------------------------------------ windows
 
-def test_window_step_equals_full_domain_step():
+@pytest.mark.parametrize("forced", [False, True])
+def test_window_step_equals_full_domain_step(forced):
     c = gen.make_config_case("fp64_32x32x16")
     g = oracle.Grid.from_case(c)
     Y0 = c.state()
-    Yf, _ = oracle.step(g, Y0, c.mu, c.mv, c.mw, c.dt, 2)
+    tend = np.random.default_rng(4).uniform(-1e-6, 1e-6, (g.F - 1,) + Y0.shape[1:]) if forced else None
+    Yf, _ = oracle.step(g, Y0, c.mu, c.mv, c.mw, c.dt, 2, tend=tend)
     for (i0, j0, w, h) in [(30, 5, 4, 3), (0, 0, 1, 1), (31, 31, 2, 2)]:
-        win = oracle.step_window(g, Y0, c.mu, c.mv, c.mw, c.dt, 2, i0, j0, w, h)
+        win = oracle.step_window(g, Y0, c.mu, c.mv, c.mw, c.dt, 2, i0, j0, w, h, tend=tend)
         ii = [(i0 + q) % c.nx for q in range(w)]
         jj = [(j0 + q) % c.ny for q in range(h)]
         ref = Yf[:, :, jj][:, :, :, ii]
