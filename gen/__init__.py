@@ -5,7 +5,7 @@ grid spacing, the initial prognostic fields, the (given, steady) mass fluxes
 and the time step length that both implementations take as inputs.
 """
 from .fields import (  # noqa: F401
-    CONFIGS, SEED_BASE, Case, make_dz, make_case, make_config_case,
+    CONFIGS, SEED_BASE, DX, DY, Case, make_dz, make_case, make_config_case,
     make_ensemble_cases, ensemble_sizes, DAMPING, make_boundary_data,
     ACOUSTIC, make_acoustic_state, halo_periodic, halo_strips, extend_fluxes, split_extent,
     subdomain, make_open_boundary, HEVI, make_hevi_state,

@@ -2,7 +2,8 @@
 
 * dot-product tests <TL dx, dy> = <dx, AD dy> for the RHS, the column pass
   and whole steps (branches frozen; exact up to rounding);
-* the TL against central differences of the nonlinear oracle;
+* the TL against central differences of the nonlinear oracle (also with
+  dx != dy);
 * the adjoint gradient of J = 1/2 sum (q - q_target)^2 against central
   differences (eps = 1e-6) on seeded directions scaled by each field's RMS,
   redrawing any direction whose perturbed trajectories change a limiter
@@ -15,8 +16,8 @@ import gen
 import oracle
 
 
-def _case(nx=12, ny=10, nz=8, ntr=2, seed=5):
-    c = gen.make_case(nx, ny, nz, ntr, seed=seed)
+def _case(nx=12, ny=10, nz=8, ntr=2, seed=5, dy=gen.DY):
+    c = gen.make_case(nx, ny, nz, ntr, seed=seed, dy=dy)
     return c, oracle.Grid.from_case(c)
 
 
@@ -49,8 +50,9 @@ def test_rhs_dot_product(lim):
     assert abs(lhs - rhs) <= 1e-12 * max(abs(lhs), abs(rhs))
 
 
-def test_rhs_tl_matches_central_differences():
-    c, g = _case()
+@pytest.mark.parametrize("dy", [gen.DY, 1500.0])
+def test_rhs_tl_matches_central_differences(dy):
+    c, g = _case(dy=dy)
     rng = np.random.default_rng(2)
     Y = c.state()
     dY, dmu, dmv, dmw = _dirs(rng, c)
