@@ -398,17 +398,20 @@ def test_gradcheck_through_autograd_function(asuca):
     assert torch.autograd.gradcheck(f, (q0, mu), eps=1e-6, atol=1e-9, rtol=1e-6)
 
 
-def test_fp32_adjoint_against_oracle_along_its_branches(asuca):
+@pytest.mark.parametrize("gkw,okw", [(dict(), dict()), (dict(k0=0.0), dict(k0=0.0)),
+                                     (dict(tau_theta=0.0, k0=0.0, v_sed=0.0), dict(tau=0.0, k0=0.0, vsed=0.0))])
+def test_fp32_adjoint_against_oracle_along_its_branches(asuca, gkw, okw):
     """The FP32 adjoint linearises the FP32 forward pass, whose branches differ
     from the FP64 pass at faces whose limiter arguments are rounding noise; it is
-    compared with the FP64 oracle adjoint taken along the FP32 pass's branches."""
+    compared with the FP64 oracle adjoint taken along the FP32 pass's branches
+    (with the column physics on, without vertical diffusion, and with none)."""
     c = gen.make_case(32, 24, 16, 3, seed=41)
     lam = np.random.default_rng(2).standard_normal(c.state().shape)
     n = 5
-    br = _gpu_branches(asuca, c, n, prec=1)
-    og = oracle.Grid.from_case(c)
+    br = _gpu_branches(asuca, c, n, prec=1, **gkw)
+    og = oracle.Grid.from_case(c, **okw)
     ref = oracle.step_adj(og, c.state(), c.mu, c.mv, c.mw, c.dt, n, lam, traj_br=br)
-    a32 = _gpu_adjoint(asuca, c, lam, n, n, prec=1)
+    a32 = _gpu_adjoint(asuca, c, lam, n, n, prec=1, **gkw)
     for name, x, y in zip(("lam0", "gmu", "gmv", "gmw"), a32, ref):
         l2, _ = _rel(x, y)
         assert l2 <= 1e-4, (name, l2)
