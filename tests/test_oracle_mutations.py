@@ -301,6 +301,37 @@ MUTANTS = [
      "r * (THETA_REF0 + THETA_REF_LAPSE * zc[k])) / (1.0 + r);"),
     ("column adjoint's sedimentation without dz",
      "lq[k] = nu * g->dz[k] / (g->dz[k] + dt * g->vsed);", "lq[k] = nu / (g->dz[k] + dt * g->vsed);"),
+    ("column adjoint's diffusion right-hand side without the density",
+     "d[k] = w->Yb[k] * lu[k];", "d[k] = lu[k];"),
+    ("column adjoint's upper face term with the lower face's weight",
+     "if (k < nz - 1) lr -= w->kcf[k + 1] * (psi[k] - psi[k + 1]) * (ph[k] - ph[k + 1]);",
+     "if (k < nz - 1) lr -= w->kcf[k] * (psi[k] - psi[k + 1]) * (ph[k] - ph[k + 1]);"),
+    ("column adjoint's result without dz",
+     "lu[k] = g->dz[k] * psi[k];", "lu[k] = psi[k];"),
+    ("column adjoint's relaxation drops the reference profile",
+     "lam[k] += lt * r * (THETA_REF0 + THETA_REF_LAPSE * zc[k]) / (1.0 + r);", "lam[k] += lt * r / (1.0 + r);"),
+    ("south ghost rows in reverse order",
+     "if (j < 0) return ghost[halo_index(g, 2, f - 1, k, j + 2, i)];",
+     "if (j < 0) return ghost[halo_index(g, 2, f - 1, k, -1 - j, i)];"),
+    ("south and north strips as long as the west and east ones",
+     "const size_t len = strip < 2 ? (size_t)g->ny : (size_t)g->nx;",
+     "const size_t len = strip < 2 ? (size_t)g->ny : (size_t)g->ny;"),
+    ("7-point stencil's lower j neighbour two rows away",
+     "const int jd = wrap(j - 1, ny), ju = wrap(j + 1, ny);", "const int jd = wrap(j - 2, ny), ju = wrap(j + 1, ny);"),
+    ("damping weight of the first dataset taken as 1 - tratio",
+     "const double ptb = mtratio * (ref[q] + b0[q])", "const double ptb = (1.0 - tratio) * (ref[q] + b0[q])"),
+    ("acoustic vertical force with the face density below",
+     "const double g = tau * cs2 * rho0f[f] / dzc;", "const double g = tau * cs2 * rho0f[f - 1] / dzc;"),
+    ("acoustic elimination of the right-hand side sign",
+     "rhs[r] -= m * rhs[r - 1];", "rhs[r] += m * rhs[r - 1];"),
+    ("nested step keeps the old V",
+     "memcpy(V, Va, C * sizeof(double));", "memcpy(V, V, C * sizeof(double));"),
+    ("linear scheme recorded as the 2r branch",
+     "br = 2;\n        L = (d0 + 2.0 * d1) / 3.0;", "br = 1;\n        L = (d0 + 2.0 * d1) / 3.0;"),
+    ("branch trajectory builds each stage on the previous one",
+     "S[e] = Y[e] + c[q] * R[e];", "S[e] = S[e] + c[q] * R[e];"),
+    ("step adjoint's first stage with the second weight",
+     "mu_r[e] = c[0] * l1[e];", "mu_r[e] = c[1] * l1[e];"),
 ]
 
 

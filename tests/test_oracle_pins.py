@@ -518,6 +518,21 @@ def test_damping_strong_limit_is_the_interpolated_boundary_state(tratio):
     assert np.array_equal(out[:, ~edge], Y[:, ~edge])
 
 
+def test_damping_strong_limit_with_independent_weights():
+    """The target weights the two boundary datasets by mtratio and tratio
+    independently (Sec. 2.1's damping kernel; they need not add to one): with
+    a very large rate the edge cells land on mtratio (ref + bnd0) +
+    tratio (ref + bnd1)."""
+    F, nz, ny, nx = 2, 4, 8, 9
+    Y, R, B0, B1 = _damp_fields(F, nz, ny, nx, 5)
+    out = oracle.damping(Y, R, B0, B1, 0.3, 1.0, width=1, ntop=0, nu_lat=1e15, nu_top=0.0, mtratio=0.55)
+    want = 0.55 * (R + B0) + 0.3 * (R + B1)
+    edge = np.zeros((nz, ny, nx), bool)
+    edge[:, 0, :] = edge[:, -1, :] = edge[:, :, 0] = edge[:, :, -1] = True
+    assert np.max(np.abs(out[:, edge] - want[:, edge])) <= 1e-12 * np.abs(want).max()
+    assert np.array_equal(out[:, ~edge], Y[:, ~edge])
+
+
 def test_damping_is_backward_euler_of_the_relaxation_ode():
     """Repeated calls with a fixed target integrate dy/dt = -nu (y - target):
     the result stays between y0 and the target for any step (unconditionally
