@@ -332,6 +332,22 @@ MUTANTS = [
      "S[e] = Y[e] + c[q] * R[e];", "S[e] = S[e] + c[q] * R[e];"),
     ("step adjoint's first stage with the second weight",
      "mu_r[e] = c[0] * l1[e];", "mu_r[e] = c[1] * l1[e];"),
+    ("a stage may get no short step",
+     "return n < 1 ? 1 : n;", "return n;"),
+    ("acoustic momentum unknown stored a face low",
+     "else Wn[(r + 1) / 2] = x;", "else Wn[(r - 1) / 2] = x;"),
+    ("acoustic lower coefficient's sign",
+     "lo[r] = k > 0 ? -tau * beta / dz[k] : 0.0;", "lo[r] = k > 0 ? tau * beta / dz[k] : 0.0;"),
+    ("acoustic density equation reads the lids' momenta",
+     "const double Wk = k > 0 ? W[k] : 0.0, Wk1 = k < nz - 1 ? W[k + 1] : 0.0;",
+     "const double Wk = W[k], Wk1 = W[k + 1];"),
+    ("first-order upwind recorded as the cap branch",
+     "br = 0;\n        L = 0.0;\n    } else if (lim == 1)", "br = 3;\n        L = 0.0;\n    } else if (lim == 1)"),
+    ("relaxation toward 300 K at every height",
+     "th = (th + r * (THETA_REF0 + THETA_REF_LAPSE * zc[k])) / (1.0 + r);\n            Y[fs + k * cs]",
+     "th = (th + r * (THETA_REF0)) / (1.0 + r);\n            Y[fs + k * cs]"),
+    ("precipitation with an extra factor dx",
+     "*precip += dt * P * g->dx * g->dy;", "*precip += dt * P * g->dx * g->dy * g->dx;"),
 ]
 
 
