@@ -70,6 +70,32 @@ def _recorded_traffic(kernel, cells):
     return _recorded(kernel, "bytes_per_cell", cells)
 
 
+def _floor_and_dram(kern, F, s, C, ms, steps, peak):
+    """Two more fractions of the measured HBM peak over the timed region (ms for
+    `steps` steps of C cells): the compulsory floor (read the state and M once,
+    write the state once: 2F+3 values per cell and step), and the DRAM rate the
+    recorded ncu traffic of the timed launches implies (kern: the per-kernel
+    report, each with its launches and recorded bytes per launch; None when a
+    kernel that moves algorithmic bytes has no current record)."""
+    out = {"floor_bytes_per_cell": (2 * F + 3) * s, "floor_frac": None, "dram_gbs_ncu": None,
+           "dram_frac_ncu": None}
+    try:
+        out["floor_frac"] = (2 * F + 3) * s * C * steps / (ms * 1e-3) / 1e9 / peak
+        total = 0.0
+        for v in kern.values():
+            if v.get("algo_bytes_per_launch", 0.0) > 0.0:
+                t = v.get("traffic_bytes_per_launch")
+                if t is None:
+                    return out
+                total += t * v["launches"]
+        if total > 0.0:
+            out["dram_gbs_ncu"] = total / (ms * 1e-3) / 1e9
+            out["dram_frac_ncu"] = out["dram_gbs_ncu"] / peak
+    except (ArithmeticError, KeyError, TypeError, ValueError):
+        pass
+    return out
+
+
 # FP64 pipe: 2 DFMA/DADD/DMUL per clock per SM (ncu's
 # sm__sass_thread_inst_executed_op_dfma_pred_on peak), 152 SMs, 2070 MHz maximum clock
 FP64_INST_PEAK = 2 * 152 * 2.07e9
@@ -899,6 +925,7 @@ def run_ours(args):
                 "traffic": _recorded_traffic(dname, C),
                 "step_frac": (10 * F + 8) * s * C / (ms / args.steps * 1e-3) / 1e9 / hbm_peak,
                 "step_model_bytes_per_cell": (10 * F + 8) * s, "kernels": kern}
+    roofline.update(_floor_and_dram(kern, F, s, C, ms, args.steps, hbm_peak))
 
     # ---- e2e through the C ABI with pinned host buffers, copies inside the timed region
     e2e = None

@@ -3,7 +3,8 @@ kernels as they are: each record's sources hash to the value stored with it,
 so the benchmark line carries the measured DRAM traffic of the dominant
 kernel rather than null.  The recorded traffic per cell also stays within a
 few percent of the kernels' algorithmic bytes (FP32, 10 fields), the figure
-the roofline divides by.
+the roofline divides by.  The benchmark's compulsory-floor fraction and its
+DRAM rate from the recorded traffic are checked on a report of known figures.
 """
 import json
 import os
@@ -38,3 +39,23 @@ def test_recorded_traffic_is_close_to_the_algorithmic_bytes(kernel):
     per_cell = bench._recorded_traffic(kernel, 1)
     assert per_cell is not None
     assert 0.95 * ALGO[kernel] <= per_cell <= 1.1 * ALGO[kernel], (kernel, per_cell, ALGO[kernel])
+
+
+def test_floor_and_dram_fractions():
+    """The compulsory-floor fraction and the DRAM rate from the recorded
+    traffic, on a report shaped like the benchmark's (100 steps of the
+    1024x1024x58 workload in 828.7 ms against a 6770.5 GB/s peak)."""
+    C, peak, ms = 60817408, 6770.5, 828.7393
+    per_cell = {"stage": (92, 96.42), "stage2_factor": (156, 157.18), "stage3_column": (176, 175.81),
+                "column": (128, 126.43)}
+    kern = {k: {"launches": 100, "algo_bytes_per_launch": a * C, "traffic_bytes_per_launch": t * C}
+            for k, (a, t) in per_cell.items()}
+    kern["budget_reduce"] = {"launches": 100, "algo_bytes_per_launch": 0.0, "traffic_bytes_per_launch": None}
+    out = bench._floor_and_dram(kern, 10, 4, C, ms, 100, peak)
+    assert out["floor_bytes_per_cell"] == 92
+    assert abs(out["floor_frac"] - 92 * C * 100 / (ms * 1e-3) / 1e9 / peak) < 1e-12
+    dram = sum(t for _, t in per_cell.values()) * C * 100 / (ms * 1e-3) / 1e9
+    assert abs(out["dram_gbs_ncu"] - dram) < 1e-6 * dram and abs(out["dram_frac_ncu"] - dram / peak) < 1e-12
+    kern["stage"]["traffic_bytes_per_launch"] = None          # a kernel without a current record
+    assert bench._floor_and_dram(kern, 10, 4, C, ms, 100, peak)["dram_gbs_ncu"] is None
+    assert bench._floor_and_dram({}, 10, 4, C, 0.0, 100, peak)["floor_frac"] is None
