@@ -254,10 +254,39 @@ def cpu_oracle_rate(min_seconds=10.0, nx=256, ny=256, steps_cap=50):
         el = time.perf_counter() - t0
         if el >= min_seconds or n >= steps_cap:
             break
-    return {"value": case.cells * n / el, "unit": UNIT, "cores": oracle.get_threads(),
-            "kind": "oracle",
-            "sample": f"{n} step(s) of a {nx}x{ny}x58 periodic domain with 8 tracers (same per-cell "
-                      f"work as the 1024x1024x58 workload), {el:.1f} s, FP64, OpenMP over j"}
+    out = {"value": case.cells * n / el, "unit": UNIT, "cores": oracle.get_threads(),
+           "kind": "oracle",
+           "sample": f"{n} step(s) of a {nx}x{ny}x58 periodic domain with 8 tracers (same per-cell "
+                     f"work as the 1024x1024x58 workload), {el:.1f} s, FP64, OpenMP over j"}
+    out["single_thread"] = _cpu_oracle_rate_one_thread(min_seconds / 2, steps_cap)
+    return out
+
+
+def _cpu_oracle_rate_one_thread(min_seconds, steps_cap, n=128):
+    """The same oracle step on one host thread, on an n x n x 58 sample (None
+    if it cannot be timed); the thread count is restored afterwards."""
+    import gen
+    import oracle
+    threads = oracle.get_threads()
+    try:
+        oracle.set_threads(1)
+        case = gen.make_case(n, n, 58, 8, seed=gen.SEED_BASE + 4)
+        g = oracle.Grid.from_case(case)
+        Y = case.state()
+        t0 = time.perf_counter()
+        k = 0
+        while True:
+            Y, _ = oracle.step(g, Y, case.mu, case.mv, case.mw, case.dt, 1)
+            k += 1
+            el = time.perf_counter() - t0
+            if el >= min_seconds or k >= steps_cap:
+                break
+        return {"value": case.cells * k / el, "unit": UNIT, "cores": 1,
+                "sample": f"{k} step(s) of a {n}x{n}x58 periodic domain with 8 tracers, {el:.1f} s, FP64"}
+    except (OSError, RuntimeError, ValueError, ArithmeticError):
+        return None
+    finally:
+        oracle.set_threads(threads)
 
 
 # ---------------------------------------------------------------- reference arm
