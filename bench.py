@@ -259,7 +259,25 @@ def cpu_oracle_rate(min_seconds=10.0, nx=256, ny=256, steps_cap=50):
            "sample": f"{n} step(s) of a {nx}x{ny}x58 periodic domain with 8 tracers (same per-cell "
                      f"work as the 1024x1024x58 workload), {el:.1f} s, FP64, OpenMP over j"}
     out["single_thread"] = _cpu_oracle_rate_one_thread(min_seconds / 2, steps_cap)
+    out["host"] = _host_cpu()
     return out
+
+
+def _host_cpu():
+    """The host's processor model (lscpu, where present), architecture and
+    logical CPU count."""
+    import platform
+    import subprocess
+    model = None
+    try:
+        r = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10)
+        for line in r.stdout.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return {"cpu_model": model, "arch": platform.machine(), "logical_cpus": os.cpu_count()}
 
 
 def _cpu_oracle_rate_one_thread(min_seconds, steps_cap, n=128):
